@@ -1,0 +1,112 @@
+"""Assembled finite-element operators over the master unknowns (FP64).
+
+Sec. 3.1 defines the discretisation: the mass matrix M_kl = int b_k b_l, the
+one-body matrix (H1)_kl = int b_k H1 b_l and every integral by GLL quadrature
+on the cell nodes.  With collocated GLL quadrature the cell matrices of a cube
+of side h are (1D factors on [0,1]; Khat the 1D stiffness, W = diag(w)):
+
+  stiffness  A_K = h (Khat (x) W (x) W + W (x) Khat (x) W + W (x) W (x) Khat)
+  mass       M_K = h^3 W (x) W (x) W      (diagonal)
+  potential  F_K[f] = h^3 diag(w (x) w (x) w) diag(f at the nodes)
+
+Assembly runs over the support points (A_f = sum_K P_K^T A_K P_K) and is then
+constrained to the masters by C: A = C^T A_f C.  The mass used everywhere is
+the lumped row-sum M_L = C^T m_f (m_f = assembled GLL weights); away from
+hanging masters it equals the consistent GLL mass exactly.
+
+The length-gauge one-body Hamiltonian is H1 = -1/2 Laplacian
+- sum_a Z_a / |r - R_a| + E(t) . r, so its matrix is
+H1~ = 1/2 A + F[V] + F[E . x], and orbitals vanish on the box surface.
+
+Test infrastructure only (see the package docstring).
+"""
+import numpy as np
+import scipy.sparse as sp
+
+from . import gll
+
+# Mean of 1/|r| over the unit cube centred at the origin: 3 ln(2 + sqrt 3) - pi/2.
+CUBE_MEAN_INV_R = 3.0 * np.log(2.0 + np.sqrt(3.0)) - np.pi / 2.0
+
+
+def cell_matrices(p):
+    """(A_hat, m_hat): reference-cube stiffness (to be scaled by h) and mass diagonal (by h^3)."""
+    xi, w = gll.gll_nodes_weights(p)
+    K = gll.stiffness_1d(p)
+    W = np.diag(w)
+    A_hat = np.kron(W, np.kron(W, K)) + np.kron(W, np.kron(K, W)) + np.kron(K, np.kron(W, W))
+    m_hat = np.kron(w, np.kron(w, w))
+    return A_hat, m_hat
+
+
+class Operators:
+    """Assembled sparse operators of one mesh (see module docstring)."""
+
+    def __init__(self, mesh):
+        self.mesh = mesh
+        p1 = mesh.p + 1
+        A_hat, m_hat = cell_matrices(mesh.p)
+        nn = p1 ** 3
+        ncell = len(mesh.lev)
+        rows = np.repeat(mesh.cell_pts, nn, axis=1).ravel()
+        cols = np.tile(mesh.cell_pts, (1, nn)).ravel()
+        vals = (mesh.h[:, None, None] * A_hat[None, :, :]).reshape(ncell, -1).ravel()
+        self.A_f = sp.csr_matrix((vals, (rows, cols)), shape=(mesh.nf, mesh.nf))
+        self.m_f = np.bincount(mesh.cell_pts.ravel(),
+                               weights=(mesh.h[:, None] ** 3 * m_hat[None, :]).ravel(),
+                               minlength=mesh.nf)
+        C = mesh.C
+        self.C = C
+        self.A = (C.T @ self.A_f @ C).tocsr()
+        self.ML = C.T @ self.m_f
+        self.interior = ~mesh.boundary
+        self.V_f = self.nuclear_potential(mesh.X)
+
+    # ----------------------------------------------------------- potentials
+    def nuclear_potential(self, X):
+        """V(x) = -sum_a Z_a / |x - R_a| at the support points X (nf, 3).
+
+        At a support point that coincides with a nucleus the singular value is
+        replaced by -Z c3 / s with s = m_f^(1/3) and c3 the mean of 1/|r| over
+        a unit cube: the cell-averaged Coulomb value of a cube of the point's
+        quadrature volume.
+        """
+        V = np.zeros(len(X))
+        s = np.cbrt(self.m_f)
+        for (R, Z, _L) in self.mesh.nuclei:
+            d = np.linalg.norm(X - R[None, :], axis=1)
+            on = d < 1e-10
+            V[~on] -= Z / d[~on]
+            V[on] -= Z * CUBE_MEAN_INV_R / s[on]
+        return V
+
+    def pointwise(self, f):
+        """F[f] = C^T diag(m_f o f) C for a function f given at the support points."""
+        return (self.C.T @ sp.diags(self.m_f * f) @ self.C).tocsr()
+
+    def H1_matrix(self, E=(0.0, 0.0, 0.0)):
+        """H1~ = 1/2 A + F[V + E . x] over all masters (boundary rows/cols kept)."""
+        E = np.asarray(E, dtype=np.float64)
+        f = self.V_f + self.mesh.X @ E
+        return (0.5 * self.A + self.pointwise(f)).tocsr()
+
+    def h1_apply(self, x, E=(0.0, 0.0, 0.0)):
+        """y = M_L^{-1} H1~ x on interior masters; boundary entries of x are taken as 0
+        and boundary entries of y are 0 (orbitals vanish on the box surface).
+
+        x: (N,) or (N, nvec), real or complex.
+        """
+        H = self.H1_matrix(E)
+        mask = self.interior.astype(np.float64)
+        xm = x * (mask if x.ndim == 1 else mask[:, None])
+        y = H @ xm
+        scale = mask / self.ML
+        return y * (scale if y.ndim == 1 else scale[:, None])
+
+    def stiffness_apply(self, x):
+        """y = A x (full Neumann stiffness over all masters)."""
+        return self.A @ x
+
+    def full_values(self, x):
+        """Values at all support points of the FE function with master coefficients x (C x)."""
+        return self.C @ x
