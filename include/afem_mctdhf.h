@@ -1,0 +1,141 @@
+/*
+ * afem_mctdhf.h - C ABI of the GB300 (sm_103a) library for MCTDHF on an
+ * adaptive finite-element mesh (Orimo, Sato, Ishikawa, arXiv 2301.02387).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every function returns an int status: AFEM_OK (0) or one of the AFEM_E*
+ *    codes below.  A human-readable message for the last failure on the
+ *    calling host thread is returned by afem_last_error().  No entry point
+ *    traps, aborts or exits; device loops carry iteration caps and report
+ *    through the status.
+ *  - "device" pointers are CUDA global-memory addresses on the device that was
+ *    current when the mesh was created; they are owned by the caller and must
+ *    stay valid until the work queued on `stream` has finished.  "host"
+ *    pointers are ordinary CPU memory owned by the caller.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is queued asynchronously on it unless stated otherwise.
+ *  - Vectors over the global unknowns are DoF-major: element (k, v) of an
+ *    [N][n_vec] array is at offset k * n_vec + v.  Complex values are
+ *    interleaved (re, im) float64 pairs (complex128).
+ *  - Global unknowns ("masters") are numbered interior-first: indices
+ *    [0, n_interior) are the masters inside the box, [n_interior, N) the
+ *    masters on the box surface.  Within each group the order follows the
+ *    Morton (Z-order) traversal of the leaf cells.
+ *  - The library owns the mesh object and every internal workspace; it
+ *    allocates device memory only inside afem_mesh_create and the
+ *    workspace-reserving calls documented below.
+ */
+#ifndef AFEM_MCTDHF_H
+#define AFEM_MCTDHF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AFEM_OK 0
+#define AFEM_EINVAL 1         /* bad argument: shape, degree, null pointer, kind */
+#define AFEM_ENOMEM 2         /* device or host allocation failed */
+#define AFEM_ECUDA 3          /* a CUDA runtime call failed */
+#define AFEM_EMESH 4          /* mesh construction failed (constraint chain, size limits) */
+#define AFEM_ECG_MAXIT 5      /* Poisson CG hit its iteration cap before rtol */
+#define AFEM_EBREAKDOWN 6     /* Arnoldi happy breakdown (informational; result valid) */
+#define AFEM_ESINGULAR 7      /* one-body density matrix singular */
+#define AFEM_ENAN 8           /* a non-finite value was detected */
+
+#define AFEM_MAX_NUCLEI 8
+
+/* Mesh description (Sec. 3.1 and Sec. 4 of the paper).
+ *
+ * The box [lo, hi]^3 is covered by n_coarse^3 cubes (the coarse uniform
+ * cells); a leaf of level l (side h_l = (hi - lo) / n_coarse / 2^l) is halved
+ * while some nucleus a with l < nuc_levels[a] lies within distance
+ * refine_c * h_l of the closed cell; the leaves are then 2:1 balanced across
+ * faces, edges and vertices.  The paper selects cells with Kelly's error
+ * indicator on the nuclear Coulomb potential; this geometric rule stands in
+ * for it.  Each leaf carries the tensor-product Lagrange basis of degree
+ * `degree` (1..4) through the Gauss-Lobatto points; continuity across
+ * coarse/fine interfaces is enforced by hanging-node constraints (the paper's
+ * "bridged" functions). */
+typedef struct afem_mesh_desc {
+    double lo, hi;                          /* box [lo, hi]^3, bohr */
+    int32_t n_coarse;                       /* coarse cells per axis (1..1024) */
+    int32_t degree;                         /* polynomial degree p (1..4) */
+    int32_t n_nuclei;                       /* 0..AFEM_MAX_NUCLEI */
+    int32_t pad0;
+    double nuc_pos[AFEM_MAX_NUCLEI][3];     /* nucleus positions, bohr */
+    double nuc_charge[AFEM_MAX_NUCLEI];     /* nuclear charges Z_a */
+    int32_t nuc_levels[AFEM_MAX_NUCLEI];    /* refinement levels L_a toward each nucleus */
+    double refine_c;                        /* refinement radius in units of the cell side */
+} afem_mesh_desc;
+
+typedef struct afem_mesh_info {
+    int64_t n_cells;        /* leaf cells */
+    int64_t n_masters;      /* global unknowns N (interior + surface) */
+    int64_t n_interior;     /* masters inside the box (orbital unknowns) */
+    int64_t n_hanging;      /* constrained support points */
+    int64_t n_constraint_entries; /* nonzeros of the hanging rows of C */
+    int32_t degree;
+    int32_t max_level;
+    double h_min, h_max;    /* smallest / largest leaf side */
+} afem_mesh_info;
+
+typedef struct afem_mesh afem_mesh;   /* opaque */
+
+/* Message describing the last failure on this host thread ("" if none). */
+const char* afem_last_error(void);
+
+/* Build the mesh on the host and upload every table to the current device.
+ * Sec. 3.1 (coarse cubes halved toward the nuclei; GLL tensor basis; bridged
+ * functions).  *out receives a library-owned object; free it with
+ * afem_mesh_destroy.  Returns AFEM_EINVAL for a bad description, AFEM_EMESH
+ * if a hanging point would be constrained by another hanging point (cannot
+ * happen after 2:1 balance), AFEM_ENOMEM / AFEM_ECUDA on device failures.
+ * Synchronous. */
+int afem_mesh_create(const afem_mesh_desc* desc, afem_mesh** out);
+
+/* As afem_mesh_create, but with flags.  AFEM_MESH_HOST_ONLY builds the host
+ * tables only (no device allocation, no CUDA call): afem_mesh_get_info and
+ * afem_mesh_tables work, every device entry point returns AFEM_EINVAL.  Used
+ * to inspect meshes on machines without a GPU.  Synchronous. */
+#define AFEM_MESH_HOST_ONLY 1
+int afem_mesh_create_ex(const afem_mesh_desc* desc, int flags, afem_mesh** out);
+
+/* Release the mesh and its device tables.  NULL is accepted.  Synchronous. */
+int afem_mesh_destroy(afem_mesh* mesh);
+
+/* Sizes of the mesh (host struct, caller-owned). */
+int afem_mesh_get_info(const afem_mesh* mesh, afem_mesh_info* info);
+
+/* Copy mesh tables to caller-owned HOST buffers (any pointer may be NULL to
+ * skip it).  coords: [N][3] master coordinates; lumped_mass: [N] lumped mass
+ * M_L = C^T m_f (Sec. 3.1, mass matrix with GLL quadrature, row-summed at
+ * hanging masters); cells: [n_cells][4] (level, i, j, k) of each leaf in the
+ * library's cell order. */
+int afem_mesh_tables(const afem_mesh* mesh, double* coords, double* lumped_mass,
+                     int32_t* cells);
+
+/* Operator kinds for afem_op_apply. */
+#define AFEM_OP_H1 0      /* y = M_L^{-1} H1~ x, complex128, Dirichlet (Eq. discretized_eom) */
+#define AFEM_OP_STIFF 1   /* y = A x, float64, full Neumann stiffness over all masters */
+
+/* Matrix-free operator application on n_vec vectors at once (Sec. 3.1).
+ *
+ * AFEM_OP_H1: H1~ = 1/2 A + F[V + E.r] is the length-gauge one-body
+ *   Hamiltonian matrix (H1)_kl = int b_k H1 b_l with GLL quadrature, V the
+ *   nuclear Coulomb potential; x and y are complex128 [N][n_vec] device
+ *   arrays.  Surface entries of x are treated as zero and surface entries of
+ *   y are written as zero (orbitals vanish on the box surface).  E is a host
+ *   array of 3 doubles (field in a.u.); NULL means zero field.
+ * AFEM_OP_STIFF: A = C^T (sum_K P_K^T A_K P_K) C with the GLL cell stiffness
+ *   A_K; x and y are float64 [N][n_vec] device arrays; E is ignored.
+ * n_vec: 1..64.  x and y must not overlap.  Asynchronous on `stream`. */
+int afem_op_apply(afem_mesh* mesh, int kind, const double* E, const void* x, void* y,
+                  int n_vec, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AFEM_MCTDHF_H */

@@ -175,9 +175,12 @@ class Mesh:
         keys = self._node_keys()
         ncell, nn, _ = keys.shape
         flat = keys.reshape(-1, 3)
-        uniq, inv = np.unique(flat, axis=0, return_inverse=True)
+        uniq, first, inv = np.unique(flat, axis=0, return_index=True, return_inverse=True)
         self.pkey = uniq
         self.cell_pts = inv.reshape(ncell, nn)
+        # one (cell, local node) that carries each point, for exact local coordinates
+        self.gen_cell = first // nn
+        self.gen_node = first % nn
         unit = self.h0 / 2.0 ** self.Lf / 2.0 ** KEY_BITS
         self.X = self.lo + uniq.astype(np.float64) * unit
         self.nf = len(uniq)
@@ -202,10 +205,20 @@ class Mesh:
         return out
 
     def _local_coords(self, pt, cell):
+        """Coordinates of support point `pt` in the reference cube of `cell`.
+
+        Computed from the leaf that carries the point as a node:
+        t = (i_g 2^(l - l_g) - i) + xi_a 2^(l - l_g), where both terms are exact
+        in floating point, so t is correctly rounded.
+        """
         l, i, j, k = cell
-        s = float((1 << (self.Lf - l)) << KEY_BITS)
-        K = self.pkey[pt].astype(np.float64)
-        return (K - np.array([i, j, k], dtype=np.float64) * s) / s
+        q = self.gen_cell[pt]
+        n = self.gen_node[pt]
+        p1 = self.p + 1
+        loc = (n % p1, (n // p1) % p1, n // (p1 * p1))
+        s = 2.0 ** (l - int(self.lev[q]))
+        return np.array([(float(self.ijk[q, ax]) * s - float(c)) + self.xi[loc[ax]] * s
+                         for ax, c in enumerate((i, j, k))])
 
     def _is_node(self, t):
         return all(np.min(np.abs(self.xi - t[ax])) < 1e-9 for ax in range(3))

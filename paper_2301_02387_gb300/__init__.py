@@ -1,0 +1,124 @@
+"""GB300 (sm_103a) library for MCTDHF on an adaptive finite-element mesh
+(Orimo, Sato, Ishikawa, arXiv 2301.02387).
+
+Thin Python binding over the C ABI of ``include/afem_mctdhf.h``: each function
+here checks and marshals its arguments (torch CUDA tensors -> device
+pointers, the current torch stream) and calls the entry point of the same
+name.  Every step of the computation runs in the library's CUDA kernels.
+"""
+import ctypes
+
+import numpy as np
+
+from . import _capi
+from ._capi import AfemError, OP_H1, OP_STIFF  # noqa: F401
+
+__all__ = ["Mesh", "op_apply", "AfemError", "OP_H1", "OP_STIFF", "load_library"]
+
+
+def load_library():
+    return _capi.load()
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_ptr(t, dtype, shape0=None, name="tensor"):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape0 is not None and t.shape[0] != shape0:
+        raise ValueError(f"{name} must have leading dimension {shape0}, got {t.shape[0]}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Mesh:
+    """Adaptive octree mesh (Sec. 3.1) built on the host and resident on the current GPU.
+
+    nuclei: sequence of (position (3,), charge Z, refinement levels L).
+    """
+
+    def __init__(self, lo, hi, n_coarse, degree, nuclei, refine_c=2.0, host_only=False):
+        lib = _capi.load()
+        d = _capi.MeshDesc()
+        d.lo, d.hi = float(lo), float(hi)
+        d.n_coarse, d.degree = int(n_coarse), int(degree)
+        nuclei = list(nuclei)
+        if len(nuclei) > _capi.MAX_NUCLEI:
+            raise ValueError("too many nuclei")
+        d.n_nuclei = len(nuclei)
+        for a, (R, Z, L) in enumerate(nuclei):
+            for ax in range(3):
+                d.nuc_pos[a][ax] = float(R[ax])
+            d.nuc_charge[a] = float(Z)
+            d.nuc_levels[a] = int(L)
+        d.refine_c = float(refine_c)
+        self.desc = d
+        self.nuclei = [(np.asarray(R, dtype=np.float64), float(Z), int(L)) for (R, Z, L) in nuclei]
+        h = ctypes.c_void_p()
+        flags = _capi.MESH_HOST_ONLY if host_only else 0
+        _capi.check(lib.afem_mesh_create_ex(ctypes.byref(d), flags, ctypes.byref(h)))
+        self._h = h
+        info = _capi.MeshInfo()
+        _capi.check(lib.afem_mesh_get_info(h, ctypes.byref(info)))
+        self.n_cells = info.n_cells
+        self.N = info.n_masters
+        self.n_interior = info.n_interior
+        self.n_hanging = info.n_hanging
+        self.n_constraint_entries = info.n_constraint_entries
+        self.degree = info.degree
+        self.max_level = info.max_level
+        self.h_min, self.h_max = info.h_min, info.h_max
+
+    @property
+    def handle(self):
+        return self._h
+
+    def tables(self):
+        """(coords (N,3), lumped mass (N,), cells (n_cells,4) level,i,j,k) as numpy arrays."""
+        X = np.empty((self.N, 3), dtype=np.float64)
+        ml = np.empty(self.N, dtype=np.float64)
+        cells = np.empty((self.n_cells, 4), dtype=np.int32)
+        _capi.check(_capi.load().afem_mesh_tables(
+            self._h, X.ctypes.data_as(ctypes.c_void_p), ml.ctypes.data_as(ctypes.c_void_p),
+            cells.ctypes.data_as(ctypes.c_void_p)))
+        return X, ml, cells
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _capi.load().afem_mesh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def op_apply(mesh, kind, x, y, E=None, stream=None):
+    """afem_op_apply: y = op(x) for all columns of x ([N, n_vec], DoF-major).
+
+    OP_H1: complex128, y = M_L^{-1} H1~ x (Dirichlet); OP_STIFF: float64, y = A x.
+    """
+    import torch
+    dtype = {OP_H1: torch.complex128, OP_STIFF: torch.float64}.get(kind, x.dtype)
+    xp = _dev_ptr(x, dtype, mesh.N, "x")
+    yp = _dev_ptr(y, dtype, mesh.N, "y")
+    if x.shape != y.shape:
+        raise ValueError("x and y must have the same shape")
+    nvec = 1 if x.dim() == 1 else int(x.shape[1])
+    Earr = None
+    if E is not None:
+        Earr = (ctypes.c_double * 3)(*[float(e) for e in E])
+    _capi.check(_capi.load().afem_op_apply(
+        mesh.handle, int(kind), ctypes.cast(Earr, ctypes.c_void_p) if Earr is not None else None,
+        xp, yp, nvec, _stream_ptr(stream)))
+    return y

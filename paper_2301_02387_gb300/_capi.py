@@ -1,0 +1,93 @@
+"""ctypes binding of the C ABI in include/afem_mctdhf.h (argument marshalling only).
+
+The shared library is built in-tree by ``paper_2301_02387_gb300.build`` and
+loaded from ``paper_2301_02387_gb300/_lib/libafem.so``.  Loading fails loudly
+if it is missing: there is no CPU fallback.
+"""
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libafem.so")
+
+AFEM_OK = 0
+AFEM_EINVAL = 1
+AFEM_ENOMEM = 2
+AFEM_ECUDA = 3
+AFEM_EMESH = 4
+AFEM_ECG_MAXIT = 5
+AFEM_EBREAKDOWN = 6
+AFEM_ESINGULAR = 7
+AFEM_ENAN = 8
+MAX_NUCLEI = 8
+
+MESH_HOST_ONLY = 1
+
+OP_H1 = 0
+OP_STIFF = 1
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [
+        ("lo", ctypes.c_double), ("hi", ctypes.c_double),
+        ("n_coarse", ctypes.c_int32), ("degree", ctypes.c_int32),
+        ("n_nuclei", ctypes.c_int32), ("pad0", ctypes.c_int32),
+        ("nuc_pos", (ctypes.c_double * 3) * MAX_NUCLEI),
+        ("nuc_charge", ctypes.c_double * MAX_NUCLEI),
+        ("nuc_levels", ctypes.c_int32 * MAX_NUCLEI),
+        ("refine_c", ctypes.c_double),
+    ]
+
+
+class MeshInfo(ctypes.Structure):
+    _fields_ = [
+        ("n_cells", ctypes.c_int64), ("n_masters", ctypes.c_int64),
+        ("n_interior", ctypes.c_int64), ("n_hanging", ctypes.c_int64),
+        ("n_constraint_entries", ctypes.c_int64),
+        ("degree", ctypes.c_int32), ("max_level", ctypes.c_int32),
+        ("h_min", ctypes.c_double), ("h_max", ctypes.c_double),
+    ]
+
+
+class AfemError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"afem error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+# name -> (restype, argtypes); every symbol include/afem_mctdhf.h declares
+_P = ctypes.c_void_p
+SIGNATURES = {
+    "afem_last_error": (ctypes.c_char_p, []),
+    "afem_mesh_create": (ctypes.c_int, [ctypes.POINTER(MeshDesc), ctypes.POINTER(_P)]),
+    "afem_mesh_create_ex": (ctypes.c_int, [ctypes.POINTER(MeshDesc), ctypes.c_int, ctypes.POINTER(_P)]),
+    "afem_mesh_destroy": (ctypes.c_int, [_P]),
+    "afem_mesh_get_info": (ctypes.c_int, [_P, ctypes.POINTER(MeshInfo)]),
+    "afem_mesh_tables": (ctypes.c_int, [_P, _P, _P, _P]),
+    "afem_op_apply": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, ctypes.c_int, _P]),
+}
+
+
+def load(path=LIB_PATH):
+    """Load the shared library (once) and declare every entry point."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def check(rc):
+    if rc != AFEM_OK:
+        msg = load().afem_last_error().decode(errors="replace")
+        raise AfemError(rc, msg)
+    return rc

@@ -1,0 +1,92 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/afem_mctdhf.h"
+
+namespace afem {
+
+constexpr int kMaxDegree = 4;
+constexpr int kMaxP1 = kMaxDegree + 1;
+
+// Record the message for afem_last_error() and return `code`.
+int set_error(int code, const std::string& msg);
+int cuda_error(cudaError_t e, const char* what);
+
+#define AFEM_CUDA_TRY(call)                                      \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return ::afem::cuda_error(e_, #call); \
+    } while (0)
+
+// 1D Gauss-Lobatto-Legendre basis on [0, 1] (Sec. 3.1).
+struct Basis1D {
+    int p = 0;
+    double xi[kMaxP1] = {};          // nodes, ascending
+    double w[kMaxP1] = {};           // quadrature weights (sum 1)
+    double K[kMaxP1][kMaxP1] = {};   // 1D stiffness sum_q w_q L_i'(xi_q) L_j'(xi_q)
+};
+Basis1D make_basis(int p);
+double lagrange_value(const Basis1D& b, int j, double t);
+
+// Host-side mesh tables (built once; the mesh is static during a run).
+struct HostMesh {
+    int p = 0;
+    int max_level = 0;
+    double lo = 0, hi = 0, h0 = 0;
+    int n_coarse = 0;
+    // leaves in Morton order
+    std::vector<int32_t> lev, ci, cj, ck;
+    std::vector<double> corner;            // [ncell][3]
+    std::vector<double> h;                 // [ncell]
+    // cell node map: >= 0 master index, < 0 -(hanging index) - 1
+    std::vector<int32_t> cell_node;        // [ncell][(p+1)^3]
+    int64_t n_master = 0, n_interior = 0, n_hanging = 0;
+    std::vector<double> master_xyz;        // [N][3]
+    std::vector<double> hang_xyz;          // [nh][3]
+    std::vector<int32_t> hang_ptr;         // [nh+1]
+    std::vector<int32_t> hang_master;      // [nnz]
+    std::vector<double> hang_w;            // [nnz]
+    std::vector<double> ml;                // [N] lumped mass C^T m_f
+    std::vector<double> v_master, v_hang;  // nuclear potential at masters / hanging points
+};
+
+int build_host_mesh(const afem_mesh_desc& d, HostMesh& out);
+
+// Device-resident mesh.
+struct DeviceMesh {
+    int p = 0;
+    int64_t ncell = 0, n_master = 0, n_interior = 0, n_hanging = 0, nnz = 0;
+    int32_t* cell_node = nullptr;   // [ncell][(p+1)^3]
+    double4* cell_geom = nullptr;   // (corner x, y, z, h)
+    int32_t* hang_ptr = nullptr;
+    int32_t* hang_master = nullptr;
+    double* hang_w = nullptr;
+    double* ml = nullptr;           // [N]
+    double* ml_inv = nullptr;       // [N]
+    double* v_master = nullptr;     // [N]
+    double* v_hang = nullptr;       // [nh]
+};
+
+}  // namespace afem
+
+struct afem_mesh {
+    afem_mesh_desc desc;
+    afem::HostMesh host;
+    afem::Basis1D basis;
+    afem::DeviceMesh dev;
+    int device = 0;
+    bool host_only = false;
+};
+
+namespace afem {
+int upload_mesh(afem_mesh* m);
+void free_device_mesh(DeviceMesh& d);
+int launch_op_apply(afem_mesh* m, int kind, const double* E, const void* x, void* y, int nvec,
+                    cudaStream_t s);
+}  // namespace afem

@@ -1,0 +1,110 @@
+// C ABI entry points (declared in include/afem_mctdhf.h).
+#include <cstring>
+#include <new>
+
+#include "afem_internal.h"
+
+namespace afem {
+const char* last_error_cstr();
+}
+
+using namespace afem;
+
+extern "C" {
+
+const char* afem_last_error(void) { return last_error_cstr(); }
+
+int afem_mesh_create(const afem_mesh_desc* desc, afem_mesh** out) {
+    return afem_mesh_create_ex(desc, 0, out);
+}
+
+int afem_mesh_create_ex(const afem_mesh_desc* desc, int flags, afem_mesh** out) {
+    if (!desc || !out) return set_error(AFEM_EINVAL, "afem_mesh_create: null argument");
+    if (flags & ~AFEM_MESH_HOST_ONLY) return set_error(AFEM_EINVAL, "afem_mesh_create_ex: unknown flags");
+    *out = nullptr;
+    const afem_mesh_desc& d = *desc;
+    if (d.degree < 1 || d.degree > kMaxDegree)
+        return set_error(AFEM_EINVAL, "afem_mesh_create: degree must be 1..4");
+    if (d.n_coarse < 1 || d.n_coarse > 1024)
+        return set_error(AFEM_EINVAL, "afem_mesh_create: n_coarse must be 1..1024");
+    if (!(d.hi > d.lo)) return set_error(AFEM_EINVAL, "afem_mesh_create: empty box");
+    if (d.n_nuclei < 0 || d.n_nuclei > AFEM_MAX_NUCLEI)
+        return set_error(AFEM_EINVAL, "afem_mesh_create: n_nuclei out of range");
+    if (!(d.refine_c >= 0.0)) return set_error(AFEM_EINVAL, "afem_mesh_create: refine_c < 0");
+    for (int n = 0; n < d.n_nuclei; ++n)
+        if (d.nuc_levels[n] < 0 || d.nuc_levels[n] > 12)
+            return set_error(AFEM_EINVAL, "afem_mesh_create: nuc_levels must be 0..12");
+    afem_mesh* m = new (std::nothrow) afem_mesh();
+    if (!m) return set_error(AFEM_ENOMEM, "afem_mesh_create: host allocation failed");
+    m->desc = d;
+    m->host_only = (flags & AFEM_MESH_HOST_ONLY) != 0;
+    int rc = build_host_mesh(d, m->host);
+    if (rc == AFEM_OK) {
+        m->basis = make_basis(d.degree);
+        if (!m->host_only) {
+            cudaError_t e = cudaGetDevice(&m->device);
+            rc = e == cudaSuccess ? upload_mesh(m) : cuda_error(e, "cudaGetDevice");
+        }
+    }
+    if (rc != AFEM_OK) {
+        free_device_mesh(m->dev);
+        delete m;
+        return rc;
+    }
+    *out = m;
+    return AFEM_OK;
+}
+
+int afem_mesh_destroy(afem_mesh* mesh) {
+    if (!mesh) return AFEM_OK;
+    if (!mesh->host_only) free_device_mesh(mesh->dev);
+    delete mesh;
+    return AFEM_OK;
+}
+
+int afem_mesh_get_info(const afem_mesh* m, afem_mesh_info* info) {
+    if (!m || !info) return set_error(AFEM_EINVAL, "afem_mesh_get_info: null argument");
+    const HostMesh& H = m->host;
+    info->n_cells = int64_t(H.lev.size());
+    info->n_masters = H.n_master;
+    info->n_interior = H.n_interior;
+    info->n_hanging = H.n_hanging;
+    info->n_constraint_entries = int64_t(H.hang_master.size());
+    info->degree = H.p;
+    info->max_level = H.max_level;
+    double hmin = 1e300, hmax = 0.0;
+    for (double h : H.h) {
+        hmin = h < hmin ? h : hmin;
+        hmax = h > hmax ? h : hmax;
+    }
+    info->h_min = hmin;
+    info->h_max = hmax;
+    return AFEM_OK;
+}
+
+int afem_mesh_tables(const afem_mesh* m, double* coords, double* lumped_mass, int32_t* cells) {
+    if (!m) return set_error(AFEM_EINVAL, "afem_mesh_tables: null mesh");
+    const HostMesh& H = m->host;
+    if (coords) std::memcpy(coords, H.master_xyz.data(), H.master_xyz.size() * sizeof(double));
+    if (lumped_mass) std::memcpy(lumped_mass, H.ml.data(), H.ml.size() * sizeof(double));
+    if (cells) {
+        for (size_t q = 0; q < H.lev.size(); ++q) {
+            cells[4 * q + 0] = H.lev[q];
+            cells[4 * q + 1] = H.ci[q];
+            cells[4 * q + 2] = H.cj[q];
+            cells[4 * q + 3] = H.ck[q];
+        }
+    }
+    return AFEM_OK;
+}
+
+int afem_op_apply(afem_mesh* m, int kind, const double* E, const void* x, void* y, int n_vec,
+                  void* stream) {
+    if (!m || !x || !y) return set_error(AFEM_EINVAL, "afem_op_apply: null argument");
+    if (n_vec < 1 || n_vec > 64) return set_error(AFEM_EINVAL, "afem_op_apply: n_vec must be 1..64");
+    if (x == y) return set_error(AFEM_EINVAL, "afem_op_apply: x and y must not alias");
+    if (m->host_only) return set_error(AFEM_EINVAL, "afem_op_apply: mesh was built host-only");
+    return launch_op_apply(m, kind, E, x, y, n_vec, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

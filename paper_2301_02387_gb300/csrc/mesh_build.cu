@@ -1,0 +1,539 @@
+// Host-side construction of the adaptive mesh and its device tables.
+//
+// Sec. 3.1 of the paper: the box is first covered by coarse uniform cubes and
+// cells are halved where resolution is needed; each cell carries the tensor
+// product of 1D Lagrange polynomials through the Gauss-Lobatto points, and
+// "bridged" functions make the discrete space continuous across cells.  On a
+// 2:1-balanced octree this is the conforming Q_p space: a node of a fine leaf
+// that lies on the face or edge of a coarser neighbour without being one of
+// that neighbour's nodes is a hanging node, whose value is the coarse
+// neighbour's polynomial evaluated there.  The mesh is static during a run
+// (Sec. 4), so everything here runs once, on the host, before upload.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <unordered_map>
+#include <unordered_set>
+
+#include "afem_internal.h"
+
+namespace afem {
+
+// ---------------------------------------------------------------- errors
+static thread_local std::string g_last_error;
+
+int set_error(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+int cuda_error(cudaError_t e, const char* what) {
+    return set_error(AFEM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+const char* last_error_cstr() { return g_last_error.c_str(); }
+
+// ---------------------------------------------------------- 1D GLL basis
+// Nodes on [-1,1]: the endpoints and the roots of P_p'.  The interior roots
+// are found by Newton's method on P_p', with P_p'' from Legendre's equation
+// (1 - x^2) P'' = 2 x P' - p (p+1) P, started from the Chebyshev extrema.
+static void legendre_and_deriv(int p, double x, double& P, double& dP) {
+    double p0 = 1.0, p1 = x;
+    if (p == 0) { P = 1.0; dP = 0.0; return; }
+    for (int k = 2; k <= p; ++k) {
+        double pk = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = pk;
+    }
+    P = p1;
+    // P_p' = p (x P_p - P_{p-1}) / (x^2 - 1), valid away from +-1.
+    dP = p * (x * p1 - p0) / (x * x - 1.0);
+}
+
+Basis1D make_basis(int p) {
+    Basis1D b;
+    b.p = p;
+    double x[kMaxP1];
+    x[0] = -1.0;
+    x[p] = 1.0;
+    for (int j = 1; j < p; ++j) {
+        double t = -std::cos(M_PI * j / p);
+        for (int it = 0; it < 100; ++it) {
+            double P, dP;
+            legendre_and_deriv(p, t, P, dP);
+            double d2P = (2.0 * t * dP - p * (p + 1.0) * P) / (1.0 - t * t);
+            double step = dP / d2P;
+            t -= step;
+            if (std::fabs(step) < 1e-16) break;
+        }
+        x[j] = t;
+    }
+    for (int j = 0; j <= p; ++j) {
+        double P, dP;
+        legendre_and_deriv(p, x[j], P, dP);
+        if (j == 0 || j == p) {  // P_p(+-1) = (+-1)^p
+            P = (j == 0 && (p % 2)) ? -1.0 : 1.0;
+        }
+        b.xi[j] = 0.5 * (x[j] + 1.0);
+        b.w[j] = 0.5 * 2.0 / (p * (p + 1.0) * P * P);
+    }
+    b.xi[0] = 0.0;
+    b.xi[p] = 1.0;
+    // Lagrange derivative matrix D[q][j] = L_j'(xi_q) by barycentric weights.
+    double lam[kMaxP1], D[kMaxP1][kMaxP1];
+    for (int j = 0; j <= p; ++j) {
+        double prod = 1.0;
+        for (int m = 0; m <= p; ++m)
+            if (m != j) prod *= (b.xi[j] - b.xi[m]);
+        lam[j] = 1.0 / prod;
+    }
+    for (int q = 0; q <= p; ++q) {
+        double diag = 0.0;
+        for (int j = 0; j <= p; ++j) {
+            if (j == q) continue;
+            D[q][j] = (lam[j] / lam[q]) / (b.xi[q] - b.xi[j]);
+            diag -= D[q][j];
+        }
+        D[q][q] = diag;
+    }
+    for (int i = 0; i <= p; ++i)
+        for (int j = 0; j <= p; ++j) {
+            double s = 0.0;
+            for (int q = 0; q <= p; ++q) s += b.w[q] * D[q][i] * D[q][j];
+            b.K[i][j] = s;
+        }
+    return b;
+}
+
+double lagrange_value(const Basis1D& b, int j, double t) {
+    double v = 1.0;
+    for (int m = 0; m <= b.p; ++m)
+        if (m != j) v *= (t - b.xi[m]) / (b.xi[j] - b.xi[m]);
+    return v;
+}
+
+// ------------------------------------------------------------ octree
+namespace {
+
+constexpr int kFracBits = 40;    // fractional bits of integer point coordinates
+constexpr int kCoordBits = 20;   // bits per axis of a leaf index at its level
+
+struct Leaf {
+    int32_t l;
+    int64_t i, j, k;
+};
+
+inline uint64_t leaf_key(int l, int64_t i, int64_t j, int64_t k) {
+    return (uint64_t(l) << 60) | (uint64_t(i) << 40) | (uint64_t(j) << 20) | uint64_t(k);
+}
+
+struct Key3 {
+    int64_t x, y, z;
+    bool operator==(const Key3& o) const { return x == o.x && y == o.y && z == o.z; }
+};
+struct Key3Hash {
+    size_t operator()(const Key3& k) const {
+        uint64_t h = uint64_t(k.x) * 0x9E3779B97F4A7C15ull;
+        h ^= uint64_t(k.y) + 0x7F4A7C159E3779B9ull + (h << 6) + (h >> 2);
+        h ^= uint64_t(k.z) + 0x94D049BB133111EBull + (h << 6) + (h >> 2);
+        return size_t(h ^ (h >> 31));
+    }
+};
+
+uint64_t spread3(uint64_t v) {  // 21 bits -> every third bit
+    uint64_t r = 0;
+    for (int b = 0; b < 21; ++b) r |= ((v >> b) & 1ull) << (3 * b);
+    return r;
+}
+
+}  // namespace
+
+int build_host_mesh(const afem_mesh_desc& d, HostMesh& M) {
+    const int p = d.degree;
+    const int p1 = p + 1;
+    const int nn = p1 * p1 * p1;
+    const int nc = d.n_coarse;
+    M.p = p;
+    M.lo = d.lo;
+    M.hi = d.hi;
+    M.n_coarse = nc;
+    M.h0 = (d.hi - d.lo) / nc;
+    const double h0 = M.h0;
+    const Basis1D B = make_basis(p);
+
+    // ---- refinement toward the nuclei (geometric stand-in for Kelly's indicator)
+    std::vector<Leaf> leaves;
+    leaves.reserve(size_t(nc) * nc * nc);
+    for (int i = 0; i < nc; ++i)
+        for (int j = 0; j < nc; ++j)
+            for (int k = 0; k < nc; ++k) leaves.push_back({0, i, j, k});
+    for (;;) {
+        bool any = false;
+        std::vector<Leaf> next;
+        next.reserve(leaves.size() * 2);
+        for (const Leaf& c : leaves) {
+            const double h = h0 / double(int64_t(1) << c.l);
+            const double a[3] = {d.lo + double(c.i) * h, d.lo + double(c.j) * h, d.lo + double(c.k) * h};
+            bool split = false;
+            for (int n = 0; n < d.n_nuclei && !split; ++n) {
+                if (c.l >= d.nuc_levels[n]) continue;
+                double d2 = 0.0;
+                for (int ax = 0; ax < 3; ++ax) {
+                    const double R = d.nuc_pos[n][ax];
+                    const double b = a[ax] + h;
+                    if (R < a[ax]) {
+                        const double t = a[ax] - R;
+                        d2 += t * t;
+                    } else if (R > b) {
+                        const double t = R - b;
+                        d2 += t * t;
+                    }
+                }
+                const double ch = d.refine_c * h;
+                split = d2 <= ch * ch;
+            }
+            if (split) {
+                any = true;
+                for (int s = 0; s < 8; ++s)
+                    next.push_back({c.l + 1, 2 * c.i + (s & 1), 2 * c.j + ((s >> 1) & 1),
+                                    2 * c.k + ((s >> 2) & 1)});
+            } else {
+                next.push_back(c);
+            }
+        }
+        leaves.swap(next);
+        if (!any) break;
+        if (leaves.size() > (size_t(1) << 26))
+            return set_error(AFEM_EMESH, "mesh: more than 2^26 leaves");
+    }
+
+    // ---- 2:1 balance across faces, edges and vertices
+    std::unordered_set<uint64_t> leafset;
+    auto rebuild_set = [&]() {
+        leafset.clear();
+        leafset.reserve(leaves.size() * 2);
+        for (const Leaf& c : leaves) leafset.insert(leaf_key(c.l, c.i, c.j, c.k));
+    };
+    // Leaf containing the level-l cell (i,j,k): that cell or one of its ancestors.
+    auto find_leaf = [&](int l, int64_t i, int64_t j, int64_t k, Leaf& out) -> bool {
+        for (int l2 = l; l2 >= 0; --l2) {
+            const int s = l - l2;
+            if (leafset.count(leaf_key(l2, i >> s, j >> s, k >> s))) {
+                out = {l2, i >> s, j >> s, k >> s};
+                return true;
+            }
+        }
+        return false;
+    };
+    rebuild_set();
+    for (;;) {
+        std::unordered_set<uint64_t> split;
+        for (const Leaf& c : leaves) {
+            if (c.l < 2) continue;
+            const int64_t n = int64_t(nc) << c.l;
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        if (!dx && !dy && !dz) continue;
+                        const int64_t a = c.i + dx, b = c.j + dy, e = c.k + dz;
+                        if (a < 0 || b < 0 || e < 0 || a >= n || b >= n || e >= n) continue;
+                        Leaf f;
+                        if (find_leaf(c.l, a, b, e, f) && f.l < c.l - 1)
+                            split.insert(leaf_key(f.l, f.i, f.j, f.k));
+                    }
+        }
+        if (split.empty()) break;
+        std::vector<Leaf> next;
+        next.reserve(leaves.size() + 8 * split.size());
+        for (const Leaf& c : leaves) {
+            if (split.count(leaf_key(c.l, c.i, c.j, c.k))) {
+                for (int s = 0; s < 8; ++s)
+                    next.push_back({c.l + 1, 2 * c.i + (s & 1), 2 * c.j + ((s >> 1) & 1),
+                                    2 * c.k + ((s >> 2) & 1)});
+            } else {
+                next.push_back(c);
+            }
+        }
+        leaves.swap(next);
+        rebuild_set();
+    }
+    int Lf = 0;
+    for (const Leaf& c : leaves) Lf = std::max(Lf, int(c.l));
+    M.max_level = Lf;
+    if ((int64_t(nc) << Lf) >= (int64_t(1) << kCoordBits))
+        return set_error(AFEM_EMESH, "mesh: n_coarse * 2^levels exceeds 2^20");
+
+    // ---- Morton (Z-order) traversal of the leaves
+    std::vector<std::pair<uint64_t, size_t>> order(leaves.size());
+    for (size_t q = 0; q < leaves.size(); ++q) {
+        const Leaf& c = leaves[q];
+        const int s = Lf - c.l;
+        order[q] = {spread3(uint64_t(c.i) << s) | (spread3(uint64_t(c.j) << s) << 1) |
+                        (spread3(uint64_t(c.k) << s) << 2),
+                    q};
+    }
+    std::sort(order.begin(), order.end());
+    const size_t ncell = leaves.size();
+    {
+        std::vector<Leaf> sorted(ncell);
+        for (size_t q = 0; q < ncell; ++q) sorted[q] = leaves[order[q].second];
+        leaves.swap(sorted);
+    }
+    std::unordered_map<uint64_t, int64_t> cell_of;
+    cell_of.reserve(ncell * 2);
+    for (size_t q = 0; q < ncell; ++q)
+        cell_of[leaf_key(leaves[q].l, leaves[q].i, leaves[q].j, leaves[q].k)] = int64_t(q);
+
+    // ---- support points: integer coordinates in units of h_finest / 2^kFracBits
+    std::unordered_map<Key3, int64_t, Key3Hash> point_of;
+    point_of.reserve(ncell * nn);
+    std::vector<Key3> pkey;
+    std::vector<int64_t> cellpt(ncell * nn);
+    std::vector<double> mf;   // assembled GLL weight per support point
+    for (size_t q = 0; q < ncell; ++q) {
+        const Leaf& c = leaves[q];
+        const int64_t S = int64_t(1) << (Lf - c.l + kFracBits);
+        int64_t off[kMaxP1];
+        for (int a = 0; a < p1; ++a) off[a] = std::llround(B.xi[a] * double(S));
+        const double h = h0 / double(int64_t(1) << c.l);
+        const double h3 = h * h * h;
+        for (int cz = 0; cz < p1; ++cz)
+            for (int cy = 0; cy < p1; ++cy)
+                for (int cx = 0; cx < p1; ++cx) {
+                    const Key3 key{c.i * S + off[cx], c.j * S + off[cy], c.k * S + off[cz]};
+                    auto it = point_of.find(key);
+                    int64_t id;
+                    if (it == point_of.end()) {
+                        id = int64_t(pkey.size());
+                        point_of.emplace(key, id);
+                        pkey.push_back(key);
+                        mf.push_back(0.0);
+                    } else {
+                        id = it->second;
+                    }
+                    cellpt[q * nn + cx + p1 * (cy + p1 * cz)] = id;
+                    mf[id] += h3 * B.w[cx] * B.w[cy] * B.w[cz];
+                }
+    }
+    const int64_t npts = int64_t(pkey.size());
+
+    // ---- hanging nodes: nodes of a leaf inside the closure of a coarser
+    // face/edge/vertex neighbour that are not nodes of that neighbour.
+    std::vector<int64_t> hang_src_ptr(npts + 1, 0);
+    std::vector<std::vector<std::pair<int64_t, double>>> hang_rows;   // per hanging point
+    std::vector<int64_t> hang_row_of(npts, -1);
+    for (size_t q = 0; q < ncell; ++q) {
+        const Leaf& c = leaves[q];
+        if (c.l == 0) continue;
+        const int64_t n = int64_t(nc) << c.l;
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    if (!dx && !dy && !dz) continue;
+                    const int64_t a = c.i + dx, b = c.j + dy, e = c.k + dz;
+                    if (a < 0 || b < 0 || e < 0 || a >= n || b >= n || e >= n) continue;
+                    Leaf f;
+                    if (!find_leaf(c.l, a, b, e, f) || f.l != c.l - 1) continue;
+                    const int64_t qc = cell_of.at(leaf_key(f.l, f.i, f.j, f.k));
+                    // offsets of this leaf inside the coarse neighbour, in fine cells
+                    const int64_t del[3] = {c.i - 2 * f.i, c.j - 2 * f.j, c.k - 2 * f.k};
+                    for (int cz = 0; cz < p1; ++cz)
+                        for (int cy = 0; cy < p1; ++cy)
+                            for (int cx = 0; cx < p1; ++cx) {
+                                const int loc[3] = {cx, cy, cz};
+                                double t[3];
+                                bool inside = true, is_node = true;
+                                for (int ax = 0; ax < 3; ++ax) {
+                                    t[ax] = (double(del[ax]) + B.xi[loc[ax]]) * 0.5;
+                                    if (t[ax] < -1e-12 || t[ax] > 1.0 + 1e-12) inside = false;
+                                    double best = 1.0;
+                                    for (int m = 0; m < p1; ++m)
+                                        best = std::min(best, std::fabs(t[ax] - B.xi[m]));
+                                    if (best > 1e-9) is_node = false;
+                                }
+                                if (!inside || is_node) continue;
+                                const int64_t pt = cellpt[q * nn + cx + p1 * (cy + p1 * cz)];
+                                if (hang_row_of[pt] >= 0) continue;
+                                hang_row_of[pt] = int64_t(hang_rows.size());
+                                std::vector<std::pair<int64_t, double>> row;
+                                double Lx[kMaxP1], Ly[kMaxP1], Lz[kMaxP1];
+                                for (int m = 0; m < p1; ++m) {
+                                    Lx[m] = lagrange_value(B, m, t[0]);
+                                    Ly[m] = lagrange_value(B, m, t[1]);
+                                    Lz[m] = lagrange_value(B, m, t[2]);
+                                }
+                                for (int mz = 0; mz < p1; ++mz)
+                                    for (int my = 0; my < p1; ++my)
+                                        for (int mx = 0; mx < p1; ++mx) {
+                                            const double wgt = Lx[mx] * Ly[my] * Lz[mz];
+                                            if (wgt == 0.0) continue;
+                                            row.push_back({cellpt[qc * nn + mx + p1 * (my + p1 * mz)], wgt});
+                                        }
+                                hang_rows.push_back(std::move(row));
+                            }
+                }
+    }
+    (void)hang_src_ptr;
+
+    // ---- numbering: interior masters, then surface masters, each in first-touch order
+    const int64_t top = (int64_t(nc) << Lf) << kFracBits;
+    std::vector<int64_t> master_id(npts, -1), hang_id(npts, -1);
+    int64_t nint = 0, nmaster = 0, nhang = 0;
+    auto on_surface = [&](const Key3& k) {
+        return k.x == 0 || k.y == 0 || k.z == 0 || k.x == top || k.y == top || k.z == top;
+    };
+    for (int64_t pt = 0; pt < npts; ++pt)
+        if (hang_row_of[pt] < 0 && !on_surface(pkey[pt])) master_id[pt] = nint++;
+    nmaster = nint;
+    for (int64_t pt = 0; pt < npts; ++pt)
+        if (hang_row_of[pt] < 0 && on_surface(pkey[pt])) master_id[pt] = nmaster++;
+    for (int64_t pt = 0; pt < npts; ++pt)
+        if (hang_row_of[pt] >= 0) hang_id[pt] = nhang++;
+    if (nmaster >= (int64_t(1) << 31) || nhang >= (int64_t(1) << 30))
+        return set_error(AFEM_EMESH, "mesh: index range exceeds int32");
+
+    M.n_master = nmaster;
+    M.n_interior = nint;
+    M.n_hanging = nhang;
+    M.lev.resize(ncell);
+    M.ci.resize(ncell);
+    M.cj.resize(ncell);
+    M.ck.resize(ncell);
+    M.corner.resize(ncell * 3);
+    M.h.resize(ncell);
+    M.cell_node.resize(ncell * nn);
+    for (size_t q = 0; q < ncell; ++q) {
+        const Leaf& c = leaves[q];
+        M.lev[q] = c.l;
+        M.ci[q] = int32_t(c.i);
+        M.cj[q] = int32_t(c.j);
+        M.ck[q] = int32_t(c.k);
+        const double h = h0 / double(int64_t(1) << c.l);
+        M.h[q] = h;
+        M.corner[3 * q + 0] = d.lo + double(c.i) * h;
+        M.corner[3 * q + 1] = d.lo + double(c.j) * h;
+        M.corner[3 * q + 2] = d.lo + double(c.k) * h;
+        for (int n = 0; n < nn; ++n) {
+            const int64_t pt = cellpt[q * nn + n];
+            M.cell_node[q * nn + n] =
+                master_id[pt] >= 0 ? int32_t(master_id[pt]) : int32_t(-hang_id[pt] - 1);
+        }
+    }
+    const double unit = h0 / double(int64_t(1) << Lf) / double(int64_t(1) << kFracBits);
+    auto coord = [&](const Key3& k, double* x) {
+        x[0] = d.lo + double(k.x) * unit;
+        x[1] = d.lo + double(k.y) * unit;
+        x[2] = d.lo + double(k.z) * unit;
+    };
+    M.master_xyz.assign(nmaster * 3, 0.0);
+    M.hang_xyz.assign(nhang * 3, 0.0);
+    M.ml.assign(nmaster, 0.0);
+    std::vector<double> mf_master(nmaster, 0.0), mf_hang(nhang, 0.0);
+    for (int64_t pt = 0; pt < npts; ++pt) {
+        if (master_id[pt] >= 0) {
+            coord(pkey[pt], &M.master_xyz[3 * master_id[pt]]);
+            M.ml[master_id[pt]] += mf[pt];
+            mf_master[master_id[pt]] = mf[pt];
+        } else {
+            coord(pkey[pt], &M.hang_xyz[3 * hang_id[pt]]);
+            mf_hang[hang_id[pt]] = mf[pt];
+        }
+    }
+    M.hang_ptr.assign(nhang + 1, 0);
+    M.hang_master.clear();
+    M.hang_w.clear();
+    {
+        std::vector<int64_t> pt_of_hang(nhang);
+        for (int64_t pt = 0; pt < npts; ++pt)
+            if (hang_id[pt] >= 0) pt_of_hang[hang_id[pt]] = pt;
+        for (int64_t hh = 0; hh < nhang; ++hh) {
+            const auto& row = hang_rows[hang_row_of[pt_of_hang[hh]]];
+            for (const auto& e : row) {
+                const int64_t m = master_id[e.first];
+                if (m < 0)
+                    return set_error(AFEM_EMESH,
+                                     "mesh: hanging point constrained by another hanging point");
+                M.hang_master.push_back(int32_t(m));
+                M.hang_w.push_back(e.second);
+                M.ml[m] += e.second * mf_hang[hh];
+            }
+            M.hang_ptr[hh + 1] = int32_t(M.hang_master.size());
+        }
+    }
+
+    // ---- nuclear potential V = -sum_a Z_a / |x - R_a| at masters and hanging points.
+    // A support point on a nucleus takes -Z c3 / s with s = m_f^(1/3) and
+    // c3 = 3 ln(2 + sqrt 3) - pi/2, the mean of 1/|r| over a unit cube.
+    const double c3 = 3.0 * std::log(2.0 + std::sqrt(3.0)) - M_PI / 2.0;
+    auto potential = [&](const double* x, double mfx) {
+        double v = 0.0;
+        for (int n = 0; n < d.n_nuclei; ++n) {
+            const double rx = x[0] - d.nuc_pos[n][0], ry = x[1] - d.nuc_pos[n][1],
+                         rz = x[2] - d.nuc_pos[n][2];
+            const double r = std::sqrt(rx * rx + ry * ry + rz * rz);
+            if (r < 1e-10)
+                v -= d.nuc_charge[n] * c3 / std::cbrt(mfx);
+            else
+                v -= d.nuc_charge[n] / r;
+        }
+        return v;
+    };
+    M.v_master.resize(nmaster);
+    M.v_hang.resize(nhang);
+    for (int64_t m = 0; m < nmaster; ++m) M.v_master[m] = potential(&M.master_xyz[3 * m], mf_master[m]);
+    for (int64_t hh = 0; hh < nhang; ++hh) M.v_hang[hh] = potential(&M.hang_xyz[3 * hh], mf_hang[hh]);
+    return AFEM_OK;
+}
+
+// ------------------------------------------------------------ upload
+template <typename T>
+static int upload(T*& dst, const T* src, size_t n) {
+    dst = nullptr;
+    if (n == 0) return AFEM_OK;
+    cudaError_t e = cudaMalloc(&dst, n * sizeof(T));
+    if (e != cudaSuccess) return set_error(AFEM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    AFEM_CUDA_TRY(cudaMemcpy(dst, src, n * sizeof(T), cudaMemcpyHostToDevice));
+    return AFEM_OK;
+}
+
+int upload_mesh(afem_mesh* m) {
+    const HostMesh& H = m->host;
+    DeviceMesh& D = m->dev;
+    const int nn = (H.p + 1) * (H.p + 1) * (H.p + 1);
+    D.p = H.p;
+    D.ncell = int64_t(H.lev.size());
+    D.n_master = H.n_master;
+    D.n_interior = H.n_interior;
+    D.n_hanging = H.n_hanging;
+    D.nnz = int64_t(H.hang_master.size());
+    std::vector<double4> geom(D.ncell);
+    for (int64_t q = 0; q < D.ncell; ++q)
+        geom[q] = make_double4(H.corner[3 * q], H.corner[3 * q + 1], H.corner[3 * q + 2], H.h[q]);
+    std::vector<double> ml_inv(H.n_master);
+    for (int64_t k = 0; k < H.n_master; ++k) ml_inv[k] = 1.0 / H.ml[k];
+    int rc;
+    if ((rc = upload(D.cell_node, H.cell_node.data(), H.cell_node.size()))) return rc;
+    if ((rc = upload(D.cell_geom, geom.data(), geom.size()))) return rc;
+    if ((rc = upload(D.hang_ptr, H.hang_ptr.data(), H.hang_ptr.size()))) return rc;
+    if ((rc = upload(D.hang_master, H.hang_master.data(), H.hang_master.size()))) return rc;
+    if ((rc = upload(D.hang_w, H.hang_w.data(), H.hang_w.size()))) return rc;
+    if ((rc = upload(D.ml, H.ml.data(), H.ml.size()))) return rc;
+    if ((rc = upload(D.ml_inv, ml_inv.data(), ml_inv.size()))) return rc;
+    if ((rc = upload(D.v_master, H.v_master.data(), H.v_master.size()))) return rc;
+    if ((rc = upload(D.v_hang, H.v_hang.data(), H.v_hang.size()))) return rc;
+    (void)nn;
+    return AFEM_OK;
+}
+
+void free_device_mesh(DeviceMesh& D) {
+    cudaFree(D.cell_node);
+    cudaFree(D.cell_geom);
+    cudaFree(D.hang_ptr);
+    cudaFree(D.hang_master);
+    cudaFree(D.hang_w);
+    cudaFree(D.ml);
+    cudaFree(D.ml_inv);
+    cudaFree(D.v_master);
+    cudaFree(D.v_hang);
+    D = DeviceMesh{};
+}
+
+}  // namespace afem

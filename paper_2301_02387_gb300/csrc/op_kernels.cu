@@ -1,0 +1,183 @@
+// Matrix-free finite-element operators on the hanging-node octree mesh.
+//
+// Sec. 3.1: with the tensor-product GLL basis and collocated GLL quadrature,
+// the cell stiffness of a cube of side h is
+//     A_K = h (Khat (x) W (x) W + W (x) Khat (x) W + W (x) W (x) Khat)
+// (Khat the 1D stiffness, W the diagonal of 1D weights), the cell mass is the
+// diagonal h^3 W (x) W (x) W and a pointwise potential f contributes
+// h^3 (w (x) w (x) w) f at the nodes.  Each output node therefore needs only
+// three 1D line contractions, so one kernel pass per cell does
+//   gather (with hanging-node interpolation, the "bridged" functions)
+//   -> sum-factorised contraction in shared memory
+//   -> scatter-add through C^T (atomics) ,
+// and the one-body operator of Eq. discretized_eom, H1~ = 1/2 A + F[V + E.r],
+// is this pass followed by the inverse lumped mass.
+#include "afem_internal.h"
+#include "cell_common.cuh"
+
+namespace afem {
+
+// ------------------------------------------------------------------ kernels
+template <int P, typename T>
+__global__ void __launch_bounds__(256) cell_op_kernel(CellArgs a, const T* __restrict__ x,
+                                                      T* __restrict__ y, int nv) {
+    constexpr int P1 = P + 1;
+    constexpr int NN = P1 * P1 * P1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* s_u = reinterpret_cast<T*>(smem_raw);
+    __shared__ int s_idx[NN];
+    __shared__ double s_pot[NN];
+    __shared__ double s_K[P1 * P1];
+    __shared__ double s_w[P1];
+
+    const int64_t cell = blockIdx.x;
+    const int tid = threadIdx.x;
+    const int bs = blockDim.x;
+    const double4 g = a.geom[cell];
+    for (int n = tid; n < NN; n += bs) s_idx[n] = a.cell_node[cell * NN + n];
+    if (tid < P1 * P1) s_K[tid] = a.B.K[tid];
+    if (tid < P1) s_w[tid] = a.B.w[tid];
+    __syncthreads();
+
+    const int total = NN * nv;
+    for (int it = tid; it < total; it += bs) {
+        const int n = it / nv;
+        const int v = it - n * nv;
+        s_u[it] = gather_value<T>(a, s_idx[n], x, nv, v);
+    }
+    if (a.with_pot) {
+        const double h3 = g.w * g.w * g.w;
+        for (int n = tid; n < NN; n += bs) {
+            const int ia = n % P1, ib = (n / P1) % P1, ic = n / (P1 * P1);
+            const int idx = s_idx[n];
+            const double V = idx >= 0 ? a.v_master[idx] : a.v_hang[-idx - 1];
+            const double px = g.x + g.w * a.B.xi[ia];
+            const double py = g.y + g.w * a.B.xi[ib];
+            const double pz = g.z + g.w * a.B.xi[ic];
+            const double f = V + a.E[0] * px + a.E[1] * py + a.E[2] * pz;
+            s_pot[n] = h3 * s_w[ia] * s_w[ib] * s_w[ic] * f;
+        }
+    }
+    __syncthreads();
+
+    const double ck = a.c_kin * g.w;
+    for (int it = tid; it < total; it += bs) {
+        const int n = it / nv;
+        const int v = it - n * nv;
+        const int ia = n % P1, ib = (n / P1) % P1, ic = n / (P1 * P1);
+        T ax = vzero<T>(), ay = vzero<T>(), az = vzero<T>();
+#pragma unroll
+        for (int m = 0; m < P1; ++m) {
+            vfma(ax, s_K[ia * P1 + m], s_u[(m + P1 * (ib + P1 * ic)) * nv + v]);
+            vfma(ay, s_K[ib * P1 + m], s_u[(ia + P1 * (m + P1 * ic)) * nv + v]);
+            vfma(az, s_K[ic * P1 + m], s_u[(ia + P1 * (ib + P1 * m)) * nv + v]);
+        }
+        T r = vzero<T>();
+        vfma(r, ck * s_w[ib] * s_w[ic], ax);
+        vfma(r, ck * s_w[ia] * s_w[ic], ay);
+        vfma(r, ck * s_w[ia] * s_w[ib], az);
+        if (a.with_pot) vfma(r, s_pot[n], s_u[it]);
+        scatter_value<T>(a, s_idx[n], y, nv, v, r);
+    }
+}
+
+template <typename T>
+__global__ void scale_rows_kernel(T* __restrict__ y, const double* __restrict__ s, int64_t n, int nv) {
+    const int64_t total = n * nv;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        y[i] = vscale(y[i], s[i / nv]);
+    }
+}
+
+// ------------------------------------------------------------------ host
+CellArgs make_cell_args(const afem_mesh* m) {
+    CellArgs a{};
+    const DeviceMesh& D = m->dev;
+    a.cell_node = D.cell_node;
+    a.geom = D.cell_geom;
+    a.hp = D.hang_ptr;
+    a.hm = D.hang_master;
+    a.hw = D.hang_w;
+    a.v_master = D.v_master;
+    a.v_hang = D.v_hang;
+    a.n_interior = D.n_interior;
+    const Basis1D& b = m->basis;
+    const int p1 = b.p + 1;
+    for (int i = 0; i < p1; ++i) {
+        a.B.xi[i] = b.xi[i];
+        a.B.w[i] = b.w[i];
+        for (int j = 0; j < p1; ++j) a.B.K[i * p1 + j] = b.K[i][j];
+    }
+    return a;
+}
+
+template <typename T>
+static int launch_cell_op(const afem_mesh* m, const CellArgs& a, const T* x, T* y, int nv,
+                          cudaStream_t s) {
+    const int p = m->dev.p;
+    const int p1 = p + 1;
+    const size_t smem = size_t(p1) * p1 * p1 * nv * sizeof(T);
+    const unsigned grid = unsigned(m->dev.ncell);
+    if (grid == 0) return AFEM_OK;
+    const int block = 256;
+    switch (p) {
+#define AFEM_CASE(PP)                                                                          \
+    case PP: {                                                                                 \
+        auto k = cell_op_kernel<PP, T>;                                                        \
+        if (smem > 48 * 1024)                                                                  \
+            AFEM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                               int(smem)));                                    \
+        k<<<grid, block, smem, s>>>(a, x, y, nv);                                              \
+        break;                                                                                 \
+    }
+        AFEM_CASE(1)
+        AFEM_CASE(2)
+        AFEM_CASE(3)
+        AFEM_CASE(4)
+#undef AFEM_CASE
+        default:
+            return set_error(AFEM_EINVAL, "degree out of range");
+    }
+    AFEM_CUDA_TRY(cudaGetLastError());
+    return AFEM_OK;
+}
+
+template <typename T>
+static int launch_scale_rows(T* y, const double* s, int64_t n, int nv, cudaStream_t st) {
+    if (n == 0) return AFEM_OK;
+    const int64_t total = n * nv;
+    const int block = 256;
+    const unsigned grid = unsigned(std::min<int64_t>((total + block - 1) / block, 152 * 32));
+    scale_rows_kernel<T><<<grid, block, 0, st>>>(y, s, n, nv);
+    AFEM_CUDA_TRY(cudaGetLastError());
+    return AFEM_OK;
+}
+
+int launch_op_apply(afem_mesh* m, int kind, const double* E, const void* x, void* y, int nv,
+                    cudaStream_t s) {
+    CellArgs a = make_cell_args(m);
+    const int64_t N = m->dev.n_master;
+    if (kind == AFEM_OP_H1) {
+        a.c_kin = 0.5;
+        a.with_pot = 1;
+        a.masked = 1;
+        for (int i = 0; i < 3; ++i) a.E[i] = E ? E[i] : 0.0;
+        auto* yy = static_cast<double2*>(y);
+        AFEM_CUDA_TRY(cudaMemsetAsync(yy, 0, size_t(N) * nv * sizeof(double2), s));
+        int rc = launch_cell_op<double2>(m, a, static_cast<const double2*>(x), yy, nv, s);
+        if (rc) return rc;
+        return launch_scale_rows<double2>(yy, m->dev.ml_inv, N, nv, s);
+    }
+    if (kind == AFEM_OP_STIFF) {
+        a.c_kin = 1.0;
+        a.with_pot = 0;
+        a.masked = 0;
+        auto* yy = static_cast<double*>(y);
+        AFEM_CUDA_TRY(cudaMemsetAsync(yy, 0, size_t(N) * nv * sizeof(double), s));
+        return launch_cell_op<double>(m, a, static_cast<const double*>(x), yy, nv, s);
+    }
+    return set_error(AFEM_EINVAL, "afem_op_apply: unknown operator kind");
+}
+
+}  // namespace afem

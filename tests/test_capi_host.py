@@ -1,0 +1,75 @@
+"""CPU checks of the C ABI library: it loads, exports every declared symbol,
+and its host mesh builder agrees exactly with the oracle's mesh."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import mesh as omesh
+from tests._match import coord_permutation
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+pytestmark = pytest.mark.filterwarnings("ignore")
+
+
+def _lib():
+    from paper_2301_02387_gb300 import _capi
+    if not os.path.exists(_capi.LIB_PATH):
+        from paper_2301_02387_gb300 import build
+        build.build(verbose=False)
+    return _capi.load()
+
+
+def test_every_declared_symbol_is_exported():
+    lib = _lib()
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        txt = open(os.path.join(ROOT, "include", h)).read()
+        names |= set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(afem_\w+)\s*\(", txt, re.M))
+    assert len(names) >= 6
+    from paper_2301_02387_gb300 import _capi
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+        assert n in _capi.SIGNATURES, n
+
+
+CASES = [
+    (-10.0, 10.0, 4, 2, [((0.0, 0.0, 0.0), 1.0, 3)], 2.0),
+    (-8.0, 8.0, 4, 3, [((0.3, -0.45, 0.7), 1.0, 2), ((-1.1, 0.2, -0.35), 2.0, 3)], 1.5),
+    (-8.0, 8.0, 3, 4, [((0.0, 0.0, 0.7), 1.0, 2), ((0.0, 0.0, -0.7), 1.0, 2)], 2.0),
+    (-6.0, 6.0, 2, 1, [((0.5, 0.5, 0.5), 8.0, 3)], 1.0),
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_host_mesh_matches_oracle(case):
+    from paper_2301_02387_gb300 import Mesh
+    lo, hi, nc, p, nuclei, c = case
+    lib_mesh = Mesh(lo, hi, nc, p, nuclei, c, host_only=True)
+    om = omesh.Mesh(lo, hi, nc, p, nuclei, c)
+    X, ml, cells = lib_mesh.tables()
+    # identical leaf sets (integer work: bit-exact)
+    assert sorted(map(tuple, cells.tolist())) == [tuple(t) for t in om.leaf_tuples()]
+    assert lib_mesh.N == om.N and lib_mesh.n_hanging == om.n_hanging
+    assert lib_mesh.n_interior == int((~om.boundary).sum())
+    assert lib_mesh.n_constraint_entries == om.C.nnz - om.N
+    perm = coord_permutation(X, om.Xm)
+    # interior-first numbering
+    assert not om.boundary[perm[:lib_mesh.n_interior]].any()
+    assert om.boundary[perm[lib_mesh.n_interior:]].all()
+    from oracle import fem
+    op = fem.Operators(om)
+    np.testing.assert_allclose(ml, op.ML[perm], rtol=1e-12)
+
+
+def test_bad_descriptions_are_rejected():
+    from paper_2301_02387_gb300 import Mesh, AfemError
+    with pytest.raises(AfemError):
+        Mesh(-1.0, 1.0, 2, 5, [], 2.0, host_only=True)
+    with pytest.raises(AfemError):
+        Mesh(1.0, -1.0, 2, 2, [], 2.0, host_only=True)
+    with pytest.raises(AfemError):
+        Mesh(-1.0, 1.0, 0, 2, [], 2.0, host_only=True)
