@@ -135,6 +135,31 @@ int afem_mesh_tables(const afem_mesh* mesh, double* coords, double* lumped_mass,
 int afem_op_apply(afem_mesh* mesh, int kind, const double* E, const void* x, void* y,
                   int n_vec, void* stream);
 
+/* Mean-field potentials of all orbital pairs by batched Poisson solves
+ * (Sec. 3.1: Delta W^r_s = -4 pi phi_r^* phi_s, Dirichlet data = the direct
+ * integral of Eq. mean-field on the box surface, solved by CG).
+ *
+ * phi: complex128 [N][n_orb] device array of orbital nodal values (surface
+ *   entries are treated as zero).  n_orb: 1..8.
+ * W: float64 [N][n_orb^2] device array, in/out.  Column c holds the real
+ *   potential of density column c: c < n_orb is |phi_c|^2; then, for each
+ *   pair r < s in row-major order, Re and Im of conj(phi_r) phi_s.  The
+ *   complex W^r_s is (Re column) + i (Im column), W^s_r its conjugate.
+ *   On return the surface rows hold the Dirichlet data (multipole expansion
+ *   about the box centre, l <= 12) and the interior rows the CG solution.
+ *   warm_start != 0 starts CG from the interior rows passed in.
+ * Jacobi-preconditioned CG per column; column c stops when
+ *   ||r_c|| <= rtol ||b_c - A_IB g_c||.  iters_out (host, may be NULL)
+ *   receives the iterations run; relres_out (host [n_orb^2], may be NULL) the
+ *   final relative residuals.
+ * Returns AFEM_ECG_MAXIT if some column has not converged after max_it
+ * iterations (W holds the last iterate), AFEM_ENAN on non-finite residuals.
+ * Allocates (grow-only) device workspace owned by the mesh on first use.
+ * Synchronises `stream` every few iterations to test convergence. */
+int afem_poisson_batch(afem_mesh* mesh, const void* phi, int n_orb, void* W, double rtol,
+                       int max_it, int warm_start, int* iters_out, double* relres_out,
+                       void* stream);
+
 #ifdef __cplusplus
 }
 #endif

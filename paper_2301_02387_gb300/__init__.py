@@ -103,6 +103,29 @@ class Mesh:
             pass
 
 
+def poisson_batch(mesh, phi, W, rtol=1e-10, max_it=20000, warm_start=False, stream=None,
+                  raise_on_maxit=True):
+    """afem_poisson_batch: pair mean fields W ([N, n^2] float64) of orbitals phi ([N, n] complex128).
+
+    Returns (iterations, relative residuals per column, status code).
+    """
+    import torch
+    n = int(phi.shape[1])
+    _dev_ptr(phi, torch.complex128, mesh.N, "phi")
+    _dev_ptr(W, torch.float64, mesh.N, "W")
+    if W.shape[1] != n * n:
+        raise ValueError("W must have n_orb^2 columns")
+    it = ctypes.c_int(0)
+    rel = np.zeros(n * n, dtype=np.float64)
+    rc = _capi.load().afem_poisson_batch(
+        mesh.handle, ctypes.c_void_p(phi.data_ptr()), n, ctypes.c_void_p(W.data_ptr()), float(rtol),
+        int(max_it), 1 if warm_start else 0, ctypes.byref(it), rel.ctypes.data_as(ctypes.c_void_p),
+        _stream_ptr(stream))
+    if rc != _capi.AFEM_OK and (raise_on_maxit or rc != _capi.AFEM_ECG_MAXIT):
+        _capi.check(rc)
+    return it.value, rel, rc
+
+
 def op_apply(mesh, kind, x, y, E=None, stream=None):
     """afem_op_apply: y = op(x) for all columns of x ([N, n_vec], DoF-major).
 

@@ -24,6 +24,27 @@ int cuda_error(cudaError_t e, const char* what);
         if (e_ != cudaSuccess) return ::afem::cuda_error(e_, #call); \
     } while (0)
 
+// Grow-only device scratch owned by a mesh.
+struct Workspace {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    int reserve(size_t need) {
+        if (need <= bytes) return AFEM_OK;
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        bytes = 0;
+        cudaError_t e = cudaMalloc(&ptr, need);
+        if (e != cudaSuccess) return set_error(AFEM_ENOMEM, std::string("workspace cudaMalloc: ") + cudaGetErrorString(e));
+        bytes = need;
+        return AFEM_OK;
+    }
+    void release() {
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        bytes = 0;
+    }
+};
+
 // 1D Gauss-Lobatto-Legendre basis on [0, 1] (Sec. 3.1).
 struct Basis1D {
     int p = 0;
@@ -54,6 +75,8 @@ struct HostMesh {
     std::vector<double> hang_w;            // [nnz]
     std::vector<double> ml;                // [N] lumped mass C^T m_f
     std::vector<double> v_master, v_hang;  // nuclear potential at masters / hanging points
+    std::vector<double> stiff_diag;        // [N] diagonal of the constrained stiffness A
+    std::vector<double> mf_master, mf_hang;  // assembled GLL weight m_f at masters / hanging points
 };
 
 int build_host_mesh(const afem_mesh_desc& d, HostMesh& out);
@@ -71,6 +94,11 @@ struct DeviceMesh {
     double* ml_inv = nullptr;       // [N]
     double* v_master = nullptr;     // [N]
     double* v_hang = nullptr;       // [nh]
+    double* stiff_dinv = nullptr;   // [N] 1 / diag(A) on interior masters, 0 on the surface
+    double* master_xyz = nullptr;   // [N][3]
+    double* hang_xyz = nullptr;     // [nh][3]
+    double* mf_master = nullptr;    // [N] assembled GLL weight m_f
+    double* mf_hang = nullptr;      // [nh]
 };
 
 }  // namespace afem
@@ -82,6 +110,7 @@ struct afem_mesh {
     afem::DeviceMesh dev;
     int device = 0;
     bool host_only = false;
+    afem::Workspace ws_poisson;
 };
 
 namespace afem {
@@ -89,4 +118,7 @@ int upload_mesh(afem_mesh* m);
 void free_device_mesh(DeviceMesh& d);
 int launch_op_apply(afem_mesh* m, int kind, const double* E, const void* x, void* y, int nvec,
                     cudaStream_t s);
+int launch_stiffness(const afem_mesh* m, const double* x, double* y, int nv, int masked, cudaStream_t s);
+int poisson_batch(afem_mesh* m, const double2* phi, int n, double* W, double rtol, int max_it, int warm,
+                  int* iters_out, double* relres_out, cudaStream_t s);
 }  // namespace afem

@@ -58,6 +58,7 @@ int afem_mesh_create_ex(const afem_mesh_desc* desc, int flags, afem_mesh** out) 
 int afem_mesh_destroy(afem_mesh* mesh) {
     if (!mesh) return AFEM_OK;
     if (!mesh->host_only) free_device_mesh(mesh->dev);
+    mesh->ws_poisson.release();
     delete mesh;
     return AFEM_OK;
 }
@@ -105,6 +106,16 @@ int afem_op_apply(afem_mesh* m, int kind, const double* E, const void* x, void* 
     if (x == y) return set_error(AFEM_EINVAL, "afem_op_apply: x and y must not alias");
     if (m->host_only) return set_error(AFEM_EINVAL, "afem_op_apply: mesh was built host-only");
     return launch_op_apply(m, kind, E, x, y, n_vec, static_cast<cudaStream_t>(stream));
+}
+
+int afem_poisson_batch(afem_mesh* m, const void* phi, int n_orb, void* W, double rtol, int max_it,
+                       int warm_start, int* iters_out, double* relres_out, void* stream) {
+    if (!m || !phi || !W) return set_error(AFEM_EINVAL, "afem_poisson_batch: null argument");
+    if (m->host_only) return set_error(AFEM_EINVAL, "afem_poisson_batch: mesh was built host-only");
+    if (n_orb < 1 || n_orb > 8) return set_error(AFEM_EINVAL, "afem_poisson_batch: n_orb must be 1..8");
+    if (!(rtol > 0.0) || max_it < 0) return set_error(AFEM_EINVAL, "afem_poisson_batch: bad rtol/max_it");
+    return poisson_batch(m, static_cast<const double2*>(phi), n_orb, static_cast<double*>(W), rtol, max_it,
+                         warm_start, iters_out, relres_out, static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

@@ -426,7 +426,10 @@ int build_host_mesh(const afem_mesh_desc& d, HostMesh& M) {
     M.master_xyz.assign(nmaster * 3, 0.0);
     M.hang_xyz.assign(nhang * 3, 0.0);
     M.ml.assign(nmaster, 0.0);
-    std::vector<double> mf_master(nmaster, 0.0), mf_hang(nhang, 0.0);
+    M.mf_master.assign(nmaster, 0.0);
+    M.mf_hang.assign(nhang, 0.0);
+    std::vector<double>& mf_master = M.mf_master;
+    std::vector<double>& mf_hang = M.mf_hang;
     for (int64_t pt = 0; pt < npts; ++pt) {
         if (master_id[pt] >= 0) {
             coord(pkey[pt], &M.master_xyz[3 * master_id[pt]]);
@@ -480,6 +483,50 @@ int build_host_mesh(const afem_mesh_desc& d, HostMesh& M) {
     M.v_hang.resize(nhang);
     for (int64_t m = 0; m < nmaster; ++m) M.v_master[m] = potential(&M.master_xyz[3 * m], mf_master[m]);
     for (int64_t hh = 0; hh < nhang; ++hh) M.v_hang[hh] = potential(&M.hang_xyz[3 * hh], mf_hang[hh]);
+
+    // ---- diagonal of the constrained stiffness A = C^T (sum_K P_K^T A_K P_K) C:
+    // per cell, each master k has local coefficients c_k (1 at its own node,
+    // the constraint weights at hanging nodes), and adds c_k^T A_K c_k.
+    M.stiff_diag.assign(nmaster, 0.0);
+    {
+        std::vector<std::pair<int32_t, std::pair<int, double>>> loc;   // (master, (node, coef))
+        for (size_t q = 0; q < ncell; ++q) {
+            loc.clear();
+            for (int n = 0; n < nn; ++n) {
+                const int32_t id = M.cell_node[q * nn + n];
+                if (id >= 0) {
+                    loc.push_back({id, {n, 1.0}});
+                } else {
+                    const int32_t hh = -id - 1;
+                    for (int32_t e = M.hang_ptr[hh]; e < M.hang_ptr[hh + 1]; ++e)
+                        loc.push_back({M.hang_master[e], {n, M.hang_w[e]}});
+                }
+            }
+            std::sort(loc.begin(), loc.end(),
+                      [](const auto& a, const auto& b) { return a.first < b.first; });
+            const double h = M.h[q];
+            auto Aloc = [&](int i, int j) {
+                const int ia = i % p1, ib = (i / p1) % p1, ic = i / (p1 * p1);
+                const int ja = j % p1, jb = (j / p1) % p1, jc = j / (p1 * p1);
+                double v = 0.0;
+                if (ib == jb && ic == jc) v += B.K[ia][ja] * B.w[ib] * B.w[ic];
+                if (ia == ja && ic == jc) v += B.w[ia] * B.K[ib][jb] * B.w[ic];
+                if (ia == ja && ib == jb) v += B.w[ia] * B.w[ib] * B.K[ic][jc];
+                return h * v;
+            };
+            for (size_t s0 = 0; s0 < loc.size();) {
+                size_t s1 = s0;
+                while (s1 < loc.size() && loc[s1].first == loc[s0].first) ++s1;
+                double acc = 0.0;
+                for (size_t a = s0; a < s1; ++a)
+                    for (size_t b = s0; b < s1; ++b)
+                        acc += loc[a].second.second * loc[b].second.second *
+                               Aloc(loc[a].second.first, loc[b].second.first);
+                M.stiff_diag[loc[s0].first] += acc;
+                s0 = s1;
+            }
+        }
+    }
     return AFEM_OK;
 }
 
@@ -519,11 +566,24 @@ int upload_mesh(afem_mesh* m) {
     if ((rc = upload(D.ml_inv, ml_inv.data(), ml_inv.size()))) return rc;
     if ((rc = upload(D.v_master, H.v_master.data(), H.v_master.size()))) return rc;
     if ((rc = upload(D.v_hang, H.v_hang.data(), H.v_hang.size()))) return rc;
+    {
+        std::vector<double> dinv(H.n_master, 0.0);
+        for (int64_t k = 0; k < H.n_interior; ++k) dinv[k] = 1.0 / H.stiff_diag[k];
+        if ((rc = upload(D.stiff_dinv, dinv.data(), dinv.size()))) return rc;
+    }
+    {
+        std::vector<double> mxyz(H.master_xyz);
+        if ((rc = upload(D.master_xyz, mxyz.data(), mxyz.size()))) return rc;
+        if ((rc = upload(D.hang_xyz, H.hang_xyz.data(), H.hang_xyz.size()))) return rc;
+        if ((rc = upload(D.mf_master, H.mf_master.data(), H.mf_master.size()))) return rc;
+        if ((rc = upload(D.mf_hang, H.mf_hang.data(), H.mf_hang.size()))) return rc;
+    }
     (void)nn;
     return AFEM_OK;
 }
 
 void free_device_mesh(DeviceMesh& D) {
+    // workspaces live on the mesh object; see afem_mesh_destroy
     cudaFree(D.cell_node);
     cudaFree(D.cell_geom);
     cudaFree(D.hang_ptr);
@@ -533,6 +593,11 @@ void free_device_mesh(DeviceMesh& D) {
     cudaFree(D.ml_inv);
     cudaFree(D.v_master);
     cudaFree(D.v_hang);
+    cudaFree(D.stiff_dinv);
+    cudaFree(D.master_xyz);
+    cudaFree(D.hang_xyz);
+    cudaFree(D.mf_master);
+    cudaFree(D.mf_hang);
     D = DeviceMesh{};
 }
 

@@ -154,6 +154,15 @@ static int launch_scale_rows(T* y, const double* s, int64_t n, int nv, cudaStrea
     return AFEM_OK;
 }
 
+int launch_stiffness(const afem_mesh* m, const double* x, double* y, int nv, int masked, cudaStream_t s) {
+    CellArgs a = make_cell_args(m);
+    a.c_kin = 1.0;
+    a.with_pot = 0;
+    a.masked = masked;
+    AFEM_CUDA_TRY(cudaMemsetAsync(y, 0, size_t(m->dev.n_master) * nv * sizeof(double), s));
+    return launch_cell_op<double>(m, a, x, y, nv, s);
+}
+
 int launch_op_apply(afem_mesh* m, int kind, const double* E, const void* x, void* y, int nv,
                     cudaStream_t s) {
     CellArgs a = make_cell_args(m);
