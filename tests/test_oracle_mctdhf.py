@@ -1,0 +1,190 @@
+"""Pins for the oracle's Arnoldi propagator (Sec. 3.2), CI algebra (Sec. 2) and
+MCTDHF step (Eqs. ci_eom, orb_eom, packed_orb_eom)."""
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+from oracle import ci, fem, krylov, mctdhf, mesh
+from paper_2301_02387_gb300 import inputs
+
+TINY = (-4.0, 4.0, 2, 2, [((0.0, 0.0, 0.35), 1.0, 1), ((0.0, 0.0, -0.35), 1.0, 1)], 2.0)
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    m = mesh.Mesh(*TINY)
+    return m, fem.Operators(m)
+
+
+# ------------------------------------------------------------------ Arnoldi
+def test_arnoldi_full_dimension_is_exact_dense_expm():
+    rng = np.random.default_rng(0)
+    n = 30
+    G = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    w = rng.random(n) + 0.5
+    phi = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    inner = lambda u, v: np.sum(np.conj(u) * w * v)
+    out, err, H, m_used, brk = krylov.arnoldi_expm(lambda v: G @ v, phi, inner, n, 0.05)
+    ref = scipy.linalg.expm(-1j * 0.05 * G) @ phi
+    assert np.linalg.norm(out - ref) < 1e-11 * np.linalg.norm(ref)
+
+
+def test_arnoldi_estimate_bounds_truncation_error():
+    rng = np.random.default_rng(1)
+    n = 60
+    A = rng.standard_normal((n, n))
+    G = (A + A.T) + 0.3 * rng.standard_normal((n, n))
+    phi = rng.standard_normal(n) + 0j
+    inner = lambda u, v: np.vdot(u, v)
+    ref = scipy.linalg.expm(-1j * 0.02 * G) @ phi
+    errs = []
+    for m in (4, 6, 8):
+        out, est, *_ = krylov.arnoldi_expm(lambda v: G @ v, phi, inner, m, 0.02)
+        true = np.linalg.norm(out - ref)
+        errs.append(true)
+        assert true < 5.0 * est + 1e-13
+    assert errs[0] > errs[1] > errs[2]
+
+
+def test_arnoldi_happy_breakdown_on_eigenvector():
+    G = np.diag([1.0, 2.0, 3.0]).astype(complex)
+    phi = np.array([0.0, 1.0, 0.0], dtype=complex)
+    out, err, H, m_used, brk = krylov.arnoldi_expm(lambda v: G @ v, phi, lambda u, v: np.vdot(u, v), 5, 0.1)
+    assert brk and m_used == 1 and err == 0.0
+    np.testing.assert_allclose(out, np.exp(-0.2j) * phi, atol=1e-15)
+
+
+# ----------------------------------------------------------------------- CI
+def test_ci_two_electron_first_quantised():
+    """For 1 alpha + 1 beta electron, H_CI acting on C_pq equals
+    h C + C h^T + sum_rs (pr|qs) C_rs (the two-particle Schroedinger operator)."""
+    n = 3
+    rng = np.random.default_rng(2)
+    h = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    h = h + h.conj().T
+    eri = rng.standard_normal((n, n, n, n)) + 1j * rng.standard_normal((n, n, n, n))
+    eri = eri + eri.transpose(2, 3, 0, 1)                 # (pq|rs) = (rs|pq)
+    eri = eri + eri.transpose(1, 0, 3, 2).conj()          # (pq|rs) = (qp|sr)^*
+    space = ci.CISpace(n, 1, 1)
+    H = space.hamiltonian(h, eri)
+    Cm = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    # alpha string of orbital p has bit-mask 1 << p -> index p; likewise beta
+    ref = h @ Cm + Cm @ h.T + np.einsum("prqs,rs->pq", eri, Cm)
+    out = (H @ Cm.ravel()).reshape(n, n)
+    np.testing.assert_allclose(out, ref, atol=1e-12)
+    np.testing.assert_allclose(H, H.conj().T, atol=1e-12)
+
+
+def test_rdm_traces_and_closed_shell_energy():
+    n, na, nb = 4, 2, 2
+    space = ci.CISpace(n, na, nb)
+    C = inputs.initial_ci(n, na, nb, seed=5, amp=0.2)
+    g1 = space.rdm1(C)
+    g2 = space.rdm2(C)
+    Ne = na + nb
+    assert abs(np.trace(g1) - Ne) < 1e-12
+    assert abs(np.einsum("pprr->", g2) - Ne * (Ne - 1)) < 1e-11
+    np.testing.assert_allclose(g1, g1.conj().T, atol=1e-14)
+    np.testing.assert_allclose(g2, g2.transpose(2, 3, 0, 1), atol=1e-14)
+    ev = np.linalg.eigvalsh(g1)
+    assert ev.min() > -1e-12 and ev.max() < 2 + 1e-12
+    # closed-shell determinant: E = 2 sum_i h_ii + sum_ij [2 (ii|jj) - (ij|ji)]
+    rng = np.random.default_rng(3)
+    h = rng.standard_normal((n, n))
+    h = h + h.T
+    eri = rng.standard_normal((n, n, n, n))
+    eri = eri + eri.transpose(1, 0, 2, 3)
+    eri = eri + eri.transpose(0, 1, 3, 2)
+    eri = eri + eri.transpose(2, 3, 0, 1)
+    H = space.hamiltonian(h, eri)
+    occ = range(na)
+    E = 2 * sum(h[i, i] for i in occ) + sum(2 * eri[i, i, j, j] - eri[i, j, j, i] for i in occ for j in occ)
+    assert abs(H[0, 0] - E) < 1e-12
+
+
+# ------------------------------------------------------------------- MCTDHF
+def _one_electron_setup(tiny):
+    m, op = tiny
+    interior = ~m.boundary
+    phi = inputs.gaussian_orbital(m.Xm, interior, alpha=1.0)[:, None]
+    phi = inputs.lowdin(phi, op.ML)
+    return m, op, phi
+
+
+def test_one_electron_step_reduces_to_tdse(tiny):
+    """One orbital, one electron: Psi = C phi follows exp(-i H t) Psi0 with a
+    first-order error: halving dt halves the deviation."""
+    m, op, phi0 = _one_electron_setup(tiny)
+    I = np.nonzero(~m.boundary)[0]
+    Hd = op.H1_matrix((0.0, 0.0, 0.05)).toarray()[np.ix_(I, I)] / op.ML[I][:, None]
+    T = 0.4
+    ref = scipy.linalg.expm(-1j * T * Hd) @ phi0[I, 0]
+    sim = mctdhf.MCTDHF(op, 1, 1, 0)
+    devs = []
+    for dt in (0.1, 0.05):
+        phi, C = phi0.copy(), np.array([1.0 + 0j])
+        for _ in range(int(round(T / dt))):
+            phi, C, info = sim.step(phi, C, (0.0, 0.0, 0.05), dt, 12)
+        devs.append(np.linalg.norm(C[0] * phi[I, 0] - ref))
+    assert 0.4 < devs[1] / devs[0] < 0.6      # first order in dt
+    assert devs[1] < 0.05
+
+
+def test_eigenvector_is_stationary(tiny):
+    """Q H1 phi0 = 0 for an eigenvector: the orbital does not move (breakdown) and
+    C picks up exp(-i eps dt)."""
+    m, op, _ = _one_electron_setup(tiny)
+    I = np.nonzero(~m.boundary)[0]
+    Hd = op.H1_matrix().toarray()[np.ix_(I, I)]
+    ev, V = scipy.linalg.eigh(Hd, np.diag(op.ML[I]))
+    phi = np.zeros((m.N, 1), dtype=complex)
+    phi[I, 0] = V[:, 0]
+    sim = mctdhf.MCTDHF(op, 1, 1, 0)
+    phi1, C1, info = sim.step(phi, np.array([1.0 + 0j]), (0.0, 0.0, 0.0), 0.05, 8)
+    assert info["breakdown"] and info["m_used"] == 1
+    np.testing.assert_allclose(phi1, phi, atol=1e-11)
+    assert abs(C1[0] - np.exp(-0.05j * ev[0])) < 1e-12
+
+
+def test_two_electron_closed_shell_is_tdhf(tiny):
+    """n = 1, one alpha + one beta: gamma = 2, Gamma = 2, so U = W_11 (time-dependent
+    Hartree-Fock); field-free energy drift shrinks with dt."""
+    m, op, phi0 = _one_electron_setup(tiny)
+    sim = mctdhf.MCTDHF(op, 1, 1, 1)
+    C0 = np.array([1.0 + 0j])
+    g1, g2 = sim.ci.rdm1(C0), sim.ci.rdm2(C0)
+    assert abs(g1[0, 0] - 2) < 1e-15 and abs(g2[0, 0, 0, 0] - 2) < 1e-15
+    W, _ = sim.mean_fields(phi0)
+    U = sim.mean_field_operator(g1, g2, W)
+    np.testing.assert_allclose(U[0, 0], W[0, 0], atol=1e-15)
+    E0 = sim.energy(phi0, C0)
+    drifts = []
+    for dt in (0.04, 0.02):
+        phi, C = phi0.copy(), C0.copy()
+        for _ in range(int(round(0.16 / dt))):
+            phi, C, _ = sim.step(phi, C, (0.0, 0.0, 0.0), dt, 10)
+        drifts.append(abs(sim.energy(phi, C) - E0))
+    assert drifts[1] < 0.7 * drifts[0]
+
+
+def test_h2_like_two_orbital_invariants(tiny):
+    m, op = tiny
+    interior = ~m.boundary
+    phi = inputs.lowdin(inputs.molecular_orbitals(m.Xm, interior, TINY[4], 2), op.ML)
+    C0 = inputs.initial_ci(2, 1, 1, amp=0.1)
+    sim = mctdhf.MCTDHF(op, 2, 1, 1)
+    E = (0.0, 0.0, 0.02)
+    drift = []
+    for dt in (0.02, 0.01):
+        p, C = phi.copy(), C0.copy()
+        for _ in range(int(round(0.06 / dt))):
+            p, C, info = sim.step(p, C, E, dt, 10)
+            assert abs(np.linalg.norm(C) - 1.0) < 1e-13
+            assert abs(np.trace(info["gamma"]) - 2.0) < 1e-12
+            assert info["arnoldi_err"] < 1e-10
+        S = np.conj(p).T @ (op.ML[:, None] * p)
+        drift.append(np.abs(S - np.eye(2)).max())
+    # the frozen-operator step is first order: orthonormality drift ~ dt
+    assert 0.4 < drift[1] / drift[0] < 0.6 and drift[0] < 2e-3
