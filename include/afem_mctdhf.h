@@ -160,6 +160,25 @@ int afem_poisson_batch(afem_mesh* mesh, const void* phi, int n_orb, void* W, dou
                        int max_it, int warm_start, int* iters_out, double* relres_out,
                        void* stream);
 
+/* One short-iterative Arnoldi step of the packed orbital equation with the
+ * operator frozen (Sec. 3.2, Eq. packed_orb_eom; Eq. orb_eom with X = 0):
+ *   (G v)_p = Q [ M_L^-1 ( H1~ v_p + C^T diag(m_f) sum_q (C U_pq) o (C v_q) ) ],
+ *   Q y = y - sum_j phi_j (phi_j^H M_L y),
+ *   phi_out = beta V_m exp(-i dt H_m) e_1   (Arnoldi, modified Gram-Schmidt,
+ *   inner product <u,v> = sum_p u_p^H M_L v_p, beta = ||phi||).
+ * phi, phi_out: complex128 [N][n_orb] device arrays (must not alias).
+ * U: complex128 [N][n_orb][n_orb] device array of mean-field operator
+ *   fields U_pq = sum_o (D^-1)^o_p sum_rs P^{qs}_{or} W^r_s at the masters,
+ *   or NULL for no mean field.  E: host double[3] field (NULL = 0).
+ * krylov_m: 1..16.  err_est (host, may be NULL): beta |h_{m+1,m}|
+ *   |e_m^T exp(-i dt H_m) e_1|, 0 after a happy breakdown; m_used and
+ *   breakdown (host, may be NULL) report the dimension actually used.
+ * Allocates (grow-only) mesh-owned workspace; synchronises `stream` once
+ * per Krylov vector (breakdown test). */
+int afem_arnoldi_step(afem_mesh* mesh, const double* E, const void* phi, const void* U, int n_orb,
+                      int krylov_m, double dt, void* phi_out, double* err_est, int* m_used,
+                      int* breakdown, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

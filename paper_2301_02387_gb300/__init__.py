@@ -126,6 +126,39 @@ def poisson_batch(mesh, phi, W, rtol=1e-10, max_it=20000, warm_start=False, stre
     return it.value, rel, rc
 
 
+def _E3(E):
+    if E is None:
+        return None
+    return (ctypes.c_double * 3)(*[float(e) for e in E])
+
+
+def arnoldi_step(mesh, phi, U, krylov_m, dt, E=None, out=None, stream=None):
+    """afem_arnoldi_step: phi_out = exp(-i G dt) phi by short-iterative Arnoldi.
+
+    phi: [N, n] complex128; U: [N, n, n] complex128 or None.  Returns
+    (phi_out, err_est, m_used, breakdown).
+    """
+    import torch
+    n = int(phi.shape[1])
+    _dev_ptr(phi, torch.complex128, mesh.N, "phi")
+    if U is not None:
+        _dev_ptr(U, torch.complex128, mesh.N, "U")
+        if tuple(U.shape[1:]) != (n, n):
+            raise ValueError("U must be [N, n, n]")
+    out = torch.empty_like(phi) if out is None else out
+    _dev_ptr(out, torch.complex128, mesh.N, "out")
+    err = ctypes.c_double(0.0)
+    mu = ctypes.c_int(0)
+    brk = ctypes.c_int(0)
+    Earr = _E3(E)
+    _capi.check(_capi.load().afem_arnoldi_step(
+        mesh.handle, ctypes.cast(Earr, ctypes.c_void_p) if Earr is not None else None,
+        ctypes.c_void_p(phi.data_ptr()), ctypes.c_void_p(U.data_ptr()) if U is not None else None,
+        n, int(krylov_m), float(dt), ctypes.c_void_p(out.data_ptr()), ctypes.byref(err), ctypes.byref(mu),
+        ctypes.byref(brk), _stream_ptr(stream)))
+    return out, err.value, mu.value, bool(brk.value)
+
+
 def op_apply(mesh, kind, x, y, E=None, stream=None):
     """afem_op_apply: y = op(x) for all columns of x ([N, n_vec], DoF-major).
 

@@ -69,6 +69,8 @@ SIGNATURES = {
     "afem_op_apply": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, ctypes.c_int, _P]),
     "afem_poisson_batch": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_double, ctypes.c_int,
                                           ctypes.c_int, _P, _P, _P]),
+    "afem_arnoldi_step": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_double, _P,
+                                         _P, _P, _P, _P]),
 }
 
 

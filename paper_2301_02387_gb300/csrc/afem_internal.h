@@ -111,6 +111,7 @@ struct afem_mesh {
     int device = 0;
     bool host_only = false;
     afem::Workspace ws_poisson;
+    afem::Workspace ws_arnoldi;
 };
 
 namespace afem {

@@ -1,0 +1,28 @@
+// Arnoldi workspace layout and the G-operator entry points shared by the
+// Arnoldi step and the MCTDHF step.
+#pragma once
+
+#include "afem_internal.h"
+
+namespace afem {
+
+constexpr int kMaxKrylov = 16;
+
+struct ArnoldiWork {
+    double2* V;          // [m+1][N][n] Krylov basis
+    double2* z;          // [N][n] cell-pass output
+    double2* cpartial;   // reduction partials
+    double2* S;          // [n][n] projector overlaps
+    double2* H;          // (kMaxKrylov+1) x kMaxKrylov Hessenberg, column-major
+    double2* E;          // exp(-i dt H_m)
+    double2* y;          // beta E e_1
+    double2* beta2;      // scalar scratch
+    int64_t stride;      // N * n
+};
+
+int cdot(const double2* A, int na, const double2* B, int nb, const double* w, int64_t rows, int diag,
+         double2* partial, double2* out, int sum_all, cudaStream_t s);
+int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double2* U, int n, int mk, double dt,
+                 double2* phi_out, double* err_est, int* m_used_out, int* breakdown_out, cudaStream_t s);
+
+}  // namespace afem

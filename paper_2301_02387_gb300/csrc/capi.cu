@@ -3,6 +3,7 @@
 #include <new>
 
 #include "afem_internal.h"
+#include "arnoldi.cuh"
 
 namespace afem {
 const char* last_error_cstr();
@@ -59,6 +60,7 @@ int afem_mesh_destroy(afem_mesh* mesh) {
     if (!mesh) return AFEM_OK;
     if (!mesh->host_only) free_device_mesh(mesh->dev);
     mesh->ws_poisson.release();
+    mesh->ws_arnoldi.release();
     delete mesh;
     return AFEM_OK;
 }
@@ -116,6 +118,18 @@ int afem_poisson_batch(afem_mesh* m, const void* phi, int n_orb, void* W, double
     if (!(rtol > 0.0) || max_it < 0) return set_error(AFEM_EINVAL, "afem_poisson_batch: bad rtol/max_it");
     return poisson_batch(m, static_cast<const double2*>(phi), n_orb, static_cast<double*>(W), rtol, max_it,
                          warm_start, iters_out, relres_out, static_cast<cudaStream_t>(stream));
+}
+
+int afem_arnoldi_step(afem_mesh* m, const double* E, const void* phi, const void* U, int n_orb, int krylov_m,
+                      double dt, void* phi_out, double* err_est, int* m_used, int* breakdown, void* stream) {
+    if (!m || !phi || !phi_out) return set_error(AFEM_EINVAL, "afem_arnoldi_step: null argument");
+    if (m->host_only) return set_error(AFEM_EINVAL, "afem_arnoldi_step: mesh was built host-only");
+    if (n_orb < 1 || n_orb > 8) return set_error(AFEM_EINVAL, "afem_arnoldi_step: n_orb must be 1..8");
+    if (krylov_m < 1 || krylov_m > kMaxKrylov) return set_error(AFEM_EINVAL, "afem_arnoldi_step: krylov_m must be 1..16");
+    if (phi == phi_out) return set_error(AFEM_EINVAL, "afem_arnoldi_step: phi and phi_out must not alias");
+    return arnoldi_step(m, E, static_cast<const double2*>(phi), static_cast<const double2*>(U), n_orb, krylov_m,
+                        dt, static_cast<double2*>(phi_out), err_est, m_used, breakdown,
+                        static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

@@ -81,6 +81,125 @@ __global__ void __launch_bounds__(256) cell_op_kernel(CellArgs a, const T* __res
     }
 }
 
+// Packed orbital operator before projection and inverse mass (Eqs. orb_eom,
+// discretized_eom):  z_p = H1~ v_p + C^T diag(m_f) sum_q (C U_pq) o (C v_q),
+// for all n orbitals of one cell at once.  U: complex [N][n][n] nodal fields.
+template <int P>
+__global__ void __launch_bounds__(256) g_cell_kernel(CellArgs a, const double2* __restrict__ v,
+                                                     const double2* __restrict__ U, double2* __restrict__ z,
+                                                     int n) {
+    constexpr int P1 = P + 1;
+    constexpr int NN = P1 * P1 * P1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double2* s_u = reinterpret_cast<double2*>(smem_raw);   // [NN][n]
+    double2* s_U = s_u + NN * n;                            // [NN][n*n]
+    __shared__ int s_idx[NN];
+    __shared__ double s_pot[NN];
+    __shared__ double s_wq[NN];
+    __shared__ double s_K[P1 * P1];
+    __shared__ double s_w[P1];
+
+    const int64_t cell = blockIdx.x;
+    const int tid = threadIdx.x;
+    const int bs = blockDim.x;
+    const double4 g = a.geom[cell];
+    for (int i = tid; i < NN; i += bs) s_idx[i] = a.cell_node[cell * NN + i];
+    if (tid < P1 * P1) s_K[tid] = a.B.K[tid];
+    if (tid < P1) s_w[tid] = a.B.w[tid];
+    __syncthreads();
+    const int nn2 = n * n;
+    for (int it = tid; it < NN * n; it += bs) {
+        const int i = it / n, q = it - i * n;
+        s_u[it] = gather_value<double2>(a, s_idx[i], v, n, q);
+    }
+    if (U) {
+        CellArgs au = a;
+        au.masked = 0;   // the mean fields are defined on all masters
+        for (int it = tid; it < NN * nn2; it += bs) {
+            const int i = it / nn2, pq = it - i * nn2;
+            s_U[it] = gather_value<double2>(au, s_idx[i], U, nn2, pq);
+        }
+    }
+    {
+        const double h3 = g.w * g.w * g.w;
+        for (int i = tid; i < NN; i += bs) {
+            const int ia = i % P1, ib = (i / P1) % P1, ic = i / (P1 * P1);
+            const int idx = s_idx[i];
+            const double V = idx >= 0 ? a.v_master[idx] : a.v_hang[-idx - 1];
+            const double px = g.x + g.w * a.B.xi[ia];
+            const double py = g.y + g.w * a.B.xi[ib];
+            const double pz = g.z + g.w * a.B.xi[ic];
+            const double wq = h3 * s_w[ia] * s_w[ib] * s_w[ic];
+            s_wq[i] = wq;
+            s_pot[i] = wq * (V + a.E[0] * px + a.E[1] * py + a.E[2] * pz);
+        }
+    }
+    __syncthreads();
+    const double ck = 0.5 * g.w;
+    for (int it = tid; it < NN * n; it += bs) {
+        const int i = it / n, p = it - i * n;
+        const int ia = i % P1, ib = (i / P1) % P1, ic = i / (P1 * P1);
+        double2 ax = vzero<double2>(), ay = vzero<double2>(), az = vzero<double2>();
+#pragma unroll
+        for (int m = 0; m < P1; ++m) {
+            vfma(ax, s_K[ia * P1 + m], s_u[(m + P1 * (ib + P1 * ic)) * n + p]);
+            vfma(ay, s_K[ib * P1 + m], s_u[(ia + P1 * (m + P1 * ic)) * n + p]);
+            vfma(az, s_K[ic * P1 + m], s_u[(ia + P1 * (ib + P1 * m)) * n + p]);
+        }
+        double2 r = vzero<double2>();
+        vfma(r, ck * s_w[ib] * s_w[ic], ax);
+        vfma(r, ck * s_w[ia] * s_w[ic], ay);
+        vfma(r, ck * s_w[ia] * s_w[ib], az);
+        vfma(r, s_pot[i], s_u[it]);
+        if (U) {
+            double2 mf = vzero<double2>();
+            const double2* Ui = s_U + i * nn2 + p * n;
+            const double2* ui = s_u + i * n;
+            for (int q = 0; q < n; ++q) {
+                mf.x = fma(Ui[q].x, ui[q].x, fma(-Ui[q].y, ui[q].y, mf.x));
+                mf.y = fma(Ui[q].x, ui[q].y, fma(Ui[q].y, ui[q].x, mf.y));
+            }
+            vfma(r, s_wq[i], mf);
+        }
+        scatter_value<double2>(a, s_idx[i], z, n, p, r);
+    }
+}
+
+int launch_g_cell(const afem_mesh* m, const double* E, const double2* v, const double2* U, double2* z, int n,
+                  cudaStream_t s) {
+    CellArgs a = make_cell_args(m);
+    a.c_kin = 0.5;
+    a.with_pot = 1;
+    a.masked = 1;
+    for (int i = 0; i < 3; ++i) a.E[i] = E ? E[i] : 0.0;
+    const int p = m->dev.p;
+    const int nn = (p + 1) * (p + 1) * (p + 1);
+    const size_t smem = size_t(nn) * n * sizeof(double2) + (U ? size_t(nn) * n * n * sizeof(double2) : 0);
+    const unsigned grid = unsigned(m->dev.ncell);
+    AFEM_CUDA_TRY(cudaMemsetAsync(z, 0, size_t(m->dev.n_master) * n * sizeof(double2), s));
+    if (grid == 0) return AFEM_OK;
+    switch (p) {
+#define AFEM_CASE(PP)                                                                          \
+    case PP: {                                                                                 \
+        auto k = g_cell_kernel<PP>;                                                            \
+        if (smem > 48 * 1024)                                                                  \
+            AFEM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                               int(smem)));                                    \
+        k<<<grid, 256, smem, s>>>(a, v, U, z, n);                                              \
+        break;                                                                                 \
+    }
+        AFEM_CASE(1)
+        AFEM_CASE(2)
+        AFEM_CASE(3)
+        AFEM_CASE(4)
+#undef AFEM_CASE
+        default:
+            return set_error(AFEM_EINVAL, "degree out of range");
+    }
+    AFEM_CUDA_TRY(cudaGetLastError());
+    return AFEM_OK;
+}
+
 template <typename T>
 __global__ void scale_rows_kernel(T* __restrict__ y, const double* __restrict__ s, int64_t n, int nv) {
     const int64_t total = n * nv;

@@ -462,29 +462,31 @@ int poisson_batch(afem_mesh* m, const double2* phi, int n, double* W, double rto
     const int64_t N = D.n_master, Ni = D.n_interior;
     const int nblk = kRedBlocks;
     const size_t NK = size_t(N) * k;
-    size_t need = carve_size({NK * 8, NK * 8, NK * 8, NK * 8, NK * 8, NK * 8, size_t(nblk) * 3 * k * 8,
-                              size_t(kMomBlocks) * kNlm * k * 8, size_t(kNlm) * k * 8, 5 * size_t(k) * 8,
-                              size_t(k + 1) * 4});
-    int rc = m->ws_poisson.reserve(need);
+    PoissonWork w{};
+    auto carve = [&](Carver& cv) {
+        w.b = cv.take<double>(NK);
+        w.r = cv.take<double>(NK);
+        w.z = cv.take<double>(NK);
+        w.p = cv.take<double>(NK);
+        w.Ap = cv.take<double>(NK);
+        w.t = cv.take<double>(NK);
+        w.partial = cv.take<double>(size_t(nblk) * 3 * k);
+        w.qpart = cv.take<double>(size_t(kMomBlocks) * kNlm * k);
+        w.q = cv.take<double>(size_t(kNlm) * k);
+        w.alpha = cv.take<double>(k);
+        w.beta = cv.take<double>(k);
+        w.rz = cv.take<double>(k);
+        w.bb = cv.take<double>(k);
+        w.rr = cv.take<double>(k);
+        w.active = cv.take<int>(k);
+        w.n_active = cv.take<int>(1);
+    };
+    Carver measure(nullptr);
+    carve(measure);
+    int rc = m->ws_poisson.reserve(measure.size());
     if (rc) return rc;
     Carver cv(m->ws_poisson.ptr);
-    PoissonWork w{};
-    w.b = cv.take<double>(NK);
-    w.r = cv.take<double>(NK);
-    w.z = cv.take<double>(NK);
-    w.p = cv.take<double>(NK);
-    w.Ap = cv.take<double>(NK);
-    w.t = cv.take<double>(NK);
-    w.partial = cv.take<double>(size_t(nblk) * 3 * k);
-    w.qpart = cv.take<double>(size_t(kMomBlocks) * kNlm * k);
-    w.q = cv.take<double>(size_t(kNlm) * k);
-    w.alpha = cv.take<double>(k);
-    w.beta = cv.take<double>(k);
-    w.rz = cv.take<double>(k);
-    w.bb = cv.take<double>(k);
-    w.rr = cv.take<double>(k);
-    w.active = cv.take<int>(k);
-    w.n_active = cv.take<int>(1);
+    carve(cv);
     PcgState st{w.alpha, w.beta, w.rz, w.bb, w.rr, w.active, w.n_active, rtol * rtol};
 
     if (!warm) AFEM_CUDA_TRY(cudaMemsetAsync(W, 0, NK * sizeof(double), s));

@@ -34,7 +34,10 @@ __device__ __forceinline__ void reduce_columns(double* s, int k, int R, double* 
 __global__ void finalize_columns_kernel(const double* __restrict__ partial, int nblk, int k,
                                         double* __restrict__ out);
 
-// Carve aligned sub-buffers out of one allocation.
+// Carve 256-byte-aligned sub-buffers out of one allocation.  A Carver built
+// with a null base only measures: run the same sequence of take() calls once
+// to size the allocation, then again on the real base, so the two can never
+// disagree.
 struct Carver {
     char* base;
     size_t off = 0;
@@ -42,16 +45,12 @@ struct Carver {
     template <typename T>
     T* take(size_t n) {
         off = (off + 255) & ~size_t(255);
-        T* p = reinterpret_cast<T*>(base + off);
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
         off += n * sizeof(T);
         return p;
     }
+    size_t size() const { return off + 256; }
 };
-inline size_t carve_size(std::initializer_list<size_t> sizes) {
-    size_t s = 0;
-    for (size_t b : sizes) s = ((s + 255) & ~size_t(255)) + b;
-    return s + 256;
-}
 
 inline unsigned grid_for(int64_t n, int block = 256, int64_t cap = 152 * 16) {
     int64_t g = (n + block - 1) / block;

@@ -1,0 +1,77 @@
+"""GPU parity of afem_arnoldi_step (Sec. 3.2, Eq. packed_orb_eom) against the
+oracle's Arnoldi on its assembled G operator.  FP64 bar: 1e-10 relative."""
+import numpy as np
+import pytest
+
+from oracle import fem, krylov, mctdhf, mesh as omesh
+from paper_2301_02387_gb300 import inputs
+from tests._match import coord_permutation
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    ((-8.0, 8.0, 3, 2, [((0.0, 0.0, 0.7), 1.0, 2), ((0.0, 0.0, -0.7), 1.0, 2)], 2.0), 2, True),
+    ((-8.0, 8.0, 3, 3, [((0.3, -0.45, 0.7), 1.0, 2), ((-1.1, 0.2, -0.35), 2.0, 2)], 1.5), 3, True),
+    ((-6.0, 6.0, 2, 4, [((0.0, 0.0, 0.0), 1.0, 2)], 2.0), 1, False),
+]
+
+
+def _fields(X, n, seed):
+    rng = np.random.default_rng(seed)
+    U = np.zeros((n, n, len(X)), dtype=np.complex128)
+    for p in range(n):
+        for q in range(n):
+            c = rng.standard_normal(3)
+            U[p, q] = (0.3 + 0.2j * rng.standard_normal()) * np.exp(-0.2 * np.sum((X - c) ** 2, axis=1))
+    return U
+
+
+@pytest.mark.parametrize("case,n,with_U", CASES)
+@pytest.mark.parametrize("m", [1, 6, 10])
+def test_arnoldi_step_parity(case, n, with_U, m):
+    import torch
+    import paper_2301_02387_gb300 as pkg
+    gm = pkg.Mesh(*case)
+    om = omesh.Mesh(*case)
+    op = fem.Operators(om)
+    X, _, _ = gm.tables()
+    perm = coord_permutation(X, om.Xm)
+    interior = ~om.boundary
+    phi_o = inputs.lowdin(inputs.molecular_orbitals(om.Xm, interior, case[4], n), op.ML)
+    U_o = _fields(om.Xm, n, 3) if with_U else np.zeros((n, n, om.N), dtype=np.complex128)
+    E = (0.01, -0.02, 0.03)
+    sim = mctdhf.MCTDHF.__new__(mctdhf.MCTDHF)
+    sim.ops, sim.mesh, sim.n = op, om, n
+    sim.interior = interior.astype(np.float64)
+    ref, err, H, m_used, brk = krylov.arnoldi_expm(
+        lambda v: sim.G_apply(v, phi_o, U_o, E), phi_o, sim.inner, m, 0.02)
+    phi = torch.from_numpy(np.ascontiguousarray(phi_o[perm])).cuda()
+    U = torch.from_numpy(np.ascontiguousarray(U_o.transpose(2, 0, 1)[perm])).cuda() if with_U else None
+    out, err_g, mu, brk_g = pkg.arnoldi_step(gm, phi, U, m, 0.02, E=E)
+    torch.cuda.synchronize()
+    og = out.cpu().numpy()
+    rel = np.linalg.norm(og - ref[perm]) / np.linalg.norm(ref)
+    assert rel < 1e-10
+    assert mu == m_used and brk_g == brk
+    assert abs(err_g - err) <= 1e-6 * abs(err) + 1e-18
+
+
+def test_arnoldi_eigenvector_breakdown():
+    """A discrete eigenvector of M_L^-1 H1~ is a fixed point of G (Q H phi0 = 0)."""
+    import scipy.linalg
+    import torch
+    import paper_2301_02387_gb300 as pkg
+    case = (-5.0, 5.0, 2, 2, [((0.0, 0.0, 0.0), 1.0, 1)], 2.0)
+    gm = pkg.Mesh(*case)
+    om = omesh.Mesh(*case)
+    op = fem.Operators(om)
+    X, _, _ = gm.tables()
+    perm = coord_permutation(X, om.Xm)
+    I = np.nonzero(~om.boundary)[0]
+    ev, V = scipy.linalg.eigh(op.H1_matrix().toarray()[np.ix_(I, I)], np.diag(op.ML[I]))
+    phi_o = np.zeros((om.N, 1), dtype=np.complex128)
+    phi_o[I, 0] = V[:, 0]
+    phi = torch.from_numpy(np.ascontiguousarray(phi_o[perm])).cuda()
+    out, err, mu, brk = pkg.arnoldi_step(gm, phi, None, 8, 0.05)
+    assert brk and mu == 1 and err == 0.0
+    np.testing.assert_allclose(out.cpu().numpy(), phi_o[perm], atol=1e-10)
