@@ -87,6 +87,11 @@ typedef struct afem_mesh afem_mesh;   /* opaque */
 /* Message describing the last failure on this host thread ("" if none). */
 const char* afem_last_error(void);
 
+/* Number of CUDA kernels this library has launched in this process so far
+ * (host-side counter, all devices and threads).  Library bookkeeping with no
+ * counterpart in the paper. */
+int afem_kernel_launch_count(int64_t* count);
+
 /* Build the mesh on the host and upload every table to the current device.
  * Sec. 3.1 (coarse cubes halved toward the nuclei; GLL tensor basis; bridged
  * functions).  *out receives a library-owned object; free it with
@@ -178,6 +183,49 @@ int afem_poisson_batch(afem_mesh* mesh, const void* phi, int n_orb, void* W, dou
 int afem_arnoldi_step(afem_mesh* mesh, const double* E, const void* phi, const void* U, int n_orb,
                       int krylov_m, double dt, void* phi_out, double* err_est, int* m_used,
                       int* breakdown, void* stream);
+
+/* MCTDHF time stepper (Sec. 2 and Sec. 3.2): owns the determinant-space
+ * tables and its device workspace; the mesh must outlive it. */
+typedef struct afem_mctdhf afem_mctdhf;
+
+typedef struct afem_step_info {
+    double energy;          /* electronic energy at t: sum h_pq gamma_pq + 1/2 sum (pq|rs) Gamma_pqrs */
+    double arnoldi_err;     /* Krylov error estimate of the orbital step */
+    double cg_relres_max;   /* largest final relative residual of the Poisson batch */
+    int32_t krylov_m_used;
+    int32_t breakdown;
+    int32_t cg_iters;
+    int32_t pad0;
+} afem_step_info;
+
+/* n_orb spatial orbitals (1..8), n_alpha / n_beta electrons per spin
+ * (0..n_orb each, not both 0), Krylov dimension krylov_m (1..16).  The CI
+ * vector holds all determinants: index I = i_alpha * n_beta_strings + i_beta,
+ * strings of occupied orbitals ordered by ascending bit mask (bit p =
+ * orbital p); |I> = prod_alpha a+ prod_beta a+ |0> in ascending orbital order.
+ * Synchronous. */
+int afem_mctdhf_create(afem_mesh* mesh, int n_orb, int n_alpha, int n_beta, int krylov_m,
+                       afem_mctdhf** out);
+int afem_mctdhf_destroy(afem_mctdhf* solver);
+/* Number of determinants (host). */
+int afem_mctdhf_ci_dim(const afem_mctdhf* solver, int64_t* dim);
+
+/* One time step t -> t + dt with the field E(t) frozen (first order, Sec. 3.2):
+ *   W <- pair mean fields of phi(t) (afem_poisson_batch, warm-started from W);
+ *   h_pq, (pq|rs), gamma, Gamma at t; C <- exp(-i dt H_CI(t)) C (Eq. ci_eom,
+ *   X = 0; Taylor series of H_CI - <H_CI> with 30 terms, accurate while
+ *   ||H_CI - <H_CI>|| dt <= 3); phi <- exp(-i G(t) dt) phi by short-iterative
+ *   Arnoldi (Eq. packed_orb_eom).
+ * phi: complex128 [N][n_orb] device, in/out (surface rows must be zero).
+ * C: complex128 [ci_dim] device, in/out.  W: float64 [N][n_orb^2] device,
+ *   in/out (column layout of afem_poisson_batch; pass zeros at the first step).
+ * E: host double[3] (NULL = 0).  info: host, may be NULL.
+ * Returns AFEM_ESINGULAR if the one-body density matrix cannot be inverted
+ * (nothing is updated then), AFEM_ECG_MAXIT if the Poisson batch did not reach
+ * cg_rtol (the step is still taken with the last iterate).
+ * Synchronises `stream` several times per step. */
+int afem_mctdhf_step(afem_mctdhf* solver, void* phi, void* C, void* W, const double* E, double dt,
+                     double cg_rtol, int cg_max_it, afem_step_info* info, void* stream);
 
 #ifdef __cplusplus
 }

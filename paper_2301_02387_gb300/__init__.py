@@ -159,6 +159,53 @@ def arnoldi_step(mesh, phi, U, krylov_m, dt, E=None, out=None, stream=None):
     return out, err.value, mu.value, bool(brk.value)
 
 
+class MCTDHF:
+    """afem_mctdhf_*: the MCTDHF time stepper of one mesh (Sec. 2, Sec. 3.2).
+
+    State lives in caller tensors: phi [N, n] complex128, C [ci_dim] complex128,
+    W [N, n^2] float64 (zeros before the first step).
+    """
+
+    def __init__(self, mesh, n_orb, n_alpha, n_beta, krylov_m):
+        self.mesh = mesh
+        self.n, self.n_alpha, self.n_beta, self.krylov_m = n_orb, n_alpha, n_beta, krylov_m
+        h = ctypes.c_void_p()
+        _capi.check(_capi.load().afem_mctdhf_create(mesh.handle, n_orb, n_alpha, n_beta, krylov_m,
+                                                    ctypes.byref(h)))
+        self._h = h
+        d = ctypes.c_int64(0)
+        _capi.check(_capi.load().afem_mctdhf_ci_dim(h, ctypes.byref(d)))
+        self.ci_dim = d.value
+
+    def step(self, phi, C, W, E, dt, cg_rtol=1e-10, cg_max_it=20000, stream=None, raise_on_maxit=True):
+        import torch
+        _dev_ptr(phi, torch.complex128, self.mesh.N, "phi")
+        _dev_ptr(C, torch.complex128, self.ci_dim, "C")
+        _dev_ptr(W, torch.float64, self.mesh.N, "W")
+        info = _capi.StepInfo()
+        Earr = _E3(E)
+        rc = _capi.load().afem_mctdhf_step(
+            self._h, ctypes.c_void_p(phi.data_ptr()), ctypes.c_void_p(C.data_ptr()),
+            ctypes.c_void_p(W.data_ptr()), ctypes.cast(Earr, ctypes.c_void_p) if Earr is not None else None,
+            float(dt), float(cg_rtol), int(cg_max_it), ctypes.byref(info), _stream_ptr(stream))
+        if rc != _capi.AFEM_OK and (raise_on_maxit or rc != _capi.AFEM_ECG_MAXIT):
+            _capi.check(rc)
+        return dict(energy=info.energy, arnoldi_err=info.arnoldi_err, cg_relres_max=info.cg_relres_max,
+                    krylov_m_used=info.krylov_m_used, breakdown=bool(info.breakdown), cg_iters=info.cg_iters,
+                    status=rc)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _capi.load().afem_mctdhf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def op_apply(mesh, kind, x, y, E=None, stream=None):
     """afem_op_apply: y = op(x) for all columns of x ([N, n_vec], DoF-major).
 

@@ -49,6 +49,15 @@ class MeshInfo(ctypes.Structure):
     ]
 
 
+class StepInfo(ctypes.Structure):
+    _fields_ = [
+        ("energy", ctypes.c_double), ("arnoldi_err", ctypes.c_double),
+        ("cg_relres_max", ctypes.c_double),
+        ("krylov_m_used", ctypes.c_int32), ("breakdown", ctypes.c_int32),
+        ("cg_iters", ctypes.c_int32), ("pad0", ctypes.c_int32),
+    ]
+
+
 class AfemError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"afem error {code}: {msg}")
@@ -61,6 +70,7 @@ _lib = None
 _P = ctypes.c_void_p
 SIGNATURES = {
     "afem_last_error": (ctypes.c_char_p, []),
+    "afem_kernel_launch_count": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int64)]),
     "afem_mesh_create": (ctypes.c_int, [ctypes.POINTER(MeshDesc), ctypes.POINTER(_P)]),
     "afem_mesh_create_ex": (ctypes.c_int, [ctypes.POINTER(MeshDesc), ctypes.c_int, ctypes.POINTER(_P)]),
     "afem_mesh_destroy": (ctypes.c_int, [_P]),
@@ -71,6 +81,12 @@ SIGNATURES = {
                                           ctypes.c_int, _P, _P, _P]),
     "afem_arnoldi_step": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_double, _P,
                                          _P, _P, _P, _P]),
+    "afem_mctdhf_create": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.POINTER(_P)]),
+    "afem_mctdhf_destroy": (ctypes.c_int, [_P]),
+    "afem_mctdhf_ci_dim": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
+    "afem_mctdhf_step": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                        ctypes.POINTER(StepInfo), _P]),
 }
 
 

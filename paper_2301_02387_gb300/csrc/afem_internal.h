@@ -18,7 +18,17 @@ constexpr int kMaxP1 = kMaxDegree + 1;
 int set_error(int code, const std::string& msg);
 int cuda_error(cudaError_t e, const char* what);
 
-#define AFEM_CUDA_TRY(call)                                      \
+// Host-side count of kernel launches made by this library (process-wide).
+void note_launch();
+int64_t launch_count();
+
+#define AFEM_LAUNCH(kern, grid, block, smem, stream, ...)           \
+    do {                                                             \
+        ::afem::note_launch();                                       \
+        kern<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);    \
+    } while (0)
+
+#define AFEM_CUDA_TRY(call)                                    \
     do {                                                         \
         cudaError_t e_ = (call);                                 \
         if (e_ != cudaSuccess) return ::afem::cuda_error(e_, #call); \
@@ -122,4 +132,9 @@ int launch_op_apply(afem_mesh* m, int kind, const double* E, const void* x, void
 int launch_stiffness(const afem_mesh* m, const double* x, double* y, int nv, int masked, cudaStream_t s);
 int poisson_batch(afem_mesh* m, const double2* phi, int n, double* W, double rtol, int max_it, int warm,
                   int* iters_out, double* relres_out, cudaStream_t s);
+int mctdhf_create(afem_mesh* m, int n, int na, int nb, int mk, afem_mctdhf** out);
+void mctdhf_destroy(afem_mctdhf* S);
+int64_t mctdhf_ci_dim(const afem_mctdhf* S);
+int mctdhf_step(afem_mctdhf* S, double2* phi, double2* C, double* W, const double* E, double dt, double cg_rtol,
+                int cg_max_it, afem_step_info* info, cudaStream_t s);
 }  // namespace afem

@@ -266,8 +266,8 @@ int launch_g_cell(const afem_mesh* m, const double* E, const double2* v, const d
 int cdot(const double2* A, int na, const double2* B, int nb, const double* w, int64_t rows, int diag,
          double2* partial, double2* out, int sum_all, cudaStream_t s) {
     const int kout = diag ? na : na * nb;
-    cdot_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(A, na, B, nb, w, rows, diag, partial);
-    cfinalize_kernel<<<1, 256, 0, s>>>(partial, kRedBlocks, kout, sum_all, out);
+    AFEM_LAUNCH((cdot_kernel), kRedBlocks, kRedThreads, 0, s, A, na, B, nb, w, rows, diag, partial);
+    AFEM_LAUNCH((cfinalize_kernel), 1, 256, 0, s, partial, kRedBlocks, kout, sum_all, out);
     AFEM_CUDA_TRY(cudaGetLastError());
     return AFEM_OK;
 }
@@ -279,7 +279,7 @@ int g_apply(afem_mesh* m, const double* E, const double2* phi, const double2* U,
     if (rc) return rc;
     // S[j][p] = phi_j^H z_p  (equals phi_j^H M_L y_p)
     if ((rc = cdot(phi, n, z, n, nullptr, D.n_interior, 0, w.cpartial, w.S, 0, s))) return rc;
-    project_kernel<<<grid_for(D.n_master * n), 256, 0, s>>>(z, phi, w.S, D.ml_inv, D.n_interior, D.n_master, n,
+    AFEM_LAUNCH((project_kernel), grid_for(D.n_master * n), 256, 0, s, z, phi, w.S, D.ml_inv, D.n_interior, D.n_master, n,
                                                             out);
     AFEM_CUDA_TRY(cudaGetLastError());
     return AFEM_OK;
@@ -318,11 +318,11 @@ int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double
     const int ldh = kMaxKrylov + 1;
     AFEM_CUDA_TRY(cudaMemsetAsync(w.H, 0, sizeof(double2) * ldh * kMaxKrylov, s));
     // beta^2 = <phi, phi>_M ; V_0 = phi / beta
-    mgs_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(const_cast<double2*>(phi), nullptr, nullptr, nullptr, D.ml,
+    AFEM_LAUNCH((mgs_kernel), kRedBlocks, kRedThreads, 0, s, const_cast<double2*>(phi), nullptr, nullptr, nullptr, D.ml,
                                                   D.n_interior, n, w.cpartial);
-    sum_partials_kernel<<<1, 32, 0, s>>>(w.cpartial, kRedBlocks, w.beta2);
+    AFEM_LAUNCH((sum_partials_kernel), 1, 32, 0, s, w.cpartial, kRedBlocks, w.beta2);
     AFEM_CUDA_TRY(cudaMemcpyAsync(w.V, phi, NV * sizeof(double2), cudaMemcpyDeviceToDevice, s));
-    cscale_kernel<<<grid_for(NV), 256, 0, s>>>(w.V, NV, w.beta2, 1.0, 1);
+    AFEM_LAUNCH((cscale_kernel), grid_for(NV), 256, 0, s, w.V, NV, w.beta2, 1.0, 1);
     AFEM_CUDA_TRY(cudaGetLastError());
     double2 beta2_h;
     AFEM_CUDA_TRY(cudaMemcpyAsync(&beta2_h, w.beta2, sizeof(double2), cudaMemcpyDeviceToHost, s));
@@ -340,14 +340,14 @@ int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double
         for (int i = 0; i <= j; ++i) {
             const double2* Vprev = i > 0 ? w.V + (i - 1) * NV : nullptr;
             const double2* hprev = i > 0 ? w.H + j * ldh + (i - 1) : nullptr;
-            mgs_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(Wn, Vprev, hprev, w.V + i * NV, D.ml, D.n_interior, n,
+            AFEM_LAUNCH((mgs_kernel), kRedBlocks, kRedThreads, 0, s, Wn, Vprev, hprev, w.V + i * NV, D.ml, D.n_interior, n,
                                                           w.cpartial);
-            sum_partials_kernel<<<1, 32, 0, s>>>(w.cpartial, kRedBlocks, w.H + j * ldh + i);
+            AFEM_LAUNCH((sum_partials_kernel), 1, 32, 0, s, w.cpartial, kRedBlocks, w.H + j * ldh + i);
         }
         // last update and the norm
-        mgs_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(Wn, w.V + j * NV, w.H + j * ldh + j, nullptr, D.ml,
+        AFEM_LAUNCH((mgs_kernel), kRedBlocks, kRedThreads, 0, s, Wn, w.V + j * NV, w.H + j * ldh + j, nullptr, D.ml,
                                                       D.n_interior, n, w.cpartial);
-        sum_partials_kernel<<<1, 32, 0, s>>>(w.cpartial, kRedBlocks, w.beta2);
+        AFEM_LAUNCH((sum_partials_kernel), 1, 32, 0, s, w.cpartial, kRedBlocks, w.beta2);
         AFEM_CUDA_TRY(cudaGetLastError());
         double2 nn2;
         AFEM_CUDA_TRY(cudaMemcpyAsync(&nn2, w.beta2, sizeof(double2), cudaMemcpyDeviceToHost, s));
@@ -362,10 +362,10 @@ int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double
             brk = 1;
             break;
         }
-        cscale_kernel<<<grid_for(NV), 256, 0, s>>>(Wn, NV, nullptr, 1.0 / hn, 0);
+        AFEM_LAUNCH((cscale_kernel), grid_for(NV), 256, 0, s, Wn, NV, nullptr, 1.0 / hn, 0);
         AFEM_CUDA_TRY(cudaGetLastError());
     }
-    small_expm_kernel<<<1, 256, 0, s>>>(w.H, ldh, m_used, dt, w.E);
+    AFEM_LAUNCH((small_expm_kernel), 1, 256, 0, s, w.H, ldh, m_used, dt, w.E);
     AFEM_CUDA_TRY(cudaGetLastError());
     // y = beta exp(-i dt H_m) e_1, formed from the first column on the host
     std::vector<double2> Eh(size_t(m_used) * m_used);
@@ -374,7 +374,7 @@ int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double
     std::vector<double2> yh(m_used);
     for (int i = 0; i < m_used; ++i) yh[i] = make_double2(beta * Eh[i].x, beta * Eh[i].y);
     AFEM_CUDA_TRY(cudaMemcpyAsync(w.y, yh.data(), m_used * sizeof(double2), cudaMemcpyHostToDevice, s));
-    combine_kernel<<<grid_for(NV), 256, 0, s>>>(w.V, NV, m_used, w.y, NV, phi_out);
+    AFEM_LAUNCH((combine_kernel), grid_for(NV), 256, 0, s, w.V, NV, m_used, w.y, NV, phi_out);
     AFEM_CUDA_TRY(cudaGetLastError());
     AFEM_CUDA_TRY(cudaStreamSynchronize(s));
     if (err_est) {

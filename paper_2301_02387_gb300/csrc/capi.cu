@@ -5,8 +5,13 @@
 #include "afem_internal.h"
 #include "arnoldi.cuh"
 
+#include <atomic>
+
 namespace afem {
 const char* last_error_cstr();
+static std::atomic<int64_t> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 }
 
 using namespace afem;
@@ -14,6 +19,12 @@ using namespace afem;
 extern "C" {
 
 const char* afem_last_error(void) { return last_error_cstr(); }
+
+int afem_kernel_launch_count(int64_t* count) {
+    if (!count) return set_error(AFEM_EINVAL, "afem_kernel_launch_count: null argument");
+    *count = launch_count();
+    return AFEM_OK;
+}
 
 int afem_mesh_create(const afem_mesh_desc* desc, afem_mesh** out) {
     return afem_mesh_create_ex(desc, 0, out);
@@ -130,6 +141,37 @@ int afem_arnoldi_step(afem_mesh* m, const double* E, const void* phi, const void
     return arnoldi_step(m, E, static_cast<const double2*>(phi), static_cast<const double2*>(U), n_orb, krylov_m,
                         dt, static_cast<double2*>(phi_out), err_est, m_used, breakdown,
                         static_cast<cudaStream_t>(stream));
+}
+
+int afem_mctdhf_create(afem_mesh* m, int n_orb, int n_alpha, int n_beta, int krylov_m, afem_mctdhf** out) {
+    if (!m || !out) return set_error(AFEM_EINVAL, "afem_mctdhf_create: null argument");
+    *out = nullptr;
+    if (m->host_only) return set_error(AFEM_EINVAL, "afem_mctdhf_create: mesh was built host-only");
+    if (n_orb < 1 || n_orb > 8) return set_error(AFEM_EINVAL, "afem_mctdhf_create: n_orb must be 1..8");
+    if (n_alpha < 0 || n_beta < 0 || n_alpha > n_orb || n_beta > n_orb || n_alpha + n_beta == 0)
+        return set_error(AFEM_EINVAL, "afem_mctdhf_create: bad electron counts");
+    if (krylov_m < 1 || krylov_m > kMaxKrylov) return set_error(AFEM_EINVAL, "afem_mctdhf_create: krylov_m must be 1..16");
+    return mctdhf_create(m, n_orb, n_alpha, n_beta, krylov_m, out);
+}
+
+int afem_mctdhf_destroy(afem_mctdhf* s) {
+    mctdhf_destroy(s);
+    return AFEM_OK;
+}
+
+int afem_mctdhf_ci_dim(const afem_mctdhf* s, int64_t* dim) {
+    if (!s || !dim) return set_error(AFEM_EINVAL, "afem_mctdhf_ci_dim: null argument");
+    *dim = mctdhf_ci_dim(s);
+    return AFEM_OK;
+}
+
+int afem_mctdhf_step(afem_mctdhf* s, void* phi, void* C, void* W, const double* E, double dt, double cg_rtol,
+                     int cg_max_it, afem_step_info* info, void* stream) {
+    if (!s || !phi || !C || !W) return set_error(AFEM_EINVAL, "afem_mctdhf_step: null argument");
+    if (!(dt > 0.0) || !(cg_rtol > 0.0) || cg_max_it < 0)
+        return set_error(AFEM_EINVAL, "afem_mctdhf_step: bad dt / cg_rtol / cg_max_it");
+    return mctdhf_step(s, static_cast<double2*>(phi), static_cast<double2*>(C), static_cast<double*>(W), E, dt,
+                       cg_rtol, cg_max_it, info, static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

@@ -185,7 +185,7 @@ int launch_g_cell(const afem_mesh* m, const double* E, const double2* v, const d
         if (smem > 48 * 1024)                                                                  \
             AFEM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                                int(smem)));                                    \
-        k<<<grid, 256, smem, s>>>(a, v, U, z, n);                                              \
+        AFEM_LAUNCH((k), grid, 256, smem, s, a, v, U, z, n);                                              \
         break;                                                                                 \
     }
         AFEM_CASE(1)
@@ -247,7 +247,7 @@ static int launch_cell_op(const afem_mesh* m, const CellArgs& a, const T* x, T* 
         if (smem > 48 * 1024)                                                                  \
             AFEM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                                int(smem)));                                    \
-        k<<<grid, block, smem, s>>>(a, x, y, nv);                                              \
+        AFEM_LAUNCH((k), grid, block, smem, s, a, x, y, nv);                                              \
         break;                                                                                 \
     }
         AFEM_CASE(1)
@@ -268,7 +268,7 @@ static int launch_scale_rows(T* y, const double* s, int64_t n, int nv, cudaStrea
     const int64_t total = n * nv;
     const int block = 256;
     const unsigned grid = unsigned(std::min<int64_t>((total + block - 1) / block, 152 * 32));
-    scale_rows_kernel<T><<<grid, block, 0, st>>>(y, s, n, nv);
+    AFEM_LAUNCH((scale_rows_kernel<T>), grid, block, 0, st, y, s, n, nv);
     AFEM_CUDA_TRY(cudaGetLastError());
     return AFEM_OK;
 }

@@ -439,16 +439,16 @@ int poisson_rhs_bc(afem_mesh* m, const double2* phi, int n, double* W, double* b
     AFEM_CUDA_TRY(cudaFuncSetAttribute(pair_rhs_moments_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        int(smem)));
     const int nblk = kMomBlocks;
-    pair_rhs_moments_kernel<<<nblk, 256, smem, s>>>(a, b, qpart);
+    AFEM_LAUNCH((pair_rhs_moments_kernel), nblk, 256, smem, s, a, b, qpart);
     AFEM_CUDA_TRY(cudaGetLastError());
-    finalize_columns_kernel<<<1, 256, 0, s>>>(qpart, nblk, kNlm * ncol, q);
+    AFEM_LAUNCH((finalize_columns_kernel), 1, 256, 0, s, qpart, nblk, kNlm * ncol, q);
     AFEM_CUDA_TRY(cudaGetLastError());
     const int64_t nb = D.n_master - D.n_interior;
     if (nb > 0) {
         const size_t sm2 = size_t(kNlm) * ncol * sizeof(double);
         AFEM_CUDA_TRY(cudaFuncSetAttribute(multipole_bc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            int(sm2)));
-        multipole_bc_kernel<<<grid_for(nb, 128, 152 * 8), 128, sm2, s>>>(q, ncol, D.master_xyz, D.n_interior,
+        AFEM_LAUNCH((multipole_bc_kernel), grid_for(nb, 128, 152 * 8), 128, sm2, s, q, ncol, D.master_xyz, D.n_interior,
                                                                           D.n_master, c0, c0, c0, W);
         AFEM_CUDA_TRY(cudaGetLastError());
     }
@@ -492,13 +492,13 @@ int poisson_batch(afem_mesh* m, const double2* phi, int n, double* W, double rto
     if (!warm) AFEM_CUDA_TRY(cudaMemsetAsync(W, 0, NK * sizeof(double), s));
     if ((rc = poisson_rhs_bc(m, phi, n, W, w.b, w.qpart, w.q, s))) return rc;
     // t = A g_ext (surface data only), Ap = A_II x_I
-    surface_only_kernel<<<grid_for(int64_t(NK)), 256, 0, s>>>(W, w.z, Ni, N, k);
+    AFEM_LAUNCH((surface_only_kernel), grid_for(int64_t(NK)), 256, 0, s, W, w.z, Ni, N, k);
     AFEM_CUDA_TRY(cudaGetLastError());
     if ((rc = launch_stiffness(m, w.z, w.t, k, 0, s))) return rc;
     if ((rc = launch_stiffness(m, W, w.Ap, k, 1, s))) return rc;
-    pcg_init_kernel<<<nblk, kRedThreads, 0, s>>>(w.b, w.t, w.Ap, D.stiff_dinv, w.r, w.z, w.p, Ni, k, w.partial);
+    AFEM_LAUNCH((pcg_init_kernel), nblk, kRedThreads, 0, s, w.b, w.t, w.Ap, D.stiff_dinv, w.r, w.z, w.p, Ni, k, w.partial);
     AFEM_CUDA_TRY(cudaGetLastError());
-    pcg_init_finalize_kernel<<<1, 64, 0, s>>>(w.partial, nblk, k, st);
+    AFEM_LAUNCH((pcg_init_finalize_kernel), 1, 64, 0, s, w.partial, nblk, k, st);
     AFEM_CUDA_TRY(cudaGetLastError());
 
     int it = 0, n_active = 1;
@@ -510,11 +510,11 @@ int poisson_batch(afem_mesh* m, const double2* phi, int n, double* W, double rto
             if (n_active == 0) break;
         }
         if ((rc = launch_stiffness(m, w.p, w.Ap, k, 1, s))) return rc;
-        col_dot_kernel<<<nblk, kRedThreads, 0, s>>>(w.p, w.Ap, Ni, k, w.partial);
-        pcg_alpha_kernel<<<1, 64, 0, s>>>(w.partial, nblk, k, st);
-        pcg_update_kernel<<<nblk, kRedThreads, 0, s>>>(W, w.r, w.z, w.p, w.Ap, D.stiff_dinv, Ni, k, st, w.partial);
-        pcg_beta_kernel<<<1, 64, 0, s>>>(w.partial, nblk, k, st);
-        pcg_p_kernel<<<grid_for(Ni * k), 256, 0, s>>>(w.p, w.z, Ni, k, st);
+        AFEM_LAUNCH((col_dot_kernel), nblk, kRedThreads, 0, s, w.p, w.Ap, Ni, k, w.partial);
+        AFEM_LAUNCH((pcg_alpha_kernel), 1, 64, 0, s, w.partial, nblk, k, st);
+        AFEM_LAUNCH((pcg_update_kernel), nblk, kRedThreads, 0, s, W, w.r, w.z, w.p, w.Ap, D.stiff_dinv, Ni, k, st, w.partial);
+        AFEM_LAUNCH((pcg_beta_kernel), 1, 64, 0, s, w.partial, nblk, k, st);
+        AFEM_LAUNCH((pcg_p_kernel), grid_for(Ni * k), 256, 0, s, w.p, w.z, Ni, k, st);
         AFEM_CUDA_TRY(cudaGetLastError());
         ++it;
     }
