@@ -47,6 +47,15 @@ extern "C" {
 
 #define AFEM_MAX_NUCLEI 8
 
+/* Arithmetic forms.  AFEM_PREC_FP64: everything in float64 / complex128.
+ * AFEM_PREC_MIXED: the cell operators (stiffness in the Poisson CG sweeps,
+ * the packed orbital operator G) run in float32 / complex64; the Poisson
+ * solution is refined with float64 residuals to the requested rtol, and the
+ * Arnoldi Gram-Schmidt, the small Krylov exponential, the density-matrix
+ * inverse and the CI propagation stay float64. */
+#define AFEM_PREC_FP64 0
+#define AFEM_PREC_MIXED 1
+
 /* Mesh description (Sec. 3.1 and Sec. 4 of the paper).
  *
  * The box [lo, hi]^3 is covered by n_coarse^3 cubes (the coarse uniform
@@ -165,6 +174,17 @@ int afem_poisson_batch(afem_mesh* mesh, const void* phi, int n_orb, void* W, dou
                        int max_it, int warm_start, int* iters_out, double* relres_out,
                        void* stream);
 
+/* As afem_poisson_batch with a choice of arithmetic.  AFEM_PREC_MIXED solves
+ * by iterative refinement: each outer pass forms the float64 residual with the
+ * float64 operator, runs Jacobi-PCG in float32 on the residual scaled to unit
+ * norm (to relative residual 1e-4), and adds the correction in float64; it
+ * stops on the same float64 test as afem_poisson_batch.  iters_out counts
+ * inner (float32) iterations, outer_out (host, may be NULL) the refinement
+ * passes; max_it bounds the inner iterations summed over passes. */
+int afem_poisson_batch_ex(afem_mesh* mesh, const void* phi, int n_orb, void* W, double rtol,
+                          int max_it, int warm_start, int precision, int* iters_out,
+                          int* outer_out, double* relres_out, void* stream);
+
 /* One short-iterative Arnoldi step of the packed orbital equation with the
  * operator frozen (Sec. 3.2, Eq. packed_orb_eom; Eq. orb_eom with X = 0):
  *   (G v)_p = Q [ M_L^-1 ( H1~ v_p + C^T diag(m_f) sum_q (C U_pq) o (C v_q) ) ],
@@ -183,6 +203,14 @@ int afem_poisson_batch(afem_mesh* mesh, const void* phi, int n_orb, void* W, dou
 int afem_arnoldi_step(afem_mesh* mesh, const double* E, const void* phi, const void* U, int n_orb,
                       int krylov_m, double dt, void* phi_out, double* err_est, int* m_used,
                       int* breakdown, void* stream);
+
+/* As afem_arnoldi_step with a choice of arithmetic.  AFEM_PREC_MIXED applies
+ * the cell pass of G in complex64 to a complex64 copy of each Krylov vector
+ * (and of U); the projector overlaps, the projection, Gram-Schmidt, the small
+ * exponential and the combination stay complex128. */
+int afem_arnoldi_step_ex(afem_mesh* mesh, const double* E, const void* phi, const void* U, int n_orb,
+                         int krylov_m, double dt, int precision, void* phi_out, double* err_est,
+                         int* m_used, int* breakdown, void* stream);
 
 /* MCTDHF time stepper (Sec. 2 and Sec. 3.2): owns the determinant-space
  * tables and its device workspace; the mesh must outlive it. */
@@ -207,6 +235,10 @@ typedef struct afem_step_info {
 int afem_mctdhf_create(afem_mesh* mesh, int n_orb, int n_alpha, int n_beta, int krylov_m,
                        afem_mctdhf** out);
 int afem_mctdhf_destroy(afem_mctdhf* solver);
+/* Arithmetic of later steps: AFEM_PREC_FP64 (default) or AFEM_PREC_MIXED
+ * (Poisson by float32 PCG inside float64 refinement, G cell pass in
+ * complex64; everything else float64).  Host only, no device work. */
+int afem_mctdhf_set_precision(afem_mctdhf* solver, int precision);
 /* Number of determinants (host). */
 int afem_mctdhf_ci_dim(const afem_mctdhf* solver, int64_t* dim);
 

@@ -109,6 +109,12 @@ struct DeviceMesh {
     double* hang_xyz = nullptr;     // [nh][3]
     double* mf_master = nullptr;    // [N] assembled GLL weight m_f
     double* mf_hang = nullptr;      // [nh]
+    // float copies for the FP32 kernels
+    float4* cell_geom32 = nullptr;
+    float* hang_w32 = nullptr;
+    float* v_master32 = nullptr;
+    float* v_hang32 = nullptr;
+    float* stiff_dinv32 = nullptr;
 };
 
 }  // namespace afem
@@ -132,9 +138,12 @@ int launch_op_apply(afem_mesh* m, int kind, const double* E, const void* x, void
 int launch_stiffness(const afem_mesh* m, const double* x, double* y, int nv, int masked, cudaStream_t s);
 int poisson_batch(afem_mesh* m, const double2* phi, int n, double* W, double rtol, int max_it, int warm,
                   int* iters_out, double* relres_out, cudaStream_t s);
+int poisson_batch_mixed(afem_mesh* m, const double2* phi, int n, double* W, double rtol, int max_it, int warm,
+                        double inner_rtol, int* iters_out, int* outer_out, double* relres_out, cudaStream_t s);
 int mctdhf_create(afem_mesh* m, int n, int na, int nb, int mk, afem_mctdhf** out);
 void mctdhf_destroy(afem_mctdhf* S);
 int64_t mctdhf_ci_dim(const afem_mctdhf* S);
+void mctdhf_set_precision(afem_mctdhf* S, int precision);
 int mctdhf_step(afem_mctdhf* S, double2* phi, double2* C, double* W, const double* E, double dt, double cg_rtol,
                 int cg_max_it, afem_step_info* info, cudaStream_t s);
 }  // namespace afem

@@ -20,7 +20,11 @@ namespace afem {
 
 // S[a][b] partials: sum_k w_k conj(A[k][a]) B[k][b] over rows k < n_rows.
 // diag != 0: only a == b (k_out = na), else all na*nb pairs (k_out = na*nb <= 256).
-__global__ void cdot_kernel(const double2* __restrict__ A, int na, const double2* __restrict__ B, int nb,
+__device__ __forceinline__ double2 to_d2(double2 v) { return v; }
+__device__ __forceinline__ double2 to_d2(float2 v) { return make_double2(v.x, v.y); }
+
+template <typename TB>
+__global__ void cdot_kernel(const double2* __restrict__ A, int na, const TB* __restrict__ B, int nb,
                             const double* __restrict__ w, int64_t n_rows, int diag,
                             double2* __restrict__ partial) {
     __shared__ double sx[kRedThreads], sy[kRedThreads];
@@ -34,7 +38,7 @@ __global__ void cdot_kernel(const double2* __restrict__ A, int na, const double2
         const int ib = diag ? o : o - ia * nb;
         for (int64_t k = int64_t(blockIdx.x) * R + r; k < n_rows; k += int64_t(gridDim.x) * R) {
             const double2 u = A[k * na + ia];
-            const double2 v = B[k * nb + ib];
+            const double2 v = to_d2(B[k * nb + ib]);
             const double wk = w ? w[k] : 1.0;
             ax = fma(wk, fma(u.x, v.x, u.y * v.y), ax);
             ay = fma(wk, fma(u.x, v.y, -u.y * v.x), ay);
@@ -84,7 +88,8 @@ __global__ void cfinalize_kernel(const double2* __restrict__ partial, int nblk, 
 }
 
 // w[k][p] = ML^-1[k] z[k][p] - sum_j phi[k][j] S[j][p]   (interior rows; others 0)
-__global__ void project_kernel(const double2* __restrict__ z, const double2* __restrict__ phi,
+template <typename TZ>
+__global__ void project_kernel(const TZ* __restrict__ z, const double2* __restrict__ phi,
                                const double2* __restrict__ S, const double* __restrict__ ml_inv, int64_t n_int,
                                int64_t N, int n, double2* __restrict__ w) {
     const int64_t total = N * n;
@@ -95,7 +100,8 @@ __global__ void project_kernel(const double2* __restrict__ z, const double2* __r
         double2 r = make_double2(0.0, 0.0);
         if (k < n_int) {
             const double s = ml_inv[k];
-            r = make_double2(z[o].x * s, z[o].y * s);
+            const double2 zo = to_d2(z[o]);
+            r = make_double2(zo.x * s, zo.y * s);
             for (int j = 0; j < n; ++j) {
                 const double2 f = phi[k * n + j];
                 const double2 c = S[j * n + p];
@@ -263,11 +269,46 @@ __global__ void small_expm_kernel(const double2* __restrict__ H, int ldh, int m,
 int launch_g_cell(const afem_mesh* m, const double* E, const double2* v, const double2* U, double2* z, int n,
                   cudaStream_t s);
 
+template <typename TB>
+int cdot_t(const double2* A, int na, const TB* B, int nb, const double* w, int64_t rows, int diag,
+           double2* partial, double2* out, int sum_all, cudaStream_t s) {
+    const int kout = diag ? na : na * nb;
+    AFEM_LAUNCH((cdot_kernel<TB>), kRedBlocks, kRedThreads, 0, s, A, na, B, nb, w, rows, diag, partial);
+    AFEM_LAUNCH((cfinalize_kernel), 1, 256, 0, s, partial, kRedBlocks, kout, sum_all, out);
+    AFEM_CUDA_TRY(cudaGetLastError());
+    return AFEM_OK;
+}
+
 int cdot(const double2* A, int na, const double2* B, int nb, const double* w, int64_t rows, int diag,
          double2* partial, double2* out, int sum_all, cudaStream_t s) {
-    const int kout = diag ? na : na * nb;
-    AFEM_LAUNCH((cdot_kernel), kRedBlocks, kRedThreads, 0, s, A, na, B, nb, w, rows, diag, partial);
-    AFEM_LAUNCH((cfinalize_kernel), 1, 256, 0, s, partial, kRedBlocks, kout, sum_all, out);
+    return cdot_t<double2>(A, na, B, nb, w, rows, diag, partial, out, sum_all, s);
+}
+
+__global__ void to_c64_kernel(const double2* __restrict__ x, float2* __restrict__ y, int64_t n) {
+    for (int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; o < n; o += int64_t(gridDim.x) * blockDim.x)
+        y[o] = make_float2(float(x[o].x), float(x[o].y));
+}
+
+int to_c64(const double2* x, float2* y, int64_t n, cudaStream_t s) {
+    AFEM_LAUNCH((to_c64_kernel), grid_for(n), 256, 0, s, x, y, n);
+    AFEM_CUDA_TRY(cudaGetLastError());
+    return AFEM_OK;
+}
+
+int launch_g_cell32(const afem_mesh* m, const double* E, const float2* v, const float2* U, float2* z, int n,
+                    cudaStream_t s);
+
+// Mixed form: the cell pass in complex64 on a complex64 copy of v; projector
+// overlaps, the projection and everything after stay FP64.
+int g_apply32(afem_mesh* m, const double* E, const double2* phi, const float2* U32, int n, const double2* v,
+              ArnoldiWork& w, double2* out, cudaStream_t s) {
+    const DeviceMesh& D = m->dev;
+    int rc = to_c64(v, w.v32, D.n_master * n, s);
+    if (rc) return rc;
+    if ((rc = launch_g_cell32(m, E, w.v32, U32, w.z32, n, s))) return rc;
+    if ((rc = cdot_t<float2>(phi, n, w.z32, n, nullptr, D.n_interior, 0, w.cpartial, w.S, 0, s))) return rc;
+    AFEM_LAUNCH((project_kernel<float2>), grid_for(D.n_master * n), 256, 0, s, w.z32, phi, w.S, D.ml_inv,
+                D.n_interior, D.n_master, n, out);
     AFEM_CUDA_TRY(cudaGetLastError());
     return AFEM_OK;
 }
@@ -279,7 +320,7 @@ int g_apply(afem_mesh* m, const double* E, const double2* phi, const double2* U,
     if (rc) return rc;
     // S[j][p] = phi_j^H z_p  (equals phi_j^H M_L y_p)
     if ((rc = cdot(phi, n, z, n, nullptr, D.n_interior, 0, w.cpartial, w.S, 0, s))) return rc;
-    AFEM_LAUNCH((project_kernel), grid_for(D.n_master * n), 256, 0, s, z, phi, w.S, D.ml_inv, D.n_interior, D.n_master, n,
+    AFEM_LAUNCH((project_kernel<double2>), grid_for(D.n_master * n), 256, 0, s, z, phi, w.S, D.ml_inv, D.n_interior, D.n_master, n,
                                                             out);
     AFEM_CUDA_TRY(cudaGetLastError());
     return AFEM_OK;
@@ -296,6 +337,9 @@ int arnoldi_reserve(afem_mesh* m, int n, int mk, ArnoldiWork& w) {
         w.E = cv.take<double2>(kMaxKrylov * kMaxKrylov);
         w.y = cv.take<double2>(kMaxKrylov);
         w.beta2 = cv.take<double2>(1);
+        w.v32 = cv.take<float2>(NV);
+        w.z32 = cv.take<float2>(NV);
+        w.U32 = cv.take<float2>(NV * n);
     };
     Carver measure(nullptr);
     carve(measure);
@@ -307,12 +351,17 @@ int arnoldi_reserve(afem_mesh* m, int n, int mk, ArnoldiWork& w) {
     return AFEM_OK;
 }
 
-int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double2* U, int n, int mk, double dt,
-                 double2* phi_out, double* err_est, int* m_used_out, int* breakdown_out, cudaStream_t s) {
+int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double2* U, const float2* U32, int n,
+                 int mk, double dt, int mixed, double2* phi_out, double* err_est, int* m_used_out,
+                 int* breakdown_out, cudaStream_t s) {
     const DeviceMesh& D = m->dev;
     ArnoldiWork w{};
     int rc = arnoldi_reserve(m, n, mk, w);
     if (rc) return rc;
+    if (mixed && U && !U32) {
+        if ((rc = to_c64(U, w.U32, D.n_master * n * n, s))) return rc;
+        U32 = w.U32;
+    }
     const int64_t NV = w.stride;
     const int64_t NIV = D.n_interior * n;
     const int ldh = kMaxKrylov + 1;
@@ -335,7 +384,11 @@ int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double
     for (int j = 0; j < mk; ++j) {
         double2* Vj = w.V + j * NV;
         double2* Wn = w.V + (j + 1) * NV;
-        if ((rc = g_apply(m, E, phi, U, n, Vj, w.z, Wn, w, s))) return rc;
+        if (mixed) {
+            if ((rc = g_apply32(m, E, phi, U32, n, Vj, w, Wn, s))) return rc;
+        } else {
+            if ((rc = g_apply(m, E, phi, U, n, Vj, w.z, Wn, w, s))) return rc;
+        }
         // modified Gram-Schmidt against V_0..V_j
         for (int i = 0; i <= j; ++i) {
             const double2* Vprev = i > 0 ? w.V + (i - 1) * NV : nullptr;

@@ -123,24 +123,47 @@ int afem_op_apply(afem_mesh* m, int kind, const double* E, const void* x, void* 
 
 int afem_poisson_batch(afem_mesh* m, const void* phi, int n_orb, void* W, double rtol, int max_it,
                        int warm_start, int* iters_out, double* relres_out, void* stream) {
+    return afem_poisson_batch_ex(m, phi, n_orb, W, rtol, max_it, warm_start, AFEM_PREC_FP64, iters_out, nullptr,
+                                 relres_out, stream);
+}
+
+int afem_poisson_batch_ex(afem_mesh* m, const void* phi, int n_orb, void* W, double rtol, int max_it,
+                          int warm_start, int precision, int* iters_out, int* outer_out, double* relres_out,
+                          void* stream) {
+    if (precision != AFEM_PREC_FP64 && precision != AFEM_PREC_MIXED)
+        return set_error(AFEM_EINVAL, "afem_poisson_batch_ex: unknown precision");
     if (!m || !phi || !W) return set_error(AFEM_EINVAL, "afem_poisson_batch: null argument");
     if (m->host_only) return set_error(AFEM_EINVAL, "afem_poisson_batch: mesh was built host-only");
     if (n_orb < 1 || n_orb > 8) return set_error(AFEM_EINVAL, "afem_poisson_batch: n_orb must be 1..8");
     if (!(rtol > 0.0) || max_it < 0) return set_error(AFEM_EINVAL, "afem_poisson_batch: bad rtol/max_it");
+    if (precision == AFEM_PREC_MIXED)
+        return poisson_batch_mixed(m, static_cast<const double2*>(phi), n_orb, static_cast<double*>(W), rtol,
+                                   max_it, warm_start, 1e-4, iters_out, outer_out, relres_out,
+                                   static_cast<cudaStream_t>(stream));
+    if (outer_out) *outer_out = 0;
     return poisson_batch(m, static_cast<const double2*>(phi), n_orb, static_cast<double*>(W), rtol, max_it,
                          warm_start, iters_out, relres_out, static_cast<cudaStream_t>(stream));
 }
 
 int afem_arnoldi_step(afem_mesh* m, const double* E, const void* phi, const void* U, int n_orb, int krylov_m,
                       double dt, void* phi_out, double* err_est, int* m_used, int* breakdown, void* stream) {
+    return afem_arnoldi_step_ex(m, E, phi, U, n_orb, krylov_m, dt, AFEM_PREC_FP64, phi_out, err_est, m_used,
+                                breakdown, stream);
+}
+
+int afem_arnoldi_step_ex(afem_mesh* m, const double* E, const void* phi, const void* U, int n_orb, int krylov_m,
+                         double dt, int precision, void* phi_out, double* err_est, int* m_used, int* breakdown,
+                         void* stream) {
+    if (precision != AFEM_PREC_FP64 && precision != AFEM_PREC_MIXED)
+        return set_error(AFEM_EINVAL, "afem_arnoldi_step_ex: unknown precision");
     if (!m || !phi || !phi_out) return set_error(AFEM_EINVAL, "afem_arnoldi_step: null argument");
     if (m->host_only) return set_error(AFEM_EINVAL, "afem_arnoldi_step: mesh was built host-only");
     if (n_orb < 1 || n_orb > 8) return set_error(AFEM_EINVAL, "afem_arnoldi_step: n_orb must be 1..8");
     if (krylov_m < 1 || krylov_m > kMaxKrylov) return set_error(AFEM_EINVAL, "afem_arnoldi_step: krylov_m must be 1..16");
     if (phi == phi_out) return set_error(AFEM_EINVAL, "afem_arnoldi_step: phi and phi_out must not alias");
-    return arnoldi_step(m, E, static_cast<const double2*>(phi), static_cast<const double2*>(U), n_orb, krylov_m,
-                        dt, static_cast<double2*>(phi_out), err_est, m_used, breakdown,
-                        static_cast<cudaStream_t>(stream));
+    return arnoldi_step(m, E, static_cast<const double2*>(phi), static_cast<const double2*>(U), nullptr, n_orb,
+                        krylov_m, dt, precision == AFEM_PREC_MIXED, static_cast<double2*>(phi_out), err_est,
+                        m_used, breakdown, static_cast<cudaStream_t>(stream));
 }
 
 int afem_mctdhf_create(afem_mesh* m, int n_orb, int n_alpha, int n_beta, int krylov_m, afem_mctdhf** out) {
@@ -156,6 +179,14 @@ int afem_mctdhf_create(afem_mesh* m, int n_orb, int n_alpha, int n_beta, int kry
 
 int afem_mctdhf_destroy(afem_mctdhf* s) {
     mctdhf_destroy(s);
+    return AFEM_OK;
+}
+
+int afem_mctdhf_set_precision(afem_mctdhf* s, int precision) {
+    if (!s) return set_error(AFEM_EINVAL, "afem_mctdhf_set_precision: null argument");
+    if (precision != AFEM_PREC_FP64 && precision != AFEM_PREC_MIXED)
+        return set_error(AFEM_EINVAL, "afem_mctdhf_set_precision: unknown precision");
+    mctdhf_set_precision(s, precision);
     return AFEM_OK;
 }
 

@@ -1,0 +1,208 @@
+// FP32 forms of the fused cell operators (precision form of the hot path).
+//
+// Same operators as the FP64 kernels (Sec. 3.1: GLL sum-factorised cell
+// stiffness, pointwise potential, hanging-node gather/scatter; Eq.
+// discretized_eom): the per-cell data and the arithmetic are in float /
+// complex64, reading float copies of the mesh tables, so no FP64 instruction
+// runs inside the cell loop.  Callers keep the accuracy-critical parts in FP64
+// (Krylov Gram-Schmidt, residuals of the Poisson refinement).
+#include "afem_internal.h"
+#include "cell_common.cuh"
+
+namespace afem {
+
+struct CellArgs32 {
+    const int32_t* cell_node;
+    const float4* geom;       // (corner, h)
+    const int32_t* hp;
+    const int32_t* hm;
+    const float* hw;
+    const float* v_master;
+    const float* v_hang;
+    int64_t n_interior;
+    float xi[kMaxP1], w[kMaxP1], K[kMaxP1 * kMaxP1];
+    float E[3];
+    int masked;
+};
+
+template <typename T>
+__device__ __forceinline__ T gather32(const CellArgs32& a, int idx, const T* __restrict__ x, int nv, int v) {
+    T val = vzero<T>();
+    if (idx >= 0) {
+        if (!(a.masked && idx >= a.n_interior)) val = x[int64_t(idx) * nv + v];
+    } else {
+        const int hh = -idx - 1;
+        for (int e = a.hp[hh]; e < a.hp[hh + 1]; ++e) {
+            const int m = a.hm[e];
+            if (a.masked && m >= a.n_interior) continue;
+            vfma(val, a.hw[e], x[int64_t(m) * nv + v]);
+        }
+    }
+    return val;
+}
+
+__device__ __forceinline__ float2 fscale(float2 v, float s) { return make_float2(v.x * s, v.y * s); }
+__device__ __forceinline__ float fscale(float v, float s) { return v * s; }
+
+template <typename T>
+__device__ __forceinline__ void scatter32(const CellArgs32& a, int idx, T* __restrict__ y, int nv, int v, T r) {
+    if (idx >= 0) {
+        if (!(a.masked && idx >= a.n_interior)) vatomic_add(&y[int64_t(idx) * nv + v], r);
+    } else {
+        const int hh = -idx - 1;
+        for (int e = a.hp[hh]; e < a.hp[hh + 1]; ++e) {
+            const int m = a.hm[e];
+            if (a.masked && m >= a.n_interior) continue;
+            vatomic_add(&y[int64_t(m) * nv + v], fscale(r, a.hw[e]));
+        }
+    }
+}
+
+// y += A x for nv real columns (c_kin = 1), or the G-operator cell pass for
+// complex columns: z_p = H1~ v_p + sum_q (C U_pq) o (C v_q) weighted (U may be null).
+template <int P, typename T, bool G>
+__global__ void __launch_bounds__(256) cell32_kernel(CellArgs32 a, const T* __restrict__ x,
+                                                     const float2* __restrict__ U, T* __restrict__ y, int nv) {
+    constexpr int P1 = P + 1;
+    constexpr int NN = P1 * P1 * P1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* s_u = reinterpret_cast<T*>(smem_raw);
+    float2* s_U = reinterpret_cast<float2*>(s_u + NN * nv);
+    __shared__ int s_idx[NN];
+    __shared__ float s_pot[NN];
+    __shared__ float s_wq[NN];
+    __shared__ float s_K[P1 * P1];
+    __shared__ float s_w[P1];
+    const int64_t cell = blockIdx.x;
+    const int tid = threadIdx.x, bs = blockDim.x;
+    const float4 g = a.geom[cell];
+    for (int i = tid; i < NN; i += bs) s_idx[i] = a.cell_node[cell * NN + i];
+    if (tid < P1 * P1) s_K[tid] = a.K[tid];
+    if (tid < P1) s_w[tid] = a.w[tid];
+    __syncthreads();
+    for (int it = tid; it < NN * nv; it += bs) {
+        const int i = it / nv, q = it - i * nv;
+        s_u[it] = gather32<T>(a, s_idx[i], x, nv, q);
+    }
+    const int nn2 = nv * nv;
+    if (G) {
+        if (U) {
+            CellArgs32 au = a;
+            au.masked = 0;
+            for (int it = tid; it < NN * nn2; it += bs) {
+                const int i = it / nn2, pq = it - i * nn2;
+                s_U[it] = gather32<float2>(au, s_idx[i], U, nn2, pq);
+            }
+        }
+        const float h3 = g.w * g.w * g.w;
+        for (int i = tid; i < NN; i += bs) {
+            const int ia = i % P1, ib = (i / P1) % P1, ic = i / (P1 * P1);
+            const int idx = s_idx[i];
+            const float V = idx >= 0 ? a.v_master[idx] : a.v_hang[-idx - 1];
+            const float px = g.x + g.w * a.xi[ia], py = g.y + g.w * a.xi[ib], pz = g.z + g.w * a.xi[ic];
+            const float wq = h3 * s_w[ia] * s_w[ib] * s_w[ic];
+            s_wq[i] = wq;
+            s_pot[i] = wq * (V + a.E[0] * px + a.E[1] * py + a.E[2] * pz);
+        }
+    }
+    __syncthreads();
+    const float ck = (G ? 0.5f : 1.0f) * g.w;
+    for (int it = tid; it < NN * nv; it += bs) {
+        const int i = it / nv, p = it - i * nv;
+        const int ia = i % P1, ib = (i / P1) % P1, ic = i / (P1 * P1);
+        T ax = vzero<T>(), ay = vzero<T>(), az = vzero<T>();
+#pragma unroll
+        for (int m = 0; m < P1; ++m) {
+            vfma(ax, s_K[ia * P1 + m], s_u[(m + P1 * (ib + P1 * ic)) * nv + p]);
+            vfma(ay, s_K[ib * P1 + m], s_u[(ia + P1 * (m + P1 * ic)) * nv + p]);
+            vfma(az, s_K[ic * P1 + m], s_u[(ia + P1 * (ib + P1 * m)) * nv + p]);
+        }
+        T r = vzero<T>();
+        vfma(r, ck * s_w[ib] * s_w[ic], ax);
+        vfma(r, ck * s_w[ia] * s_w[ic], ay);
+        vfma(r, ck * s_w[ia] * s_w[ib], az);
+        if constexpr (G) {
+            vfma(r, s_pot[i], s_u[it]);
+            if (U) {
+                float2 mf = make_float2(0.0f, 0.0f);
+                const float2* Ui = s_U + i * nn2 + p * nv;
+                const T* ui = s_u + i * nv;
+                for (int q = 0; q < nv; ++q) {
+                    mf.x = fmaf(Ui[q].x, ui[q].x, fmaf(-Ui[q].y, ui[q].y, mf.x));
+                    mf.y = fmaf(Ui[q].x, ui[q].y, fmaf(Ui[q].y, ui[q].x, mf.y));
+                }
+                vfma(r, s_wq[i], mf);
+            }
+        }
+        scatter32<T>(a, s_idx[i], y, nv, p, r);
+    }
+}
+
+CellArgs32 make_cell_args32(const afem_mesh* m) {
+    CellArgs32 a{};
+    const DeviceMesh& D = m->dev;
+    a.cell_node = D.cell_node;
+    a.geom = D.cell_geom32;
+    a.hp = D.hang_ptr;
+    a.hm = D.hang_master;
+    a.hw = D.hang_w32;
+    a.v_master = D.v_master32;
+    a.v_hang = D.v_hang32;
+    a.n_interior = D.n_interior;
+    const Basis1D& b = m->basis;
+    const int p1 = b.p + 1;
+    for (int i = 0; i < p1; ++i) {
+        a.xi[i] = float(b.xi[i]);
+        a.w[i] = float(b.w[i]);
+        for (int j = 0; j < p1; ++j) a.K[i * p1 + j] = float(b.K[i][j]);
+    }
+    return a;
+}
+
+template <typename T, bool G>
+static int launch32(const afem_mesh* m, const CellArgs32& a, const T* x, const float2* U, T* y, int nv,
+                    cudaStream_t s) {
+    const int p = m->dev.p;
+    const int nn = (p + 1) * (p + 1) * (p + 1);
+    const size_t smem = size_t(nn) * nv * sizeof(T) + ((G && U) ? size_t(nn) * nv * nv * sizeof(float2) : 0);
+    const unsigned grid = unsigned(m->dev.ncell);
+    AFEM_CUDA_TRY(cudaMemsetAsync(y, 0, size_t(m->dev.n_master) * nv * sizeof(T), s));
+    if (grid == 0) return AFEM_OK;
+    switch (p) {
+#define AFEM_CASE(PP)                                                                          \
+    case PP: {                                                                                 \
+        auto k = cell32_kernel<PP, T, G>;                                                      \
+        if (smem > 48 * 1024)                                                                  \
+            AFEM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                               int(smem)));                                    \
+        AFEM_LAUNCH((k), grid, 256, smem, s, a, x, U, y, nv);                                  \
+        break;                                                                                 \
+    }
+        AFEM_CASE(1)
+        AFEM_CASE(2)
+        AFEM_CASE(3)
+        AFEM_CASE(4)
+#undef AFEM_CASE
+        default:
+            return set_error(AFEM_EINVAL, "degree out of range");
+    }
+    AFEM_CUDA_TRY(cudaGetLastError());
+    return AFEM_OK;
+}
+
+int launch_stiffness32(const afem_mesh* m, const float* x, float* y, int nv, int masked, cudaStream_t s) {
+    CellArgs32 a = make_cell_args32(m);
+    a.masked = masked;
+    return launch32<float, false>(m, a, x, nullptr, y, nv, s);
+}
+
+// z = H1~ v + mean field (complex64), Dirichlet-masked.
+int launch_g_cell32(const afem_mesh* m, const double* E, const float2* v, const float2* U, float2* z, int n,
+                    cudaStream_t s) {
+    CellArgs32 a = make_cell_args32(m);
+    a.masked = 1;
+    for (int i = 0; i < 3; ++i) a.E[i] = E ? float(E[i]) : 0.0f;
+    return launch32<float2, true>(m, a, v, U, z, n, s);
+}
+
+}  // namespace afem

@@ -475,6 +475,7 @@ constexpr int kTaylorTerms = 30;
 struct afem_mctdhf {
     afem_mesh* mesh = nullptr;
     int n = 0, na = 0, nb = 0, krylov_m = 0;
+    int precision = AFEM_PREC_FP64;
     afem::CiTables ci;
     afem::Workspace ws;
 };
@@ -486,9 +487,10 @@ struct StepWork {
     double2 *D, *Y, *sigma, *t0, *t1, *acc;
     double *energy, *shift;
     int* status;
+    float2* U32;
 };
 
-static void carve_step(Carver& cv, StepWork& w, int64_t N, int n, int64_t dim) {
+static void carve_step(Carver& cv, StepWork& w, int64_t N, int n, int64_t dim, bool mixed) {
     const int nn = n * n;
     w.y = cv.take<double2>(size_t(N) * n);
     w.phi_new = cv.take<double2>(size_t(N) * n);
@@ -511,6 +513,7 @@ static void carve_step(Carver& cv, StepWork& w, int64_t N, int n, int64_t dim) {
     w.energy = cv.take<double>(1);
     w.shift = cv.take<double>(1);
     w.status = cv.take<int>(1);
+    w.U32 = mixed ? cv.take<float2>(size_t(N) * nn) : nullptr;
 }
 
 static void finalize_cpartials(const double2* partial, int nblk, int k, double2* out, cudaStream_t s);
@@ -551,16 +554,21 @@ int mctdhf_step(afem_mctdhf* S, double2* phi, double2* C, double* W, const doubl
     const int64_t N = D.n_master, dim = S->ci.dim;
     StepWork w{};
     Carver measure(nullptr);
-    carve_step(measure, w, N, n, dim);
+    const bool mixed_form = S->precision == AFEM_PREC_MIXED;
+    carve_step(measure, w, N, n, dim, mixed_form);
     int rc = S->ws.reserve(measure.size());
     if (rc) return rc;
     Carver cv(S->ws.ptr);
-    carve_step(cv, w, N, n, dim);
+    carve_step(cv, w, N, n, dim, mixed_form);
 
     // 1. mean fields
     int iters = 0;
     std::vector<double> relres(nn);
-    rc = poisson_batch(m, phi, n, W, cg_rtol, cg_max_it, 1, &iters, relres.data(), s);
+    int outer = 0;
+    if (mixed_form)
+        rc = poisson_batch_mixed(m, phi, n, W, cg_rtol, cg_max_it, 1, 1e-4, &iters, &outer, relres.data(), s);
+    else
+        rc = poisson_batch(m, phi, n, W, cg_rtol, cg_max_it, 1, &iters, relres.data(), s);
     if (rc && rc != AFEM_ECG_MAXIT) return rc;
     const int cg_rc = rc;
     // 2. integrals: h_pq = phi_p^H M_L (M_L^-1 H1~ phi_q);  (pq|rs)
@@ -604,7 +612,15 @@ int mctdhf_step(afem_mctdhf* S, double2* phi, double2* C, double* W, const doubl
     AFEM_CUDA_TRY(cudaGetLastError());
     double err = 0.0;
     int m_used = 0, brk = 0;
-    if ((rc = arnoldi_step(m, E, phi, w.U, n, S->krylov_m, dt, w.phi_new, &err, &m_used, &brk, s))) return rc;
+    const int mixed = S->precision == AFEM_PREC_MIXED;
+    float2* U32 = nullptr;
+    if (mixed) {
+        U32 = w.U32;
+        if ((rc = to_c64(w.U, U32, N * nn, s))) return rc;
+    }
+    if ((rc = arnoldi_step(m, E, phi, mixed ? nullptr : w.U, U32, n, S->krylov_m, dt, mixed, w.phi_new, &err,
+                           &m_used, &brk, s)))
+        return rc;
     // commit: phi <- phi_new, C <- exp(-i dt shift) acc
     AFEM_CUDA_TRY(cudaMemcpyAsync(phi, w.phi_new, size_t(N) * n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
     AFEM_LAUNCH((ci_phase_kernel), ci_grid(dim), 128, 0, s, dim, w.acc, w.shift, dt, C);
@@ -662,5 +678,7 @@ void mctdhf_destroy(afem_mctdhf* S) {
 }
 
 int64_t mctdhf_ci_dim(const afem_mctdhf* S) { return S->ci.dim; }
+
+void mctdhf_set_precision(afem_mctdhf* S, int precision) { S->precision = precision; }
 
 }  // namespace afem

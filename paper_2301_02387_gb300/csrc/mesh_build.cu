@@ -578,6 +578,21 @@ int upload_mesh(afem_mesh* m) {
         if ((rc = upload(D.mf_master, H.mf_master.data(), H.mf_master.size()))) return rc;
         if ((rc = upload(D.mf_hang, H.mf_hang.data(), H.mf_hang.size()))) return rc;
     }
+    {
+        auto to_f = [](const std::vector<double>& v) { return std::vector<float>(v.begin(), v.end()); };
+        std::vector<float4> g32(D.ncell);
+        for (int64_t q = 0; q < D.ncell; ++q)
+            g32[q] = make_float4(float(H.corner[3 * q]), float(H.corner[3 * q + 1]), float(H.corner[3 * q + 2]),
+                                 float(H.h[q]));
+        std::vector<float> dinv32(H.n_master, 0.0f);
+        for (int64_t k = 0; k < H.n_interior; ++k) dinv32[k] = float(1.0 / H.stiff_diag[k]);
+        if ((rc = upload(D.cell_geom32, g32.data(), g32.size()))) return rc;
+        auto hw = to_f(H.hang_w), vm = to_f(H.v_master), vh = to_f(H.v_hang);
+        if ((rc = upload(D.hang_w32, hw.data(), hw.size()))) return rc;
+        if ((rc = upload(D.v_master32, vm.data(), vm.size()))) return rc;
+        if ((rc = upload(D.v_hang32, vh.data(), vh.size()))) return rc;
+        if ((rc = upload(D.stiff_dinv32, dinv32.data(), dinv32.size()))) return rc;
+    }
     (void)nn;
     return AFEM_OK;
 }
@@ -598,6 +613,11 @@ void free_device_mesh(DeviceMesh& D) {
     cudaFree(D.hang_xyz);
     cudaFree(D.mf_master);
     cudaFree(D.mf_hang);
+    cudaFree(D.cell_geom32);
+    cudaFree(D.hang_w32);
+    cudaFree(D.v_master32);
+    cudaFree(D.v_hang32);
+    cudaFree(D.stiff_dinv32);
     D = DeviceMesh{};
 }
 

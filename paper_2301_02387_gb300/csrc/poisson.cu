@@ -536,4 +536,263 @@ int poisson_batch(afem_mesh* m, const double2* phi, int n, double* W, double rto
     return AFEM_OK;
 }
 
+// ------------------------------------------------ mixed precision (FP32 inner)
+// Precision form: the same Dirichlet problems are solved by iterative
+// refinement.  Each outer pass forms the FP64 residual r = b - A_IB g - A_II W
+// with the FP64 operator, solves A d = r / ||r|| per column by Jacobi-PCG in
+// FP32 to a loose tolerance, and updates W += ||r|| d in FP64, until the FP64
+// residual meets rtol.
+
+// r = b - t - Ap (interior rows), partial r.r ; r32 filled later after scaling.
+__global__ void residual64_kernel(const double* __restrict__ b, const double* __restrict__ t,
+                                  const double* __restrict__ Ap, double* __restrict__ r, int64_t n, int k,
+                                  double* __restrict__ partial /*[blk][2k]*/) {
+    __shared__ double s[kRedThreads];
+    const int R = kRedThreads / k, used = R * k;
+    const int tid = threadIdx.x;
+    double arr = 0.0, abb = 0.0;
+    if (tid < used) {
+        const int c = tid % k, r0 = tid / k;
+        for (int64_t i = int64_t(blockIdx.x) * R + r0; i < n; i += int64_t(gridDim.x) * R) {
+            const int64_t o = i * k + c;
+            const double be = b[o] - t[o];
+            const double ri = be - Ap[o];
+            r[o] = ri;
+            arr = fma(ri, ri, arr);
+            abb = fma(be, be, abb);
+        }
+    }
+    double* out = partial + int64_t(blockIdx.x) * 2 * k;
+    s[tid] = arr;
+    reduce_columns(s, k, R, out);
+    __syncthreads();
+    s[tid] = abb;
+    reduce_columns(s, k, R, out + k);
+}
+
+// Inner FP32 PCG start: r32 = r64 / scale_c, z = Dinv r32, p = z, d = 0; partials r.z, r.r.
+__global__ void pcg32_init_kernel(const double* __restrict__ r64, const double* __restrict__ scale,
+                                  const float* __restrict__ dinv, float* __restrict__ r, float* __restrict__ z,
+                                  float* __restrict__ p, float* __restrict__ d, int64_t n, int k,
+                                  double* __restrict__ partial) {
+    __shared__ double s[kRedThreads];
+    const int R = kRedThreads / k, used = R * k;
+    const int tid = threadIdx.x;
+    double arz = 0.0, arr = 0.0;
+    if (tid < used) {
+        const int c = tid % k, r0 = tid / k;
+        const double sc = scale[c] > 0.0 ? 1.0 / scale[c] : 0.0;
+        for (int64_t i = int64_t(blockIdx.x) * R + r0; i < n; i += int64_t(gridDim.x) * R) {
+            const int64_t o = i * k + c;
+            const float ri = float(r64[o] * sc);
+            const float zi = dinv[i] * ri;
+            r[o] = ri;
+            z[o] = zi;
+            p[o] = zi;
+            d[o] = 0.0f;
+            arz += double(ri) * double(zi);
+            arr += double(ri) * double(ri);
+        }
+    }
+    double* out = partial + int64_t(blockIdx.x) * 3 * k;
+    s[tid] = arr;                      // bb of the inner problem = ||r32||^2
+    reduce_columns(s, k, R, out);
+    __syncthreads();
+    s[tid] = arz;
+    reduce_columns(s, k, R, out + k);
+    __syncthreads();
+    s[tid] = arr;
+    reduce_columns(s, k, R, out + 2 * k);
+}
+
+__global__ void col_dot32_kernel(const float* __restrict__ a, const float* __restrict__ b, int64_t n, int k,
+                                 double* __restrict__ partial) {
+    __shared__ double s[kRedThreads];
+    const int R = kRedThreads / k, used = R * k;
+    const int t = threadIdx.x;
+    double acc = 0.0;
+    if (t < used) {
+        const int c = t % k, r = t / k;
+        for (int64_t i = int64_t(blockIdx.x) * R + r; i < n; i += int64_t(gridDim.x) * R)
+            acc += double(a[i * k + c]) * double(b[i * k + c]);
+    }
+    s[t] = acc;
+    reduce_columns(s, k, R, partial + int64_t(blockIdx.x) * k);
+}
+
+__global__ void pcg32_update_kernel(float* __restrict__ x, float* __restrict__ r, float* __restrict__ z,
+                                    const float* __restrict__ p, const float* __restrict__ Ap,
+                                    const float* __restrict__ dinv, int64_t n, int k, PcgState st,
+                                    double* __restrict__ partial) {
+    __shared__ double s[kRedThreads];
+    const int R = kRedThreads / k, used = R * k;
+    const int tid = threadIdx.x;
+    double arz = 0.0, arr = 0.0;
+    if (tid < used) {
+        const int c = tid % k, r0 = tid / k;
+        const float al = float(st.alpha[c]);
+        for (int64_t i = int64_t(blockIdx.x) * R + r0; i < n; i += int64_t(gridDim.x) * R) {
+            const int64_t o = i * k + c;
+            x[o] = fmaf(al, p[o], x[o]);
+            const float ri = fmaf(-al, Ap[o], r[o]);
+            const float zi = dinv[i] * ri;
+            r[o] = ri;
+            z[o] = zi;
+            arz += double(ri) * double(zi);
+            arr += double(ri) * double(ri);
+        }
+    }
+    double* out = partial + int64_t(blockIdx.x) * 2 * k;
+    s[tid] = arz;
+    reduce_columns(s, k, R, out);
+    __syncthreads();
+    s[tid] = arr;
+    reduce_columns(s, k, R, out + k);
+}
+
+__global__ void pcg32_p_kernel(float* __restrict__ p, const float* __restrict__ z, int64_t n, int k, PcgState st) {
+    const int64_t total = n * k;
+    for (int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; o < total;
+         o += int64_t(gridDim.x) * blockDim.x) {
+        const int c = int(o % k);
+        if (st.active[c]) p[o] = fmaf(float(st.beta[c]), p[o], z[o]);
+    }
+}
+
+// W_interior += scale_c d_c ; per-column norms of the FP64 residual in scale.
+__global__ void refine_update_kernel(double* __restrict__ W, const float* __restrict__ d,
+                                     const double* __restrict__ scale, int64_t n, int k) {
+    const int64_t total = n * k;
+    for (int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; o < total;
+         o += int64_t(gridDim.x) * blockDim.x)
+        W[o] = fma(scale[o % k], double(d[o]), W[o]);
+}
+
+__global__ void finalize_residual_kernel(const double* __restrict__ partial, int nblk, int k, double rtol2,
+                                         double* __restrict__ rr, double* __restrict__ bb,
+                                         double* __restrict__ scale, int* __restrict__ n_active) {
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        double a = 0.0, b = 0.0;
+        for (int q = 0; q < nblk; ++q) {
+            a += partial[int64_t(q) * 2 * k + c];
+            b += partial[int64_t(q) * 2 * k + k + c];
+        }
+        rr[c] = a;
+        bb[c] = b;
+        const int act = (b > 0.0 && a > rtol2 * b && isfinite(a)) ? 1 : 0;
+        scale[c] = act ? sqrt(a) : 0.0;
+        if (act) atomicAdd(&cnt, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *n_active = cnt;
+}
+
+int launch_stiffness32(const afem_mesh* m, const float* x, float* y, int nv, int masked, cudaStream_t s);
+
+int poisson_batch_mixed(afem_mesh* m, const double2* phi, int n, double* W, double rtol, int max_it, int warm,
+                        double inner_rtol, int* iters_out, int* outer_out, double* relres_out, cudaStream_t s) {
+    const DeviceMesh& D = m->dev;
+    const int k = n * n;
+    const int64_t N = D.n_master, Ni = D.n_interior;
+    const int nblk = kRedBlocks;
+    const size_t NK = size_t(N) * k;
+    PoissonWork w{};
+    float *r32, *z32, *p32, *Ap32, *d32;
+    double *scale, *rr64, *bb64;
+    int* nact64;
+    auto carve = [&](Carver& cv) {
+        w.b = cv.take<double>(NK);
+        w.r = cv.take<double>(NK);
+        w.Ap = cv.take<double>(NK);
+        w.t = cv.take<double>(NK);
+        w.z = cv.take<double>(NK);
+        r32 = cv.take<float>(NK);
+        z32 = cv.take<float>(NK);
+        p32 = cv.take<float>(NK);
+        Ap32 = cv.take<float>(NK);
+        d32 = cv.take<float>(NK);
+        w.partial = cv.take<double>(size_t(nblk) * 3 * k);
+        w.qpart = cv.take<double>(size_t(kMomBlocks) * kNlm * k);
+        w.q = cv.take<double>(size_t(kNlm) * k);
+        w.alpha = cv.take<double>(k);
+        w.beta = cv.take<double>(k);
+        w.rz = cv.take<double>(k);
+        w.bb = cv.take<double>(k);
+        w.rr = cv.take<double>(k);
+        w.active = cv.take<int>(k);
+        w.n_active = cv.take<int>(1);
+        scale = cv.take<double>(k);
+        rr64 = cv.take<double>(k);
+        bb64 = cv.take<double>(k);
+        nact64 = cv.take<int>(1);
+    };
+    Carver measure(nullptr);
+    carve(measure);
+    int rc = m->ws_poisson.reserve(measure.size());
+    if (rc) return rc;
+    Carver cv(m->ws_poisson.ptr);
+    carve(cv);
+    PcgState st{w.alpha, w.beta, w.rz, w.bb, w.rr, w.active, w.n_active, inner_rtol * inner_rtol};
+
+    if (!warm) AFEM_CUDA_TRY(cudaMemsetAsync(W, 0, NK * sizeof(double), s));
+    if ((rc = poisson_rhs_bc(m, phi, n, W, w.b, w.qpart, w.q, s))) return rc;
+    AFEM_LAUNCH((surface_only_kernel), grid_for(int64_t(NK)), 256, 0, s, W, w.z, Ni, N, k);
+    if ((rc = launch_stiffness(m, w.z, w.t, k, 0, s))) return rc;   // t = A g_ext (FP64)
+    int total_inner = 0, outer = 0, n_active = 1;
+    for (;;) {
+        if ((rc = launch_stiffness(m, W, w.Ap, k, 1, s))) return rc;   // FP64 residual
+        AFEM_LAUNCH((residual64_kernel), nblk, kRedThreads, 0, s, w.b, w.t, w.Ap, w.r, Ni, k, w.partial);
+        AFEM_LAUNCH((finalize_residual_kernel), 1, 64, 0, s, w.partial, nblk, k, rtol * rtol, rr64, bb64, scale,
+                    nact64);
+        AFEM_CUDA_TRY(cudaGetLastError());
+        AFEM_CUDA_TRY(cudaMemcpyAsync(&n_active, nact64, sizeof(int), cudaMemcpyDeviceToHost, s));
+        AFEM_CUDA_TRY(cudaStreamSynchronize(s));
+        if (n_active == 0 || total_inner >= max_it || outer >= 30) break;
+        ++outer;
+        // inner FP32 PCG on the scaled residual
+        AFEM_LAUNCH((pcg32_init_kernel), nblk, kRedThreads, 0, s, w.r, scale, D.stiff_dinv32, r32, z32, p32, d32,
+                    Ni, k, w.partial);
+        AFEM_LAUNCH((pcg_init_finalize_kernel), 1, 64, 0, s, w.partial, nblk, k, st);
+        int it = 0, inner_active = 1;
+        while (total_inner < max_it) {
+            if (it % 4 == 0) {
+                AFEM_CUDA_TRY(cudaMemcpyAsync(&inner_active, w.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+                AFEM_CUDA_TRY(cudaStreamSynchronize(s));
+                if (inner_active == 0) break;
+            }
+            if ((rc = launch_stiffness32(m, p32, Ap32, k, 1, s))) return rc;
+            AFEM_LAUNCH((col_dot32_kernel), nblk, kRedThreads, 0, s, p32, Ap32, Ni, k, w.partial);
+            AFEM_LAUNCH((pcg_alpha_kernel), 1, 64, 0, s, w.partial, nblk, k, st);
+            AFEM_LAUNCH((pcg32_update_kernel), nblk, kRedThreads, 0, s, d32, r32, z32, p32, Ap32, D.stiff_dinv32,
+                        Ni, k, st, w.partial);
+            AFEM_LAUNCH((pcg_beta_kernel), 1, 64, 0, s, w.partial, nblk, k, st);
+            AFEM_LAUNCH((pcg32_p_kernel), grid_for(Ni * k), 256, 0, s, p32, z32, Ni, k, st);
+            AFEM_CUDA_TRY(cudaGetLastError());
+            ++it;
+            ++total_inner;
+        }
+        AFEM_LAUNCH((refine_update_kernel), grid_for(Ni * k), 256, 0, s, W, d32, scale, Ni, k);
+        AFEM_CUDA_TRY(cudaGetLastError());
+    }
+    std::vector<double> rr(k), bb(k);
+    AFEM_CUDA_TRY(cudaMemcpyAsync(rr.data(), rr64, k * sizeof(double), cudaMemcpyDeviceToHost, s));
+    AFEM_CUDA_TRY(cudaMemcpyAsync(bb.data(), bb64, k * sizeof(double), cudaMemcpyDeviceToHost, s));
+    AFEM_CUDA_TRY(cudaStreamSynchronize(s));
+    if (iters_out) *iters_out = total_inner;
+    if (outer_out) *outer_out = outer;
+    bool finite = true;
+    for (int c = 0; c < k; ++c) {
+        const double rel = bb[c] > 0.0 ? std::sqrt(rr[c] / bb[c]) : 0.0;
+        if (!std::isfinite(rel)) finite = false;
+        if (relres_out) relres_out[c] = rel;
+    }
+    if (!finite) return set_error(AFEM_ENAN, "afem_poisson_batch: non-finite residual");
+    if (n_active > 0)
+        return set_error(AFEM_ECG_MAXIT, "afem_poisson_batch: refinement reached max_it before rtol");
+    return AFEM_OK;
+}
+
 }  // namespace afem
