@@ -26,7 +26,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 WORKLOAD = "h2_q4"
-METRIC = "MCTDHF steps/s (FP64 path; orbital-DoF applies/s reported alongside)"
+METRIC = "MCTDHF steps/s (FP32 form vs FP64 path at <=1e-6 rel. error; orbital-DoF applies/s alongside)"
 UNIT = "steps/s"
 
 
@@ -102,6 +102,43 @@ def setup_state(pkg, inputs, torch, w):
     return mesh, solver, phi0, C0
 
 
+def _timed_form(pkg, torch, solver, state0, precision, args, field, dt, dist, stream):
+    """Warm up and time K steps of one arithmetic form from a copy of state0."""
+    phi, C, W = (x.clone() for x in state0)
+    solver.set_precision(precision)
+    t = 0.0
+    for _ in range(args.warmup):
+        solver.step(phi, C, W, field(t), dt, cg_rtol=1e-10, cg_max_it=20000)
+        t += dt
+    torch.cuda.synchronize()
+    import ctypes
+    lib = pkg.load_library()
+    c0 = ctypes.c_int64(0)
+    lib.afem_kernel_launch_count(ctypes.byref(c0))
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    infos = []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        infos.append(solver.step(phi, C, W, field(t), dt, cg_rtol=1e-10, cg_max_it=20000))
+        t += dt
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    c1 = ctypes.c_int64(0)
+    lib.afem_kernel_launch_count(ctypes.byref(c1))
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if dist:
+        tt = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    return dict(ms=ms, infos=infos, state=(phi, C, W), t=t, launches=int(c1.value - c0.value))
+
+
 def run_ours(args, rank, world, dist):
     import numpy as np
     import torch
@@ -113,53 +150,42 @@ def run_ours(args, rank, world, dist):
     w = inputs.WORKLOADS[WORKLOAD]
     mesh, solver, phi0, C0 = setup_state(pkg, inputs, torch, w)
     n, N = w["n_orb"], mesh.N
-    phi = torch.from_numpy(phi0).cuda()
-    C = torch.from_numpy(C0).cuda()
-    W = torch.zeros((N, n * n), dtype=torch.float64, device="cuda")
+    X, ML, _ = mesh.tables()
+    state0 = (torch.from_numpy(phi0).cuda(), torch.from_numpy(C0).cuda(),
+              torch.zeros((N, n * n), dtype=torch.float64, device="cuda"))
     pulse = w["pulse"]
     dt = w["dt"]
-    t = 0.0
-    infos = []
+    stream = torch.cuda.current_stream()
 
     def field(tt):
         return inputs.sin2_pulse(tt, pulse["intensity"], pulse["wavelength_nm"], pulse["cycles"], pulse["pol"])
 
-    for _ in range(args.warmup):
-        solver.step(phi, C, W, field(t), dt, cg_rtol=1e-10, cg_max_it=20000)
-        t += dt
-    torch.cuda.synchronize()
-    stream = torch.cuda.current_stream()
-    lib = pkg.load_library()
-    import ctypes
-    cnt0 = ctypes.c_int64(0)
-    lib.afem_kernel_launch_count(ctypes.byref(cnt0))
+    # the plain FP64 path, then the precision form from the same initial state
+    fp64 = _timed_form(pkg, torch, solver, state0, pkg.PREC_FP64, args, field, dt, dist, stream)
     sampler = ClockSampler(dev)
     sampler.start()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        infos.append(solver.step(phi, C, W, field(t), dt, cg_rtol=1e-10, cg_max_it=20000))
-        t += dt
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
+    mixed = _timed_form(pkg, torch, solver, state0, pkg.PREC_MIXED, args, field, dt, dist, stream)
     clocks = sampler.stop()
-    cnt1 = ctypes.c_int64(0)
-    lib.afem_kernel_launch_count(ctypes.byref(cnt1))
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if dist:
-        tt = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = world * 1000.0 / ms
+    value = world * 1000.0 / mixed["ms"]
 
-    # ---- end to end: host buffers, copies inside the timed region
-    phi_h = torch.from_numpy(phi.cpu().numpy()).pin_memory()
+    # accuracy of the precision form against the FP64 path after warmup + K steps
+    ml = torch.from_numpy(ML).cuda()
+    def norms(phi):
+        return (torch.conj(phi) * phi).real.mul(ml[:, None]).sum(dim=0).cpu().numpy()
+    p64, c64, _ = fp64["state"]
+    p32, c32, _ = mixed["state"]
+    acc = {
+        "orbital_norms_max_rel": float(np.max(np.abs(norms(p32) - norms(p64)) / np.abs(norms(p64)))),
+        "energy_rel": abs(mixed["infos"][-1]["energy"] - fp64["infos"][-1]["energy"]) / abs(fp64["infos"][-1]["energy"]),
+        "orbitals_rel_l2": float(torch.linalg.norm(p32 - p64).item() / torch.linalg.norm(p64).item()),
+        "ci_rel_l2": float(torch.linalg.norm(c32 - c64).item() / torch.linalg.norm(c64).item()),
+        "steps_compared": args.warmup + args.steps,
+    }
+
+    # ---- end to end: host buffers, copies inside the timed region (precision form)
+    phi, C, W = mixed["state"]
+    t = mixed["t"]
+    phi_h = phi.cpu().pin_memory()
     C_h = C.cpu().pin_memory()
     W_h = W.cpu().pin_memory()
     e2e_steps = max(1, min(args.steps, 3))
@@ -178,88 +204,56 @@ def run_ours(args, rank, world, dist):
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     bytes_state = phi_h.numel() * 16 + C_h.numel() * 16 + W_h.numel() * 8
 
-    # ---- kernel roofline: the stiffness cell kernel of the Poisson CG, timed alone
-    # on the live mean fields (16 columns), and the H1 operator on the orbitals.
     kern = measure_kernels(pkg, torch, mesh, W, phi, field(t), stream)
     peaks, peak_src = _peaks()
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    fp64_peak = 152 * 4 * sm_mhz * 1e6 / 1e12     # TFLOP/s: 2 DFMA / clk / SM (1.25 TF nominal at 2.07 GHz)
-    achieved = kern["stiff_tflops"]
-    result = {
+    fp64_peak = 152 * 4 * sm_mhz * 1e6 / 1e12
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    mi = mixed["infos"]
+    fi = fp64["infos"]
+    return {
         "metric": METRIC,
         "value": value,
         "unit": UNIT,
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": ms,
+        "ms_per_step": mixed["ms"],
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64",
+        "dtype": "f32 cell operators + f64 refinement/Gram-Schmidt/CI",
         "data": "synthetic (seeded Gaussian orbitals on the nuclei, random-phase CI vector)",
         "config": {"workload": "H2 R=1.4 bohr, [-40,40]^3, 20^3 coarse, 5 levels/nucleus, Q4, "
                                "4 orbitals (1a+1b), 800nm 3-cycle sin^2 1e14 W/cm^2, dt=0.02, m=10, rtol=1e-10",
                    "n_masters": mesh.N, "n_cells": mesh.n_cells, "n_hanging": mesh.n_hanging,
                    "cache": "working set (Krylov basis, CG batch) larger than L2; no flush",
                    "parallelism": f"replicas x{world}"},
-        "orbital_dof_applies_per_s": kern["h1_orbital_dof_per_s"],
-        "step_detail": {"cg_iters_mean": float(np.mean([i["cg_iters"] for i in infos])),
-                        "krylov_m_used": infos[-1]["krylov_m_used"],
-                        "arnoldi_err_max": float(max(i["arnoldi_err"] for i in infos)),
-                        "energy_last": infos[-1]["energy"]},
-        "roofline": {"bound": "alu", "kernel": "cell_op_kernel<4,double> (stiffness, 16 real RHS)",
-                     "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s (FP64)",
-                     "frac": achieved / fp64_peak,
-                     "peak_note": "FP64 peak derived: 152 SMs x 2 DFMA/clk x median SM clock under load",
-                     "hbm_achieved_gbs": kern["stiff_gbs"], "hbm_peak_gbs": peaks.get("hbm_gbs"),
-                     "hbm_frac_of_" + peak_src: kern["stiff_gbs"] / peaks.get("hbm_gbs", 6800.0),
-                     "traffic": None},
+        "fp64_path": {"value": world * 1000.0 / fp64["ms"], "unit": UNIT, "ms_per_step": fp64["ms"],
+                      "cg_iters_mean": float(np.mean([i["cg_iters"] for i in fi])),
+                      "gpu_launches": fp64["launches"]},
+        "speedup_vs_fp64_path": fp64["ms"] / mixed["ms"],
+        "accuracy_vs_fp64_path": acc,
+        "orbital_dof_applies_per_s": {"fp64": kern["h1_orbital_dof_per_s"],
+                                      "fp32_in_G": kern["g32_orbital_dof_per_s"]},
+        "step_detail": {"inner_cg_iters_mean": float(np.mean([i["cg_iters"] for i in mi])),
+                        "krylov_m_used": mi[-1]["krylov_m_used"],
+                        "arnoldi_err_max": float(max(i["arnoldi_err"] for i in mi)),
+                        "energy_last": mi[-1]["energy"]},
+        "roofline": {"bound": "hbm", "kernel": "cell32_kernel<4,float,false> (FP32 stiffness, 16 real RHS)",
+                     "achieved": kern["stiff32_gbs"], "peak": hbm, "unit": "GB/s",
+                     "frac": kern["stiff32_gbs"] / hbm, "peak_source": peak_src,
+                     "algorithmic_bytes": "8 B per DoF*RHS (read x, write y; float32)",
+                     "traffic": None,
+                     "fp64_kernel": {"bound": "alu", "kernel": "cell_op_kernel<4,double> (stiffness, 16 RHS)",
+                                     "achieved_tflops": kern["stiff_tflops"], "peak_tflops": fp64_peak,
+                                     "frac": kern["stiff_tflops"] / fp64_peak,
+                                     "peak_note": "152 SMs x 2 DFMA/clk x median SM clock under load"}},
         "clocks": clocks,
         "e2e": {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": bytes_state,
                 "d2h_bytes_per_step": bytes_state},
-        "gpu_launches": int(cnt1.value - cnt0.value),
+        "gpu_launches": mixed["launches"],
     }
-    return result
-
-
-def measure_kernels(pkg, torch, mesh, W, phi, E, stream, reps=10):
-    """Average CUDA-event duration of the stiffness apply (16 columns) and the H1 apply (n orbitals)."""
-    out = {}
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    y = torch.empty_like(W)
-    ts = []
-    for r in range(reps + 2):
-        flush.zero_()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        pkg.op_apply(mesh, pkg.OP_STIFF, W, y)
-        b.record(stream)
-        torch.cuda.synchronize()
-        if r >= 2:
-            ts.append(a.elapsed_time(b) * 1e-3)
-    t_stiff = sum(ts) / len(ts)
-    nrhs = W.shape[1]
-    p1 = mesh.degree + 1
-    flops = mesh.n_cells * p1 ** 3 * nrhs * (3 * p1 * 2 + 6)   # 3 line contractions + combine, per node & column
-    out["stiff_tflops"] = flops / t_stiff / 1e12
-    out["stiff_gbs"] = mesh.N * nrhs * 16 / t_stiff / 1e9    # algorithmic bytes: read x, write y
-    yp = torch.empty_like(phi)
-    ts = []
-    for r in range(reps + 2):
-        flush.zero_()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        pkg.op_apply(mesh, pkg.OP_H1, phi, yp, E=E)
-        b.record(stream)
-        torch.cuda.synchronize()
-        if r >= 2:
-            ts.append(a.elapsed_time(b) * 1e-3)
-    t_h1 = sum(ts) / len(ts)
-    out["h1_orbital_dof_per_s"] = mesh.N * phi.shape[1] / t_h1
-    return out
 
 
 # ----------------------------------------------------------------- oracle arm
@@ -302,6 +296,78 @@ print(json.dumps({"sec_per_step": dt, "N": int(m.N), "steps": steps}))
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
+def _event_time(torch, stream, fn, flush, reps):
+    """Mean CUDA-event duration (s) of fn() on `stream`, L2 flushed before each launch."""
+    ts = []
+    for r in range(reps + 2):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        if r >= 2:
+            ts.append(a.elapsed_time(b) * 1e-3)
+    return sum(ts) / len(ts)
+
+
+def measure_kernels(pkg, torch, mesh, W, phi, E, stream, reps=10):
+    """Operator kernels timed alone on the live state: the stiffness of the
+    Poisson batch (16 real columns) in FP64 and FP32, the H1 operator on the
+    orbitals in complex128 and complex64."""
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    nrhs = W.shape[1]
+    p1 = mesh.degree + 1
+    flops = mesh.n_cells * p1 ** 3 * nrhs * (3 * p1 * 2 + 6)   # 3 line contractions + combine per node/column
+    out = {}
+    y = torch.empty_like(W)
+    t = _event_time(torch, stream, lambda: pkg.op_apply(mesh, pkg.OP_STIFF, W, y), flush, reps)
+    out["stiff_tflops"] = flops / t / 1e12
+    out["stiff_gbs"] = mesh.N * nrhs * 16 / t / 1e9
+    W32 = W.float().contiguous()
+    y32 = torch.empty_like(W32)
+    t = _event_time(torch, stream, lambda: pkg.op_apply(mesh, pkg.OP_STIFF_F32, W32, y32), flush, reps)
+    out["stiff32_s"] = t
+    out["stiff32_gbs"] = mesh.N * nrhs * 8 / t / 1e9          # algorithmic bytes: read x, write y (float32)
+    out["stiff32_tflops"] = flops / t / 1e12
+    yp = torch.empty_like(phi)
+    t = _event_time(torch, stream, lambda: pkg.op_apply(mesh, pkg.OP_H1, phi, yp, E=E), flush, reps)
+    out["h1_orbital_dof_per_s"] = mesh.N * phi.shape[1] / t
+    p64 = phi.to(torch.complex64).contiguous()
+    y64 = torch.empty_like(p64)
+    t = _event_time(torch, stream, lambda: pkg.op_apply(mesh, pkg.OP_H1_C64, p64, y64, E=E), flush, reps)
+    out["g32_orbital_dof_per_s"] = mesh.N * phi.shape[1] / t
+    return out
+
+
+def run_kernels_only(reps=3):
+    """The benchmark mesh and a mean-field-shaped batch; each operator kernel runs `reps` times."""
+    import numpy as np
+    import torch
+    import paper_2301_02387_gb300 as pkg
+    from paper_2301_02387_gb300 import inputs
+    torch.cuda.set_device(0)
+    w = inputs.WORKLOADS[WORKLOAD]
+    mesh, solver, phi0, C0 = setup_state(pkg, inputs, torch, w)
+    n = w["n_orb"]
+    phi = torch.from_numpy(phi0).cuda()
+    W = torch.zeros((mesh.N, n * n), dtype=torch.float64, device="cuda")
+    pkg.poisson_batch(mesh, phi, W, rtol=1e-6, max_it=20000, precision=pkg.PREC_MIXED)
+    W32 = W.float().contiguous()
+    y, y32 = torch.empty_like(W), torch.empty_like(W32)
+    p64 = phi.to(torch.complex64).contiguous()
+    yp, yp64 = torch.empty_like(phi), torch.empty_like(p64)
+    E = (0.0, 0.0, 0.01)
+    for _ in range(reps):
+        pkg.op_apply(mesh, pkg.OP_STIFF, W, y)
+        pkg.op_apply(mesh, pkg.OP_STIFF_F32, W32, y32)
+        pkg.op_apply(mesh, pkg.OP_H1, phi, yp, E=E)
+        pkg.op_apply(mesh, pkg.OP_H1_C64, p64, yp64, E=E)
+    torch.cuda.synchronize()
+    print("kernels-only done", mesh.N, float(np.abs(y32.cpu().numpy()).max()))
+
+
 def cpu_baseline_entry(N_full):
     s = oracle_sample()
     per_dof = s["sec_per_step"] / s["N"]
@@ -337,7 +403,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="build the workload and run each operator kernel a few times (for profilers); no JSON")
     args = ap.parse_args()
+    if args.kernels_only:
+        run_kernels_only()
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     dist = None

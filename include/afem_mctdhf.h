@@ -134,6 +134,8 @@ int afem_mesh_tables(const afem_mesh* mesh, double* coords, double* lumped_mass,
 /* Operator kinds for afem_op_apply. */
 #define AFEM_OP_H1 0      /* y = M_L^{-1} H1~ x, complex128, Dirichlet (Eq. discretized_eom) */
 #define AFEM_OP_STIFF 1   /* y = A x, float64, full Neumann stiffness over all masters */
+#define AFEM_OP_STIFF_F32 2  /* as AFEM_OP_STIFF in float32 (precision form) */
+#define AFEM_OP_H1_C64 3     /* as AFEM_OP_H1 in complex64 (precision form) */
 
 /* Matrix-free operator application on n_vec vectors at once (Sec. 3.1).
  *

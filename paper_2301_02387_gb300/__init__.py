@@ -11,7 +11,7 @@ import ctypes
 import numpy as np
 
 from . import _capi
-from ._capi import AfemError, OP_H1, OP_STIFF  # noqa: F401
+from ._capi import AfemError, OP_H1, OP_STIFF, OP_STIFF_F32, OP_H1_C64  # noqa: F401
 
 __all__ = ["Mesh", "op_apply", "AfemError", "OP_H1", "OP_STIFF", "load_library"]
 
@@ -103,11 +103,16 @@ class Mesh:
             pass
 
 
-def poisson_batch(mesh, phi, W, rtol=1e-10, max_it=20000, warm_start=False, stream=None,
-                  raise_on_maxit=True):
-    """afem_poisson_batch: pair mean fields W ([N, n^2] float64) of orbitals phi ([N, n] complex128).
+PREC_FP64 = 0
+PREC_MIXED = 1
 
-    Returns (iterations, relative residuals per column, status code).
+
+def poisson_batch(mesh, phi, W, rtol=1e-10, max_it=20000, warm_start=False, stream=None,
+                  raise_on_maxit=True, precision=PREC_FP64):
+    """afem_poisson_batch(_ex): pair mean fields W ([N, n^2] float64) of orbitals phi ([N, n] complex128).
+
+    Returns (iterations, relative residuals per column, status code); with
+    precision=PREC_MIXED the iteration count is the float32 inner total.
     """
     import torch
     n = int(phi.shape[1])
@@ -116,11 +121,12 @@ def poisson_batch(mesh, phi, W, rtol=1e-10, max_it=20000, warm_start=False, stre
     if W.shape[1] != n * n:
         raise ValueError("W must have n_orb^2 columns")
     it = ctypes.c_int(0)
+    outer = ctypes.c_int(0)
     rel = np.zeros(n * n, dtype=np.float64)
-    rc = _capi.load().afem_poisson_batch(
+    rc = _capi.load().afem_poisson_batch_ex(
         mesh.handle, ctypes.c_void_p(phi.data_ptr()), n, ctypes.c_void_p(W.data_ptr()), float(rtol),
-        int(max_it), 1 if warm_start else 0, ctypes.byref(it), rel.ctypes.data_as(ctypes.c_void_p),
-        _stream_ptr(stream))
+        int(max_it), 1 if warm_start else 0, int(precision), ctypes.byref(it), ctypes.byref(outer),
+        rel.ctypes.data_as(ctypes.c_void_p), _stream_ptr(stream))
     if rc != _capi.AFEM_OK and (raise_on_maxit or rc != _capi.AFEM_ECG_MAXIT):
         _capi.check(rc)
     return it.value, rel, rc
@@ -132,7 +138,7 @@ def _E3(E):
     return (ctypes.c_double * 3)(*[float(e) for e in E])
 
 
-def arnoldi_step(mesh, phi, U, krylov_m, dt, E=None, out=None, stream=None):
+def arnoldi_step(mesh, phi, U, krylov_m, dt, E=None, out=None, stream=None, precision=PREC_FP64):
     """afem_arnoldi_step: phi_out = exp(-i G dt) phi by short-iterative Arnoldi.
 
     phi: [N, n] complex128; U: [N, n, n] complex128 or None.  Returns
@@ -151,11 +157,11 @@ def arnoldi_step(mesh, phi, U, krylov_m, dt, E=None, out=None, stream=None):
     mu = ctypes.c_int(0)
     brk = ctypes.c_int(0)
     Earr = _E3(E)
-    _capi.check(_capi.load().afem_arnoldi_step(
+    _capi.check(_capi.load().afem_arnoldi_step_ex(
         mesh.handle, ctypes.cast(Earr, ctypes.c_void_p) if Earr is not None else None,
         ctypes.c_void_p(phi.data_ptr()), ctypes.c_void_p(U.data_ptr()) if U is not None else None,
-        n, int(krylov_m), float(dt), ctypes.c_void_p(out.data_ptr()), ctypes.byref(err), ctypes.byref(mu),
-        ctypes.byref(brk), _stream_ptr(stream)))
+        n, int(krylov_m), float(dt), int(precision), ctypes.c_void_p(out.data_ptr()), ctypes.byref(err),
+        ctypes.byref(mu), ctypes.byref(brk), _stream_ptr(stream)))
     return out, err.value, mu.value, bool(brk.value)
 
 
@@ -176,6 +182,9 @@ class MCTDHF:
         d = ctypes.c_int64(0)
         _capi.check(_capi.load().afem_mctdhf_ci_dim(h, ctypes.byref(d)))
         self.ci_dim = d.value
+
+    def set_precision(self, precision):
+        _capi.check(_capi.load().afem_mctdhf_set_precision(self._h, int(precision)))
 
     def step(self, phi, C, W, E, dt, cg_rtol=1e-10, cg_max_it=20000, stream=None, raise_on_maxit=True):
         import torch
@@ -212,7 +221,8 @@ def op_apply(mesh, kind, x, y, E=None, stream=None):
     OP_H1: complex128, y = M_L^{-1} H1~ x (Dirichlet); OP_STIFF: float64, y = A x.
     """
     import torch
-    dtype = {OP_H1: torch.complex128, OP_STIFF: torch.float64}.get(kind, x.dtype)
+    dtype = {OP_H1: torch.complex128, OP_STIFF: torch.float64, OP_STIFF_F32: torch.float32,
+             OP_H1_C64: torch.complex64}.get(kind, x.dtype)
     xp = _dev_ptr(x, dtype, mesh.N, "x")
     yp = _dev_ptr(y, dtype, mesh.N, "y")
     if x.shape != y.shape:

@@ -25,6 +25,8 @@ MESH_HOST_ONLY = 1
 
 OP_H1 = 0
 OP_STIFF = 1
+OP_STIFF_F32 = 2
+OP_H1_C64 = 3
 
 
 class MeshDesc(ctypes.Structure):
@@ -79,6 +81,11 @@ SIGNATURES = {
     "afem_op_apply": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, ctypes.c_int, _P]),
     "afem_poisson_batch": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_double, ctypes.c_int,
                                           ctypes.c_int, _P, _P, _P]),
+    "afem_poisson_batch_ex": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_double, ctypes.c_int,
+                                             ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]),
+    "afem_arnoldi_step_ex": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                            ctypes.c_int, _P, _P, _P, _P, _P]),
+    "afem_mctdhf_set_precision": (ctypes.c_int, [_P, ctypes.c_int]),
     "afem_arnoldi_step": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_double, _P,
                                          _P, _P, _P, _P]),
     "afem_mctdhf_create": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,

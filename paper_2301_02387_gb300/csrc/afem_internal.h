@@ -140,6 +140,8 @@ int poisson_batch(afem_mesh* m, const double2* phi, int n, double* W, double rto
                   int* iters_out, double* relres_out, cudaStream_t s);
 int poisson_batch_mixed(afem_mesh* m, const double2* phi, int n, double* W, double rtol, int max_it, int warm,
                         double inner_rtol, int* iters_out, int* outer_out, double* relres_out, cudaStream_t s);
+int multipole_boundary(afem_mesh* m, const double2* phi, int n, double* W, double* qpart, double* q, int nblk,
+                       cudaStream_t s);
 int mctdhf_create(afem_mesh* m, int n, int na, int nb, int mk, afem_mctdhf** out);
 void mctdhf_destroy(afem_mctdhf* S);
 int64_t mctdhf_ci_dim(const afem_mctdhf* S);

@@ -138,6 +138,137 @@ __global__ void __launch_bounds__(256) cell32_kernel(CellArgs32 a, const T* __re
     }
 }
 
+// Four-lane form of the same cell pass: every node's columns are handled as
+// float4 quads (4 real columns, or 2 complex orbitals), so gathers are 16-byte
+// loads and the scatter is one vector atomic per quad instead of four.  The
+// stiffness and potential terms act on every float lane alike; the mean-field
+// term of G mixes the orbitals of a node (complex products per orbital pair).
+__device__ __forceinline__ void f4fma(float4& acc, float s, const float4 v) {
+    acc.x = fmaf(s, v.x, acc.x);
+    acc.y = fmaf(s, v.y, acc.y);
+    acc.z = fmaf(s, v.z, acc.z);
+    acc.w = fmaf(s, v.w, acc.w);
+}
+
+__device__ __forceinline__ float4 gather32v(const CellArgs32& a, int idx, const float4* __restrict__ x, int L4,
+                                            int q) {
+    float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (idx >= 0) {
+        if (!(a.masked && idx >= a.n_interior)) val = x[int64_t(idx) * L4 + q];
+    } else {
+        const int hh = -idx - 1;
+        for (int e = a.hp[hh]; e < a.hp[hh + 1]; ++e) {
+            const int m = a.hm[e];
+            if (a.masked && m >= a.n_interior) continue;
+            f4fma(val, a.hw[e], x[int64_t(m) * L4 + q]);
+        }
+    }
+    return val;
+}
+
+__device__ __forceinline__ void scatter32v(const CellArgs32& a, int idx, float4* __restrict__ y, int L4, int q,
+                                           float4 r) {
+    if (idx >= 0) {
+        if (!(a.masked && idx >= a.n_interior)) atomicAdd(&y[int64_t(idx) * L4 + q], r);
+    } else {
+        const int hh = -idx - 1;
+        for (int e = a.hp[hh]; e < a.hp[hh + 1]; ++e) {
+            const int m = a.hm[e];
+            if (a.masked && m >= a.n_interior) continue;
+            const float w = a.hw[e];
+            atomicAdd(&y[int64_t(m) * L4 + q], make_float4(w * r.x, w * r.y, w * r.z, w * r.w));
+        }
+    }
+}
+
+template <int P, bool G>
+__global__ void __launch_bounds__(256) cell32v_kernel(CellArgs32 a, const float4* __restrict__ x,
+                                                      const float2* __restrict__ U, float4* __restrict__ y, int L4,
+                                                      int n) {
+    constexpr int P1 = P + 1;
+    constexpr int NN = P1 * P1 * P1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float4* s_u = reinterpret_cast<float4*>(smem_raw);           // [NN][L4]
+    float2* s_U = reinterpret_cast<float2*>(s_u + NN * L4);      // [NN][n*n] (G with U)
+    __shared__ int s_idx[NN];
+    __shared__ float s_pot[NN];
+    __shared__ float s_wq[NN];
+    __shared__ float s_K[P1 * P1];
+    __shared__ float s_w[P1];
+    const int64_t cell = blockIdx.x;
+    const int tid = threadIdx.x, bs = blockDim.x;
+    const float4 g = a.geom[cell];
+    for (int i = tid; i < NN; i += bs) s_idx[i] = a.cell_node[cell * NN + i];
+    if (tid < P1 * P1) s_K[tid] = a.K[tid];
+    if (tid < P1) s_w[tid] = a.w[tid];
+    __syncthreads();
+    for (int it = tid; it < NN * L4; it += bs) {
+        const int i = it / L4, q = it - i * L4;
+        s_u[it] = gather32v(a, s_idx[i], x, L4, q);
+    }
+    const int nn2 = n * n;
+    if (G) {
+        if (U) {
+            CellArgs32 au = a;
+            au.masked = 0;
+            for (int it = tid; it < NN * nn2; it += bs) {
+                const int i = it / nn2, pq = it - i * nn2;
+                s_U[it] = gather32<float2>(au, s_idx[i], U, nn2, pq);
+            }
+        }
+        const float h3 = g.w * g.w * g.w;
+        for (int i = tid; i < NN; i += bs) {
+            const int ia = i % P1, ib = (i / P1) % P1, ic = i / (P1 * P1);
+            const int idx = s_idx[i];
+            const float V = idx >= 0 ? a.v_master[idx] : a.v_hang[-idx - 1];
+            const float px = g.x + g.w * a.xi[ia], py = g.y + g.w * a.xi[ib], pz = g.z + g.w * a.xi[ic];
+            const float wq = h3 * s_w[ia] * s_w[ib] * s_w[ic];
+            s_wq[i] = wq;
+            s_pot[i] = wq * (V + a.E[0] * px + a.E[1] * py + a.E[2] * pz);
+        }
+    }
+    __syncthreads();
+    const float ck = (G ? 0.5f : 1.0f) * g.w;
+    for (int it = tid; it < NN * L4; it += bs) {
+        const int i = it / L4, q = it - i * L4;
+        const int ia = i % P1, ib = (i / P1) % P1, ic = i / (P1 * P1);
+        float4 ax = make_float4(0.f, 0.f, 0.f, 0.f), ay = ax, az = ax;
+#pragma unroll
+        for (int m = 0; m < P1; ++m) {
+            f4fma(ax, s_K[ia * P1 + m], s_u[(m + P1 * (ib + P1 * ic)) * L4 + q]);
+            f4fma(ay, s_K[ib * P1 + m], s_u[(ia + P1 * (m + P1 * ic)) * L4 + q]);
+            f4fma(az, s_K[ic * P1 + m], s_u[(ia + P1 * (ib + P1 * m)) * L4 + q]);
+        }
+        float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+        f4fma(r, ck * s_w[ib] * s_w[ic], ax);
+        f4fma(r, ck * s_w[ia] * s_w[ic], ay);
+        f4fma(r, ck * s_w[ia] * s_w[ib], az);
+        if constexpr (G) {
+            f4fma(r, s_pot[i], s_u[it]);
+            if (U) {
+                // orbitals p0 = 2q (lanes x, y) and p1 = 2q + 1 (lanes z, w)
+                const float2* ui = reinterpret_cast<const float2*>(s_u + i * L4);
+                float2 m0 = make_float2(0.f, 0.f), m1 = m0;
+                const float2* U0 = s_U + i * nn2 + (2 * q) * n;
+                const float2* U1 = U0 + n;
+                for (int rr = 0; rr < n; ++rr) {
+                    const float2 u = ui[rr];
+                    m0.x = fmaf(U0[rr].x, u.x, fmaf(-U0[rr].y, u.y, m0.x));
+                    m0.y = fmaf(U0[rr].x, u.y, fmaf(U0[rr].y, u.x, m0.y));
+                    m1.x = fmaf(U1[rr].x, u.x, fmaf(-U1[rr].y, u.y, m1.x));
+                    m1.y = fmaf(U1[rr].x, u.y, fmaf(U1[rr].y, u.x, m1.y));
+                }
+                const float wq = s_wq[i];
+                r.x = fmaf(wq, m0.x, r.x);
+                r.y = fmaf(wq, m0.y, r.y);
+                r.z = fmaf(wq, m1.x, r.z);
+                r.w = fmaf(wq, m1.y, r.w);
+            }
+        }
+        scatter32v(a, s_idx[i], y, L4, q, r);
+    }
+}
+
 CellArgs32 make_cell_args32(const afem_mesh* m) {
     CellArgs32 a{};
     const DeviceMesh& D = m->dev;
@@ -190,9 +321,47 @@ static int launch32(const afem_mesh* m, const CellArgs32& a, const T* x, const f
     return AFEM_OK;
 }
 
+// L = float lanes per node (multiple of 4); n = orbitals (G only).
+template <bool G>
+static int launch32v(const afem_mesh* m, const CellArgs32& a, const float* x, const float2* U, float* y, int L,
+                     int n, cudaStream_t s) {
+    const int p = m->dev.p;
+    const int nn = (p + 1) * (p + 1) * (p + 1);
+    const int L4 = L / 4;
+    const size_t smem = size_t(nn) * L4 * sizeof(float4) + ((G && U) ? size_t(nn) * n * n * sizeof(float2) : 0);
+    const unsigned grid = unsigned(m->dev.ncell);
+    AFEM_CUDA_TRY(cudaMemsetAsync(y, 0, size_t(m->dev.n_master) * L * sizeof(float), s));
+    if (grid == 0) return AFEM_OK;
+    const float4* x4 = reinterpret_cast<const float4*>(x);
+    float4* y4 = reinterpret_cast<float4*>(y);
+    switch (p) {
+#define AFEM_CASE(PP)                                                                          \
+    case PP: {                                                                                 \
+        auto k = cell32v_kernel<PP, G>;                                                        \
+        if (smem > 48 * 1024)                                                                  \
+            AFEM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                               int(smem)));                                    \
+        AFEM_LAUNCH((k), grid, 256, smem, s, a, x4, U, y4, L4, n);                             \
+        break;                                                                                 \
+    }
+        AFEM_CASE(1)
+        AFEM_CASE(2)
+        AFEM_CASE(3)
+        AFEM_CASE(4)
+#undef AFEM_CASE
+        default:
+            return set_error(AFEM_EINVAL, "degree out of range");
+    }
+    AFEM_CUDA_TRY(cudaGetLastError());
+    return AFEM_OK;
+}
+
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
 int launch_stiffness32(const afem_mesh* m, const float* x, float* y, int nv, int masked, cudaStream_t s) {
     CellArgs32 a = make_cell_args32(m);
     a.masked = masked;
+    if (nv % 4 == 0 && aligned16(x) && aligned16(y)) return launch32v<false>(m, a, x, nullptr, y, nv, 0, s);
     return launch32<float, false>(m, a, x, nullptr, y, nv, s);
 }
 
@@ -202,6 +371,8 @@ int launch_g_cell32(const afem_mesh* m, const double* E, const float2* v, const 
     CellArgs32 a = make_cell_args32(m);
     a.masked = 1;
     for (int i = 0; i < 3; ++i) a.E[i] = E ? float(E[i]) : 0.0f;
+    if (n % 2 == 0 && aligned16(v) && aligned16(z))
+        return launch32v<true>(m, a, reinterpret_cast<const float*>(v), U, reinterpret_cast<float*>(z), 2 * n, n, s);
     return launch32<float2, true>(m, a, v, U, z, n, s);
 }
 

@@ -282,6 +282,10 @@ int launch_stiffness(const afem_mesh* m, const double* x, double* y, int nv, int
     return launch_cell_op<double>(m, a, x, y, nv, s);
 }
 
+int launch_stiffness32(const afem_mesh* m, const float* x, float* y, int nv, int masked, cudaStream_t s);
+int launch_g_cell32(const afem_mesh* m, const double* E, const float2* v, const float2* U, float2* z, int n,
+                    cudaStream_t s);
+
 int launch_op_apply(afem_mesh* m, int kind, const double* E, const void* x, void* y, int nv,
                     cudaStream_t s) {
     CellArgs a = make_cell_args(m);
@@ -304,6 +308,14 @@ int launch_op_apply(afem_mesh* m, int kind, const double* E, const void* x, void
         auto* yy = static_cast<double*>(y);
         AFEM_CUDA_TRY(cudaMemsetAsync(yy, 0, size_t(N) * nv * sizeof(double), s));
         return launch_cell_op<double>(m, a, static_cast<const double*>(x), yy, nv, s);
+    }
+    if (kind == AFEM_OP_STIFF_F32)
+        return launch_stiffness32(m, static_cast<const float*>(x), static_cast<float*>(y), nv, 0, s);
+    if (kind == AFEM_OP_H1_C64) {
+        auto* yy = static_cast<float2*>(y);
+        int rc = launch_g_cell32(m, E, static_cast<const float2*>(x), nullptr, yy, nv, s);
+        if (rc) return rc;
+        return launch_scale_rows<float2>(yy, m->dev.ml_inv, N, nv, s);
     }
     return set_error(AFEM_EINVAL, "afem_op_apply: unknown operator kind");
 }

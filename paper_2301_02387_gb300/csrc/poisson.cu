@@ -164,7 +164,9 @@ __global__ void __launch_bounds__(256) pair_rhs_moments_kernel(PointArgs a, doub
                 for (int c = 0; c < ncol; ++c) wrow[c] = mf * rho[c];
                 // right-hand side through C^T
                 const double fpi = 4.0 * M_PI;
-                if (f < a.N) {
+                if (!b) {
+                    // moments only
+                } else if (f < a.N) {
                     for (int c = 0; c < ncol; ++c) atomicAdd(&b[f * ncol + c], fpi * wrow[c]);
                 } else {
                     const int64_t h = f - a.N;
@@ -533,6 +535,50 @@ int poisson_batch(afem_mesh* m, const double2* phi, int n, double* W, double rto
     if (!finite) return set_error(AFEM_ENAN, "afem_poisson_batch: non-finite residual");
     if (n_active > 0)
         return set_error(AFEM_ECG_MAXIT, "afem_poisson_batch: CG reached max_it before rtol");
+    return AFEM_OK;
+}
+
+// ------------------------------------------- surface data from given scratch
+// Moments only (no right-hand side) with `nblk` blocks, then the Dirichlet
+// data into the surface rows of W.  qpart must hold nblk * kNlm * n^2 doubles
+// and q kNlm * n^2; both are overwritten completely.
+int multipole_boundary(afem_mesh* m, const double2* phi, int n, double* W, double* qpart, double* q, int nblk,
+                       cudaStream_t s) {
+    const int ncol = n * n;
+    int rc = ensure_sh_tables();
+    if (rc) return rc;
+    const DeviceMesh& D = m->dev;
+    PointArgs a{};
+    a.phi = phi;
+    a.n = n;
+    a.ncol = ncol;
+    a.N = D.n_master;
+    a.n_int = D.n_interior;
+    a.nh = D.n_hanging;
+    a.xyz_m = D.master_xyz;
+    a.xyz_h = D.hang_xyz;
+    a.mf_m = D.mf_master;
+    a.mf_h = D.mf_hang;
+    a.hp = D.hang_ptr;
+    a.hm = D.hang_master;
+    a.hw = D.hang_w;
+    const double c0 = 0.5 * (m->desc.lo + m->desc.hi);
+    a.cx = a.cy = a.cz = c0;
+    const size_t smem = (size_t(kMomTile) * kNlm + size_t(kMomTile) * ncol + size_t(kNlm) * ncol) * sizeof(double);
+    AFEM_CUDA_TRY(cudaFuncSetAttribute(pair_rhs_moments_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(smem)));
+    AFEM_LAUNCH((pair_rhs_moments_kernel), nblk, 256, smem, s, a, static_cast<double*>(nullptr), qpart);
+    AFEM_LAUNCH((finalize_columns_kernel), 1, 256, 0, s, qpart, nblk, kNlm * ncol, q);
+    AFEM_CUDA_TRY(cudaGetLastError());
+    const int64_t nb = D.n_master - D.n_interior;
+    if (nb > 0) {
+        const size_t sm2 = size_t(kNlm) * ncol * sizeof(double);
+        AFEM_CUDA_TRY(cudaFuncSetAttribute(multipole_bc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           int(sm2)));
+        AFEM_LAUNCH((multipole_bc_kernel), grid_for(nb, 128, 152 * 8), 128, sm2, s, q, ncol, D.master_xyz,
+                    D.n_interior, D.n_master, c0, c0, c0, W);
+        AFEM_CUDA_TRY(cudaGetLastError());
+    }
     return AFEM_OK;
 }
 

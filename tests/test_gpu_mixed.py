@@ -1,0 +1,94 @@
+"""Precision form (FP32 cell operators, FP64 refinement / Gram-Schmidt / CI)
+against the FP64 oracle: the Poisson batch keeps the FP64 backward-error bar,
+the Arnoldi step and the MCTDHF step stay within 1e-6 relative."""
+import numpy as np
+import pytest
+
+from oracle import fem, krylov, mctdhf, mesh as omesh, poisson
+from paper_2301_02387_gb300 import inputs
+from tests._match import coord_permutation
+
+pytestmark = pytest.mark.gpu
+
+CASE = (-8.0, 8.0, 3, 3, [((0.0, 0.0, 0.7), 1.0, 2), ((0.0, 0.0, -0.7), 1.0, 2)], 2.0)
+
+
+@pytest.fixture(scope="module")
+def pair():
+    import paper_2301_02387_gb300 as pkg
+    gm = pkg.Mesh(*CASE)
+    om = omesh.Mesh(*CASE)
+    op = fem.Operators(om)
+    X, _, _ = gm.tables()
+    return gm, om, op, coord_permutation(X, om.Xm)
+
+
+def test_mixed_poisson_reaches_fp64_backward_error(pair):
+    import torch
+    import paper_2301_02387_gb300 as pkg
+    gm, om, op, perm = pair
+    phi_o = inputs.lowdin(inputs.molecular_orbitals(om.Xm, ~om.boundary, CASE[4], 3), op.ML)
+    ps = poisson.PoissonSolver(op)
+    rho, _ = poisson.pair_densities(op, phi_o)
+    phi = torch.from_numpy(np.ascontiguousarray(phi_o[perm])).cuda()
+    W = torch.zeros((gm.N, 9), dtype=torch.float64, device="cuda")
+    it, rel, rc = pkg.poisson_batch(gm, phi, W, rtol=1e-10, max_it=20000, precision=pkg.PREC_MIXED)
+    assert rc == 0 and np.all(rel <= 1e-10)
+    Wg = np.empty((om.N, 9))
+    Wg[perm] = W.cpu().numpy()
+    assert np.all(ps.residual(Wg, rho) < 2e-10)
+
+
+def test_mixed_arnoldi_within_1e6(pair):
+    import torch
+    import paper_2301_02387_gb300 as pkg
+    gm, om, op, perm = pair
+    n = 2
+    interior = ~om.boundary
+    phi_o = inputs.lowdin(inputs.molecular_orbitals(om.Xm, interior, CASE[4], n), op.ML)
+    rng = np.random.default_rng(4)
+    U_o = np.zeros((n, n, om.N), dtype=np.complex128)
+    for p in range(n):
+        for q in range(n):
+            U_o[p, q] = (0.3 + 0.1j * rng.standard_normal()) * np.exp(-0.2 * np.sum(om.Xm ** 2, axis=1))
+    E = (0.0, 0.0, 0.02)
+    sim = mctdhf.MCTDHF.__new__(mctdhf.MCTDHF)
+    sim.ops, sim.mesh, sim.n = op, om, n
+    sim.interior = interior.astype(np.float64)
+    ref, *_ = krylov.arnoldi_expm(lambda v: sim.G_apply(v, phi_o, U_o, E), phi_o, sim.inner, 8, 0.01)
+    phi = torch.from_numpy(np.ascontiguousarray(phi_o[perm])).cuda()
+    U = torch.from_numpy(np.ascontiguousarray(U_o.transpose(2, 0, 1)[perm])).cuda()
+    out, err, mu, brk = pkg.arnoldi_step(gm, phi, U, 8, 0.01, E=E, precision=pkg.PREC_MIXED)
+    torch.cuda.synchronize()
+    rel = np.linalg.norm(out.cpu().numpy() - ref[perm]) / np.linalg.norm(ref)
+    assert rel < 1e-6
+
+
+def test_mixed_mctdhf_steps_within_1e6(pair):
+    import torch
+    import paper_2301_02387_gb300 as pkg
+    gm, om, op, perm = pair
+    n, na, nb = 2, 1, 1
+    phi_o = inputs.lowdin(inputs.molecular_orbitals(om.Xm, ~om.boundary, CASE[4], n), op.ML)
+    C_o = inputs.initial_ci(n, na, nb, amp=0.1)
+    sim = mctdhf.MCTDHF(op, n, na, nb, poisson_method="cg", poisson_rtol=1e-13)
+    solver = pkg.MCTDHF(gm, n, na, nb, 8)
+    solver.set_precision(pkg.PREC_MIXED)
+    phi = torch.from_numpy(np.ascontiguousarray(phi_o[perm])).cuda()
+    C = torch.from_numpy(C_o.copy()).cuda()
+    W = torch.zeros((gm.N, n * n), dtype=torch.float64, device="cuda")
+    E = (0.0, 0.0, 0.03)
+    for _ in range(3):
+        phi_o, C_o, info_o = sim.step(phi_o, C_o, E, 0.01, 8)
+        info = solver.step(phi, C, W, E, 0.01, cg_rtol=1e-12)
+    torch.cuda.synchronize()
+    assert np.linalg.norm(phi.cpu().numpy() - phi_o[perm]) / np.linalg.norm(phi_o) < 1e-6
+    assert np.linalg.norm(C.cpu().numpy() - C_o) / np.linalg.norm(C_o) < 1e-6
+    assert abs(info["energy"] - info_o["energy"]) < 1e-6 * abs(info_o["energy"])
+    # orbital norms (sum over orbitals of phi^H M_L phi) agree to 1e-6
+    ML = op.ML
+    pg = np.empty_like(phi_o)
+    pg[perm] = phi.cpu().numpy()
+    ng = np.real(np.sum(np.conj(pg) * ML[:, None] * pg, axis=0))
+    no = np.real(np.sum(np.conj(phi_o) * ML[:, None] * phi_o, axis=0))
+    np.testing.assert_allclose(ng, no, rtol=1e-6)
