@@ -187,6 +187,34 @@ int afem_poisson_batch_ex(afem_mesh* mesh, const void* phi, int n_orb, void* W, 
                           int max_it, int warm_start, int precision, int* iters_out,
                           int* outer_out, double* relres_out, void* stream);
 
+/* Surface data of the pair mean fields without any device allocation.
+ *
+ * The paper has no counterpart: this is a library service.  It computes the
+ * same Dirichlet data as afem_poisson_batch (multipole expansion about the
+ * box centre, l <= 12, of every pair density of phi) and writes it into the
+ * surface rows [n_interior, N) of W (float64 [N][n_orb^2], same column
+ * layout); interior rows are not touched.  phi: complex128 [N][n_orb].
+ *
+ * It exists for callers that must not allocate device memory once they are
+ * running: for example a process whose device memory is fully reserved by
+ * another allocator's pool, or a service loop with a fixed memory budget.
+ * Such callers cannot use afem_poisson_batch, which grows a workspace on first
+ * use.  Here the scratch (moment partials and moments) is one file-scope
+ * device array of 413,712 doubles (about 3.2 MiB), held by every GPU that
+ * loads the library until the process exits; nothing is allocated or freed.
+ *
+ * Limits and behaviour:
+ *  - n_orb must be 1..AFEM_NOALLOC_MAX_ORB; larger values return AFEM_EINVAL.
+ *  - The first call on a device looks up the device address of the scratch
+ *    array (with that device current); make that first call before any stream
+ *    capture.
+ *  - All calls share the one scratch array and each call overwrites it
+ *    completely before reading it; calls that overlap on the GPU (other
+ *    streams, other host threads) race and must be serialised by the caller.
+ * Asynchronous on `stream`. */
+#define AFEM_NOALLOC_MAX_ORB 4
+int afem_poisson_boundary_noalloc(afem_mesh* mesh, const void* phi, int n_orb, void* W, void* stream);
+
 /* One short-iterative Arnoldi step of the packed orbital equation with the
  * operator frozen (Sec. 3.2, Eq. packed_orb_eom; Eq. orb_eom with X = 0):
  *   (G v)_p = Q [ M_L^-1 ( H1~ v_p + C^T diag(m_f) sum_q (C U_pq) o (C v_q) ) ],
