@@ -77,3 +77,38 @@ def test_op_apply_rejects_bad_arguments():
         op_apply(gm, 7, x, torch.empty_like(x))
     with pytest.raises(AfemError):
         op_apply(gm, OP_H1, x, x)
+
+
+@pytest.mark.parametrize("case", CASES[:3])
+@pytest.mark.parametrize("nvec", [3, 16])     # 3: scalar-lane kernel, 16: four-lane kernel
+def test_stiffness_f32_within_fp32_tolerance(case, nvec):
+    """Precision form of the stiffness: relative error a few float32 ulps x operator norm."""
+    import torch
+    from paper_2301_02387_gb300 import op_apply, OP_STIFF_F32
+    gm, om, op, perm = _pair(case)
+    rng = np.random.default_rng(9)
+    xo = rng.standard_normal((om.N, nvec)).astype(np.float32).astype(np.float64)
+    yo = op.stiffness_apply(xo)
+    x = torch.from_numpy(np.ascontiguousarray(xo[perm])).float().cuda()
+    y = torch.empty_like(x)
+    op_apply(gm, OP_STIFF_F32, x, y)
+    torch.cuda.synchronize()
+    assert _relerr(y.double().cpu().numpy(), yo[perm]) < 2e-5
+
+
+@pytest.mark.parametrize("case", CASES[:3])
+@pytest.mark.parametrize("nvec", [1, 4])      # 1: scalar-lane kernel, 4: four-lane kernel
+def test_h1_c64_within_fp32_tolerance(case, nvec):
+    import torch
+    from paper_2301_02387_gb300 import op_apply, OP_H1_C64
+    gm, om, op, perm = _pair(case)
+    rng = np.random.default_rng(12)
+    xo = (rng.standard_normal((om.N, nvec)) + 1j * rng.standard_normal((om.N, nvec))).astype(np.complex64)
+    xo = xo.astype(np.complex128)
+    E = (0.013, -0.02, 0.031)
+    yo = op.h1_apply(xo, E=E)
+    x = torch.from_numpy(np.ascontiguousarray(xo[perm])).to(torch.complex64).cuda()
+    y = torch.empty_like(x)
+    op_apply(gm, OP_H1_C64, x, y, E=E)
+    torch.cuda.synchronize()
+    assert _relerr(y.to(torch.complex128).cpu().numpy(), yo[perm]) < 2e-5
