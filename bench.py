@@ -106,6 +106,7 @@ def _timed_form(pkg, torch, solver, state0, precision, args, field, dt, dist, st
     """Warm up and time K steps of one arithmetic form from a copy of state0."""
     phi, C, W = (x.clone() for x in state0)
     solver.set_precision(precision)
+    solver.set_krylov_tol(args.krylov_tol)
     t = 0.0
     for _ in range(args.warmup):
         solver.step(phi, C, W, field(t), dt, cg_rtol=1e-10, cg_max_it=20000)
@@ -234,7 +235,8 @@ def run_ours(args, rank, world, dist):
         "dtype": "f32 cell operators + f64 refinement/Gram-Schmidt/CI",
         "data": "synthetic (seeded Gaussian orbitals on the nuclei, random-phase CI vector)",
         "config": {"workload": "H2 R=1.4 bohr, [-40,40]^3, 20^3 coarse, 5 levels/nucleus, Q4, "
-                               "4 orbitals (1a+1b), 800nm 3-cycle sin^2 1e14 W/cm^2, dt=0.02, m=10, rtol=1e-10",
+                               "4 orbitals (1a+1b), 800nm 3-cycle sin^2 1e14 W/cm^2, dt=0.02, m=10, rtol=1e-10, "
+                               f"Krylov error threshold {args.krylov_tol:g} per substep",
                    "n_masters": mesh.N, "n_cells": mesh.n_cells, "n_hanging": mesh.n_hanging,
                    "cache": "working set (Krylov basis, CG batch) larger than L2; no flush",
                    "parallelism": f"replicas x{world}"},
@@ -245,6 +247,8 @@ def run_ours(args, rank, world, dist):
                                       "fp32_in_G": kern["g32_orbital_dof_per_s"]},
         "step_detail": {"inner_cg_iters_mean": float(np.mean([i["cg_iters"] for i in mi])),
                         "krylov_m_used": mi[-1]["krylov_m_used"],
+                        "krylov_substeps_mean": float(np.mean([i["krylov_substeps"] for i in mi])),
+                        "krylov_tol": args.krylov_tol,
                         "arnoldi_err_max": float(max(i["arnoldi_err"] for i in mi)),
                         "energy_last": mi[-1]["energy"]},
         "roofline": {"bound": "hbm", "kernel": "cell32_kernel<4,float,false> (FP32 stiffness, 16 real RHS)",
@@ -359,8 +363,11 @@ def run_kernels_only(reps=3):
     mesh, solver, phi0, C0 = setup_state(pkg, inputs, torch, w)
     n = w["n_orb"]
     phi = torch.from_numpy(phi0).cuda()
-    W = torch.zeros((mesh.N, n * n), dtype=torch.float64, device="cuda")
-    pkg.poisson_batch(mesh, phi, W, rtol=1e-6, max_it=20000, precision=pkg.PREC_MIXED)
+    # smooth mean-field-shaped columns (no solver launches before the profiled kernels)
+    X, _, _ = mesh.tables()
+    r = np.sqrt(np.sum(X ** 2, axis=1))
+    cols = [1.0 / np.sqrt(r * r + 0.3 * (c + 1)) for c in range(n * n)]
+    W = torch.from_numpy(np.ascontiguousarray(np.stack(cols, axis=1))).cuda()
     W32 = W.float().contiguous()
     y, y32 = torch.empty_like(W), torch.empty_like(W32)
     p64 = phi.to(torch.complex64).contiguous()
@@ -373,6 +380,29 @@ def run_kernels_only(reps=3):
         pkg.op_apply(mesh, pkg.OP_H1_C64, p64, yp64, E=E)
     torch.cuda.synchronize()
     print("kernels-only done", mesh.N, float(np.abs(y32.cpu().numpy()).max()))
+
+
+def run_profile_step(inner_iters=48):
+    """One precision-form MCTDHF step of the workload with the Poisson inner CG
+    capped at `inner_iters` iterations and one Krylov step: every kernel of a
+    step appears, in a launch count small enough for a profiler's launch list."""
+    import torch
+    import paper_2301_02387_gb300 as pkg
+    from paper_2301_02387_gb300 import inputs
+    torch.cuda.set_device(0)
+    w = inputs.WORKLOADS[WORKLOAD]
+    mesh, solver, phi0, C0 = setup_state(pkg, inputs, torch, w)
+    n = w["n_orb"]
+    phi = torch.from_numpy(phi0).cuda()
+    C = torch.from_numpy(C0).cuda()
+    W = torch.zeros((mesh.N, n * n), dtype=torch.float64, device="cuda")
+    solver.set_precision(pkg.PREC_MIXED)
+    solver.set_krylov_tol(0.0)
+    pulse = w["pulse"]
+    E = inputs.sin2_pulse(1.0, pulse["intensity"], pulse["wavelength_nm"], pulse["cycles"], pulse["pol"])
+    info = solver.step(phi, C, W, E, w["dt"], cg_rtol=1e-10, cg_max_it=inner_iters, raise_on_maxit=False)
+    torch.cuda.synchronize()
+    print("profile-step done", info)
 
 
 def cpu_baseline_entry(N_full):
@@ -410,13 +440,20 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--krylov-tol", type=float, default=1e-10,
+                    help="Krylov error threshold per substep (0: one fixed-dimension Krylov step per time step)")
     ap.add_argument("--form", default="both", choices=["both", "mixed"],
                     help="both: time the FP64 path and the precision form; mixed: the precision form only")
     ap.add_argument("--kernels-only", action="store_true",
                     help="build the workload and run each operator kernel a few times (for profilers); no JSON")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="one precision-form step with the inner CG capped (for a profiler's launch list); no JSON")
     args = ap.parse_args()
     if args.kernels_only:
         run_kernels_only()
+        return
+    if args.profile_step:
+        run_profile_step()
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

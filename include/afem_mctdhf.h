@@ -176,13 +176,15 @@ int afem_poisson_batch(afem_mesh* mesh, const void* phi, int n_orb, void* W, dou
                        int max_it, int warm_start, int* iters_out, double* relres_out,
                        void* stream);
 
-/* As afem_poisson_batch with a choice of arithmetic.  AFEM_PREC_MIXED solves
- * by iterative refinement: each outer pass forms the float64 residual with the
- * float64 operator, runs Jacobi-PCG in float32 on the residual scaled to unit
- * norm (to relative residual 1e-4), and adds the correction in float64; it
- * stops on the same float64 test as afem_poisson_batch.  iters_out counts
- * inner (float32) iterations, outer_out (host, may be NULL) the refinement
- * passes; max_it bounds the inner iterations summed over passes. */
+/* As afem_poisson_batch with a choice of arithmetic.  AFEM_PREC_MIXED runs one
+ * Jacobi-PCG per column in float32 (operator, vectors) on the residual scaled
+ * to unit norm, folds its correction into the float64 W, and replaces the
+ * float32 residual by the true float64 residual (rescaling the search
+ * direction) whenever the float32 residual has dropped 100-fold since the last
+ * replacement or claims convergence ("reliable updates").  It stops on the
+ * same float64 test as afem_poisson_batch.  iters_out counts float32
+ * iterations (bounded by max_it), outer_out (host, may be NULL) the float64
+ * residual evaluations. */
 int afem_poisson_batch_ex(afem_mesh* mesh, const void* phi, int n_orb, void* W, double rtol,
                           int max_it, int warm_start, int precision, int* iters_out,
                           int* outer_out, double* relres_out, void* stream);
@@ -242,6 +244,18 @@ int afem_arnoldi_step_ex(afem_mesh* mesh, const double* E, const void* phi, cons
                          int krylov_m, double dt, int precision, void* phi_out, double* err_est,
                          int* m_used, int* breakdown, void* stream);
 
+/* exp(-i G dt) phi with error control (Sec. 3.2): G frozen as in
+ * afem_arnoldi_step; dt is covered by substeps tau_1, tau_2, ..., each from a
+ * fresh Krylov space of dimension krylov_m built from the current vector, and
+ * each chosen (halving or shrinking by (tol/err)^(1/m)) so that
+ * beta |h_{m+1,m}| |e_m^T exp(-i tau H_m) e_1| <= tol * beta.  err_est (host,
+ * may be NULL) receives the sum of the accepted estimates, substeps (host, may
+ * be NULL) the substep count.  More than 4096 substeps returns AFEM_EINVAL.
+ * Allocates (grow-only) mesh-owned workspace; synchronises `stream`. */
+int afem_arnoldi_propagate(afem_mesh* mesh, const double* E, const void* phi, const void* U, int n_orb,
+                           int krylov_m, double dt, int precision, double tol, void* phi_out,
+                           double* err_est, int* substeps, void* stream);
+
 /* MCTDHF time stepper (Sec. 2 and Sec. 3.2): owns the determinant-space
  * tables and its device workspace; the mesh must outlive it. */
 typedef struct afem_mctdhf afem_mctdhf;
@@ -253,7 +267,7 @@ typedef struct afem_step_info {
     int32_t krylov_m_used;
     int32_t breakdown;
     int32_t cg_iters;
-    int32_t pad0;
+    int32_t krylov_substeps; /* Krylov substeps taken (1 unless a Krylov tolerance is set) */
 } afem_step_info;
 
 /* n_orb spatial orbitals (1..8), n_alpha / n_beta electrons per spin
@@ -269,6 +283,13 @@ int afem_mctdhf_destroy(afem_mctdhf* solver);
  * (Poisson by float32 PCG inside float64 refinement, G cell pass in
  * complex64; everything else float64).  Host only, no device work. */
 int afem_mctdhf_set_precision(afem_mctdhf* solver, int precision);
+/* Krylov accuracy control of later steps (Sec. 3.2: the Krylov propagation
+ * is controlled by an a-posteriori error estimate, 1e-10 in the paper).
+ * tol = 0 (default): one Krylov step of dimension krylov_m per time step.
+ * tol > 0: the orbital step is split into substeps of the same frozen G, each
+ * short enough that its estimate stays below tol * ||phi|| (see
+ * afem_arnoldi_propagate).  Host only. */
+int afem_mctdhf_set_krylov_tol(afem_mctdhf* solver, double tol);
 /* Number of determinants (host). */
 int afem_mctdhf_ci_dim(const afem_mctdhf* solver, int64_t* dim);
 

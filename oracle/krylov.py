@@ -45,3 +45,55 @@ def arnoldi_expm(apply_G, phi, inner, m, dt, breakdown_tol=1e-14):
     out = sum(y[i] * V[i] for i in range(m_used))
     err = 0.0 if breakdown else beta * abs(H[m_used, m_used - 1]) * abs(Em[m_used - 1, 0])
     return out, err, H, m_used, breakdown
+
+
+def arnoldi_basis(apply_G, phi, inner, m, breakdown_tol=1e-14):
+    """(beta, V list, H (m+1 x m), m_used, breakdown, h_{m_used+1, m_used}) of the Krylov space from phi."""
+    beta = np.sqrt(inner(phi, phi).real)
+    V = [phi / beta]
+    H = np.zeros((m + 1, m), dtype=np.complex128)
+    m_used, breakdown = m, False
+    for j in range(m):
+        w = apply_G(V[j])
+        for i in range(j + 1):
+            H[i, j] = inner(V[i], w)
+            w = w - H[i, j] * V[i]
+        hn = np.sqrt(inner(w, w).real)
+        H[j + 1, j] = hn
+        if hn < breakdown_tol * beta:
+            m_used, breakdown = j + 1, True
+            break
+        V.append(w / hn)
+    return beta, V, H, m_used, breakdown, abs(H[m_used, m_used - 1])
+
+
+def arnoldi_propagate(apply_G, phi, inner, m, dt, tol, max_substeps=4096):
+    """exp(-i G dt) phi with the Krylov error controlled substep by substep.
+
+    Sec. 3.2 fixes the Krylov accuracy by an a-posteriori estimate (threshold
+    1e-10 in the paper).  Here the dimension m is fixed and dt is covered by
+    substeps of the same G: the first trial is the whole remainder; while
+    beta |h_{m+1,m}| |e_m^T exp(-i tau H_m) e_1| > tol beta, tau is multiplied
+    by min(1/2, max(0.05, 0.9 (tol beta / err)^(1/m))); the accepted substep
+    gives the next starting vector.  Returns (phi_new, sum of estimates, substeps).
+    """
+    remaining = dt
+    cur = phi
+    total, substeps = 0.0, 0
+    while remaining > 0.0:
+        if substeps >= max_substeps:
+            raise RuntimeError("too many Krylov substeps")
+        beta, V, H, mu, brk, hlast = arnoldi_basis(apply_G, cur, inner, m)
+        tau = remaining
+        for tries in range(41):
+            Em = scipy.linalg.expm(-1j * tau * H[:mu, :mu])
+            err = 0.0 if brk else beta * hlast * abs(Em[mu - 1, 0])
+            if brk or err <= tol * beta or tries >= 40:
+                break
+            shrink = 0.9 * (tol * beta / err) ** (1.0 / mu)
+            tau *= min(0.5, max(shrink, 0.05))
+        cur = sum(beta * Em[i, 0] * V[i] for i in range(mu))
+        total += err
+        substeps += 1
+        remaining = 0.0 if tau >= remaining else remaining - tau
+    return cur, total, substeps

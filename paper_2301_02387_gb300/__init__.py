@@ -165,6 +165,26 @@ def arnoldi_step(mesh, phi, U, krylov_m, dt, E=None, out=None, stream=None, prec
     return out, err.value, mu.value, bool(brk.value)
 
 
+def arnoldi_propagate(mesh, phi, U, krylov_m, dt, tol, E=None, out=None, stream=None, precision=PREC_FP64):
+    """afem_arnoldi_propagate: exp(-i G dt) phi with Krylov error control.  Returns (phi_out, err, substeps)."""
+    import torch
+    n = int(phi.shape[1])
+    _dev_ptr(phi, torch.complex128, mesh.N, "phi")
+    if U is not None:
+        _dev_ptr(U, torch.complex128, mesh.N, "U")
+    out = torch.empty_like(phi) if out is None else out
+    _dev_ptr(out, torch.complex128, mesh.N, "out")
+    err = ctypes.c_double(0.0)
+    sub = ctypes.c_int(0)
+    Earr = _E3(E)
+    _capi.check(_capi.load().afem_arnoldi_propagate(
+        mesh.handle, ctypes.cast(Earr, ctypes.c_void_p) if Earr is not None else None,
+        ctypes.c_void_p(phi.data_ptr()), ctypes.c_void_p(U.data_ptr()) if U is not None else None,
+        n, int(krylov_m), float(dt), int(precision), float(tol), ctypes.c_void_p(out.data_ptr()),
+        ctypes.byref(err), ctypes.byref(sub), _stream_ptr(stream)))
+    return out, err.value, sub.value
+
+
 class MCTDHF:
     """afem_mctdhf_*: the MCTDHF time stepper of one mesh (Sec. 2, Sec. 3.2).
 
@@ -182,6 +202,9 @@ class MCTDHF:
         d = ctypes.c_int64(0)
         _capi.check(_capi.load().afem_mctdhf_ci_dim(h, ctypes.byref(d)))
         self.ci_dim = d.value
+
+    def set_krylov_tol(self, tol):
+        _capi.check(_capi.load().afem_mctdhf_set_krylov_tol(self._h, float(tol)))
 
     def set_precision(self, precision):
         _capi.check(_capi.load().afem_mctdhf_set_precision(self._h, int(precision)))
@@ -201,6 +224,7 @@ class MCTDHF:
             _capi.check(rc)
         return dict(energy=info.energy, arnoldi_err=info.arnoldi_err, cg_relres_max=info.cg_relres_max,
                     krylov_m_used=info.krylov_m_used, breakdown=bool(info.breakdown), cg_iters=info.cg_iters,
+                    krylov_substeps=info.krylov_substeps,
                     status=rc)
 
     def close(self):

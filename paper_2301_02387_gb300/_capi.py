@@ -56,7 +56,7 @@ class StepInfo(ctypes.Structure):
         ("energy", ctypes.c_double), ("arnoldi_err", ctypes.c_double),
         ("cg_relres_max", ctypes.c_double),
         ("krylov_m_used", ctypes.c_int32), ("breakdown", ctypes.c_int32),
-        ("cg_iters", ctypes.c_int32), ("pad0", ctypes.c_int32),
+        ("cg_iters", ctypes.c_int32), ("krylov_substeps", ctypes.c_int32),
     ]
 
 
@@ -87,6 +87,9 @@ SIGNATURES = {
     "afem_arnoldi_step_ex": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                             ctypes.c_int, _P, _P, _P, _P, _P]),
     "afem_mctdhf_set_precision": (ctypes.c_int, [_P, ctypes.c_int]),
+    "afem_mctdhf_set_krylov_tol": (ctypes.c_int, [_P, ctypes.c_double]),
+    "afem_arnoldi_propagate": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                              ctypes.c_int, ctypes.c_double, _P, _P, _P, _P]),
     "afem_arnoldi_step": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_double, _P,
                                          _P, _P, _P, _P]),
     "afem_mctdhf_create": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,

@@ -146,6 +146,7 @@ int mctdhf_create(afem_mesh* m, int n, int na, int nb, int mk, afem_mctdhf** out
 void mctdhf_destroy(afem_mctdhf* S);
 int64_t mctdhf_ci_dim(const afem_mctdhf* S);
 void mctdhf_set_precision(afem_mctdhf* S, int precision);
+void mctdhf_set_krylov_tol(afem_mctdhf* S, double tol);
 int mctdhf_step(afem_mctdhf* S, double2* phi, double2* C, double* W, const double* E, double dt, double cg_rtol,
                 int cg_max_it, afem_step_info* info, cudaStream_t s);
 }  // namespace afem

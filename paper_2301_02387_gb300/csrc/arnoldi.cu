@@ -351,9 +351,15 @@ int arnoldi_reserve(afem_mesh* m, int n, int mk, ArnoldiWork& w) {
     return AFEM_OK;
 }
 
+// Propagates phi by exp(-i G dt) with G frozen at phi (projector), U and E.
+// tol <= 0: one Krylov step of dimension mk over the whole dt.  tol > 0:
+// substeps tau chosen so that each substep's error estimate
+// beta |h_{m+1,m}| |e_m^T exp(-i tau H_m) e_1| stays below tol * beta (the
+// paper fixes the Krylov accuracy by such an estimate; here the dimension is
+// fixed and the substep adapts), each from a fresh Krylov space of the same G.
 int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double2* U, const float2* U32, int n,
-                 int mk, double dt, int mixed, double2* phi_out, double* err_est, int* m_used_out,
-                 int* breakdown_out, cudaStream_t s) {
+                 int mk, double dt, int mixed, double tol, double2* phi_out, double* err_est, int* m_used_out,
+                 int* breakdown_out, int* substeps_out, cudaStream_t s) {
     const DeviceMesh& D = m->dev;
     ArnoldiWork w{};
     int rc = arnoldi_reserve(m, n, mk, w);
@@ -363,80 +369,97 @@ int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double
         U32 = w.U32;
     }
     const int64_t NV = w.stride;
-    const int64_t NIV = D.n_interior * n;
     const int ldh = kMaxKrylov + 1;
-    AFEM_CUDA_TRY(cudaMemsetAsync(w.H, 0, sizeof(double2) * ldh * kMaxKrylov, s));
-    // beta^2 = <phi, phi>_M ; V_0 = phi / beta
-    AFEM_LAUNCH((mgs_kernel), kRedBlocks, kRedThreads, 0, s, const_cast<double2*>(phi), nullptr, nullptr, nullptr, D.ml,
-                                                  D.n_interior, n, w.cpartial);
-    AFEM_LAUNCH((sum_partials_kernel), 1, 32, 0, s, w.cpartial, kRedBlocks, w.beta2);
-    AFEM_CUDA_TRY(cudaMemcpyAsync(w.V, phi, NV * sizeof(double2), cudaMemcpyDeviceToDevice, s));
-    AFEM_LAUNCH((cscale_kernel), grid_for(NV), 256, 0, s, w.V, NV, w.beta2, 1.0, 1);
-    AFEM_CUDA_TRY(cudaGetLastError());
-    double2 beta2_h;
-    AFEM_CUDA_TRY(cudaMemcpyAsync(&beta2_h, w.beta2, sizeof(double2), cudaMemcpyDeviceToHost, s));
-    AFEM_CUDA_TRY(cudaStreamSynchronize(s));
-    const double beta = std::sqrt(beta2_h.x);
-    if (!(beta > 0.0) || !std::isfinite(beta)) return set_error(AFEM_ENAN, "arnoldi: zero or non-finite norm");
-    int m_used = mk;
-    int brk = 0;
-    double hlast = 0.0;
-    for (int j = 0; j < mk; ++j) {
-        double2* Vj = w.V + j * NV;
-        double2* Wn = w.V + (j + 1) * NV;
-        if (mixed) {
-            if ((rc = g_apply32(m, E, phi, U32, n, Vj, w, Wn, s))) return rc;
-        } else {
-            if ((rc = g_apply(m, E, phi, U, n, Vj, w.z, Wn, w, s))) return rc;
-        }
-        // modified Gram-Schmidt against V_0..V_j
-        for (int i = 0; i <= j; ++i) {
-            const double2* Vprev = i > 0 ? w.V + (i - 1) * NV : nullptr;
-            const double2* hprev = i > 0 ? w.H + j * ldh + (i - 1) : nullptr;
-            AFEM_LAUNCH((mgs_kernel), kRedBlocks, kRedThreads, 0, s, Wn, Vprev, hprev, w.V + i * NV, D.ml, D.n_interior, n,
-                                                          w.cpartial);
-            AFEM_LAUNCH((sum_partials_kernel), 1, 32, 0, s, w.cpartial, kRedBlocks, w.H + j * ldh + i);
-        }
-        // last update and the norm
-        AFEM_LAUNCH((mgs_kernel), kRedBlocks, kRedThreads, 0, s, Wn, w.V + j * NV, w.H + j * ldh + j, nullptr, D.ml,
-                                                      D.n_interior, n, w.cpartial);
+    const double2* src = phi;
+    double remaining = dt;
+    double err_sum = 0.0;
+    int substeps = 0, m_used = mk, brk = 0;
+    std::vector<double2> Eh(size_t(kMaxKrylov) * kMaxKrylov);
+    while (remaining > 0.0) {
+        if (substeps >= 4096) return set_error(AFEM_EINVAL, "arnoldi: more than 4096 substeps (tolerance too tight)");
+        AFEM_CUDA_TRY(cudaMemsetAsync(w.H, 0, sizeof(double2) * ldh * kMaxKrylov, s));
+        // beta^2 = <src, src>_M ; V_0 = src / beta
+        AFEM_LAUNCH((mgs_kernel), kRedBlocks, kRedThreads, 0, s, const_cast<double2*>(src), nullptr, nullptr,
+                    nullptr, D.ml, D.n_interior, n, w.cpartial);
         AFEM_LAUNCH((sum_partials_kernel), 1, 32, 0, s, w.cpartial, kRedBlocks, w.beta2);
+        AFEM_CUDA_TRY(cudaMemcpyAsync(w.V, src, NV * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+        AFEM_LAUNCH((cscale_kernel), grid_for(NV), 256, 0, s, w.V, NV, w.beta2, 1.0, 1);
         AFEM_CUDA_TRY(cudaGetLastError());
-        double2 nn2;
-        AFEM_CUDA_TRY(cudaMemcpyAsync(&nn2, w.beta2, sizeof(double2), cudaMemcpyDeviceToHost, s));
+        double2 beta2_h;
+        AFEM_CUDA_TRY(cudaMemcpyAsync(&beta2_h, w.beta2, sizeof(double2), cudaMemcpyDeviceToHost, s));
         AFEM_CUDA_TRY(cudaStreamSynchronize(s));
-        const double hn = std::sqrt(std::fmax(nn2.x, 0.0));
-        if (!std::isfinite(hn)) return set_error(AFEM_ENAN, "arnoldi: non-finite Krylov vector");
-        const double2 hv = make_double2(hn, 0.0);
-        AFEM_CUDA_TRY(cudaMemcpyAsync(w.H + j * ldh + (j + 1), &hv, sizeof(double2), cudaMemcpyHostToDevice, s));
-        hlast = hn;
-        if (hn < 1e-14 * beta) {
-            m_used = j + 1;
-            brk = 1;
-            break;
+        const double beta = std::sqrt(beta2_h.x);
+        if (!(beta > 0.0) || !std::isfinite(beta)) return set_error(AFEM_ENAN, "arnoldi: zero or non-finite norm");
+        m_used = mk;
+        brk = 0;
+        double hlast = 0.0;
+        for (int j = 0; j < mk; ++j) {
+            double2* Vj = w.V + j * NV;
+            double2* Wn = w.V + (j + 1) * NV;
+            if (mixed) {
+                if ((rc = g_apply32(m, E, phi, U32, n, Vj, w, Wn, s))) return rc;
+            } else {
+                if ((rc = g_apply(m, E, phi, U, n, Vj, w.z, Wn, w, s))) return rc;
+            }
+            // modified Gram-Schmidt against V_0..V_j
+            for (int i = 0; i <= j; ++i) {
+                const double2* Vprev = i > 0 ? w.V + (i - 1) * NV : nullptr;
+                const double2* hprev = i > 0 ? w.H + j * ldh + (i - 1) : nullptr;
+                AFEM_LAUNCH((mgs_kernel), kRedBlocks, kRedThreads, 0, s, Wn, Vprev, hprev, w.V + i * NV, D.ml,
+                            D.n_interior, n, w.cpartial);
+                AFEM_LAUNCH((sum_partials_kernel), 1, 32, 0, s, w.cpartial, kRedBlocks, w.H + j * ldh + i);
+            }
+            // last update and the norm
+            AFEM_LAUNCH((mgs_kernel), kRedBlocks, kRedThreads, 0, s, Wn, w.V + j * NV, w.H + j * ldh + j, nullptr,
+                        D.ml, D.n_interior, n, w.cpartial);
+            AFEM_LAUNCH((sum_partials_kernel), 1, 32, 0, s, w.cpartial, kRedBlocks, w.beta2);
+            AFEM_CUDA_TRY(cudaGetLastError());
+            double2 nn2;
+            AFEM_CUDA_TRY(cudaMemcpyAsync(&nn2, w.beta2, sizeof(double2), cudaMemcpyDeviceToHost, s));
+            AFEM_CUDA_TRY(cudaStreamSynchronize(s));
+            const double hn = std::sqrt(std::fmax(nn2.x, 0.0));
+            if (!std::isfinite(hn)) return set_error(AFEM_ENAN, "arnoldi: non-finite Krylov vector");
+            const double2 hv = make_double2(hn, 0.0);
+            AFEM_CUDA_TRY(cudaMemcpyAsync(w.H + j * ldh + (j + 1), &hv, sizeof(double2), cudaMemcpyHostToDevice, s));
+            hlast = hn;
+            if (hn < 1e-14 * beta) {
+                m_used = j + 1;
+                brk = 1;
+                break;
+            }
+            AFEM_LAUNCH((cscale_kernel), grid_for(NV), 256, 0, s, Wn, NV, nullptr, 1.0 / hn, 0);
+            AFEM_CUDA_TRY(cudaGetLastError());
         }
-        AFEM_LAUNCH((cscale_kernel), grid_for(NV), 256, 0, s, Wn, NV, nullptr, 1.0 / hn, 0);
+        // substep length: the whole remainder, or shortened until the estimate meets tol
+        double tau = remaining, err = 0.0;
+        for (int tries = 0;; ++tries) {
+            AFEM_LAUNCH((small_expm_kernel), 1, 256, 0, s, w.H, ldh, m_used, tau, w.E);
+            AFEM_CUDA_TRY(cudaGetLastError());
+            AFEM_CUDA_TRY(cudaMemcpyAsync(Eh.data(), w.E, size_t(m_used) * m_used * sizeof(double2),
+                                          cudaMemcpyDeviceToHost, s));
+            AFEM_CUDA_TRY(cudaStreamSynchronize(s));
+            const double2 em = Eh[m_used - 1];
+            err = brk ? 0.0 : beta * hlast * std::hypot(em.x, em.y);
+            if (tol <= 0.0 || brk || err <= tol * beta || tries >= 40) break;
+            const double shrink = 0.9 * std::pow(tol * beta / err, 1.0 / m_used);
+            tau *= std::fmin(0.5, std::fmax(shrink, 0.05));
+        }
+        // phi_out = beta V_m exp(-i tau H_m) e_1
+        std::vector<double2> yh(m_used);
+        for (int i = 0; i < m_used; ++i) yh[i] = make_double2(beta * Eh[i].x, beta * Eh[i].y);
+        AFEM_CUDA_TRY(cudaMemcpyAsync(w.y, yh.data(), m_used * sizeof(double2), cudaMemcpyHostToDevice, s));
+        AFEM_LAUNCH((combine_kernel), grid_for(NV), 256, 0, s, w.V, NV, m_used, w.y, NV, phi_out);
         AFEM_CUDA_TRY(cudaGetLastError());
+        AFEM_CUDA_TRY(cudaStreamSynchronize(s));
+        err_sum += err;
+        ++substeps;
+        remaining = (tau >= remaining) ? 0.0 : remaining - tau;
+        src = phi_out;
     }
-    AFEM_LAUNCH((small_expm_kernel), 1, 256, 0, s, w.H, ldh, m_used, dt, w.E);
-    AFEM_CUDA_TRY(cudaGetLastError());
-    // y = beta exp(-i dt H_m) e_1, formed from the first column on the host
-    std::vector<double2> Eh(size_t(m_used) * m_used);
-    AFEM_CUDA_TRY(cudaMemcpyAsync(Eh.data(), w.E, Eh.size() * sizeof(double2), cudaMemcpyDeviceToHost, s));
-    AFEM_CUDA_TRY(cudaStreamSynchronize(s));
-    std::vector<double2> yh(m_used);
-    for (int i = 0; i < m_used; ++i) yh[i] = make_double2(beta * Eh[i].x, beta * Eh[i].y);
-    AFEM_CUDA_TRY(cudaMemcpyAsync(w.y, yh.data(), m_used * sizeof(double2), cudaMemcpyHostToDevice, s));
-    AFEM_LAUNCH((combine_kernel), grid_for(NV), 256, 0, s, w.V, NV, m_used, w.y, NV, phi_out);
-    AFEM_CUDA_TRY(cudaGetLastError());
-    AFEM_CUDA_TRY(cudaStreamSynchronize(s));
-    if (err_est) {
-        const double2 em = Eh[m_used - 1];
-        *err_est = brk ? 0.0 : beta * hlast * std::hypot(em.x, em.y);
-    }
+    if (err_est) *err_est = err_sum;
     if (m_used_out) *m_used_out = m_used;
     if (breakdown_out) *breakdown_out = brk;
-    (void)NIV;
+    if (substeps_out) *substeps_out = substeps;
     return AFEM_OK;
 }
 

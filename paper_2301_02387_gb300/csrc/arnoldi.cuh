@@ -26,8 +26,8 @@ struct ArnoldiWork {
 int cdot(const double2* A, int na, const double2* B, int nb, const double* w, int64_t rows, int diag,
          double2* partial, double2* out, int sum_all, cudaStream_t s);
 int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double2* U, const float2* U32, int n,
-                 int mk, double dt, int mixed, double2* phi_out, double* err_est, int* m_used_out,
-                 int* breakdown_out, cudaStream_t s);
+                 int mk, double dt, int mixed, double tol, double2* phi_out, double* err_est, int* m_used_out,
+                 int* breakdown_out, int* substeps_out, cudaStream_t s);
 int to_c64(const double2* x, float2* y, int64_t n, cudaStream_t s);
 
 }  // namespace afem

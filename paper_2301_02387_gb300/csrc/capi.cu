@@ -138,7 +138,7 @@ int afem_poisson_batch_ex(afem_mesh* m, const void* phi, int n_orb, void* W, dou
     if (!(rtol > 0.0) || max_it < 0) return set_error(AFEM_EINVAL, "afem_poisson_batch: bad rtol/max_it");
     if (precision == AFEM_PREC_MIXED)
         return poisson_batch_mixed(m, static_cast<const double2*>(phi), n_orb, static_cast<double*>(W), rtol,
-                                   max_it, warm_start, 1e-4, iters_out, outer_out, relres_out,
+                                   max_it, warm_start, 1e-2, iters_out, outer_out, relres_out,
                                    static_cast<cudaStream_t>(stream));
     if (outer_out) *outer_out = 0;
     return poisson_batch(m, static_cast<const double2*>(phi), n_orb, static_cast<double*>(W), rtol, max_it,
@@ -162,8 +162,25 @@ int afem_arnoldi_step_ex(afem_mesh* m, const double* E, const void* phi, const v
     if (krylov_m < 1 || krylov_m > kMaxKrylov) return set_error(AFEM_EINVAL, "afem_arnoldi_step: krylov_m must be 1..16");
     if (phi == phi_out) return set_error(AFEM_EINVAL, "afem_arnoldi_step: phi and phi_out must not alias");
     return arnoldi_step(m, E, static_cast<const double2*>(phi), static_cast<const double2*>(U), nullptr, n_orb,
-                        krylov_m, dt, precision == AFEM_PREC_MIXED, static_cast<double2*>(phi_out), err_est,
-                        m_used, breakdown, static_cast<cudaStream_t>(stream));
+                        krylov_m, dt, precision == AFEM_PREC_MIXED, 0.0, static_cast<double2*>(phi_out), err_est,
+                        m_used, breakdown, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+int afem_arnoldi_propagate(afem_mesh* m, const double* E, const void* phi, const void* U, int n_orb, int krylov_m,
+                           double dt, int precision, double tol, void* phi_out, double* err_est, int* substeps,
+                           void* stream) {
+    if (precision != AFEM_PREC_FP64 && precision != AFEM_PREC_MIXED)
+        return set_error(AFEM_EINVAL, "afem_arnoldi_propagate: unknown precision");
+    if (!m || !phi || !phi_out) return set_error(AFEM_EINVAL, "afem_arnoldi_propagate: null argument");
+    if (m->host_only) return set_error(AFEM_EINVAL, "afem_arnoldi_propagate: mesh was built host-only");
+    if (n_orb < 1 || n_orb > 8) return set_error(AFEM_EINVAL, "afem_arnoldi_propagate: n_orb must be 1..8");
+    if (krylov_m < 1 || krylov_m > kMaxKrylov)
+        return set_error(AFEM_EINVAL, "afem_arnoldi_propagate: krylov_m must be 1..16");
+    if (!(tol > 0.0) || !(dt > 0.0)) return set_error(AFEM_EINVAL, "afem_arnoldi_propagate: tol and dt must be > 0");
+    if (phi == phi_out) return set_error(AFEM_EINVAL, "afem_arnoldi_propagate: phi and phi_out must not alias");
+    return arnoldi_step(m, E, static_cast<const double2*>(phi), static_cast<const double2*>(U), nullptr, n_orb,
+                        krylov_m, dt, precision == AFEM_PREC_MIXED, tol, static_cast<double2*>(phi_out), err_est,
+                        nullptr, nullptr, substeps, static_cast<cudaStream_t>(stream));
 }
 
 int afem_mctdhf_create(afem_mesh* m, int n_orb, int n_alpha, int n_beta, int krylov_m, afem_mctdhf** out) {
@@ -187,6 +204,13 @@ int afem_mctdhf_set_precision(afem_mctdhf* s, int precision) {
     if (precision != AFEM_PREC_FP64 && precision != AFEM_PREC_MIXED)
         return set_error(AFEM_EINVAL, "afem_mctdhf_set_precision: unknown precision");
     mctdhf_set_precision(s, precision);
+    return AFEM_OK;
+}
+
+int afem_mctdhf_set_krylov_tol(afem_mctdhf* s, double tol) {
+    if (!s) return set_error(AFEM_EINVAL, "afem_mctdhf_set_krylov_tol: null argument");
+    if (!(tol >= 0.0)) return set_error(AFEM_EINVAL, "afem_mctdhf_set_krylov_tol: tol must be >= 0");
+    mctdhf_set_krylov_tol(s, tol);
     return AFEM_OK;
 }
 

@@ -476,6 +476,7 @@ struct afem_mctdhf {
     afem_mesh* mesh = nullptr;
     int n = 0, na = 0, nb = 0, krylov_m = 0;
     int precision = AFEM_PREC_FP64;
+    double krylov_tol = 0.0;   // 0: one Krylov step per time step (fixed dimension)
     afem::CiTables ci;
     afem::Workspace ws;
 };
@@ -566,7 +567,7 @@ int mctdhf_step(afem_mctdhf* S, double2* phi, double2* C, double* W, const doubl
     std::vector<double> relres(nn);
     int outer = 0;
     if (mixed_form)
-        rc = poisson_batch_mixed(m, phi, n, W, cg_rtol, cg_max_it, 1, 1e-4, &iters, &outer, relres.data(), s);
+        rc = poisson_batch_mixed(m, phi, n, W, cg_rtol, cg_max_it, 1, 1e-2, &iters, &outer, relres.data(), s);
     else
         rc = poisson_batch(m, phi, n, W, cg_rtol, cg_max_it, 1, &iters, relres.data(), s);
     if (rc && rc != AFEM_ECG_MAXIT) return rc;
@@ -618,8 +619,9 @@ int mctdhf_step(afem_mctdhf* S, double2* phi, double2* C, double* W, const doubl
         U32 = w.U32;
         if ((rc = to_c64(w.U, U32, N * nn, s))) return rc;
     }
-    if ((rc = arnoldi_step(m, E, phi, mixed ? nullptr : w.U, U32, n, S->krylov_m, dt, mixed, w.phi_new, &err,
-                           &m_used, &brk, s)))
+    int substeps = 1;
+    if ((rc = arnoldi_step(m, E, phi, mixed ? nullptr : w.U, U32, n, S->krylov_m, dt, mixed, S->krylov_tol,
+                           w.phi_new, &err, &m_used, &brk, &substeps, s)))
         return rc;
     // commit: phi <- phi_new, C <- exp(-i dt shift) acc
     AFEM_CUDA_TRY(cudaMemcpyAsync(phi, w.phi_new, size_t(N) * n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
@@ -631,6 +633,7 @@ int mctdhf_step(afem_mctdhf* S, double2* phi, double2* C, double* W, const doubl
         info->arnoldi_err = err;
         info->krylov_m_used = m_used;
         info->breakdown = brk;
+        info->krylov_substeps = substeps;
         info->cg_iters = iters;
         double mx = 0.0;
         for (double r : relres) mx = std::max(mx, r);
@@ -680,5 +683,7 @@ void mctdhf_destroy(afem_mctdhf* S) {
 int64_t mctdhf_ci_dim(const afem_mctdhf* S) { return S->ci.dim; }
 
 void mctdhf_set_precision(afem_mctdhf* S, int precision) { S->precision = precision; }
+
+void mctdhf_set_krylov_tol(afem_mctdhf* S, double tol) { S->krylov_tol = tol; }
 
 }  // namespace afem

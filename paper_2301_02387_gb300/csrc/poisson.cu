@@ -738,8 +738,132 @@ __global__ void finalize_residual_kernel(const double* __restrict__ partial, int
 
 int launch_stiffness32(const afem_mesh* m, const float* x, float* y, int nv, int masked, cudaStream_t s);
 
+// Reliable-update form of the mixed solve: one continuous float32 CG per
+// column whose correction d is folded into the float64 W, and whose residual is
+// replaced by the true float64 residual (search direction rescaled), whenever
+// the float32 residual has dropped by `delta` since the last replacement or
+// claims convergence.  Convergence is only ever declared on the float64
+// residual.
+
+// beta, and per column whether a residual replacement is due.
+__global__ void pcg32_beta_ru_kernel(const double* __restrict__ partial, int nblk, int k, PcgState st,
+                                     const double* __restrict__ scale, const double* __restrict__ rr_upd,
+                                     const double* __restrict__ bb64, double rtol2, double delta2,
+                                     int* __restrict__ flags) {
+    __shared__ int need;
+    if (threadIdx.x == 0) need = 0;
+    __syncthreads();
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        double rz = 0.0, rr = 0.0;
+        for (int b = 0; b < nblk; ++b) {
+            rz += partial[int64_t(b) * 2 * k + c];
+            rr += partial[int64_t(b) * 2 * k + k + c];
+        }
+        if (st.active[c]) {
+            st.beta[c] = st.rz[c] != 0.0 ? rz / st.rz[c] : 0.0;
+            st.rz[c] = rz;
+            st.rr[c] = rr;
+            const bool due = !(rr >= delta2 * rr_upd[c]) || scale[c] * scale[c] * rr <= rtol2 * bb64[c];
+            if (due) atomicAdd(&need, 1);
+        } else {
+            st.beta[c] = 0.0;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) flags[1] = need;
+}
+
+// W += s d ; d = 0   (interior rows)
+__global__ void ru_fold_kernel(double* __restrict__ W, float* __restrict__ d, const double* __restrict__ scale,
+                               int64_t n, int k) {
+    const int64_t total = n * k;
+    for (int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; o < total;
+         o += int64_t(gridDim.x) * blockDim.x) {
+        W[o] = fma(scale[o % k], double(d[o]), W[o]);
+        d[o] = 0.0f;
+    }
+}
+
+// rr64, bb64, new scale and activity from the float64 residual partials.
+__global__ void ru_residual_finalize_kernel(const double* __restrict__ partial, int nblk, int k, double rtol2,
+                                            double* __restrict__ rr64, double* __restrict__ bb64,
+                                            double* __restrict__ s_new, int* __restrict__ active,
+                                            int* __restrict__ flags) {
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        double a = 0.0, b = 0.0;
+        for (int q = 0; q < nblk; ++q) {
+            a += partial[int64_t(q) * 2 * k + c];
+            b += partial[int64_t(q) * 2 * k + k + c];
+        }
+        rr64[c] = a;
+        bb64[c] = b;
+        const int act = (b > 0.0 && a > rtol2 * b && isfinite(a)) ? 1 : 0;
+        active[c] = act;
+        s_new[c] = act ? sqrt(a) : 0.0;
+        if (act) atomicAdd(&cnt, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        flags[0] = cnt;
+        flags[1] = 0;
+    }
+}
+
+// r32 = r64 / s_new, z = Dinv r32, p = z (init) or p *= s_old / s_new; partials r.z, r.r.
+__global__ void ru_rescale_kernel(const double* __restrict__ r64, const double* __restrict__ s_old,
+                                  const double* __restrict__ s_new, const float* __restrict__ dinv,
+                                  float* __restrict__ r, float* __restrict__ z, float* __restrict__ p,
+                                  const int* __restrict__ active, int init, int64_t n, int k,
+                                  double* __restrict__ partial) {
+    __shared__ double sh[kRedThreads];
+    const int R = kRedThreads / k, used = R * k;
+    const int tid = threadIdx.x;
+    double arz = 0.0, arr = 0.0;
+    if (tid < used) {
+        const int c = tid % k, r0 = tid / k;
+        const bool act = active[c] != 0;
+        const double inv = act ? 1.0 / s_new[c] : 0.0;
+        const float pf = (act && !init && s_new[c] > 0.0) ? float(s_old[c] / s_new[c]) : 0.0f;
+        for (int64_t i = int64_t(blockIdx.x) * R + r0; i < n; i += int64_t(gridDim.x) * R) {
+            const int64_t o = i * k + c;
+            const float ri = float(r64[o] * inv);
+            const float zi = dinv[i] * ri;
+            r[o] = ri;
+            z[o] = zi;
+            p[o] = init ? zi : (act ? p[o] * pf : 0.0f);
+            arz += double(ri) * double(zi);
+            arr += double(ri) * double(ri);
+        }
+    }
+    double* out = partial + int64_t(blockIdx.x) * 2 * k;
+    sh[tid] = arz;
+    reduce_columns(sh, k, R, out);
+    __syncthreads();
+    sh[tid] = arr;
+    reduce_columns(sh, k, R, out + k);
+}
+
+__global__ void ru_finalize_kernel(const double* __restrict__ partial, int nblk, int k, PcgState st,
+                                   double* __restrict__ rr_upd, double* __restrict__ s_old,
+                                   const double* __restrict__ s_new) {
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        double rz = 0.0, rr = 0.0;
+        for (int q = 0; q < nblk; ++q) {
+            rz += partial[int64_t(q) * 2 * k + c];
+            rr += partial[int64_t(q) * 2 * k + k + c];
+        }
+        st.rz[c] = rz;
+        st.rr[c] = rr;
+        rr_upd[c] = rr;
+        s_old[c] = s_new[c];
+    }
+}
+
 int poisson_batch_mixed(afem_mesh* m, const double2* phi, int n, double* W, double rtol, int max_it, int warm,
-                        double inner_rtol, int* iters_out, int* outer_out, double* relres_out, cudaStream_t s) {
+                        double delta, int* iters_out, int* outer_out, double* relres_out, cudaStream_t s) {
     const DeviceMesh& D = m->dev;
     const int k = n * n;
     const int64_t N = D.n_master, Ni = D.n_interior;
@@ -747,8 +871,8 @@ int poisson_batch_mixed(afem_mesh* m, const double2* phi, int n, double* W, doub
     const size_t NK = size_t(N) * k;
     PoissonWork w{};
     float *r32, *z32, *p32, *Ap32, *d32;
-    double *scale, *rr64, *bb64;
-    int* nact64;
+    double *s_old, *s_new, *rr64, *bb64, *rr_upd;
+    int* flags;
     auto carve = [&](Carver& cv) {
         w.b = cv.take<double>(NK);
         w.r = cv.take<double>(NK);
@@ -770,10 +894,12 @@ int poisson_batch_mixed(afem_mesh* m, const double2* phi, int n, double* W, doub
         w.rr = cv.take<double>(k);
         w.active = cv.take<int>(k);
         w.n_active = cv.take<int>(1);
-        scale = cv.take<double>(k);
+        s_old = cv.take<double>(k);
+        s_new = cv.take<double>(k);
         rr64 = cv.take<double>(k);
         bb64 = cv.take<double>(k);
-        nact64 = cv.take<int>(1);
+        rr_upd = cv.take<double>(k);
+        flags = cv.take<int>(2);
     };
     Carver measure(nullptr);
     carve(measure);
@@ -781,54 +907,62 @@ int poisson_batch_mixed(afem_mesh* m, const double2* phi, int n, double* W, doub
     if (rc) return rc;
     Carver cv(m->ws_poisson.ptr);
     carve(cv);
-    PcgState st{w.alpha, w.beta, w.rz, w.bb, w.rr, w.active, w.n_active, inner_rtol * inner_rtol};
+    PcgState st{w.alpha, w.beta, w.rz, w.bb, w.rr, w.active, w.n_active, 0.0};
+    const double rtol2 = rtol * rtol, delta2 = delta * delta;
 
     if (!warm) AFEM_CUDA_TRY(cudaMemsetAsync(W, 0, NK * sizeof(double), s));
     if ((rc = poisson_rhs_bc(m, phi, n, W, w.b, w.qpart, w.q, s))) return rc;
     AFEM_LAUNCH((surface_only_kernel), grid_for(int64_t(NK)), 256, 0, s, W, w.z, Ni, N, k);
     if ((rc = launch_stiffness(m, w.z, w.t, k, 0, s))) return rc;   // t = A g_ext (FP64)
-    int total_inner = 0, outer = 0, n_active = 1;
-    for (;;) {
-        if ((rc = launch_stiffness(m, W, w.Ap, k, 1, s))) return rc;   // FP64 residual
+    AFEM_CUDA_TRY(cudaMemsetAsync(d32, 0, NK * sizeof(float), s));
+
+    int flags_h[2] = {0, 0};
+    int replacements = 0;
+    // float64 residual of the current W, and the float32 state built from it
+    auto replace = [&](int init) -> int {
+        int r_;
+        if ((r_ = launch_stiffness(m, W, w.Ap, k, 1, s))) return r_;
         AFEM_LAUNCH((residual64_kernel), nblk, kRedThreads, 0, s, w.b, w.t, w.Ap, w.r, Ni, k, w.partial);
-        AFEM_LAUNCH((finalize_residual_kernel), 1, 64, 0, s, w.partial, nblk, k, rtol * rtol, rr64, bb64, scale,
-                    nact64);
+        AFEM_LAUNCH((ru_residual_finalize_kernel), 1, 64, 0, s, w.partial, nblk, k, rtol2, rr64, bb64, s_new,
+                    w.active, flags);
+        AFEM_LAUNCH((ru_rescale_kernel), nblk, kRedThreads, 0, s, w.r, s_old, s_new, D.stiff_dinv32, r32, z32, p32,
+                    w.active, init, Ni, k, w.partial);
+        AFEM_LAUNCH((ru_finalize_kernel), 1, 64, 0, s, w.partial, nblk, k, st, rr_upd, s_old, s_new);
         AFEM_CUDA_TRY(cudaGetLastError());
-        AFEM_CUDA_TRY(cudaMemcpyAsync(&n_active, nact64, sizeof(int), cudaMemcpyDeviceToHost, s));
+        AFEM_CUDA_TRY(cudaMemcpyAsync(flags_h, flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
         AFEM_CUDA_TRY(cudaStreamSynchronize(s));
-        if (n_active == 0 || total_inner >= max_it || outer >= 30) break;
-        ++outer;
-        // inner FP32 PCG on the scaled residual
-        AFEM_LAUNCH((pcg32_init_kernel), nblk, kRedThreads, 0, s, w.r, scale, D.stiff_dinv32, r32, z32, p32, d32,
-                    Ni, k, w.partial);
-        AFEM_LAUNCH((pcg_init_finalize_kernel), 1, 64, 0, s, w.partial, nblk, k, st);
-        int it = 0, inner_active = 1;
-        while (total_inner < max_it) {
-            if (it % 4 == 0) {
-                AFEM_CUDA_TRY(cudaMemcpyAsync(&inner_active, w.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
-                AFEM_CUDA_TRY(cudaStreamSynchronize(s));
-                if (inner_active == 0) break;
-            }
-            if ((rc = launch_stiffness32(m, p32, Ap32, k, 1, s))) return rc;
-            AFEM_LAUNCH((col_dot32_kernel), nblk, kRedThreads, 0, s, p32, Ap32, Ni, k, w.partial);
-            AFEM_LAUNCH((pcg_alpha_kernel), 1, 64, 0, s, w.partial, nblk, k, st);
-            AFEM_LAUNCH((pcg32_update_kernel), nblk, kRedThreads, 0, s, d32, r32, z32, p32, Ap32, D.stiff_dinv32,
-                        Ni, k, st, w.partial);
-            AFEM_LAUNCH((pcg_beta_kernel), 1, 64, 0, s, w.partial, nblk, k, st);
-            AFEM_LAUNCH((pcg32_p_kernel), grid_for(Ni * k), 256, 0, s, p32, z32, Ni, k, st);
-            AFEM_CUDA_TRY(cudaGetLastError());
-            ++it;
-            ++total_inner;
-        }
-        AFEM_LAUNCH((refine_update_kernel), grid_for(Ni * k), 256, 0, s, W, d32, scale, Ni, k);
+        ++replacements;
+        return AFEM_OK;
+    };
+    if ((rc = replace(1))) return rc;
+    int it = 0;
+    const int check_every = 8;
+    while (flags_h[0] > 0 && it < max_it) {
+        if ((rc = launch_stiffness32(m, p32, Ap32, k, 1, s))) return rc;
+        AFEM_LAUNCH((col_dot32_kernel), nblk, kRedThreads, 0, s, p32, Ap32, Ni, k, w.partial);
+        AFEM_LAUNCH((pcg_alpha_kernel), 1, 64, 0, s, w.partial, nblk, k, st);
+        AFEM_LAUNCH((pcg32_update_kernel), nblk, kRedThreads, 0, s, d32, r32, z32, p32, Ap32, D.stiff_dinv32, Ni, k,
+                    st, w.partial);
+        AFEM_LAUNCH((pcg32_beta_ru_kernel), 1, 64, 0, s, w.partial, nblk, k, st, s_old, rr_upd, bb64, rtol2, delta2,
+                    flags);
+        AFEM_LAUNCH((pcg32_p_kernel), grid_for(Ni * k), 256, 0, s, p32, z32, Ni, k, st);
         AFEM_CUDA_TRY(cudaGetLastError());
+        ++it;
+        if (it % check_every == 0 || it >= max_it) {
+            AFEM_CUDA_TRY(cudaMemcpyAsync(flags_h, flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+            AFEM_CUDA_TRY(cudaStreamSynchronize(s));
+            if (flags_h[1] > 0 || it >= max_it) {
+                AFEM_LAUNCH((ru_fold_kernel), grid_for(Ni * k), 256, 0, s, W, d32, s_old, Ni, k);
+                if ((rc = replace(0))) return rc;
+            }
+        }
     }
+    if (iters_out) *iters_out = it;
+    if (outer_out) *outer_out = replacements;
     std::vector<double> rr(k), bb(k);
     AFEM_CUDA_TRY(cudaMemcpyAsync(rr.data(), rr64, k * sizeof(double), cudaMemcpyDeviceToHost, s));
     AFEM_CUDA_TRY(cudaMemcpyAsync(bb.data(), bb64, k * sizeof(double), cudaMemcpyDeviceToHost, s));
     AFEM_CUDA_TRY(cudaStreamSynchronize(s));
-    if (iters_out) *iters_out = total_inner;
-    if (outer_out) *outer_out = outer;
     bool finite = true;
     for (int c = 0; c < k; ++c) {
         const double rel = bb[c] > 0.0 ? std::sqrt(rr[c] / bb[c]) : 0.0;
@@ -836,8 +970,8 @@ int poisson_batch_mixed(afem_mesh* m, const double2* phi, int n, double* W, doub
         if (relres_out) relres_out[c] = rel;
     }
     if (!finite) return set_error(AFEM_ENAN, "afem_poisson_batch: non-finite residual");
-    if (n_active > 0)
-        return set_error(AFEM_ECG_MAXIT, "afem_poisson_batch: refinement reached max_it before rtol");
+    if (flags_h[0] > 0)
+        return set_error(AFEM_ECG_MAXIT, "afem_poisson_batch: mixed CG reached max_it before rtol");
     return AFEM_OK;
 }
 

@@ -75,3 +75,40 @@ def test_arnoldi_eigenvector_breakdown():
     out, err, mu, brk = pkg.arnoldi_step(gm, phi, None, 8, 0.05)
     assert brk and mu == 1 and err == 0.0
     np.testing.assert_allclose(out.cpu().numpy(), phi_o[perm], atol=1e-10)
+
+
+@pytest.mark.parametrize("precision_name", ["fp64", "mixed"])
+def test_arnoldi_propagate_substeps_parity(precision_name):
+    """Error-controlled substepping: same substep count as the oracle; FP64 result
+    within 1e-10, the mixed form within 1e-6."""
+    import torch
+    import paper_2301_02387_gb300 as pkg
+    case = (-6.0, 6.0, 2, 3, [((0.0, 0.0, 0.7), 1.0, 2), ((0.0, 0.0, -0.7), 1.0, 2)], 2.0)
+    gm = pkg.Mesh(*case)
+    om = omesh.Mesh(*case)
+    op = fem.Operators(om)
+    X, _, _ = gm.tables()
+    perm = coord_permutation(X, om.Xm)
+    n = 2
+    interior = ~om.boundary
+    phi_o = inputs.lowdin(inputs.molecular_orbitals(om.Xm, interior, case[4], n), op.ML)
+    U_o = _fields(om.Xm, n, 8)
+    E = (0.0, 0.0, 0.02)
+    sim = mctdhf.MCTDHF.__new__(mctdhf.MCTDHF)
+    sim.ops, sim.mesh, sim.n = op, om, n
+    sim.interior = interior.astype(np.float64)
+    ref, err, sub = krylov.arnoldi_propagate(lambda v: sim.G_apply(v, phi_o, U_o, E), phi_o, sim.inner, 6, 0.05,
+                                             1e-9)
+    assert sub > 1
+    phi = torch.from_numpy(np.ascontiguousarray(phi_o[perm])).cuda()
+    U = torch.from_numpy(np.ascontiguousarray(U_o.transpose(2, 0, 1)[perm])).cuda()
+    prec = pkg.PREC_FP64 if precision_name == "fp64" else pkg.PREC_MIXED
+    out, err_g, sub_g = pkg.arnoldi_propagate(gm, phi, U, 6, 0.05, 1e-9, E=E, precision=prec)
+    torch.cuda.synchronize()
+    rel = np.linalg.norm(out.cpu().numpy() - ref[perm]) / np.linalg.norm(ref)
+    if precision_name == "fp64":
+        assert sub_g == sub
+        assert rel < 1e-10
+    else:
+        assert abs(sub_g - sub) <= 1
+        assert rel < 1e-6

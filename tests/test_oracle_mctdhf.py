@@ -188,3 +188,22 @@ def test_h2_like_two_orbital_invariants(tiny):
         drift.append(np.abs(S - np.eye(2)).max())
     # the frozen-operator step is first order: orthonormality drift ~ dt
     assert 0.4 < drift[1] / drift[0] < 0.6 and drift[0] < 2e-3
+
+
+def test_arnoldi_propagate_meets_tolerance_on_stiff_operator():
+    """A stiff Hermitian operator (eigenvalues up to 400) over dt = 0.05 with m = 6:
+    one Krylov step is far off, substeps controlled by the estimate land within
+    a small multiple of tol * substeps of the dense exponential."""
+    rng = np.random.default_rng(5)
+    n = 80
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = np.concatenate([rng.uniform(-1, 1, n - 10), rng.uniform(200, 400, 10)])
+    G = (Q * lam) @ Q.T
+    phi = rng.standard_normal(n) + 0j
+    inner = lambda u, v: np.vdot(u, v)
+    ref = scipy.linalg.expm(-1j * 0.05 * G) @ phi
+    one, est1, *_ = krylov.arnoldi_expm(lambda v: G @ v, phi, inner, 6, 0.05)
+    assert np.linalg.norm(one - ref) > 1e-3 * np.linalg.norm(ref)
+    out, est, sub = krylov.arnoldi_propagate(lambda v: G @ v, phi, inner, 6, 0.05, 1e-10)
+    assert sub > 1
+    assert np.linalg.norm(out - ref) < 50 * 1e-10 * sub * np.linalg.norm(phi)
