@@ -96,7 +96,8 @@ def setup_state(pkg, inputs, torch, w):
     mesh = pkg.Mesh(*inputs.mesh_args(WORKLOAD))
     X, ml, _ = mesh.tables()
     interior = np.arange(mesh.N) < mesh.n_interior
-    phi0 = inputs.lowdin(inputs.molecular_orbitals(X, interior, w["nuclei"], w["n_orb"]), ml)
+    # smooth seeded orbitals: the H2 workload specifies no per-point phase noise
+    phi0 = inputs.lowdin(inputs.molecular_orbitals(X, interior, w["nuclei"], w["n_orb"], phase_noise=0.0), ml)
     C0 = inputs.initial_ci(w["n_orb"], w["n_alpha"], w["n_beta"])
     solver = pkg.MCTDHF(mesh, w["n_orb"], w["n_alpha"], w["n_beta"], w["m"])
     return mesh, solver, phi0, C0

@@ -57,6 +57,45 @@ __global__ void cdot_kernel(const double2* __restrict__ A, int na, const TB* __r
     }
 }
 
+// cdot with the block sums finished in the same launch (no sum_all form):
+// partial rows of 2*kout doubles (re, im interleaved); the last block writes out[kout].
+template <typename TB>
+__global__ void cdot_fused_kernel(const double2* __restrict__ A, int na, const TB* __restrict__ B, int nb,
+                                  const double* __restrict__ w, int64_t n_rows, int diag, double* __restrict__ partial,
+                                  unsigned* __restrict__ counter, double2* __restrict__ out) {
+    __shared__ double sx[kRedThreads], sy[kRedThreads];
+    const int kout = diag ? na : na * nb;
+    const int R = kRedThreads / kout, used = R * kout;
+    const int t = threadIdx.x;
+    double ax = 0.0, ay = 0.0;
+    if (t < used) {
+        const int o = t % kout, r = t / kout;
+        const int ia = diag ? o : o / nb;
+        const int ib = diag ? o : o - ia * nb;
+        for (int64_t k = int64_t(blockIdx.x) * R + r; k < n_rows; k += int64_t(gridDim.x) * R) {
+            const double2 u = A[k * na + ia];
+            const double2 v = to_d2(B[k * nb + ib]);
+            const double wk = w ? w[k] : 1.0;
+            ax = fma(wk, fma(u.x, v.x, u.y * v.y), ax);
+            ay = fma(wk, fma(u.x, v.y, -u.y * v.x), ay);
+        }
+    }
+    sx[t] = ax;
+    sy[t] = ay;
+    __syncthreads();
+    for (int o = t; o < kout; o += blockDim.x) {
+        double x = 0.0, y = 0.0;
+        for (int r = 0; r < R; ++r) {
+            x += sx[o + kout * r];
+            y += sy[o + kout * r];
+        }
+        partial[int64_t(blockIdx.x) * 2 * kout + 2 * o] = x;
+        partial[int64_t(blockIdx.x) * 2 * kout + 2 * o + 1] = y;
+    }
+    if (!last_block_sum(partial, 2 * kout, counter, sx)) return;
+    for (int o = t; o < kout; o += blockDim.x) out[o] = make_double2(sx[2 * o], sx[2 * o + 1]);
+}
+
 // out[o] = sum_b partial[b][o]; if sum_all, out[0] = sum over o as well.
 __global__ void cfinalize_kernel(const double2* __restrict__ partial, int nblk, int kout, int sum_all,
                                  double2* __restrict__ out) {
@@ -146,6 +185,48 @@ __global__ void mgs_kernel(double2* __restrict__ w, const double2* __restrict__ 
         }
         partial[blockIdx.x] = make_double2(x, y);
     }
+}
+
+// The MGS step above with its reduction finished in the same launch: block
+// partials (re, im) go to partial[2 * block], the last block writes *out.
+__global__ void mgs_fused_kernel(double2* __restrict__ w, const double2* __restrict__ Vprev,
+                                 const double2* __restrict__ hprev, const double2* __restrict__ Vi,
+                                 const double* __restrict__ ml, int64_t n_int, int n, double* __restrict__ partial,
+                                 unsigned* __restrict__ counter, double2* __restrict__ out) {
+    __shared__ double sx[kRedThreads], sy[kRedThreads];
+    const int64_t total = n_int * n;
+    double ax = 0.0, ay = 0.0;
+    const double2 h = Vprev ? *hprev : make_double2(0.0, 0.0);
+    for (int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; o < total;
+         o += int64_t(gridDim.x) * blockDim.x) {
+        double2 x = w[o];
+        if (Vprev) {
+            const double2 v = Vprev[o];
+            x.x -= h.x * v.x - h.y * v.y;
+            x.y -= h.x * v.y + h.y * v.x;
+            w[o] = x;
+        }
+        const double2 u = Vi ? Vi[o] : x;
+        const double m = ml[o / n];
+        ax = fma(m, fma(u.x, x.x, u.y * x.y), ax);
+        ay = fma(m, fma(u.x, x.y, -u.y * x.x), ay);
+    }
+    sx[threadIdx.x] = ax;
+    sy[threadIdx.x] = ay;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) {
+            sx[threadIdx.x] += sx[threadIdx.x + st];
+            sy[threadIdx.x] += sy[threadIdx.x + st];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = sx[0];
+        partial[2 * blockIdx.x + 1] = sy[0];
+    }
+    if (!last_block_sum(partial, 2, counter, sx)) return;
+    if (threadIdx.x == 0) *out = make_double2(sx[0], sx[1]);
 }
 
 // Sum block partials into *out (one thread, fixed order).
@@ -271,17 +352,16 @@ int launch_g_cell(const afem_mesh* m, const double* E, const double2* v, const d
 
 template <typename TB>
 int cdot_t(const double2* A, int na, const TB* B, int nb, const double* w, int64_t rows, int diag,
-           double2* partial, double2* out, int sum_all, cudaStream_t s) {
-    const int kout = diag ? na : na * nb;
-    AFEM_LAUNCH((cdot_kernel<TB>), kRedBlocks, kRedThreads, 0, s, A, na, B, nb, w, rows, diag, partial);
-    AFEM_LAUNCH((cfinalize_kernel), 1, 256, 0, s, partial, kRedBlocks, kout, sum_all, out);
+           double2* partial, double2* out, unsigned* counter, cudaStream_t s) {
+    AFEM_LAUNCH((cdot_fused_kernel<TB>), kRedBlocks, kRedThreads, 0, s, A, na, B, nb, w, rows, diag,
+                reinterpret_cast<double*>(partial), counter, out);
     AFEM_CUDA_TRY(cudaGetLastError());
     return AFEM_OK;
 }
 
 int cdot(const double2* A, int na, const double2* B, int nb, const double* w, int64_t rows, int diag,
-         double2* partial, double2* out, int sum_all, cudaStream_t s) {
-    return cdot_t<double2>(A, na, B, nb, w, rows, diag, partial, out, sum_all, s);
+         double2* partial, double2* out, unsigned* counter, cudaStream_t s) {
+    return cdot_t<double2>(A, na, B, nb, w, rows, diag, partial, out, counter, s);
 }
 
 __global__ void to_c64_kernel(const double2* __restrict__ x, float2* __restrict__ y, int64_t n) {
@@ -306,7 +386,7 @@ int g_apply32(afem_mesh* m, const double* E, const double2* phi, const float2* U
     int rc = to_c64(v, w.v32, D.n_master * n, s);
     if (rc) return rc;
     if ((rc = launch_g_cell32(m, E, w.v32, U32, w.z32, n, s))) return rc;
-    if ((rc = cdot_t<float2>(phi, n, w.z32, n, nullptr, D.n_interior, 0, w.cpartial, w.S, 0, s))) return rc;
+    if ((rc = cdot_t<float2>(phi, n, w.z32, n, nullptr, D.n_interior, 0, w.cpartial, w.S, w.counters, s))) return rc;
     AFEM_LAUNCH((project_kernel<float2>), grid_for(D.n_master * n), 256, 0, s, w.z32, phi, w.S, D.ml_inv,
                 D.n_interior, D.n_master, n, out);
     AFEM_CUDA_TRY(cudaGetLastError());
@@ -319,7 +399,7 @@ int g_apply(afem_mesh* m, const double* E, const double2* phi, const double2* U,
     int rc = launch_g_cell(m, E, v, U, z, n, s);
     if (rc) return rc;
     // S[j][p] = phi_j^H z_p  (equals phi_j^H M_L y_p)
-    if ((rc = cdot(phi, n, z, n, nullptr, D.n_interior, 0, w.cpartial, w.S, 0, s))) return rc;
+    if ((rc = cdot(phi, n, z, n, nullptr, D.n_interior, 0, w.cpartial, w.S, w.counters, s))) return rc;
     AFEM_LAUNCH((project_kernel<double2>), grid_for(D.n_master * n), 256, 0, s, z, phi, w.S, D.ml_inv, D.n_interior, D.n_master, n,
                                                             out);
     AFEM_CUDA_TRY(cudaGetLastError());
@@ -340,6 +420,7 @@ int arnoldi_reserve(afem_mesh* m, int n, int mk, ArnoldiWork& w) {
         w.v32 = cv.take<float2>(NV);
         w.z32 = cv.take<float2>(NV);
         w.U32 = cv.take<float2>(NV * n);
+        w.counters = cv.take<unsigned>(4);
     };
     Carver measure(nullptr);
     carve(measure);
@@ -368,6 +449,7 @@ int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double
         if ((rc = to_c64(U, w.U32, D.n_master * n * n, s))) return rc;
         U32 = w.U32;
     }
+    AFEM_CUDA_TRY(cudaMemsetAsync(w.counters, 0, 4 * sizeof(unsigned), s));
     const int64_t NV = w.stride;
     const int ldh = kMaxKrylov + 1;
     const double2* src = phi;
@@ -379,9 +461,8 @@ int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double
         if (substeps >= 4096) return set_error(AFEM_EINVAL, "arnoldi: more than 4096 substeps (tolerance too tight)");
         AFEM_CUDA_TRY(cudaMemsetAsync(w.H, 0, sizeof(double2) * ldh * kMaxKrylov, s));
         // beta^2 = <src, src>_M ; V_0 = src / beta
-        AFEM_LAUNCH((mgs_kernel), kRedBlocks, kRedThreads, 0, s, const_cast<double2*>(src), nullptr, nullptr,
-                    nullptr, D.ml, D.n_interior, n, w.cpartial);
-        AFEM_LAUNCH((sum_partials_kernel), 1, 32, 0, s, w.cpartial, kRedBlocks, w.beta2);
+        AFEM_LAUNCH((mgs_fused_kernel), kRedBlocks, kRedThreads, 0, s, const_cast<double2*>(src), nullptr, nullptr,
+                    nullptr, D.ml, D.n_interior, n, reinterpret_cast<double*>(w.cpartial), w.counters + 1, w.beta2);
         AFEM_CUDA_TRY(cudaMemcpyAsync(w.V, src, NV * sizeof(double2), cudaMemcpyDeviceToDevice, s));
         AFEM_LAUNCH((cscale_kernel), grid_for(NV), 256, 0, s, w.V, NV, w.beta2, 1.0, 1);
         AFEM_CUDA_TRY(cudaGetLastError());
@@ -405,14 +486,14 @@ int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double
             for (int i = 0; i <= j; ++i) {
                 const double2* Vprev = i > 0 ? w.V + (i - 1) * NV : nullptr;
                 const double2* hprev = i > 0 ? w.H + j * ldh + (i - 1) : nullptr;
-                AFEM_LAUNCH((mgs_kernel), kRedBlocks, kRedThreads, 0, s, Wn, Vprev, hprev, w.V + i * NV, D.ml,
-                            D.n_interior, n, w.cpartial);
-                AFEM_LAUNCH((sum_partials_kernel), 1, 32, 0, s, w.cpartial, kRedBlocks, w.H + j * ldh + i);
+                AFEM_LAUNCH((mgs_fused_kernel), kRedBlocks, kRedThreads, 0, s, Wn, Vprev, hprev, w.V + i * NV, D.ml,
+                            D.n_interior, n, reinterpret_cast<double*>(w.cpartial), w.counters + 1,
+                            w.H + j * ldh + i);
             }
             // last update and the norm
-            AFEM_LAUNCH((mgs_kernel), kRedBlocks, kRedThreads, 0, s, Wn, w.V + j * NV, w.H + j * ldh + j, nullptr,
-                        D.ml, D.n_interior, n, w.cpartial);
-            AFEM_LAUNCH((sum_partials_kernel), 1, 32, 0, s, w.cpartial, kRedBlocks, w.beta2);
+            AFEM_LAUNCH((mgs_fused_kernel), kRedBlocks, kRedThreads, 0, s, Wn, w.V + j * NV, w.H + j * ldh + j,
+                        nullptr, D.ml, D.n_interior, n, reinterpret_cast<double*>(w.cpartial), w.counters + 1,
+                        w.beta2);
             AFEM_CUDA_TRY(cudaGetLastError());
             double2 nn2;
             AFEM_CUDA_TRY(cudaMemcpyAsync(&nn2, w.beta2, sizeof(double2), cudaMemcpyDeviceToHost, s));

@@ -20,11 +20,12 @@ struct ArnoldiWork {
     float2* v32;         // [N][n] complex64 copy of the vector G is applied to (mixed form)
     float2* z32;         // [N][n] complex64 cell-pass output (mixed form)
     float2* U32;         // [N][n][n] complex64 mean-field fields (mixed form)
+    unsigned* counters;  // last-block reduction counters (zeroed per call)
     int64_t stride;      // N * n
 };
 
 int cdot(const double2* A, int na, const double2* B, int nb, const double* w, int64_t rows, int diag,
-         double2* partial, double2* out, int sum_all, cudaStream_t s);
+         double2* partial, double2* out, unsigned* counter, cudaStream_t s);
 int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double2* U, const float2* U32, int n,
                  int mk, double dt, int mixed, double tol, double2* phi_out, double* err_est, int* m_used_out,
                  int* breakdown_out, int* substeps_out, cudaStream_t s);

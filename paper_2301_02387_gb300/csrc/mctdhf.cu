@@ -489,6 +489,7 @@ struct StepWork {
     double *energy, *shift;
     int* status;
     float2* U32;
+    unsigned* counters;
 };
 
 static void carve_step(Carver& cv, StepWork& w, int64_t N, int n, int64_t dim, bool mixed) {
@@ -515,6 +516,7 @@ static void carve_step(Carver& cv, StepWork& w, int64_t N, int n, int64_t dim, b
     w.shift = cv.take<double>(1);
     w.status = cv.take<int>(1);
     w.U32 = mixed ? cv.take<float2>(size_t(N) * nn) : nullptr;
+    w.counters = cv.take<unsigned>(4);
 }
 
 static void finalize_cpartials(const double2* partial, int nblk, int k, double2* out, cudaStream_t s);
@@ -574,7 +576,8 @@ int mctdhf_step(afem_mctdhf* S, double2* phi, double2* C, double* W, const doubl
     const int cg_rc = rc;
     // 2. integrals: h_pq = phi_p^H M_L (M_L^-1 H1~ phi_q);  (pq|rs)
     if ((rc = launch_op_apply(m, AFEM_OP_H1, E, phi, w.y, n, s))) return rc;
-    if ((rc = cdot(phi, n, w.y, n, D.ml, D.n_interior, 0, w.cpart, w.h, 0, s))) return rc;
+    AFEM_CUDA_TRY(cudaMemsetAsync(w.counters, 0, 4 * sizeof(unsigned), s));
+    if ((rc = cdot(phi, n, w.y, n, D.ml, D.n_interior, 0, w.cpart, w.h, w.counters, s))) return rc;
     IntArgs ia{phi, W, n, N, D.n_interior, D.n_hanging, D.mf_master, D.mf_hang, D.hang_ptr, D.hang_master, D.hang_w};
     const size_t ismem = size_t(kIntTile) * nn * (sizeof(double2) + sizeof(double)) + size_t(nn) * nn * sizeof(double2);
     AFEM_CUDA_TRY(cudaFuncSetAttribute(integrals_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ismem)));

@@ -398,6 +398,104 @@ __global__ void pcg_p_kernel(double* __restrict__ p, const double* __restrict__ 
     }
 }
 
+// ---- fused CG kernels: block partials + last-block finalize (alpha or beta)
+// p.Ap per column; the last block sets alpha = rz / pAp for active columns.
+template <typename T>
+__global__ void dot_alpha_kernel(const T* __restrict__ p, const T* __restrict__ Ap, int64_t n, int k,
+                                 double* __restrict__ partial, unsigned* __restrict__ counter, PcgState st) {
+    __shared__ double s[kRedThreads];
+    const int R = kRedThreads / k, used = R * k;
+    const int t = threadIdx.x;
+    double acc = 0.0;
+    if (t < used) {
+        const int c = t % k, r = t / k;
+        for (int64_t i = int64_t(blockIdx.x) * R + r; i < n; i += int64_t(gridDim.x) * R)
+            acc += double(p[i * k + c]) * double(Ap[i * k + c]);
+    }
+    s[t] = acc;
+    reduce_columns(s, k, R, partial + int64_t(blockIdx.x) * k);
+    if (!last_block_sum(partial, k, counter, s)) return;
+    for (int c = t; c < k; c += blockDim.x) {
+        const double pAp = s[c];
+        st.alpha[c] = (st.active[c] && pAp > 0.0) ? st.rz[c] / pAp : 0.0;
+    }
+}
+
+// x += alpha p, r -= alpha Ap; partials of r.(Dinv r) and r.r; the last block
+// sets beta, rz, rr and, with reliable updates (rr_upd != null), the number of
+// columns due for a float64 residual replacement in flags[1]; without them it
+// retires converged columns (rr <= rtol2 bb) and counts the active ones in
+// *st.n_active.
+template <typename T>
+__global__ void update_beta_kernel(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
+                                   const T* __restrict__ Ap, const T* __restrict__ dinv, int64_t n, int k, PcgState st,
+                                   double* __restrict__ partial, unsigned* __restrict__ counter,
+                                   const double* __restrict__ scale, const double* __restrict__ rr_upd,
+                                   const double* __restrict__ bb64, double rtol2, double delta2,
+                                   int* __restrict__ flags) {
+    __shared__ double s[kRedThreads];
+    const int R = kRedThreads / k, used = R * k;
+    const int tid = threadIdx.x;
+    double arz = 0.0, arr = 0.0;
+    if (tid < used) {
+        const int c = tid % k, r0 = tid / k;
+        const T al = T(st.alpha[c]);
+        for (int64_t i = int64_t(blockIdx.x) * R + r0; i < n; i += int64_t(gridDim.x) * R) {
+            const int64_t o = i * k + c;
+            x[o] = x[o] + al * p[o];
+            const T ri = r[o] - al * Ap[o];
+            r[o] = ri;
+            const double rd = double(ri);
+            arz += rd * double(dinv[i] * ri);
+            arr += rd * rd;
+        }
+    }
+    double* out = partial + int64_t(blockIdx.x) * 2 * k;
+    s[tid] = arz;
+    reduce_columns(s, k, R, out);
+    __syncthreads();
+    s[tid] = arr;
+    reduce_columns(s, k, R, out + k);
+    if (!last_block_sum(partial, 2 * k, counter, s)) return;
+    __shared__ int s_cnt;
+    if (tid == 0) s_cnt = 0;
+    __syncthreads();
+    for (int c = tid; c < k; c += blockDim.x) {
+        const double rz = s[c], rr = s[k + c];
+        if (st.active[c]) {
+            st.beta[c] = st.rz[c] != 0.0 ? rz / st.rz[c] : 0.0;
+            st.rz[c] = rz;
+            st.rr[c] = rr;
+            if (rr_upd) {
+                const bool due = !(rr >= delta2 * rr_upd[c]) || scale[c] * scale[c] * rr <= rtol2 * bb64[c];
+                if (due) atomicAdd(&s_cnt, 1);
+            } else {
+                if (!(rr > st.rtol2 * st.bb[c]) || !isfinite(rr)) st.active[c] = 0;
+                if (st.active[c]) atomicAdd(&s_cnt, 1);
+            }
+        } else {
+            st.beta[c] = 0.0;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        if (rr_upd) flags[1] = s_cnt;
+        else *st.n_active = s_cnt;
+    }
+}
+
+// p = Dinv r + beta p (active columns)
+template <typename T>
+__global__ void p_update_kernel(T* __restrict__ p, const T* __restrict__ r, const T* __restrict__ dinv, int64_t n,
+                                int k, PcgState st) {
+    const int64_t total = n * k;
+    for (int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; o < total;
+         o += int64_t(gridDim.x) * blockDim.x) {
+        const int c = int(o % k);
+        if (st.active[c]) p[o] = dinv[o / k] * r[o] + T(st.beta[c]) * p[o];
+    }
+}
+
 // Copy the surface rows of x into g_ext (interior rows zero).
 __global__ void surface_only_kernel(const double* __restrict__ x, double* __restrict__ gext, int64_t n_int,
                                     int64_t N, int k) {
@@ -412,6 +510,7 @@ struct PoissonWork {
     double *b, *r, *z, *p, *Ap, *t, *partial, *qpart, *q;
     double *alpha, *beta, *rz, *bb, *rr;
     int *active, *n_active;
+    unsigned* counters;   // last-block reduction counters (zeroed per call)
 };
 
 int poisson_rhs_bc(afem_mesh* m, const double2* phi, int n, double* W, double* b, double* qpart, double* q,
@@ -482,6 +581,7 @@ int poisson_batch(afem_mesh* m, const double2* phi, int n, double* W, double rto
         w.rr = cv.take<double>(k);
         w.active = cv.take<int>(k);
         w.n_active = cv.take<int>(1);
+        w.counters = cv.take<unsigned>(4);
     };
     Carver measure(nullptr);
     carve(measure);
@@ -490,6 +590,7 @@ int poisson_batch(afem_mesh* m, const double2* phi, int n, double* W, double rto
     Carver cv(m->ws_poisson.ptr);
     carve(cv);
     PcgState st{w.alpha, w.beta, w.rz, w.bb, w.rr, w.active, w.n_active, rtol * rtol};
+    AFEM_CUDA_TRY(cudaMemsetAsync(w.counters, 0, 4 * sizeof(unsigned), s));
 
     if (!warm) AFEM_CUDA_TRY(cudaMemsetAsync(W, 0, NK * sizeof(double), s));
     if ((rc = poisson_rhs_bc(m, phi, n, W, w.b, w.qpart, w.q, s))) return rc;
@@ -512,11 +613,13 @@ int poisson_batch(afem_mesh* m, const double2* phi, int n, double* W, double rto
             if (n_active == 0) break;
         }
         if ((rc = launch_stiffness(m, w.p, w.Ap, k, 1, s))) return rc;
-        AFEM_LAUNCH((col_dot_kernel), nblk, kRedThreads, 0, s, w.p, w.Ap, Ni, k, w.partial);
-        AFEM_LAUNCH((pcg_alpha_kernel), 1, 64, 0, s, w.partial, nblk, k, st);
-        AFEM_LAUNCH((pcg_update_kernel), nblk, kRedThreads, 0, s, W, w.r, w.z, w.p, w.Ap, D.stiff_dinv, Ni, k, st, w.partial);
-        AFEM_LAUNCH((pcg_beta_kernel), 1, 64, 0, s, w.partial, nblk, k, st);
-        AFEM_LAUNCH((pcg_p_kernel), grid_for(Ni * k), 256, 0, s, w.p, w.z, Ni, k, st);
+        AFEM_LAUNCH((dot_alpha_kernel<double>), nblk, kRedThreads, 0, s, w.p, w.Ap, Ni, k, w.partial,
+                    w.counters + 0, st);
+        AFEM_LAUNCH((update_beta_kernel<double>), nblk, kRedThreads, 0, s, W, w.r, w.p, w.Ap, D.stiff_dinv, Ni, k, st,
+                    w.partial, w.counters + 1, static_cast<const double*>(nullptr),
+                    static_cast<const double*>(nullptr), static_cast<const double*>(nullptr), 0.0, 0.0,
+                    static_cast<int*>(nullptr));
+        AFEM_LAUNCH((p_update_kernel<double>), grid_for(Ni * k), 256, 0, s, w.p, w.r, D.stiff_dinv, Ni, k, st);
         AFEM_CUDA_TRY(cudaGetLastError());
         ++it;
     }
@@ -900,6 +1003,7 @@ int poisson_batch_mixed(afem_mesh* m, const double2* phi, int n, double* W, doub
         bb64 = cv.take<double>(k);
         rr_upd = cv.take<double>(k);
         flags = cv.take<int>(2);
+        w.counters = cv.take<unsigned>(4);
     };
     Carver measure(nullptr);
     carve(measure);
@@ -909,6 +1013,7 @@ int poisson_batch_mixed(afem_mesh* m, const double2* phi, int n, double* W, doub
     carve(cv);
     PcgState st{w.alpha, w.beta, w.rz, w.bb, w.rr, w.active, w.n_active, 0.0};
     const double rtol2 = rtol * rtol, delta2 = delta * delta;
+    AFEM_CUDA_TRY(cudaMemsetAsync(w.counters, 0, 4 * sizeof(unsigned), s));
 
     if (!warm) AFEM_CUDA_TRY(cudaMemsetAsync(W, 0, NK * sizeof(double), s));
     if ((rc = poisson_rhs_bc(m, phi, n, W, w.b, w.qpart, w.q, s))) return rc;
@@ -939,13 +1044,11 @@ int poisson_batch_mixed(afem_mesh* m, const double2* phi, int n, double* W, doub
     const int check_every = 8;
     while (flags_h[0] > 0 && it < max_it) {
         if ((rc = launch_stiffness32(m, p32, Ap32, k, 1, s))) return rc;
-        AFEM_LAUNCH((col_dot32_kernel), nblk, kRedThreads, 0, s, p32, Ap32, Ni, k, w.partial);
-        AFEM_LAUNCH((pcg_alpha_kernel), 1, 64, 0, s, w.partial, nblk, k, st);
-        AFEM_LAUNCH((pcg32_update_kernel), nblk, kRedThreads, 0, s, d32, r32, z32, p32, Ap32, D.stiff_dinv32, Ni, k,
-                    st, w.partial);
-        AFEM_LAUNCH((pcg32_beta_ru_kernel), 1, 64, 0, s, w.partial, nblk, k, st, s_old, rr_upd, bb64, rtol2, delta2,
-                    flags);
-        AFEM_LAUNCH((pcg32_p_kernel), grid_for(Ni * k), 256, 0, s, p32, z32, Ni, k, st);
+        AFEM_LAUNCH((dot_alpha_kernel<float>), nblk, kRedThreads, 0, s, p32, Ap32, Ni, k, w.partial,
+                    w.counters + 0, st);
+        AFEM_LAUNCH((update_beta_kernel<float>), nblk, kRedThreads, 0, s, d32, r32, p32, Ap32, D.stiff_dinv32, Ni, k,
+                    st, w.partial, w.counters + 1, s_old, rr_upd, bb64, rtol2, delta2, flags);
+        AFEM_LAUNCH((p_update_kernel<float>), grid_for(Ni * k), 256, 0, s, p32, r32, D.stiff_dinv32, Ni, k, st);
         AFEM_CUDA_TRY(cudaGetLastError());
         ++it;
         if (it % check_every == 0 || it >= max_it) {

@@ -30,6 +30,42 @@ __device__ __forceinline__ void reduce_columns(double* s, int k, int R, double* 
     }
 }
 
+// Last-block reduction: every block has written its row partial[blockIdx][0..kout)
+// (kout <= blockDim).  All threads of all blocks call this; it returns true only
+// in the block that finishes last, where s_sum[0..kout) then holds the column
+// sums over all blocks.  The sums are formed in a fixed order (thread j of a
+// column adds blocks j, j+J, ..., then a fixed tree), independent of which block
+// finishes last.  *counter must be 0 before the launch; the last block resets it.
+__device__ __forceinline__ bool last_block_sum(const double* partial, int kout, unsigned* counter,
+                                               double* s_sum /* >= blockDim doubles */) {
+    __shared__ bool s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    const int J = blockDim.x / kout;
+    const int t = threadIdx.x;
+    double acc = 0.0;
+    if (t < J * kout) {
+        const int c = t % kout, j = t / kout;
+        for (unsigned b = j; b < gridDim.x; b += J) acc += __ldcg(partial + size_t(b) * kout + c);
+    }
+    s_sum[t] = acc;
+    __syncthreads();
+    if (t < kout) {
+        double s = 0.0;
+        for (int j = 0; j < J; ++j) s += s_sum[t + j * kout];
+        acc = s;
+    }
+    __syncthreads();
+    if (t < kout) s_sum[t] = acc;
+    __syncthreads();
+    if (t == 0) *counter = 0u;
+    return true;
+}
+
 // Sum partial[b][c] over blocks b into out[c] (one block, fixed order).
 __global__ void finalize_columns_kernel(const double* __restrict__ partial, int nblk, int k,
                                         double* __restrict__ out);

@@ -97,12 +97,13 @@ def gaussian_orbital(X, interior, center=(0.0, 0.0, 0.0), alpha=1.0, phase_noise
     return np.where(interior, amp * np.exp(1j * theta), 0.0)
 
 
-def molecular_orbitals(X, interior, nuclei, n, seed=BASE_SEED):
+def molecular_orbitals(X, interior, nuclei, n, seed=BASE_SEED, phase_noise=1e-3):
     """n seeded Gaussian / 1s-like orbitals on the nuclei (not yet orthonormal).
 
     Orbital j sits on nucleus j mod n_nuclei with exponent 0.5 + 0.4 j / n and a
     small seeded displacement, times a polynomial factor (1, x, y, z, ...) of
-    the displacement so that the set is linearly independent.
+    the displacement so that the set is linearly independent; phase_noise is
+    the standard deviation of a per-point random phase (0 for smooth orbitals).
     """
     out = np.zeros((len(X), n), dtype=np.complex128)
     rng = np.random.default_rng(seed)
@@ -111,7 +112,7 @@ def molecular_orbitals(X, interior, nuclei, n, seed=BASE_SEED):
         d = X - R
         alpha = 0.5 + 0.4 * j / max(n, 1)
         poly = np.ones(len(X)) if j < len(nuclei) else d[:, (j - len(nuclei)) % 3]
-        theta = 1e-3 * coord_normal(X, seed, stream=j + 1)
+        theta = phase_noise * coord_normal(X, seed, stream=j + 1) if phase_noise else 0.0
         out[:, j] = poly * np.exp(-alpha * np.sum(d * d, axis=1)) * np.exp(1j * theta)
     out[~interior] = 0
     return out
