@@ -120,6 +120,14 @@ int afem_mesh_create_ex(const afem_mesh_desc* desc, int flags, afem_mesh** out);
 /* Release the mesh and its device tables.  NULL is accepted.  Synchronous. */
 int afem_mesh_destroy(afem_mesh* mesh);
 
+/* Kernel-shape options of a mesh (library tuning; no counterpart in the paper).
+ * AFEM_OPT_CELL32_VARIANT selects the float32 four-lane cell pass: 0 (default)
+ * computes the 1D contractions line by line with direction-wise accumulation
+ * in shared memory, 1 computes each output node in one thread.  Both give the
+ * same operator.  Host only. */
+#define AFEM_OPT_CELL32_VARIANT 1
+int afem_mesh_set_option(afem_mesh* mesh, int option, int value);
+
 /* Sizes of the mesh (host struct, caller-owned). */
 int afem_mesh_get_info(const afem_mesh* mesh, afem_mesh_info* info);
 

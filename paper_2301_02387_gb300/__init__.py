@@ -259,3 +259,11 @@ def op_apply(mesh, kind, x, y, E=None, stream=None):
         mesh.handle, int(kind), ctypes.cast(Earr, ctypes.c_void_p) if Earr is not None else None,
         xp, yp, nvec, _stream_ptr(stream)))
     return y
+
+
+OPT_CELL32_VARIANT = 1
+
+
+def mesh_set_option(mesh, option, value):
+    """afem_mesh_set_option (kernel-shape tuning)."""
+    _capi.check(_capi.load().afem_mesh_set_option(mesh.handle, int(option), int(value)))

@@ -77,6 +77,7 @@ SIGNATURES = {
     "afem_mesh_create_ex": (ctypes.c_int, [ctypes.POINTER(MeshDesc), ctypes.c_int, ctypes.POINTER(_P)]),
     "afem_mesh_destroy": (ctypes.c_int, [_P]),
     "afem_mesh_get_info": (ctypes.c_int, [_P, ctypes.POINTER(MeshInfo)]),
+    "afem_mesh_set_option": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
     "afem_mesh_tables": (ctypes.c_int, [_P, _P, _P, _P]),
     "afem_op_apply": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, ctypes.c_int, _P]),
     "afem_poisson_batch": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_double, ctypes.c_int,

@@ -76,6 +76,16 @@ int afem_mesh_destroy(afem_mesh* mesh) {
     return AFEM_OK;
 }
 
+int afem_mesh_set_option(afem_mesh* m, int option, int value) {
+    if (!m) return set_error(AFEM_EINVAL, "afem_mesh_set_option: null mesh");
+    if (option == AFEM_OPT_CELL32_VARIANT) {
+        if (value != 0 && value != 1) return set_error(AFEM_EINVAL, "afem_mesh_set_option: variant must be 0 or 1");
+        m->cell32_variant = value;
+        return AFEM_OK;
+    }
+    return set_error(AFEM_EINVAL, "afem_mesh_set_option: unknown option");
+}
+
 int afem_mesh_get_info(const afem_mesh* m, afem_mesh_info* info) {
     if (!m || !info) return set_error(AFEM_EINVAL, "afem_mesh_get_info: null argument");
     const HostMesh& H = m->host;

@@ -269,6 +269,144 @@ __global__ void __launch_bounds__(256) cell32v_kernel(CellArgs32 a, const float4
     }
 }
 
+// Line-ordered form of the four-lane pass: the three 1D contractions run as
+// whole lines (each thread loads the P1 values of one line once and writes P1
+// outputs), accumulated direction by direction in shared memory, which cuts
+// the shared-memory loads per cell from 3 (p+1) per output to about 3 per
+// output.  Node-local terms (potential, mean field) are added with the first
+// direction.  128 threads per cell.
+template <int P, bool G>
+__global__ void __launch_bounds__(128) cell32L_kernel(CellArgs32 a, const float4* __restrict__ x,
+                                                      const float2* __restrict__ U, float4* __restrict__ y, int L4,
+                                                      int n) {
+    constexpr int P1 = P + 1;
+    constexpr int NN = P1 * P1 * P1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float4* s_u = reinterpret_cast<float4*>(smem_raw);          // [NN][L4]
+    float4* s_acc = s_u + NN * L4;                              // [NN][L4]
+    float2* s_U = reinterpret_cast<float2*>(s_acc + NN * L4);   // [NN][n*n] (G with U)
+    __shared__ int s_idx[NN];
+    __shared__ float s_pot[NN];
+    __shared__ float s_wq[NN];
+    __shared__ float s_K[P1 * P1];
+    __shared__ float s_w[P1];
+    const int64_t cell = blockIdx.x;
+    const int tid = threadIdx.x, bs = blockDim.x;
+    const float4 g = a.geom[cell];
+    for (int i = tid; i < NN; i += bs) s_idx[i] = a.cell_node[cell * NN + i];
+    if (tid < P1 * P1) s_K[tid] = a.K[tid];
+    if (tid < P1) s_w[tid] = a.w[tid];
+    __syncthreads();
+    for (int it = tid; it < NN * L4; it += bs) {
+        const int i = it / L4, q = it - i * L4;
+        s_u[it] = gather32v(a, s_idx[i], x, L4, q);
+    }
+    const int nn2 = n * n;
+    if (G) {
+        if (U) {
+            CellArgs32 au = a;
+            au.masked = 0;
+            for (int it = tid; it < NN * nn2; it += bs) {
+                const int i = it / nn2, pq = it - i * nn2;
+                s_U[it] = gather32<float2>(au, s_idx[i], U, nn2, pq);
+            }
+        }
+        const float h3 = g.w * g.w * g.w;
+        for (int i = tid; i < NN; i += bs) {
+            const int ia = i % P1, ib = (i / P1) % P1, ic = i / (P1 * P1);
+            const int idx = s_idx[i];
+            const float V = idx >= 0 ? a.v_master[idx] : a.v_hang[-idx - 1];
+            const float px = g.x + g.w * a.xi[ia], py = g.y + g.w * a.xi[ib], pz = g.z + g.w * a.xi[ic];
+            const float wq = h3 * s_w[ia] * s_w[ib] * s_w[ic];
+            s_wq[i] = wq;
+            s_pot[i] = wq * (V + a.E[0] * px + a.E[1] * py + a.E[2] * pz);
+        }
+    }
+    __syncthreads();
+    const float ck = (G ? 0.5f : 1.0f) * g.w;
+    constexpr int NL = P1 * P1;   // lines per direction
+    // direction 0 (x): line (b, c), nodes a + P1 (b + P1 c); stores
+    for (int it = tid; it < NL * L4; it += bs) {
+        const int line = it / L4, q = it - line * L4;
+        const int b = line % P1, c = line / P1;
+        float4 u[P1];
+#pragma unroll
+        for (int m = 0; m < P1; ++m) u[m] = s_u[(m + P1 * (b + P1 * c)) * L4 + q];
+        const float sc = ck * s_w[b] * s_w[c];
+#pragma unroll
+        for (int aa = 0; aa < P1; ++aa) {
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int m = 0; m < P1; ++m) f4fma(acc, s_K[aa * P1 + m], u[m]);
+            const int node = aa + P1 * (b + P1 * c);
+            float4 r = make_float4(sc * acc.x, sc * acc.y, sc * acc.z, sc * acc.w);
+            if constexpr (G) {
+                f4fma(r, s_pot[node], u[aa]);
+                if (U) {
+                    const float2* ui = reinterpret_cast<const float2*>(s_u + node * L4);
+                    const float2* U0 = s_U + node * nn2 + (2 * q) * n;
+                    const float2* U1 = U0 + n;
+                    float2 m0 = make_float2(0.f, 0.f), m1 = m0;
+                    for (int rr = 0; rr < n; ++rr) {
+                        const float2 uu = ui[rr];
+                        m0.x = fmaf(U0[rr].x, uu.x, fmaf(-U0[rr].y, uu.y, m0.x));
+                        m0.y = fmaf(U0[rr].x, uu.y, fmaf(U0[rr].y, uu.x, m0.y));
+                        m1.x = fmaf(U1[rr].x, uu.x, fmaf(-U1[rr].y, uu.y, m1.x));
+                        m1.y = fmaf(U1[rr].x, uu.y, fmaf(U1[rr].y, uu.x, m1.y));
+                    }
+                    const float wq = s_wq[node];
+                    r.x = fmaf(wq, m0.x, r.x);
+                    r.y = fmaf(wq, m0.y, r.y);
+                    r.z = fmaf(wq, m1.x, r.z);
+                    r.w = fmaf(wq, m1.y, r.w);
+                }
+            }
+            s_acc[node * L4 + q] = r;
+        }
+    }
+    __syncthreads();
+    // direction 1 (y): line (a, c)
+    for (int it = tid; it < NL * L4; it += bs) {
+        const int line = it / L4, q = it - line * L4;
+        const int aa = line % P1, c = line / P1;
+        float4 u[P1];
+#pragma unroll
+        for (int m = 0; m < P1; ++m) u[m] = s_u[(aa + P1 * (m + P1 * c)) * L4 + q];
+        const float sc = ck * s_w[aa] * s_w[c];
+#pragma unroll
+        for (int b = 0; b < P1; ++b) {
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int m = 0; m < P1; ++m) f4fma(acc, s_K[b * P1 + m], u[m]);
+            float4& o = s_acc[(aa + P1 * (b + P1 * c)) * L4 + q];
+            f4fma(o, sc, acc);
+        }
+    }
+    __syncthreads();
+    // direction 2 (z): line (a, b)
+    for (int it = tid; it < NL * L4; it += bs) {
+        const int line = it / L4, q = it - line * L4;
+        const int aa = line % P1, b = line / P1;
+        float4 u[P1];
+#pragma unroll
+        for (int m = 0; m < P1; ++m) u[m] = s_u[(aa + P1 * (b + P1 * m)) * L4 + q];
+        const float sc = ck * s_w[aa] * s_w[b];
+#pragma unroll
+        for (int c = 0; c < P1; ++c) {
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int m = 0; m < P1; ++m) f4fma(acc, s_K[c * P1 + m], u[m]);
+            float4& o = s_acc[(aa + P1 * (b + P1 * c)) * L4 + q];
+            f4fma(o, sc, acc);
+        }
+    }
+    __syncthreads();
+    for (int it = tid; it < NN * L4; it += bs) {
+        const int i = it / L4, q = it - i * L4;
+        scatter32v(a, s_idx[i], y, L4, q, s_acc[it]);
+    }
+}
+
 CellArgs32 make_cell_args32(const afem_mesh* m) {
     CellArgs32 a{};
     const DeviceMesh& D = m->dev;
@@ -328,12 +466,36 @@ static int launch32v(const afem_mesh* m, const CellArgs32& a, const float* x, co
     const int p = m->dev.p;
     const int nn = (p + 1) * (p + 1) * (p + 1);
     const int L4 = L / 4;
-    const size_t smem = size_t(nn) * L4 * sizeof(float4) + ((G && U) ? size_t(nn) * n * n * sizeof(float2) : 0);
     const unsigned grid = unsigned(m->dev.ncell);
     AFEM_CUDA_TRY(cudaMemsetAsync(y, 0, size_t(m->dev.n_master) * L * sizeof(float), s));
     if (grid == 0) return AFEM_OK;
     const float4* x4 = reinterpret_cast<const float4*>(x);
     float4* y4 = reinterpret_cast<float4*>(y);
+    if (m->cell32_variant == 0) {
+        const size_t smemL =
+            2 * size_t(nn) * L4 * sizeof(float4) + ((G && U) ? size_t(nn) * n * n * sizeof(float2) : 0);
+        switch (p) {
+#define AFEM_CASE(PP)                                                                          \
+    case PP: {                                                                                 \
+        auto k = cell32L_kernel<PP, G>;                                                        \
+        if (smemL > 48 * 1024)                                                                 \
+            AFEM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                               int(smemL)));                                   \
+        AFEM_LAUNCH((k), grid, 128, smemL, s, a, x4, U, y4, L4, n);                            \
+        break;                                                                                 \
+    }
+            AFEM_CASE(1)
+            AFEM_CASE(2)
+            AFEM_CASE(3)
+            AFEM_CASE(4)
+#undef AFEM_CASE
+            default:
+                return set_error(AFEM_EINVAL, "degree out of range");
+        }
+        AFEM_CUDA_TRY(cudaGetLastError());
+        return AFEM_OK;
+    }
+    const size_t smem = size_t(nn) * L4 * sizeof(float4) + ((G && U) ? size_t(nn) * n * n * sizeof(float2) : 0);
     switch (p) {
 #define AFEM_CASE(PP)                                                                          \
     case PP: {                                                                                 \

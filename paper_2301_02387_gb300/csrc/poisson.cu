@@ -90,6 +90,42 @@ __device__ void regular_solid_harmonics(double x, double y, double z, double* R)
     }
 }
 
+// One order m of the same harmonics (l = m..kLmax): C_mm, S_mm by the same
+// recurrence in m, then the recurrence in l; lets several threads share a point.
+__device__ void solid_harmonics_order(double x, double y, double z, int m, double* R) {
+    const double r2 = x * x + y * y + z * z;
+    double cmm = 1.0, smm = 0.0;
+    for (int q = 0; q < m; ++q) {
+        const double nc = -(2 * q + 1) * (x * cmm - y * smm);
+        const double ns = -(2 * q + 1) * (x * smm + y * cmm);
+        cmm = nc;
+        smm = ns;
+    }
+    double c2 = 0.0, s2 = 0.0, c1 = cmm, s1 = smm;
+    {
+        const int i = m * m + m;
+        R[i + m] = c_sh_norm[i + m] * cmm;
+        if (m > 0) R[i - m] = c_sh_norm[i + m] * smm;
+    }
+    for (int l = m + 1; l <= kLmax; ++l) {
+        double c, s;
+        if (l == m + 1) {
+            c = (2 * m + 1) * z * c1;
+            s = (2 * m + 1) * z * s1;
+        } else {
+            c = ((2 * l - 1) * z * c1 - (l + m - 1) * r2 * c2) / (l - m);
+            s = ((2 * l - 1) * z * s1 - (l + m - 1) * r2 * s2) / (l - m);
+        }
+        const int i = l * l + l;
+        R[i + m] = c_sh_norm[i + m] * c;
+        if (m > 0) R[i - m] = c_sh_norm[i + m] * s;
+        c2 = c1;
+        s2 = s1;
+        c1 = c;
+        s1 = s;
+    }
+}
+
 // Column c of the pair-density right-hand sides from orbital values at one point.
 // Order: c < n: |phi_c|^2; then for r < s: Re(conj(phi_r) phi_s), Im(...).
 __device__ __forceinline__ void pair_columns(const double2* ph, int n, double* rho) {
@@ -124,6 +160,7 @@ __global__ void __launch_bounds__(256) pair_rhs_moments_kernel(PointArgs a, doub
     double* s_R = smem_d;                          // [kMomTile][kNlm]
     double* s_w = s_R + kMomTile * kNlm;           // [kMomTile][ncol]
     double* s_Q = s_w + kMomTile * a.ncol;         // [kNlm][ncol]
+    __shared__ double4 s_pt[kMomTile];             // point relative to the centre, valid flag
     const int ncol = a.ncol;
     const int tid = threadIdx.x;
     for (int o = tid; o < kNlm * ncol; o += blockDim.x) s_Q[o] = 0.0;
@@ -175,10 +212,28 @@ __global__ void __launch_bounds__(256) pair_rhs_moments_kernel(PointArgs a, doub
                         for (int c = 0; c < ncol; ++c) atomicAdd(&b[m * ncol + c], fpi * a.hw[e] * wrow[c]);
                     }
                 }
-                regular_solid_harmonics(x - a.cx, y - a.cy, z - a.cz, Rrow);
+                s_pt[tid] = make_double4(x - a.cx, y - a.cy, z - a.cz, 1.0);
             } else {
                 for (int c = 0; c < ncol; ++c) wrow[c] = 0.0;
-                for (int i = 0; i < kNlm; ++i) Rrow[i] = 0.0;
+                s_pt[tid] = make_double4(0.0, 0.0, 0.0, 0.0);
+            }
+            (void)Rrow;
+        }
+        __syncthreads();
+        // harmonics of the tile: 8 threads per point, orders m and m + 8
+        for (int it = tid; it < kMomTile * 8; it += blockDim.x) {
+            const int tp = it >> 3, j = it & 7;
+            const double4 q = s_pt[tp];
+            double* Rr = s_R + tp * kNlm;
+            for (int m = j; m <= kLmax; m += 8) {
+                if (q.w != 0.0) {
+                    solid_harmonics_order(q.x, q.y, q.z, m, Rr);
+                } else {
+                    for (int l = m; l <= kLmax; ++l) {
+                        Rr[l * l + l + m] = 0.0;
+                        if (m > 0) Rr[l * l + l - m] = 0.0;
+                    }
+                }
             }
         }
         __syncthreads();

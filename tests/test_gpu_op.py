@@ -80,12 +80,14 @@ def test_op_apply_rejects_bad_arguments():
 
 
 @pytest.mark.parametrize("case", CASES[:3])
-@pytest.mark.parametrize("nvec", [3, 16])     # 3: scalar-lane kernel, 16: four-lane kernel
-def test_stiffness_f32_within_fp32_tolerance(case, nvec):
+@pytest.mark.parametrize("nvec", [3, 16])     # 3: scalar-lane kernel, 16: four-lane kernels
+@pytest.mark.parametrize("variant", [0, 1])   # four-lane: line-ordered / node-per-thread
+def test_stiffness_f32_within_fp32_tolerance(case, nvec, variant):
     """Precision form of the stiffness: relative error a few float32 ulps x operator norm."""
     import torch
-    from paper_2301_02387_gb300 import op_apply, OP_STIFF_F32
+    from paper_2301_02387_gb300 import op_apply, OP_STIFF_F32, mesh_set_option, OPT_CELL32_VARIANT
     gm, om, op, perm = _pair(case)
+    mesh_set_option(gm, OPT_CELL32_VARIANT, variant)
     rng = np.random.default_rng(9)
     xo = rng.standard_normal((om.N, nvec)).astype(np.float32).astype(np.float64)
     yo = op.stiffness_apply(xo)
@@ -97,11 +99,13 @@ def test_stiffness_f32_within_fp32_tolerance(case, nvec):
 
 
 @pytest.mark.parametrize("case", CASES[:3])
-@pytest.mark.parametrize("nvec", [1, 4])      # 1: scalar-lane kernel, 4: four-lane kernel
-def test_h1_c64_within_fp32_tolerance(case, nvec):
+@pytest.mark.parametrize("nvec", [1, 4])      # 1: scalar-lane kernel, 4: four-lane kernels
+@pytest.mark.parametrize("variant", [0, 1])
+def test_h1_c64_within_fp32_tolerance(case, nvec, variant):
     import torch
-    from paper_2301_02387_gb300 import op_apply, OP_H1_C64
+    from paper_2301_02387_gb300 import op_apply, OP_H1_C64, mesh_set_option, OPT_CELL32_VARIANT
     gm, om, op, perm = _pair(case)
+    mesh_set_option(gm, OPT_CELL32_VARIANT, variant)
     rng = np.random.default_rng(12)
     xo = (rng.standard_normal((om.N, nvec)) + 1j * rng.standard_normal((om.N, nvec))).astype(np.complex64)
     xo = xo.astype(np.complex128)
