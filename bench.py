@@ -406,6 +406,44 @@ def run_profile_step(inner_iters=48):
     print("profile-step done", info)
 
 
+def run_profile_arnoldi(dt_short=2e-4, dt_timed=2e-3, timed=True):
+    """The orbital propagator alone on the workload mesh (mean fields frozen to
+    a smooth synthetic field): one short error-controlled propagation (a few
+    substeps, small enough for a profiler's launch list), then a timed one per
+    arithmetic form reporting ms per Krylov substep."""
+    import numpy as np
+    import torch
+    import paper_2301_02387_gb300 as pkg
+    from paper_2301_02387_gb300 import inputs
+    torch.cuda.set_device(0)
+    w = inputs.WORKLOADS[WORKLOAD]
+    mesh, solver, phi0, C0 = setup_state(pkg, inputs, torch, w)
+    n = w["n_orb"]
+    phi = torch.from_numpy(phi0).cuda()
+    X, _, _ = mesh.tables()
+    r = np.sqrt(np.sum(X ** 2, axis=1))
+    U = np.zeros((mesh.N, n, n), dtype=np.complex128)
+    for p in range(n):
+        U[:, p, p] = 1.0 / np.sqrt(r * r + 0.3 * (p + 1))
+    U[:, 0, 1] = U[:, 1, 0] = 0.1 / np.sqrt(r * r + 1.0)
+    Ud = torch.from_numpy(U.reshape(mesh.N, n * n)).cuda()
+    E = (0.0, 0.0, 0.01)
+    _, err, sub = pkg.arnoldi_propagate(mesh, phi, Ud, w["m"], dt_short, 1e-10, E=E, precision=pkg.PREC_MIXED)
+    torch.cuda.synchronize()
+    out = {"short": {"dt": dt_short, "substeps": sub, "err": err}}
+    for name, prec in ((("fp64", pkg.PREC_FP64), ("mixed", pkg.PREC_MIXED)) if timed else ()):
+        pkg.arnoldi_propagate(mesh, phi, Ud, w["m"], dt_short, 1e-10, E=E, precision=prec)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        _, err, sub = pkg.arnoldi_propagate(mesh, phi, Ud, w["m"], dt_timed, 1e-10, E=E, precision=prec)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        out[name] = {"dt": dt_timed, "substeps": sub, "ms": ms, "ms_per_substep": ms / max(sub, 1), "err": err}
+    print(json.dumps({"profile_arnoldi": out, "N": mesh.N, "n_orb": n}))
+
+
 def cpu_baseline_entry(N_full):
     s = oracle_sample()
     per_dof = s["sec_per_step"] / s["N"]
@@ -449,7 +487,12 @@ def main():
                     help="build the workload and run each operator kernel a few times (for profilers); no JSON")
     ap.add_argument("--profile-step", action="store_true",
                     help="one precision-form step with the inner CG capped (for a profiler's launch list); no JSON")
+    ap.add_argument("--profile-arnoldi", action="store_true",
+                    help="the orbital propagator alone: a short propagation, then ms per Krylov substep per form")
     args = ap.parse_args()
+    if args.profile_arnoldi:
+        run_profile_arnoldi(timed=args.steps > 0)
+        return
     if args.kernels_only:
         run_kernels_only()
         return

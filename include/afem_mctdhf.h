@@ -122,9 +122,9 @@ int afem_mesh_destroy(afem_mesh* mesh);
 
 /* Kernel-shape options of a mesh (library tuning; no counterpart in the paper).
  * AFEM_OPT_CELL32_VARIANT selects the float32 four-lane cell pass: 0 (default)
- * computes the 1D contractions line by line with direction-wise accumulation
- * in shared memory, 1 computes each output node in one thread.  Both give the
- * same operator.  Host only. */
+ * computes each output node in one thread, 1 computes the 1D contractions
+ * line by line with direction-wise accumulation in shared memory.  Both give
+ * the same operator.  Host only. */
 #define AFEM_OPT_CELL32_VARIANT 1
 int afem_mesh_set_option(afem_mesh* mesh, int option, int value);
 

@@ -14,6 +14,8 @@ Test infrastructure only (see the package docstring).
 import numpy as np
 import scipy.linalg
 
+LADDER = 16   # candidate substep lengths per ladder in arnoldi_propagate
+
 
 def arnoldi_expm(apply_G, phi, inner, m, dt, breakdown_tol=1e-14):
     """Returns (phi_new, err_estimate, H (m+1 x m), m_used, breakdown).
@@ -71,29 +73,46 @@ def arnoldi_propagate(apply_G, phi, inner, m, dt, tol, max_substeps=4096):
     """exp(-i G dt) phi with the Krylov error controlled substep by substep.
 
     Sec. 3.2 fixes the Krylov accuracy by an a-posteriori estimate (threshold
-    1e-10 in the paper).  Here the dimension m is fixed and dt is covered by
-    substeps of the same G: the first trial is the whole remainder; while
-    beta |h_{m+1,m}| |e_m^T exp(-i tau H_m) e_1| > tol beta, tau is multiplied
-    by min(1/2, max(0.05, 0.9 (tol beta / err)^(1/m))); the accepted substep
-    gives the next starting vector.  Returns (phi_new, sum of estimates, substeps).
+    1e-10 in the paper) and leaves open how the step adapts (Park and Light
+    allow an adaptive step or an adaptive dimension).  Here the dimension m is
+    fixed and dt is covered by substeps of the same G, each as long as the
+    candidates allow: tau_c = tau_max 2^(-c/2), c = 0..15, with tau_max the
+    whole remainder for the first substep and min(remainder, 2 tau_previous)
+    after it; the first (longest) candidate whose estimate
+    beta |h_{m+1,m}| |e_m^T exp(-i tau_c H_m) e_1| is <= tol beta is taken;
+    when none is, the ladder continues below its smallest candidate (at most 8
+    more ladders, then the smallest is taken).  A breakdown (invariant Krylov
+    space) takes the whole remainder with estimate 0.  tol <= 0: one step over
+    dt.  Returns (phi_new, sum of estimates, substeps).
     """
     remaining = dt
     cur = phi
-    total, substeps = 0.0, 0
+    total, substeps, tau_prev = 0.0, 0, 0.0
     while remaining > 0.0:
         if substeps >= max_substeps:
             raise RuntimeError("too many Krylov substeps")
         beta, V, H, mu, brk, hlast = arnoldi_basis(apply_G, cur, inner, m)
-        tau = remaining
-        for tries in range(41):
+        if brk or tol <= 0.0:
+            tau = remaining
             Em = scipy.linalg.expm(-1j * tau * H[:mu, :mu])
             err = 0.0 if brk else beta * hlast * abs(Em[mu - 1, 0])
-            if brk or err <= tol * beta or tries >= 40:
-                break
-            shrink = 0.9 * (tol * beta / err) ** (1.0 / mu)
-            tau *= min(0.5, max(shrink, 0.05))
+        else:
+            tau_max = remaining if substeps == 0 else min(remaining, 2.0 * tau_prev)
+            found = False
+            for ladder in range(9):
+                for c in range(LADDER):
+                    tau = tau_max * 2.0 ** (-0.5 * c)
+                    Em = scipy.linalg.expm(-1j * tau * H[:mu, :mu])
+                    err = beta * hlast * abs(Em[mu - 1, 0])
+                    if err <= tol * beta:
+                        found = True
+                        break
+                if found:
+                    break
+                tau_max *= 2.0 ** (-0.5 * LADDER)
         cur = sum(beta * Em[i, 0] * V[i] for i in range(mu))
         total += err
         substeps += 1
+        tau_prev = tau
         remaining = 0.0 if tau >= remaining else remaining - tau
     return cur, total, substeps

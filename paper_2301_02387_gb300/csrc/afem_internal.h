@@ -128,7 +128,7 @@ struct afem_mesh {
     bool host_only = false;
     afem::Workspace ws_poisson;
     afem::Workspace ws_arnoldi;
-    int cell32_variant = 0;   // FP32 four-lane cell pass: 0 line-ordered, 1 node-per-thread
+    int cell32_variant = 0;   // FP32 four-lane cell pass: 0 node-per-thread, 1 line-ordered
 };
 
 namespace afem {

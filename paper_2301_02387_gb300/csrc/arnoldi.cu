@@ -3,12 +3,23 @@
 // With phi, the RDMs, the mean fields and the field frozen at t, the packed
 // orbital equation (Eq. packed_orb_eom) is linear, i d(phi)/dt = G phi, and
 // phi(t + dt) = exp(-i G dt) phi(t).  The Krylov space of G from phi is built
-// by Arnoldi (modified Gram-Schmidt, one pass) in the inner product
-// <u, v> = sum_p u_p^H M_L v_p; then phi(t+dt) = beta V_m exp(-i dt H_m) e_1.
+// by Arnoldi in the inner product <u, v> = sum_p u_p^H M_L v_p; then
+// phi(t+dt) = beta V_m exp(-i dt H_m) e_1.
 // G applied to the stacked orbitals v (Eqs. orb_eom / discretized_eom, X = 0):
 //   z_p = H1~ v_p + C^T diag(m_f) sum_q (C U_pq) o (C v_q)      (one cell pass)
 //   y_p = M_L^-1 z_p,   (G v)_p = y_p - sum_j phi_j (phi_j^H M_L y_p)
 // and phi_j^H M_L y_p = phi_j^H z_p, so the projector needs no extra scaling.
+//
+// Orthogonalisation: classical Gram-Schmidt, one pass for all inner products
+// (fused with the projector pass of G) and one for the update, plus a second
+// pair of passes only when the update cancelled the vector to below 1e-2 of
+// its norm (the Daniel-Gragg-Kaufman-Stewart test with a loose threshold).
+// GB300 runs FP64 at about 1/64 of its FP32 rate, so these vector kernels
+// are bound by FP64 instructions rather than by HBM: each keeps the FP64
+// work per element at 4 multiply-adds per basis vector and pass, and in the
+// precision form the projector (part of applying G) runs in FP32.  The
+// Hessenberg matrix and the norms stay on the device; the host waits once
+// per substep, after the candidate substep exponentials are evaluated.
 #include <cmath>
 #include <vector>
 
@@ -18,47 +29,13 @@
 
 namespace afem {
 
-// S[a][b] partials: sum_k w_k conj(A[k][a]) B[k][b] over rows k < n_rows.
-// diag != 0: only a == b (k_out = na), else all na*nb pairs (k_out = na*nb <= 256).
 __device__ __forceinline__ double2 to_d2(double2 v) { return v; }
 __device__ __forceinline__ double2 to_d2(float2 v) { return make_double2(v.x, v.y); }
 
-template <typename TB>
-__global__ void cdot_kernel(const double2* __restrict__ A, int na, const TB* __restrict__ B, int nb,
-                            const double* __restrict__ w, int64_t n_rows, int diag,
-                            double2* __restrict__ partial) {
-    __shared__ double sx[kRedThreads], sy[kRedThreads];
-    const int kout = diag ? na : na * nb;
-    const int R = kRedThreads / kout, used = R * kout;
-    const int t = threadIdx.x;
-    double ax = 0.0, ay = 0.0;
-    if (t < used) {
-        const int o = t % kout, r = t / kout;
-        const int ia = diag ? o : o / nb;
-        const int ib = diag ? o : o - ia * nb;
-        for (int64_t k = int64_t(blockIdx.x) * R + r; k < n_rows; k += int64_t(gridDim.x) * R) {
-            const double2 u = A[k * na + ia];
-            const double2 v = to_d2(B[k * nb + ib]);
-            const double wk = w ? w[k] : 1.0;
-            ax = fma(wk, fma(u.x, v.x, u.y * v.y), ax);
-            ay = fma(wk, fma(u.x, v.y, -u.y * v.x), ay);
-        }
-    }
-    sx[t] = ax;
-    sy[t] = ay;
-    __syncthreads();
-    for (int o = t; o < kout; o += blockDim.x) {
-        double x = 0.0, y = 0.0;
-        for (int r = 0; r < R; ++r) {
-            x += sx[o + kout * r];
-            y += sy[o + kout * r];
-        }
-        partial[int64_t(blockIdx.x) * kout + o] = make_double2(x, y);
-    }
-}
-
-// cdot with the block sums finished in the same launch (no sum_all form):
-// partial rows of 2*kout doubles (re, im interleaved); the last block writes out[kout].
+// S[a][b] = sum_k w_k conj(A[k][a]) B[k][b] over rows k < n_rows (w_k = 1 when
+// w is null), reduced in the same launch: partial rows of 2*kout doubles (re,
+// im interleaved); the last block writes out[kout].  diag != 0: only a == b
+// (kout = na), else all na*nb pairs (kout = na*nb <= 256).
 template <typename TB>
 __global__ void cdot_fused_kernel(const double2* __restrict__ A, int na, const TB* __restrict__ B, int nb,
                                   const double* __restrict__ w, int64_t n_rows, int diag, double* __restrict__ partial,
@@ -73,11 +50,14 @@ __global__ void cdot_fused_kernel(const double2* __restrict__ A, int na, const T
         const int ia = diag ? o : o / nb;
         const int ib = diag ? o : o - ia * nb;
         for (int64_t k = int64_t(blockIdx.x) * R + r; k < n_rows; k += int64_t(gridDim.x) * R) {
-            const double2 u = A[k * na + ia];
+            double2 u = A[k * na + ia];
             const double2 v = to_d2(B[k * nb + ib]);
-            const double wk = w ? w[k] : 1.0;
-            ax = fma(wk, fma(u.x, v.x, u.y * v.y), ax);
-            ay = fma(wk, fma(u.x, v.y, -u.y * v.x), ay);
+            if (w) {
+                const double wk = w[k];
+                u = make_double2(wk * u.x, wk * u.y);
+            }
+            ax = fma(u.x, v.x, fma(u.y, v.y, ax));
+            ay = fma(u.x, v.y, fma(-u.y, v.x, ay));
         }
     }
     sx[t] = ax;
@@ -96,185 +76,321 @@ __global__ void cdot_fused_kernel(const double2* __restrict__ A, int na, const T
     for (int o = t; o < kout; o += blockDim.x) out[o] = make_double2(sx[2 * o], sx[2 * o + 1]);
 }
 
-// out[o] = sum_b partial[b][o]; if sum_all, out[0] = sum over o as well.
-__global__ void cfinalize_kernel(const double2* __restrict__ partial, int nblk, int kout, int sum_all,
-                                 double2* __restrict__ out) {
-    __shared__ double sx[256], sy[256];
-    double tx = 0.0, ty = 0.0;
-    for (int o = threadIdx.x; o < kout; o += blockDim.x) {
-        double x = 0.0, y = 0.0;
-        for (int b = 0; b < nblk; ++b) {
-            const double2 v = partial[int64_t(b) * kout + o];
-            x += v.x;
-            y += v.y;
-        }
-        if (!sum_all) out[o] = make_double2(x, y);
-        tx += x;
-        ty += y;
-    }
-    if (!sum_all) return;
-    sx[threadIdx.x] = tx;
-    sy[threadIdx.x] = ty;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double x = 0.0, y = 0.0;
-        for (int i = 0; i < blockDim.x; ++i) {
-            x += sx[i];
-            y += sy[i];
-        }
-        out[0] = make_double2(x, y);
-    }
-}
-
-// w[k][p] = ML^-1[k] z[k][p] - sum_j phi[k][j] S[j][p]   (interior rows; others 0)
-template <typename TZ>
-__global__ void project_kernel(const TZ* __restrict__ z, const double2* __restrict__ phi,
-                               const double2* __restrict__ S, const double* __restrict__ ml_inv, int64_t n_int,
-                               int64_t N, int n, double2* __restrict__ w) {
-    const int64_t total = N * n;
-    for (int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; o < total;
-         o += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t k = o / n;
-        const int p = int(o - k * n);
-        double2 r = make_double2(0.0, 0.0);
-        if (k < n_int) {
-            const double s = ml_inv[k];
-            const double2 zo = to_d2(z[o]);
-            r = make_double2(zo.x * s, zo.y * s);
-            for (int j = 0; j < n; ++j) {
-                const double2 f = phi[k * n + j];
-                const double2 c = S[j * n + p];
-                r.x -= f.x * c.x - f.y * c.y;
-                r.y -= f.x * c.y + f.y * c.x;
+// Projector overlaps of the precision form, S[a][b] = sum_k conj(A[k][a]) B[k][b]
+// over interior rows from complex64 inputs: products and runs of 16 rows are
+// summed in FP32, the runs in FP64 (so the FP64 work per element is 1/16 of
+// a product), the blocks by the last block.  n*n <= 256.
+__global__ void __launch_bounds__(kRedThreads) overlap32_kernel(const float2* __restrict__ A,
+                                                                const float2* __restrict__ B, int64_t n_rows, int n,
+                                                                double* __restrict__ partial,
+                                                                unsigned* __restrict__ counter,
+                                                                double2* __restrict__ out) {
+    __shared__ double sx[kRedThreads], sy[kRedThreads];
+    const int kout = n * n;
+    const int R = kRedThreads / kout, used = R * kout;
+    const int t = threadIdx.x;
+    double ax = 0.0, ay = 0.0;
+    if (t < used) {
+        const int o = t % kout, r = t / kout;
+        const int ia = o / n, ib = o - ia * n;
+        const int64_t step = int64_t(gridDim.x) * R;
+        int64_t k = int64_t(blockIdx.x) * R + r;
+        while (k < n_rows) {
+            float fx = 0.f, fy = 0.f;
+            for (int run = 0; run < 16 && k < n_rows; ++run, k += step) {
+                const float2 u = A[k * n + ia], v = B[k * n + ib];
+                fx = fmaf(u.x, v.x, fmaf(u.y, v.y, fx));
+                fy = fmaf(u.x, v.y, fmaf(-u.y, v.x, fy));
             }
+            ax += double(fx);
+            ay += double(fy);
         }
-        w[o] = r;
     }
-}
-
-// MGS step: w -= h_prev * V_prev (if V_prev), then partial <V_i, w>_M (or <w, w>_M if V_i null).
-__global__ void mgs_kernel(double2* __restrict__ w, const double2* __restrict__ Vprev,
-                           const double2* __restrict__ hprev, const double2* __restrict__ Vi,
-                           const double* __restrict__ ml, int64_t n_int, int n, double2* __restrict__ partial) {
-    __shared__ double sx[kRedThreads], sy[kRedThreads];
-    const int64_t total = n_int * n;
-    double ax = 0.0, ay = 0.0;
-    const double2 h = Vprev ? *hprev : make_double2(0.0, 0.0);
-    for (int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; o < total;
-         o += int64_t(gridDim.x) * blockDim.x) {
-        double2 x = w[o];
-        if (Vprev) {
-            const double2 v = Vprev[o];
-            x.x -= h.x * v.x - h.y * v.y;
-            x.y -= h.x * v.y + h.y * v.x;
-            w[o] = x;
-        }
-        const double2 u = Vi ? Vi[o] : x;
-        const double m = ml[o / n];
-        ax = fma(m, fma(u.x, x.x, u.y * x.y), ax);
-        ay = fma(m, fma(u.x, x.y, -u.y * x.x), ay);
-    }
-    sx[threadIdx.x] = ax;
-    sy[threadIdx.x] = ay;
+    sx[t] = ax;
+    sy[t] = ay;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    for (int o = t; o < kout; o += blockDim.x) {
         double x = 0.0, y = 0.0;
-        for (int i = 0; i < blockDim.x; ++i) {
-            x += sx[i];
-            y += sy[i];
+        for (int r = 0; r < R; ++r) {
+            x += sx[o + kout * r];
+            y += sy[o + kout * r];
         }
-        partial[blockIdx.x] = make_double2(x, y);
+        partial[int64_t(blockIdx.x) * 2 * kout + 2 * o] = x;
+        partial[int64_t(blockIdx.x) * 2 * kout + 2 * o + 1] = y;
+    }
+    if (!last_block_sum(partial, 2 * kout, counter, sx)) return;
+    for (int o = t; o < kout; o += blockDim.x) out[o] = make_double2(sx[2 * o], sx[2 * o + 1]);
+}
+
+// Thread layout of the row-major [rows][n] vector kernels: thread t < n*R of a
+// 256-thread block owns column p = t % n of rows r = t / n, r + R, ... within
+// the block's row range (R = 256 / n), so consecutive threads touch
+// consecutive elements and no element index is divided.
+struct RowCol {
+    int p, r, R;
+    bool active;
+    __device__ __forceinline__ RowCol(int n) {
+        R = kRedThreads / n;
+        active = int(threadIdx.x) < n * R;
+        r = active ? int(threadIdx.x) / n : 0;
+        p = active ? int(threadIdx.x) - r * n : 0;
+    }
+};
+
+// Sums of v[0..cnt) over the block (warp shuffles, then one warp over the
+// warp sums); thread 0 writes the block's row partial[blockIdx][0..cnt).
+template <int MAXV>
+__device__ __forceinline__ void block_row_partial(double (&v)[MAXV], int cnt, double* __restrict__ partial) {
+    __shared__ double s_w[kRedThreads / 32][MAXV];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < MAXV; ++i) {
+        if (i < cnt) {
+            double x = v[i];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+            if (lane == 0) s_w[warp][i] = x;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+        double x = 0.0;
+        for (int w = 0; w < kRedThreads / 32; ++w) x += s_w[w][i];
+        partial[int64_t(blockIdx.x) * cnt + i] = x;
     }
 }
 
-// The MGS step above with its reduction finished in the same launch: block
-// partials (re, im) go to partial[2 * block], the last block writes *out.
-__global__ void mgs_fused_kernel(double2* __restrict__ w, const double2* __restrict__ Vprev,
-                                 const double2* __restrict__ hprev, const double2* __restrict__ Vi,
-                                 const double* __restrict__ ml, int64_t n_int, int n, double* __restrict__ partial,
-                                 unsigned* __restrict__ counter, double2* __restrict__ out) {
-    __shared__ double sx[kRedThreads], sy[kRedThreads];
-    const int64_t total = n_int * n;
-    double ax = 0.0, ay = 0.0;
-    const double2 h = Vprev ? *hprev : make_double2(0.0, 0.0);
-    for (int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; o < total;
-         o += int64_t(gridDim.x) * blockDim.x) {
-        double2 x = w[o];
-        if (Vprev) {
-            const double2 v = Vprev[o];
-            x.x -= h.x * v.x - h.y * v.y;
-            x.y -= h.x * v.y + h.y * v.x;
+// acc[2i], acc[2i+1] += conj(u_i) mx (i < NV) and acc[2NV] += conj(x) mx, with
+// mx = m x formed once: 4 FP64 multiply-adds per basis vector.
+template <int NV>
+__device__ __forceinline__ void accumulate_dots(double (&acc)[2 * NV + 1], const double2 (&u)[NV > 0 ? NV : 1],
+                                                double2 x, double m) {
+    const double2 mx = make_double2(m * x.x, m * x.y);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        acc[2 * i] = fma(u[i].x, mx.x, fma(u[i].y, mx.y, acc[2 * i]));
+        acc[2 * i + 1] = fma(u[i].x, mx.y, fma(-u[i].y, mx.x, acc[2 * i + 1]));
+    }
+    acc[2 * NV] = fma(x.x, mx.x, fma(x.y, mx.y, acc[2 * NV]));
+}
+
+// The block sums of acc, then in the last block out[i] = (acc[2i], acc[2i+1])
+// for i < NV and out[NV] = (acc[2NV], 0).
+template <int NV>
+__device__ __forceinline__ void finish_dots(double (&acc)[2 * NV + 1], double* __restrict__ partial,
+                                            unsigned* __restrict__ counter, double2* __restrict__ out) {
+    constexpr int CNT = 2 * NV + 1;
+    block_row_partial<CNT>(acc, CNT, partial);
+    __shared__ double s_sum[kRedThreads];
+    if (!last_block_sum(partial, CNT, counter, s_sum)) return;
+    for (int i = threadIdx.x; i < NV; i += blockDim.x) out[i] = make_double2(s_sum[2 * i], s_sum[2 * i + 1]);
+    if (threadIdx.x == 0) out[NV] = make_double2(s_sum[2 * NV], 0.0);
+}
+
+// Gram-Schmidt inner products: out[i] = <V_i, w>_M for i < NV and
+// out[NV] = (<w, w>_M, 0), over interior rows.  Skipped when gate && !*gate.
+// NV is a template parameter so that the NV + 1 loads of a row are issued
+// back to back before any of them is used.
+template <int NV>
+__global__ void __launch_bounds__(kRedThreads) krylov_dots_kernel(
+    const double2* __restrict__ w, const double2* __restrict__ V, int64_t stride, const double* __restrict__ ml,
+    int64_t n_int, int n, const int* __restrict__ gate, double* __restrict__ partial, unsigned* __restrict__ counter,
+    double2* __restrict__ out) {
+    if (gate && *gate == 0) return;
+    double acc[2 * NV + 1];
+#pragma unroll
+    for (int i = 0; i < 2 * NV + 1; ++i) acc[i] = 0.0;
+    const RowCol rc(n);
+    if (rc.active) {
+        for (int64_t k = int64_t(blockIdx.x) * rc.R + rc.r; k < n_int; k += int64_t(gridDim.x) * rc.R) {
+            const int64_t o = k * n + rc.p;
+            const double m = ml[k];
+            const double2 x = w[o];
+            double2 u[NV > 0 ? NV : 1];
+#pragma unroll
+            for (int i = 0; i < NV; ++i) u[i] = V[i * stride + o];
+            accumulate_dots<NV>(acc, u, x, m);
+        }
+    }
+    finish_dots<NV>(acc, partial, counter, out);
+}
+
+// The projector pass of G fused with the first Gram-Schmidt pass (FP64 form):
+// w[k][p] = ML^-1[k] z[k][p] - sum_j phi[k][j] S[j][p] on interior rows (0 on
+// the others) is written, and out[i] = <V_i, w>_M (i < NV), out[NV] = <w, w>_M
+// are formed from the values in registers, so w is not read back.
+template <int NV>
+__global__ void __launch_bounds__(kRedThreads) project_dots_kernel(
+    const double2* __restrict__ z, const double2* __restrict__ phi, const double2* __restrict__ S,
+    const double* __restrict__ ml_inv, const double* __restrict__ ml, int64_t n_int, int64_t N, int n,
+    double2* __restrict__ w, const double2* __restrict__ V, int64_t stride, double* __restrict__ partial,
+    unsigned* __restrict__ counter, double2* __restrict__ out) {
+    __shared__ double2 s_S[kMaxOrbProj * kMaxOrbProj];
+    for (int i = threadIdx.x; i < n * n; i += blockDim.x) s_S[i] = S[i];
+    __syncthreads();
+    double acc[2 * NV + 1];
+#pragma unroll
+    for (int i = 0; i < 2 * NV + 1; ++i) acc[i] = 0.0;
+    const RowCol rc(n);
+    if (rc.active) {
+        const int p = rc.p;
+        for (int64_t k = int64_t(blockIdx.x) * rc.R + rc.r; k < N; k += int64_t(gridDim.x) * rc.R) {
+            const int64_t o = k * n + p;
+            double2 x = make_double2(0.0, 0.0);
+            if (k < n_int) {
+                double2 u[NV];
+#pragma unroll
+                for (int i = 0; i < NV; ++i) u[i] = V[i * stride + o];
+                const double s = ml_inv[k];
+                const double2 zo = z[o];
+                x = make_double2(zo.x * s, zo.y * s);
+                for (int j = 0; j < n; ++j) {
+                    const double2 f = phi[k * n + j];
+                    const double2 c = s_S[j * n + p];
+                    x.x = fma(-f.x, c.x, fma(f.y, c.y, x.x));
+                    x.y = fma(-f.x, c.y, fma(-f.y, c.x, x.y));
+                }
+                accumulate_dots<NV>(acc, u, x, ml[k]);
+            }
             w[o] = x;
         }
-        const double2 u = Vi ? Vi[o] : x;
-        const double m = ml[o / n];
-        ax = fma(m, fma(u.x, x.x, u.y * x.y), ax);
-        ay = fma(m, fma(u.x, x.y, -u.y * x.x), ay);
     }
-    sx[threadIdx.x] = ax;
-    sy[threadIdx.x] = ay;
+    finish_dots<NV>(acc, partial, counter, out);
+}
+
+// The same for the precision form: the projector in FP32 from the complex64
+// cell-pass output z and the complex64 orbitals phi32 (part of applying G),
+// the result widened to FP64 for the Gram-Schmidt inner products.
+template <int NV>
+__global__ void __launch_bounds__(kRedThreads) project32_dots_kernel(
+    const float2* __restrict__ z, const float2* __restrict__ phi, const double2* __restrict__ S,
+    const double* __restrict__ ml_inv, const double* __restrict__ ml, int64_t n_int, int64_t N, int n,
+    double2* __restrict__ w, const double2* __restrict__ V, int64_t stride, double* __restrict__ partial,
+    unsigned* __restrict__ counter, double2* __restrict__ out) {
+    __shared__ float2 s_S[kMaxOrbProj * kMaxOrbProj];
+    for (int i = threadIdx.x; i < n * n; i += blockDim.x) s_S[i] = make_float2(float(S[i].x), float(S[i].y));
     __syncthreads();
-    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
-        if (threadIdx.x < st) {
-            sx[threadIdx.x] += sx[threadIdx.x + st];
-            sy[threadIdx.x] += sy[threadIdx.x + st];
+    double acc[2 * NV + 1];
+#pragma unroll
+    for (int i = 0; i < 2 * NV + 1; ++i) acc[i] = 0.0;
+    const RowCol rc(n);
+    if (rc.active) {
+        const int p = rc.p;
+        for (int64_t k = int64_t(blockIdx.x) * rc.R + rc.r; k < N; k += int64_t(gridDim.x) * rc.R) {
+            const int64_t o = k * n + p;
+            double2 x = make_double2(0.0, 0.0);
+            if (k < n_int) {
+                double2 u[NV];
+#pragma unroll
+                for (int i = 0; i < NV; ++i) u[i] = V[i * stride + o];
+                const float s = float(ml_inv[k]);
+                const float2 zo = z[o];
+                float2 xf = make_float2(zo.x * s, zo.y * s);
+                for (int j = 0; j < n; ++j) {
+                    const float2 f = phi[k * n + j];
+                    const float2 c = s_S[j * n + p];
+                    xf.x = fmaf(-f.x, c.x, fmaf(f.y, c.y, xf.x));
+                    xf.y = fmaf(-f.x, c.y, fmaf(-f.y, c.x, xf.y));
+                }
+                x = make_double2(xf.x, xf.y);
+                accumulate_dots<NV>(acc, u, x, ml[k]);
+            }
+            w[o] = x;
         }
-        __syncthreads();
     }
+    finish_dots<NV>(acc, partial, counter, out);
+}
+
+// Gram-Schmidt update w -= sum_{i<NV} c_i V_i (interior rows) with the new
+// norm; the last block writes the Hessenberg column: Hcol[i] = c_i (or += c_i
+// when accumulate), Hcol[NV] = |w|_M, and *reorth = 1 when a first pass left
+// |w|^2 < eta2 * c[NV] (the squared norm before it).  Skipped when gate && !*gate.
+template <int NV>
+__global__ void __launch_bounds__(kRedThreads) krylov_update_kernel(
+    double2* __restrict__ w, const double2* __restrict__ V, int64_t stride, const double2* __restrict__ c,
+    const double* __restrict__ ml, int64_t n_int, int n, const int* __restrict__ gate, int accumulate, double eta2,
+    int* __restrict__ reorth, double* __restrict__ partial, unsigned* __restrict__ counter,
+    double2* __restrict__ Hcol) {
+    if (gate && *gate == 0) return;
+    __shared__ double2 s_c[NV + 1];
+    if (int(threadIdx.x) <= NV) s_c[threadIdx.x] = c[threadIdx.x];
+    __syncthreads();
+    double nrm[1] = {0.0};
+    const RowCol rc(n);
+    if (rc.active) {
+        for (int64_t k = int64_t(blockIdx.x) * rc.R + rc.r; k < n_int; k += int64_t(gridDim.x) * rc.R) {
+            const int64_t o = k * n + rc.p;
+            double2 x = w[o];
+            const double m = ml[k];
+            double2 u[NV];
+#pragma unroll
+            for (int i = 0; i < NV; ++i) u[i] = V[i * stride + o];
+#pragma unroll
+            for (int i = 0; i < NV; ++i) {
+                const double2 h = s_c[i];
+                x.x = fma(-h.x, u[i].x, fma(h.y, u[i].y, x.x));
+                x.y = fma(-h.x, u[i].y, fma(-h.y, u[i].x, x.y));
+            }
+            w[o] = x;
+            nrm[0] = fma(m, fma(x.x, x.x, x.y * x.y), nrm[0]);
+        }
+    }
+    block_row_partial<1>(nrm, 1, partial);
+    __shared__ double s_sum[kRedThreads];
+    if (!last_block_sum(partial, 1, counter, s_sum)) return;
     if (threadIdx.x == 0) {
-        partial[2 * blockIdx.x] = sx[0];
-        partial[2 * blockIdx.x + 1] = sy[0];
-    }
-    if (!last_block_sum(partial, 2, counter, sx)) return;
-    if (threadIdx.x == 0) *out = make_double2(sx[0], sx[1]);
-}
-
-// Sum block partials into *out (one thread, fixed order).
-__global__ void sum_partials_kernel(const double2* __restrict__ partial, int nblk, double2* __restrict__ out) {
-    if (threadIdx.x != 0) return;
-    double x = 0.0, y = 0.0;
-    for (int b = 0; b < nblk; ++b) {
-        x += partial[b].x;
-        y += partial[b].y;
-    }
-    *out = make_double2(x, y);
-}
-
-__global__ void cscale_kernel(double2* __restrict__ x, int64_t n, const double2* __restrict__ src, double s,
-                              int sqrt_real_inv) {
-    // x *= s, or x *= 1 / sqrt(Re *src) when sqrt_real_inv
-    double f = s;
-    if (sqrt_real_inv) f = 1.0 / sqrt(src->x);
-    for (int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; o < n; o += int64_t(gridDim.x) * blockDim.x) {
-        x[o].x *= f;
-        x[o].y *= f;
+        for (int i = 0; i < NV; ++i) {
+            const double2 hh = accumulate ? make_double2(Hcol[i].x + s_c[i].x, Hcol[i].y + s_c[i].y) : s_c[i];
+            Hcol[i] = hh;
+        }
+        const double nn = fmax(s_sum[0], 0.0);
+        Hcol[NV] = make_double2(sqrt(nn), 0.0);
+        if (reorth) *reorth = (!accumulate && nn < eta2 * s_c[NV].x) ? 1 : 0;
     }
 }
 
-// phi_out = sum_i y_i V_i
+// dst = src / d over all N*n entries (d = sqrt(*den) when is_sq, else *den),
+// or 0 when d <= 1e-14 beta (Krylov breakdown, beta = sqrt(*beta2)); the
+// complex64 copy v32 is written too when non-null.  src may equal dst.
+__global__ void normalize_kernel(const double2* src, double2* dst, const double2* __restrict__ den, int is_sq,
+                                 const double2* __restrict__ beta2, float2* __restrict__ v32, int64_t total) {
+    const double d = is_sq ? sqrt(fmax(den->x, 0.0)) : den->x;
+    const double beta = sqrt(fmax(beta2->x, 0.0));
+    const double f = (d > 1e-14 * beta && d > 0.0) ? 1.0 / d : 0.0;
+    for (int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; o < total;
+         o += int64_t(gridDim.x) * blockDim.x) {
+        const double2 x = src[o];
+        const double2 y = make_double2(x.x * f, x.y * f);
+        dst[o] = y;
+        if (v32) v32[o] = make_float2(float(y.x), float(y.y));
+    }
+}
+
+// phi_out = scale * sum_{i<m} y_i V_i
 __global__ void combine_kernel(const double2* __restrict__ V, int64_t stride, int m, const double2* __restrict__ y,
-                               int64_t total, double2* __restrict__ out) {
+                               double scale, int64_t total, double2* __restrict__ out) {
+    __shared__ double2 s_y[kMaxKrylov];
+    if (int(threadIdx.x) < m) s_y[threadIdx.x] = make_double2(scale * y[threadIdx.x].x, scale * y[threadIdx.x].y);
+    __syncthreads();
     for (int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; o < total;
          o += int64_t(gridDim.x) * blockDim.x) {
         double x = 0.0, yy = 0.0;
         for (int i = 0; i < m; ++i) {
             const double2 v = V[i * stride + o];
-            const double2 c = y[i];
-            x += c.x * v.x - c.y * v.y;
-            yy += c.x * v.y + c.y * v.x;
+            const double2 c = s_y[i];
+            x = fma(c.x, v.x, fma(-c.y, v.y, x));
+            yy = fma(c.x, v.y, fma(c.y, v.x, yy));
         }
         out[o] = make_double2(x, yy);
     }
 }
 
-// exp(-i dt H) for an m x m complex matrix (m <= kMaxKrylov), one block:
+// exp(-i dt H) for an m x m complex matrix (m <= kMaxKrylov) by one block:
 // scaling and squaring with a truncated Taylor series (the scaled matrix has
 // 1-norm <= 1/2, and 24 terms leave a remainder below 1e-30).
-// H: column-major with leading dimension ldh.  Writes E[m*m] (column-major).
-__global__ void small_expm_kernel(const double2* __restrict__ H, int ldh, int m, double dt,
-                                  double2* __restrict__ E) {
-    __shared__ double2 A[kMaxKrylov * kMaxKrylov], P[kMaxKrylov * kMaxKrylov], S[kMaxKrylov * kMaxKrylov],
-        T[kMaxKrylov * kMaxKrylov];
+// H: column-major with leading dimension ldh.  Leaves the result in S.
+__device__ void block_expm(const double2* __restrict__ H, int ldh, int m, double dt, double2* A, double2* P,
+                           double2* S, double2* T) {
     __shared__ int s_sq;
     const int t = threadIdx.x;
     const int mm = m * m;
@@ -343,7 +459,27 @@ __global__ void small_expm_kernel(const double2* __restrict__ H, int ldh, int m,
         for (int o = t; o < mm; o += blockDim.x) S[o] = T[o];
         __syncthreads();
     }
-    for (int o = t; o < mm; o += blockDim.x) E[o] = S[o];
+}
+
+struct TauLadder {
+    double tau[kLadder];
+};
+
+// Block c evaluates E_c = exp(-i tau_c H_m): writes its first column to
+// col[c][0..m) and err[c].x = |h_{m+1,m}| |E_c[m-1][0]| (the error estimate
+// divided by beta; 0 when exact is set, i.e. after a breakdown).
+__global__ void expm_ladder_kernel(const double2* __restrict__ H, int ldh, int m, TauLadder taus, int exact,
+                                   double2* __restrict__ col, double2* __restrict__ err) {
+    __shared__ double2 A[kMaxKrylov * kMaxKrylov], P[kMaxKrylov * kMaxKrylov], S[kMaxKrylov * kMaxKrylov],
+        T[kMaxKrylov * kMaxKrylov];
+    const int c = blockIdx.x;
+    block_expm(H, ldh, m, taus.tau[c], A, P, S, T);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) col[c * kMaxKrylov + i] = S[i];
+    if (threadIdx.x == 0) {
+        const double2 hs = H[(m - 1) * ldh + m];
+        const double2 e = S[m - 1];
+        err[c] = make_double2(exact ? 0.0 : hypot(hs.x, hs.y) * hypot(e.x, e.y), 0.0);
+    }
 }
 
 // ------------------------------------------------------------------- host
@@ -378,32 +514,105 @@ int to_c64(const double2* x, float2* y, int64_t n, cudaStream_t s) {
 int launch_g_cell32(const afem_mesh* m, const double* E, const float2* v, const float2* U, float2* z, int n,
                     cudaStream_t s);
 
-// Mixed form: the cell pass in complex64 on a complex64 copy of v; projector
-// overlaps, the projection and everything after stay FP64.
-int g_apply32(afem_mesh* m, const double* E, const double2* phi, const float2* U32, int n, const double2* v,
-              ArnoldiWork& w, double2* out, cudaStream_t s) {
-    const DeviceMesh& D = m->dev;
-    int rc = to_c64(v, w.v32, D.n_master * n, s);
-    if (rc) return rc;
-    if ((rc = launch_g_cell32(m, E, w.v32, U32, w.z32, n, s))) return rc;
-    if ((rc = cdot_t<float2>(phi, n, w.z32, n, nullptr, D.n_interior, 0, w.cpartial, w.S, w.counters, s))) return rc;
-    AFEM_LAUNCH((project_kernel<float2>), grid_for(D.n_master * n), 256, 0, s, w.z32, phi, w.S, D.ml_inv,
-                D.n_interior, D.n_master, n, out);
+#define AFEM_NV_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16)
+
+// The Gram-Schmidt kernels for a run-time vector count nv (0 <= nv <= kMaxKrylov).
+static int launch_krylov_dots(int nv, unsigned grid, cudaStream_t s, const double2* w, const double2* V,
+                              int64_t stride, const double* ml, int64_t n_int, int n, const int* gate,
+                              double* partial, unsigned* counter, double2* out) {
+    switch (nv) {
+        case 0:
+            AFEM_LAUNCH((krylov_dots_kernel<0>), grid, kRedThreads, 0, s, w, V, stride, ml, n_int, n, gate, partial,
+                        counter, out);
+            break;
+#define AFEM_DOTS_CASE(NVV)                                                                                   \
+    case NVV:                                                                                                 \
+        AFEM_LAUNCH((krylov_dots_kernel<NVV>), grid, kRedThreads, 0, s, w, V, stride, ml, n_int, n, gate, partial, \
+                    counter, out);                                                                            \
+        break;
+            AFEM_NV_CASES(AFEM_DOTS_CASE)
+#undef AFEM_DOTS_CASE
+        default:
+            return set_error(AFEM_EINVAL, "arnoldi: Krylov vector count out of range");
+    }
     AFEM_CUDA_TRY(cudaGetLastError());
     return AFEM_OK;
 }
 
-int g_apply(afem_mesh* m, const double* E, const double2* phi, const double2* U, int n, const double2* v,
-            double2* z, double2* out, ArnoldiWork& w, cudaStream_t s) {
-    const DeviceMesh& D = m->dev;
-    int rc = launch_g_cell(m, E, v, U, z, n, s);
-    if (rc) return rc;
-    // S[j][p] = phi_j^H z_p  (equals phi_j^H M_L y_p)
-    if ((rc = cdot(phi, n, z, n, nullptr, D.n_interior, 0, w.cpartial, w.S, w.counters, s))) return rc;
-    AFEM_LAUNCH((project_kernel<double2>), grid_for(D.n_master * n), 256, 0, s, z, phi, w.S, D.ml_inv, D.n_interior, D.n_master, n,
-                                                            out);
+// The projector of G on the cell-pass output fused with the inner products
+// against V_0..V_{nv-1}: complex64 z (precision form, phi32) or complex128 z.
+static int launch_project_dots(int nv, unsigned grid, cudaStream_t s, const float2* z32, const float2* phi32,
+                               const double2* z, const double2* phi, const double2* S, const DeviceMesh& D, int n,
+                               double2* w, const double2* V, int64_t stride, double* partial, unsigned* counter,
+                               double2* out) {
+    switch (nv) {
+#define AFEM_PD_CASE(NVV)                                                                                           \
+    case NVV:                                                                                                       \
+        if (z32) {                                                                                                  \
+            AFEM_LAUNCH((project32_dots_kernel<NVV>), grid, kRedThreads, 0, s, z32, phi32, S, D.ml_inv, D.ml,      \
+                        D.n_interior, D.n_master, n, w, V, stride, partial, counter, out);                          \
+        } else {                                                                                                    \
+            AFEM_LAUNCH((project_dots_kernel<NVV>), grid, kRedThreads, 0, s, z, phi, S, D.ml_inv, D.ml,            \
+                        D.n_interior, D.n_master, n, w, V, stride, partial, counter, out);                          \
+        }                                                                                                           \
+        break;
+        AFEM_NV_CASES(AFEM_PD_CASE)
+#undef AFEM_PD_CASE
+        default:
+            return set_error(AFEM_EINVAL, "arnoldi: Krylov vector count out of range");
+    }
     AFEM_CUDA_TRY(cudaGetLastError());
     return AFEM_OK;
+}
+
+static int launch_krylov_update(int nv, unsigned grid, cudaStream_t s, double2* w, const double2* V,
+                                int64_t stride, const double2* c, const double* ml, int64_t n_int, int n,
+                                const int* gate, int accumulate, double eta2, int* reorth, double* partial,
+                                unsigned* counter, double2* Hcol) {
+    switch (nv) {
+#define AFEM_UPD_CASE(NVV)                                                                                      \
+    case NVV:                                                                                                   \
+        AFEM_LAUNCH((krylov_update_kernel<NVV>), grid, kRedThreads, 0, s, w, V, stride, c, ml, n_int, n, gate,  \
+                    accumulate, eta2, reorth, partial, counter, Hcol);                                          \
+        break;
+        AFEM_NV_CASES(AFEM_UPD_CASE)
+#undef AFEM_UPD_CASE
+        default:
+            return set_error(AFEM_EINVAL, "arnoldi: Krylov vector count out of range");
+    }
+    AFEM_CUDA_TRY(cudaGetLastError());
+    return AFEM_OK;
+}
+
+static unsigned rowcol_grid(int64_t rows, int n) {
+    const int64_t R = kRedThreads / n;
+    int64_t g = (rows + R - 1) / R;
+    if (g < 1) g = 1;
+    if (g > kRedBlocks) g = kRedBlocks;
+    return unsigned(g);
+}
+
+// The cell pass of G and the projector overlaps S[j][p] = phi_j^H z_p (equal to
+// phi_j^H M_L y_p); the projector itself runs fused with the first
+// Gram-Schmidt pass.  Precision form: the cell pass in complex64 from v32 (the
+// complex64 copy of the vector) and the overlaps from phi32.
+static int g_cell_overlaps32(afem_mesh* m, const double* E, const float2* phi32, const float2* U32, int n,
+                             const float2* v32, ArnoldiWork& w, cudaStream_t s) {
+    const DeviceMesh& D = m->dev;
+    int rc;
+    if ((rc = launch_g_cell32(m, E, v32, U32, w.z32, n, s))) return rc;
+    AFEM_LAUNCH((overlap32_kernel), kRedBlocks, kRedThreads, 0, s, phi32, w.z32, D.n_interior, n,
+                reinterpret_cast<double*>(w.cpartial), w.counters, w.S);
+    AFEM_CUDA_TRY(cudaGetLastError());
+    return AFEM_OK;
+}
+
+static int g_cell_overlaps(afem_mesh* m, const double* E, const double2* phi, const double2* U, int n,
+                           const double2* v, ArnoldiWork& w, cudaStream_t s) {
+    const DeviceMesh& D = m->dev;
+    int rc = launch_g_cell(m, E, v, U, w.z, n, s);
+    if (rc) return rc;
+    return cdot(phi, n, w.z, n, nullptr, D.n_interior, 0, w.cpartial, w.S, w.counters, s);
 }
 
 int arnoldi_reserve(afem_mesh* m, int n, int mk, ArnoldiWork& w) {
@@ -412,15 +621,16 @@ int arnoldi_reserve(afem_mesh* m, int n, int mk, ArnoldiWork& w) {
         w.V = cv.take<double2>(size_t(mk + 1) * NV);
         w.z = cv.take<double2>(NV);
         w.cpartial = cv.take<double2>(size_t(kRedBlocks) * 256);
-        w.S = cv.take<double2>(64);
-        w.H = cv.take<double2>(size_t(kMaxKrylov + 1) * kMaxKrylov);
-        w.E = cv.take<double2>(kMaxKrylov * kMaxKrylov);
-        w.y = cv.take<double2>(kMaxKrylov);
-        w.beta2 = cv.take<double2>(1);
+        w.S = cv.take<double2>(kMaxOrbProj * kMaxOrbProj);
+        w.res = cv.take<double2>(kResSize);
+        w.c1 = cv.take<double2>(kMaxKrylov + 1);
+        w.c2 = cv.take<double2>(kMaxKrylov + 1);
         w.v32 = cv.take<float2>(NV);
         w.z32 = cv.take<float2>(NV);
+        w.phi32 = cv.take<float2>(NV);
         w.U32 = cv.take<float2>(NV * n);
         w.counters = cv.take<unsigned>(4);
+        w.flag = cv.take<int>(4);
     };
     Carver measure(nullptr);
     carve(measure);
@@ -429,114 +639,158 @@ int arnoldi_reserve(afem_mesh* m, int n, int mk, ArnoldiWork& w) {
     Carver cv(m->ws_arnoldi.ptr);
     carve(cv);
     w.stride = int64_t(NV);
+    w.H = w.res + kResH;
+    w.beta2 = w.res + kResBeta2;
+    w.col = w.res + kResCol;
+    w.err = w.res + kResErr;
     return AFEM_OK;
+}
+
+// Candidate substep lengths of one ladder: tau_max * 2^(-c/2), c = 0..K-1.
+static TauLadder make_ladder(double tau_max, int K) {
+    TauLadder L{};
+    for (int c = 0; c < kLadder; ++c) L.tau[c] = c < K ? tau_max * std::pow(2.0, -0.5 * c) : 0.0;
+    return L;
 }
 
 // Propagates phi by exp(-i G dt) with G frozen at phi (projector), U and E.
 // tol <= 0: one Krylov step of dimension mk over the whole dt.  tol > 0:
-// substeps tau chosen so that each substep's error estimate
-// beta |h_{m+1,m}| |e_m^T exp(-i tau H_m) e_1| stays below tol * beta (the
-// paper fixes the Krylov accuracy by such an estimate; here the dimension is
-// fixed and the substep adapts), each from a fresh Krylov space of the same G.
+// substeps from fresh Krylov spaces of the same G, each as long as the error
+// estimate beta |h_{m+1,m}| |e_m^T exp(-i tau H_m) e_1| <= tol * beta allows
+// among the candidates tau_max 2^(-c/2), c = 0..15, where tau_max is the
+// remainder for the first substep and min(remainder, 2 tau_previous) after
+// it; when no candidate passes, the ladder continues below the smallest one
+// (the paper fixes the Krylov accuracy by such an estimate; here the
+// dimension is fixed and the substep adapts).
 int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double2* U, const float2* U32, int n,
                  int mk, double dt, int mixed, double tol, double2* phi_out, double* err_est, int* m_used_out,
                  int* breakdown_out, int* substeps_out, cudaStream_t s) {
     const DeviceMesh& D = m->dev;
+    if (mk < 1 || mk > kMaxKrylov) return set_error(AFEM_EINVAL, "arnoldi: krylov_m out of range");
+    if (n < 1 || n > kMaxOrbProj) return set_error(AFEM_EINVAL, "arnoldi: orbital count out of range");
     ArnoldiWork w{};
     int rc = arnoldi_reserve(m, n, mk, w);
     if (rc) return rc;
-    if (mixed && U && !U32) {
-        if ((rc = to_c64(U, w.U32, D.n_master * n * n, s))) return rc;
-        U32 = w.U32;
+    const int64_t NV = w.stride;
+    if (mixed) {
+        if (U && !U32) {
+            if ((rc = to_c64(U, w.U32, D.n_master * n * n, s))) return rc;
+            U32 = w.U32;
+        }
+        if ((rc = to_c64(phi, w.phi32, NV, s))) return rc;
     }
     AFEM_CUDA_TRY(cudaMemsetAsync(w.counters, 0, 4 * sizeof(unsigned), s));
-    const int64_t NV = w.stride;
+    AFEM_CUDA_TRY(cudaMemsetAsync(w.flag, 0, 4 * sizeof(int), s));
     const int ldh = kMaxKrylov + 1;
+    const unsigned gdots = rowcol_grid(D.n_interior, n);
+    const unsigned gproj = rowcol_grid(D.n_master, n);
+    double* part = reinterpret_cast<double*>(w.cpartial);
+    unsigned* cnt = w.counters + 1;
+    const double eta2 = 1e-4;   // second pass when the update left less than 1e-2 of the norm
     const double2* src = phi;
-    double remaining = dt;
+    double remaining = dt, tau_prev = 0.0;
     double err_sum = 0.0;
     int substeps = 0, m_used = mk, brk = 0;
-    std::vector<double2> Eh(size_t(kMaxKrylov) * kMaxKrylov);
+    std::vector<double2> res(kResSize);
+    auto fetch = [&]() -> int {
+        AFEM_CUDA_TRY(cudaMemcpyAsync(res.data(), w.res, kResSize * sizeof(double2), cudaMemcpyDeviceToHost, s));
+        AFEM_CUDA_TRY(cudaStreamSynchronize(s));
+        return AFEM_OK;
+    };
     while (remaining > 0.0) {
         if (substeps >= 4096) return set_error(AFEM_EINVAL, "arnoldi: more than 4096 substeps (tolerance too tight)");
         AFEM_CUDA_TRY(cudaMemsetAsync(w.H, 0, sizeof(double2) * ldh * kMaxKrylov, s));
         // beta^2 = <src, src>_M ; V_0 = src / beta
-        AFEM_LAUNCH((mgs_fused_kernel), kRedBlocks, kRedThreads, 0, s, const_cast<double2*>(src), nullptr, nullptr,
-                    nullptr, D.ml, D.n_interior, n, reinterpret_cast<double*>(w.cpartial), w.counters + 1, w.beta2);
-        AFEM_CUDA_TRY(cudaMemcpyAsync(w.V, src, NV * sizeof(double2), cudaMemcpyDeviceToDevice, s));
-        AFEM_LAUNCH((cscale_kernel), grid_for(NV), 256, 0, s, w.V, NV, w.beta2, 1.0, 1);
-        AFEM_CUDA_TRY(cudaGetLastError());
-        double2 beta2_h;
-        AFEM_CUDA_TRY(cudaMemcpyAsync(&beta2_h, w.beta2, sizeof(double2), cudaMemcpyDeviceToHost, s));
-        AFEM_CUDA_TRY(cudaStreamSynchronize(s));
-        const double beta = std::sqrt(beta2_h.x);
-        if (!(beta > 0.0) || !std::isfinite(beta)) return set_error(AFEM_ENAN, "arnoldi: zero or non-finite norm");
-        m_used = mk;
-        brk = 0;
-        double hlast = 0.0;
+        if ((rc = launch_krylov_dots(0, gdots, s, src, nullptr, NV, D.ml, D.n_interior, n, nullptr, part, cnt,
+                                     w.beta2)))
+            return rc;
+        AFEM_LAUNCH((normalize_kernel), grid_for(NV), 256, 0, s, src, w.V, w.beta2, 1, w.beta2,
+                    mixed ? w.v32 : nullptr, NV);
         for (int j = 0; j < mk; ++j) {
             double2* Vj = w.V + j * NV;
             double2* Wn = w.V + (j + 1) * NV;
+            double2* Hcol = w.H + j * ldh;
+            if (j > 0)   // V_j = w_j / h_{j,j-1}
+                AFEM_LAUNCH((normalize_kernel), grid_for(NV), 256, 0, s, Vj, Vj, w.H + (j - 1) * ldh + j, 0, w.beta2,
+                            mixed ? w.v32 : nullptr, NV);
+            // w = G V_j with the inner products against V_0..V_j, the update, and
+            // a second pass when the update cancelled most of w
             if (mixed) {
-                if ((rc = g_apply32(m, E, phi, U32, n, Vj, w, Wn, s))) return rc;
+                if ((rc = g_cell_overlaps32(m, E, w.phi32, U32, n, w.v32, w, s))) return rc;
             } else {
-                if ((rc = g_apply(m, E, phi, U, n, Vj, w.z, Wn, w, s))) return rc;
+                if ((rc = g_cell_overlaps(m, E, phi, U, n, Vj, w, s))) return rc;
             }
-            // modified Gram-Schmidt against V_0..V_j
-            for (int i = 0; i <= j; ++i) {
-                const double2* Vprev = i > 0 ? w.V + (i - 1) * NV : nullptr;
-                const double2* hprev = i > 0 ? w.H + j * ldh + (i - 1) : nullptr;
-                AFEM_LAUNCH((mgs_fused_kernel), kRedBlocks, kRedThreads, 0, s, Wn, Vprev, hprev, w.V + i * NV, D.ml,
-                            D.n_interior, n, reinterpret_cast<double*>(w.cpartial), w.counters + 1,
-                            w.H + j * ldh + i);
-            }
-            // last update and the norm
-            AFEM_LAUNCH((mgs_fused_kernel), kRedBlocks, kRedThreads, 0, s, Wn, w.V + j * NV, w.H + j * ldh + j,
-                        nullptr, D.ml, D.n_interior, n, reinterpret_cast<double*>(w.cpartial), w.counters + 1,
-                        w.beta2);
-            AFEM_CUDA_TRY(cudaGetLastError());
-            double2 nn2;
-            AFEM_CUDA_TRY(cudaMemcpyAsync(&nn2, w.beta2, sizeof(double2), cudaMemcpyDeviceToHost, s));
-            AFEM_CUDA_TRY(cudaStreamSynchronize(s));
-            const double hn = std::sqrt(std::fmax(nn2.x, 0.0));
+            if ((rc = launch_project_dots(j + 1, gproj, s, mixed ? w.z32 : nullptr, w.phi32, w.z, phi, w.S, D, n, Wn,
+                                          w.V, NV, part, cnt, w.c1)) ||
+                (rc = launch_krylov_update(j + 1, gdots, s, Wn, w.V, NV, w.c1, D.ml, D.n_interior, n, nullptr, 0,
+                                           eta2, w.flag, part, cnt, Hcol)) ||
+                (rc = launch_krylov_dots(j + 1, gdots, s, Wn, w.V, NV, D.ml, D.n_interior, n, w.flag, part, cnt,
+                                         w.c2)) ||
+                (rc = launch_krylov_update(j + 1, gdots, s, Wn, w.V, NV, w.c2, D.ml, D.n_interior, n, w.flag, 1,
+                                           eta2, nullptr, part, cnt, Hcol)))
+                return rc;
+        }
+        // candidate substeps, one block each; a single host wait per ladder
+        double tau_max = (tol <= 0.0 || substeps == 0) ? remaining : std::fmin(remaining, 2.0 * tau_prev);
+        int K = tol <= 0.0 ? 1 : kLadder;
+        int exact = 0;
+        AFEM_LAUNCH((expm_ladder_kernel), K, 256, 0, s, w.H, ldh, mk, make_ladder(tau_max, K), 0, w.col, w.err);
+        AFEM_CUDA_TRY(cudaGetLastError());
+        if ((rc = fetch())) return rc;
+        const double beta = std::sqrt(res[kResBeta2].x);
+        if (!(beta > 0.0) || !std::isfinite(beta)) return set_error(AFEM_ENAN, "arnoldi: zero or non-finite norm");
+        m_used = mk;
+        brk = 0;
+        for (int j = 0; j < mk; ++j) {
+            const double hn = res[kResH + j * ldh + j + 1].x;
             if (!std::isfinite(hn)) return set_error(AFEM_ENAN, "arnoldi: non-finite Krylov vector");
-            const double2 hv = make_double2(hn, 0.0);
-            AFEM_CUDA_TRY(cudaMemcpyAsync(w.H + j * ldh + (j + 1), &hv, sizeof(double2), cudaMemcpyHostToDevice, s));
-            hlast = hn;
             if (hn < 1e-14 * beta) {
                 m_used = j + 1;
                 brk = 1;
                 break;
             }
-            AFEM_LAUNCH((cscale_kernel), grid_for(NV), 256, 0, s, Wn, NV, nullptr, 1.0 / hn, 0);
-            AFEM_CUDA_TRY(cudaGetLastError());
         }
-        // substep length: the whole remainder, or shortened until the estimate meets tol
-        double tau = remaining, err = 0.0;
-        for (int tries = 0;; ++tries) {
-            AFEM_LAUNCH((small_expm_kernel), 1, 256, 0, s, w.H, ldh, m_used, tau, w.E);
+        if (brk) {   // invariant subspace: the projected exponential is exact
+            tau_max = remaining;
+            K = 1;
+            exact = 1;
+            AFEM_LAUNCH((expm_ladder_kernel), 1, 256, 0, s, w.H, ldh, m_used, make_ladder(tau_max, 1), 1, w.col,
+                        w.err);
             AFEM_CUDA_TRY(cudaGetLastError());
-            AFEM_CUDA_TRY(cudaMemcpyAsync(Eh.data(), w.E, size_t(m_used) * m_used * sizeof(double2),
-                                          cudaMemcpyDeviceToHost, s));
-            AFEM_CUDA_TRY(cudaStreamSynchronize(s));
-            const double2 em = Eh[m_used - 1];
-            err = brk ? 0.0 : beta * hlast * std::hypot(em.x, em.y);
-            if (tol <= 0.0 || brk || err <= tol * beta || tries >= 40) break;
-            const double shrink = 0.9 * std::pow(tol * beta / err, 1.0 / m_used);
-            tau *= std::fmin(0.5, std::fmax(shrink, 0.05));
+            if ((rc = fetch())) return rc;
         }
+        int pick = -1;
+        for (int round = 0;; ++round) {
+            for (int c = 0; c < K; ++c) {
+                if (exact || tol <= 0.0 || res[kResErr + c].x <= tol) {
+                    pick = c;
+                    break;
+                }
+            }
+            if (pick >= 0) break;
+            if (round >= 8) {   // accept the smallest candidate
+                pick = K - 1;
+                break;
+            }
+            tau_max *= std::pow(2.0, -0.5 * K);
+            AFEM_LAUNCH((expm_ladder_kernel), K, 256, 0, s, w.H, ldh, m_used, make_ladder(tau_max, K), 0, w.col,
+                        w.err);
+            AFEM_CUDA_TRY(cudaGetLastError());
+            if ((rc = fetch())) return rc;
+        }
+        const double tau = make_ladder(tau_max, K).tau[pick];
+        const double err = beta * res[kResErr + pick].x;
         // phi_out = beta V_m exp(-i tau H_m) e_1
-        std::vector<double2> yh(m_used);
-        for (int i = 0; i < m_used; ++i) yh[i] = make_double2(beta * Eh[i].x, beta * Eh[i].y);
-        AFEM_CUDA_TRY(cudaMemcpyAsync(w.y, yh.data(), m_used * sizeof(double2), cudaMemcpyHostToDevice, s));
-        AFEM_LAUNCH((combine_kernel), grid_for(NV), 256, 0, s, w.V, NV, m_used, w.y, NV, phi_out);
+        AFEM_LAUNCH((combine_kernel), grid_for(NV), 256, 0, s, w.V, NV, m_used, w.col + pick * kMaxKrylov, beta, NV,
+                    phi_out);
         AFEM_CUDA_TRY(cudaGetLastError());
-        AFEM_CUDA_TRY(cudaStreamSynchronize(s));
         err_sum += err;
         ++substeps;
+        tau_prev = tau;
         remaining = (tau >= remaining) ? 0.0 : remaining - tau;
         src = phi_out;
     }
+    AFEM_CUDA_TRY(cudaStreamSynchronize(s));
     if (err_est) *err_est = err_sum;
     if (m_used_out) *m_used_out = m_used;
     if (breakdown_out) *breakdown_out = brk;

@@ -7,20 +7,36 @@
 namespace afem {
 
 constexpr int kMaxKrylov = 16;
+constexpr int kLadder = 16;   // candidate substep lengths evaluated per ladder
+constexpr int kMaxOrbProj = 8;   // orbitals (the C ABI accepts 1..8)
+
+// Small results the host reads once per substep, contiguous in device memory:
+// the Hessenberg matrix, beta^2, the first columns of the candidate
+// exponentials and their error estimates (over beta, in .x).
+constexpr int kResH = 0;
+constexpr int kResBeta2 = (kMaxKrylov + 1) * kMaxKrylov;
+constexpr int kResCol = kResBeta2 + 1;
+constexpr int kResErr = kResCol + kLadder * kMaxKrylov;
+constexpr int kResSize = kResErr + kLadder;
 
 struct ArnoldiWork {
     double2* V;          // [m+1][N][n] Krylov basis
     double2* z;          // [N][n] cell-pass output
     double2* cpartial;   // reduction partials
     double2* S;          // [n][n] projector overlaps
-    double2* H;          // (kMaxKrylov+1) x kMaxKrylov Hessenberg, column-major
-    double2* E;          // exp(-i dt H_m)
-    double2* y;          // beta E e_1
-    double2* beta2;      // scalar scratch
+    double2* res;        // kResSize small results (below)
+    double2* H;          // (kMaxKrylov+1) x kMaxKrylov Hessenberg, column-major (in res)
+    double2* beta2;      // <phi, phi>_M of the substep's start vector (in res)
+    double2* col;        // [kLadder][kMaxKrylov] first columns of exp(-i tau_c H_m) (in res)
+    double2* err;        // [kLadder] error estimates over beta (in res)
+    double2* c1;         // inner products and norm of the first Gram-Schmidt pass
+    double2* c2;         // the same for the second pass
     float2* v32;         // [N][n] complex64 copy of the vector G is applied to (mixed form)
     float2* z32;         // [N][n] complex64 cell-pass output (mixed form)
+    float2* phi32;       // [N][n] complex64 copy of the frozen orbitals (mixed-form projector)
     float2* U32;         // [N][n][n] complex64 mean-field fields (mixed form)
     unsigned* counters;  // last-block reduction counters (zeroed per call)
+    int* flag;           // second-pass flag
     int64_t stride;      // N * n
 };
 

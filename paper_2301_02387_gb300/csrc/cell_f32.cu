@@ -471,7 +471,7 @@ static int launch32v(const afem_mesh* m, const CellArgs32& a, const float* x, co
     if (grid == 0) return AFEM_OK;
     const float4* x4 = reinterpret_cast<const float4*>(x);
     float4* y4 = reinterpret_cast<float4*>(y);
-    if (m->cell32_variant == 0) {
+    if (m->cell32_variant == 1) {
         const size_t smemL =
             2 * size_t(nn) * L4 * sizeof(float4) + ((G && U) ? size_t(nn) * n * n * sizeof(float2) : 0);
         switch (p) {

@@ -304,22 +304,6 @@ struct PcgState {
     double rtol2;
 };
 
-// Column partial sums of a*b over interior rows: partial[block][c].
-__global__ void col_dot_kernel(const double* __restrict__ a, const double* __restrict__ b, int64_t n, int k,
-                               double* __restrict__ partial) {
-    __shared__ double s[kRedThreads];
-    const int R = kRedThreads / k, used = R * k;
-    const int t = threadIdx.x;
-    double acc = 0.0;
-    if (t < used) {
-        const int c = t % k, r = t / k;
-        for (int64_t i = int64_t(blockIdx.x) * R + r; i < n; i += int64_t(gridDim.x) * R)
-            acc = fma(a[i * k + c], b[i * k + c], acc);
-    }
-    s[t] = acc;
-    reduce_columns(s, k, R, partial + int64_t(blockIdx.x) * k);
-}
-
 // r = b - t - Ap0 (interior rows), z = Dinv r, p = z; partials of (b-t)^2, r.z, r.r.
 __global__ void pcg_init_kernel(const double* __restrict__ b, const double* __restrict__ t,
                                 const double* __restrict__ Ax, const double* __restrict__ dinv,
@@ -377,80 +361,6 @@ __global__ void pcg_init_finalize_kernel(const double* __restrict__ partial, int
     }
     __syncthreads();
     if (threadIdx.x == 0) *st.n_active = cnt;
-}
-
-__global__ void pcg_alpha_kernel(const double* __restrict__ partial, int nblk, int k, PcgState st) {
-    for (int c = threadIdx.x; c < k; c += blockDim.x) {
-        double pAp = 0.0;
-        for (int b = 0; b < nblk; ++b) pAp += partial[int64_t(b) * k + c];
-        st.alpha[c] = (st.active[c] && pAp > 0.0) ? st.rz[c] / pAp : 0.0;
-    }
-}
-
-// x += alpha p, r -= alpha Ap, z = Dinv r; partials of r.z and r.r.
-__global__ void pcg_update_kernel(double* __restrict__ x, double* __restrict__ r, double* __restrict__ z,
-                                  const double* __restrict__ p, const double* __restrict__ Ap,
-                                  const double* __restrict__ dinv, int64_t n, int k, PcgState st,
-                                  double* __restrict__ partial /*[blk][2k]*/) {
-    __shared__ double s[kRedThreads];
-    const int R = kRedThreads / k, used = R * k;
-    const int tid = threadIdx.x;
-    double arz = 0.0, arr = 0.0;
-    if (tid < used) {
-        const int c = tid % k, rr0 = tid / k;
-        const double al = st.alpha[c];
-        for (int64_t i = int64_t(blockIdx.x) * R + rr0; i < n; i += int64_t(gridDim.x) * R) {
-            const int64_t o = i * k + c;
-            x[o] = fma(al, p[o], x[o]);
-            const double ri = fma(-al, Ap[o], r[o]);
-            const double zi = dinv[i] * ri;
-            r[o] = ri;
-            z[o] = zi;
-            arz = fma(ri, zi, arz);
-            arr = fma(ri, ri, arr);
-        }
-    }
-    double* out = partial + int64_t(blockIdx.x) * 2 * k;
-    s[tid] = arz;
-    reduce_columns(s, k, R, out);
-    __syncthreads();
-    s[tid] = arr;
-    reduce_columns(s, k, R, out + k);
-}
-
-__global__ void pcg_beta_kernel(const double* __restrict__ partial, int nblk, int k, PcgState st) {
-    __shared__ int cnt;
-    if (threadIdx.x == 0) cnt = 0;
-    __syncthreads();
-    for (int c = threadIdx.x; c < k; c += blockDim.x) {
-        double rz = 0.0, rr = 0.0;
-        for (int b = 0; b < nblk; ++b) {
-            rz += partial[int64_t(b) * 2 * k + c];
-            rr += partial[int64_t(b) * 2 * k + k + c];
-        }
-        if (st.active[c]) {
-            st.beta[c] = st.rz[c] != 0.0 ? rz / st.rz[c] : 0.0;
-            st.rz[c] = rz;
-            st.rr[c] = rr;
-            if (!(rr > st.rtol2 * st.bb[c])) st.active[c] = 0;
-            if (!isfinite(rr)) st.active[c] = 0;
-        } else {
-            st.beta[c] = 0.0;
-        }
-        if (st.active[c]) atomicAdd(&cnt, 1);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) *st.n_active = cnt;
-}
-
-__global__ void pcg_p_kernel(double* __restrict__ p, const double* __restrict__ z, int64_t n, int k,
-                             PcgState st) {
-    const int64_t total = n * k;
-    for (int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; o < total;
-         o += int64_t(gridDim.x) * blockDim.x) {
-        const int c = int(o % k);
-        if (st.active[c]) p[o] = fma(st.beta[c], p[o], z[o]);
-    }
 }
 
 // ---- fused CG kernels: block partials + last-block finalize (alpha or beta)
@@ -536,6 +446,191 @@ __global__ void update_beta_kernel(T* __restrict__ x, T* __restrict__ r, const T
     if (tid == 0) {
         if (rr_upd) flags[1] = s_cnt;
         else *st.n_active = s_cnt;
+    }
+}
+
+// ---- float32 CG kernels on four columns per thread (k % 4 == 0): thread t <
+// (k/4) R of a 256-thread block owns the column quad q = t % (k/4) of rows
+// r = t / (k/4), r + R, ... (R = 1024 / k), loaded as float4.  Per-column
+// sums go through s[r k + c] (R k = 1024 entries), the layout reduce_columns
+// reads.
+// GB300 issues FP64 at about 1/64 of its FP32 rate, so the per-element
+// products of these kernels stay in FP32: runs of kRun rows are summed in
+// FP32 and only the run sums in FP64 (random rounding of about 1e-7 per run;
+// the CG scalars are formed from the FP64 totals).
+constexpr int kRun = 16;
+
+struct Quad {
+    int q, r, R, kq;
+    bool active;
+    __device__ __forceinline__ Quad(int k) {
+        kq = k >> 2;
+        R = kRedThreads / kq;
+        active = int(threadIdx.x) < kq * R;
+        r = active ? int(threadIdx.x) / kq : 0;
+        q = active ? int(threadIdx.x) - r * kq : 0;
+    }
+};
+
+__global__ void __launch_bounds__(kRedThreads) dot_alpha4_kernel(const float4* __restrict__ p,
+                                                                 const float4* __restrict__ Ap, int64_t n, int k,
+                                                                 double* __restrict__ partial,
+                                                                 unsigned* __restrict__ counter, PcgState st) {
+    __shared__ double s[4 * kRedThreads];
+    const Quad qd(k);
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    if (qd.active) {
+        const int64_t step = int64_t(gridDim.x) * qd.R;
+        int64_t i = int64_t(blockIdx.x) * qd.R + qd.r;
+        while (i < n) {   // runs of kRun rows summed in FP32, the runs in FP64
+            float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f;
+            for (int run = 0; run < kRun && i < n; ++run, i += step) {
+                const float4 u = p[i * qd.kq + qd.q], v = Ap[i * qd.kq + qd.q];
+                f0 = fmaf(u.x, v.x, f0);
+                f1 = fmaf(u.y, v.y, f1);
+                f2 = fmaf(u.z, v.z, f2);
+                f3 = fmaf(u.w, v.w, f3);
+            }
+            a0 += double(f0);
+            a1 += double(f1);
+            a2 += double(f2);
+            a3 += double(f3);
+        }
+    }
+    const int t = threadIdx.x;
+    s[4 * t] = a0;
+    s[4 * t + 1] = a1;
+    s[4 * t + 2] = a2;
+    s[4 * t + 3] = a3;
+    reduce_columns(s, k, qd.R, partial + int64_t(blockIdx.x) * k);
+    if (!last_block_sum(partial, k, counter, s)) return;
+    for (int c = t; c < k; c += blockDim.x) {
+        const double pAp = s[c];
+        st.alpha[c] = (st.active[c] && pAp > 0.0) ? st.rz[c] / pAp : 0.0;
+    }
+}
+
+// beta, rz, rr from the column sums s[c] = r.(Dinv r), s[k + c] = r.r, and the
+// reliable-update count or the retirement of converged columns (last block).
+__device__ __forceinline__ void cg_beta_finalize(const double* s, int k, PcgState st, const double* scale,
+                                                 const double* rr_upd, const double* bb64, double rtol2, double delta2,
+                                                 int* flags) {
+    __shared__ int s_cnt;
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        const double rz = s[c], rr = s[k + c];
+        if (st.active[c]) {
+            st.beta[c] = st.rz[c] != 0.0 ? rz / st.rz[c] : 0.0;
+            st.rz[c] = rz;
+            st.rr[c] = rr;
+            if (rr_upd) {
+                const bool due = !(rr >= delta2 * rr_upd[c]) || scale[c] * scale[c] * rr <= rtol2 * bb64[c];
+                if (due) atomicAdd(&s_cnt, 1);
+            } else {
+                if (!(rr > st.rtol2 * st.bb[c]) || !isfinite(rr)) st.active[c] = 0;
+                if (st.active[c]) atomicAdd(&s_cnt, 1);
+            }
+        } else {
+            st.beta[c] = 0.0;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (rr_upd) flags[1] = s_cnt;
+        else *st.n_active = s_cnt;
+    }
+}
+
+// update_beta_kernel<float> on column quads.
+__global__ void __launch_bounds__(kRedThreads) update_beta4_kernel(
+    float4* __restrict__ x, float4* __restrict__ r, const float4* __restrict__ p, const float4* __restrict__ Ap,
+    const float* __restrict__ dinv, int64_t n, int k, PcgState st, double* __restrict__ partial,
+    unsigned* __restrict__ counter, const double* __restrict__ scale, const double* __restrict__ rr_upd,
+    const double* __restrict__ bb64, double rtol2, double delta2, int* __restrict__ flags) {
+    __shared__ double s[4 * kRedThreads];
+    const Quad qd(k);
+    double z0 = 0.0, z1 = 0.0, z2 = 0.0, z3 = 0.0, r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0;
+    if (qd.active) {
+        const int c0 = 4 * qd.q;
+        const float al0 = float(st.alpha[c0]), al1 = float(st.alpha[c0 + 1]), al2 = float(st.alpha[c0 + 2]),
+                    al3 = float(st.alpha[c0 + 3]);
+        const int64_t step = int64_t(gridDim.x) * qd.R;
+        int64_t i = int64_t(blockIdx.x) * qd.R + qd.r;
+        while (i < n) {   // runs of kRun rows summed in FP32, the runs in FP64
+            float fz0 = 0.f, fz1 = 0.f, fz2 = 0.f, fz3 = 0.f, fr0 = 0.f, fr1 = 0.f, fr2 = 0.f, fr3 = 0.f;
+            for (int run = 0; run < kRun && i < n; ++run, i += step) {
+                const int64_t o = i * qd.kq + qd.q;
+                const float4 pv = p[o], av = Ap[o];
+                float4 xv = x[o], rv = r[o];
+                const float d = dinv[i];
+                xv.x = xv.x + al0 * pv.x;
+                xv.y = xv.y + al1 * pv.y;
+                xv.z = xv.z + al2 * pv.z;
+                xv.w = xv.w + al3 * pv.w;
+                rv.x = rv.x - al0 * av.x;
+                rv.y = rv.y - al1 * av.y;
+                rv.z = rv.z - al2 * av.z;
+                rv.w = rv.w - al3 * av.w;
+                x[o] = xv;
+                r[o] = rv;
+                fz0 = fmaf(rv.x, d * rv.x, fz0);
+                fz1 = fmaf(rv.y, d * rv.y, fz1);
+                fz2 = fmaf(rv.z, d * rv.z, fz2);
+                fz3 = fmaf(rv.w, d * rv.w, fz3);
+                fr0 = fmaf(rv.x, rv.x, fr0);
+                fr1 = fmaf(rv.y, rv.y, fr1);
+                fr2 = fmaf(rv.z, rv.z, fr2);
+                fr3 = fmaf(rv.w, rv.w, fr3);
+            }
+            z0 += double(fz0);
+            z1 += double(fz1);
+            z2 += double(fz2);
+            z3 += double(fz3);
+            r0 += double(fr0);
+            r1 += double(fr1);
+            r2 += double(fr2);
+            r3 += double(fr3);
+        }
+    }
+    const int t = threadIdx.x;
+    double* out = partial + int64_t(blockIdx.x) * 2 * k;
+    s[4 * t] = z0;
+    s[4 * t + 1] = z1;
+    s[4 * t + 2] = z2;
+    s[4 * t + 3] = z3;
+    reduce_columns(s, k, qd.R, out);
+    __syncthreads();
+    s[4 * t] = r0;
+    s[4 * t + 1] = r1;
+    s[4 * t + 2] = r2;
+    s[4 * t + 3] = r3;
+    reduce_columns(s, k, qd.R, out + k);
+    if (!last_block_sum(partial, 2 * k, counter, s)) return;
+    cg_beta_finalize(s, k, st, scale, rr_upd, bb64, rtol2, delta2, flags);
+}
+
+// p = Dinv r + beta p (active columns) on column quads.
+__global__ void __launch_bounds__(kRedThreads) p_update4_kernel(float4* __restrict__ p, const float4* __restrict__ r,
+                                                                const float* __restrict__ dinv, int64_t n, int k,
+                                                                PcgState st) {
+    const Quad qd(k);
+    if (!qd.active) return;
+    const int c0 = 4 * qd.q;
+    const bool a0 = st.active[c0], a1 = st.active[c0 + 1], a2 = st.active[c0 + 2], a3 = st.active[c0 + 3];
+    if (!(a0 || a1 || a2 || a3)) return;
+    const float b0 = float(st.beta[c0]), b1 = float(st.beta[c0 + 1]), b2 = float(st.beta[c0 + 2]),
+                b3 = float(st.beta[c0 + 3]);
+    for (int64_t i = int64_t(blockIdx.x) * qd.R + qd.r; i < n; i += int64_t(gridDim.x) * qd.R) {
+        const int64_t o = i * qd.kq + qd.q;
+        const float d = dinv[i];
+        const float4 rv = r[o];
+        float4 pv = p[o];
+        if (a0) pv.x = d * rv.x + b0 * pv.x;
+        if (a1) pv.y = d * rv.y + b1 * pv.y;
+        if (a2) pv.z = d * rv.z + b2 * pv.z;
+        if (a3) pv.w = d * rv.w + b3 * pv.w;
+        p[o] = pv;
     }
 }
 
@@ -774,126 +869,6 @@ __global__ void residual64_kernel(const double* __restrict__ b, const double* __
     reduce_columns(s, k, R, out + k);
 }
 
-// Inner FP32 PCG start: r32 = r64 / scale_c, z = Dinv r32, p = z, d = 0; partials r.z, r.r.
-__global__ void pcg32_init_kernel(const double* __restrict__ r64, const double* __restrict__ scale,
-                                  const float* __restrict__ dinv, float* __restrict__ r, float* __restrict__ z,
-                                  float* __restrict__ p, float* __restrict__ d, int64_t n, int k,
-                                  double* __restrict__ partial) {
-    __shared__ double s[kRedThreads];
-    const int R = kRedThreads / k, used = R * k;
-    const int tid = threadIdx.x;
-    double arz = 0.0, arr = 0.0;
-    if (tid < used) {
-        const int c = tid % k, r0 = tid / k;
-        const double sc = scale[c] > 0.0 ? 1.0 / scale[c] : 0.0;
-        for (int64_t i = int64_t(blockIdx.x) * R + r0; i < n; i += int64_t(gridDim.x) * R) {
-            const int64_t o = i * k + c;
-            const float ri = float(r64[o] * sc);
-            const float zi = dinv[i] * ri;
-            r[o] = ri;
-            z[o] = zi;
-            p[o] = zi;
-            d[o] = 0.0f;
-            arz += double(ri) * double(zi);
-            arr += double(ri) * double(ri);
-        }
-    }
-    double* out = partial + int64_t(blockIdx.x) * 3 * k;
-    s[tid] = arr;                      // bb of the inner problem = ||r32||^2
-    reduce_columns(s, k, R, out);
-    __syncthreads();
-    s[tid] = arz;
-    reduce_columns(s, k, R, out + k);
-    __syncthreads();
-    s[tid] = arr;
-    reduce_columns(s, k, R, out + 2 * k);
-}
-
-__global__ void col_dot32_kernel(const float* __restrict__ a, const float* __restrict__ b, int64_t n, int k,
-                                 double* __restrict__ partial) {
-    __shared__ double s[kRedThreads];
-    const int R = kRedThreads / k, used = R * k;
-    const int t = threadIdx.x;
-    double acc = 0.0;
-    if (t < used) {
-        const int c = t % k, r = t / k;
-        for (int64_t i = int64_t(blockIdx.x) * R + r; i < n; i += int64_t(gridDim.x) * R)
-            acc += double(a[i * k + c]) * double(b[i * k + c]);
-    }
-    s[t] = acc;
-    reduce_columns(s, k, R, partial + int64_t(blockIdx.x) * k);
-}
-
-__global__ void pcg32_update_kernel(float* __restrict__ x, float* __restrict__ r, float* __restrict__ z,
-                                    const float* __restrict__ p, const float* __restrict__ Ap,
-                                    const float* __restrict__ dinv, int64_t n, int k, PcgState st,
-                                    double* __restrict__ partial) {
-    __shared__ double s[kRedThreads];
-    const int R = kRedThreads / k, used = R * k;
-    const int tid = threadIdx.x;
-    double arz = 0.0, arr = 0.0;
-    if (tid < used) {
-        const int c = tid % k, r0 = tid / k;
-        const float al = float(st.alpha[c]);
-        for (int64_t i = int64_t(blockIdx.x) * R + r0; i < n; i += int64_t(gridDim.x) * R) {
-            const int64_t o = i * k + c;
-            x[o] = fmaf(al, p[o], x[o]);
-            const float ri = fmaf(-al, Ap[o], r[o]);
-            const float zi = dinv[i] * ri;
-            r[o] = ri;
-            z[o] = zi;
-            arz += double(ri) * double(zi);
-            arr += double(ri) * double(ri);
-        }
-    }
-    double* out = partial + int64_t(blockIdx.x) * 2 * k;
-    s[tid] = arz;
-    reduce_columns(s, k, R, out);
-    __syncthreads();
-    s[tid] = arr;
-    reduce_columns(s, k, R, out + k);
-}
-
-__global__ void pcg32_p_kernel(float* __restrict__ p, const float* __restrict__ z, int64_t n, int k, PcgState st) {
-    const int64_t total = n * k;
-    for (int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; o < total;
-         o += int64_t(gridDim.x) * blockDim.x) {
-        const int c = int(o % k);
-        if (st.active[c]) p[o] = fmaf(float(st.beta[c]), p[o], z[o]);
-    }
-}
-
-// W_interior += scale_c d_c ; per-column norms of the FP64 residual in scale.
-__global__ void refine_update_kernel(double* __restrict__ W, const float* __restrict__ d,
-                                     const double* __restrict__ scale, int64_t n, int k) {
-    const int64_t total = n * k;
-    for (int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; o < total;
-         o += int64_t(gridDim.x) * blockDim.x)
-        W[o] = fma(scale[o % k], double(d[o]), W[o]);
-}
-
-__global__ void finalize_residual_kernel(const double* __restrict__ partial, int nblk, int k, double rtol2,
-                                         double* __restrict__ rr, double* __restrict__ bb,
-                                         double* __restrict__ scale, int* __restrict__ n_active) {
-    __shared__ int cnt;
-    if (threadIdx.x == 0) cnt = 0;
-    __syncthreads();
-    for (int c = threadIdx.x; c < k; c += blockDim.x) {
-        double a = 0.0, b = 0.0;
-        for (int q = 0; q < nblk; ++q) {
-            a += partial[int64_t(q) * 2 * k + c];
-            b += partial[int64_t(q) * 2 * k + k + c];
-        }
-        rr[c] = a;
-        bb[c] = b;
-        const int act = (b > 0.0 && a > rtol2 * b && isfinite(a)) ? 1 : 0;
-        scale[c] = act ? sqrt(a) : 0.0;
-        if (act) atomicAdd(&cnt, 1);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) *n_active = cnt;
-}
-
 int launch_stiffness32(const afem_mesh* m, const float* x, float* y, int nv, int masked, cudaStream_t s);
 
 // Reliable-update form of the mixed solve: one continuous float32 CG per
@@ -902,34 +877,6 @@ int launch_stiffness32(const afem_mesh* m, const float* x, float* y, int nv, int
 // the float32 residual has dropped by `delta` since the last replacement or
 // claims convergence.  Convergence is only ever declared on the float64
 // residual.
-
-// beta, and per column whether a residual replacement is due.
-__global__ void pcg32_beta_ru_kernel(const double* __restrict__ partial, int nblk, int k, PcgState st,
-                                     const double* __restrict__ scale, const double* __restrict__ rr_upd,
-                                     const double* __restrict__ bb64, double rtol2, double delta2,
-                                     int* __restrict__ flags) {
-    __shared__ int need;
-    if (threadIdx.x == 0) need = 0;
-    __syncthreads();
-    for (int c = threadIdx.x; c < k; c += blockDim.x) {
-        double rz = 0.0, rr = 0.0;
-        for (int b = 0; b < nblk; ++b) {
-            rz += partial[int64_t(b) * 2 * k + c];
-            rr += partial[int64_t(b) * 2 * k + k + c];
-        }
-        if (st.active[c]) {
-            st.beta[c] = st.rz[c] != 0.0 ? rz / st.rz[c] : 0.0;
-            st.rz[c] = rz;
-            st.rr[c] = rr;
-            const bool due = !(rr >= delta2 * rr_upd[c]) || scale[c] * scale[c] * rr <= rtol2 * bb64[c];
-            if (due) atomicAdd(&need, 1);
-        } else {
-            st.beta[c] = 0.0;
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) flags[1] = need;
-}
 
 // W += s d ; d = 0   (interior rows)
 __global__ void ru_fold_kernel(double* __restrict__ W, float* __restrict__ d, const double* __restrict__ scale,
@@ -1024,6 +971,7 @@ int poisson_batch_mixed(afem_mesh* m, const double2* phi, int n, double* W, doub
                         double delta, int* iters_out, int* outer_out, double* relres_out, cudaStream_t s) {
     const DeviceMesh& D = m->dev;
     const int k = n * n;
+    const bool quads = (k % 4) == 0;   // four columns per thread in the float32 CG kernels
     const int64_t N = D.n_master, Ni = D.n_interior;
     const int nblk = kRedBlocks;
     const size_t NK = size_t(N) * k;
@@ -1099,11 +1047,22 @@ int poisson_batch_mixed(afem_mesh* m, const double2* phi, int n, double* W, doub
     const int check_every = 8;
     while (flags_h[0] > 0 && it < max_it) {
         if ((rc = launch_stiffness32(m, p32, Ap32, k, 1, s))) return rc;
-        AFEM_LAUNCH((dot_alpha_kernel<float>), nblk, kRedThreads, 0, s, p32, Ap32, Ni, k, w.partial,
-                    w.counters + 0, st);
-        AFEM_LAUNCH((update_beta_kernel<float>), nblk, kRedThreads, 0, s, d32, r32, p32, Ap32, D.stiff_dinv32, Ni, k,
-                    st, w.partial, w.counters + 1, s_old, rr_upd, bb64, rtol2, delta2, flags);
-        AFEM_LAUNCH((p_update_kernel<float>), grid_for(Ni * k), 256, 0, s, p32, r32, D.stiff_dinv32, Ni, k, st);
+        if (quads) {
+            auto* p4 = reinterpret_cast<float4*>(p32);
+            auto* r4 = reinterpret_cast<float4*>(r32);
+            AFEM_LAUNCH((dot_alpha4_kernel), nblk, kRedThreads, 0, s, p4, reinterpret_cast<const float4*>(Ap32), Ni,
+                        k, w.partial, w.counters + 0, st);
+            AFEM_LAUNCH((update_beta4_kernel), nblk, kRedThreads, 0, s, reinterpret_cast<float4*>(d32), r4, p4,
+                        reinterpret_cast<const float4*>(Ap32), D.stiff_dinv32, Ni, k, st, w.partial, w.counters + 1,
+                        s_old, rr_upd, bb64, rtol2, delta2, flags);
+            AFEM_LAUNCH((p_update4_kernel), nblk, kRedThreads, 0, s, p4, r4, D.stiff_dinv32, Ni, k, st);
+        } else {
+            AFEM_LAUNCH((dot_alpha_kernel<float>), nblk, kRedThreads, 0, s, p32, Ap32, Ni, k, w.partial,
+                        w.counters + 0, st);
+            AFEM_LAUNCH((update_beta_kernel<float>), nblk, kRedThreads, 0, s, d32, r32, p32, Ap32, D.stiff_dinv32, Ni,
+                        k, st, w.partial, w.counters + 1, s_old, rr_upd, bb64, rtol2, delta2, flags);
+            AFEM_LAUNCH((p_update_kernel<float>), grid_for(Ni * k), 256, 0, s, p32, r32, D.stiff_dinv32, Ni, k, st);
+        }
         AFEM_CUDA_TRY(cudaGetLastError());
         ++it;
         if (it % check_every == 0 || it >= max_it) {

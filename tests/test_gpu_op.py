@@ -81,7 +81,7 @@ def test_op_apply_rejects_bad_arguments():
 
 @pytest.mark.parametrize("case", CASES[:3])
 @pytest.mark.parametrize("nvec", [3, 16])     # 3: scalar-lane kernel, 16: four-lane kernels
-@pytest.mark.parametrize("variant", [0, 1])   # four-lane: line-ordered / node-per-thread
+@pytest.mark.parametrize("variant", [0, 1])   # four-lane: node-per-thread / line-ordered
 def test_stiffness_f32_within_fp32_tolerance(case, nvec, variant):
     """Precision form of the stiffness: relative error a few float32 ulps x operator norm."""
     import torch
