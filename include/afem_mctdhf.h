@@ -101,6 +101,26 @@ const char* afem_last_error(void);
  * counterpart in the paper. */
 int afem_kernel_launch_count(int64_t* count);
 
+/* Kernel-class timing (library instrumentation with no counterpart in the
+ * paper).  While enabled (process-wide), the library brackets each call of a
+ * class's kernels with a pair of CUDA events recorded on the stream the
+ * kernels are launched on, and adds the call's algorithmic work: FP64 flops
+ * for AFEM_PROF_GS (8 per complex multiply-add with a Krylov vector, 4 per
+ * squared norm) and AFEM_PROF_CELL64 (3 (p+1) 2 + 6 per node and real
+ * column), bytes for the others (each input and output element once).
+ * afem_profile_read waits for the recorded events of class `cls` and returns
+ * (each pointer may be NULL) the summed event time in milliseconds, the
+ * number of bracketed calls and the summed work; reset != 0 clears the class
+ * afterwards.  Errors: AFEM_EINVAL (unknown class), AFEM_ECUDA. */
+#define AFEM_PROF_GS 0      /* Arnoldi Gram-Schmidt passes (FP64)            */
+#define AFEM_PROF_GCELL32 1 /* complex64 cell pass of G (precision form)     */
+#define AFEM_PROF_STIFF32 2 /* float32 stiffness of the CG sweeps            */
+#define AFEM_PROF_CGVEC32 3 /* float32 CG vector kernels                     */
+#define AFEM_PROF_CELL64 4  /* FP64 cell passes (G and stiffness)            */
+#define AFEM_PROF_COUNT 5
+int afem_profile_enable(int on);
+int afem_profile_read(int cls, double* ms, int64_t* calls, double* work, int reset);
+
 /* Build the mesh on the host and upload every table to the current device.
  * Sec. 3.1 (coarse cubes halved toward the nuclei; GLL tensor basis; bridged
  * functions).  *out receives a library-owned object; free it with

@@ -267,3 +267,20 @@ OPT_CELL32_VARIANT = 1
 def mesh_set_option(mesh, option, value):
     """afem_mesh_set_option (kernel-shape tuning)."""
     _capi.check(_capi.load().afem_mesh_set_option(mesh.handle, int(option), int(value)))
+
+
+from ._capi import (PROF_GS, PROF_GCELL32, PROF_STIFF32, PROF_CGVEC32, PROF_CELL64,  # noqa: E402,F401
+                    PROF_COUNT)
+
+
+def profile_enable(on=True):
+    """afem_profile_enable: bracket the kernel classes with CUDA events."""
+    _capi.check(_capi.load().afem_profile_enable(1 if on else 0))
+
+
+def profile_read(cls, reset=False):
+    """afem_profile_read: (ms, calls, work) of one kernel class."""
+    ms, calls, work = ctypes.c_double(0.0), ctypes.c_int64(0), ctypes.c_double(0.0)
+    _capi.check(_capi.load().afem_profile_read(int(cls), ctypes.byref(ms), ctypes.byref(calls),
+                                               ctypes.byref(work), 1 if reset else 0))
+    return ms.value, calls.value, work.value

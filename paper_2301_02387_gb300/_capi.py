@@ -28,6 +28,13 @@ OP_STIFF = 1
 OP_STIFF_F32 = 2
 OP_H1_C64 = 3
 
+PROF_GS = 0
+PROF_GCELL32 = 1
+PROF_STIFF32 = 2
+PROF_CGVEC32 = 3
+PROF_CELL64 = 4
+PROF_COUNT = 5
+
 
 class MeshDesc(ctypes.Structure):
     _fields_ = [
@@ -73,6 +80,10 @@ _P = ctypes.c_void_p
 SIGNATURES = {
     "afem_last_error": (ctypes.c_char_p, []),
     "afem_kernel_launch_count": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int64)]),
+    "afem_profile_enable": (ctypes.c_int, [ctypes.c_int]),
+    "afem_profile_read": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
+                                         ctypes.c_int]),
     "afem_mesh_create": (ctypes.c_int, [ctypes.POINTER(MeshDesc), ctypes.POINTER(_P)]),
     "afem_mesh_create_ex": (ctypes.c_int, [ctypes.POINTER(MeshDesc), ctypes.c_int, ctypes.POINTER(_P)]),
     "afem_mesh_destroy": (ctypes.c_int, [_P]),

@@ -28,6 +28,19 @@ int64_t launch_count();
         kern<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);    \
     } while (0)
 
+// Kernel-class timing (afem_profile_*): while enabled, a ProfScope brackets
+// the launches made in its lifetime with CUDA events on stream s and adds
+// `work` (the class's algorithmic flops or bytes) to the class.
+bool profile_on();
+struct ProfScope {
+    int cls;
+    cudaStream_t s;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    double work;
+    ProfScope(int cls_, cudaStream_t s_, double work_);
+    ~ProfScope();
+};
+
 #define AFEM_CUDA_TRY(call)                                    \
     do {                                                         \
         cudaError_t e_ = (call);                                 \

@@ -76,52 +76,6 @@ __global__ void cdot_fused_kernel(const double2* __restrict__ A, int na, const T
     for (int o = t; o < kout; o += blockDim.x) out[o] = make_double2(sx[2 * o], sx[2 * o + 1]);
 }
 
-// Projector overlaps of the precision form, S[a][b] = sum_k conj(A[k][a]) B[k][b]
-// over interior rows from complex64 inputs: products and runs of 16 rows are
-// summed in FP32, the runs in FP64 (so the FP64 work per element is 1/16 of
-// a product), the blocks by the last block.  n*n <= 256.
-__global__ void __launch_bounds__(kRedThreads) overlap32_kernel(const float2* __restrict__ A,
-                                                                const float2* __restrict__ B, int64_t n_rows, int n,
-                                                                double* __restrict__ partial,
-                                                                unsigned* __restrict__ counter,
-                                                                double2* __restrict__ out) {
-    __shared__ double sx[kRedThreads], sy[kRedThreads];
-    const int kout = n * n;
-    const int R = kRedThreads / kout, used = R * kout;
-    const int t = threadIdx.x;
-    double ax = 0.0, ay = 0.0;
-    if (t < used) {
-        const int o = t % kout, r = t / kout;
-        const int ia = o / n, ib = o - ia * n;
-        const int64_t step = int64_t(gridDim.x) * R;
-        int64_t k = int64_t(blockIdx.x) * R + r;
-        while (k < n_rows) {
-            float fx = 0.f, fy = 0.f;
-            for (int run = 0; run < 16 && k < n_rows; ++run, k += step) {
-                const float2 u = A[k * n + ia], v = B[k * n + ib];
-                fx = fmaf(u.x, v.x, fmaf(u.y, v.y, fx));
-                fy = fmaf(u.x, v.y, fmaf(-u.y, v.x, fy));
-            }
-            ax += double(fx);
-            ay += double(fy);
-        }
-    }
-    sx[t] = ax;
-    sy[t] = ay;
-    __syncthreads();
-    for (int o = t; o < kout; o += blockDim.x) {
-        double x = 0.0, y = 0.0;
-        for (int r = 0; r < R; ++r) {
-            x += sx[o + kout * r];
-            y += sy[o + kout * r];
-        }
-        partial[int64_t(blockIdx.x) * 2 * kout + 2 * o] = x;
-        partial[int64_t(blockIdx.x) * 2 * kout + 2 * o + 1] = y;
-    }
-    if (!last_block_sum(partial, 2 * kout, counter, sx)) return;
-    for (int o = t; o < kout; o += blockDim.x) out[o] = make_double2(sx[2 * o], sx[2 * o + 1]);
-}
-
 // Thread layout of the row-major [rows][n] vector kernels: thread t < n*R of a
 // 256-thread block owns column p = t % n of rows r = t / n, r + R, ... within
 // the block's row range (R = 256 / n), so consecutive threads touch
@@ -137,27 +91,110 @@ struct RowCol {
     }
 };
 
-// Sums of v[0..cnt) over the block (warp shuffles, then one warp over the
-// warp sums); thread 0 writes the block's row partial[blockIdx][0..cnt).
+// Sums of v[0..cnt) over the block; the block's row partial[blockIdx][0..cnt)
+// is written.  FP64 adds are the scarce resource on GB300, so for more than
+// a few values the sums go through shared memory in chunks of 8 values
+// (transposed: warp j sums value j of the chunk, 8 adds per lane and a 5-step
+// shuffle) instead of a 5-step shuffle per value and thread: about 1.6 FP64
+// adds per value and thread instead of 5.
 template <int MAXV>
 __device__ __forceinline__ void block_row_partial(double (&v)[MAXV], int cnt, double* __restrict__ partial) {
-    __shared__ double s_w[kRedThreads / 32][MAXV];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if constexpr (MAXV < 4) {
+        __shared__ double s_w[kRedThreads / 32][MAXV];
 #pragma unroll
-    for (int i = 0; i < MAXV; ++i) {
-        if (i < cnt) {
-            double x = v[i];
+        for (int i = 0; i < MAXV; ++i) {
+            if (i < cnt) {
+                double x = v[i];
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-            if (lane == 0) s_w[warp][i] = x;
+                for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+                if (lane == 0) s_w[warp][i] = x;
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+            double x = 0.0;
+            for (int w = 0; w < kRedThreads / 32; ++w) x += s_w[w][i];
+            partial[int64_t(blockIdx.x) * cnt + i] = x;
+        }
+    } else {
+        static_assert(kRedThreads == 256, "the chunked block sum assumes 8 warps of 32");
+        __shared__ double s_t[8][kRedThreads + 8];
+        const int t = threadIdx.x;
+#pragma unroll
+        for (int c0 = 0; c0 < MAXV; c0 += 8) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (c0 + j < MAXV) s_t[j][t + (t >> 5)] = v[c0 + j];   // padded against bank conflicts
+            __syncthreads();
+            if (c0 + warp < cnt) {
+                double x = 0.0;
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const int src = lane * 8 + r;
+                    x += s_t[warp][src + (src >> 5)];
+                }
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+                if (lane == 0) partial[int64_t(blockIdx.x) * cnt + c0 + warp] = x;
+            }
+            __syncthreads();
         }
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-        double x = 0.0;
-        for (int w = 0; w < kRedThreads / 32; ++w) x += s_w[w][i];
-        partial[int64_t(blockIdx.x) * cnt + i] = x;
+}
+
+// Projector overlaps of the precision form, S[a][b] = sum_k conj(A[k][a]) B[k][b]
+// over interior rows from complex64 inputs (NO = n orbitals): one thread per
+// row forms all NO^2 products in FP32 registers (each thread covers a few
+// rows), the per-thread sums are widened to FP64 once and summed over the
+// block and then by the last block, so the FP64 work is per thread, not per
+// element.
+template <int NO>
+__global__ void __launch_bounds__(kRedThreads) overlap32_kernel(const float2* __restrict__ A,
+                                                                const float2* __restrict__ B, int64_t n_rows,
+                                                                double* __restrict__ partial,
+                                                                unsigned* __restrict__ counter,
+                                                                double2* __restrict__ out) {
+    constexpr int CNT = 2 * NO * NO;
+    float f[CNT];
+#pragma unroll
+    for (int i = 0; i < CNT; ++i) f[i] = 0.f;
+    for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < n_rows;
+         k += int64_t(gridDim.x) * blockDim.x) {
+        float2 a[NO], b[NO];
+        if constexpr (NO % 2 == 0) {   // a row is NO/2 16-byte words
+            const float4* A4 = reinterpret_cast<const float4*>(A + k * NO);
+            const float4* B4 = reinterpret_cast<const float4*>(B + k * NO);
+#pragma unroll
+            for (int i = 0; i < NO / 2; ++i) {
+                const float4 ua = A4[i], ub = B4[i];
+                a[2 * i] = make_float2(ua.x, ua.y);
+                a[2 * i + 1] = make_float2(ua.z, ua.w);
+                b[2 * i] = make_float2(ub.x, ub.y);
+                b[2 * i + 1] = make_float2(ub.z, ub.w);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < NO; ++i) {
+                a[i] = A[k * NO + i];
+                b[i] = B[k * NO + i];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NO; ++i)
+#pragma unroll
+            for (int j = 0; j < NO; ++j) {
+                f[2 * (i * NO + j)] = fmaf(a[i].x, b[j].x, fmaf(a[i].y, b[j].y, f[2 * (i * NO + j)]));
+                f[2 * (i * NO + j) + 1] = fmaf(a[i].x, b[j].y, fmaf(-a[i].y, b[j].x, f[2 * (i * NO + j) + 1]));
+            }
     }
+    double d[CNT];
+#pragma unroll
+    for (int i = 0; i < CNT; ++i) d[i] = double(f[i]);
+    block_row_partial<CNT>(d, CNT, partial);
+    __shared__ double s_sum[kRedThreads];
+    if (!last_block_sum(partial, CNT, counter, s_sum)) return;
+    for (int o = threadIdx.x; o < NO * NO; o += blockDim.x) out[o] = make_double2(s_sum[2 * o], s_sum[2 * o + 1]);
 }
 
 // acc[2i], acc[2i+1] += conj(u_i) mx (i < NV) and acc[2NV] += conj(x) mx, with
@@ -174,29 +211,52 @@ __device__ __forceinline__ void accumulate_dots(double (&acc)[2 * NV + 1], const
     acc[2 * NV] = fma(x.x, mx.x, fma(x.y, mx.y, acc[2 * NV]));
 }
 
-// The block sums of acc, then in the last block out[i] = (acc[2i], acc[2i+1])
-// for i < NV and out[NV] = (acc[2NV], 0).
+// Krylov vectors are stored unnormalised: V_0 = q_0, V_i = h_{i,i-1} q_i for
+// i >= 1 (the Gram-Schmidt remainder), so no pass over the basis only to
+// scale it.  s_f[i] = 1 / h_{i,i-1} (0 after a breakdown, h <= 1e-14 beta),
+// s_f[0] = 1; callers __syncthreads() before use.
+__device__ __forceinline__ void krylov_scales(const double2* __restrict__ H, int ldh,
+                                              const double2* __restrict__ beta2, int nv, double* s_f) {
+    const double beta = sqrt(fmax(beta2->x, 0.0));
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+        double f = 1.0;
+        if (i > 0) {
+            const double h = H[(i - 1) * ldh + i].x;
+            f = (h > 1e-14 * beta && h > 0.0) ? 1.0 / h : 0.0;
+        }
+        s_f[i] = f;
+    }
+}
+
+// The block sums of acc, then in the last block out[i] = s_f[i] (acc[2i],
+// acc[2i+1]) for i < NV (the inner products with q_i from those with V_i) and
+// out[NV] = (acc[2NV], 0).
 template <int NV>
-__device__ __forceinline__ void finish_dots(double (&acc)[2 * NV + 1], double* __restrict__ partial,
-                                            unsigned* __restrict__ counter, double2* __restrict__ out) {
+__device__ __forceinline__ void finish_dots(double (&acc)[2 * NV + 1], const double* s_f,
+                                            double* __restrict__ partial, unsigned* __restrict__ counter,
+                                            double2* __restrict__ out) {
     constexpr int CNT = 2 * NV + 1;
     block_row_partial<CNT>(acc, CNT, partial);
     __shared__ double s_sum[kRedThreads];
     if (!last_block_sum(partial, CNT, counter, s_sum)) return;
-    for (int i = threadIdx.x; i < NV; i += blockDim.x) out[i] = make_double2(s_sum[2 * i], s_sum[2 * i + 1]);
+    for (int i = threadIdx.x; i < NV; i += blockDim.x)
+        out[i] = make_double2(s_f[i] * s_sum[2 * i], s_f[i] * s_sum[2 * i + 1]);
     if (threadIdx.x == 0) out[NV] = make_double2(s_sum[2 * NV], 0.0);
 }
 
-// Gram-Schmidt inner products: out[i] = <V_i, w>_M for i < NV and
+// Gram-Schmidt inner products: out[i] = <q_i, w>_M for i < NV and
 // out[NV] = (<w, w>_M, 0), over interior rows.  Skipped when gate && !*gate.
 // NV is a template parameter so that the NV + 1 loads of a row are issued
 // back to back before any of them is used.
 template <int NV>
 __global__ void __launch_bounds__(kRedThreads) krylov_dots_kernel(
     const double2* __restrict__ w, const double2* __restrict__ V, int64_t stride, const double* __restrict__ ml,
-    int64_t n_int, int n, const int* __restrict__ gate, double* __restrict__ partial, unsigned* __restrict__ counter,
+    int64_t n_int, int n, const int* __restrict__ gate, const double2* __restrict__ H, int ldh,
+    const double2* __restrict__ beta2, double* __restrict__ partial, unsigned* __restrict__ counter,
     double2* __restrict__ out) {
     if (gate && *gate == 0) return;
+    __shared__ double s_f[NV > 0 ? NV : 1];
+    if (NV > 0) krylov_scales(H, ldh, beta2, NV, s_f);
     double acc[2 * NV + 1];
 #pragma unroll
     for (int i = 0; i < 2 * NV + 1; ++i) acc[i] = 0.0;
@@ -212,22 +272,28 @@ __global__ void __launch_bounds__(kRedThreads) krylov_dots_kernel(
             accumulate_dots<NV>(acc, u, x, m);
         }
     }
-    finish_dots<NV>(acc, partial, counter, out);
+    finish_dots<NV>(acc, s_f, partial, counter, out);
 }
 
 // The projector pass of G fused with the first Gram-Schmidt pass (FP64 form):
-// w[k][p] = ML^-1[k] z[k][p] - sum_j phi[k][j] S[j][p] on interior rows (0 on
-// the others) is written, and out[i] = <V_i, w>_M (i < NV), out[NV] = <w, w>_M
-// are formed from the values in registers, so w is not read back.
+// z is the cell pass applied to the stored V_{NV-1}, so
+// w[k][p] = f (ML^-1[k] z[k][p] - sum_j phi[k][j] S[j][p]) with f = s_f[NV-1]
+// is G q_{NV-1} on interior rows (0 on the others); it is written, and
+// out[i] = <q_i, w>_M (i < NV), out[NV] = <w, w>_M are formed from the values
+// in registers, so w is not read back.
 template <int NV>
 __global__ void __launch_bounds__(kRedThreads) project_dots_kernel(
     const double2* __restrict__ z, const double2* __restrict__ phi, const double2* __restrict__ S,
     const double* __restrict__ ml_inv, const double* __restrict__ ml, int64_t n_int, int64_t N, int n,
-    double2* __restrict__ w, const double2* __restrict__ V, int64_t stride, double* __restrict__ partial,
-    unsigned* __restrict__ counter, double2* __restrict__ out) {
+    double2* __restrict__ w, const double2* __restrict__ V, int64_t stride, const double2* __restrict__ H, int ldh,
+    const double2* __restrict__ beta2, double* __restrict__ partial, unsigned* __restrict__ counter,
+    double2* __restrict__ out) {
     __shared__ double2 s_S[kMaxOrbProj * kMaxOrbProj];
+    __shared__ double s_f[NV];
     for (int i = threadIdx.x; i < n * n; i += blockDim.x) s_S[i] = S[i];
+    krylov_scales(H, ldh, beta2, NV, s_f);
     __syncthreads();
+    const double fz = s_f[NV - 1];
     double acc[2 * NV + 1];
 #pragma unroll
     for (int i = 0; i < 2 * NV + 1; ++i) acc[i] = 0.0;
@@ -250,12 +316,13 @@ __global__ void __launch_bounds__(kRedThreads) project_dots_kernel(
                     x.x = fma(-f.x, c.x, fma(f.y, c.y, x.x));
                     x.y = fma(-f.x, c.y, fma(-f.y, c.x, x.y));
                 }
+                x = make_double2(fz * x.x, fz * x.y);
                 accumulate_dots<NV>(acc, u, x, ml[k]);
             }
             w[o] = x;
         }
     }
-    finish_dots<NV>(acc, partial, counter, out);
+    finish_dots<NV>(acc, s_f, partial, counter, out);
 }
 
 // The same for the precision form: the projector in FP32 from the complex64
@@ -265,11 +332,15 @@ template <int NV>
 __global__ void __launch_bounds__(kRedThreads) project32_dots_kernel(
     const float2* __restrict__ z, const float2* __restrict__ phi, const double2* __restrict__ S,
     const double* __restrict__ ml_inv, const double* __restrict__ ml, int64_t n_int, int64_t N, int n,
-    double2* __restrict__ w, const double2* __restrict__ V, int64_t stride, double* __restrict__ partial,
-    unsigned* __restrict__ counter, double2* __restrict__ out) {
+    double2* __restrict__ w, const double2* __restrict__ V, int64_t stride, const double2* __restrict__ H, int ldh,
+    const double2* __restrict__ beta2, double* __restrict__ partial, unsigned* __restrict__ counter,
+    double2* __restrict__ out) {
     __shared__ float2 s_S[kMaxOrbProj * kMaxOrbProj];
+    __shared__ double s_f[NV];
     for (int i = threadIdx.x; i < n * n; i += blockDim.x) s_S[i] = make_float2(float(S[i].x), float(S[i].y));
+    krylov_scales(H, ldh, beta2, NV, s_f);
     __syncthreads();
+    const double fz = s_f[NV - 1];
     double acc[2 * NV + 1];
 #pragma unroll
     for (int i = 0; i < 2 * NV + 1; ++i) acc[i] = 0.0;
@@ -292,28 +363,37 @@ __global__ void __launch_bounds__(kRedThreads) project32_dots_kernel(
                     xf.x = fmaf(-f.x, c.x, fmaf(f.y, c.y, xf.x));
                     xf.y = fmaf(-f.x, c.y, fmaf(-f.y, c.x, xf.y));
                 }
-                x = make_double2(xf.x, xf.y);
+                x = make_double2(fz * double(xf.x), fz * double(xf.y));
                 accumulate_dots<NV>(acc, u, x, ml[k]);
             }
             w[o] = x;
         }
     }
-    finish_dots<NV>(acc, partial, counter, out);
+    finish_dots<NV>(acc, s_f, partial, counter, out);
 }
 
-// Gram-Schmidt update w -= sum_{i<NV} c_i V_i (interior rows) with the new
-// norm; the last block writes the Hessenberg column: Hcol[i] = c_i (or += c_i
-// when accumulate), Hcol[NV] = |w|_M, and *reorth = 1 when a first pass left
-// |w|^2 < eta2 * c[NV] (the squared norm before it).  Skipped when gate && !*gate.
+// Gram-Schmidt update w -= sum_{i<NV} c_i q_i (interior rows; q_i = s_f[i] V_i)
+// with the new norm, and the complex64 copy of w in w32 when non-null (the
+// input of the next cell pass); the last block writes the Hessenberg column:
+// Hcol[i] = c_i (or += c_i when accumulate), Hcol[NV] = |w|_M, and
+// *reorth = 1 when a first pass left |w|^2 < eta2 * c[NV] (the squared norm
+// before it).  Skipped when gate && !*gate.
 template <int NV>
 __global__ void __launch_bounds__(kRedThreads) krylov_update_kernel(
     double2* __restrict__ w, const double2* __restrict__ V, int64_t stride, const double2* __restrict__ c,
     const double* __restrict__ ml, int64_t n_int, int n, const int* __restrict__ gate, int accumulate, double eta2,
-    int* __restrict__ reorth, double* __restrict__ partial, unsigned* __restrict__ counter,
+    int* __restrict__ reorth, const double2* __restrict__ H, int ldh, const double2* __restrict__ beta2,
+    float2* __restrict__ w32, double* __restrict__ partial, unsigned* __restrict__ counter,
     double2* __restrict__ Hcol) {
     if (gate && *gate == 0) return;
     __shared__ double2 s_c[NV + 1];
+    __shared__ double2 s_cf[NV];
+    __shared__ double s_f[NV];
+    krylov_scales(H, ldh, beta2, NV, s_f);
     if (int(threadIdx.x) <= NV) s_c[threadIdx.x] = c[threadIdx.x];
+    __syncthreads();
+    if (int(threadIdx.x) < NV)
+        s_cf[threadIdx.x] = make_double2(s_c[threadIdx.x].x * s_f[threadIdx.x], s_c[threadIdx.x].y * s_f[threadIdx.x]);
     __syncthreads();
     double nrm[1] = {0.0};
     const RowCol rc(n);
@@ -327,11 +407,12 @@ __global__ void __launch_bounds__(kRedThreads) krylov_update_kernel(
             for (int i = 0; i < NV; ++i) u[i] = V[i * stride + o];
 #pragma unroll
             for (int i = 0; i < NV; ++i) {
-                const double2 h = s_c[i];
+                const double2 h = s_cf[i];
                 x.x = fma(-h.x, u[i].x, fma(h.y, u[i].y, x.x));
                 x.y = fma(-h.x, u[i].y, fma(-h.y, u[i].x, x.y));
             }
             w[o] = x;
+            if (w32) w32[o] = make_float2(float(x.x), float(x.y));
             nrm[0] = fma(m, fma(x.x, x.x, x.y * x.y), nrm[0]);
         }
     }
@@ -366,11 +447,18 @@ __global__ void normalize_kernel(const double2* src, double2* dst, const double2
     }
 }
 
-// phi_out = scale * sum_{i<m} y_i V_i
+// phi_out = scale * sum_{i<m} y_i q_i  (q_i = s_f[i] V_i)
 __global__ void combine_kernel(const double2* __restrict__ V, int64_t stride, int m, const double2* __restrict__ y,
-                               double scale, int64_t total, double2* __restrict__ out) {
+                               double scale, const double2* __restrict__ H, int ldh, const double2* __restrict__ beta2,
+                               int64_t total, double2* __restrict__ out) {
     __shared__ double2 s_y[kMaxKrylov];
-    if (int(threadIdx.x) < m) s_y[threadIdx.x] = make_double2(scale * y[threadIdx.x].x, scale * y[threadIdx.x].y);
+    __shared__ double s_f[kMaxKrylov];
+    krylov_scales(H, ldh, beta2, m, s_f);
+    __syncthreads();
+    if (int(threadIdx.x) < m) {
+        const double f = scale * s_f[threadIdx.x];
+        s_y[threadIdx.x] = make_double2(f * y[threadIdx.x].x, f * y[threadIdx.x].y);
+    }
     __syncthreads();
     for (int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; o < total;
          o += int64_t(gridDim.x) * blockDim.x) {
@@ -387,7 +475,9 @@ __global__ void combine_kernel(const double2* __restrict__ V, int64_t stride, in
 
 // exp(-i dt H) for an m x m complex matrix (m <= kMaxKrylov) by one block:
 // scaling and squaring with a truncated Taylor series (the scaled matrix has
-// 1-norm <= 1/2, and 24 terms leave a remainder below 1e-30).
+// 1-norm <= 1/2; the remainder after 16 terms is below 0.5^17 / 17! ~ 2e-20
+// relative, under the FP64 rounding of the squarings).
+constexpr int kTaylorTerms = 16;
 // H: column-major with leading dimension ldh.  Leaves the result in S.
 __device__ void block_expm(const double2* __restrict__ H, int ldh, int m, double dt, double2* A, double2* P,
                            double2* S, double2* T) {
@@ -424,8 +514,9 @@ __device__ void block_expm(const double2* __restrict__ H, int ldh, int m, double
         P[o] = S[o];
     }
     __syncthreads();
-    for (int k = 1; k <= 24; ++k) {
+    for (int k = 1; k <= kTaylorTerms; ++k) {
         // P <- P A / k
+        const double ik = 1.0 / k;
         for (int o = t; o < mm; o += blockDim.x) {
             const int i = o % m, j = o / m;
             double x = 0.0, y = 0.0;
@@ -434,7 +525,7 @@ __device__ void block_expm(const double2* __restrict__ H, int ldh, int m, double
                 x += a.x * b.x - a.y * b.y;
                 y += a.x * b.y + a.y * b.x;
             }
-            T[o] = make_double2(x / k, y / k);
+            T[o] = make_double2(x * ik, y * ik);
         }
         __syncthreads();
         for (int o = t; o < mm; o += blockDim.x) {
@@ -519,16 +610,17 @@ int launch_g_cell32(const afem_mesh* m, const double* E, const float2* v, const 
 // The Gram-Schmidt kernels for a run-time vector count nv (0 <= nv <= kMaxKrylov).
 static int launch_krylov_dots(int nv, unsigned grid, cudaStream_t s, const double2* w, const double2* V,
                               int64_t stride, const double* ml, int64_t n_int, int n, const int* gate,
-                              double* partial, unsigned* counter, double2* out) {
+                              const double2* H, int ldh, const double2* beta2, double* partial, unsigned* counter,
+                              double2* out) {
     switch (nv) {
         case 0:
-            AFEM_LAUNCH((krylov_dots_kernel<0>), grid, kRedThreads, 0, s, w, V, stride, ml, n_int, n, gate, partial,
-                        counter, out);
+            AFEM_LAUNCH((krylov_dots_kernel<0>), grid, kRedThreads, 0, s, w, V, stride, ml, n_int, n, gate, H, ldh,
+                        beta2, partial, counter, out);
             break;
-#define AFEM_DOTS_CASE(NVV)                                                                                   \
-    case NVV:                                                                                                 \
-        AFEM_LAUNCH((krylov_dots_kernel<NVV>), grid, kRedThreads, 0, s, w, V, stride, ml, n_int, n, gate, partial, \
-                    counter, out);                                                                            \
+#define AFEM_DOTS_CASE(NVV)                                                                                       \
+    case NVV:                                                                                                     \
+        AFEM_LAUNCH((krylov_dots_kernel<NVV>), grid, kRedThreads, 0, s, w, V, stride, ml, n_int, n, gate, H, ldh, \
+                    beta2, partial, counter, out);                                                                \
         break;
             AFEM_NV_CASES(AFEM_DOTS_CASE)
 #undef AFEM_DOTS_CASE
@@ -543,17 +635,17 @@ static int launch_krylov_dots(int nv, unsigned grid, cudaStream_t s, const doubl
 // against V_0..V_{nv-1}: complex64 z (precision form, phi32) or complex128 z.
 static int launch_project_dots(int nv, unsigned grid, cudaStream_t s, const float2* z32, const float2* phi32,
                                const double2* z, const double2* phi, const double2* S, const DeviceMesh& D, int n,
-                               double2* w, const double2* V, int64_t stride, double* partial, unsigned* counter,
-                               double2* out) {
+                               double2* w, const double2* V, int64_t stride, const double2* H, int ldh,
+                               const double2* beta2, double* partial, unsigned* counter, double2* out) {
     switch (nv) {
 #define AFEM_PD_CASE(NVV)                                                                                           \
     case NVV:                                                                                                       \
         if (z32) {                                                                                                  \
             AFEM_LAUNCH((project32_dots_kernel<NVV>), grid, kRedThreads, 0, s, z32, phi32, S, D.ml_inv, D.ml,      \
-                        D.n_interior, D.n_master, n, w, V, stride, partial, counter, out);                          \
+                        D.n_interior, D.n_master, n, w, V, stride, H, ldh, beta2, partial, counter, out);           \
         } else {                                                                                                    \
             AFEM_LAUNCH((project_dots_kernel<NVV>), grid, kRedThreads, 0, s, z, phi, S, D.ml_inv, D.ml,            \
-                        D.n_interior, D.n_master, n, w, V, stride, partial, counter, out);                          \
+                        D.n_interior, D.n_master, n, w, V, stride, H, ldh, beta2, partial, counter, out);           \
         }                                                                                                           \
         break;
         AFEM_NV_CASES(AFEM_PD_CASE)
@@ -567,13 +659,14 @@ static int launch_project_dots(int nv, unsigned grid, cudaStream_t s, const floa
 
 static int launch_krylov_update(int nv, unsigned grid, cudaStream_t s, double2* w, const double2* V,
                                 int64_t stride, const double2* c, const double* ml, int64_t n_int, int n,
-                                const int* gate, int accumulate, double eta2, int* reorth, double* partial,
-                                unsigned* counter, double2* Hcol) {
+                                const int* gate, int accumulate, double eta2, int* reorth, const double2* H, int ldh,
+                                const double2* beta2, float2* w32, double* partial, unsigned* counter,
+                                double2* Hcol) {
     switch (nv) {
 #define AFEM_UPD_CASE(NVV)                                                                                      \
     case NVV:                                                                                                   \
         AFEM_LAUNCH((krylov_update_kernel<NVV>), grid, kRedThreads, 0, s, w, V, stride, c, ml, n_int, n, gate,  \
-                    accumulate, eta2, reorth, partial, counter, Hcol);                                          \
+                    accumulate, eta2, reorth, H, ldh, beta2, w32, partial, counter, Hcol);                      \
         break;
         AFEM_NV_CASES(AFEM_UPD_CASE)
 #undef AFEM_UPD_CASE
@@ -600,9 +693,29 @@ static int g_cell_overlaps32(afem_mesh* m, const double* E, const float2* phi32,
                              const float2* v32, ArnoldiWork& w, cudaStream_t s) {
     const DeviceMesh& D = m->dev;
     int rc;
-    if ((rc = launch_g_cell32(m, E, v32, U32, w.z32, n, s))) return rc;
-    AFEM_LAUNCH((overlap32_kernel), kRedBlocks, kRedThreads, 0, s, phi32, w.z32, D.n_interior, n,
-                reinterpret_cast<double*>(w.cpartial), w.counters, w.S);
+    {   // algorithmic bytes: read v, U (n^2 fields), write z, complex64
+        ProfScope ps(AFEM_PROF_GCELL32, s, double(D.n_master) * 8.0 * n * (2 + n));
+        if ((rc = launch_g_cell32(m, E, v32, U32, w.z32, n, s))) return rc;
+    }
+    auto* part = reinterpret_cast<double*>(w.cpartial);
+    switch (n) {
+#define AFEM_OV_CASE(NO)                                                                                        \
+    case NO:                                                                                                    \
+        AFEM_LAUNCH((overlap32_kernel<NO>), kRedBlocks / 2, kRedThreads, 0, s, phi32, w.z32, D.n_interior,     \
+                    part, w.counters, w.S);                                                                     \
+        break;
+        AFEM_OV_CASE(1)
+        AFEM_OV_CASE(2)
+        AFEM_OV_CASE(3)
+        AFEM_OV_CASE(4)
+        AFEM_OV_CASE(5)
+        AFEM_OV_CASE(6)
+        AFEM_OV_CASE(7)
+        AFEM_OV_CASE(8)
+#undef AFEM_OV_CASE
+        default:
+            return set_error(AFEM_EINVAL, "arnoldi: orbital count out of range");
+    }
     AFEM_CUDA_TRY(cudaGetLastError());
     return AFEM_OK;
 }
@@ -610,7 +723,12 @@ static int g_cell_overlaps32(afem_mesh* m, const double* E, const float2* phi32,
 static int g_cell_overlaps(afem_mesh* m, const double* E, const double2* phi, const double2* U, int n,
                            const double2* v, ArnoldiWork& w, cudaStream_t s) {
     const DeviceMesh& D = m->dev;
-    int rc = launch_g_cell(m, E, v, U, w.z, n, s);
+    int rc;
+    {
+        const int p1 = D.p + 1;
+        ProfScope ps(AFEM_PROF_CELL64, s, double(D.ncell) * p1 * p1 * p1 * 2.0 * n * (3.0 * p1 * 2.0 + 6.0));
+        rc = launch_g_cell(m, E, v, U, w.z, n, s);
+    }
     if (rc) return rc;
     return cdot(phi, n, w.z, n, nullptr, D.n_interior, 0, w.cpartial, w.S, w.counters, s);
 }
@@ -701,33 +819,39 @@ int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double
         if (substeps >= 4096) return set_error(AFEM_EINVAL, "arnoldi: more than 4096 substeps (tolerance too tight)");
         AFEM_CUDA_TRY(cudaMemsetAsync(w.H, 0, sizeof(double2) * ldh * kMaxKrylov, s));
         // beta^2 = <src, src>_M ; V_0 = src / beta
-        if ((rc = launch_krylov_dots(0, gdots, s, src, nullptr, NV, D.ml, D.n_interior, n, nullptr, part, cnt,
-                                     w.beta2)))
+        if ((rc = launch_krylov_dots(0, gdots, s, src, nullptr, NV, D.ml, D.n_interior, n, nullptr, w.H, ldh,
+                                     w.beta2, part, cnt, w.beta2)))
             return rc;
-        AFEM_LAUNCH((normalize_kernel), grid_for(NV), 256, 0, s, src, w.V, w.beta2, 1, w.beta2,
-                    mixed ? w.v32 : nullptr, NV);
+        float2* v32 = mixed ? w.v32 : nullptr;
+        AFEM_LAUNCH((normalize_kernel), grid_for(NV), 256, 0, s, src, w.V, w.beta2, 1, w.beta2, v32, NV);
         for (int j = 0; j < mk; ++j) {
-            double2* Vj = w.V + j * NV;
             double2* Wn = w.V + (j + 1) * NV;
             double2* Hcol = w.H + j * ldh;
-            if (j > 0)   // V_j = w_j / h_{j,j-1}
-                AFEM_LAUNCH((normalize_kernel), grid_for(NV), 256, 0, s, Vj, Vj, w.H + (j - 1) * ldh + j, 0, w.beta2,
-                            mixed ? w.v32 : nullptr, NV);
-            // w = G V_j with the inner products against V_0..V_j, the update, and
-            // a second pass when the update cancelled most of w
+            // w = G q_j (the cell pass on the stored V_j, scaled in the projector
+            // pass) with the inner products against q_0..q_j, the update (which
+            // leaves V_{j+1} = h_{j+1,j} q_{j+1}), and a second pass when the
+            // update cancelled most of w
             if (mixed) {
                 if ((rc = g_cell_overlaps32(m, E, w.phi32, U32, n, w.v32, w, s))) return rc;
             } else {
-                if ((rc = g_cell_overlaps(m, E, phi, U, n, Vj, w, s))) return rc;
+                if ((rc = g_cell_overlaps(m, E, phi, U, n, w.V + j * NV, w, s))) return rc;
             }
-            if ((rc = launch_project_dots(j + 1, gproj, s, mixed ? w.z32 : nullptr, w.phi32, w.z, phi, w.S, D, n, Wn,
-                                          w.V, NV, part, cnt, w.c1)) ||
-                (rc = launch_krylov_update(j + 1, gdots, s, Wn, w.V, NV, w.c1, D.ml, D.n_interior, n, nullptr, 0,
-                                           eta2, w.flag, part, cnt, Hcol)) ||
-                (rc = launch_krylov_dots(j + 1, gdots, s, Wn, w.V, NV, D.ml, D.n_interior, n, w.flag, part, cnt,
-                                         w.c2)) ||
+            const double gs_flops = double(D.n_interior) * n * (8.0 * (j + 1) + 4.0);   // one pass
+            {
+                ProfScope ps(AFEM_PROF_GS, s, gs_flops);
+                rc = launch_project_dots(j + 1, gproj, s, mixed ? w.z32 : nullptr, w.phi32, w.z, phi, w.S, D, n, Wn,
+                                         w.V, NV, w.H, ldh, w.beta2, part, cnt, w.c1);
+            }
+            if (!rc) {
+                ProfScope ps(AFEM_PROF_GS, s, gs_flops);
+                rc = launch_krylov_update(j + 1, gdots, s, Wn, w.V, NV, w.c1, D.ml, D.n_interior, n, nullptr, 0, eta2,
+                                          w.flag, w.H, ldh, w.beta2, v32, part, cnt, Hcol);
+            }
+            if (rc ||
+                (rc = launch_krylov_dots(j + 1, gdots, s, Wn, w.V, NV, D.ml, D.n_interior, n, w.flag, w.H, ldh,
+                                         w.beta2, part, cnt, w.c2)) ||
                 (rc = launch_krylov_update(j + 1, gdots, s, Wn, w.V, NV, w.c2, D.ml, D.n_interior, n, w.flag, 1,
-                                           eta2, nullptr, part, cnt, Hcol)))
+                                           eta2, nullptr, w.H, ldh, w.beta2, v32, part, cnt, Hcol)))
                 return rc;
         }
         // candidate substeps, one block each; a single host wait per ladder
@@ -781,8 +905,8 @@ int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double
         const double tau = make_ladder(tau_max, K).tau[pick];
         const double err = beta * res[kResErr + pick].x;
         // phi_out = beta V_m exp(-i tau H_m) e_1
-        AFEM_LAUNCH((combine_kernel), grid_for(NV), 256, 0, s, w.V, NV, m_used, w.col + pick * kMaxKrylov, beta, NV,
-                    phi_out);
+        AFEM_LAUNCH((combine_kernel), grid_for(NV), 256, 0, s, w.V, NV, m_used, w.col + pick * kMaxKrylov, beta, w.H,
+                    ldh, w.beta2, NV, phi_out);
         AFEM_CUDA_TRY(cudaGetLastError());
         err_sum += err;
         ++substeps;

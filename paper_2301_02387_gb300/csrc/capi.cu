@@ -7,12 +7,75 @@
 
 #include <atomic>
 
+#include <mutex>
+
 namespace afem {
 const char* last_error_cstr();
 static std::atomic<int64_t> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+// Kernel-class timing: event pairs are kept per class until read, events are
+// recycled through a pool.  Process-wide, guarded by one mutex.
+namespace {
+struct ProfClass {
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+    double ms = 0.0, work = 0.0;
+    int64_t launches = 0;
+};
+std::mutex g_prof_mu;
+std::atomic<bool> g_prof_on{false};
+ProfClass g_prof[AFEM_PROF_COUNT];
+std::vector<cudaEvent_t> g_event_pool;
+
+cudaEvent_t take_event() {
+    if (!g_event_pool.empty()) {
+        cudaEvent_t e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
 }
+
+// Sums the finished event pairs of a class (waits for them).
+int drain(ProfClass& c) {
+    for (auto& pr : c.pending) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(pr.second);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, pr.first, pr.second);
+        if (e != cudaSuccess) return cuda_error(e, "afem_profile_read");
+        c.ms += ms;
+        g_event_pool.push_back(pr.first);
+        g_event_pool.push_back(pr.second);
+    }
+    c.pending.clear();
+    return AFEM_OK;
+}
+}  // namespace
+
+bool profile_on() { return g_prof_on.load(std::memory_order_relaxed); }
+
+ProfScope::ProfScope(int cls_, cudaStream_t s_, double work_) : cls(cls_), s(s_), work(work_) {
+    if (!profile_on() || cls < 0 || cls >= AFEM_PROF_COUNT) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    e0 = take_event();
+    e1 = take_event();
+    if (e0 && e1) cudaEventRecord(e0, s);
+}
+
+ProfScope::~ProfScope() {
+    if (!e0 || !e1) return;
+    cudaEventRecord(e1, s);
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    ProfClass& c = g_prof[cls];
+    c.pending.emplace_back(e0, e1);
+    c.work += work;
+    c.launches += 1;
+    if (c.pending.size() > 4096) drain(c);   // bound the events held
+}
+}  // namespace afem
 
 using namespace afem;
 
@@ -23,6 +86,28 @@ const char* afem_last_error(void) { return last_error_cstr(); }
 int afem_kernel_launch_count(int64_t* count) {
     if (!count) return set_error(AFEM_EINVAL, "afem_kernel_launch_count: null argument");
     *count = launch_count();
+    return AFEM_OK;
+}
+
+int afem_profile_enable(int on) {
+    afem::g_prof_on.store(on != 0, std::memory_order_relaxed);
+    return AFEM_OK;
+}
+
+int afem_profile_read(int cls, double* ms, int64_t* calls, double* work, int reset) {
+    if (cls < 0 || cls >= AFEM_PROF_COUNT) return set_error(AFEM_EINVAL, "afem_profile_read: unknown class");
+    std::lock_guard<std::mutex> lk(afem::g_prof_mu);
+    afem::ProfClass& c = afem::g_prof[cls];
+    int rc = afem::drain(c);
+    if (rc) return rc;
+    if (ms) *ms = c.ms;
+    if (calls) *calls = c.launches;
+    if (work) *work = c.work;
+    if (reset) {
+        c.ms = 0.0;
+        c.work = 0.0;
+        c.launches = 0;
+    }
     return AFEM_OK;
 }
 

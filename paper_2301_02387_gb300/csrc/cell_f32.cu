@@ -181,12 +181,15 @@ __device__ __forceinline__ void scatter32v(const CellArgs32& a, int idx, float4*
     }
 }
 
-template <int P, bool G>
+// L4C > 0 fixes the quad count at compile time (no integer division per item);
+// L4C = 0 takes it from L4rt.
+template <int P, bool G, int L4C>
 __global__ void __launch_bounds__(256) cell32v_kernel(CellArgs32 a, const float4* __restrict__ x,
-                                                      const float2* __restrict__ U, float4* __restrict__ y, int L4,
+                                                      const float2* __restrict__ U, float4* __restrict__ y, int L4rt,
                                                       int n) {
     constexpr int P1 = P + 1;
     constexpr int NN = P1 * P1 * P1;
+    const int L4 = L4C > 0 ? L4C : L4rt;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4* s_u = reinterpret_cast<float4*>(smem_raw);           // [NN][L4]
     float2* s_U = reinterpret_cast<float2*>(s_u + NN * L4);      // [NN][n*n] (G with U)
@@ -206,14 +209,25 @@ __global__ void __launch_bounds__(256) cell32v_kernel(CellArgs32 a, const float4
         const int i = it / L4, q = it - i * L4;
         s_u[it] = gather32v(a, s_idx[i], x, L4, q);
     }
-    const int nn2 = n * n;
+    // with the quad count fixed, the orbital count n = 2 L4 is too
+    const int nn2 = (G && L4C > 0) ? 4 * L4C * L4C : n * n;
     if (G) {
         if (U) {
             CellArgs32 au = a;
             au.masked = 0;
-            for (int it = tid; it < NN * nn2; it += bs) {
-                const int i = it / nn2, pq = it - i * nn2;
-                s_U[it] = gather32<float2>(au, s_idx[i], U, nn2, pq);
+            if (nn2 % 2 == 0) {   // the n^2 complex fields of a node as float4 pairs
+                const int h2 = nn2 / 2;
+                const float4* U4 = reinterpret_cast<const float4*>(U);
+                float4* s_U4 = reinterpret_cast<float4*>(s_U);
+                for (int it = tid; it < NN * h2; it += bs) {
+                    const int i = it / h2, c = it - i * h2;
+                    s_U4[it] = gather32v(au, s_idx[i], U4, h2, c);
+                }
+            } else {
+                for (int it = tid; it < NN * nn2; it += bs) {
+                    const int i = it / nn2, pq = it - i * nn2;
+                    s_U[it] = gather32<float2>(au, s_idx[i], U, nn2, pq);
+                }
             }
         }
         const float h3 = g.w * g.w * g.w;
@@ -249,9 +263,11 @@ __global__ void __launch_bounds__(256) cell32v_kernel(CellArgs32 a, const float4
                 // orbitals p0 = 2q (lanes x, y) and p1 = 2q + 1 (lanes z, w)
                 const float2* ui = reinterpret_cast<const float2*>(s_u + i * L4);
                 float2 m0 = make_float2(0.f, 0.f), m1 = m0;
-                const float2* U0 = s_U + i * nn2 + (2 * q) * n;
-                const float2* U1 = U0 + n;
-                for (int rr = 0; rr < n; ++rr) {
+                const int nl = L4C > 0 ? 2 * L4C : n;
+                const float2* U0 = s_U + i * nn2 + (2 * q) * nl;
+                const float2* U1 = U0 + nl;
+#pragma unroll
+                for (int rr = 0; rr < nl; ++rr) {
                     const float2 u = ui[rr];
                     m0.x = fmaf(U0[rr].x, u.x, fmaf(-U0[rr].y, u.y, m0.x));
                     m0.y = fmaf(U0[rr].x, u.y, fmaf(U0[rr].y, u.x, m0.y));
@@ -499,7 +515,10 @@ static int launch32v(const afem_mesh* m, const CellArgs32& a, const float* x, co
     switch (p) {
 #define AFEM_CASE(PP)                                                                          \
     case PP: {                                                                                 \
-        auto k = cell32v_kernel<PP, G>;                                                        \
+        auto k = L4 == 1   ? cell32v_kernel<PP, G, 1>                                          \
+                 : L4 == 2 ? cell32v_kernel<PP, G, 2>                                          \
+                 : L4 == 4 ? cell32v_kernel<PP, G, 4>                                          \
+                           : cell32v_kernel<PP, G, 0>;                                         \
         if (smem > 48 * 1024)                                                                  \
             AFEM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                                int(smem)));                                    \

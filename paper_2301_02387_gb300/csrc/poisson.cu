@@ -762,7 +762,11 @@ int poisson_batch(afem_mesh* m, const double2* phi, int n, double* W, double rto
             AFEM_CUDA_TRY(cudaStreamSynchronize(s));
             if (n_active == 0) break;
         }
-        if ((rc = launch_stiffness(m, w.p, w.Ap, k, 1, s))) return rc;
+        {
+            const int p1 = D.p + 1;
+            ProfScope ps(AFEM_PROF_CELL64, s, double(D.ncell) * p1 * p1 * p1 * k * (3.0 * p1 * 2.0 + 6.0));
+            if ((rc = launch_stiffness(m, w.p, w.Ap, k, 1, s))) return rc;
+        }
         AFEM_LAUNCH((dot_alpha_kernel<double>), nblk, kRedThreads, 0, s, w.p, w.Ap, Ni, k, w.partial,
                     w.counters + 0, st);
         AFEM_LAUNCH((update_beta_kernel<double>), nblk, kRedThreads, 0, s, W, w.r, w.p, w.Ap, D.stiff_dinv, Ni, k, st,
@@ -1046,7 +1050,12 @@ int poisson_batch_mixed(afem_mesh* m, const double2* phi, int n, double* W, doub
     int it = 0;
     const int check_every = 8;
     while (flags_h[0] > 0 && it < max_it) {
-        if ((rc = launch_stiffness32(m, p32, Ap32, k, 1, s))) return rc;
+        {   // algorithmic bytes: read p, write Ap (float32)
+            ProfScope ps(AFEM_PROF_STIFF32, s, double(N) * k * 8.0);
+            if ((rc = launch_stiffness32(m, p32, Ap32, k, 1, s))) return rc;
+        }
+        // algorithmic bytes: p.Ap 8, x/r update 24, p update 12 per element (float32)
+        ProfScope psv(AFEM_PROF_CGVEC32, s, double(Ni) * k * 44.0);
         if (quads) {
             auto* p4 = reinterpret_cast<float4*>(p32);
             auto* r4 = reinterpret_cast<float4*>(r32);

@@ -73,3 +73,16 @@ def test_bad_descriptions_are_rejected():
         Mesh(1.0, -1.0, 2, 2, [], 2.0, host_only=True)
     with pytest.raises(AfemError):
         Mesh(-1.0, 1.0, 0, 2, [], 2.0, host_only=True)
+
+
+def test_profile_classes_host_side():
+    """Kernel-class timing bookkeeping: an unknown class is rejected, a class
+    with nothing recorded reads as zero (no device work involved)."""
+    import paper_2301_02387_gb300 as pkg
+    with pytest.raises(pkg.AfemError):
+        pkg.profile_read(pkg.PROF_COUNT)
+    with pytest.raises(pkg.AfemError):
+        pkg.profile_read(-1)
+    pkg.profile_enable(False)
+    for c in range(pkg.PROF_COUNT):
+        assert pkg.profile_read(c, reset=True) == (0.0, 0, 0.0)
