@@ -14,7 +14,8 @@ Test infrastructure only (see the package docstring).
 import numpy as np
 import scipy.linalg
 
-LADDER = 16   # candidate substep lengths per ladder in arnoldi_propagate
+LADDER = 64          # candidate substep lengths per ladder in arnoldi_propagate
+LADDER_LOG2 = 0.125  # candidate c is tau_max 2^(-c LADDER_LOG2)
 
 
 def arnoldi_expm(apply_G, phi, inner, m, dt, breakdown_tol=1e-14):
@@ -76,7 +77,7 @@ def arnoldi_propagate(apply_G, phi, inner, m, dt, tol, max_substeps=4096):
     1e-10 in the paper) and leaves open how the step adapts (Park and Light
     allow an adaptive step or an adaptive dimension).  Here the dimension m is
     fixed and dt is covered by substeps of the same G, each as long as the
-    candidates allow: tau_c = tau_max 2^(-c/2), c = 0..15, with tau_max the
+    candidates allow: tau_c = tau_max 2^(-c/8), c = 0..63, with tau_max the
     whole remainder for the first substep and min(remainder, 2 tau_previous)
     after it; the first (longest) candidate whose estimate
     beta |h_{m+1,m}| |e_m^T exp(-i tau_c H_m) e_1| is <= tol beta is taken;
@@ -101,7 +102,7 @@ def arnoldi_propagate(apply_G, phi, inner, m, dt, tol, max_substeps=4096):
             found = False
             for ladder in range(9):
                 for c in range(LADDER):
-                    tau = tau_max * 2.0 ** (-0.5 * c)
+                    tau = tau_max * 2.0 ** (-LADDER_LOG2 * c)
                     Em = scipy.linalg.expm(-1j * tau * H[:mu, :mu])
                     err = beta * hlast * abs(Em[mu - 1, 0])
                     if err <= tol * beta:
@@ -109,7 +110,7 @@ def arnoldi_propagate(apply_G, phi, inner, m, dt, tol, max_substeps=4096):
                         break
                 if found:
                     break
-                tau_max *= 2.0 ** (-0.5 * LADDER)
+                tau_max *= 2.0 ** (-LADDER_LOG2 * LADDER)
         cur = sum(beta * Em[i, 0] * V[i] for i in range(mu))
         total += err
         substeps += 1

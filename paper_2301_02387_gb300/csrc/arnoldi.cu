@@ -211,26 +211,29 @@ __device__ __forceinline__ void accumulate_dots(double (&acc)[2 * NV + 1], const
     acc[2 * NV] = fma(x.x, mx.x, fma(x.y, mx.y, acc[2 * NV]));
 }
 
-// Krylov vectors are stored unnormalised: V_0 = q_0, V_i = h_{i,i-1} q_i for
-// i >= 1 (the Gram-Schmidt remainder), so no pass over the basis only to
-// scale it.  s_f[i] = 1 / h_{i,i-1} (0 after a breakdown, h <= 1e-14 beta),
-// s_f[0] = 1; callers __syncthreads() before use.
+// Krylov vectors are stored unscaled: V_0 is the substep's start vector and
+// V_{i+1} the raw Gram-Schmidt remainder of the cell pass applied to V_i, with
+// q_i = s_f[i] V_i, s_f[0] = 1 / beta, s_f[i] = s_f[i-1] / h_{i,i-1} (= 1 / |V_i|_M),
+// so no pass over the basis only to scale it and no FP64 scaling of the new
+// vector (0 after a breakdown, h <= 1e-14 beta).  Callers __syncthreads()
+// before use.
 __device__ __forceinline__ void krylov_scales(const double2* __restrict__ H, int ldh,
                                               const double2* __restrict__ beta2, int nv, double* s_f) {
+    if (threadIdx.x != 0 || nv <= 0) return;
     const double beta = sqrt(fmax(beta2->x, 0.0));
-    for (int i = threadIdx.x; i < nv; i += blockDim.x) {
-        double f = 1.0;
-        if (i > 0) {
-            const double h = H[(i - 1) * ldh + i].x;
-            f = (h > 1e-14 * beta && h > 0.0) ? 1.0 / h : 0.0;
-        }
+    double f = beta > 0.0 ? 1.0 / beta : 0.0;
+    s_f[0] = f;
+    for (int i = 1; i < nv; ++i) {
+        const double h = H[(i - 1) * ldh + i].x;
+        f = (h > 1e-14 * beta && h > 0.0) ? f / h : 0.0;
         s_f[i] = f;
     }
 }
 
-// The block sums of acc, then in the last block out[i] = s_f[i] (acc[2i],
-// acc[2i+1]) for i < NV (the inner products with q_i from those with V_i) and
-// out[NV] = (acc[2NV], 0).
+// The block sums of acc (inner products of the raw vector w with the stored
+// V_i), then in the last block the true values for the vector fw w with
+// fw = s_f[NV-1] (1 when NV = 0): out[i] = s_f[i] fw (acc[2i], acc[2i+1]) =
+// <q_i, fw w> for i < NV and out[NV] = (fw^2 acc[2NV], 0) = |fw w|^2.
 template <int NV>
 __device__ __forceinline__ void finish_dots(double (&acc)[2 * NV + 1], const double* s_f,
                                             double* __restrict__ partial, unsigned* __restrict__ counter,
@@ -239,9 +242,12 @@ __device__ __forceinline__ void finish_dots(double (&acc)[2 * NV + 1], const dou
     block_row_partial<CNT>(acc, CNT, partial);
     __shared__ double s_sum[kRedThreads];
     if (!last_block_sum(partial, CNT, counter, s_sum)) return;
-    for (int i = threadIdx.x; i < NV; i += blockDim.x)
-        out[i] = make_double2(s_f[i] * s_sum[2 * i], s_f[i] * s_sum[2 * i + 1]);
-    if (threadIdx.x == 0) out[NV] = make_double2(s_sum[2 * NV], 0.0);
+    const double fw = NV > 0 ? s_f[NV > 0 ? NV - 1 : 0] : 1.0;
+    for (int i = threadIdx.x; i < NV; i += blockDim.x) {
+        const double f = s_f[i] * fw;
+        out[i] = make_double2(f * s_sum[2 * i], f * s_sum[2 * i + 1]);
+    }
+    if (threadIdx.x == 0) out[NV] = make_double2(fw * fw * s_sum[2 * NV], 0.0);
 }
 
 // Gram-Schmidt inner products: out[i] = <q_i, w>_M for i < NV and
@@ -276,11 +282,11 @@ __global__ void __launch_bounds__(kRedThreads) krylov_dots_kernel(
 }
 
 // The projector pass of G fused with the first Gram-Schmidt pass (FP64 form):
-// z is the cell pass applied to the stored V_{NV-1}, so
-// w[k][p] = f (ML^-1[k] z[k][p] - sum_j phi[k][j] S[j][p]) with f = s_f[NV-1]
-// is G q_{NV-1} on interior rows (0 on the others); it is written, and
-// out[i] = <q_i, w>_M (i < NV), out[NV] = <w, w>_M are formed from the values
-// in registers, so w is not read back.
+// z is the cell pass applied to the stored V_{NV-1}, so the raw vector
+// w[k][p] = ML^-1[k] z[k][p] - sum_j phi[k][j] S[j][p] on interior rows (0 on
+// the others) is G q_{NV-1} / s_f[NV-1]; it is written unscaled, and
+// out[i] = <q_i, G q_{NV-1}>_M (i < NV), out[NV] = |G q_{NV-1}|_M^2 are formed
+// from the values in registers, so w is not read back.
 template <int NV>
 __global__ void __launch_bounds__(kRedThreads) project_dots_kernel(
     const double2* __restrict__ z, const double2* __restrict__ phi, const double2* __restrict__ S,
@@ -293,7 +299,6 @@ __global__ void __launch_bounds__(kRedThreads) project_dots_kernel(
     for (int i = threadIdx.x; i < n * n; i += blockDim.x) s_S[i] = S[i];
     krylov_scales(H, ldh, beta2, NV, s_f);
     __syncthreads();
-    const double fz = s_f[NV - 1];
     double acc[2 * NV + 1];
 #pragma unroll
     for (int i = 0; i < 2 * NV + 1; ++i) acc[i] = 0.0;
@@ -316,7 +321,6 @@ __global__ void __launch_bounds__(kRedThreads) project_dots_kernel(
                     x.x = fma(-f.x, c.x, fma(f.y, c.y, x.x));
                     x.y = fma(-f.x, c.y, fma(-f.y, c.x, x.y));
                 }
-                x = make_double2(fz * x.x, fz * x.y);
                 accumulate_dots<NV>(acc, u, x, ml[k]);
             }
             w[o] = x;
@@ -340,7 +344,6 @@ __global__ void __launch_bounds__(kRedThreads) project32_dots_kernel(
     for (int i = threadIdx.x; i < n * n; i += blockDim.x) s_S[i] = make_float2(float(S[i].x), float(S[i].y));
     krylov_scales(H, ldh, beta2, NV, s_f);
     __syncthreads();
-    const double fz = s_f[NV - 1];
     double acc[2 * NV + 1];
 #pragma unroll
     for (int i = 0; i < 2 * NV + 1; ++i) acc[i] = 0.0;
@@ -363,7 +366,7 @@ __global__ void __launch_bounds__(kRedThreads) project32_dots_kernel(
                     xf.x = fmaf(-f.x, c.x, fmaf(f.y, c.y, xf.x));
                     xf.y = fmaf(-f.x, c.y, fmaf(-f.y, c.x, xf.y));
                 }
-                x = make_double2(fz * double(xf.x), fz * double(xf.y));
+                x = make_double2(double(xf.x), double(xf.y));
                 accumulate_dots<NV>(acc, u, x, ml[k]);
             }
             w[o] = x;
@@ -372,12 +375,13 @@ __global__ void __launch_bounds__(kRedThreads) project32_dots_kernel(
     finish_dots<NV>(acc, s_f, partial, counter, out);
 }
 
-// Gram-Schmidt update w -= sum_{i<NV} c_i q_i (interior rows; q_i = s_f[i] V_i)
-// with the new norm, and the complex64 copy of w in w32 when non-null (the
-// input of the next cell pass); the last block writes the Hessenberg column:
-// Hcol[i] = c_i (or += c_i when accumulate), Hcol[NV] = |w|_M, and
-// *reorth = 1 when a first pass left |w|^2 < eta2 * c[NV] (the squared norm
-// before it).  Skipped when gate && !*gate.
+// Gram-Schmidt update of the raw vector w (the true vector is fw w with
+// fw = s_f[NV-1]): fw w -= sum_{i<NV} c_i q_i, i.e. w -= sum_i (c_i s_f[i] / fw)
+// V_i (interior rows), with the new norm, and the complex64 copy of w in w32
+// when non-null (the input of the next cell pass); the last block writes the
+// Hessenberg column: Hcol[i] = c_i (or += c_i when accumulate),
+// Hcol[NV] = fw |w|_M, and *reorth = 1 when a first pass left
+// |fw w|^2 < eta2 * c[NV] (the squared norm before it).  Skipped when gate && !*gate.
 template <int NV>
 __global__ void __launch_bounds__(kRedThreads) krylov_update_kernel(
     double2* __restrict__ w, const double2* __restrict__ V, int64_t stride, const double2* __restrict__ c,
@@ -392,8 +396,11 @@ __global__ void __launch_bounds__(kRedThreads) krylov_update_kernel(
     krylov_scales(H, ldh, beta2, NV, s_f);
     if (int(threadIdx.x) <= NV) s_c[threadIdx.x] = c[threadIdx.x];
     __syncthreads();
-    if (int(threadIdx.x) < NV)
-        s_cf[threadIdx.x] = make_double2(s_c[threadIdx.x].x * s_f[threadIdx.x], s_c[threadIdx.x].y * s_f[threadIdx.x]);
+    const double fw = s_f[NV - 1];
+    if (int(threadIdx.x) < NV) {
+        const double f = fw > 0.0 ? s_f[threadIdx.x] / fw : 0.0;
+        s_cf[threadIdx.x] = make_double2(s_c[threadIdx.x].x * f, s_c[threadIdx.x].y * f);
+    }
     __syncthreads();
     double nrm[1] = {0.0};
     const RowCol rc(n);
@@ -424,53 +431,64 @@ __global__ void __launch_bounds__(kRedThreads) krylov_update_kernel(
             const double2 hh = accumulate ? make_double2(Hcol[i].x + s_c[i].x, Hcol[i].y + s_c[i].y) : s_c[i];
             Hcol[i] = hh;
         }
-        const double nn = fmax(s_sum[0], 0.0);
+        const double nn = fw * fw * fmax(s_sum[0], 0.0);   // |fw w|^2
         Hcol[NV] = make_double2(sqrt(nn), 0.0);
         if (reorth) *reorth = (!accumulate && nn < eta2 * s_c[NV].x) ? 1 : 0;
     }
 }
 
-// dst = src / d over all N*n entries (d = sqrt(*den) when is_sq, else *den),
-// or 0 when d <= 1e-14 beta (Krylov breakdown, beta = sqrt(*beta2)); the
-// complex64 copy v32 is written too when non-null.  src may equal dst.
-__global__ void normalize_kernel(const double2* src, double2* dst, const double2* __restrict__ den, int is_sq,
-                                 const double2* __restrict__ beta2, float2* __restrict__ v32, int64_t total) {
-    const double d = is_sq ? sqrt(fmax(den->x, 0.0)) : den->x;
-    const double beta = sqrt(fmax(beta2->x, 0.0));
-    const double f = (d > 1e-14 * beta && d > 0.0) ? 1.0 / d : 0.0;
-    for (int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; o < total;
-         o += int64_t(gridDim.x) * blockDim.x) {
-        const double2 x = src[o];
-        const double2 y = make_double2(x.x * f, x.y * f);
-        dst[o] = y;
-        if (v32) v32[o] = make_float2(float(y.x), float(y.y));
-    }
-}
-
-// phi_out = scale * sum_{i<m} y_i q_i  (q_i = s_f[i] V_i)
-__global__ void combine_kernel(const double2* __restrict__ V, int64_t stride, int m, const double2* __restrict__ y,
-                               double scale, const double2* __restrict__ H, int ldh, const double2* __restrict__ beta2,
-                               int64_t total, double2* __restrict__ out) {
-    __shared__ double2 s_y[kMaxKrylov];
-    __shared__ double s_f[kMaxKrylov];
-    krylov_scales(H, ldh, beta2, m, s_f);
+// Closes a substep and opens the next: x = scale sum_{i<M} y_i q_i (q_i =
+// s_f[i] V_i) is written to out (phi after the substep) and, as the next
+// substep's unscaled V_0, to V itself (element by element after its reads),
+// with the complex64 copy in v32 when non-null; the last block writes
+// beta2_out = |x|_M^2 over interior rows.  M = 0 opens the first substep
+// from src (out unused).  beta2_out may be beta2: every block reads beta2 at
+// its start and the last block writes after all others have finished.
+template <int M>
+__global__ void __launch_bounds__(kRedThreads) substep_close_kernel(
+    double2* V, int64_t stride, const double2* __restrict__ y, double scale, const double2* __restrict__ H, int ldh,
+    const double2* beta2, const double2* __restrict__ src, const double* __restrict__ ml, int64_t n_int, int64_t N,
+    int n, double2* __restrict__ out, float2* __restrict__ v32, double* __restrict__ partial,
+    unsigned* __restrict__ counter, double2* beta2_out) {
+    __shared__ double2 s_y[M > 0 ? M : 1];
+    __shared__ double s_f[M > 0 ? M : 1];
+    if (M > 0) krylov_scales(H, ldh, beta2, M, s_f);
     __syncthreads();
-    if (int(threadIdx.x) < m) {
+    if (int(threadIdx.x) < M) {
         const double f = scale * s_f[threadIdx.x];
         s_y[threadIdx.x] = make_double2(f * y[threadIdx.x].x, f * y[threadIdx.x].y);
     }
     __syncthreads();
-    for (int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; o < total;
-         o += int64_t(gridDim.x) * blockDim.x) {
-        double x = 0.0, yy = 0.0;
-        for (int i = 0; i < m; ++i) {
-            const double2 v = V[i * stride + o];
-            const double2 c = s_y[i];
-            x = fma(c.x, v.x, fma(-c.y, v.y, x));
-            yy = fma(c.x, v.y, fma(c.y, v.x, yy));
+    double nrm[1] = {0.0};
+    const RowCol rc(n);
+    if (rc.active) {
+        for (int64_t k = int64_t(blockIdx.x) * rc.R + rc.r; k < N; k += int64_t(gridDim.x) * rc.R) {
+            const int64_t o = k * n + rc.p;
+            double2 x;
+            if (M == 0) {
+                x = src[o];
+            } else {
+                double2 u[M > 0 ? M : 1];
+#pragma unroll
+                for (int i = 0; i < M; ++i) u[i] = V[i * stride + o];
+                x = make_double2(0.0, 0.0);
+#pragma unroll
+                for (int i = 0; i < M; ++i) {
+                    const double2 c = s_y[i];
+                    x.x = fma(c.x, u[i].x, fma(-c.y, u[i].y, x.x));
+                    x.y = fma(c.x, u[i].y, fma(c.y, u[i].x, x.y));
+                }
+                out[o] = x;
+            }
+            V[o] = x;
+            if (v32) v32[o] = make_float2(float(x.x), float(x.y));
+            if (k < n_int) nrm[0] = fma(ml[k], fma(x.x, x.x, x.y * x.y), nrm[0]);
         }
-        out[o] = make_double2(x, yy);
     }
+    block_row_partial<1>(nrm, 1, partial);
+    __shared__ double s_sum[kRedThreads];
+    if (!last_block_sum(partial, 1, counter, s_sum)) return;
+    if (threadIdx.x == 0) *beta2_out = make_double2(fmax(s_sum[0], 0.0), 0.0);
 }
 
 // exp(-i dt H) for an m x m complex matrix (m <= kMaxKrylov) by one block:
@@ -607,6 +625,27 @@ int launch_g_cell32(const afem_mesh* m, const double* E, const float2* v, const 
 
 #define AFEM_NV_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16)
 
+// One resident wave of kernel K (its occupancy per SM x the SMs), at most
+// `cap` blocks: the FP64-bound Gram-Schmidt kernels then have no tail wave,
+// and each thread covers more rows per FP64 block reduction.
+template <auto K>
+static unsigned wave_grid(unsigned cap) {
+    static const int per_sm = [] {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, K, kRedThreads, 0) != cudaSuccess || b < 1) b = 1;
+        return b;
+    }();
+    static const int sms = [] {
+        int dev = 0, c = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || c < 1)
+            c = 152;
+        return c;
+    }();
+    const unsigned g = unsigned(sms * per_sm);
+    return g < cap ? g : cap;
+}
+
 // The Gram-Schmidt kernels for a run-time vector count nv (0 <= nv <= kMaxKrylov).
 static int launch_krylov_dots(int nv, unsigned grid, cudaStream_t s, const double2* w, const double2* V,
                               int64_t stride, const double* ml, int64_t n_int, int n, const int* gate,
@@ -614,12 +653,14 @@ static int launch_krylov_dots(int nv, unsigned grid, cudaStream_t s, const doubl
                               double2* out) {
     switch (nv) {
         case 0:
-            AFEM_LAUNCH((krylov_dots_kernel<0>), grid, kRedThreads, 0, s, w, V, stride, ml, n_int, n, gate, H, ldh,
+            AFEM_LAUNCH((krylov_dots_kernel<0>), wave_grid<krylov_dots_kernel<0>>(grid), kRedThreads, 0, s, w, V,
+                        stride, ml, n_int, n, gate, H, ldh,
                         beta2, partial, counter, out);
             break;
 #define AFEM_DOTS_CASE(NVV)                                                                                       \
     case NVV:                                                                                                     \
-        AFEM_LAUNCH((krylov_dots_kernel<NVV>), grid, kRedThreads, 0, s, w, V, stride, ml, n_int, n, gate, H, ldh, \
+        AFEM_LAUNCH((krylov_dots_kernel<NVV>), wave_grid<krylov_dots_kernel<NVV>>(grid), kRedThreads, 0, s, w, V, \
+                    stride, ml, n_int, n, gate, H, ldh,                                                       \
                     beta2, partial, counter, out);                                                                \
         break;
             AFEM_NV_CASES(AFEM_DOTS_CASE)
@@ -641,10 +682,12 @@ static int launch_project_dots(int nv, unsigned grid, cudaStream_t s, const floa
 #define AFEM_PD_CASE(NVV)                                                                                           \
     case NVV:                                                                                                       \
         if (z32) {                                                                                                  \
-            AFEM_LAUNCH((project32_dots_kernel<NVV>), grid, kRedThreads, 0, s, z32, phi32, S, D.ml_inv, D.ml,      \
+            AFEM_LAUNCH((project32_dots_kernel<NVV>), wave_grid<project32_dots_kernel<NVV>>(grid), kRedThreads, 0, \
+                        s, z32, phi32, S, D.ml_inv, D.ml,                                                           \
                         D.n_interior, D.n_master, n, w, V, stride, H, ldh, beta2, partial, counter, out);           \
         } else {                                                                                                    \
-            AFEM_LAUNCH((project_dots_kernel<NVV>), grid, kRedThreads, 0, s, z, phi, S, D.ml_inv, D.ml,            \
+            AFEM_LAUNCH((project_dots_kernel<NVV>), wave_grid<project_dots_kernel<NVV>>(grid), kRedThreads, 0, s, \
+                        z, phi, S, D.ml_inv, D.ml,                                                                  \
                         D.n_interior, D.n_master, n, w, V, stride, H, ldh, beta2, partial, counter, out);           \
         }                                                                                                           \
         break;
@@ -665,13 +708,41 @@ static int launch_krylov_update(int nv, unsigned grid, cudaStream_t s, double2* 
     switch (nv) {
 #define AFEM_UPD_CASE(NVV)                                                                                      \
     case NVV:                                                                                                   \
-        AFEM_LAUNCH((krylov_update_kernel<NVV>), grid, kRedThreads, 0, s, w, V, stride, c, ml, n_int, n, gate,  \
+        AFEM_LAUNCH((krylov_update_kernel<NVV>), wave_grid<krylov_update_kernel<NVV>>(grid), kRedThreads, 0, s, \
+                    w, V, stride, c, ml, n_int, n, gate,                                                          \
                     accumulate, eta2, reorth, H, ldh, beta2, w32, partial, counter, Hcol);                      \
         break;
         AFEM_NV_CASES(AFEM_UPD_CASE)
 #undef AFEM_UPD_CASE
         default:
             return set_error(AFEM_EINVAL, "arnoldi: Krylov vector count out of range");
+    }
+    AFEM_CUDA_TRY(cudaGetLastError());
+    return AFEM_OK;
+}
+
+// substep_close_kernel for m = 0 (open the first substep from src) or the
+// substep's Krylov dimension m (1..kMaxKrylov).
+static int launch_substep_close(int m, unsigned grid, cudaStream_t s, double2* V, int64_t stride, const double2* y,
+                                double scale, const double2* H, int ldh, double2* beta2, const double2* src,
+                                const DeviceMesh& D, int n, double2* out, float2* v32, double* partial,
+                                unsigned* counter) {
+    switch (m) {
+        case 0:
+            AFEM_LAUNCH((substep_close_kernel<0>), wave_grid<substep_close_kernel<0>>(grid), kRedThreads, 0, s, V,
+                        stride, y, scale, H, ldh, beta2, src, D.ml, D.n_interior, D.n_master, n, out, v32, partial,
+                        counter, beta2);
+            break;
+#define AFEM_CLOSE_CASE(MM)                                                                                   \
+    case MM:                                                                                                  \
+        AFEM_LAUNCH((substep_close_kernel<MM>), wave_grid<substep_close_kernel<MM>>(grid), kRedThreads, 0, s, \
+                    V, stride, y, scale, H, ldh, beta2, src, D.ml, D.n_interior, D.n_master, n, out, v32,      \
+                    partial, counter, beta2);                                                                 \
+        break;
+            AFEM_NV_CASES(AFEM_CLOSE_CASE)
+#undef AFEM_CLOSE_CASE
+        default:
+            return set_error(AFEM_EINVAL, "arnoldi: Krylov dimension out of range");
     }
     AFEM_CUDA_TRY(cudaGetLastError());
     return AFEM_OK;
@@ -764,10 +835,10 @@ int arnoldi_reserve(afem_mesh* m, int n, int mk, ArnoldiWork& w) {
     return AFEM_OK;
 }
 
-// Candidate substep lengths of one ladder: tau_max * 2^(-c/2), c = 0..K-1.
+// Candidate substep lengths of one ladder: tau_max * 2^(-c/8), c = 0..K-1.
 static TauLadder make_ladder(double tau_max, int K) {
     TauLadder L{};
-    for (int c = 0; c < kLadder; ++c) L.tau[c] = c < K ? tau_max * std::pow(2.0, -0.5 * c) : 0.0;
+    for (int c = 0; c < kLadder; ++c) L.tau[c] = c < K ? tau_max * std::pow(2.0, -kLadderLog2 * c) : 0.0;
     return L;
 }
 
@@ -775,7 +846,7 @@ static TauLadder make_ladder(double tau_max, int K) {
 // tol <= 0: one Krylov step of dimension mk over the whole dt.  tol > 0:
 // substeps from fresh Krylov spaces of the same G, each as long as the error
 // estimate beta |h_{m+1,m}| |e_m^T exp(-i tau H_m) e_1| <= tol * beta allows
-// among the candidates tau_max 2^(-c/2), c = 0..15, where tau_max is the
+// among the candidates tau_max 2^(-c/8), c = 0..63, where tau_max is the
 // remainder for the first substep and min(remainder, 2 tau_previous) after
 // it; when no candidate passes, the ladder continues below the smallest one
 // (the paper fixes the Krylov accuracy by such an estimate; here the
@@ -805,7 +876,6 @@ int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double
     double* part = reinterpret_cast<double*>(w.cpartial);
     unsigned* cnt = w.counters + 1;
     const double eta2 = 1e-4;   // second pass when the update left less than 1e-2 of the norm
-    const double2* src = phi;
     double remaining = dt, tau_prev = 0.0;
     double err_sum = 0.0;
     int substeps = 0, m_used = mk, brk = 0;
@@ -815,15 +885,15 @@ int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double
         AFEM_CUDA_TRY(cudaStreamSynchronize(s));
         return AFEM_OK;
     };
+    float2* v32 = mixed ? w.v32 : nullptr;
+    // V_0 = phi (unscaled), its complex64 copy and beta^2 = <phi, phi>_M; later
+    // substeps get theirs from the closing pass of the previous one
+    if ((rc = launch_substep_close(0, gproj, s, w.V, NV, nullptr, 0.0, w.H, ldh, w.beta2, phi, D, n, nullptr, v32,
+                                   part, cnt)))
+        return rc;
     while (remaining > 0.0) {
         if (substeps >= 4096) return set_error(AFEM_EINVAL, "arnoldi: more than 4096 substeps (tolerance too tight)");
         AFEM_CUDA_TRY(cudaMemsetAsync(w.H, 0, sizeof(double2) * ldh * kMaxKrylov, s));
-        // beta^2 = <src, src>_M ; V_0 = src / beta
-        if ((rc = launch_krylov_dots(0, gdots, s, src, nullptr, NV, D.ml, D.n_interior, n, nullptr, w.H, ldh,
-                                     w.beta2, part, cnt, w.beta2)))
-            return rc;
-        float2* v32 = mixed ? w.v32 : nullptr;
-        AFEM_LAUNCH((normalize_kernel), grid_for(NV), 256, 0, s, src, w.V, w.beta2, 1, w.beta2, v32, NV);
         for (int j = 0; j < mk; ++j) {
             double2* Wn = w.V + (j + 1) * NV;
             double2* Hcol = w.H + j * ldh;
@@ -896,7 +966,7 @@ int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double
                 pick = K - 1;
                 break;
             }
-            tau_max *= std::pow(2.0, -0.5 * K);
+            tau_max *= std::pow(2.0, -kLadderLog2 * K);
             AFEM_LAUNCH((expm_ladder_kernel), K, 256, 0, s, w.H, ldh, m_used, make_ladder(tau_max, K), 0, w.col,
                         w.err);
             AFEM_CUDA_TRY(cudaGetLastError());
@@ -904,15 +974,14 @@ int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double
         }
         const double tau = make_ladder(tau_max, K).tau[pick];
         const double err = beta * res[kResErr + pick].x;
-        // phi_out = beta V_m exp(-i tau H_m) e_1
-        AFEM_LAUNCH((combine_kernel), grid_for(NV), 256, 0, s, w.V, NV, m_used, w.col + pick * kMaxKrylov, beta, w.H,
-                    ldh, w.beta2, NV, phi_out);
-        AFEM_CUDA_TRY(cudaGetLastError());
+        // phi_out = beta V_m exp(-i tau H_m) e_1, which also opens the next substep
+        if ((rc = launch_substep_close(m_used, gproj, s, w.V, NV, w.col + pick * kMaxKrylov, beta, w.H, ldh, w.beta2,
+                                       nullptr, D, n, phi_out, v32, part, cnt)))
+            return rc;
         err_sum += err;
         ++substeps;
         tau_prev = tau;
         remaining = (tau >= remaining) ? 0.0 : remaining - tau;
-        src = phi_out;
     }
     AFEM_CUDA_TRY(cudaStreamSynchronize(s));
     if (err_est) *err_est = err_sum;

@@ -7,7 +7,8 @@
 namespace afem {
 
 constexpr int kMaxKrylov = 16;
-constexpr int kLadder = 16;   // candidate substep lengths evaluated per ladder
+constexpr int kLadder = 64;             // candidate substep lengths evaluated per ladder
+constexpr double kLadderLog2 = 0.125;   // candidate c is tau_max * 2^(-c kLadderLog2)
 constexpr int kMaxOrbProj = 8;   // orbitals (the C ABI accepts 1..8)
 
 // Small results the host reads once per substep, contiguous in device memory:
