@@ -338,6 +338,45 @@ int afem_mctdhf_ci_dim(const afem_mctdhf* solver, int64_t* dim);
 int afem_mctdhf_step(afem_mctdhf* solver, void* phi, void* C, void* W, const double* E, double dt,
                      double cg_rtol, int cg_max_it, afem_step_info* info, void* stream);
 
+/* ---- Batching form: many independent instances in one launch.
+ * The FP32 cell passes of Sec. 3.1 (Eq. discretized_eom) applied to every
+ * instance of a batch of meshes (uneven sizes, degrees 1..4) by one persistent
+ * kernel: for each instance i, y_i = M_L^-1 H1~(E_i) x_i with Dirichlet rows
+ * zero (AFEM_OP_H1_C64: x_i, y_i complex64 [N_i][n_vec_i], n_vec_i even) or
+ * y_i = A x_i (AFEM_OP_STIFF_F32: float32 [N_i][n_vec_i], n_vec_i % 4 == 0),
+ * the same result as afem_op_apply on that mesh up to the order of the
+ * floating-point atomic sums.  The first apply of a (kind, n_vec) signature
+ * times candidate launch shapes on the batch itself (persistent grids of 1,
+ * 2 or all resident blocks per SM at 256 and 128 threads, and one block per
+ * cell) and keeps the fastest (afem_batch_get_tuning).  With
+ * AFEM_BATCH_GRAPH the zero, cell and scale passes are captured once into a
+ * CUDA graph on a private stream and replayed on `stream`; the per-instance
+ * table (pointers, fields) lives in device memory and is re-uploaded when
+ * an argument changes, so new buffers or fields need no new capture.
+ * Ownership: the batch holds the mesh handles (which must outlive it) and
+ * its own device table; x_i, y_i are caller-owned device buffers, 16-byte
+ * aligned, x_i != y_i.  E: host [count][3] or NULL (0 field); x, y, n_vec:
+ * host arrays of count entries.  Errors: AFEM_EINVAL (count outside 1..256,
+ * host-only mesh or mesh on another device, lanes not a multiple of 4,
+ * misaligned or aliased buffers), AFEM_ENOMEM, AFEM_ECUDA.  Asynchronous on
+ * `stream`, except that a changed table or a new signature synchronises it. */
+#define AFEM_BATCH_MAX 256
+#define AFEM_BATCH_GRAPH 1
+#define AFEM_BATCH_MAX_CAND 8
+typedef struct afem_batch afem_batch;   /* opaque */
+typedef struct {
+    int32_t tuned, block, grid, blocks_per_sm, n_candidates, count;
+    int64_t total_cells;
+    double cand_ms[AFEM_BATCH_MAX_CAND];   /* best-of-3 time of each candidate, ms */
+    int32_t cand_block[AFEM_BATCH_MAX_CAND];
+    int32_t cand_grid[AFEM_BATCH_MAX_CAND];
+} afem_batch_tuning;
+int afem_batch_create(afem_mesh* const* meshes, int count, afem_batch** out);
+int afem_batch_destroy(afem_batch* batch);
+int afem_batch_op_apply(afem_batch* batch, int kind, const double* E, void* const* x, void* const* y,
+                        const int* n_vec, int flags, void* stream);
+int afem_batch_get_tuning(const afem_batch* batch, afem_batch_tuning* out);
+
 #ifdef __cplusplus
 }
 #endif

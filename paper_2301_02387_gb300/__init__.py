@@ -284,3 +284,61 @@ def profile_read(cls, reset=False):
     _capi.check(_capi.load().afem_profile_read(int(cls), ctypes.byref(ms), ctypes.byref(calls),
                                                ctypes.byref(work), 1 if reset else 0))
     return ms.value, calls.value, work.value
+
+
+class Batch:
+    """afem_batch_*: the FP32 cell passes of many meshes in one persistent
+    launch (batching form), optionally replayed from a captured CUDA graph.
+
+    meshes: list of uploaded Mesh objects (kept alive by the batch)."""
+
+    def __init__(self, meshes):
+        self.meshes = list(meshes)
+        arr = (ctypes.c_void_p * len(self.meshes))(*[m.handle for m in self.meshes])
+        h = ctypes.c_void_p()
+        _capi.check(_capi.load().afem_batch_create(arr, len(self.meshes), ctypes.byref(h)))
+        self.handle = h
+
+    def apply(self, kind, xs, ys, E=None, graph=True, stream=None):
+        """y_i = op(x_i) for every instance: kind OP_H1_C64 (complex64 [N_i, n_i],
+        n_i even; E: list of 3-vectors or None) or OP_STIFF_F32 (float32 [N_i, k_i],
+        k_i % 4 == 0)."""
+        import torch
+        k = len(self.meshes)
+        if len(xs) != k or len(ys) != k:
+            raise ValueError("one input and one output per instance")
+        dt = torch.complex64 if kind == OP_H1_C64 else torch.float32
+        for m, x, y in zip(self.meshes, xs, ys):
+            _dev_ptr(x, dt, m.N, "x")
+            _dev_ptr(y, dt, m.N, "y")
+            if x.shape != y.shape:
+                raise ValueError("x and y shapes differ")
+        xa = (ctypes.c_void_p * k)(*[x.data_ptr() for x in xs])
+        ya = (ctypes.c_void_p * k)(*[y.data_ptr() for y in ys])
+        nv = (ctypes.c_int * k)(*[int(x.shape[1]) for x in xs])
+        Earr = None
+        if E is not None:
+            Earr = (ctypes.c_double * (3 * k))(*[float(v) for e in E for v in e])
+        _capi.check(_capi.load().afem_batch_op_apply(
+            self.handle, int(kind), ctypes.cast(Earr, ctypes.c_void_p) if Earr is not None else None,
+            xa, ya, nv, _capi.BATCH_GRAPH if graph else 0, _stream_ptr(stream)))
+        return ys
+
+    def tuning(self):
+        """The launch shape the autotuner kept and every candidate's time (ms)."""
+        t = _capi.BatchTuning()
+        _capi.check(_capi.load().afem_batch_get_tuning(self.handle, ctypes.byref(t)))
+        cands = [(int(t.cand_block[i]), int(t.cand_grid[i]), float(t.cand_ms[i])) for i in range(t.n_candidates)]
+        return {"tuned": bool(t.tuned), "block": t.block, "grid": t.grid, "blocks_per_sm": t.blocks_per_sm,
+                "count": t.count, "total_cells": int(t.total_cells), "candidates": cands}
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            _capi.load().afem_batch_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

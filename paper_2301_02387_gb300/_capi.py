@@ -67,6 +67,22 @@ class StepInfo(ctypes.Structure):
     ]
 
 
+BATCH_MAX = 256
+BATCH_GRAPH = 1
+BATCH_MAX_CAND = 8
+
+
+class BatchTuning(ctypes.Structure):
+    _fields_ = [
+        ("tuned", ctypes.c_int32), ("block", ctypes.c_int32), ("grid", ctypes.c_int32),
+        ("blocks_per_sm", ctypes.c_int32), ("n_candidates", ctypes.c_int32), ("count", ctypes.c_int32),
+        ("total_cells", ctypes.c_int64),
+        ("cand_ms", ctypes.c_double * BATCH_MAX_CAND),
+        ("cand_block", ctypes.c_int32 * BATCH_MAX_CAND),
+        ("cand_grid", ctypes.c_int32 * BATCH_MAX_CAND),
+    ]
+
+
 class AfemError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"afem error {code}: {msg}")
@@ -110,6 +126,11 @@ SIGNATURES = {
     "afem_mctdhf_ci_dim": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
     "afem_mctdhf_step": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                         ctypes.POINTER(StepInfo), _P]),
+    "afem_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P)]),
+    "afem_batch_destroy": (ctypes.c_int, [_P]),
+    "afem_batch_op_apply": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                           ctypes.POINTER(ctypes.c_int), ctypes.c_int, _P]),
+    "afem_batch_get_tuning": (ctypes.c_int, [_P, ctypes.POINTER(BatchTuning)]),
 }
 
 

@@ -6,6 +6,9 @@
 // complex64, reading float copies of the mesh tables, so no FP64 instruction
 // runs inside the cell loop.  Callers keep the accuracy-critical parts in FP64
 // (Krylov Gram-Schmidt, residuals of the Poisson refinement).
+#include <algorithm>
+#include <cstring>
+
 #include "afem_internal.h"
 #include "cell_common.cuh"
 
@@ -181,12 +184,16 @@ __device__ __forceinline__ void scatter32v(const CellArgs32& a, int idx, float4*
     }
 }
 
+// The four-lane cell pass of one cell by the whole block (any block size):
+// the body of cell32v_kernel, also called per (instance, cell) by the batched
+// kernels.  Uses the block's shared memory; a caller looping over cells
+// synchronises the block between two calls.
 // L4C > 0 fixes the quad count at compile time (no integer division per item);
 // L4C = 0 takes it from L4rt.
 template <int P, bool G, int L4C>
-__global__ void __launch_bounds__(256) cell32v_kernel(CellArgs32 a, const float4* __restrict__ x,
-                                                      const float2* __restrict__ U, float4* __restrict__ y, int L4rt,
-                                                      int n) {
+__device__ __forceinline__ void cell32v_body(const CellArgs32& a, int64_t cell, const float4* __restrict__ x,
+                                             const float2* __restrict__ U, float4* __restrict__ y, int L4rt,
+                                             int n) {
     constexpr int P1 = P + 1;
     constexpr int NN = P1 * P1 * P1;
     const int L4 = L4C > 0 ? L4C : L4rt;
@@ -198,7 +205,6 @@ __global__ void __launch_bounds__(256) cell32v_kernel(CellArgs32 a, const float4
     __shared__ float s_wq[NN];
     __shared__ float s_K[P1 * P1];
     __shared__ float s_w[P1];
-    const int64_t cell = blockIdx.x;
     const int tid = threadIdx.x, bs = blockDim.x;
     const float4 g = a.geom[cell];
     for (int i = tid; i < NN; i += bs) s_idx[i] = a.cell_node[cell * NN + i];
@@ -283,6 +289,13 @@ __global__ void __launch_bounds__(256) cell32v_kernel(CellArgs32 a, const float4
         }
         scatter32v(a, s_idx[i], y, L4, q, r);
     }
+}
+
+template <int P, bool G, int L4C>
+__global__ void __launch_bounds__(256) cell32v_kernel(const __grid_constant__ CellArgs32 a,
+                                                      const float4* __restrict__ x, const float2* __restrict__ U,
+                                                      float4* __restrict__ y, int L4rt, int n) {
+    cell32v_body<P, G, L4C>(a, blockIdx.x, x, U, y, L4rt, n);
 }
 
 // Line-ordered form of the four-lane pass: the three 1D contractions run as
@@ -555,6 +568,168 @@ int launch_g_cell32(const afem_mesh* m, const double* E, const float2* v, const 
     if (n % 2 == 0 && aligned16(v) && aligned16(z))
         return launch32v<true>(m, a, reinterpret_cast<const float*>(v), U, reinterpret_cast<float*>(z), 2 * n, n, s);
     return launch32<float2, true>(m, a, v, U, z, n, s);
+}
+
+// ---------------------------------------------------------------- batching
+// One instance of a batched FP32 cell pass (the batching form: many meshes of
+// uneven size and degree in one persistent launch).  Kept in device memory and
+// read by the batched kernels, so a captured graph holds no instance pointer.
+struct BatchInst32 {
+    CellArgs32 a;             // mesh tables; masked and E set per apply
+    const float4* x;          // [N][4 L4] input
+    float4* y;                // [N][4 L4] output
+    const double* ml_inv;     // M_L^-1 for the orbital operator, null for the stiffness
+    int64_t cell0;            // first global work item of the instance
+    int64_t n_rows;           // masters
+    int p, L4;
+};
+
+size_t batch32_inst_bytes() { return sizeof(BatchInst32); }
+
+// Fills the instance record for mesh m: kind AFEM_OP_H1_C64 (nvec complex
+// orbitals, nvec even) or AFEM_OP_STIFF_F32 (nvec real columns, nvec % 4 == 0).
+int batch32_fill(const afem_mesh* m, int kind, const double* E, const void* x, void* y, int nvec, int64_t cell0,
+                 void* out) {
+    BatchInst32 b{};
+    b.a = make_cell_args32(m);
+    const int L = kind == AFEM_OP_H1_C64 ? 2 * nvec : nvec;
+    if (L % 4 != 0 || !aligned16(x) || !aligned16(y))
+        return set_error(AFEM_EINVAL, "afem_batch_op_apply: needs 16-byte aligned buffers and 4 float lanes per "
+                                      "quad (an even orbital count, or real columns in multiples of 4)");
+    b.a.masked = kind == AFEM_OP_H1_C64 ? 1 : 0;
+    for (int i = 0; i < 3; ++i) b.a.E[i] = (kind == AFEM_OP_H1_C64 && E) ? float(E[i]) : 0.0f;
+    b.x = static_cast<const float4*>(x);
+    b.y = static_cast<float4*>(y);
+    b.ml_inv = kind == AFEM_OP_H1_C64 ? m->dev.ml_inv : nullptr;
+    b.cell0 = cell0;
+    b.n_rows = m->dev.n_master;
+    b.p = m->dev.p;
+    b.L4 = L / 4;
+    std::memcpy(out, &b, sizeof(b));
+    return AFEM_OK;
+}
+
+constexpr int kBatchMaxInst = 256;
+
+// Out-of-line copies of the cell-pass bodies: each keeps its own register
+// budget instead of the batched kernel taking the largest of all of them.
+template <int P, bool G, int L4C>
+__device__ __noinline__ void cell32v_body_call(const BatchInst32& b, int64_t cell) {
+    cell32v_body<P, G, L4C>(b.a, cell, b.x, nullptr, b.y, b.L4, 2 * b.L4);
+}
+
+// The cell pass of one work item (instance, cell) by the whole block.
+template <bool G>
+__device__ __forceinline__ void batch_item(const BatchInst32& b, int64_t cell) {
+    switch (b.p * 8 + (b.L4 == 1 ? 1 : b.L4 == 2 ? 2 : b.L4 == 4 ? 4 : 0)) {
+#define AFEM_BI(PP, LL)                          \
+    case PP * 8 + LL:                            \
+        cell32v_body_call<PP, G, LL>(b, cell);   \
+        break;
+        AFEM_BI(1, 0) AFEM_BI(1, 1) AFEM_BI(1, 2) AFEM_BI(1, 4)
+        AFEM_BI(2, 0) AFEM_BI(2, 1) AFEM_BI(2, 2) AFEM_BI(2, 4)
+        AFEM_BI(3, 0) AFEM_BI(3, 1) AFEM_BI(3, 2) AFEM_BI(3, 4)
+        AFEM_BI(4, 0) AFEM_BI(4, 1) AFEM_BI(4, 2) AFEM_BI(4, 4)
+#undef AFEM_BI
+        default:
+            break;
+    }
+}
+
+// Persistent batched cell pass: block b takes work items b, b + grid, ... of
+// the concatenated cell lists (all instances' cells, instance by instance).
+// The current instance's record is staged in shared memory (its tables, 1D
+// matrices and field are then read from there, as the single-instance kernel
+// reads them from its parameters), refreshed only when the instance changes.
+template <bool G>
+__global__ void batch_cell32_kernel(const BatchInst32* __restrict__ inst, int count, int64_t total) {
+    __shared__ int64_t s_off[kBatchMaxInst + 1];
+    __shared__ BatchInst32 s_inst;
+    static_assert(sizeof(BatchInst32) % 8 == 0, "instance record is copied as 8-byte words");
+    for (int i = threadIdx.x; i <= count; i += blockDim.x)
+        s_off[i] = i < count ? inst[i].cell0 : total;
+    __syncthreads();
+    int lo = 0, cur = -1;
+    for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
+        while (lo + 1 < count && s_off[lo + 1] <= g) ++lo;   // items ascend within a block
+        if (lo != cur) {   // the same for every thread of the block
+            const auto* src = reinterpret_cast<const unsigned long long*>(inst + lo);
+            auto* dst = reinterpret_cast<unsigned long long*>(&s_inst);
+            for (int i = threadIdx.x; i < int(sizeof(BatchInst32) / 8); i += blockDim.x) dst[i] = src[i];
+            cur = lo;
+            __syncthreads();
+        }
+        batch_item<G>(s_inst, g - s_off[lo]);
+        __syncthreads();
+    }
+}
+
+// y_i = 0 for every instance before the scatter.
+__global__ void batch_zero_kernel(const BatchInst32* __restrict__ inst, int count) {
+    for (int i = 0; i < count; ++i) {
+        float4* y = inst[i].y;
+        const int64_t total = inst[i].n_rows * inst[i].L4;
+        for (int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; o < total;
+             o += int64_t(gridDim.x) * blockDim.x)
+            y[o] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+// y_i[k] *= M_L^-1[k] (the orbital operator).
+__global__ void batch_scale_kernel(const BatchInst32* __restrict__ inst, int count) {
+    for (int i = 0; i < count; ++i) {
+        const double* s = inst[i].ml_inv;
+        if (!s) continue;
+        float4* y = inst[i].y;
+        const int L4 = inst[i].L4;
+        const int64_t total = inst[i].n_rows * L4;
+        for (int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; o < total;
+             o += int64_t(gridDim.x) * blockDim.x) {
+            const float f = float(s[o / L4]);
+            float4 v = y[o];
+            v.x *= f;
+            v.y *= f;
+            v.z *= f;
+            v.w *= f;
+            y[o] = v;
+        }
+    }
+}
+
+// Dynamic shared memory of the batched cell pass: the largest instance's
+// [(p+1)^3][L4] float4 tile.
+size_t batch32_smem(const std::vector<int>& p, const std::vector<int>& L4) {
+    size_t mx = 0;
+    for (size_t i = 0; i < p.size(); ++i) {
+        const size_t nn = size_t(p[i] + 1) * (p[i] + 1) * (p[i] + 1);
+        mx = std::max(mx, nn * L4[i] * sizeof(float4));
+    }
+    return mx;
+}
+
+int batch32_occupancy(int kind, int block, size_t smem, int* per_sm) {
+    const void* k = kind == AFEM_OP_H1_C64 ? reinterpret_cast<const void*>(batch_cell32_kernel<true>)
+                                           : reinterpret_cast<const void*>(batch_cell32_kernel<false>);
+    if (smem > 48 * 1024) AFEM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    AFEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k, block, smem));
+    if (*per_sm < 1) return set_error(AFEM_EINVAL, "afem_batch: the batched cell pass does not fit on an SM");
+    return AFEM_OK;
+}
+
+// zero, persistent cell pass over all instances, M_L^-1 (orbital operator).
+int batch32_launch(int kind, const void* d_inst, int count, int64_t total, int block, unsigned grid, size_t smem,
+                   cudaStream_t s) {
+    if (count < 1 || count > kBatchMaxInst) return set_error(AFEM_EINVAL, "afem_batch: 1..256 instances");
+    const auto* inst = static_cast<const BatchInst32*>(d_inst);
+    AFEM_LAUNCH((batch_zero_kernel), 152 * 8, 256, 0, s, inst, count);
+    if (kind == AFEM_OP_H1_C64) {
+        AFEM_LAUNCH((batch_cell32_kernel<true>), grid, block, smem, s, inst, count, total);
+        AFEM_LAUNCH((batch_scale_kernel), 152 * 8, 256, 0, s, inst, count);
+    } else {
+        AFEM_LAUNCH((batch_cell32_kernel<false>), grid, block, smem, s, inst, count, total);
+    }
+    AFEM_CUDA_TRY(cudaGetLastError());
+    return AFEM_OK;
 }
 
 }  // namespace afem

@@ -136,3 +136,32 @@ def initial_ci(n_orb, n_alpha, n_beta, seed=BASE_SEED, amp=1e-2):
     C = amp * (rng.standard_normal(na_str * nb_str) + 1j * rng.standard_normal(na_str * nb_str))
     C[0] = 1.0
     return C / np.linalg.norm(C)
+
+
+def batch_instances(count=64, seed=BASE_SEED, dof_range=(5e4, 2e6), box=30.0):
+    """Seeded instances of the batching form: target DoF counts log-uniform in
+    dof_range, degree p in {2, 3, 4}, 1-3 nuclei with Z in 1..8 uniformly within
+    3 bohr of the origin (2 refinement levels each), an even orbital count in
+    {2, 4, 6, 8} (the batched FP32 pass takes orbitals in pairs), and a field of
+    amplitude uniform in [0.01, 0.08] along a random direction.  The coarse
+    count n_c = round(N_target^(1/3) / p) (at least 2) sets the size; the
+    refinement adds a few percent.  Returns a list of dicts with mesh_args,
+    n_orb and E."""
+    rng = np.random.default_rng(seed + 7)
+    out = []
+    for i in range(count):
+        target = float(np.exp(rng.uniform(np.log(dof_range[0]), np.log(dof_range[1]))))
+        p = int(rng.integers(2, 5))
+        nc = max(2, int(round(target ** (1.0 / 3.0) / p)))
+        nnuc = int(rng.integers(1, 4))
+        nuclei = []
+        for _ in range(nnuc):
+            d = rng.standard_normal(3)
+            d *= rng.uniform(0.0, 3.0) / max(np.linalg.norm(d), 1e-12)
+            nuclei.append(((float(d[0]), float(d[1]), float(d[2])), float(rng.integers(1, 9)), 2))
+        n_orb = int(2 * rng.integers(1, 5))
+        e = rng.standard_normal(3)
+        e *= rng.uniform(0.01, 0.08) / np.linalg.norm(e)
+        out.append(dict(mesh_args=(-box, box, nc, p, nuclei, 2.0), n_orb=n_orb, E=tuple(float(v) for v in e),
+                        target_dofs=target))
+    return out

@@ -86,3 +86,16 @@ def test_profile_classes_host_side():
     pkg.profile_enable(False)
     for c in range(pkg.PROF_COUNT):
         assert pkg.profile_read(c, reset=True) == (0.0, 0, 0.0)
+
+
+def test_batch_create_rejects_bad_inputs_host_side():
+    """afem_batch_create refuses an empty batch and host-only meshes before
+    touching a device."""
+    import ctypes
+    from paper_2301_02387_gb300 import _capi, Mesh
+    lib = _capi.load()
+    h = ctypes.c_void_p()
+    assert lib.afem_batch_create(None, 0, ctypes.byref(h)) == _capi.AFEM_EINVAL
+    m = Mesh(-2.0, 2.0, 1, 2, [], 2.0, host_only=True)
+    arr = (ctypes.c_void_p * 1)(m.handle)
+    assert lib.afem_batch_create(arr, 1, ctypes.byref(h)) == _capi.AFEM_EINVAL and not h.value
