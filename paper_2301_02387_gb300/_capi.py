@@ -27,6 +27,7 @@ OP_H1 = 0
 OP_STIFF = 1
 OP_STIFF_F32 = 2
 OP_H1_C64 = 3
+OP_POS = 4
 
 PROF_GS = 0
 PROF_GCELL32 = 1
@@ -131,6 +132,12 @@ SIGNATURES = {
     "afem_batch_op_apply": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.POINTER(_P), ctypes.POINTER(_P),
                                            ctypes.POINTER(ctypes.c_int), ctypes.c_int, _P]),
     "afem_batch_get_tuning": (ctypes.c_int, [_P, ctypes.POINTER(BatchTuning)]),
+    "afem_tdse_forward": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                         ctypes.c_double, ctypes.c_int, _P, _P, _P, _P, ctypes.c_int, _P]),
+    "afem_tdse_jvp": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                     ctypes.c_int, _P, _P, _P, _P, _P]),
+    "afem_tdse_vjp": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                     ctypes.c_int, _P, ctypes.c_int, _P, _P, _P, _P]),
 }
 
 

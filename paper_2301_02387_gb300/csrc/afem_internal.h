@@ -141,6 +141,7 @@ struct afem_mesh {
     bool host_only = false;
     afem::Workspace ws_poisson;
     afem::Workspace ws_arnoldi;
+    afem::Workspace ws_tdse;
     int cell32_variant = 0;   // FP32 four-lane cell pass: 0 node-per-thread, 1 line-ordered
 };
 
@@ -163,4 +164,12 @@ void mctdhf_set_precision(afem_mctdhf* S, int precision);
 void mctdhf_set_krylov_tol(afem_mctdhf* S, double tol);
 int mctdhf_step(afem_mctdhf* S, double2* phi, double2* C, double* W, const double* E, double dt, double cg_rtol,
                 int cg_max_it, afem_step_info* info, cudaStream_t s);
+int tdse_forward(afem_mesh* m, const double* e_dir, const double* E, int K, double dt, int mk, double tol,
+                 int precision, const double2* phi0, double2* phi_end, double* d, double2* ckpt, int every,
+                 cudaStream_t s);
+int tdse_jvp(afem_mesh* m, const double* e_dir, const double* E, int K, double dt, int mk, double tol,
+             int precision, const double2* phi0, const double* v, double* d, double* dd, cudaStream_t s);
+int tdse_vjp(afem_mesh* m, const double* e_dir, const double* E, int K, double dt, int mk, double tol,
+             int precision, const double2* ckpt, int every, const double* g, double* grad_E, double2* lam0,
+             cudaStream_t s);
 }  // namespace afem

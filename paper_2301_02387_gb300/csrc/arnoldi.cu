@@ -853,7 +853,7 @@ static TauLadder make_ladder(double tau_max, int K) {
 // dimension is fixed and the substep adapts).
 int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double2* U, const float2* U32, int n,
                  int mk, double dt, int mixed, double tol, double2* phi_out, double* err_est, int* m_used_out,
-                 int* breakdown_out, int* substeps_out, cudaStream_t s) {
+                 int* breakdown_out, int* substeps_out, cudaStream_t s, int flags) {
     const DeviceMesh& D = m->dev;
     if (mk < 1 || mk > kMaxKrylov) return set_error(AFEM_EINVAL, "arnoldi: krylov_m out of range");
     if (n < 1 || n > kMaxOrbProj) return set_error(AFEM_EINVAL, "arnoldi: orbital count out of range");
@@ -861,6 +861,15 @@ int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double
     int rc = arnoldi_reserve(m, n, mk, w);
     if (rc) return rc;
     const int64_t NV = w.stride;
+    const bool projector = !(flags & kArnNoProjector);
+    // candidate exponentials exp(-i tau H_m), or exp(+i tau H_m) propagating backward
+    auto signed_ladder = [&](double tm, int K) {
+        TauLadder L = make_ladder(tm, K);
+        if (flags & kArnBackward)
+            for (int c = 0; c < kLadder; ++c) L.tau[c] = -L.tau[c];
+        return L;
+    };
+    if (!projector) AFEM_CUDA_TRY(cudaMemsetAsync(w.S, 0, sizeof(double2) * kMaxOrbProj * kMaxOrbProj, s));
     if (mixed) {
         if (U && !U32) {
             if ((rc = to_c64(U, w.U32, D.n_master * n * n, s))) return rc;
@@ -901,7 +910,13 @@ int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double
             // pass) with the inner products against q_0..q_j, the update (which
             // leaves V_{j+1} = h_{j+1,j} q_{j+1}), and a second pass when the
             // update cancelled most of w
-            if (mixed) {
+            if (!projector) {   // the cell pass alone; S stays zero
+                if (mixed) {
+                    if ((rc = launch_g_cell32(m, E, w.v32, U32, w.z32, n, s))) return rc;
+                } else {
+                    if ((rc = launch_g_cell(m, E, w.V + j * NV, U, w.z, n, s))) return rc;
+                }
+            } else if (mixed) {
                 if ((rc = g_cell_overlaps32(m, E, w.phi32, U32, n, w.v32, w, s))) return rc;
             } else {
                 if ((rc = g_cell_overlaps(m, E, phi, U, n, w.V + j * NV, w, s))) return rc;
@@ -928,7 +943,7 @@ int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double
         double tau_max = (tol <= 0.0 || substeps == 0) ? remaining : std::fmin(remaining, 2.0 * tau_prev);
         int K = tol <= 0.0 ? 1 : kLadder;
         int exact = 0;
-        AFEM_LAUNCH((expm_ladder_kernel), K, 256, 0, s, w.H, ldh, mk, make_ladder(tau_max, K), 0, w.col, w.err);
+        AFEM_LAUNCH((expm_ladder_kernel), K, 256, 0, s, w.H, ldh, mk, signed_ladder(tau_max, K), 0, w.col, w.err);
         AFEM_CUDA_TRY(cudaGetLastError());
         if ((rc = fetch())) return rc;
         const double beta = std::sqrt(res[kResBeta2].x);
@@ -948,7 +963,7 @@ int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double
             tau_max = remaining;
             K = 1;
             exact = 1;
-            AFEM_LAUNCH((expm_ladder_kernel), 1, 256, 0, s, w.H, ldh, m_used, make_ladder(tau_max, 1), 1, w.col,
+            AFEM_LAUNCH((expm_ladder_kernel), 1, 256, 0, s, w.H, ldh, m_used, signed_ladder(tau_max, 1), 1, w.col,
                         w.err);
             AFEM_CUDA_TRY(cudaGetLastError());
             if ((rc = fetch())) return rc;
@@ -967,7 +982,7 @@ int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double
                 break;
             }
             tau_max *= std::pow(2.0, -kLadderLog2 * K);
-            AFEM_LAUNCH((expm_ladder_kernel), K, 256, 0, s, w.H, ldh, m_used, make_ladder(tau_max, K), 0, w.col,
+            AFEM_LAUNCH((expm_ladder_kernel), K, 256, 0, s, w.H, ldh, m_used, signed_ladder(tau_max, K), 0, w.col,
                         w.err);
             AFEM_CUDA_TRY(cudaGetLastError());
             if ((rc = fetch())) return rc;

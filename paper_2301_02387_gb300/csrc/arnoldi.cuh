@@ -43,9 +43,14 @@ struct ArnoldiWork {
 
 int cdot(const double2* A, int na, const double2* B, int nb, const double* w, int64_t rows, int diag,
          double2* partial, double2* out, unsigned* counter, cudaStream_t s);
+// flags: kArnNoProjector applies H1~ + mean field without the projector Q
+// (the one-electron Schroedinger propagator and its block Frechet form);
+// kArnBackward propagates by exp(+i G dt).
+constexpr int kArnNoProjector = 1;
+constexpr int kArnBackward = 2;
 int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double2* U, const float2* U32, int n,
                  int mk, double dt, int mixed, double tol, double2* phi_out, double* err_est, int* m_used_out,
-                 int* breakdown_out, int* substeps_out, cudaStream_t s);
+                 int* breakdown_out, int* substeps_out, cudaStream_t s, int flags = 0);
 int to_c64(const double2* x, float2* y, int64_t n, cudaStream_t s);
 
 }  // namespace afem

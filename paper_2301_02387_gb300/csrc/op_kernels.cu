@@ -50,7 +50,8 @@ __global__ void __launch_bounds__(256) cell_op_kernel(CellArgs a, const T* __res
         for (int n = tid; n < NN; n += bs) {
             const int ia = n % P1, ib = (n / P1) % P1, ic = n / (P1 * P1);
             const int idx = s_idx[n];
-            const double V = idx >= 0 ? a.v_master[idx] : a.v_hang[-idx - 1];
+            // with_pot == 2: the field term E.r alone (the position operator)
+            const double V = a.with_pot == 2 ? 0.0 : (idx >= 0 ? a.v_master[idx] : a.v_hang[-idx - 1]);
             const double px = g.x + g.w * a.B.xi[ia];
             const double py = g.y + g.w * a.B.xi[ib];
             const double pz = g.z + g.w * a.B.xi[ic];
@@ -308,6 +309,17 @@ int launch_op_apply(afem_mesh* m, int kind, const double* E, const void* x, void
         auto* yy = static_cast<double*>(y);
         AFEM_CUDA_TRY(cudaMemsetAsync(yy, 0, size_t(N) * nv * sizeof(double), s));
         return launch_cell_op<double>(m, a, static_cast<const double*>(x), yy, nv, s);
+    }
+    if (kind == AFEM_OP_POS) {   // y = M_L^-1 F[e.r] x, Dirichlet-masked
+        a.c_kin = 0.0;
+        a.with_pot = 2;
+        a.masked = 1;
+        for (int i = 0; i < 3; ++i) a.E[i] = E ? E[i] : 0.0;
+        auto* yy = static_cast<double2*>(y);
+        AFEM_CUDA_TRY(cudaMemsetAsync(yy, 0, size_t(N) * nv * sizeof(double2), s));
+        int rc = launch_cell_op<double2>(m, a, static_cast<const double2*>(x), yy, nv, s);
+        if (rc) return rc;
+        return launch_scale_rows<double2>(yy, m->dev.ml_inv, N, nv, s);
     }
     if (kind == AFEM_OP_STIFF_F32)
         return launch_stiffness32(m, static_cast<const float*>(x), static_cast<float*>(y), nv, 0, s);

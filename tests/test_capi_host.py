@@ -99,3 +99,55 @@ def test_batch_create_rejects_bad_inputs_host_side():
     m = Mesh(-2.0, 2.0, 1, 2, [], 2.0, host_only=True)
     arr = (ctypes.c_void_p * 1)(m.handle)
     assert lib.afem_batch_create(arr, 1, ctypes.byref(h)) == _capi.AFEM_EINVAL and not h.value
+
+
+def test_tdse_entry_points_reject_bad_inputs_host_side():
+    """afem_tdse_* refuse host-only meshes, negative step counts, non-positive
+    dt, bad Krylov dimensions and missing checkpoints before any device work."""
+    from paper_2301_02387_gb300 import _capi, Mesh
+    lib = _capi.load()
+    m = Mesh(-2.0, 2.0, 1, 2, [], 2.0, host_only=True)
+    e = (ctypes.c_double * 3)(0.0, 0.0, 1.0)
+    E = (ctypes.c_double * 2)(0.01, 0.02)
+    d = (ctypes.c_double * 3)()
+    g = (ctypes.c_double * 3)(1.0, 1.0, 1.0)
+    x = ctypes.c_void_p(16)   # never dereferenced: every call below fails its checks first
+    assert lib.afem_tdse_forward(m.handle, e, E, 2, 0.1, 8, 0.0, 0, x, None, d, None, 0, None) == _capi.AFEM_EINVAL
+    assert b"host-only" in lib.afem_last_error()
+    m2 = Mesh(-2.0, 2.0, 1, 2, [], 2.0, host_only=True)
+    for args, why in [((2, -0.1, 8, 0.0, 0), b"dt"), ((2, 0.1, 0, 0.0, 0), b"krylov_m"),
+                      ((2, 0.1, 17, 0.0, 0), b"krylov_m"), ((2, 0.1, 8, -1.0, 0), b"tol"),
+                      ((2, 0.1, 8, 0.0, 5), b"precision"), ((-1, 0.1, 8, 0.0, 0), b"n_steps")]:
+        K, dt, mk, tol, prec = args
+        assert lib.afem_tdse_forward(m2.handle, e, E, K, dt, mk, tol, prec, x, None, d, None, 0,
+                                     None) == _capi.AFEM_EINVAL
+        assert why in lib.afem_last_error(), (args, lib.afem_last_error())
+    assert lib.afem_tdse_vjp(m2.handle, e, E, 0, 0.1, 8, 0.0, 0, x, 1, g, d, None, None) == _capi.AFEM_EINVAL
+    assert lib.afem_tdse_vjp(m2.handle, e, E, 2, 0.1, 8, 0.0, 0, None, 1, g, d, None, None) == _capi.AFEM_EINVAL
+    assert lib.afem_tdse_jvp(None, e, E, 2, 0.1, 8, 0.0, 0, x, E, d, d, None) == _capi.AFEM_EINVAL
+
+
+def test_spline_and_harmonic_yield_helpers():
+    """The cubic-spline field map reproduces linear fields exactly and
+    interpolates its samples; the harmonic yield equals the band sum of the
+    squared FFT of the second-difference acceleration."""
+    import torch
+    from paper_2301_02387_gb300 import adjoint as adj
+    S = adj.spline_matrix(9, 33)
+    assert S.shape == (33, 9)
+    t = np.linspace(0.0, 1.0, 9)
+    x = np.linspace(0.0, 1.0, 33)
+    np.testing.assert_allclose(S @ (2.0 - 3.0 * t), 2.0 - 3.0 * x, atol=1e-13)
+    np.testing.assert_allclose(S[::4], np.eye(9), atol=1e-13)
+    assert adj.n_checkpoints(100, 50) == 2 and adj.n_checkpoints(101, 50) == 3 and adj.n_checkpoints(1, 50) == 1
+    rng = np.random.default_rng(0)
+    d = rng.standard_normal(64)
+    dt, w0 = 0.1, 0.4
+    a = np.diff(d, 2) / dt ** 2
+    A = np.fft.rfft(a)
+    w = 2 * np.pi * np.arange(len(A)) / (len(a) * dt)
+    band = (w >= 3 * w0) & (w <= 9 * w0)
+    assert band.sum() >= 2
+    ref = np.sum(np.abs(A[band]) ** 2)
+    got = adj.harmonic_yield(torch.from_numpy(d), dt, w0, 3, 9).item()
+    assert abs(got - ref) <= 1e-12 * ref
