@@ -221,6 +221,63 @@ def run_batch(torch, pkg, inputs, reps=10, count=64):
                       "1-3 nuclei Z 1..8 within 3 bohr, 2-8 orbitals (even), |E| 0.01..0.08"}
 
 
+def run_diff(torch, pkg, inputs, mesh, phi_col, steps=10, every=5, krylov_tol=1e-10):
+    """Differentiation form on the full mesh (one-electron limit: one orbital,
+    no projector or mean field): the forward pass with checkpoints, the
+    adjoint sweep that gives dJ/dE_k for every step, and the tangent map, each
+    timed with CUDA events on the current stream over `steps` time steps of
+    the workload's dt inside the pulse.  A full-size check: the dot-product
+    identity <g, J v> = <J^T g, v> between tangent and adjoint."""
+    import numpy as np
+    from paper_2301_02387_gb300 import adjoint as adj
+    w = inputs.WORKLOADS[WORKLOAD]
+    pulse, dt, m = w["pulse"], w["dt"], w["m"]
+    omega = 45.5634 / pulse["wavelength_nm"]
+    tau = pulse["cycles"] * 2.0 * np.pi / omega
+    t0 = 0.5 * tau
+    E = np.array([inputs.sin2_pulse(t0 + k * dt, pulse["intensity"], pulse["wavelength_nm"], pulse["cycles"],
+                                    (0.0, 0.0, 1.0))[2] for k in range(steps)])
+    e_dir = (0.0, 0.0, 1.0)
+    rng = np.random.default_rng(inputs.BASE_SEED + 21)
+    g = rng.standard_normal(steps + 1)
+    v = rng.standard_normal(steps)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, prec in (("fp64", pkg.PREC_FP64), ("mixed", pkg.PREC_MIXED)):
+        adj.tdse_forward(mesh, phi_col, E[:1], dt, e_dir, m, krylov_tol, prec, ckpt_every=every)   # warm-up
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        torch.cuda.synchronize()
+        a.record(stream)
+        _, _, ckpt = adj.tdse_forward(mesh, phi_col, E, dt, e_dir, m, krylov_tol, prec, ckpt_every=every)
+        b.record(stream)
+        grad, _ = adj.tdse_vjp(mesh, ckpt, every, E, g, dt, e_dir, m, krylov_tol, prec)
+        c.record(stream)
+        torch.cuda.synchronize()
+        t_f, t_b = a.elapsed_time(b) / steps, b.elapsed_time(c) / steps
+        d0 = torch.cuda.Event(enable_timing=True)
+        d1 = torch.cuda.Event(enable_timing=True)
+        d0.record(stream)
+        _, dd = adj.tdse_jvp(mesh, phi_col, E, v, dt, e_dir, m, krylov_tol, prec)
+        d1.record(stream)
+        torch.cuda.synchronize()
+        lhs, rhs = float(g @ dd), float(v @ grad)
+        out[name] = {"forward_ms_per_step": t_f, "adjoint_ms_per_step": t_b,
+                     "tangent_ms_per_step": d0.elapsed_time(d1) / steps,
+                     "gradient_over_forward": (t_f + t_b) / t_f,
+                     # central differences over 256 spline samples need 2 x 256 forward passes
+                     "speedup_vs_central_differences_256": 512.0 * t_f / (t_f + t_b),
+                     "dot_product_rel": abs(lhs - rhs) / max(abs(lhs), abs(rhs))}
+    fp = out["fp64"]
+    return {"metric": "time steps/s of the gradient dJ/dE_k (forward with checkpoints + adjoint sweep)",
+            "value": 1000.0 / (fp["forward_ms_per_step"] + fp["adjoint_ms_per_step"]),
+            "unit": "steps/s", "steps": steps, "ckpt_every": every, "krylov_m": m, "krylov_tol": krylov_tol,
+            "fp64": out["fp64"], "mixed": out["mixed"],
+            "projected_2000_step_gradient_s": 2000.0 * (fp["forward_ms_per_step"] + fp["adjoint_ms_per_step"])
+            * 1e-3,
+            "workload": "one-electron limit on the H2 mesh (H2+ electron, orbital 0 of the seeded set), "
+                        "field of the 800 nm sin^2 pulse from its peak, dt=0.02, e = z"}
+
+
 # Kernel classes of the library's event timing: name, bound, unit of work.
 PROF_CLASSES = {
     0: ("Gram-Schmidt passes (krylov_update / project*_dots, FP64)", "alu", "flops"),
@@ -345,6 +402,8 @@ def run_ours(args, rank, world, dist):
 
     kern = measure_kernels(pkg, torch, mesh, W, phi, field(t), stream)
     batching = None if args.no_batch else run_batch(torch, pkg, inputs)
+    diff = None if args.no_diff else run_diff(torch, pkg, inputs, mesh, state0[0][:, 0].contiguous(),
+                                              krylov_tol=args.krylov_tol if args.krylov_tol > 0 else 1e-10)
     peaks, peak_src = _peaks()
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     fp64_peak = 152 * 4 * sm_mhz * 1e6 / 1e12
@@ -402,6 +461,7 @@ def run_ours(args, rank, world, dist):
                 "d2h_bytes_per_step": bytes_state},
         "gpu_launches": mixed["launches"],
         "batching_form": batching,
+        "differentiation_form": diff,
     }
 
 
@@ -619,6 +679,9 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batching-form measurement (64 instances)")
     ap.add_argument("--batch-only", action="store_true",
                     help="only the batching-form measurement (its JSON sub-entry), for profiling")
+    ap.add_argument("--no-diff", action="store_true", help="skip the differentiation-form measurement")
+    ap.add_argument("--diff-only", action="store_true",
+                    help="only the differentiation-form measurement (its JSON sub-entry)")
     ap.add_argument("--krylov-tol", type=float, default=1e-10,
                     help="Krylov error threshold per substep (0: one fixed-dimension Krylov step per time step)")
     ap.add_argument("--form", default="both", choices=["both", "mixed"],
@@ -636,6 +699,16 @@ def main():
         from paper_2301_02387_gb300 import inputs
         torch.cuda.set_device(0)
         print(json.dumps({"batching_form": run_batch(torch, pkg, inputs)}))
+        return
+    if args.diff_only:
+        import torch
+        import paper_2301_02387_gb300 as pkg
+        from paper_2301_02387_gb300 import inputs
+        torch.cuda.set_device(0)
+        w = inputs.WORKLOADS[WORKLOAD]
+        mesh, _solver, phi0, _ = setup_state(pkg, inputs, torch, w)
+        phi = torch.from_numpy(phi0[:, 0].copy()).cuda()
+        print(json.dumps({"differentiation_form": run_diff(torch, pkg, inputs, mesh, phi, steps=args.steps)}))
         return
     if args.profile_arnoldi:
         run_profile_arnoldi(timed=args.steps > 0)

@@ -137,9 +137,10 @@ def dipole_signal(E, mesh, phi0, dt, e_dir=(0.0, 0.0, 1.0), krylov_m=16, tol=0.0
 
 
 def spline_matrix(n_samples, n_steps):
-    """Natural cubic spline through n_samples equally spaced values on [0, 1],
-    evaluated at the n_steps step points k / (n_steps - 1): a [n_steps, n_samples]
-    float64 matrix S, so that E = S c."""
+    """Not-a-knot cubic spline through n_samples (>= 4) equally spaced values on
+    [0, 1], evaluated at the n_steps step points k / (n_steps - 1): a
+    [n_steps, n_samples] float64 matrix S, so that E = S c (the window's field
+    from its samples; the spline is linear in the samples, so dJ/dc = S^T dJ/dE)."""
     import scipy.interpolate
     t = np.linspace(0.0, 1.0, n_samples)
     x = np.linspace(0.0, 1.0, n_steps) if n_steps > 1 else np.zeros(1)
@@ -147,7 +148,7 @@ def spline_matrix(n_samples, n_steps):
     for j in range(n_samples):
         c = np.zeros(n_samples)
         c[j] = 1.0
-        S[:, j] = scipy.interpolate.CubicSpline(t, c, bc_type="natural")(x)
+        S[:, j] = scipy.interpolate.CubicSpline(t, c, bc_type="not-a-knot")(x)
     return S
 
 

@@ -138,6 +138,8 @@ def test_spline_and_harmonic_yield_helpers():
     t = np.linspace(0.0, 1.0, 9)
     x = np.linspace(0.0, 1.0, 33)
     np.testing.assert_allclose(S @ (2.0 - 3.0 * t), 2.0 - 3.0 * x, atol=1e-13)
+    # not-a-knot: a single cubic through the samples is reproduced exactly
+    np.testing.assert_allclose(S @ (t ** 3 - t), x ** 3 - x, atol=1e-13)
     np.testing.assert_allclose(S[::4], np.eye(9), atol=1e-13)
     assert adj.n_checkpoints(100, 50) == 2 and adj.n_checkpoints(101, 50) == 3 and adj.n_checkpoints(1, 50) == 1
     rng = np.random.default_rng(0)
