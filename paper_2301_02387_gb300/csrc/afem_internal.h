@@ -127,6 +127,7 @@ struct DeviceMesh {
     float* hang_w32 = nullptr;
     float* v_master32 = nullptr;
     float* v_hang32 = nullptr;
+    float* v_cell32 = nullptr;      // [ncell][(p+1)^3] nuclear potential at every cell node
     float* stiff_dinv32 = nullptr;
 };
 

@@ -22,6 +22,7 @@ struct CellArgs32 {
     const float* hw;
     const float* v_master;
     const float* v_hang;
+    const float* v_cell;      // [ncell][(p+1)^3] potential at the cell nodes
     int64_t n_interior;
     float xi[kMaxP1], w[kMaxP1], K[kMaxP1 * kMaxP1];
     float E[3];
@@ -217,30 +218,28 @@ __device__ __forceinline__ void cell32v_body(const CellArgs32& a, int64_t cell, 
     }
     // with the quad count fixed, the orbital count n = 2 L4 is too
     const int nn2 = (G && L4C > 0) ? 4 * L4C * L4C : n * n;
+    // float4 pairs of a node's n^2 complex fields sit SU = (n^2/2) | 1 quads apart
+    // in shared memory: an odd stride puts the rows that the 8 lanes of a quarter
+    // warp read (4 nodes x 2 orbital pairs) on distinct banks
+    const int SU = (nn2 / 2) | 1;
     if (G) {
         if (U) {
+            // the n^2 complex fields of a node as float4 pairs (n = 2 L4 is even)
             CellArgs32 au = a;
             au.masked = 0;
-            if (nn2 % 2 == 0) {   // the n^2 complex fields of a node as float4 pairs
-                const int h2 = nn2 / 2;
-                const float4* U4 = reinterpret_cast<const float4*>(U);
-                float4* s_U4 = reinterpret_cast<float4*>(s_U);
-                for (int it = tid; it < NN * h2; it += bs) {
-                    const int i = it / h2, c = it - i * h2;
-                    s_U4[it] = gather32v(au, s_idx[i], U4, h2, c);
-                }
-            } else {
-                for (int it = tid; it < NN * nn2; it += bs) {
-                    const int i = it / nn2, pq = it - i * nn2;
-                    s_U[it] = gather32<float2>(au, s_idx[i], U, nn2, pq);
-                }
+            const int h2 = nn2 / 2;
+            const float4* U4 = reinterpret_cast<const float4*>(U);
+            float4* s_U4 = reinterpret_cast<float4*>(s_U);
+            for (int it = tid; it < NN * h2; it += bs) {
+                const int i = it / h2, c = it - i * h2;
+                s_U4[i * SU + c] = gather32v(au, s_idx[i], U4, h2, c);
             }
         }
         const float h3 = g.w * g.w * g.w;
+        const float* vc = a.v_cell + cell * NN;
         for (int i = tid; i < NN; i += bs) {
             const int ia = i % P1, ib = (i / P1) % P1, ic = i / (P1 * P1);
-            const int idx = s_idx[i];
-            const float V = idx >= 0 ? a.v_master[idx] : a.v_hang[-idx - 1];
+            const float V = vc[i];
             const float px = g.x + g.w * a.xi[ia], py = g.y + g.w * a.xi[ib], pz = g.z + g.w * a.xi[ic];
             const float wq = h3 * s_w[ia] * s_w[ib] * s_w[ic];
             s_wq[i] = wq;
@@ -266,19 +265,27 @@ __device__ __forceinline__ void cell32v_body(const CellArgs32& a, int64_t cell, 
         if constexpr (G) {
             f4fma(r, s_pot[i], s_u[it]);
             if (U) {
-                // orbitals p0 = 2q (lanes x, y) and p1 = 2q + 1 (lanes z, w)
-                const float2* ui = reinterpret_cast<const float2*>(s_u + i * L4);
+                // orbitals p0 = 2q (lanes x, y) and p1 = 2q + 1 (lanes z, w); the
+                // node's orbitals and the two field rows are read as 16-byte quads
+                // (orbitals 2c, 2c + 1 with U[p][2c], U[p][2c + 1])
                 float2 m0 = make_float2(0.f, 0.f), m1 = m0;
                 const int nl = L4C > 0 ? 2 * L4C : n;
-                const float2* U0 = s_U + i * nn2 + (2 * q) * nl;
-                const float2* U1 = U0 + nl;
+                const int hl = nl / 2;   // quads per field row
+                const float4* Ur = reinterpret_cast<const float4*>(s_U) + i * SU + q * nl;
 #pragma unroll
-                for (int rr = 0; rr < nl; ++rr) {
-                    const float2 u = ui[rr];
-                    m0.x = fmaf(U0[rr].x, u.x, fmaf(-U0[rr].y, u.y, m0.x));
-                    m0.y = fmaf(U0[rr].x, u.y, fmaf(U0[rr].y, u.x, m0.y));
-                    m1.x = fmaf(U1[rr].x, u.x, fmaf(-U1[rr].y, u.y, m1.x));
-                    m1.y = fmaf(U1[rr].x, u.y, fmaf(U1[rr].y, u.x, m1.y));
+                for (int c = 0; c < (L4C > 0 ? L4C : 64); ++c) {
+                    if (L4C == 0 && c >= hl) break;
+                    const float4 u = s_u[i * L4 + c];
+                    const float4 a0 = Ur[c];
+                    const float4 a1 = Ur[hl + c];
+                    m0.x = fmaf(a0.x, u.x, fmaf(-a0.y, u.y, m0.x));
+                    m0.y = fmaf(a0.x, u.y, fmaf(a0.y, u.x, m0.y));
+                    m0.x = fmaf(a0.z, u.z, fmaf(-a0.w, u.w, m0.x));
+                    m0.y = fmaf(a0.z, u.w, fmaf(a0.w, u.z, m0.y));
+                    m1.x = fmaf(a1.x, u.x, fmaf(-a1.y, u.y, m1.x));
+                    m1.y = fmaf(a1.x, u.y, fmaf(a1.y, u.x, m1.y));
+                    m1.x = fmaf(a1.z, u.z, fmaf(-a1.w, u.w, m1.x));
+                    m1.y = fmaf(a1.z, u.w, fmaf(a1.w, u.z, m1.y));
                 }
                 const float wq = s_wq[i];
                 r.x = fmaf(wq, m0.x, r.x);
@@ -446,6 +453,7 @@ CellArgs32 make_cell_args32(const afem_mesh* m) {
     a.hw = D.hang_w32;
     a.v_master = D.v_master32;
     a.v_hang = D.v_hang32;
+    a.v_cell = D.v_cell32;
     a.n_interior = D.n_interior;
     const Basis1D& b = m->basis;
     const int p1 = b.p + 1;
@@ -524,7 +532,9 @@ static int launch32v(const afem_mesh* m, const CellArgs32& a, const float* x, co
         AFEM_CUDA_TRY(cudaGetLastError());
         return AFEM_OK;
     }
-    const size_t smem = size_t(nn) * L4 * sizeof(float4) + ((G && U) ? size_t(nn) * n * n * sizeof(float2) : 0);
+    // the mean fields sit (n^2/2) | 1 quads apart per node (see cell32v_body)
+    const size_t smem =
+        size_t(nn) * L4 * sizeof(float4) + ((G && U) ? size_t(nn) * ((n * n / 2) | 1) * sizeof(float4) : 0);
     switch (p) {
 #define AFEM_CASE(PP)                                                                          \
     case PP: {                                                                                 \

@@ -592,8 +592,15 @@ int upload_mesh(afem_mesh* m) {
         if ((rc = upload(D.v_master32, vm.data(), vm.size()))) return rc;
         if ((rc = upload(D.v_hang32, vh.data(), vh.size()))) return rc;
         if ((rc = upload(D.stiff_dinv32, dinv32.data(), dinv32.size()))) return rc;
+        // the potential at every cell node in cell order: the FP32 cell pass reads it
+        // coalesced instead of gathering it through the node map
+        std::vector<float> vc(size_t(D.ncell) * nn);
+        for (size_t o = 0; o < vc.size(); ++o) {
+            const int32_t idx = H.cell_node[o];
+            vc[o] = float(idx >= 0 ? H.v_master[idx] : H.v_hang[-idx - 1]);
+        }
+        if ((rc = upload(D.v_cell32, vc.data(), vc.size()))) return rc;
     }
-    (void)nn;
     return AFEM_OK;
 }
 
@@ -617,6 +624,7 @@ void free_device_mesh(DeviceMesh& D) {
     cudaFree(D.hang_w32);
     cudaFree(D.v_master32);
     cudaFree(D.v_hang32);
+    cudaFree(D.v_cell32);
     cudaFree(D.stiff_dinv32);
     D = DeviceMesh{};
 }
