@@ -149,3 +149,36 @@ def test_mixed_precision_gradient_close_to_fp64():
     _, _, ckpt = adj.tdse_forward(gm, phi_g, E, dt, E_DIR, ckpt_every=4, precision=PREC_MIXED)
     grad, _ = adj.tdse_vjp(gm, ckpt, 4, E, g, dt, E_DIR, precision=PREC_MIXED)
     assert np.max(np.abs(grad - grad_ref)) <= 1e-4 * np.max(np.abs(grad_ref))
+
+
+def test_full_size_dot_product_and_checkpoints():
+    """On the benchmark mesh (H2, Q4, N = 775,009): a few short steps with one
+    fixed-dimension Krylov step each (dt = 2e-4, m = 16, accurate to rounding
+    at this mesh's stiffness): the dot-product identity between tangent and
+    adjoint to 1e-10, the tangent's signal equal to the forward's, and the
+    gradient independent of the checkpoint interval.  (Central differences
+    need a window long enough for the field to move the dipole well above its
+    rounding; they run on the small meshes above.)"""
+    import torch
+    import paper_2301_02387_gb300 as pkg
+    from paper_2301_02387_gb300 import adjoint as adj
+    w = inputs.WORKLOADS["h2_q4"]
+    gm = pkg.Mesh(*inputs.mesh_args("h2_q4"))
+    X, ml, _ = gm.tables()
+    interior = np.arange(gm.N) < gm.n_interior
+    phi = inputs.lowdin(inputs.molecular_orbitals(X, interior, w["nuclei"], 1, phase_noise=0.0), ml)[:, 0]
+    phi_g = torch.from_numpy(np.ascontiguousarray(phi)).cuda()
+    K, dt = 4, 2e-4
+    E = np.array([0.05, -0.04, 0.06, 0.02])
+    rng = np.random.default_rng(61)
+    g = rng.standard_normal(K + 1)
+    v = rng.standard_normal(K)
+    d, _, ckpt = adj.tdse_forward(gm, phi_g, E, dt, E_DIR, krylov_m=16, tol=0.0, ckpt_every=3)
+    grad, _ = adj.tdse_vjp(gm, ckpt, 3, E, g, dt, E_DIR, krylov_m=16, tol=0.0)
+    dj, dd = adj.tdse_jvp(gm, phi_g, E, v, dt, E_DIR, krylov_m=16, tol=0.0)
+    assert np.max(np.abs(dj - d)) <= 1e-10 * np.max(np.abs(d))
+    lhs, rhs = g @ dd, v @ grad
+    assert abs(lhs - rhs) <= 1e-10 * max(abs(lhs), abs(rhs))
+    _, _, ck1 = adj.tdse_forward(gm, phi_g, E, dt, E_DIR, krylov_m=16, tol=0.0, ckpt_every=1)
+    grad1, _ = adj.tdse_vjp(gm, ck1, 1, E, g, dt, E_DIR, krylov_m=16, tol=0.0)
+    assert np.max(np.abs(grad1 - grad)) <= 1e-12 * np.max(np.abs(grad))
