@@ -101,6 +101,21 @@ const char* afem_last_error(void);
  * counterpart in the paper. */
 int afem_kernel_launch_count(int64_t* count);
 
+/* The binary64 <-> binary32 conversions of the precision form (library
+ * arithmetic with no counterpart in the paper), applied to n device values:
+ * AFEM_CONVERT_F64_F32 rounds x (double[n]) to nearest-even into y (float[n]),
+ * AFEM_CONVERT_F32_F64 widens x (float[n]) exactly into y (double[n]).  They
+ * follow the IEEE-754 bit layouts on the integer pipe instead of the
+ * hardware conversions (which issue on GB300's FP64 pipe); values outside the
+ * binary32 normal range map to signed zeros (below, including binary32
+ * subnormal inputs) or infinities (above).  Exposed so that tests can compare
+ * them with the hardware conversions.  Asynchronous on `stream`; x and y are
+ * caller-owned and must not overlap.  Errors: AFEM_EINVAL (n < 0, null
+ * buffers with n > 0, unknown direction), AFEM_ECUDA. */
+#define AFEM_CONVERT_F64_F32 0
+#define AFEM_CONVERT_F32_F64 1
+int afem_convert(const void* x, void* y, int64_t n, int direction, void* stream);
+
 /* Kernel-class timing (library instrumentation with no counterpart in the
  * paper).  While enabled (process-wide), the library brackets each call of a
  * class's kernels with a pair of CUDA events recorded on the stream the

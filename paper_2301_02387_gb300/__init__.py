@@ -262,6 +262,24 @@ def op_apply(mesh, kind, x, y, E=None, stream=None):
     return y
 
 
+def convert(x, y, stream=None):
+    """afem_convert: y = x rounded to float32 (x float64) or widened to float64
+    (x float32) by the library's integer-pipe conversions (same shape, CUDA)."""
+    import torch
+    if x.dtype == torch.float64:
+        direction, ydt = _capi.CONVERT_F64_F32, torch.float32
+    elif x.dtype == torch.float32:
+        direction, ydt = _capi.CONVERT_F32_F64, torch.float64
+    else:
+        raise TypeError("x must be float32 or float64")
+    xp = _dev_ptr(x, x.dtype, None, "x")
+    yp = _dev_ptr(y, ydt, None, "y")
+    if x.numel() != y.numel():
+        raise ValueError("x and y must have the same number of elements")
+    _capi.check(_capi.load().afem_convert(xp, yp, int(x.numel()), direction, _stream_ptr(stream)))
+    return y
+
+
 OPT_CELL32_VARIANT = 1
 
 

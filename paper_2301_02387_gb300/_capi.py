@@ -29,6 +29,9 @@ OP_STIFF_F32 = 2
 OP_H1_C64 = 3
 OP_POS = 4
 
+CONVERT_F64_F32 = 0
+CONVERT_F32_F64 = 1
+
 PROF_GS = 0
 PROF_GCELL32 = 1
 PROF_STIFF32 = 2
@@ -132,6 +135,7 @@ SIGNATURES = {
     "afem_batch_op_apply": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.POINTER(_P), ctypes.POINTER(_P),
                                            ctypes.POINTER(ctypes.c_int), ctypes.c_int, _P]),
     "afem_batch_get_tuning": (ctypes.c_int, [_P, ctypes.POINTER(BatchTuning)]),
+    "afem_convert": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int, _P]),
     "afem_tdse_forward": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                          ctypes.c_double, ctypes.c_int, _P, _P, _P, _P, ctypes.c_int, _P]),
     "afem_tdse_jvp": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double,

@@ -128,6 +128,7 @@ struct DeviceMesh {
     float* v_master32 = nullptr;
     float* v_hang32 = nullptr;
     float* v_cell32 = nullptr;      // [ncell][(p+1)^3] nuclear potential at every cell node
+    float* ml_inv32 = nullptr;      // [N] float copy of ml_inv (FP32 projector)
     float* stiff_dinv32 = nullptr;
 };
 
@@ -165,6 +166,8 @@ void mctdhf_set_precision(afem_mctdhf* S, int precision);
 void mctdhf_set_krylov_tol(afem_mctdhf* S, double tol);
 int mctdhf_step(afem_mctdhf* S, double2* phi, double2* C, double* W, const double* E, double dt, double cg_rtol,
                 int cg_max_it, afem_step_info* info, cudaStream_t s);
+int convert_f64_f32(const double* x, float* y, int64_t n, cudaStream_t s);
+int convert_f32_f64(const float* x, double* y, int64_t n, cudaStream_t s);
 int tdse_forward(afem_mesh* m, const double* e_dir, const double* E, int K, double dt, int mk, double tol,
                  int precision, const double2* phi0, double2* phi_end, double* d, double2* ckpt, int every,
                  cudaStream_t s);

@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(kRedThreads) project_dots_kernel(
 template <int NV>
 __global__ void __launch_bounds__(kRedThreads) project32_dots_kernel(
     const float2* __restrict__ z, const float2* __restrict__ phi, const double2* __restrict__ S,
-    const double* __restrict__ ml_inv, const double* __restrict__ ml, int64_t n_int, int64_t N, int n,
+    const float* __restrict__ ml_inv, const double* __restrict__ ml, int64_t n_int, int64_t N, int n,
     double2* __restrict__ w, const double2* __restrict__ V, int64_t stride, const double2* __restrict__ H, int ldh,
     const double2* __restrict__ beta2, double* __restrict__ partial, unsigned* __restrict__ counter,
     double2* __restrict__ out) {
@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(kRedThreads) project32_dots_kernel(
                 double2 u[NV];
 #pragma unroll
                 for (int i = 0; i < NV; ++i) u[i] = V[i * stride + o];
-                const float s = float(ml_inv[k]);
+                const float s = ml_inv[k];
                 const float2 zo = z[o];
                 float2 xf = make_float2(zo.x * s, zo.y * s);
                 for (int j = 0; j < n; ++j) {
@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(kRedThreads) project32_dots_kernel(
                     xf.x = fmaf(-f.x, c.x, fmaf(f.y, c.y, xf.x));
                     xf.y = fmaf(-f.x, c.y, fmaf(-f.y, c.x, xf.y));
                 }
-                x = make_double2(double(xf.x), double(xf.y));
+                x = make_double2(widen_f32(xf.x), widen_f32(xf.y));
                 accumulate_dots<NV>(acc, u, x, ml[k]);
             }
             w[o] = x;
@@ -419,7 +419,7 @@ __global__ void __launch_bounds__(kRedThreads) krylov_update_kernel(
                 x.y = fma(-h.x, u[i].y, fma(-h.y, u[i].x, x.y));
             }
             w[o] = x;
-            if (w32) w32[o] = make_float2(float(x.x), float(x.y));
+            if (w32) w32[o] = make_float2(narrow_f64(x.x), narrow_f64(x.y));
             nrm[0] = fma(m, fma(x.x, x.x, x.y * x.y), nrm[0]);
         }
     }
@@ -481,7 +481,7 @@ __global__ void __launch_bounds__(kRedThreads) substep_close_kernel(
                 out[o] = x;
             }
             V[o] = x;
-            if (v32) v32[o] = make_float2(float(x.x), float(x.y));
+            if (v32) v32[o] = make_float2(narrow_f64(x.x), narrow_f64(x.y));
             if (k < n_int) nrm[0] = fma(ml[k], fma(x.x, x.x, x.y * x.y), nrm[0]);
         }
     }
@@ -611,7 +611,31 @@ int cdot(const double2* A, int na, const double2* B, int nb, const double* w, in
 
 __global__ void to_c64_kernel(const double2* __restrict__ x, float2* __restrict__ y, int64_t n) {
     for (int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; o < n; o += int64_t(gridDim.x) * blockDim.x)
-        y[o] = make_float2(float(x[o].x), float(x[o].y));
+        y[o] = make_float2(narrow_f64(x[o].x), narrow_f64(x[o].y));
+}
+
+__global__ void narrow_kernel(const double* __restrict__ x, float* __restrict__ y, int64_t n) {
+    for (int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; o < n; o += int64_t(gridDim.x) * blockDim.x)
+        y[o] = narrow_f64(x[o]);
+}
+
+__global__ void widen_kernel(const float* __restrict__ x, double* __restrict__ y, int64_t n) {
+    for (int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; o < n; o += int64_t(gridDim.x) * blockDim.x)
+        y[o] = widen_f32(x[o]);
+}
+
+int convert_f64_f32(const double* x, float* y, int64_t n, cudaStream_t s) {
+    if (n <= 0) return AFEM_OK;
+    AFEM_LAUNCH((narrow_kernel), grid_for(n), 256, 0, s, x, y, n);
+    AFEM_CUDA_TRY(cudaGetLastError());
+    return AFEM_OK;
+}
+
+int convert_f32_f64(const float* x, double* y, int64_t n, cudaStream_t s) {
+    if (n <= 0) return AFEM_OK;
+    AFEM_LAUNCH((widen_kernel), grid_for(n), 256, 0, s, x, y, n);
+    AFEM_CUDA_TRY(cudaGetLastError());
+    return AFEM_OK;
 }
 
 int to_c64(const double2* x, float2* y, int64_t n, cudaStream_t s) {
@@ -683,7 +707,7 @@ static int launch_project_dots(int nv, unsigned grid, cudaStream_t s, const floa
     case NVV:                                                                                                       \
         if (z32) {                                                                                                  \
             AFEM_LAUNCH((project32_dots_kernel<NVV>), wave_grid<project32_dots_kernel<NVV>>(grid), kRedThreads, 0, \
-                        s, z32, phi32, S, D.ml_inv, D.ml,                                                           \
+                        s, z32, phi32, S, D.ml_inv32, D.ml,                                                         \
                         D.n_interior, D.n_master, n, w, V, stride, H, ldh, beta2, partial, counter, out);           \
         } else {                                                                                                    \
             AFEM_LAUNCH((project_dots_kernel<NVV>), wave_grid<project_dots_kernel<NVV>>(grid), kRedThreads, 0, s, \

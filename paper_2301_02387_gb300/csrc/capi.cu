@@ -325,6 +325,17 @@ int afem_mctdhf_step(afem_mctdhf* s, void* phi, void* C, void* W, const double* 
                        cg_rtol, cg_max_it, info, static_cast<cudaStream_t>(stream));
 }
 
+int afem_convert(const void* x, void* y, int64_t n, int direction, void* stream) {
+    if (n < 0 || (n > 0 && (!x || !y))) return set_error(AFEM_EINVAL, "afem_convert: bad arguments");
+    if (direction == AFEM_CONVERT_F64_F32)
+        return convert_f64_f32(static_cast<const double*>(x), static_cast<float*>(y), n,
+                               static_cast<cudaStream_t>(stream));
+    if (direction == AFEM_CONVERT_F32_F64)
+        return convert_f32_f64(static_cast<const float*>(x), static_cast<double*>(y), n,
+                               static_cast<cudaStream_t>(stream));
+    return set_error(AFEM_EINVAL, "afem_convert: unknown direction");
+}
+
 int afem_tdse_forward(afem_mesh* m, const double* e_dir, const double* E, int n_steps, double dt, int krylov_m,
                       double tol, int precision, const void* phi0, void* phi_end, double* d, void* ckpt,
                       int ckpt_every, void* stream) {

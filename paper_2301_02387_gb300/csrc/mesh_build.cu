@@ -600,6 +600,9 @@ int upload_mesh(afem_mesh* m) {
             vc[o] = float(idx >= 0 ? H.v_master[idx] : H.v_hang[-idx - 1]);
         }
         if ((rc = upload(D.v_cell32, vc.data(), vc.size()))) return rc;
+        std::vector<float> mli32(H.n_master);
+        for (int64_t k = 0; k < H.n_master; ++k) mli32[k] = float(1.0 / H.ml[k]);
+        if ((rc = upload(D.ml_inv32, mli32.data(), mli32.size()))) return rc;
     }
     return AFEM_OK;
 }
@@ -625,6 +628,7 @@ void free_device_mesh(DeviceMesh& D) {
     cudaFree(D.v_master32);
     cudaFree(D.v_hang32);
     cudaFree(D.v_cell32);
+    cudaFree(D.ml_inv32);
     cudaFree(D.stiff_dinv32);
     D = DeviceMesh{};
 }

@@ -12,6 +12,42 @@
 namespace afem {
 
 constexpr int kRedThreads = 256;
+
+// Conversions between binary32 and binary64 written from the IEEE-754 bit
+// layout, so that they run on the integer pipe: on GB300 the hardware
+// conversions issue on the FP64 pipe, which is the bound of the Gram-Schmidt
+// passes.
+// binary32 -> binary64: exact for zeros, normal numbers, infinities and NaNs;
+// binary32 subnormals (below 1.18e-38) become zeros of the same sign.
+__device__ __forceinline__ double widen_f32(float f) {
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xFFu;
+    uint64_t bits = uint64_t(u & 0x80000000u) << 32;
+    if (e != 0u) {
+        const uint64_t E = e == 0xFFu ? 0x7FFull : uint64_t(e) + 896ull;   // rebias 127 -> 1023
+        bits |= (E << 52) | (uint64_t(u & 0x7FFFFFu) << 29);
+    }
+    return __longlong_as_double(static_cast<long long>(bits));
+}
+// binary64 -> binary32, rounded to nearest with ties to even on the 29
+// dropped significand bits (a carry out of the significand raises the
+// exponent, as it should); results below the binary32 normal range become
+// zeros of the same sign, results above it infinities; NaNs stay NaNs.
+__device__ __forceinline__ float narrow_f64(double d) {
+    const uint64_t b = static_cast<uint64_t>(__double_as_longlong(d));
+    const uint32_t sign = uint32_t(b >> 32) & 0x80000000u;
+    const int e = int((b >> 52) & 0x7FFull);
+    const uint64_t m = b & 0xFFFFFFFFFFFFFull;
+    if (e == 0x7FF) return __uint_as_float(sign | 0x7F800000u | (m ? 0x400000u : 0u));
+    const int ef = e - 896;   // binary32 biased exponent
+    if (ef <= 0) return __uint_as_float(sign);
+    if (ef >= 255) return __uint_as_float(sign | 0x7F800000u);
+    const uint32_t keep = uint32_t(m >> 29);
+    const uint32_t rest = uint32_t(m & 0x1FFFFFFFull);
+    uint32_t r = (uint32_t(ef) << 23) | keep;
+    if (rest > 0x10000000u || (rest == 0x10000000u && (keep & 1u))) r += 1u;
+    return __uint_as_float(sign | r);
+}
 constexpr int kRedBlocks = 152 * 4;   // 4 blocks per SM on a 152-SM GB300
 
 // Threads (r, c) = (t / k, t % k) for t < k * (256 / k); the rest idle.
