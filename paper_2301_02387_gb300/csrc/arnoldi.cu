@@ -208,7 +208,9 @@ __device__ __forceinline__ void accumulate_dots(double (&acc)[2 * NV + 1], const
         acc[2 * i] = fma(u[i].x, mx.x, fma(u[i].y, mx.y, acc[2 * i]));
         acc[2 * i + 1] = fma(u[i].x, mx.y, fma(-u[i].y, mx.x, acc[2 * i + 1]));
     }
-    acc[2 * NV] = fma(x.x, mx.x, fma(x.y, mx.y, acc[2 * NV]));
+    // the norm only without basis vectors; with them finish_dots takes the
+    // in-span part of the norm from the inner products (no FP64 work per element)
+    if constexpr (NV == 0) acc[0] = fma(x.x, mx.x, fma(x.y, mx.y, acc[0]));
 }
 
 // Krylov vectors are stored unscaled: V_0 is the substep's start vector and
@@ -233,13 +235,16 @@ __device__ __forceinline__ void krylov_scales(const double2* __restrict__ H, int
 // The block sums of acc (inner products of the raw vector w with the stored
 // V_i), then in the last block the true values for the vector fw w with
 // fw = s_f[NV-1] (1 when NV = 0): out[i] = s_f[i] fw (acc[2i], acc[2i+1]) =
-// <q_i, fw w> for i < NV and out[NV] = (fw^2 acc[2NV], 0) = |fw w|^2.
+// <q_i, fw w> for i < NV and out[NV] = (sum_i |out[i]|^2, 0), the squared
+// norm of the part of fw w in the span of q_0..q_{NV-1} (for NV = 0,
+// |w|^2 itself).  By Pythagoras the norm before the update is this plus the
+// norm the update leaves, which is how the re-orthogonalisation test uses it.
 template <int NV>
 __device__ __forceinline__ void finish_dots(double (&acc)[2 * NV + 1], const double* s_f,
                                             double* __restrict__ partial, unsigned* __restrict__ counter,
                                             double2* __restrict__ out) {
-    constexpr int CNT = 2 * NV + 1;
-    block_row_partial<CNT>(acc, CNT, partial);
+    constexpr int CNT = NV > 0 ? 2 * NV : 1;
+    block_row_partial<2 * NV + 1>(acc, CNT, partial);
     __shared__ double s_sum[kRedThreads];
     if (!last_block_sum(partial, CNT, counter, s_sum)) return;
     const double fw = NV > 0 ? s_f[NV > 0 ? NV - 1 : 0] : 1.0;
@@ -247,11 +252,22 @@ __device__ __forceinline__ void finish_dots(double (&acc)[2 * NV + 1], const dou
         const double f = s_f[i] * fw;
         out[i] = make_double2(f * s_sum[2 * i], f * s_sum[2 * i + 1]);
     }
-    if (threadIdx.x == 0) out[NV] = make_double2(fw * fw * s_sum[2 * NV], 0.0);
+    if (threadIdx.x == 0) {
+        double nn = 0.0;
+        if (NV == 0) {
+            nn = s_sum[0];
+        } else {
+            for (int i = 0; i < NV; ++i) {
+                const double f = s_f[i] * fw;
+                nn += f * f * (s_sum[2 * i] * s_sum[2 * i] + s_sum[2 * i + 1] * s_sum[2 * i + 1]);
+            }
+        }
+        out[NV] = make_double2(nn, 0.0);
+    }
 }
 
-// Gram-Schmidt inner products: out[i] = <q_i, w>_M for i < NV and
-// out[NV] = (<w, w>_M, 0), over interior rows.  Skipped when gate && !*gate.
+// Gram-Schmidt inner products: out[i] = <q_i, w>_M for i < NV and out[NV] as
+// finish_dots states, over interior rows.  Skipped when gate && !*gate.
 // NV is a template parameter so that the NV + 1 loads of a row are issued
 // back to back before any of them is used.
 template <int NV>
@@ -285,8 +301,8 @@ __global__ void __launch_bounds__(kRedThreads) krylov_dots_kernel(
 // z is the cell pass applied to the stored V_{NV-1}, so the raw vector
 // w[k][p] = ML^-1[k] z[k][p] - sum_j phi[k][j] S[j][p] on interior rows (0 on
 // the others) is G q_{NV-1} / s_f[NV-1]; it is written unscaled, and
-// out[i] = <q_i, G q_{NV-1}>_M (i < NV), out[NV] = |G q_{NV-1}|_M^2 are formed
-// from the values in registers, so w is not read back.
+// out[i] = <q_i, G q_{NV-1}>_M (i < NV) and out[NV] (see finish_dots) are
+// formed from the values in registers, so w is not read back.
 template <int NV>
 __global__ void __launch_bounds__(kRedThreads) project_dots_kernel(
     const double2* __restrict__ z, const double2* __restrict__ phi, const double2* __restrict__ S,
@@ -381,7 +397,8 @@ __global__ void __launch_bounds__(kRedThreads) project32_dots_kernel(
 // when non-null (the input of the next cell pass); the last block writes the
 // Hessenberg column: Hcol[i] = c_i (or += c_i when accumulate),
 // Hcol[NV] = fw |w|_M, and *reorth = 1 when a first pass left
-// |fw w|^2 < eta2 * c[NV] (the squared norm before it).  Skipped when gate && !*gate.
+// |fw w|^2 < eta2 (c[NV] + |fw w|^2), the squared norm before it (c[NV] is
+// its part in the span of the basis).  Skipped when gate && !*gate.
 template <int NV>
 __global__ void __launch_bounds__(kRedThreads) krylov_update_kernel(
     double2* __restrict__ w, const double2* __restrict__ V, int64_t stride, const double2* __restrict__ c,
@@ -433,7 +450,8 @@ __global__ void __launch_bounds__(kRedThreads) krylov_update_kernel(
         }
         const double nn = fw * fw * fmax(s_sum[0], 0.0);   // |fw w|^2
         Hcol[NV] = make_double2(sqrt(nn), 0.0);
-        if (reorth) *reorth = (!accumulate && nn < eta2 * s_c[NV].x) ? 1 : 0;
+        // |fw w|^2 before the update = in-span part (c[NV]) + what is left (nn)
+        if (reorth) *reorth = (!accumulate && nn < eta2 * (s_c[NV].x + nn)) ? 1 : 0;
     }
 }
 
@@ -945,14 +963,16 @@ int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double
             } else {
                 if ((rc = g_cell_overlaps(m, E, phi, U, n, w.V + j * NV, w, s))) return rc;
             }
-            const double gs_flops = double(D.n_interior) * n * (8.0 * (j + 1) + 4.0);   // one pass
+            // algorithmic FP64 flops per element: 8 per basis vector in each pass
+            // (one complex multiply-add), plus 4 for the new norm in the update
+            const double gs_flops = double(D.n_interior) * n * 8.0 * (j + 1);
             {
                 ProfScope ps(AFEM_PROF_GS, s, gs_flops);
                 rc = launch_project_dots(j + 1, gproj, s, mixed ? w.z32 : nullptr, w.phi32, w.z, phi, w.S, D, n, Wn,
                                          w.V, NV, w.H, ldh, w.beta2, part, cnt, w.c1);
             }
             if (!rc) {
-                ProfScope ps(AFEM_PROF_GS, s, gs_flops);
+                ProfScope ps(AFEM_PROF_GS, s, gs_flops + double(D.n_interior) * n * 4.0);
                 rc = launch_krylov_update(j + 1, gdots, s, Wn, w.V, NV, w.c1, D.ml, D.n_interior, n, nullptr, 0, eta2,
                                           w.flag, w.H, ldh, w.beta2, v32, part, cnt, Hcol);
             }
