@@ -146,9 +146,11 @@ __device__ __forceinline__ void block_row_partial(double (&v)[MAXV], int cnt, do
 // Projector overlaps of the precision form, S[a][b] = sum_k conj(A[k][a]) B[k][b]
 // over interior rows from complex64 inputs (NO = n orbitals): one thread per
 // row forms all NO^2 products in FP32 registers (each thread covers a few
-// rows), the per-thread sums are widened to FP64 once and summed over the
-// block and then by the last block, so the FP64 work is per thread, not per
-// element.
+// rows); the block sums its threads' values in FP32 over 8 segments of 32
+// threads (through shared memory, transposed), the segment sums in FP64, and
+// the last block sums the blocks in FP64.  S is consumed in FP32 by the
+// projector, and the FP64 work is per block rather than per thread, which
+// leaves the kernel free to run a full wave of blocks.
 template <int NO>
 __global__ void __launch_bounds__(kRedThreads) overlap32_kernel(const float2* __restrict__ A,
                                                                 const float2* __restrict__ B, int64_t n_rows,
@@ -159,6 +161,7 @@ __global__ void __launch_bounds__(kRedThreads) overlap32_kernel(const float2* __
     float f[CNT];
 #pragma unroll
     for (int i = 0; i < CNT; ++i) f[i] = 0.f;
+#pragma unroll 2
     for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < n_rows;
          k += int64_t(gridDim.x) * blockDim.x) {
         float2 a[NO], b[NO];
@@ -188,10 +191,31 @@ __global__ void __launch_bounds__(kRedThreads) overlap32_kernel(const float2* __
                 f[2 * (i * NO + j) + 1] = fmaf(a[i].x, b[j].y, fmaf(-a[i].y, b[j].x, f[2 * (i * NO + j) + 1]));
             }
     }
-    double d[CNT];
+    static_assert(kRedThreads == 256, "the segment sums assume 8 warps of 32");
+    __shared__ float s_t[32][kRedThreads + 1];   // a chunk of 32 values x 256 threads
+    __shared__ float s_seg[8][32];
+    const int t = threadIdx.x, lane = t & 31, seg = t >> 5;
 #pragma unroll
-    for (int i = 0; i < CNT; ++i) d[i] = double(f[i]);
-    block_row_partial<CNT>(d, CNT, partial);
+    for (int c0 = 0; c0 < CNT; c0 += 32) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (c0 + j < CNT) s_t[j][t] = f[c0 + j];
+        __syncthreads();
+        if (c0 + lane < CNT) {   // value c0 + lane over the 32 threads of segment seg
+            float x = 0.f;
+#pragma unroll 8
+            for (int r = 0; r < 32; ++r) x += s_t[lane][seg * 32 + r];
+            s_seg[seg][lane] = x;
+        }
+        __syncthreads();
+        if (t < 32 && c0 + t < CNT) {
+            double x = 0.0;
+#pragma unroll
+            for (int g = 0; g < 8; ++g) x += widen_f32(s_seg[g][t]);
+            partial[int64_t(blockIdx.x) * CNT + c0 + t] = x;
+        }
+        __syncthreads();
+    }
     __shared__ double s_sum[kRedThreads];
     if (!last_block_sum(partial, CNT, counter, s_sum)) return;
     for (int o = threadIdx.x; o < NO * NO; o += blockDim.x) out[o] = make_double2(s_sum[2 * o], s_sum[2 * o + 1]);
@@ -814,7 +838,7 @@ static int g_cell_overlaps32(afem_mesh* m, const double* E, const float2* phi32,
     switch (n) {
 #define AFEM_OV_CASE(NO)                                                                                        \
     case NO:                                                                                                    \
-        AFEM_LAUNCH((overlap32_kernel<NO>), kRedBlocks / 2, kRedThreads, 0, s, phi32, w.z32, D.n_interior,     \
+        AFEM_LAUNCH((overlap32_kernel<NO>), kRedBlocks, kRedThreads, 0, s, phi32, w.z32, D.n_interior,         \
                     part, w.counters, w.S);                                                                     \
         break;
         AFEM_OV_CASE(1)
