@@ -11,6 +11,7 @@
 
 #include "afem_internal.h"
 #include "cell_common.cuh"
+#include "vec_common.cuh"
 
 namespace afem {
 
@@ -23,6 +24,9 @@ struct CellArgs32 {
     const float* v_master;
     const float* v_hang;
     const float* v_cell;      // [ncell][(p+1)^3] potential at the cell nodes
+    // stiffness only (null: off): p.Ap of the conjugate-gradient sweep per column,
+    // added in FP64 to slot (block % kPapSlots) of [kPapSlots][columns]
+    double* pap_slots;
     int64_t n_interior;
     float xi[kMaxP1], w[kMaxP1], K[kMaxP1 * kMaxP1];
     float E[3];
@@ -191,6 +195,10 @@ __device__ __forceinline__ void scatter32v(const CellArgs32& a, int idx, float4*
 // synchronises the block between two calls.
 // L4C > 0 fixes the quad count at compile time (no integer division per item);
 // L4C = 0 takes it from L4rt.
+// Slots of the fused p.Ap sums (spread over slots to keep the FP64 atomics of
+// the cell blocks off a single address per column).
+constexpr int kPapSlots = 64;
+
 template <int P, bool G, int L4C>
 __device__ __forceinline__ void cell32v_body(const CellArgs32& a, int64_t cell, const float4* __restrict__ x,
                                              const float2* __restrict__ U, float4* __restrict__ y, int L4rt,
@@ -248,6 +256,7 @@ __device__ __forceinline__ void cell32v_body(const CellArgs32& a, int64_t cell, 
     }
     __syncthreads();
     const float ck = (G ? 0.5f : 1.0f) * g.w;
+    float4 pap = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int it = tid; it < NN * L4; it += bs) {
         const int i = it / L4, q = it - i * L4;
         const int ia = i % P1, ib = (i / P1) % P1, ic = i / (P1 * P1);
@@ -295,6 +304,40 @@ __device__ __forceinline__ void cell32v_body(const CellArgs32& a, int64_t cell, 
             }
         }
         scatter32v(a, s_idx[i], y, L4, q, r);
+        if constexpr (!G) {   // the cell's part of p.Ap: p (gathered, zero on the surface) times A_K p
+            const float4 u = s_u[it];
+            pap.x = fmaf(u.x, r.x, pap.x);
+            pap.y = fmaf(u.y, r.y, pap.y);
+            pap.z = fmaf(u.z, r.z, pap.z);
+            pap.w = fmaf(u.w, r.w, pap.w);
+        }
+    }
+    if constexpr (!G && L4C > 0 && 32 % L4C == 0) {
+        // p.Ap = sum over cells of u_K . A_K u_K (p vanishes on the surface, so
+        // the masked scatter drops nothing): lanes with the same quad summed by
+        // shuffles, the 8 warps in FP64, one FP64 atomic per column and block
+        if (a.pap_slots) {
+#pragma unroll
+            for (int off = L4C; off < 32; off <<= 1) {
+                pap.x += __shfl_xor_sync(0xffffffffu, pap.x, off);
+                pap.y += __shfl_xor_sync(0xffffffffu, pap.y, off);
+                pap.z += __shfl_xor_sync(0xffffffffu, pap.z, off);
+                pap.w += __shfl_xor_sync(0xffffffffu, pap.w, off);
+            }
+            __shared__ float4 s_pap[8][L4C];
+            const int lane = tid & 31, warp = tid >> 5;
+            if (lane < L4C && warp < 8) s_pap[warp][lane] = pap;
+            __syncthreads();
+            if (tid < 4 * L4C) {
+                const int q = tid >> 2, comp = tid & 3;
+                double x = 0.0;
+                for (int w8 = 0; w8 < 8 && w8 * 32 < bs; ++w8) {
+                    const float4 v = s_pap[w8][q];
+                    x += widen_f32(comp == 0 ? v.x : comp == 1 ? v.y : comp == 2 ? v.z : v.w);
+                }
+                atomicAdd(&a.pap_slots[int64_t(cell % kPapSlots) * (4 * L4C) + tid], x);
+            }
+        }
     }
 }
 
@@ -303,6 +346,22 @@ __global__ void __launch_bounds__(256) cell32v_kernel(const __grid_constant__ Ce
                                                       const float4* __restrict__ x, const float2* __restrict__ U,
                                                       float4* __restrict__ y, int L4rt, int n) {
     cell32v_body<P, G, L4C>(a, blockIdx.x, x, U, y, L4rt, n);
+}
+
+// Degree 4 (the largest cells): held to 32 registers so that 8 blocks of 256
+// threads share an SM.
+template <bool G, int L4C>
+__global__ void __launch_bounds__(256, 8) cell32v_kernel_q4(const __grid_constant__ CellArgs32 a,
+                                                            const float4* __restrict__ x,
+                                                            const float2* __restrict__ U, float4* __restrict__ y,
+                                                            int L4rt, int n) {
+    cell32v_body<4, G, L4C>(a, blockIdx.x, x, U, y, L4rt, n);
+}
+
+template <int P, bool G, int L4C>
+constexpr auto cell32v_pick() {
+    if constexpr (P == 4) return cell32v_kernel_q4<G, L4C>;
+    else return cell32v_kernel<P, G, L4C>;
 }
 
 // Line-ordered form of the four-lane pass: the three 1D contractions run as
@@ -538,10 +597,10 @@ static int launch32v(const afem_mesh* m, const CellArgs32& a, const float* x, co
     switch (p) {
 #define AFEM_CASE(PP)                                                                          \
     case PP: {                                                                                 \
-        auto k = L4 == 1   ? cell32v_kernel<PP, G, 1>                                          \
-                 : L4 == 2 ? cell32v_kernel<PP, G, 2>                                          \
-                 : L4 == 4 ? cell32v_kernel<PP, G, 4>                                          \
-                           : cell32v_kernel<PP, G, 0>;                                         \
+        auto k = L4 == 1   ? cell32v_pick<PP, G, 1>()                                          \
+                 : L4 == 2 ? cell32v_pick<PP, G, 2>()                                          \
+                 : L4 == 4 ? cell32v_pick<PP, G, 4>()                                          \
+                           : cell32v_pick<PP, G, 0>();                                         \
         if (smem > 48 * 1024)                                                                  \
             AFEM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                                int(smem)));                                    \
@@ -562,10 +621,20 @@ static int launch32v(const afem_mesh* m, const CellArgs32& a, const float* x, co
 
 static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-int launch_stiffness32(const afem_mesh* m, const float* x, float* y, int nv, int masked, cudaStream_t s) {
+// pap_slots (optional): [kPapSlots][nv] FP64 sums that receive p.Ap per column
+// (x = p, masked), for nv in {4, 8, 16} on the four-lane path; returns
+// AFEM_EINVAL when they are asked for outside it.
+int launch_stiffness32(const afem_mesh* m, const float* x, float* y, int nv, int masked, cudaStream_t s,
+                       double* pap_slots) {
     CellArgs32 a = make_cell_args32(m);
     a.masked = masked;
-    if (nv % 4 == 0 && aligned16(x) && aligned16(y)) return launch32v<false>(m, a, x, nullptr, y, nv, 0, s);
+    const bool quads = nv % 4 == 0 && aligned16(x) && aligned16(y);
+    if (pap_slots) {
+        if (!quads || !(nv == 4 || nv == 8 || nv == 16) || m->cell32_variant != 0)
+            return set_error(AFEM_EINVAL, "stiffness: fused p.Ap needs 4, 8 or 16 aligned columns");
+        a.pap_slots = pap_slots;
+    }
+    if (quads) return launch32v<false>(m, a, x, nullptr, y, nv, 0, s);
     return launch32<float, false>(m, a, x, nullptr, y, nv, s);
 }
 

@@ -283,7 +283,8 @@ int launch_stiffness(const afem_mesh* m, const double* x, double* y, int nv, int
     return launch_cell_op<double>(m, a, x, y, nv, s);
 }
 
-int launch_stiffness32(const afem_mesh* m, const float* x, float* y, int nv, int masked, cudaStream_t s);
+int launch_stiffness32(const afem_mesh* m, const float* x, float* y, int nv, int masked, cudaStream_t s,
+                       double* pap_slots = nullptr);
 int launch_g_cell32(const afem_mesh* m, const double* E, const float2* v, const float2* U, float2* z, int n,
                     cudaStream_t s);
 

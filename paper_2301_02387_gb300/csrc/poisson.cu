@@ -459,6 +459,7 @@ __global__ void update_beta_kernel(T* __restrict__ x, T* __restrict__ r, const T
 // FP32 and only the run sums in FP64 (random rounding of about 1e-7 per run;
 // the CG scalars are formed from the FP64 totals).
 constexpr int kRun = 16;
+constexpr int kPapSlotsCg = 64;   // slots of the p.Ap sums of the fused stiffness pass
 
 struct Quad {
     int q, r, R, kq;
@@ -547,14 +548,28 @@ __global__ void __launch_bounds__(kRedThreads) update_beta4_kernel(
     float4* __restrict__ x, float4* __restrict__ r, const float4* __restrict__ p, const float4* __restrict__ Ap,
     const float* __restrict__ dinv, int64_t n, int k, PcgState st, double* __restrict__ partial,
     unsigned* __restrict__ counter, const double* __restrict__ scale, const double* __restrict__ rr_upd,
-    const double* __restrict__ bb64, double rtol2, double delta2, int* __restrict__ flags) {
+    const double* __restrict__ bb64, double rtol2, double delta2, int* __restrict__ flags,
+    double* __restrict__ pap_slots) {
     __shared__ double s[4 * kRedThreads];
+    __shared__ double s_alpha[64];
+    // alpha = rz / p.Ap per column: from st.alpha (formed by dot_alpha4_kernel)
+    // or, when the stiffness pass summed p.Ap into pap_slots, formed here
+    if (pap_slots) {
+        for (int c = threadIdx.x; c < k; c += blockDim.x) {
+            double pAp = 0.0;
+            for (int sl = 0; sl < kPapSlotsCg; ++sl) pAp += pap_slots[sl * k + c];
+            s_alpha[c] = (st.active[c] && pAp > 0.0) ? st.rz[c] / pAp : 0.0;
+        }
+    } else {
+        for (int c = threadIdx.x; c < k; c += blockDim.x) s_alpha[c] = st.alpha[c];
+    }
+    __syncthreads();
     const Quad qd(k);
     double z0 = 0.0, z1 = 0.0, z2 = 0.0, z3 = 0.0, r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0;
     if (qd.active) {
         const int c0 = 4 * qd.q;
-        const float al0 = float(st.alpha[c0]), al1 = float(st.alpha[c0 + 1]), al2 = float(st.alpha[c0 + 2]),
-                    al3 = float(st.alpha[c0 + 3]);
+        const float al0 = float(s_alpha[c0]), al1 = float(s_alpha[c0 + 1]), al2 = float(s_alpha[c0 + 2]),
+                    al3 = float(s_alpha[c0 + 3]);
         const int64_t step = int64_t(gridDim.x) * qd.R;
         int64_t i = int64_t(blockIdx.x) * qd.R + qd.r;
         while (i < n) {   // runs of kRun rows summed in FP32, the runs in FP64
@@ -607,6 +622,10 @@ __global__ void __launch_bounds__(kRedThreads) update_beta4_kernel(
     s[4 * t + 3] = r3;
     reduce_columns(s, k, qd.R, out + k);
     if (!last_block_sum(partial, 2 * k, counter, s)) return;
+    if (pap_slots) {   // every block has read the slots: record alpha, clear them for the next sweep
+        for (int c = threadIdx.x; c < k; c += blockDim.x) st.alpha[c] = s_alpha[c];
+        for (int o = threadIdx.x; o < kPapSlotsCg * k; o += blockDim.x) pap_slots[o] = 0.0;
+    }
     cg_beta_finalize(s, k, st, scale, rr_upd, bb64, rtol2, delta2, flags);
 }
 
@@ -873,7 +892,8 @@ __global__ void residual64_kernel(const double* __restrict__ b, const double* __
     reduce_columns(s, k, R, out + k);
 }
 
-int launch_stiffness32(const afem_mesh* m, const float* x, float* y, int nv, int masked, cudaStream_t s);
+int launch_stiffness32(const afem_mesh* m, const float* x, float* y, int nv, int masked, cudaStream_t s,
+                       double* pap_slots = nullptr);
 
 // Reliable-update form of the mixed solve: one continuous float32 CG per
 // column whose correction d is folded into the float64 W, and whose residual is
@@ -976,6 +996,8 @@ int poisson_batch_mixed(afem_mesh* m, const double2* phi, int n, double* W, doub
     const DeviceMesh& D = m->dev;
     const int k = n * n;
     const bool quads = (k % 4) == 0;   // four columns per thread in the float32 CG kernels
+    // p.Ap formed by the stiffness pass itself (its four-lane form with 1, 2 or 4 quads)
+    const bool fused = quads && (k == 4 || k == 8 || k == 16) && m->cell32_variant == 0;
     const int64_t N = D.n_master, Ni = D.n_interior;
     const int nblk = kRedBlocks;
     const size_t NK = size_t(N) * k;
@@ -983,6 +1005,7 @@ int poisson_batch_mixed(afem_mesh* m, const double2* phi, int n, double* W, doub
     float *r32, *z32, *p32, *Ap32, *d32;
     double *s_old, *s_new, *rr64, *bb64, *rr_upd;
     int* flags;
+    double* pap;
     auto carve = [&](Carver& cv) {
         w.b = cv.take<double>(NK);
         w.r = cv.take<double>(NK);
@@ -1011,6 +1034,7 @@ int poisson_batch_mixed(afem_mesh* m, const double2* phi, int n, double* W, doub
         rr_upd = cv.take<double>(k);
         flags = cv.take<int>(2);
         w.counters = cv.take<unsigned>(4);
+        pap = cv.take<double>(size_t(kPapSlotsCg) * k);
     };
     Carver measure(nullptr);
     carve(measure);
@@ -1019,6 +1043,7 @@ int poisson_batch_mixed(afem_mesh* m, const double2* phi, int n, double* W, doub
     Carver cv(m->ws_poisson.ptr);
     carve(cv);
     PcgState st{w.alpha, w.beta, w.rz, w.bb, w.rr, w.active, w.n_active, 0.0};
+    AFEM_CUDA_TRY(cudaMemsetAsync(pap, 0, sizeof(double) * kPapSlotsCg * k, s));
     const double rtol2 = rtol * rtol, delta2 = delta * delta;
     AFEM_CUDA_TRY(cudaMemsetAsync(w.counters, 0, 4 * sizeof(unsigned), s));
 
@@ -1052,18 +1077,20 @@ int poisson_batch_mixed(afem_mesh* m, const double2* phi, int n, double* W, doub
     while (flags_h[0] > 0 && it < max_it) {
         {   // algorithmic bytes: read p, write Ap (float32)
             ProfScope ps(AFEM_PROF_STIFF32, s, double(N) * k * 8.0);
-            if ((rc = launch_stiffness32(m, p32, Ap32, k, 1, s))) return rc;
+            if ((rc = launch_stiffness32(m, p32, Ap32, k, 1, s, fused ? pap : nullptr))) return rc;
         }
-        // algorithmic bytes: p.Ap 8, x/r update 24, p update 12 per element (float32)
-        ProfScope psv(AFEM_PROF_CGVEC32, s, double(Ni) * k * 44.0);
+        // algorithmic bytes: p.Ap 8 (unless the stiffness pass formed it), x/r update 24,
+        // p update 12 per element (float32)
+        ProfScope psv(AFEM_PROF_CGVEC32, s, double(Ni) * k * (fused ? 36.0 : 44.0));
         if (quads) {
             auto* p4 = reinterpret_cast<float4*>(p32);
             auto* r4 = reinterpret_cast<float4*>(r32);
-            AFEM_LAUNCH((dot_alpha4_kernel), nblk, kRedThreads, 0, s, p4, reinterpret_cast<const float4*>(Ap32), Ni,
-                        k, w.partial, w.counters + 0, st);
+            if (!fused)
+                AFEM_LAUNCH((dot_alpha4_kernel), nblk, kRedThreads, 0, s, p4, reinterpret_cast<const float4*>(Ap32),
+                            Ni, k, w.partial, w.counters + 0, st);
             AFEM_LAUNCH((update_beta4_kernel), nblk, kRedThreads, 0, s, reinterpret_cast<float4*>(d32), r4, p4,
                         reinterpret_cast<const float4*>(Ap32), D.stiff_dinv32, Ni, k, st, w.partial, w.counters + 1,
-                        s_old, rr_upd, bb64, rtol2, delta2, flags);
+                        s_old, rr_upd, bb64, rtol2, delta2, flags, fused ? pap : nullptr);
             AFEM_LAUNCH((p_update4_kernel), nblk, kRedThreads, 0, s, p4, r4, D.stiff_dinv32, Ni, k, st);
         } else {
             AFEM_LAUNCH((dot_alpha_kernel<float>), nblk, kRedThreads, 0, s, p32, Ap32, Ni, k, w.partial,
