@@ -378,7 +378,10 @@ def run_ours(args, rank, world, dist):
             "steps_compared": args.warmup + args.steps,
         }
 
-    # ---- end to end: host buffers, copies inside the timed region (precision form)
+    # ---- end to end: host buffers, copies inside the timed region (precision form;
+    # the solver was last used by the FP64 path's profiled run)
+    solver.set_precision(pkg.PREC_MIXED)
+    solver.set_krylov_tol(args.krylov_tol)
     phi, C, W = mixed["state"]
     t = mixed["t"]
     phi_h = phi.cpu().pin_memory()
