@@ -408,10 +408,13 @@ int afem_tdse_vjp(afem_mesh* mesh, const double* e_dir, const double* E, int n_s
  * zero (AFEM_OP_H1_C64: x_i, y_i complex64 [N_i][n_vec_i], n_vec_i even) or
  * y_i = A x_i (AFEM_OP_STIFF_F32: float32 [N_i][n_vec_i], n_vec_i % 4 == 0),
  * the same result as afem_op_apply on that mesh up to the order of the
- * floating-point atomic sums.  The first apply of a (kind, n_vec) signature
- * times candidate launch shapes on the batch itself (persistent grids of 1,
- * 2 or all resident blocks per SM at 256 and 128 threads, and one block per
- * cell) and keeps the fastest (afem_batch_get_tuning).  With
+ * floating-point atomic sums.  Small cells (p <= 3, few quads) are grouped
+ * into work items that fill a block.  The first apply of a (kind, n_vec)
+ * signature times candidate schedules on the batch itself -- the persistent
+ * launch with grids of 1, 2 or all resident blocks per SM at 256 and 128
+ * threads or one block per work item, and the instances' own passes on 8
+ * parallel streams (reported as block 0, grid = count) -- and keeps the
+ * fastest (afem_batch_get_tuning).  With
  * AFEM_BATCH_GRAPH the zero, cell and scale passes are captured once into a
  * CUDA graph on a private stream and replayed on `stream`; the per-instance
  * table (pointers, fields) lives in device memory and is re-uploaded when

@@ -16,6 +16,7 @@ size_t batch32_inst_bytes();
 int batch32_fill(const afem_mesh* m, int kind, const double* E, const void* x, void* y, int nvec, int64_t cell0,
                  void* out);
 size_t batch32_smem(const std::vector<int>& p, const std::vector<int>& L4);
+int64_t batch32_items(int p, int L4, int64_t ncell);
 int batch32_occupancy(int kind, int block, size_t smem, int* per_sm);
 int batch32_launch(int kind, const void* d_inst, int count, int64_t total, int block, unsigned grid, size_t smem,
                    cudaStream_t s);
@@ -23,15 +24,28 @@ int batch32_launch(int kind, const void* d_inst, int count, int64_t total, int b
 
 using namespace afem;
 
+namespace {
+constexpr int kParStreams = 8;   // streams of the per-instance schedule
+}
+
 struct afem_batch {
     std::vector<afem_mesh*> meshes;
     int64_t total_cells = 0;
+    int64_t total_items = 0;             // work items of the current signature (small cells grouped)
     int sms = 0;
     size_t rec = 0;                      // bytes of one instance record
     void* d_inst = nullptr;              // device instance table
     void* h_inst = nullptr;              // pinned host staging of each upload
     std::vector<unsigned char> last;     // contents of the last upload
     cudaStream_t cap = nullptr;          // private stream for graph capture
+    cudaStream_t par[kParStreams] = {};  // per-instance schedule: instance i runs on par[i % kParStreams]
+    cudaEvent_t fork = nullptr;
+    cudaEvent_t join[kParStreams] = {};
+    // arguments of the current apply (the per-instance schedule launches from them)
+    std::vector<const void*> cur_x;
+    std::vector<void*> cur_y;
+    std::vector<int> cur_n;
+    std::vector<double> cur_E;
     // launch shape and its graph, valid for one (kind, lanes per instance) signature
     int sig_kind = -1;
     std::vector<int> sig_L4;
@@ -49,6 +63,33 @@ void drop_graph(afem_batch* b) {
     b->exec = nullptr;
 }
 
+// The per-instance schedule: each instance's own pass (the kernels of
+// afem_op_apply) on one of kParStreams streams forked from s and joined back,
+// so that independent instances run concurrently.  Captured into the graph
+// like the persistent launch (the streams join the capture through the events).
+int launch_per_instance(afem_batch* b, int kind, cudaStream_t s) {
+    AFEM_CUDA_TRY(cudaEventRecord(b->fork, s));
+    for (int j = 0; j < kParStreams; ++j) AFEM_CUDA_TRY(cudaStreamWaitEvent(b->par[j], b->fork, 0));
+    const int count = int(b->meshes.size());
+    for (int i = 0; i < count; ++i) {
+        const double* E = b->cur_E.empty() ? nullptr : b->cur_E.data() + 3 * i;
+        int rc = launch_op_apply(b->meshes[i], kind, E, b->cur_x[i], b->cur_y[i], b->cur_n[i],
+                                 b->par[i % kParStreams]);
+        if (rc) return rc;
+    }
+    for (int j = 0; j < kParStreams; ++j) {
+        AFEM_CUDA_TRY(cudaEventRecord(b->join[j], b->par[j]));
+        AFEM_CUDA_TRY(cudaStreamWaitEvent(s, b->join[j], 0));
+    }
+    return AFEM_OK;
+}
+
+// One apply with the chosen schedule (block 0: per instance).
+int launch_schedule(afem_batch* b, int kind, int block, unsigned grid, size_t smem, cudaStream_t s) {
+    if (block == 0) return launch_per_instance(b, kind, s);
+    return batch32_launch(kind, b->d_inst, int(b->meshes.size()), b->total_items, block, grid, smem, s);
+}
+
 // Times launch shape (block, grid) on the uploaded batch: best of 3 after a warm-up.
 int time_shape(afem_batch* b, int kind, int block, unsigned grid, size_t smem, cudaStream_t s, double* ms) {
     cudaEvent_t e0, e1;
@@ -58,7 +99,7 @@ int time_shape(afem_batch* b, int kind, int block, unsigned grid, size_t smem, c
     int rc = AFEM_OK;
     for (int r = 0; r < 4 && rc == AFEM_OK; ++r) {
         cudaEventRecord(e0, s);
-        rc = batch32_launch(kind, b->d_inst, int(b->meshes.size()), b->total_cells, block, grid, smem, s);
+        rc = launch_schedule(b, kind, block, grid, smem, s);
         cudaEventRecord(e1, s);
         if (rc) break;
         cudaError_t e = cudaEventSynchronize(e1);
@@ -76,8 +117,10 @@ int time_shape(afem_batch* b, int kind, int block, unsigned grid, size_t smem, c
     return rc;
 }
 
-// Candidate launch shapes: persistent grids of 1, 2 or all resident blocks per
-// SM at 256 and 128 threads, and one block per cell.  The fastest is kept.
+// Candidate schedules: the persistent launch with grids of 1, 2 or all
+// resident blocks per SM at 256 and 128 threads, one block per work item, and
+// the per-instance passes on parallel streams (block 0, grid = instances).
+// The fastest is kept.
 int tune(afem_batch* b, int kind, cudaStream_t s) {
     b->cand_ms.clear();
     b->cand_block.clear();
@@ -88,9 +131,9 @@ int tune(afem_batch* b, int kind, cudaStream_t s) {
         int rc = batch32_occupancy(kind, block, b->smem, &per_sm);
         if (rc) return rc;
         std::vector<int64_t> grids = {int64_t(b->sms) * per_sm, int64_t(b->sms) * 2, int64_t(b->sms)};
-        if (block == 256) grids.push_back(b->total_cells);
+        if (block == 256) grids.push_back(b->total_items);
         for (int64_t g : grids) {
-            if (g > b->total_cells) g = b->total_cells;
+            if (g > b->total_items) g = b->total_items;
             if (g > 0x7fffffff) g = 0x7fffffff;
             if (g < 1) continue;
             double ms = 0.0;
@@ -105,6 +148,17 @@ int tune(afem_batch* b, int kind, cudaStream_t s) {
                 b->per_sm = per_sm;
             }
         }
+    }
+    double ms = 0.0;
+    int rc = time_shape(b, kind, 0, unsigned(b->meshes.size()), 0, s, &ms);
+    if (rc) return rc;
+    b->cand_ms.push_back(ms);
+    b->cand_block.push_back(0);
+    b->cand_grid.push_back(int(b->meshes.size()));
+    if (ms < best) {
+        b->block = 0;
+        b->grid = int(b->meshes.size());
+        b->per_sm = 0;
     }
     return AFEM_OK;
 }
@@ -142,6 +196,11 @@ int afem_batch_create(afem_mesh* const* meshes, int count, afem_batch** out) {
     e = cudaMalloc(&b->d_inst, b->rec * count);
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_inst, b->rec * count);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    for (int j = 0; j < kParStreams && e == cudaSuccess; ++j) {
+        e = cudaStreamCreateWithFlags(&b->par[j], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[j], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         afem_batch_destroy(b);
         return cuda_error(e, "afem_batch_create");
@@ -154,6 +213,11 @@ int afem_batch_destroy(afem_batch* b) {
     if (!b) return AFEM_OK;
     drop_graph(b);
     if (b->cap) cudaStreamDestroy(b->cap);
+    for (int j = 0; j < kParStreams; ++j) {
+        if (b->par[j]) cudaStreamDestroy(b->par[j]);
+        if (b->join[j]) cudaEventDestroy(b->join[j]);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
     if (b->d_inst) cudaFree(b->d_inst);
     if (b->h_inst) cudaFreeHost(b->h_inst);
     delete b;
@@ -170,20 +234,27 @@ int afem_batch_op_apply(afem_batch* b, int kind, const double* E, void* const* x
     const int count = int(b->meshes.size());
     std::vector<int> p(count), L4(count);
     std::vector<unsigned char> staged(b->rec * count);
-    int64_t cell0 = 0;
+    int64_t item0 = 0;   // first work item of each instance (small cells grouped per item)
     for (int i = 0; i < count; ++i) {
         if (!x[i] || !y[i] || n_vec[i] < 1) return set_error(AFEM_EINVAL, "afem_batch_op_apply: bad instance buffer");
         if (x[i] == y[i]) return set_error(AFEM_EINVAL, "afem_batch_op_apply: x and y must differ");
-        int rc = batch32_fill(b->meshes[i], kind, E ? E + 3 * i : nullptr, x[i], y[i], n_vec[i], cell0,
+        int rc = batch32_fill(b->meshes[i], kind, E ? E + 3 * i : nullptr, x[i], y[i], n_vec[i], item0,
                               staged.data() + b->rec * i);
         if (rc) return rc;
         p[i] = b->meshes[i]->dev.p;
         L4[i] = (kind == AFEM_OP_H1_C64 ? 2 * n_vec[i] : n_vec[i]) / 4;
-        cell0 += b->meshes[i]->dev.ncell;
+        item0 += batch32_items(p[i], L4[i], b->meshes[i]->dev.ncell);
     }
+    b->total_items = item0;
+    b->cur_x.assign(x, x + count);
+    b->cur_y.assign(y, y + count);
+    b->cur_n.assign(n_vec, n_vec + count);
+    if (E) b->cur_E.assign(E, E + 3 * count);
+    else b->cur_E.clear();
     // upload the instance table only when it changed; the pinned staging copy is
     // rewritten only after the previous upload has been consumed
     if (staged != b->last) {
+        if (b->block == 0) drop_graph(b);   // the per-instance graph holds the buffers and fields
         AFEM_CUDA_TRY(cudaStreamSynchronize(s));
         std::memcpy(b->h_inst, staged.data(), staged.size());
         AFEM_CUDA_TRY(cudaMemcpyAsync(b->d_inst, b->h_inst, staged.size(), cudaMemcpyHostToDevice, s));
@@ -200,13 +271,11 @@ int afem_batch_op_apply(afem_batch* b, int kind, const double* E, void* const* x
             return rc;
         }
     }
-    if (!(flags & AFEM_BATCH_GRAPH))
-        return batch32_launch(kind, b->d_inst, count, b->total_cells, b->block, unsigned(b->grid), b->smem, s);
+    if (!(flags & AFEM_BATCH_GRAPH)) return launch_schedule(b, kind, b->block, unsigned(b->grid), b->smem, s);
     if (!b->exec) {
         cudaGraph_t g = nullptr;
         AFEM_CUDA_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
-        int rc = batch32_launch(kind, b->d_inst, count, b->total_cells, b->block, unsigned(b->grid), b->smem,
-                                b->cap);
+        int rc = launch_schedule(b, kind, b->block, unsigned(b->grid), b->smem, b->cap);
         cudaError_t e = cudaStreamEndCapture(b->cap, &g);
         if (rc) {
             if (g) cudaGraphDestroy(g);

@@ -27,6 +27,7 @@ struct CellArgs32 {
     // stiffness only (null: off): p.Ap of the conjugate-gradient sweep per column,
     // added in FP64 to slot (block % kPapSlots) of [kPapSlots][columns]
     double* pap_slots;
+    int64_t ncell;
     int64_t n_interior;
     float xi[kMaxP1], w[kMaxP1], K[kMaxP1 * kMaxP1];
     float E[3];
@@ -189,47 +190,94 @@ __device__ __forceinline__ void scatter32v(const CellArgs32& a, int idx, float4*
     }
 }
 
-// The four-lane cell pass of one cell by the whole block (any block size):
-// the body of cell32v_kernel, also called per (instance, cell) by the batched
-// kernels.  Uses the block's shared memory; a caller looping over cells
-// synchronises the block between two calls.
-// L4C > 0 fixes the quad count at compile time (no integer division per item);
-// L4C = 0 takes it from L4rt.
 // Slots of the fused p.Ap sums (spread over slots to keep the FP64 atomics of
 // the cell blocks off a single address per column).
 constexpr int kPapSlots = 64;
 
+// Compile-time quad counts of the four-lane pass (others run with L4C = 0).
+__host__ __device__ constexpr int quads_c32(int L4) { return (L4 >= 1 && L4 <= 4) ? L4 : 0; }
+
+// Cells per work item of the four-lane pass: as many cells as fill 256 threads
+// with one (node, quad) item each, so that small cells (p <= 3, few quads) do
+// not leave most of a block idle; one cell where a cell's items already fill
+// the block (and with a run-time quad count).
+__host__ __device__ constexpr int cells_per_item32(int P, int L4C) {
+    return L4C <= 0 ? 1
+                    : ((P + 1) * (P + 1) * (P + 1) * L4C >= 256 ? 1 : 256 / ((P + 1) * (P + 1) * (P + 1) * L4C));
+}
+
+// Dynamic shared memory of one four-lane work item: the cell tiles of the
+// input (and of the mean fields when with_u), then the cells' geometry,
+// potential and quadrature weights and node indices.
+__host__ __device__ constexpr size_t cell32v_smem(int P, int L4, int n, bool with_u) {
+    return cells_per_item32(P, quads_c32(L4)) == 1
+               ? size_t((P + 1) * (P + 1) * (P + 1)) * (size_t(L4) * 16 + (with_u ? size_t((n * n / 2) | 1) * 16 : 0))
+               : size_t(cells_per_item32(P, quads_c32(L4))) *
+                     (size_t((P + 1) * (P + 1) * (P + 1)) *
+                          (size_t(L4) * 16 + (with_u ? size_t((n * n / 2) | 1) * 16 : 0) + 12) +
+                      16);
+}
+
+// The four-lane cell pass of work item `item` -- cells item * CPB ..
+// item * CPB + CPB - 1 that exist, CPB = cells_per_item32(P, L4C) -- by the
+// whole block (any block size): the body of cell32v_kernel, also called per
+// (instance, item) by the batched kernels.  Uses the block's shared memory; a
+// caller looping over items synchronises the block between two calls.
+// L4C > 0 fixes the quad count at compile time (no integer division per item);
+// L4C = 0 takes it from L4rt.
 template <int P, bool G, int L4C>
-__device__ __forceinline__ void cell32v_body(const CellArgs32& a, int64_t cell, const float4* __restrict__ x,
+__device__ __forceinline__ void cell32v_body(const CellArgs32& a, int64_t item, const float4* __restrict__ x,
                                              const float2* __restrict__ U, float4* __restrict__ y, int L4rt,
                                              int n) {
     constexpr int P1 = P + 1;
     constexpr int NN = P1 * P1 * P1;
+    constexpr int CPB = cells_per_item32(P, L4C);
     const int L4 = L4C > 0 ? L4C : L4rt;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float4* s_u = reinterpret_cast<float4*>(smem_raw);           // [NN][L4]
-    float2* s_U = reinterpret_cast<float2*>(s_u + NN * L4);      // [NN][n*n] (G with U)
-    __shared__ int s_idx[NN];
-    __shared__ float s_pot[NN];
-    __shared__ float s_wq[NN];
-    __shared__ float s_K[P1 * P1];
-    __shared__ float s_w[P1];
-    const int tid = threadIdx.x, bs = blockDim.x;
-    const float4 g = a.geom[cell];
-    for (int i = tid; i < NN; i += bs) s_idx[i] = a.cell_node[cell * NN + i];
-    if (tid < P1 * P1) s_K[tid] = a.K[tid];
-    if (tid < P1) s_w[tid] = a.w[tid];
-    __syncthreads();
-    for (int it = tid; it < NN * L4; it += bs) {
-        const int i = it / L4, q = it - i * L4;
-        s_u[it] = gather32v(a, s_idx[i], x, L4, q);
-    }
+    const int64_t cell0 = item * CPB;
+    const int nc = int(a.ncell - cell0 < CPB ? a.ncell - cell0 : CPB);
     // with the quad count fixed, the orbital count n = 2 L4 is too
     const int nn2 = (G && L4C > 0) ? 4 * L4C * L4C : n * n;
     // float4 pairs of a node's n^2 complex fields sit SU = (n^2/2) | 1 quads apart
     // in shared memory: an odd stride puts the rows that the 8 lanes of a quarter
     // warp read (4 nodes x 2 orbital pairs) on distinct banks
     const int SU = (nn2 / 2) | 1;
+    // dynamic shared memory, laid out as cell32v_smem counts it: the tiles,
+    // then (several cells per item) the per-cell arrays, which one-cell items
+    // keep in static shared memory (constant addresses, no registers)
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float4* s_u = reinterpret_cast<float4*>(smem_raw);            // [CPB][NN][L4]
+    float4* s_U4 = s_u + CPB * NN * L4;                           // [CPB][NN][SU] (G with U)
+    float4* s_g;                                                  // [CPB] cell corner, side
+    float* s_pot;                                                 // [CPB][NN]
+    float* s_wq;                                                  // [CPB][NN]
+    int* s_idx;                                                   // [CPB][NN]
+    if constexpr (CPB == 1) {
+        __shared__ float4 st_g[1];
+        __shared__ float st_pot[NN], st_wq[NN];
+        __shared__ int st_idx[NN];
+        s_g = st_g;
+        s_pot = st_pot;
+        s_wq = st_wq;
+        s_idx = st_idx;
+    } else {
+        s_g = s_U4 + ((G && U) ? CPB * NN * SU : 0);
+        s_pot = reinterpret_cast<float*>(s_g + CPB);
+        s_wq = s_pot + CPB * NN;
+        s_idx = reinterpret_cast<int*>(s_wq + CPB * NN);
+    }
+    __shared__ float s_K[P1 * P1];
+    __shared__ float s_w[P1];
+    const int tid = threadIdx.x, bs = blockDim.x;
+    for (int j = tid; j < nc * NN; j += bs) s_idx[j] = a.cell_node[cell0 * NN + j];
+    for (int c = tid; c < nc; c += bs) s_g[c] = a.geom[cell0 + c];
+    if (tid < P1 * P1) s_K[tid] = a.K[tid];
+    if (tid < P1) s_w[tid] = a.w[tid];
+    __syncthreads();
+    // j = cell slot * NN + node
+    for (int it = tid; it < nc * NN * L4; it += bs) {
+        const int j = it / L4, q = it - j * L4;
+        s_u[it] = gather32v(a, s_idx[j], x, L4, q);
+    }
     if (G) {
         if (U) {
             // the n^2 complex fields of a node as float4 pairs (n = 2 L4 is even)
@@ -237,42 +285,43 @@ __device__ __forceinline__ void cell32v_body(const CellArgs32& a, int64_t cell, 
             au.masked = 0;
             const int h2 = nn2 / 2;
             const float4* U4 = reinterpret_cast<const float4*>(U);
-            float4* s_U4 = reinterpret_cast<float4*>(s_U);
-            for (int it = tid; it < NN * h2; it += bs) {
-                const int i = it / h2, c = it - i * h2;
-                s_U4[i * SU + c] = gather32v(au, s_idx[i], U4, h2, c);
+            for (int it = tid; it < nc * NN * h2; it += bs) {
+                const int j = it / h2, c = it - j * h2;
+                s_U4[j * SU + c] = gather32v(au, s_idx[j], U4, h2, c);
             }
         }
-        const float h3 = g.w * g.w * g.w;
-        const float* vc = a.v_cell + cell * NN;
-        for (int i = tid; i < NN; i += bs) {
+        const float* vc = a.v_cell + cell0 * NN;
+        for (int j = tid; j < nc * NN; j += bs) {
+            const int cc = j / NN, i = j - cc * NN;
             const int ia = i % P1, ib = (i / P1) % P1, ic = i / (P1 * P1);
-            const float V = vc[i];
+            const float4 g = s_g[cc];
             const float px = g.x + g.w * a.xi[ia], py = g.y + g.w * a.xi[ib], pz = g.z + g.w * a.xi[ic];
-            const float wq = h3 * s_w[ia] * s_w[ib] * s_w[ic];
-            s_wq[i] = wq;
-            s_pot[i] = wq * (V + a.E[0] * px + a.E[1] * py + a.E[2] * pz);
+            const float wq = g.w * g.w * g.w * s_w[ia] * s_w[ib] * s_w[ic];
+            s_wq[j] = wq;
+            s_pot[j] = wq * (vc[j] + a.E[0] * px + a.E[1] * py + a.E[2] * pz);
         }
     }
     __syncthreads();
-    const float ck = (G ? 0.5f : 1.0f) * g.w;
     float4 pap = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int it = tid; it < NN * L4; it += bs) {
-        const int i = it / L4, q = it - i * L4;
+    for (int it = tid; it < nc * NN * L4; it += bs) {
+        const int j = it / L4, q = it - j * L4;
+        const int cc = j / NN, i = j - cc * NN;
         const int ia = i % P1, ib = (i / P1) % P1, ic = i / (P1 * P1);
+        const float4* u0 = s_u + cc * NN * L4 + q;   // this cell's tile, quad q
         float4 ax = make_float4(0.f, 0.f, 0.f, 0.f), ay = ax, az = ax;
 #pragma unroll
         for (int m = 0; m < P1; ++m) {
-            f4fma(ax, s_K[ia * P1 + m], s_u[(m + P1 * (ib + P1 * ic)) * L4 + q]);
-            f4fma(ay, s_K[ib * P1 + m], s_u[(ia + P1 * (m + P1 * ic)) * L4 + q]);
-            f4fma(az, s_K[ic * P1 + m], s_u[(ia + P1 * (ib + P1 * m)) * L4 + q]);
+            f4fma(ax, s_K[ia * P1 + m], u0[(m + P1 * (ib + P1 * ic)) * L4]);
+            f4fma(ay, s_K[ib * P1 + m], u0[(ia + P1 * (m + P1 * ic)) * L4]);
+            f4fma(az, s_K[ic * P1 + m], u0[(ia + P1 * (ib + P1 * m)) * L4]);
         }
+        const float ck = (G ? 0.5f : 1.0f) * s_g[cc].w;
         float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
         f4fma(r, ck * s_w[ib] * s_w[ic], ax);
         f4fma(r, ck * s_w[ia] * s_w[ic], ay);
         f4fma(r, ck * s_w[ia] * s_w[ib], az);
         if constexpr (G) {
-            f4fma(r, s_pot[i], s_u[it]);
+            f4fma(r, s_pot[j], s_u[it]);
             if (U) {
                 // orbitals p0 = 2q (lanes x, y) and p1 = 2q + 1 (lanes z, w); the
                 // node's orbitals and the two field rows are read as 16-byte quads
@@ -280,11 +329,11 @@ __device__ __forceinline__ void cell32v_body(const CellArgs32& a, int64_t cell, 
                 float2 m0 = make_float2(0.f, 0.f), m1 = m0;
                 const int nl = L4C > 0 ? 2 * L4C : n;
                 const int hl = nl / 2;   // quads per field row
-                const float4* Ur = reinterpret_cast<const float4*>(s_U) + i * SU + q * nl;
+                const float4* Ur = s_U4 + j * SU + q * nl;
 #pragma unroll
                 for (int c = 0; c < (L4C > 0 ? L4C : 64); ++c) {
                     if (L4C == 0 && c >= hl) break;
-                    const float4 u = s_u[i * L4 + c];
+                    const float4 u = s_u[j * L4 + c];
                     const float4 a0 = Ur[c];
                     const float4 a1 = Ur[hl + c];
                     m0.x = fmaf(a0.x, u.x, fmaf(-a0.y, u.y, m0.x));
@@ -296,14 +345,14 @@ __device__ __forceinline__ void cell32v_body(const CellArgs32& a, int64_t cell, 
                     m1.x = fmaf(a1.z, u.z, fmaf(-a1.w, u.w, m1.x));
                     m1.y = fmaf(a1.z, u.w, fmaf(a1.w, u.z, m1.y));
                 }
-                const float wq = s_wq[i];
+                const float wq = s_wq[j];
                 r.x = fmaf(wq, m0.x, r.x);
                 r.y = fmaf(wq, m0.y, r.y);
                 r.z = fmaf(wq, m1.x, r.z);
                 r.w = fmaf(wq, m1.y, r.w);
             }
         }
-        scatter32v(a, s_idx[i], y, L4, q, r);
+        scatter32v(a, s_idx[j], y, L4, q, r);
         if constexpr (!G) {   // the cell's part of p.Ap: p (gathered, zero on the surface) times A_K p
             const float4 u = s_u[it];
             pap.x = fmaf(u.x, r.x, pap.x);
@@ -330,12 +379,12 @@ __device__ __forceinline__ void cell32v_body(const CellArgs32& a, int64_t cell, 
             __syncthreads();
             if (tid < 4 * L4C) {
                 const int q = tid >> 2, comp = tid & 3;
-                double x = 0.0;
+                double xs = 0.0;
                 for (int w8 = 0; w8 < 8 && w8 * 32 < bs; ++w8) {
                     const float4 v = s_pap[w8][q];
-                    x += widen_f32(comp == 0 ? v.x : comp == 1 ? v.y : comp == 2 ? v.z : v.w);
+                    xs += widen_f32(comp == 0 ? v.x : comp == 1 ? v.y : comp == 2 ? v.z : v.w);
                 }
-                atomicAdd(&a.pap_slots[int64_t(cell % kPapSlots) * (4 * L4C) + tid], x);
+                atomicAdd(&a.pap_slots[int64_t(item % kPapSlots) * (4 * L4C) + tid], xs);
             }
         }
     }
@@ -513,6 +562,7 @@ CellArgs32 make_cell_args32(const afem_mesh* m) {
     a.v_master = D.v_master32;
     a.v_hang = D.v_hang32;
     a.v_cell = D.v_cell32;
+    a.ncell = D.ncell;
     a.n_interior = D.n_interior;
     const Basis1D& b = m->basis;
     const int p1 = b.p + 1;
@@ -591,20 +641,23 @@ static int launch32v(const afem_mesh* m, const CellArgs32& a, const float* x, co
         AFEM_CUDA_TRY(cudaGetLastError());
         return AFEM_OK;
     }
-    // the mean fields sit (n^2/2) | 1 quads apart per node (see cell32v_body)
-    const size_t smem =
-        size_t(nn) * L4 * sizeof(float4) + ((G && U) ? size_t(nn) * ((n * n / 2) | 1) * sizeof(float4) : 0);
+    // several small cells per block (cells_per_item32); the mean fields sit
+    // (n^2/2) | 1 quads apart per node (see cell32v_body)
+    const int cpb = cells_per_item32(p, quads_c32(L4));
+    const unsigned items = unsigned((m->dev.ncell + cpb - 1) / cpb);
+    const size_t smem = cell32v_smem(p, L4, n, G && U);
     switch (p) {
 #define AFEM_CASE(PP)                                                                          \
     case PP: {                                                                                 \
         auto k = L4 == 1   ? cell32v_pick<PP, G, 1>()                                          \
                  : L4 == 2 ? cell32v_pick<PP, G, 2>()                                          \
+                 : L4 == 3 ? cell32v_pick<PP, G, 3>()                                          \
                  : L4 == 4 ? cell32v_pick<PP, G, 4>()                                          \
                            : cell32v_pick<PP, G, 0>();                                         \
         if (smem > 48 * 1024)                                                                  \
             AFEM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                                int(smem)));                                    \
-        AFEM_LAUNCH((k), grid, 256, smem, s, a, x4, U, y4, L4, n);                             \
+        AFEM_LAUNCH((k), items, 256, smem, s, a, x4, U, y4, L4, n);                            \
         break;                                                                                 \
     }
         AFEM_CASE(1)
@@ -697,18 +750,19 @@ __device__ __noinline__ void cell32v_body_call(const BatchInst32& b, int64_t cel
     cell32v_body<P, G, L4C>(b.a, cell, b.x, nullptr, b.y, b.L4, 2 * b.L4);
 }
 
-// The cell pass of one work item (instance, cell) by the whole block.
+// The cell pass of one work item (instance, group of cells_per_item32 cells)
+// by the whole block.
 template <bool G>
 __device__ __forceinline__ void batch_item(const BatchInst32& b, int64_t cell) {
-    switch (b.p * 8 + (b.L4 == 1 ? 1 : b.L4 == 2 ? 2 : b.L4 == 4 ? 4 : 0)) {
+    switch (b.p * 8 + quads_c32(b.L4)) {
 #define AFEM_BI(PP, LL)                          \
     case PP * 8 + LL:                            \
         cell32v_body_call<PP, G, LL>(b, cell);   \
         break;
-        AFEM_BI(1, 0) AFEM_BI(1, 1) AFEM_BI(1, 2) AFEM_BI(1, 4)
-        AFEM_BI(2, 0) AFEM_BI(2, 1) AFEM_BI(2, 2) AFEM_BI(2, 4)
-        AFEM_BI(3, 0) AFEM_BI(3, 1) AFEM_BI(3, 2) AFEM_BI(3, 4)
-        AFEM_BI(4, 0) AFEM_BI(4, 1) AFEM_BI(4, 2) AFEM_BI(4, 4)
+        AFEM_BI(1, 0) AFEM_BI(1, 1) AFEM_BI(1, 2) AFEM_BI(1, 3) AFEM_BI(1, 4)
+        AFEM_BI(2, 0) AFEM_BI(2, 1) AFEM_BI(2, 2) AFEM_BI(2, 3) AFEM_BI(2, 4)
+        AFEM_BI(3, 0) AFEM_BI(3, 1) AFEM_BI(3, 2) AFEM_BI(3, 3) AFEM_BI(3, 4)
+        AFEM_BI(4, 0) AFEM_BI(4, 1) AFEM_BI(4, 2) AFEM_BI(4, 3) AFEM_BI(4, 4)
 #undef AFEM_BI
         default:
             break;
@@ -716,7 +770,8 @@ __device__ __forceinline__ void batch_item(const BatchInst32& b, int64_t cell) {
 }
 
 // Persistent batched cell pass: block b takes work items b, b + grid, ... of
-// the concatenated cell lists (all instances' cells, instance by instance).
+// the concatenated work-item lists (all instances' cell groups, instance by
+// instance).
 // The current instance's record is staged in shared memory (its tables, 1D
 // matrices and field are then read from there, as the single-instance kernel
 // reads them from its parameters), refreshed only when the instance changes.
@@ -776,14 +831,19 @@ __global__ void batch_scale_kernel(const BatchInst32* __restrict__ inst, int cou
 }
 
 // Dynamic shared memory of the batched cell pass: the largest instance's
-// [(p+1)^3][L4] float4 tile.
+// [cells per item][(p+1)^3][L4] float4 tile.
 size_t batch32_smem(const std::vector<int>& p, const std::vector<int>& L4) {
     size_t mx = 0;
     for (size_t i = 0; i < p.size(); ++i) {
-        const size_t nn = size_t(p[i] + 1) * (p[i] + 1) * (p[i] + 1);
-        mx = std::max(mx, nn * L4[i] * sizeof(float4));
+        mx = std::max(mx, cell32v_smem(p[i], L4[i], 2 * L4[i], false));
     }
     return mx;
+}
+
+// Work items of one instance: its cells in groups of cells_per_item32.
+int64_t batch32_items(int p, int L4, int64_t ncell) {
+    const int cpb = cells_per_item32(p, quads_c32(L4));
+    return (ncell + cpb - 1) / cpb;
 }
 
 int batch32_occupancy(int kind, int block, size_t smem, int* per_sm) {
