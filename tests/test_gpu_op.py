@@ -79,8 +79,11 @@ def test_op_apply_rejects_bad_arguments():
         op_apply(gm, OP_H1, x, x)
 
 
-@pytest.mark.parametrize("case", CASES[:3])
-@pytest.mark.parametrize("nvec", [3, 16])     # 3: scalar-lane kernel, 16: four-lane kernels
+# 3: scalar-lane kernel; 4, 8, 12, 16: four-lane kernels with 1..4 quads per node,
+# whose work items group up to floor(256 / ((p+1)^3 quads)) cells (ragged last
+# group on these meshes)
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("nvec", [3, 4, 8, 12, 16])
 @pytest.mark.parametrize("variant", [0, 1])   # four-lane: node-per-thread / line-ordered
 def test_stiffness_f32_within_fp32_tolerance(case, nvec, variant):
     """Precision form of the stiffness: relative error a few float32 ulps x operator norm."""
@@ -98,8 +101,8 @@ def test_stiffness_f32_within_fp32_tolerance(case, nvec, variant):
     assert _relerr(y.double().cpu().numpy(), yo[perm]) < 2e-5
 
 
-@pytest.mark.parametrize("case", CASES[:3])
-@pytest.mark.parametrize("nvec", [1, 4])      # 1: scalar-lane kernel, 4: four-lane kernels
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("nvec", [1, 2, 4, 6, 8])   # 1: scalar-lane kernel; 2..8: 1..4 quads per node
 @pytest.mark.parametrize("variant", [0, 1])
 def test_h1_c64_within_fp32_tolerance(case, nvec, variant):
     import torch
