@@ -281,6 +281,60 @@ def run_diff(torch, pkg, inputs, mesh, phi_col, steps=10, every=5, krylov_tol=1e
                         "field of the 800 nm sin^2 pulse from its peak, dt=0.02, e = z"}
 
 
+def run_precision_spectrum(torch, pkg, inputs, steps=300):
+    """The precision form against the FP64 path over a longer window on a
+    reduced mesh of the same molecule and elements (box [-8,8]^3, 4^3 coarse,
+    2 levels; the oracle's timing instance): both forms step from the same
+    state through the pulse from its peak; the <sum r_i> traces and the
+    spectra |FFT(a)|^2 of the acceleration a (second differences, Hann
+    window) are compared."""
+    import numpy as np
+    w = inputs.WORKLOADS[WORKLOAD]
+    args = (-8.0, 8.0, 4, w["p"], [(R, Z, 2) for (R, Z, _L) in w["nuclei"]], w["c"])
+    mesh = pkg.Mesh(*args)
+    X, ml, _ = mesh.tables()
+    interior = np.arange(mesh.N) < mesh.n_interior
+    n = w["n_orb"]
+    phi0 = inputs.lowdin(inputs.molecular_orbitals(X, interior, w["nuclei"], n, phase_noise=0.0), ml)
+    C0 = inputs.initial_ci(n, w["n_alpha"], w["n_beta"])
+    pulse, dt = w["pulse"], w["dt"]
+    omega = 45.5634 / pulse["wavelength_nm"]
+    t0 = 0.5 * pulse["cycles"] * 2.0 * np.pi / omega
+    traces, ms = {}, {}
+    for name, prec in (("fp64", pkg.PREC_FP64), ("mixed", pkg.PREC_MIXED)):
+        solver = pkg.MCTDHF(mesh, n, w["n_alpha"], w["n_beta"], w["m"])
+        solver.set_precision(prec)
+        solver.set_krylov_tol(1e-10)
+        phi = torch.from_numpy(phi0.copy()).cuda()
+        C = torch.from_numpy(C0.copy()).cuda()
+        W = torch.zeros((mesh.N, n * n), dtype=torch.float64, device="cuda")
+        d = []
+        torch.cuda.synchronize()
+        tt = time.perf_counter()
+        for k in range(steps):
+            E = inputs.sin2_pulse(t0 + k * dt, pulse["intensity"], pulse["wavelength_nm"], pulse["cycles"],
+                                  pulse["pol"])
+            d.append(solver.step(phi, C, W, E, dt, cg_rtol=1e-10, cg_max_it=20000)["dipole"][2])
+        torch.cuda.synchronize()
+        ms[name] = 1e3 * (time.perf_counter() - tt) / steps
+        traces[name] = np.array(d)
+        solver.close()
+    d64, d32 = traces["fp64"], traces["mixed"]
+    def spectrum(dd):
+        a = (dd[2:] - 2.0 * dd[1:-1] + dd[:-2]) / (dt * dt)
+        return np.abs(np.fft.rfft(a * np.hanning(len(a)))) ** 2
+    S64, S32 = spectrum(d64), spectrum(d32)
+    freq = 2.0 * np.pi * np.arange(len(S64)) / ((len(d64) - 2) * dt) / omega
+    band = freq <= 30.0
+    return {"workload": f"H2, Q4, [-8,8]^3, 4^3 coarse, 2 levels (N={mesh.N}); {steps} steps of dt={dt} from "
+                        "the 800 nm pulse's peak; FP64 path vs precision form from the same state",
+            "dipole_z_max_abs_diff": float(np.max(np.abs(d32 - d64))),
+            "dipole_z_rel": float(np.max(np.abs(d32 - d64)) / np.max(np.abs(d64))),
+            "spectrum_rel_l2_to_30_harmonics": float(np.linalg.norm(S32[band] - S64[band]) / np.linalg.norm(S64[band])),
+            "spectrum": "|FFT(a)|^2, a = second differences of <sum z_i>, Hann window",
+            "ms_per_step": ms}
+
+
 # Kernel classes of the library's event timing: name, bound, unit of work.
 PROF_CLASSES = {
     0: ("Gram-Schmidt passes (krylov_update / project*_dots, FP64)", "alu", "flops"),
@@ -378,6 +432,8 @@ def run_ours(args, rank, world, dist):
             / abs(fp64["infos"][-1]["energy"]),
             "orbitals_rel_l2": float(torch.linalg.norm(p32 - p64).item() / torch.linalg.norm(p64).item()),
             "ci_rel_l2": float(torch.linalg.norm(c32 - c64).item() / torch.linalg.norm(c64).item()),
+            "dipole_rel": float(np.max(np.abs(np.subtract(mixed["infos"][-1]["dipole"], fp64["infos"][-1]["dipole"])))
+                                / np.max(np.abs(fp64["infos"][-1]["dipole"]))),
             "steps_compared": args.warmup + args.steps,
         }
 
@@ -408,6 +464,7 @@ def run_ours(args, rank, world, dist):
 
     kern = measure_kernels(pkg, torch, mesh, W, phi, field(t), stream)
     batching = None if args.no_batch else run_batch(torch, pkg, inputs)
+    spec = None if args.no_spectrum else run_precision_spectrum(torch, pkg, inputs)
     diff = None if args.no_diff else run_diff(torch, pkg, inputs, mesh, state0[0][:, 0].contiguous(),
                                               krylov_tol=args.krylov_tol if args.krylov_tol > 0 else 1e-10)
     peaks, peak_src = _peaks()
@@ -453,6 +510,7 @@ def run_ours(args, rank, world, dist):
         "fp64_path": fp64_entry,
         "speedup_vs_fp64_path": (fp64["ms"] / mixed["ms"]) if fp64 is not None else None,
         "accuracy_vs_fp64_path": acc,
+        "precision_spectrum": spec,
         "orbital_dof_applies_per_s": {"fp64": kern["h1_orbital_dof_per_s"],
                                       "fp32_in_G": kern["g32_orbital_dof_per_s"]},
         "step_detail": {"inner_cg_iters_mean": float(np.mean([i["cg_iters"] for i in mi])),
@@ -686,6 +744,10 @@ def main():
     ap.add_argument("--batch-only", action="store_true",
                     help="only the batching-form measurement (its JSON sub-entry), for profiling")
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiation-form measurement")
+    ap.add_argument("--no-spectrum", action="store_true",
+                    help="skip the precision form's dipole-trace and spectrum comparison on the reduced mesh")
+    ap.add_argument("--spectrum-only", action="store_true",
+                    help="only the precision form's dipole-trace and spectrum comparison (its JSON sub-entry)")
     ap.add_argument("--diff-only", action="store_true",
                     help="only the differentiation-form measurement (its JSON sub-entry)")
     ap.add_argument("--krylov-tol", type=float, default=1e-10,
@@ -705,6 +767,13 @@ def main():
         from paper_2301_02387_gb300 import inputs
         torch.cuda.set_device(0)
         print(json.dumps({"batching_form": run_batch(torch, pkg, inputs)}))
+        return
+    if args.spectrum_only:
+        import torch
+        import paper_2301_02387_gb300 as pkg
+        from paper_2301_02387_gb300 import inputs
+        torch.cuda.set_device(0)
+        print(json.dumps({"precision_spectrum": run_precision_spectrum(torch, pkg, inputs, steps=args.steps)}))
         return
     if args.diff_only:
         import torch

@@ -313,6 +313,8 @@ typedef struct afem_step_info {
     int32_t breakdown;
     int32_t cg_iters;
     int32_t krylov_substeps; /* Krylov substeps taken (1 unless a Krylov tolerance is set) */
+    double dipole[3];        /* <sum_i r_i> at t: sum_pq gamma_pq phi_p^H F[x_d] phi_q, d = x, y, z
+                                (summed electron positions; the dipole moment is its negative) */
 } afem_step_info;
 
 /* n_orb spatial orbitals (1..8), n_alpha / n_beta electrons per spin

@@ -104,8 +104,23 @@ class MCTDHF:
             lambda v: self.G_apply(v, phi, U, E), phi, self.inner, m, dt)
         energy = np.real(np.sum(h * g1) + 0.5 * np.einsum("pqrs,pqrs->", eri, g2))
         info = dict(W=W, Wcols=Wc, h=h, eri=eri, Hci=Hci, gamma=g1, Gamma=g2, U=U,
-                    arnoldi_err=err, H_krylov=Hk, m_used=m_used, breakdown=brk, energy=energy)
+                    arnoldi_err=err, H_krylov=Hk, m_used=m_used, breakdown=brk, energy=energy,
+                    dipole=self.dipole(phi, C))
         return phi_new, C_new, info
+
+    def dipole(self, phi, C):
+        """<sum_i r_i> (3,): sum_pq gamma_pq phi_p^H F[x_d] phi_q, the one-body
+        expectation of the summed electron positions (the length-gauge field term
+        of Sec. 2 is E . r per electron, so this is dE_total/dE; the dipole moment
+        is its negative)."""
+        g1 = self.ci.rdm1(C)
+        pm = phi * self.interior[:, None]
+        out = np.zeros(3)
+        for d in range(3):
+            F = self.ops.pointwise(self.mesh.X[:, d])
+            Z = np.conj(pm).T @ (F @ pm)
+            out[d] = np.real(np.sum(Z * g1))
+        return out
 
     def energy(self, phi, C, E=(0.0, 0.0, 0.0)):
         """E = sum_pq h_pq gamma_pq + 1/2 sum (pq|rs) Gamma_pqrs (electronic, no nuclear repulsion)."""

@@ -224,7 +224,7 @@ class MCTDHF:
             _capi.check(rc)
         return dict(energy=info.energy, arnoldi_err=info.arnoldi_err, cg_relres_max=info.cg_relres_max,
                     krylov_m_used=info.krylov_m_used, breakdown=bool(info.breakdown), cg_iters=info.cg_iters,
-                    krylov_substeps=info.krylov_substeps,
+                    krylov_substeps=info.krylov_substeps, dipole=tuple(info.dipole),
                     status=rc)
 
     def close(self):

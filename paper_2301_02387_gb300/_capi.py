@@ -68,6 +68,7 @@ class StepInfo(ctypes.Structure):
         ("cg_relres_max", ctypes.c_double),
         ("krylov_m_used", ctypes.c_int32), ("breakdown", ctypes.c_int32),
         ("cg_iters", ctypes.c_int32), ("krylov_substeps", ctypes.c_int32),
+        ("dipole", ctypes.c_double * 3),
     ]
 
 

@@ -341,6 +341,19 @@ __global__ void small_block_kernel(int n, const double2* __restrict__ h, const d
         }
 }
 
+// <sum_i r_i>_d = sum_pq Re(Z_d[pq] gamma[pq]) for d = x, y, z (one thread; the
+// same contraction as the one-body energy, with the position matrices).
+__global__ void dipole_kernel(int n, const double2* __restrict__ Z, const double2* __restrict__ g1,
+                              double* __restrict__ dip) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int nn = n * n;
+    for (int d = 0; d < 3; ++d) {
+        double acc = 0.0;
+        for (int pq = 0; pq < nn; ++pq) acc += Z[d * nn + pq].x * g1[pq].x - Z[d * nn + pq].y * g1[pq].y;
+        dip[d] = acc;
+    }
+}
+
 // U[k][pq] = sum_c M[pq][c] Wcol[k][c]
 __global__ void ufield_kernel(int n, int64_t N, const double2* __restrict__ M, const double* __restrict__ W,
                               double2* __restrict__ U) {
@@ -486,7 +499,8 @@ namespace afem {
 struct StepWork {
     double2 *y, *phi_new, *U, *ipartial, *X, *eri, *h, *g1, *g2, *hp, *M, *cpart;
     double2 *D, *Y, *sigma, *t0, *t1, *acc;
-    double *energy, *shift;
+    double2* Z;   // [3][n][n] phi_p^H F[x_d] phi_q
+    double *energy, *shift, *dip;
     int* status;
     float2* U32;
     unsigned* counters;
@@ -514,6 +528,8 @@ static void carve_step(Carver& cv, StepWork& w, int64_t N, int n, int64_t dim, b
     w.acc = cv.take<double2>(dim);
     w.energy = cv.take<double>(1);
     w.shift = cv.take<double>(1);
+    w.Z = cv.take<double2>(size_t(3) * nn);
+    w.dip = cv.take<double>(3);
     w.status = cv.take<int>(1);
     w.U32 = mixed ? cv.take<float2>(size_t(N) * nn) : nullptr;
     w.counters = cv.take<unsigned>(4);
@@ -578,6 +594,12 @@ int mctdhf_step(afem_mctdhf* S, double2* phi, double2* C, double* W, const doubl
     if ((rc = launch_op_apply(m, AFEM_OP_H1, E, phi, w.y, n, s))) return rc;
     AFEM_CUDA_TRY(cudaMemsetAsync(w.counters, 0, 4 * sizeof(unsigned), s));
     if ((rc = cdot(phi, n, w.y, n, D.ml, D.n_interior, 0, w.cpart, w.h, w.counters, s))) return rc;
+    // position matrices Z_d[pq] = phi_p^H F[x_d] phi_q = phi_p^H M_L (M_L^-1 F[x_d] phi_q)
+    for (int d = 0; d < 3; ++d) {
+        const double e[3] = {d == 0 ? 1.0 : 0.0, d == 1 ? 1.0 : 0.0, d == 2 ? 1.0 : 0.0};
+        if ((rc = launch_op_apply(m, AFEM_OP_POS, e, phi, w.y, n, s))) return rc;
+        if ((rc = cdot(phi, n, w.y, n, D.ml, D.n_interior, 0, w.cpart, w.Z + d * nn, w.counters, s))) return rc;
+    }
     IntArgs ia{phi, W, n, N, D.n_interior, D.n_hanging, D.mf_master, D.mf_hang, D.hang_ptr, D.hang_master, D.hang_w};
     const size_t ismem = size_t(kIntTile) * nn * (sizeof(double2) + sizeof(double)) + size_t(nn) * nn * sizeof(double2);
     AFEM_CUDA_TRY(cudaFuncSetAttribute(integrals_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ismem)));
@@ -588,12 +610,14 @@ int mctdhf_step(afem_mctdhf* S, double2* phi, double2* C, double* W, const doubl
     AFEM_LAUNCH((ci_excite_kernel), ci_grid(dim), 128, 0, s, S->ci, C, w.D);
     AFEM_LAUNCH((ci_rdm_kernel), (nn + nn * nn + 127) / 128, 128, 0, s, n, dim, C, w.D, w.g1, w.g2);
     SmallOut so{w.hp, w.M, w.energy, w.status};
+    AFEM_LAUNCH((dipole_kernel), 1, 32, 0, s, n, w.Z, w.g1, w.dip);
     AFEM_LAUNCH((small_block_kernel), 1, 32, 0, s, n, w.h, w.eri, w.g1, w.g2, so);
     AFEM_CUDA_TRY(cudaGetLastError());
     int status = 0;
-    double energy = 0.0;
+    double energy = 0.0, dipole[3] = {0.0, 0.0, 0.0};
     AFEM_CUDA_TRY(cudaMemcpyAsync(&status, w.status, sizeof(int), cudaMemcpyDeviceToHost, s));
     AFEM_CUDA_TRY(cudaMemcpyAsync(&energy, w.energy, sizeof(double), cudaMemcpyDeviceToHost, s));
+    AFEM_CUDA_TRY(cudaMemcpyAsync(dipole, w.dip, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
     AFEM_CUDA_TRY(cudaStreamSynchronize(s));
     if (status) return set_error(AFEM_ESINGULAR, "afem_mctdhf_step: one-body density matrix is singular");
     // 3. C(t+dt) = exp(-i dt H_CI) C(t): Taylor series of (H - shift), times exp(-i dt shift)
@@ -633,6 +657,7 @@ int mctdhf_step(afem_mctdhf* S, double2* phi, double2* C, double* W, const doubl
     AFEM_CUDA_TRY(cudaStreamSynchronize(s));
     if (info) {
         info->energy = energy;
+        for (int d = 0; d < 3; ++d) info->dipole[d] = dipole[d];
         info->arnoldi_err = err;
         info->krylov_m_used = m_used;
         info->breakdown = brk;

@@ -1,7 +1,7 @@
 """GPU parity of afem_mctdhf_step against the oracle's MCTDHF step (Sec. 2,
 Sec. 3.2; Eqs. ci_eom, orb_eom, packed_orb_eom).  The GPU Poisson batch runs
 to rtol 1e-14 so that its forward error (kappa * rtol) stays far below the
-1e-10 bar on orbitals, CI vector and energy; the oracle solves directly."""
+1e-10 bar on orbitals, CI vector, energy and dipole; the oracle solves directly."""
 import numpy as np
 import pytest
 
@@ -52,6 +52,9 @@ def test_mctdhf_steps_parity(case, n, na, nb):
         cg = C.cpu().numpy()
         assert np.linalg.norm(cg - C_o) / np.linalg.norm(C_o) < 1e-10
         assert abs(info["energy"] - info_o["energy"]) < 1e-10 * abs(info_o["energy"])
+        # <sum r_i> at t (scale: the electron count times the box half-width)
+        dscale = max(np.max(np.abs(info_o["dipole"])), (na + nb) * 1.0)
+        assert np.max(np.abs(np.asarray(info["dipole"]) - info_o["dipole"])) < 1e-10 * dscale
         assert info["krylov_m_used"] == info_o["m_used"]
         assert abs(info["arnoldi_err"] - info_o["arnoldi_err"]) <= 1e-6 * info_o["arnoldi_err"] + 1e-16
 

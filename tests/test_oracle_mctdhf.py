@@ -207,3 +207,47 @@ def test_arnoldi_propagate_meets_tolerance_on_stiff_operator():
     out, est, sub = krylov.arnoldi_propagate(lambda v: G @ v, phi, inner, 6, 0.05, 1e-10)
     assert sub > 1
     assert np.linalg.norm(out - ref) < 50 * 1e-10 * sub * np.linalg.norm(phi)
+
+
+# ------------------------------------------------------------------- dipole
+def _dipole_state(case, n, na, nb):
+    m = mesh.Mesh(*case)
+    op = fem.Operators(m)
+    interior = ~m.boundary
+    phi = inputs.lowdin(inputs.molecular_orbitals(m.Xm, interior, case[4], n, phase_noise=0.0), op.ML)
+    C = inputs.initial_ci(n, na, nb)
+    return m, op, phi, C
+
+
+def test_dipole_is_translation_covariant():
+    """Moving the whole system (box, nuclei, orbitals) by a = (t, t, t) changes
+    <sum r_i> by N_e a (N_e = tr gamma), whatever the orbitals and CI vector."""
+    t = 2.0
+    nuclei = [((0.3, 0.1, 0.35), 1.0, 1), ((-0.2, 0.0, -0.35), 1.0, 1)]
+    base = (-4.0, 4.0, 2, 2, nuclei, 2.0)
+    moved = (-4.0 + t, 4.0 + t, 2, 2, [(tuple(np.asarray(R) + t), Z, L) for (R, Z, L) in nuclei], 2.0)
+    out = []
+    for case in (base, moved):
+        m, op, phi, C = _dipole_state(case, 2, 1, 1)
+        sim = mctdhf.MCTDHF(op, 2, 1, 1)
+        out.append((sim.dipole(phi, C), np.real(np.trace(sim.ci.rdm1(C)))))
+    (d0, ne0), (d1, ne1) = out
+    assert abs(ne0 - 2.0) < 1e-12 and abs(ne1 - 2.0) < 1e-12
+    np.testing.assert_allclose(d1 - d0, ne0 * t * np.ones(3), rtol=0, atol=1e-10)
+
+
+def test_dipole_is_the_field_derivative_of_the_energy(tiny):
+    """Length gauge: H1~(E) = H1~(0) + sum_d E_d F[x_d] is linear in E, so the
+    central difference of the electronic energy in E_d equals <sum r_i>_d."""
+    m, op = tiny
+    interior = ~m.boundary
+    phi = inputs.lowdin(inputs.molecular_orbitals(m.Xm, interior, TINY[4], 2), op.ML)
+    C = inputs.initial_ci(2, 1, 1)
+    sim = mctdhf.MCTDHF(op, 2, 1, 1)
+    d = sim.dipole(phi, C)
+    eps = 1e-3
+    for k in range(3):
+        Ep = np.zeros(3)
+        Ep[k] = eps
+        fd = (sim.energy(phi, C, Ep) - sim.energy(phi, C, -Ep)) / (2 * eps)
+        assert abs(fd - d[k]) <= 1e-9 * max(1.0, abs(d[k]))
