@@ -181,6 +181,9 @@ int afem_mesh_tables(const afem_mesh* mesh, double* coords, double* lumped_mass,
 #define AFEM_OP_H1_C64 3     /* as AFEM_OP_H1 in complex64 (precision form) */
 #define AFEM_OP_POS 4        /* y = M_L^{-1} F[e.r] x, complex128, Dirichlet: the position operator
                                 along e (passed as E); dipole and field derivative of H1~ */
+#define AFEM_OP_FORCE 5      /* y = M_L^{-1} F[e.f] x, complex128, Dirichlet, f = -grad V the nuclear
+                                force on an electron (0 at a support point on a nucleus): the
+                                potential part of the Ehrenfest acceleration along e (passed as E) */
 
 /* Matrix-free operator application on n_vec vectors at once (Sec. 3.1).
  *
@@ -362,15 +365,21 @@ int afem_mctdhf_step(afem_mctdhf* solver, void* phi, void* C, void* W, const dou
  * of Eq. orb_eom vanish and the step is the Schroedinger propagator of the
  * length-gauge H1~ (Sec. 3.1, Sec. 3.2):
  *   phi_{k+1} = exp(-i dt H~(E_k)) phi_k,  H~(E) = M_L^-1 H1~(E e_dir),
- *   d_k = <phi_k, Z~ phi_k>_M,  Z~ = M_L^-1 F[e_dir . r]  (AFEM_OP_POS),
- * k = 0..n_steps-1, for a field E(t) = E_k e_dir held fixed over step k.
+ *   d_k = <phi_k, O phi_k>_M,  k = 0..n_steps,
+ * for a field E(t) = E_k e_dir held fixed over step k (k < n_steps).  The
+ * signal's operator is chosen by `observable`: AFEM_OP_POS, O = Z~ =
+ * M_L^-1 F[e_dir . r] (the dipole), or AFEM_OP_FORCE, O = M_L^-1 F[e_dir . f]
+ * with f = -grad V (the potential part of the Ehrenfest acceleration, whose
+ * full value adds -(e_dir . e_dir) E(t_k) for the electron).  Whatever the
+ * observable, dH~/dE = Z~ drives the derivatives.
  * Each step is one afem_arnoldi_propagate without projector (krylov_m, tol
  * and precision as there, except that tol = 0 takes one Krylov step of
  * dimension krylov_m per time step).
  * Arguments common to the three calls: e_dir host [3] (unit field direction;
  * any vector is accepted and scales the field), E host [n_steps] field
  * amplitudes (a.u.), dt > 0, krylov_m 1..16, tol >= 0, precision
- * AFEM_PREC_FP64 or AFEM_PREC_MIXED.  All three synchronise `stream` and
+ * AFEM_PREC_FP64 or AFEM_PREC_MIXED, observable AFEM_OP_POS or
+ * AFEM_OP_FORCE.  All three synchronise `stream` and
  * allocate mesh-owned (grow-only) workspace.  Errors: AFEM_EINVAL (null or
  * out-of-range argument, host-only mesh), AFEM_ENOMEM, AFEM_ECUDA, and the
  * Arnoldi errors.
@@ -381,27 +390,27 @@ int afem_mctdhf_step(afem_mctdhf* solver, void* phi, void* C, void* W, const dou
  * complex128 [ceil(n_steps / ckpt_every)][N]; slot c receives phi_{c
  * ckpt_every}; ckpt_every >= 1 when ckpt is given. */
 int afem_tdse_forward(afem_mesh* mesh, const double* e_dir, const double* E, int n_steps, double dt,
-                      int krylov_m, double tol, int precision, const void* phi0, void* phi_end, double* d,
-                      void* ckpt, int ckpt_every, void* stream);
+                      int krylov_m, double tol, int precision, int observable, const void* phi0,
+                      void* phi_end, double* d, void* ckpt, int ckpt_every, void* stream);
 /* afem_tdse_jvp: the tangent map v -> dd = (dd/dE) v along the trajectory from
  * phi0, by propagating [dphi; phi] with exp(-i dt [[H~, v_k Z~], [0, H~]])
  * (the block form of the Frechet derivative of exp).  v host [n_steps]; d and
  * dd host [n_steps + 1] receive the signal and its directional derivative. */
 int afem_tdse_jvp(afem_mesh* mesh, const double* e_dir, const double* E, int n_steps, double dt,
-                  int krylov_m, double tol, int precision, const void* phi0, const double* v, double* d,
-                  double* dd, void* stream);
+                  int krylov_m, double tol, int precision, int observable, const void* phi0,
+                  const double* v, double* d, double* dd, void* stream);
 /* afem_tdse_vjp: the adjoint map g -> grad_E = (dd/dE)^T g, n_steps >= 1.
  * ckpt/ckpt_every as written by afem_tdse_forward with the same E, dt,
  * krylov_m, tol and precision; each segment of ckpt_every steps is recomputed
  * from its checkpoint, then swept backward with
  *   [lam_k; mu_k] = exp(+i dt [[H~, 0], [Z~, H~]]) [lam_{k+1}; 0],
- *   grad_E[k] = 2 Re <mu_k, phi_k>_M,  lam_k <- lam_k + g_k Z~ phi_k,
- * from lam_{n_steps} = g_{n_steps} Z~ phi_{n_steps}.  g host [n_steps + 1],
+ *   grad_E[k] = 2 Re <mu_k, phi_k>_M,  lam_k <- lam_k + g_k O phi_k,
+ * from lam_{n_steps} = g_{n_steps} O phi_{n_steps}.  g host [n_steps + 1],
  * grad_E host [n_steps]; lam0 (device complex128 [N], may be NULL) receives
  * lam_0, the gradient with respect to phi0 in <.,.>_M. */
 int afem_tdse_vjp(afem_mesh* mesh, const double* e_dir, const double* E, int n_steps, double dt,
-                  int krylov_m, double tol, int precision, const void* ckpt, int ckpt_every,
-                  const double* g, double* grad_E, void* lam0, void* stream);
+                  int krylov_m, double tol, int precision, int observable, const void* ckpt,
+                  int ckpt_every, const double* g, double* grad_E, void* lam0, void* stream);
 
 /* ---- Batching form: many independent instances in one launch.
  * The FP32 cell passes of Sec. 3.1 (Eq. discretized_eom) applied to every

@@ -80,6 +80,18 @@ class Operators:
             V[on] -= Z * CUBE_MEAN_INV_R / s[on]
         return V
 
+    def nuclear_force(self, X):
+        """-grad V (nf, 3) at the support points X: -sum_a Z_a (x - R_a) / |x - R_a|^3,
+        the force of the nuclei on an electron; 0 at a point on a nucleus (the
+        cube-averaged force vanishes there by symmetry)."""
+        F = np.zeros((len(X), 3))
+        for (R, Z, _L) in self.mesh.nuclei:
+            r = X - R[None, :]
+            d = np.linalg.norm(r, axis=1)
+            on = d < 1e-10
+            F[~on] -= Z * r[~on] / d[~on, None] ** 3
+        return F
+
     def pointwise(self, f):
         """F[f] = C^T diag(m_f o f) C for a function f given at the support points."""
         return (self.C.T @ sp.diags(self.m_f * f) @ self.C).tocsr()

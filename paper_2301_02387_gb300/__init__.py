@@ -11,7 +11,7 @@ import ctypes
 import numpy as np
 
 from . import _capi
-from ._capi import AfemError, OP_H1, OP_STIFF, OP_STIFF_F32, OP_H1_C64, OP_POS  # noqa: F401
+from ._capi import AfemError, OP_H1, OP_STIFF, OP_STIFF_F32, OP_H1_C64, OP_POS, OP_FORCE  # noqa: F401
 
 __all__ = ["Mesh", "op_apply", "AfemError", "OP_H1", "OP_STIFF", "load_library"]
 
@@ -243,11 +243,13 @@ def op_apply(mesh, kind, x, y, E=None, stream=None):
     """afem_op_apply: y = op(x) for all columns of x ([N, n_vec], DoF-major).
 
     OP_H1: complex128, y = M_L^{-1} H1~ x (Dirichlet); OP_STIFF: float64, y = A x;
-    OP_POS: complex128, y = M_L^{-1} F[e.r] x (Dirichlet) with e passed as E.
+    OP_POS: complex128, y = M_L^{-1} F[e.r] x (Dirichlet) with e passed as E;
+    OP_FORCE: the same with the nuclear force e.(-grad V) in place of e.r.
     """
     import torch
     dtype = {OP_H1: torch.complex128, OP_STIFF: torch.float64, OP_STIFF_F32: torch.float32,
-             OP_H1_C64: torch.complex64, OP_POS: torch.complex128}.get(kind, x.dtype)
+             OP_H1_C64: torch.complex64, OP_POS: torch.complex128,
+             OP_FORCE: torch.complex128}.get(kind, x.dtype)
     xp = _dev_ptr(x, dtype, mesh.N, "x")
     yp = _dev_ptr(y, dtype, mesh.N, "y")
     if x.shape != y.shape:

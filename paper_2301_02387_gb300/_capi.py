@@ -28,6 +28,7 @@ OP_STIFF = 1
 OP_STIFF_F32 = 2
 OP_H1_C64 = 3
 OP_POS = 4
+OP_FORCE = 5
 
 CONVERT_F64_F32 = 0
 CONVERT_F32_F64 = 1
@@ -138,11 +139,12 @@ SIGNATURES = {
     "afem_batch_get_tuning": (ctypes.c_int, [_P, ctypes.POINTER(BatchTuning)]),
     "afem_convert": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int, _P]),
     "afem_tdse_forward": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_int,
-                                         ctypes.c_double, ctypes.c_int, _P, _P, _P, _P, ctypes.c_int, _P]),
+                                         ctypes.c_double, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P,
+                                         ctypes.c_int, _P]),
     "afem_tdse_jvp": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double,
-                                     ctypes.c_int, _P, _P, _P, _P, _P]),
+                                     ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P]),
     "afem_tdse_vjp": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double,
-                                     ctypes.c_int, _P, ctypes.c_int, _P, _P, _P, _P]),
+                                     ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P, _P, _P, _P]),
 }
 
 

@@ -98,6 +98,7 @@ struct HostMesh {
     std::vector<double> hang_w;            // [nnz]
     std::vector<double> ml;                // [N] lumped mass C^T m_f
     std::vector<double> v_master, v_hang;  // nuclear potential at masters / hanging points
+    std::vector<double> f_master, f_hang;  // [N][3] / [nh][3] nuclear force on an electron, -grad V
     std::vector<double> stiff_diag;        // [N] diagonal of the constrained stiffness A
     std::vector<double> mf_master, mf_hang;  // assembled GLL weight m_f at masters / hanging points
 };
@@ -117,6 +118,8 @@ struct DeviceMesh {
     double* ml_inv = nullptr;       // [N]
     double* v_master = nullptr;     // [N]
     double* v_hang = nullptr;       // [nh]
+    double* f_master = nullptr;     // [N][3] -grad V
+    double* f_hang = nullptr;       // [nh][3]
     double* stiff_dinv = nullptr;   // [N] 1 / diag(A) on interior masters, 0 on the surface
     double* master_xyz = nullptr;   // [N][3]
     double* hang_xyz = nullptr;     // [nh][3]
@@ -169,11 +172,12 @@ int mctdhf_step(afem_mctdhf* S, double2* phi, double2* C, double* W, const doubl
 int convert_f64_f32(const double* x, float* y, int64_t n, cudaStream_t s);
 int convert_f32_f64(const float* x, double* y, int64_t n, cudaStream_t s);
 int tdse_forward(afem_mesh* m, const double* e_dir, const double* E, int K, double dt, int mk, double tol,
-                 int precision, const double2* phi0, double2* phi_end, double* d, double2* ckpt, int every,
-                 cudaStream_t s);
+                 int precision, int observable, const double2* phi0, double2* phi_end, double* d, double2* ckpt,
+                 int every, cudaStream_t s);
 int tdse_jvp(afem_mesh* m, const double* e_dir, const double* E, int K, double dt, int mk, double tol,
-             int precision, const double2* phi0, const double* v, double* d, double* dd, cudaStream_t s);
-int tdse_vjp(afem_mesh* m, const double* e_dir, const double* E, int K, double dt, int mk, double tol,
-             int precision, const double2* ckpt, int every, const double* g, double* grad_E, double2* lam0,
+             int precision, int observable, const double2* phi0, const double* v, double* d, double* dd,
              cudaStream_t s);
+int tdse_vjp(afem_mesh* m, const double* e_dir, const double* E, int K, double dt, int mk, double tol,
+             int precision, int observable, const double2* ckpt, int every, const double* g, double* grad_E,
+             double2* lam0, cudaStream_t s);
 }  // namespace afem

@@ -337,25 +337,27 @@ int afem_convert(const void* x, void* y, int64_t n, int direction, void* stream)
 }
 
 int afem_tdse_forward(afem_mesh* m, const double* e_dir, const double* E, int n_steps, double dt, int krylov_m,
-                      double tol, int precision, const void* phi0, void* phi_end, double* d, void* ckpt,
-                      int ckpt_every, void* stream) {
-    return tdse_forward(m, e_dir, E, n_steps, dt, krylov_m, tol, precision, static_cast<const double2*>(phi0),
+                      double tol, int precision, int observable, const void* phi0, void* phi_end, double* d,
+                      void* ckpt, int ckpt_every, void* stream) {
+    return tdse_forward(m, e_dir, E, n_steps, dt, krylov_m, tol, precision, observable,
+                        static_cast<const double2*>(phi0),
                         static_cast<double2*>(phi_end), d, static_cast<double2*>(ckpt), ckpt_every,
                         static_cast<cudaStream_t>(stream));
 }
 
 int afem_tdse_jvp(afem_mesh* m, const double* e_dir, const double* E, int n_steps, double dt, int krylov_m,
-                  double tol, int precision, const void* phi0, const double* v, double* d, double* dd,
-                  void* stream) {
-    return tdse_jvp(m, e_dir, E, n_steps, dt, krylov_m, tol, precision, static_cast<const double2*>(phi0), v, d, dd,
-                    static_cast<cudaStream_t>(stream));
+                  double tol, int precision, int observable, const void* phi0, const double* v, double* d,
+                  double* dd, void* stream) {
+    return tdse_jvp(m, e_dir, E, n_steps, dt, krylov_m, tol, precision, observable,
+                    static_cast<const double2*>(phi0), v, d, dd, static_cast<cudaStream_t>(stream));
 }
 
 int afem_tdse_vjp(afem_mesh* m, const double* e_dir, const double* E, int n_steps, double dt, int krylov_m,
-                  double tol, int precision, const void* ckpt, int ckpt_every, const double* g, double* grad_E,
-                  void* lam0, void* stream) {
-    return tdse_vjp(m, e_dir, E, n_steps, dt, krylov_m, tol, precision, static_cast<const double2*>(ckpt),
-                    ckpt_every, g, grad_E, static_cast<double2*>(lam0), static_cast<cudaStream_t>(stream));
+                  double tol, int precision, int observable, const void* ckpt, int ckpt_every, const double* g,
+                  double* grad_E, void* lam0, void* stream) {
+    return tdse_vjp(m, e_dir, E, n_steps, dt, krylov_m, tol, precision, observable,
+                    static_cast<const double2*>(ckpt), ckpt_every, g, grad_E, static_cast<double2*>(lam0),
+                    static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

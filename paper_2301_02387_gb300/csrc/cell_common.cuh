@@ -24,11 +24,13 @@ struct CellArgs {
     const double* hw;
     const double* v_master;
     const double* v_hang;
+    const double* f_master;     // [N][3] nuclear force (with_pot == 3)
+    const double* f_hang;       // [nh][3]
     int64_t n_interior;
     BasisParams B;
     double E[3];
     double c_kin;               // factor of the stiffness term
-    int with_pot;               // add the pointwise term F[V + E.r]
+    int with_pot;               // pointwise term: 1 F[V + E.r], 2 F[E.r], 3 F[E.force]
     int masked;                 // treat surface masters (>= n_interior) as zero, in and out
 };
 

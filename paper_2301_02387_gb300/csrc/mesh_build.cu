@@ -483,6 +483,23 @@ int build_host_mesh(const afem_mesh_desc& d, HostMesh& M) {
     M.v_hang.resize(nhang);
     for (int64_t m = 0; m < nmaster; ++m) M.v_master[m] = potential(&M.master_xyz[3 * m], mf_master[m]);
     for (int64_t hh = 0; hh < nhang; ++hh) M.v_hang[hh] = potential(&M.hang_xyz[3 * hh], mf_hang[hh]);
+    // ---- nuclear force on an electron, -grad V = -sum_a Z_a (x - R_a) / |x - R_a|^3
+    // (the Ehrenfest acceleration's potential part); 0 at a support point on a
+    // nucleus, where the cube-averaged value vanishes by symmetry.
+    auto force = [&](const double* x, double* f) {
+        f[0] = f[1] = f[2] = 0.0;
+        for (int n = 0; n < d.n_nuclei; ++n) {
+            const double r3[3] = {x[0] - d.nuc_pos[n][0], x[1] - d.nuc_pos[n][1], x[2] - d.nuc_pos[n][2]};
+            const double r = std::sqrt(r3[0] * r3[0] + r3[1] * r3[1] + r3[2] * r3[2]);
+            if (r < 1e-10) continue;
+            const double c = d.nuc_charge[n] / (r * r * r);
+            for (int k = 0; k < 3; ++k) f[k] -= c * r3[k];
+        }
+    };
+    M.f_master.resize(3 * size_t(nmaster));
+    M.f_hang.resize(3 * size_t(nhang));
+    for (int64_t m = 0; m < nmaster; ++m) force(&M.master_xyz[3 * m], &M.f_master[3 * m]);
+    for (int64_t hh = 0; hh < nhang; ++hh) force(&M.hang_xyz[3 * hh], &M.f_hang[3 * hh]);
 
     // ---- diagonal of the constrained stiffness A = C^T (sum_K P_K^T A_K P_K) C:
     // per cell, each master k has local coefficients c_k (1 at its own node,
@@ -566,6 +583,8 @@ int upload_mesh(afem_mesh* m) {
     if ((rc = upload(D.ml_inv, ml_inv.data(), ml_inv.size()))) return rc;
     if ((rc = upload(D.v_master, H.v_master.data(), H.v_master.size()))) return rc;
     if ((rc = upload(D.v_hang, H.v_hang.data(), H.v_hang.size()))) return rc;
+    if ((rc = upload(D.f_master, H.f_master.data(), H.f_master.size()))) return rc;
+    if ((rc = upload(D.f_hang, H.f_hang.data(), H.f_hang.size()))) return rc;
     {
         std::vector<double> dinv(H.n_master, 0.0);
         for (int64_t k = 0; k < H.n_interior; ++k) dinv[k] = 1.0 / H.stiff_diag[k];
@@ -618,6 +637,8 @@ void free_device_mesh(DeviceMesh& D) {
     cudaFree(D.ml_inv);
     cudaFree(D.v_master);
     cudaFree(D.v_hang);
+    cudaFree(D.f_master);
+    cudaFree(D.f_hang);
     cudaFree(D.stiff_dinv);
     cudaFree(D.master_xyz);
     cudaFree(D.hang_xyz);

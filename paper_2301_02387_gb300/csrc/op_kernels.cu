@@ -50,12 +50,19 @@ __global__ void __launch_bounds__(256) cell_op_kernel(CellArgs a, const T* __res
         for (int n = tid; n < NN; n += bs) {
             const int ia = n % P1, ib = (n / P1) % P1, ic = n / (P1 * P1);
             const int idx = s_idx[n];
-            // with_pot == 2: the field term E.r alone (the position operator)
-            const double V = a.with_pot == 2 ? 0.0 : (idx >= 0 ? a.v_master[idx] : a.v_hang[-idx - 1]);
-            const double px = g.x + g.w * a.B.xi[ia];
-            const double py = g.y + g.w * a.B.xi[ib];
-            const double pz = g.z + g.w * a.B.xi[ic];
-            const double f = V + a.E[0] * px + a.E[1] * py + a.E[2] * pz;
+            // with_pot == 2: the field term E.r alone (the position operator);
+            // with_pot == 3: E.force (the nuclear force along E)
+            double f;
+            if (a.with_pot == 3) {
+                const double* F = idx >= 0 ? a.f_master + 3 * int64_t(idx) : a.f_hang + 3 * int64_t(-idx - 1);
+                f = a.E[0] * F[0] + a.E[1] * F[1] + a.E[2] * F[2];
+            } else {
+                const double V = a.with_pot == 2 ? 0.0 : (idx >= 0 ? a.v_master[idx] : a.v_hang[-idx - 1]);
+                const double px = g.x + g.w * a.B.xi[ia];
+                const double py = g.y + g.w * a.B.xi[ib];
+                const double pz = g.z + g.w * a.B.xi[ic];
+                f = V + a.E[0] * px + a.E[1] * py + a.E[2] * pz;
+            }
             s_pot[n] = h3 * s_w[ia] * s_w[ib] * s_w[ic] * f;
         }
     }
@@ -221,6 +228,8 @@ CellArgs make_cell_args(const afem_mesh* m) {
     a.hw = D.hang_w;
     a.v_master = D.v_master;
     a.v_hang = D.v_hang;
+    a.f_master = D.f_master;
+    a.f_hang = D.f_hang;
     a.n_interior = D.n_interior;
     const Basis1D& b = m->basis;
     const int p1 = b.p + 1;
@@ -311,9 +320,9 @@ int launch_op_apply(afem_mesh* m, int kind, const double* E, const void* x, void
         AFEM_CUDA_TRY(cudaMemsetAsync(yy, 0, size_t(N) * nv * sizeof(double), s));
         return launch_cell_op<double>(m, a, static_cast<const double*>(x), yy, nv, s);
     }
-    if (kind == AFEM_OP_POS) {   // y = M_L^-1 F[e.r] x, Dirichlet-masked
+    if (kind == AFEM_OP_POS || kind == AFEM_OP_FORCE) {   // y = M_L^-1 F[e.r] x or M_L^-1 F[e.force] x, masked
         a.c_kin = 0.0;
-        a.with_pot = 2;
+        a.with_pot = kind == AFEM_OP_POS ? 2 : 3;
         a.masked = 1;
         for (int i = 0; i < 3; ++i) a.E[i] = E ? E[i] : 0.0;
         auto* yy = static_cast<double2*>(y);

@@ -4,7 +4,8 @@
 // Schroedinger equation with the length-gauge H1~ of Sec. 3.1).
 //
 //   phi_{k+1} = P_k phi_k,   P_k = exp(-i dt H~(E_k)),   H~(E) = M_L^-1 H1~(E e)
-//   d_k       = <phi_k, Z~ phi_k>_M,                      Z~ = M_L^-1 F[e.r] = dH~/dE
+//   d_k       = <phi_k, O phi_k>_M,  O = Z~ = M_L^-1 F[e.r] = dH~/dE (dipole) or
+//               O = M_L^-1 F[e.f], f = -grad V (the potential part of the Ehrenfest acceleration)
 //
 // Derivatives with respect to the field samples E_k use the block identity
 //   exp([[X, Y], [0, X]]) = [[exp X, L(X, Y)], [0, exp X]],
@@ -15,7 +16,8 @@
 //   adjoint:  exp(+i dt [[H~, 0], [Z~, H~]]) [lam_{k+1}; 0] = [P_k^+ lam_{k+1}; L_k^+ lam_{k+1}]
 // where ^+ is the adjoint in <.,.>_M; so each backward step is one Arnoldi
 // propagation of a two-column vector, which yields both the propagated adjoint
-// state and the field gradient dJ/dE_k = 2 Re <L_k^+ lam_{k+1}, phi_k>_M.
+// state and the field gradient dJ/dE_k = 2 Re <L_k^+ lam_{k+1}, phi_k>_M; the
+// signal's operator O enters only the seeds g_k O phi_k of the adjoint state.
 #include <vector>
 
 #include "afem_internal.h"
@@ -89,18 +91,21 @@ struct Stepper {
     double dt, tol;
     int mk, mixed;
     cudaStream_t s;
+    int obs;   // operator kind of the signal: AFEM_OP_POS (dipole) or AFEM_OP_FORCE
     int step(double Ek, const double2* in, const double2* U, int n, double2* out, int flags) const {
         const double E[3] = {Ek * e[0], Ek * e[1], Ek * e[2]};
         return arnoldi_step(m, E, in, U, nullptr, n, mk, dt, mixed, tol, out, nullptr, nullptr, nullptr, nullptr, s,
                             flags | kArnNoProjector);
     }
-    // y = Z~ x for nv columns of x
-    int pos(const double2* x, double2* y, int nv) const { return launch_op_apply(m, AFEM_OP_POS, e, x, y, nv, s); }
+    // y = O x for nv columns of x, O the signal's operator (Z~ for the dipole)
+    int pos(const double2* x, double2* y, int nv) const { return launch_op_apply(m, obs, e, x, y, nv, s); }
 };
 
 int check_common(afem_mesh* m, const double* e_dir, const double* E, int K, double dt, int mk, double tol,
-                 int precision, const char* who) {
+                 int precision, int observable, const char* who) {
     const std::string w(who);
+    if (observable != AFEM_OP_POS && observable != AFEM_OP_FORCE)
+        return set_error(AFEM_EINVAL, w + ": observable must be AFEM_OP_POS or AFEM_OP_FORCE");
     if (!m || !e_dir || (K > 0 && !E)) return set_error(AFEM_EINVAL, w + ": null argument");
     if (K < 0) return set_error(AFEM_EINVAL, w + ": n_steps must be >= 0");
     if (!(dt > 0.0)) return set_error(AFEM_EINVAL, w + ": dt must be > 0");
@@ -115,9 +120,9 @@ int check_common(afem_mesh* m, const double* e_dir, const double* E, int K, doub
 }  // namespace
 
 int tdse_forward(afem_mesh* m, const double* e_dir, const double* E, int K, double dt, int mk, double tol,
-                 int precision, const double2* phi0, double2* phi_end, double* d, double2* ckpt, int every,
-                 cudaStream_t s) {
-    int rc = check_common(m, e_dir, E, K, dt, mk, tol, precision, "afem_tdse_forward");
+                 int precision, int observable, const double2* phi0, double2* phi_end, double* d, double2* ckpt,
+                 int every, cudaStream_t s) {
+    int rc = check_common(m, e_dir, E, K, dt, mk, tol, precision, observable, "afem_tdse_forward");
     if (rc) return rc;
     if (!phi0 || !d) return set_error(AFEM_EINVAL, "afem_tdse_forward: null argument");
     if (ckpt && every < 1) return set_error(AFEM_EINVAL, "afem_tdse_forward: checkpoint interval must be >= 1");
@@ -126,7 +131,7 @@ int tdse_forward(afem_mesh* m, const double* e_dir, const double* E, int K, doub
     TdseWork w{};
     if ((rc = tdse_reserve(m, int64_t(K) + 1, 1, w))) return rc;
     AFEM_CUDA_TRY(cudaMemsetAsync(w.cnt, 0, 4 * sizeof(unsigned), s));
-    const Stepper st{m, {e_dir[0], e_dir[1], e_dir[2]}, dt, tol, mk, precision == AFEM_PREC_MIXED, s};
+    const Stepper st{m, {e_dir[0], e_dir[1], e_dir[2]}, dt, tol, mk, precision == AFEM_PREC_MIXED, s, observable};
     double2* cur = w.phis;        // ping-pong between the two segment slots
     double2* nxt = w.phis + N;
     AFEM_CUDA_TRY(cudaMemcpyAsync(cur, phi0, N * sizeof(double2), cudaMemcpyDeviceToDevice, s));
@@ -134,7 +139,7 @@ int tdse_forward(afem_mesh* m, const double* e_dir, const double* E, int K, doub
         if (ckpt && k < K && k % every == 0)
             AFEM_CUDA_TRY(cudaMemcpyAsync(ckpt + int64_t(k / every) * N, cur, N * sizeof(double2),
                                           cudaMemcpyDeviceToDevice, s));
-        // d_k = <phi_k, Z~ phi_k>_M
+        // d_k = <phi_k, O phi_k>_M
         if ((rc = st.pos(cur, w.Y, 1))) return rc;
         if ((rc = cdot(cur, 1, w.Y, 1, D.ml, D.n_interior, 0, w.part, w.dots + k, w.cnt, s))) return rc;
         if (k == K) break;
@@ -150,8 +155,9 @@ int tdse_forward(afem_mesh* m, const double* e_dir, const double* E, int K, doub
 }
 
 int tdse_jvp(afem_mesh* m, const double* e_dir, const double* E, int K, double dt, int mk, double tol,
-             int precision, const double2* phi0, const double* v, double* d, double* dd, cudaStream_t s) {
-    int rc = check_common(m, e_dir, E, K, dt, mk, tol, precision, "afem_tdse_jvp");
+             int precision, int observable, const double2* phi0, const double* v, double* d, double* dd,
+             cudaStream_t s) {
+    int rc = check_common(m, e_dir, E, K, dt, mk, tol, precision, observable, "afem_tdse_jvp");
     if (rc) return rc;
     if (!phi0 || (K > 0 && !v) || !d || !dd) return set_error(AFEM_EINVAL, "afem_tdse_jvp: null argument");
     const DeviceMesh& D = m->dev;
@@ -159,7 +165,7 @@ int tdse_jvp(afem_mesh* m, const double* e_dir, const double* E, int K, double d
     TdseWork w{};
     if ((rc = tdse_reserve(m, int64_t(K) + 1, 0, w))) return rc;
     AFEM_CUDA_TRY(cudaMemsetAsync(w.cnt, 0, 4 * sizeof(unsigned), s));
-    const Stepper st{m, {e_dir[0], e_dir[1], e_dir[2]}, dt, tol, mk, precision == AFEM_PREC_MIXED, s};
+    const Stepper st{m, {e_dir[0], e_dir[1], e_dir[2]}, dt, tol, mk, precision == AFEM_PREC_MIXED, s, observable};
     // [dphi_0; phi_0] = [0; phi_0]
     AFEM_CUDA_TRY(cudaMemsetAsync(w.X, 0, 2 * N * sizeof(double2), s));
     AFEM_CUDA_TRY(cudaMemcpy2DAsync(w.X + 1, 2 * sizeof(double2), phi0, sizeof(double2), sizeof(double2), N,
@@ -167,7 +173,7 @@ int tdse_jvp(afem_mesh* m, const double* e_dir, const double* E, int K, double d
     double2* cur = w.X;
     double2* nxt = w.Xn;
     for (int k = 0;; ++k) {
-        // S[a][b] = <X_a, Z~ X_b>_M: d_k = S[1][1], dd_k = 2 Re S[0][1]
+        // S[a][b] = <X_a, O X_b>_M: d_k = S[1][1], dd_k = 2 Re S[0][1]
         if ((rc = st.pos(cur, w.Y, 2))) return rc;
         if ((rc = cdot(cur, 2, w.Y, 2, D.ml, D.n_interior, 0, w.part, w.dots + 4 * int64_t(k), w.cnt, s))) return rc;
         if (k == K) break;
@@ -188,9 +194,9 @@ int tdse_jvp(afem_mesh* m, const double* e_dir, const double* E, int K, double d
 }
 
 int tdse_vjp(afem_mesh* m, const double* e_dir, const double* E, int K, double dt, int mk, double tol,
-             int precision, const double2* ckpt, int every, const double* g, double* grad_E, double2* lam0,
-             cudaStream_t s) {
-    int rc = check_common(m, e_dir, E, K, dt, mk, tol, precision, "afem_tdse_vjp");
+             int precision, int observable, const double2* ckpt, int every, const double* g, double* grad_E,
+             double2* lam0, cudaStream_t s) {
+    int rc = check_common(m, e_dir, E, K, dt, mk, tol, precision, observable, "afem_tdse_vjp");
     if (rc) return rc;
     if (K < 1) return set_error(AFEM_EINVAL, "afem_tdse_vjp: n_steps must be >= 1");
     if (!ckpt || !g || !grad_E) return set_error(AFEM_EINVAL, "afem_tdse_vjp: null argument");
@@ -201,7 +207,7 @@ int tdse_vjp(afem_mesh* m, const double* e_dir, const double* E, int K, double d
     TdseWork w{};
     if ((rc = tdse_reserve(m, 2 * int64_t(K), seg, w))) return rc;
     AFEM_CUDA_TRY(cudaMemsetAsync(w.cnt, 0, 4 * sizeof(unsigned), s));
-    const Stepper st{m, {e_dir[0], e_dir[1], e_dir[2]}, dt, tol, mk, precision == AFEM_PREC_MIXED, s};
+    const Stepper st{m, {e_dir[0], e_dir[1], e_dir[2]}, dt, tol, mk, precision == AFEM_PREC_MIXED, s, observable};
     // [[H~, 0], [Z~, H~]]: the position field in slot (1, 0), the same for every step
     AFEM_LAUNCH((fill_pos_field_kernel), grid_for(N), 256, 0, s, w.U, D.master_xyz, st.e[0], st.e[1], st.e[2], 0.0,
                 1.0, N);
@@ -229,7 +235,7 @@ int tdse_vjp(afem_mesh* m, const double* e_dir, const double* E, int K, double d
             // <L_j^+ lam_{j+1}, phi_j>_M in slot 1 of the pair
             if ((rc = cdot(w.Xn, 2, phij, 1, D.ml, D.n_interior, 0, w.part, w.dots + 2 * int64_t(j), w.cnt, s)))
                 return rc;
-            // lam_j = P_j^+ lam_{j+1} + g_j Z~ phi_j
+            // lam_j = P_j^+ lam_{j+1} + g_j O phi_j
             if ((rc = st.pos(phij, zphi, 1))) return rc;
             AFEM_LAUNCH((adjoint_seed_kernel), grid_for(N), 256, 0, s, w.X, w.Xn, zphi, g[j], N);
             AFEM_CUDA_TRY(cudaGetLastError());

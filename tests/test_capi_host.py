@@ -112,19 +112,25 @@ def test_tdse_entry_points_reject_bad_inputs_host_side():
     d = (ctypes.c_double * 3)()
     g = (ctypes.c_double * 3)(1.0, 1.0, 1.0)
     x = ctypes.c_void_p(16)   # never dereferenced: every call below fails its checks first
-    assert lib.afem_tdse_forward(m.handle, e, E, 2, 0.1, 8, 0.0, 0, x, None, d, None, 0, None) == _capi.AFEM_EINVAL
+    pos = _capi.OP_POS
+    assert lib.afem_tdse_forward(m.handle, e, E, 2, 0.1, 8, 0.0, 0, pos, x, None, d, None, 0,
+                                 None) == _capi.AFEM_EINVAL
     assert b"host-only" in lib.afem_last_error()
+    assert lib.afem_tdse_forward(m.handle, e, E, 2, 0.1, 8, 0.0, 0, _capi.OP_H1, x, None, d, None, 0,
+                                 None) == _capi.AFEM_EINVAL
+    assert b"observable" in lib.afem_last_error()
     m2 = Mesh(-2.0, 2.0, 1, 2, [], 2.0, host_only=True)
     for args, why in [((2, -0.1, 8, 0.0, 0), b"dt"), ((2, 0.1, 0, 0.0, 0), b"krylov_m"),
                       ((2, 0.1, 17, 0.0, 0), b"krylov_m"), ((2, 0.1, 8, -1.0, 0), b"tol"),
                       ((2, 0.1, 8, 0.0, 5), b"precision"), ((-1, 0.1, 8, 0.0, 0), b"n_steps")]:
         K, dt, mk, tol, prec = args
-        assert lib.afem_tdse_forward(m2.handle, e, E, K, dt, mk, tol, prec, x, None, d, None, 0,
+        assert lib.afem_tdse_forward(m2.handle, e, E, K, dt, mk, tol, prec, pos, x, None, d, None, 0,
                                      None) == _capi.AFEM_EINVAL
         assert why in lib.afem_last_error(), (args, lib.afem_last_error())
-    assert lib.afem_tdse_vjp(m2.handle, e, E, 0, 0.1, 8, 0.0, 0, x, 1, g, d, None, None) == _capi.AFEM_EINVAL
-    assert lib.afem_tdse_vjp(m2.handle, e, E, 2, 0.1, 8, 0.0, 0, None, 1, g, d, None, None) == _capi.AFEM_EINVAL
-    assert lib.afem_tdse_jvp(None, e, E, 2, 0.1, 8, 0.0, 0, x, E, d, d, None) == _capi.AFEM_EINVAL
+    assert lib.afem_tdse_vjp(m2.handle, e, E, 0, 0.1, 8, 0.0, 0, pos, x, 1, g, d, None, None) == _capi.AFEM_EINVAL
+    assert lib.afem_tdse_vjp(m2.handle, e, E, 2, 0.1, 8, 0.0, 0, pos, None, 1, g, d, None,
+                             None) == _capi.AFEM_EINVAL
+    assert lib.afem_tdse_jvp(None, e, E, 2, 0.1, 8, 0.0, 0, pos, x, E, d, d, None) == _capi.AFEM_EINVAL
 
 
 def test_spline_and_harmonic_yield_helpers():

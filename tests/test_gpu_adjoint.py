@@ -182,3 +182,61 @@ def test_full_size_dot_product_and_checkpoints():
     _, _, ck1 = adj.tdse_forward(gm, phi_g, E, dt, E_DIR, krylov_m=16, tol=0.0, ckpt_every=1)
     grad1, _ = adj.tdse_vjp(gm, ck1, 1, E, g, dt, E_DIR, krylov_m=16, tol=0.0)
     assert np.max(np.abs(grad1 - grad)) <= 1e-12 * np.max(np.abs(grad))
+
+
+@pytest.mark.parametrize("tol,dt", [(0.0, 0.01), (1e-12, 0.1)])
+def test_force_observable_matches_oracle(tol, dt):
+    """The signal <phi_k, M_L^-1 F[e.f] phi_k>_M (f = -grad V, the potential
+    part of the Ehrenfest acceleration), its adjoint and tangent against the
+    oracle, 1e-10 relative; oblique field direction."""
+    from oracle import adjoint as oadj2
+    from paper_2301_02387_gb300 import adjoint as adj
+    e_dir = (0.3, -0.4, 0.866)
+    gm, td, phi0, phi_g, perm, om = _setup(CASE, e_dir)
+    tdf = oadj2.TDSE(td.ops, e_dir=e_dir, observable="force")
+    K, every = 6, 4
+    E = _fields(K, 71)
+    rng = np.random.default_rng(72)
+    g = rng.standard_normal(K + 1)
+    v = rng.standard_normal(K)
+    d_ref, _ = tdf.forward(phi0, E, dt)
+    grad_ref, _ = tdf.vjp(phi0, E, dt, g)
+    _, dd_ref = tdf.jvp(phi0, E, dt, v)
+    kw = dict(krylov_m=16, tol=tol, observable="force")
+    d, _, ckpt = adj.tdse_forward(gm, phi_g, E, dt, e_dir, ckpt_every=every, **kw)
+    assert np.max(np.abs(d - d_ref)) <= 1e-10 * np.max(np.abs(d_ref))
+    grad, _ = adj.tdse_vjp(gm, ckpt, every, E, g, dt, e_dir, **kw)
+    assert np.max(np.abs(grad - grad_ref)) <= 1e-10 * np.max(np.abs(grad_ref))
+    _, dd = adj.tdse_jvp(gm, phi_g, E, v, dt, e_dir, **kw)
+    assert np.max(np.abs(dd - dd_ref)) <= 1e-10 * np.max(np.abs(dd_ref))
+
+
+def test_autograd_ehrenfest_yield_vs_central_differences():
+    """J = harmonic yield of the Ehrenfest acceleration a_k = <f.e>_k - E(t_k)
+    (the force signal from the hand-written adjoint, the explicit field term
+    and the spline by torch) against central differences (h = 1e-6) on 6
+    seeded spline samples, <= 1e-5 relative."""
+    import torch
+    from paper_2301_02387_gb300 import adjoint as adj
+    gm, td, phi0, phi_g, perm, om = _setup(CASE)
+    K, dt, n_c = 128, 0.05, 16
+    S = torch.from_numpy(adj.spline_matrix(n_c, K + 1))   # field at the K + 1 signal times
+    c0 = torch.from_numpy(0.05 * np.cos(np.linspace(0.0, 2.5 * np.pi, n_c)))
+
+    def J(c):
+        Es = S @ c
+        f = adj.dipole_signal(Es[:K], gm, phi_g, dt, E_DIR, krylov_m=16, tol=0.0, ckpt_every=16,
+                              observable="force")
+        a = adj.ehrenfest_acceleration(f, Es, E_DIR)
+        return adj.harmonic_yield(None, dt, 0.35, 2, 6, acceleration=a)
+
+    c = c0.clone().requires_grad_(True)
+    J(c).backward()
+    grad = c.grad.numpy()
+    h = 1e-6
+    for j in np.random.default_rng(81).choice(n_c, 6, replace=False):
+        cp, cm = c0.clone(), c0.clone()
+        cp[j] += h
+        cm[j] -= h
+        fd = (J(cp).item() - J(cm).item()) / (2 * h)
+        assert abs(grad[j] - fd) <= 1e-5 * np.max(np.abs(grad)), (j, grad[j], fd)

@@ -113,3 +113,57 @@ def test_adjoint_state_is_gradient_wrt_initial_state(sys1):
     fd = (g @ td.forward(phi0 + h * dphi, E, dt)[0] - g @ td.forward(phi0 - h * dphi, E, dt)[0]) / (2 * h)
     pred = 2.0 * np.real(td.inner(lam0, dphi))
     assert abs(pred - fd) <= 1e-7 * abs(fd)
+
+
+@pytest.fixture(scope="module")
+def sys_force():
+    om = omesh.Mesh(*CASE)
+    op = fem.Operators(om)
+    td = adjoint.TDSE(op, e_dir=(0.3, -0.4, 0.866), observable="force")
+    phi = inputs.lowdin(inputs.molecular_orbitals(om.Xm, ~om.boundary, CASE[4], 1), op.ML)[:, 0]
+    return td, td.restrict(phi)
+
+
+def test_nuclear_force_is_minus_grad_potential():
+    """f = -grad V against central differences of the oracle's potential at the
+    support points (those at least 0.3 bohr from every nucleus)."""
+    om = omesh.Mesh(*CASE)
+    op = fem.Operators(om)
+    X = om.X
+    F = op.nuclear_force(X)
+    far = np.ones(len(X), dtype=bool)
+    for (R, _Z, _L) in om.nuclei:
+        far &= np.linalg.norm(X - R[None, :], axis=1) > 0.3
+    assert far.sum() > 100
+    h = 1e-5
+    for k in range(3):
+        dX = np.zeros(3)
+        dX[k] = h
+        fd = -(op.nuclear_potential(X + dX) - op.nuclear_potential(X - dX)) / (2 * h)
+        np.testing.assert_allclose(F[far, k], fd[far], rtol=1e-6, atol=1e-8)
+    on = np.zeros(len(X), dtype=bool)
+    for (R, _Z, _L) in om.nuclei:
+        on |= np.linalg.norm(X - R[None, :], axis=1) < 1e-10
+    assert np.all(F[on] == 0.0)
+
+
+def test_force_observable_gradient_and_dot_product(sys_force):
+    """The adjoint with the force signal: central differences and the
+    dot-product identity, as for the dipole."""
+    td, phi0 = sys_force
+    K, dt = 4, 0.1
+    E = _fields(K, 21)
+    rng = np.random.default_rng(22)
+    g = rng.standard_normal(K + 1)
+    v = rng.standard_normal(K)
+    grad, _ = td.vjp(phi0, E, dt, g)
+    _, dd = td.jvp(phi0, E, dt, v)
+    assert abs(g @ dd - v @ grad) <= 1e-10 * max(abs(g @ dd), abs(v @ grad))
+    h = 1e-6
+    fd = np.zeros(K)
+    for k in range(K):
+        Ep, Em = E.copy(), E.copy()
+        Ep[k] += h
+        Em[k] -= h
+        fd[k] = (g @ td.forward(phi0, Ep, dt)[0] - g @ td.forward(phi0, Em, dt)[0]) / (2 * h)
+    assert np.max(np.abs(grad - fd)) <= 1e-7 * np.max(np.abs(fd))
