@@ -225,7 +225,7 @@ __host__ __device__ constexpr size_t cell32v_smem(int P, int L4, int n, bool wit
 // caller looping over items synchronises the block between two calls.
 // L4C > 0 fixes the quad count at compile time (no integer division per item);
 // L4C = 0 takes it from L4rt.
-template <int P, bool G, int L4C>
+template <int P, bool G, int L4C, bool PAP = false>
 __device__ __forceinline__ void cell32v_body(const CellArgs32& a, int64_t item, const float4* __restrict__ x,
                                              const float2* __restrict__ U, float4* __restrict__ y, int L4rt,
                                              int n) {
@@ -353,7 +353,7 @@ __device__ __forceinline__ void cell32v_body(const CellArgs32& a, int64_t item, 
             }
         }
         scatter32v(a, s_idx[j], y, L4, q, r);
-        if constexpr (!G) {   // the cell's part of p.Ap: p (gathered, zero on the surface) times A_K p
+        if constexpr (!G && PAP) {   // the cell's part of p.Ap: p (gathered, zero on the surface) times A_K p
             const float4 u = s_u[it];
             pap.x = fmaf(u.x, r.x, pap.x);
             pap.y = fmaf(u.y, r.y, pap.y);
@@ -361,11 +361,11 @@ __device__ __forceinline__ void cell32v_body(const CellArgs32& a, int64_t item, 
             pap.w = fmaf(u.w, r.w, pap.w);
         }
     }
-    if constexpr (!G && L4C > 0 && 32 % L4C == 0) {
+    if constexpr (!G && PAP && L4C > 0 && 32 % L4C == 0) {
         // p.Ap = sum over cells of u_K . A_K u_K (p vanishes on the surface, so
         // the masked scatter drops nothing): lanes with the same quad summed by
         // shuffles, the 8 warps in FP64, one FP64 atomic per column and block
-        if (a.pap_slots) {
+        {
 #pragma unroll
             for (int off = L4C; off < 32; off <<= 1) {
                 pap.x += __shfl_xor_sync(0xffffffffu, pap.x, off);
@@ -390,27 +390,29 @@ __device__ __forceinline__ void cell32v_body(const CellArgs32& a, int64_t item, 
     }
 }
 
-template <int P, bool G, int L4C>
+// PAP: the stiffness pass also forms p.Ap (into a.pap_slots) for the
+// conjugate-gradient sweep.
+template <int P, bool G, int L4C, bool PAP>
 __global__ void __launch_bounds__(256) cell32v_kernel(const __grid_constant__ CellArgs32 a,
                                                       const float4* __restrict__ x, const float2* __restrict__ U,
                                                       float4* __restrict__ y, int L4rt, int n) {
-    cell32v_body<P, G, L4C>(a, blockIdx.x, x, U, y, L4rt, n);
+    cell32v_body<P, G, L4C, PAP>(a, blockIdx.x, x, U, y, L4rt, n);
 }
 
 // Degree 4 (the largest cells): held to 32 registers so that 8 blocks of 256
 // threads share an SM.
-template <bool G, int L4C>
+template <bool G, int L4C, bool PAP>
 __global__ void __launch_bounds__(256, 8) cell32v_kernel_q4(const __grid_constant__ CellArgs32 a,
                                                             const float4* __restrict__ x,
                                                             const float2* __restrict__ U, float4* __restrict__ y,
                                                             int L4rt, int n) {
-    cell32v_body<4, G, L4C>(a, blockIdx.x, x, U, y, L4rt, n);
+    cell32v_body<4, G, L4C, PAP>(a, blockIdx.x, x, U, y, L4rt, n);
 }
 
-template <int P, bool G, int L4C>
+template <int P, bool G, int L4C, bool PAP>
 constexpr auto cell32v_pick() {
-    if constexpr (P == 4) return cell32v_kernel_q4<G, L4C>;
-    else return cell32v_kernel<P, G, L4C>;
+    if constexpr (P == 4) return cell32v_kernel_q4<G, L4C, PAP>;
+    else return cell32v_kernel<P, G, L4C, PAP>;
 }
 
 // Line-ordered form of the four-lane pass: the three 1D contractions run as
@@ -605,6 +607,22 @@ static int launch32(const afem_mesh* m, const CellArgs32& a, const T* x, const f
     return AFEM_OK;
 }
 
+// The four-lane kernel for a quad count (compile-time for 1..4), with the p.Ap
+// epilogue when asked (stiffness, 1, 2 or 4 quads).
+template <int PP, bool G>
+static auto pick32v(int L4, bool pap) {
+    if constexpr (!G) {
+        if (pap)
+            return L4 == 1 ? cell32v_pick<PP, G, 1, true>()
+                           : L4 == 2 ? cell32v_pick<PP, G, 2, true>() : cell32v_pick<PP, G, 4, true>();
+    }
+    return L4 == 1   ? cell32v_pick<PP, G, 1, false>()
+           : L4 == 2 ? cell32v_pick<PP, G, 2, false>()
+           : L4 == 3 ? cell32v_pick<PP, G, 3, false>()
+           : L4 == 4 ? cell32v_pick<PP, G, 4, false>()
+                     : cell32v_pick<PP, G, 0, false>();
+}
+
 // L = float lanes per node (multiple of 4); n = orbitals (G only).
 template <bool G>
 static int launch32v(const afem_mesh* m, const CellArgs32& a, const float* x, const float2* U, float* y, int L,
@@ -649,11 +667,7 @@ static int launch32v(const afem_mesh* m, const CellArgs32& a, const float* x, co
     switch (p) {
 #define AFEM_CASE(PP)                                                                          \
     case PP: {                                                                                 \
-        auto k = L4 == 1   ? cell32v_pick<PP, G, 1>()                                          \
-                 : L4 == 2 ? cell32v_pick<PP, G, 2>()                                          \
-                 : L4 == 3 ? cell32v_pick<PP, G, 3>()                                          \
-                 : L4 == 4 ? cell32v_pick<PP, G, 4>()                                          \
-                           : cell32v_pick<PP, G, 0>();                                         \
+        auto k = pick32v<PP, G>(L4, a.pap_slots != nullptr);                                   \
         if (smem > 48 * 1024)                                                                  \
             AFEM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                                int(smem)));                                    \
