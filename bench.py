@@ -213,11 +213,11 @@ def run_batch(torch, pkg, inputs, reps=10, count=64):
             "one_by_one_fp64_form": {"value": odofs / t_seq64, "ms": t_seq64 * 1e3},
             "speedup_vs_one_by_one_fp32": t_seq32 / t_batch, "speedup_vs_fp64_form": t_seq64 / t_batch,
             "max_rel_diff_vs_single_instance": worst,
-            "tuning": {"schedule": ("instances' own passes on 8 parallel streams" if tun["block"] == 0
+            "tuning": {"schedule": (f"instances' own passes on {tun['grid']} parallel streams" if tun["block"] == 0
                                     else "one persistent launch over all instances' cell groups"),
                        "block": tun["block"], "grid": tun["grid"], "blocks_per_sm": tun["blocks_per_sm"],
                        "candidates_ms": [[b, g, round(t, 4)] for b, g, t in tun["candidates"]],
-                       "candidates_key": "[block, grid, ms]; block 0 = per-instance passes on parallel streams"},
+                       "candidates_key": "[block, grid, ms]; block 0 = per-instance passes on grid parallel streams"},
             "graph": "the chosen schedule (zero, cell pass, M_L^-1 of every instance) captured once, replayed per apply",
             "mesh_build_s": build_s,
             "recipe": "inputs.batch_instances(64): seeded, DoFs log-uniform 5e4..2e6, p in {2,3,4}, "

@@ -422,10 +422,10 @@ int afem_tdse_vjp(afem_mesh* mesh, const double* e_dir, const double* E, int n_s
  * floating-point atomic sums.  Small cells (p <= 3, few quads) are grouped
  * into work items that fill a block.  The first apply of a (kind, n_vec)
  * signature times candidate schedules on the batch itself -- the persistent
- * launch with grids of 1, 2 or all resident blocks per SM at 256 and 128
- * threads or one block per work item, and the instances' own passes on 8
- * parallel streams (reported as block 0, grid = count) -- and keeps the
- * fastest (afem_batch_get_tuning).  With
+ * launch with grids of 2 or all resident blocks per SM at 256 and 128
+ * threads or one block per work item, and the instances' own passes on 4, 8
+ * or 16 parallel streams (reported as block 0, grid = streams) -- and keeps
+ * the fastest (afem_batch_get_tuning).  With
  * AFEM_BATCH_GRAPH the zero, cell and scale passes are captured once into a
  * CUDA graph on a private stream and replayed on `stream`; the per-instance
  * table (pointers, fields) lives in device memory and is re-uploaded when

@@ -25,7 +25,7 @@ int batch32_launch(int kind, const void* d_inst, int count, int64_t total, int b
 using namespace afem;
 
 namespace {
-constexpr int kParStreams = 8;   // streams of the per-instance schedule
+constexpr int kParStreams = 16;   // streams available to the per-instance schedule
 }
 
 struct afem_batch {
@@ -38,7 +38,7 @@ struct afem_batch {
     void* h_inst = nullptr;              // pinned host staging of each upload
     std::vector<unsigned char> last;     // contents of the last upload
     cudaStream_t cap = nullptr;          // private stream for graph capture
-    cudaStream_t par[kParStreams] = {};  // per-instance schedule: instance i runs on par[i % kParStreams]
+    cudaStream_t par[kParStreams] = {};  // per-instance schedule: instance i runs on par[i % streams]
     cudaEvent_t fork = nullptr;
     cudaEvent_t join[kParStreams] = {};
     // arguments of the current apply (the per-instance schedule launches from them)
@@ -64,29 +64,30 @@ void drop_graph(afem_batch* b) {
 }
 
 // The per-instance schedule: each instance's own pass (the kernels of
-// afem_op_apply) on one of kParStreams streams forked from s and joined back,
+// afem_op_apply) on one of `streams` streams forked from s and joined back,
 // so that independent instances run concurrently.  Captured into the graph
 // like the persistent launch (the streams join the capture through the events).
-int launch_per_instance(afem_batch* b, int kind, cudaStream_t s) {
+int launch_per_instance(afem_batch* b, int kind, int streams, cudaStream_t s) {
+    if (streams < 1 || streams > kParStreams) return set_error(AFEM_EINVAL, "afem_batch: bad stream count");
     AFEM_CUDA_TRY(cudaEventRecord(b->fork, s));
-    for (int j = 0; j < kParStreams; ++j) AFEM_CUDA_TRY(cudaStreamWaitEvent(b->par[j], b->fork, 0));
+    for (int j = 0; j < streams; ++j) AFEM_CUDA_TRY(cudaStreamWaitEvent(b->par[j], b->fork, 0));
     const int count = int(b->meshes.size());
     for (int i = 0; i < count; ++i) {
         const double* E = b->cur_E.empty() ? nullptr : b->cur_E.data() + 3 * i;
         int rc = launch_op_apply(b->meshes[i], kind, E, b->cur_x[i], b->cur_y[i], b->cur_n[i],
-                                 b->par[i % kParStreams]);
+                                 b->par[i % streams]);
         if (rc) return rc;
     }
-    for (int j = 0; j < kParStreams; ++j) {
+    for (int j = 0; j < streams; ++j) {
         AFEM_CUDA_TRY(cudaEventRecord(b->join[j], b->par[j]));
         AFEM_CUDA_TRY(cudaStreamWaitEvent(s, b->join[j], 0));
     }
     return AFEM_OK;
 }
 
-// One apply with the chosen schedule (block 0: per instance).
+// One apply with the chosen schedule (block 0: per instance on `grid` streams).
 int launch_schedule(afem_batch* b, int kind, int block, unsigned grid, size_t smem, cudaStream_t s) {
-    if (block == 0) return launch_per_instance(b, kind, s);
+    if (block == 0) return launch_per_instance(b, kind, int(grid), s);
     return batch32_launch(kind, b->d_inst, int(b->meshes.size()), b->total_items, block, grid, smem, s);
 }
 
@@ -117,10 +118,10 @@ int time_shape(afem_batch* b, int kind, int block, unsigned grid, size_t smem, c
     return rc;
 }
 
-// Candidate schedules: the persistent launch with grids of 1, 2 or all
-// resident blocks per SM at 256 and 128 threads, one block per work item, and
-// the per-instance passes on parallel streams (block 0, grid = instances).
-// The fastest is kept.
+// Candidate schedules: the persistent launch with grids of 2 or all resident
+// blocks per SM at 256 and 128 threads and one block per work item, and the
+// per-instance passes on 4, 8 or 16 parallel streams (block 0, grid =
+// streams).  The fastest is kept.
 int tune(afem_batch* b, int kind, cudaStream_t s) {
     b->cand_ms.clear();
     b->cand_block.clear();
@@ -130,7 +131,7 @@ int tune(afem_batch* b, int kind, cudaStream_t s) {
         int per_sm = 0;
         int rc = batch32_occupancy(kind, block, b->smem, &per_sm);
         if (rc) return rc;
-        std::vector<int64_t> grids = {int64_t(b->sms) * per_sm, int64_t(b->sms) * 2, int64_t(b->sms)};
+        std::vector<int64_t> grids = {int64_t(b->sms) * per_sm, int64_t(b->sms) * 2};
         if (block == 256) grids.push_back(b->total_items);
         for (int64_t g : grids) {
             if (g > b->total_items) g = b->total_items;
@@ -149,16 +150,19 @@ int tune(afem_batch* b, int kind, cudaStream_t s) {
             }
         }
     }
-    double ms = 0.0;
-    int rc = time_shape(b, kind, 0, unsigned(b->meshes.size()), 0, s, &ms);
-    if (rc) return rc;
-    b->cand_ms.push_back(ms);
-    b->cand_block.push_back(0);
-    b->cand_grid.push_back(int(b->meshes.size()));
-    if (ms < best) {
-        b->block = 0;
-        b->grid = int(b->meshes.size());
-        b->per_sm = 0;
+    for (int streams : {4, 8, 16}) {
+        double ms = 0.0;
+        int rc = time_shape(b, kind, 0, unsigned(streams), 0, s, &ms);
+        if (rc) return rc;
+        b->cand_ms.push_back(ms);
+        b->cand_block.push_back(0);
+        b->cand_grid.push_back(streams);
+        if (ms < best) {
+            best = ms;
+            b->block = 0;
+            b->grid = streams;
+            b->per_sm = 0;
+        }
     }
     return AFEM_OK;
 }
