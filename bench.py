@@ -103,6 +103,22 @@ def setup_state(pkg, inputs, torch, w):
     return mesh, solver, phi0, C0
 
 
+def max_over_ranks(dist, torch, value, device):
+    """The largest value over the ranks (a job's time is its slowest rank's);
+    the value itself without a process group."""
+    if not dist:
+        return float(value)
+    tt = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_rate(world, ms_per_step):
+    """Whole-job steps/s: each of the `world` ranks advances its own replica by
+    one step in ms_per_step (the max over ranks)."""
+    return world * 1000.0 / ms_per_step
+
+
 def _timed_form(pkg, torch, solver, state0, precision, args, field, dt, dist, stream, profile=False, t0=0.0,
                 warmup=None):
     """Warm up and time K steps of one arithmetic form from a copy of state0
@@ -144,11 +160,7 @@ def _timed_form(pkg, torch, solver, state0, precision, args, field, dt, dist, st
         dist.barrier()
     c1 = ctypes.c_int64(0)
     lib.afem_kernel_launch_count(ctypes.byref(c1))
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if dist:
-        tt = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(dist, torch, ev0.elapsed_time(ev1) / args.steps, "cuda")
     return dict(ms=ms, infos=infos, state=(phi, C, W), t=t, launches=int(c1.value - c0.value), prof=prof)
 
 
@@ -409,7 +421,7 @@ def run_ours(args, rank, world, dist):
     sampler.start()
     mixed = _timed_form(pkg, torch, solver, state0, pkg.PREC_MIXED, args, field, dt, dist, stream)
     clocks = sampler.stop()
-    value = world * 1000.0 / mixed["ms"]
+    value = job_rate(world, mixed["ms"])
     # kernel-class event timing over K further steps continuing each form's
     # timed run (the events cost a few percent, so the headline runs without)
     mixed_prof = _timed_form(pkg, torch, solver, mixed["state"], pkg.PREC_MIXED, args, field, dt, dist, stream,
@@ -485,7 +497,7 @@ def run_ours(args, rank, world, dist):
     mi = mixed["infos"]
     fp64_entry = None
     if fp64 is not None:
-        fp64_entry = {"value": world * 1000.0 / fp64["ms"], "unit": UNIT, "ms_per_step": fp64["ms"],
+        fp64_entry = {"value": job_rate(world, fp64["ms"]), "unit": UNIT, "ms_per_step": fp64["ms"],
                       "cg_iters_mean": float(np.mean([i["cg_iters"] for i in fp64["infos"]])),
                       "gpu_launches": fp64["launches"]}
     return {
