@@ -550,13 +550,17 @@ __device__ void block_expm(const double2* __restrict__ H, int ldh, int m, double
         A[o] = make_double2(dt * h.y, -dt * h.x);   // -i dt h
     }
     __syncthreads();
+    // 1-norm: column sums by m threads (each in row order), then their maximum
+    __shared__ double s_col[kMaxKrylov];
+    if (t < m) {
+        double c = 0.0;
+        for (int i = 0; i < m; ++i) c += hypot(A[t * m + i].x, A[t * m + i].y);
+        s_col[t] = c;
+    }
+    __syncthreads();
     if (t == 0) {
         double nrm = 0.0;
-        for (int j = 0; j < m; ++j) {
-            double c = 0.0;
-            for (int i = 0; i < m; ++i) c += hypot(A[j * m + i].x, A[j * m + i].y);
-            nrm = fmax(nrm, c);
-        }
+        for (int j = 0; j < m; ++j) nrm = fmax(nrm, s_col[j]);
         int sq = 0;
         while (nrm > 0.5 && sq < 60) {
             nrm *= 0.5;
