@@ -144,47 +144,49 @@ __device__ __forceinline__ void block_row_partial(double (&v)[MAXV], int cnt, do
 }
 
 // Projector overlaps of the precision form, S[a][b] = sum_k conj(A[k][a]) B[k][b]
-// over interior rows from complex64 inputs (NO = n orbitals): one thread per
-// row forms all NO^2 products in FP32 registers (each thread covers a few
-// rows); the block sums its threads' values in FP32 over 8 segments of 32
-// threads (through shared memory, transposed), the segment sums in FP64, and
-// the last block sums the blocks in FP64.  S is consumed in FP32 by the
-// projector, and the FP64 work is per block rather than per thread, which
-// leaves the kernel free to run a full wave of blocks.
+// over interior rows from complex64 inputs (NO = n orbitals), added in FP64 into
+// slot (block % kOvSlots) of slots[kOvSlots][2 NO^2] (re, im interleaved; the
+// consumer sums the slots and clears them).  For even NO two threads share a
+// row, each forming the products of half the rows a of S in FP32 registers
+// (fewer registers, more rows in flight); the block sums its threads' values in
+// FP32 over 8 segments of 32 threads (through shared memory, transposed) and
+// the segment sums in FP64.  S is consumed in FP32 by the projector, and the
+// FP64 work is per block, with no last-block pass.
+constexpr int kOvSlots = 16;
 template <int NO>
 __global__ void __launch_bounds__(kRedThreads) overlap32_kernel(const float2* __restrict__ A,
                                                                 const float2* __restrict__ B, int64_t n_rows,
-                                                                double* __restrict__ partial,
-                                                                unsigned* __restrict__ counter,
-                                                                double2* __restrict__ out) {
-    constexpr int CNT = 2 * NO * NO;
-    float f[CNT];
+                                                                double* __restrict__ slots) {
+    constexpr int HS = NO % 2 == 0 ? 2 : 1;   // threads per row
+    constexpr int NA = NO / HS;               // rows a of S per thread
+    constexpr int CNT = 2 * NO * NO;          // values of S
+    constexpr int CT = 2 * NA * NO;           // values per thread
+    const int t = threadIdx.x;
+    const int h = HS == 2 ? (t & 1) : 0;
+    float f[CT];
 #pragma unroll
-    for (int i = 0; i < CNT; ++i) f[i] = 0.f;
+    for (int i = 0; i < CT; ++i) f[i] = 0.f;
+    const int rows_per_block = kRedThreads / HS;
 #pragma unroll 2
-    for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < n_rows;
-         k += int64_t(gridDim.x) * blockDim.x) {
-        float2 a[NO], b[NO];
-        if constexpr (NO % 2 == 0) {   // a row is NO/2 16-byte words
-            const float4* A4 = reinterpret_cast<const float4*>(A + k * NO);
+    for (int64_t k = blockIdx.x * int64_t(rows_per_block) + t / HS; k < n_rows;
+         k += int64_t(gridDim.x) * rows_per_block) {
+        float2 a[NA], b[NO];
+#pragma unroll
+        for (int i = 0; i < NA; ++i) a[i] = A[k * NO + h * NA + i];
+        if constexpr (NO % 2 == 0) {   // a row of B is NO/2 16-byte words
             const float4* B4 = reinterpret_cast<const float4*>(B + k * NO);
 #pragma unroll
             for (int i = 0; i < NO / 2; ++i) {
-                const float4 ua = A4[i], ub = B4[i];
-                a[2 * i] = make_float2(ua.x, ua.y);
-                a[2 * i + 1] = make_float2(ua.z, ua.w);
+                const float4 ub = B4[i];
                 b[2 * i] = make_float2(ub.x, ub.y);
                 b[2 * i + 1] = make_float2(ub.z, ub.w);
             }
         } else {
 #pragma unroll
-            for (int i = 0; i < NO; ++i) {
-                a[i] = A[k * NO + i];
-                b[i] = B[k * NO + i];
-            }
+            for (int i = 0; i < NO; ++i) b[i] = B[k * NO + i];
         }
 #pragma unroll
-        for (int i = 0; i < NO; ++i)
+        for (int i = 0; i < NA; ++i)
 #pragma unroll
             for (int j = 0; j < NO; ++j) {
                 f[2 * (i * NO + j)] = fmaf(a[i].x, b[j].x, fmaf(a[i].y, b[j].y, f[2 * (i * NO + j)]));
@@ -194,12 +196,23 @@ __global__ void __launch_bounds__(kRedThreads) overlap32_kernel(const float2* __
     static_assert(kRedThreads == 256, "the segment sums assume 8 warps of 32");
     __shared__ float s_t[32][kRedThreads + 1];   // a chunk of 32 values x 256 threads
     __shared__ float s_seg[8][32];
-    const int t = threadIdx.x, lane = t & 31, seg = t >> 5;
+    const int lane = t & 31, seg = t >> 5;
+    double* slot = slots + int64_t(blockIdx.x % kOvSlots) * CNT;
 #pragma unroll
     for (int c0 = 0; c0 < CNT; c0 += 32) {
+        // value c0 + j of S is this thread's f[c0 + j - h CT] when that index is its own
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-            if (c0 + j < CNT) s_t[j][t] = f[c0 + j];
+        for (int j = 0; j < 32; ++j) {
+            if (c0 + j < CNT) {
+                float v = 0.f;
+                if (h == 0) {
+                    if (c0 + j < CT) v = f[c0 + j < CT ? c0 + j : 0];
+                } else {
+                    if (c0 + j >= CT) v = f[c0 + j >= CT ? c0 + j - CT : 0];
+                }
+                s_t[j][t] = v;
+            }
+        }
         __syncthreads();
         if (c0 + lane < CNT) {   // value c0 + lane over the 32 threads of segment seg
             float x = 0.f;
@@ -212,13 +225,10 @@ __global__ void __launch_bounds__(kRedThreads) overlap32_kernel(const float2* __
             double x = 0.0;
 #pragma unroll
             for (int g = 0; g < 8; ++g) x += widen_f32(s_seg[g][t]);
-            partial[int64_t(blockIdx.x) * CNT + c0 + t] = x;
+            atomicAdd(slot + c0 + t, x);
         }
         __syncthreads();
     }
-    __shared__ double s_sum[kRedThreads];
-    if (!last_block_sum(partial, CNT, counter, s_sum)) return;
-    for (int o = threadIdx.x; o < NO * NO; o += blockDim.x) out[o] = make_double2(s_sum[2 * o], s_sum[2 * o + 1]);
 }
 
 // acc[2i], acc[2i+1] += conj(u_i) mx (i < NV) and acc[2NV] += conj(x) mx, with
@@ -264,13 +274,14 @@ __device__ __forceinline__ void krylov_scales(const double2* __restrict__ H, int
 // |w|^2 itself).  By Pythagoras the norm before the update is this plus the
 // norm the update leaves, which is how the re-orthogonalisation test uses it.
 template <int NV>
-__device__ __forceinline__ void finish_dots(double (&acc)[2 * NV + 1], const double* s_f,
+// Returns true in the last block (after every block has finished its reads).
+__device__ __forceinline__ bool finish_dots(double (&acc)[2 * NV + 1], const double* s_f,
                                             double* __restrict__ partial, unsigned* __restrict__ counter,
                                             double2* __restrict__ out) {
     constexpr int CNT = NV > 0 ? 2 * NV : 1;
     block_row_partial<2 * NV + 1>(acc, CNT, partial);
     __shared__ double s_sum[kRedThreads];
-    if (!last_block_sum(partial, CNT, counter, s_sum)) return;
+    if (!last_block_sum(partial, CNT, counter, s_sum)) return false;
     const double fw = NV > 0 ? s_f[NV > 0 ? NV - 1 : 0] : 1.0;
     for (int i = threadIdx.x; i < NV; i += blockDim.x) {
         const double f = s_f[i] * fw;
@@ -288,6 +299,7 @@ __device__ __forceinline__ void finish_dots(double (&acc)[2 * NV + 1], const dou
         }
         out[NV] = make_double2(nn, 0.0);
     }
+    return true;
 }
 
 // Gram-Schmidt inner products: out[i] = <q_i, w>_M for i < NV and out[NV] as
@@ -378,10 +390,23 @@ __global__ void __launch_bounds__(kRedThreads) project32_dots_kernel(
     const float* __restrict__ ml_inv, const double* __restrict__ ml, int64_t n_int, int64_t N, int n,
     double2* __restrict__ w, const double2* __restrict__ V, int64_t stride, const double2* __restrict__ H, int ldh,
     const double2* __restrict__ beta2, double* __restrict__ partial, unsigned* __restrict__ counter,
-    double2* __restrict__ out) {
+    double2* __restrict__ out, double* __restrict__ S_slots) {
     __shared__ float2 s_S[kMaxOrbProj * kMaxOrbProj];
     __shared__ double s_f[NV];
-    for (int i = threadIdx.x; i < n * n; i += blockDim.x) s_S[i] = make_float2(float(S[i].x), float(S[i].y));
+    // the overlaps: the sum of overlap32_kernel's slots (cleared by the last
+    // block below), or S itself (zero without the projector)
+    for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
+        if (S_slots) {
+            double x = 0.0, y = 0.0;
+            for (int sl = 0; sl < kOvSlots; ++sl) {
+                x += S_slots[sl * 2 * n * n + 2 * i];
+                y += S_slots[sl * 2 * n * n + 2 * i + 1];
+            }
+            s_S[i] = make_float2(narrow_f64(x), narrow_f64(y));
+        } else {
+            s_S[i] = make_float2(narrow_f64(S[i].x), narrow_f64(S[i].y));
+        }
+    }
     krylov_scales(H, ldh, beta2, NV, s_f);
     __syncthreads();
     double acc[2 * NV + 1];
@@ -412,7 +437,8 @@ __global__ void __launch_bounds__(kRedThreads) project32_dots_kernel(
             w[o] = x;
         }
     }
-    finish_dots<NV>(acc, s_f, partial, counter, out);
+    if (finish_dots<NV>(acc, s_f, partial, counter, out) && S_slots)
+        for (int o = threadIdx.x; o < kOvSlots * 2 * n * n; o += blockDim.x) S_slots[o] = 0.0;
 }
 
 // Gram-Schmidt update of the raw vector w (the true vector is fw w with
@@ -747,14 +773,15 @@ static int launch_krylov_dots(int nv, unsigned grid, cudaStream_t s, const doubl
 static int launch_project_dots(int nv, unsigned grid, cudaStream_t s, const float2* z32, const float2* phi32,
                                const double2* z, const double2* phi, const double2* S, const DeviceMesh& D, int n,
                                double2* w, const double2* V, int64_t stride, const double2* H, int ldh,
-                               const double2* beta2, double* partial, unsigned* counter, double2* out) {
+                               const double2* beta2, double* partial, unsigned* counter, double2* out,
+                               double* S_slots) {
     switch (nv) {
 #define AFEM_PD_CASE(NVV)                                                                                           \
     case NVV:                                                                                                       \
         if (z32) {                                                                                                  \
             AFEM_LAUNCH((project32_dots_kernel<NVV>), wave_grid<project32_dots_kernel<NVV>>(grid), kRedThreads, 0, \
                         s, z32, phi32, S, D.ml_inv32, D.ml,                                                         \
-                        D.n_interior, D.n_master, n, w, V, stride, H, ldh, beta2, partial, counter, out);           \
+                        D.n_interior, D.n_master, n, w, V, stride, H, ldh, beta2, partial, counter, out, S_slots);  \
         } else {                                                                                                    \
             AFEM_LAUNCH((project_dots_kernel<NVV>), wave_grid<project_dots_kernel<NVV>>(grid), kRedThreads, 0, s, \
                         z, phi, S, D.ml_inv, D.ml,                                                                  \
@@ -843,7 +870,7 @@ static int g_cell_overlaps32(afem_mesh* m, const double* E, const float2* phi32,
 #define AFEM_OV_CASE(NO)                                                                                        \
     case NO:                                                                                                    \
         AFEM_LAUNCH((overlap32_kernel<NO>), kRedBlocks, kRedThreads, 0, s, phi32, w.z32, D.n_interior,         \
-                    part, w.counters, w.S);                                                                     \
+                    w.Sslots);                                                                                  \
         break;
         AFEM_OV_CASE(1)
         AFEM_OV_CASE(2)
@@ -881,6 +908,7 @@ int arnoldi_reserve(afem_mesh* m, int n, int mk, ArnoldiWork& w) {
         w.z = cv.take<double2>(NV);
         w.cpartial = cv.take<double2>(size_t(kRedBlocks) * 256);
         w.S = cv.take<double2>(kMaxOrbProj * kMaxOrbProj);
+        w.Sslots = cv.take<double>(size_t(kOvSlots) * 2 * kMaxOrbProj * kMaxOrbProj);
         w.res = cv.take<double2>(kResSize);
         w.c1 = cv.take<double2>(kMaxKrylov + 1);
         w.c2 = cv.take<double2>(kMaxKrylov + 1);
@@ -949,6 +977,7 @@ int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double
     }
     AFEM_CUDA_TRY(cudaMemsetAsync(w.counters, 0, 4 * sizeof(unsigned), s));
     AFEM_CUDA_TRY(cudaMemsetAsync(w.flag, 0, 4 * sizeof(int), s));
+    AFEM_CUDA_TRY(cudaMemsetAsync(w.Sslots, 0, sizeof(double) * kOvSlots * 2 * kMaxOrbProj * kMaxOrbProj, s));
     const int ldh = kMaxKrylov + 1;
     const unsigned gdots = rowcol_grid(D.n_interior, n);
     const unsigned gproj = rowcol_grid(D.n_master, n);
@@ -997,7 +1026,8 @@ int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double
             {
                 ProfScope ps(AFEM_PROF_GS, s, gs_flops);
                 rc = launch_project_dots(j + 1, gproj, s, mixed ? w.z32 : nullptr, w.phi32, w.z, phi, w.S, D, n, Wn,
-                                         w.V, NV, w.H, ldh, w.beta2, part, cnt, w.c1);
+                                         w.V, NV, w.H, ldh, w.beta2, part, cnt, w.c1,
+                                         (mixed && projector) ? w.Sslots : nullptr);
             }
             if (!rc) {
                 ProfScope ps(AFEM_PROF_GS, s, gs_flops + double(D.n_interior) * n * 4.0);

@@ -25,6 +25,7 @@ struct ArnoldiWork {
     double2* z;          // [N][n] cell-pass output
     double2* cpartial;   // reduction partials
     double2* S;          // [n][n] projector overlaps
+    double* Sslots;      // [16][2 n^2] FP64 slots of the precision form's overlaps (summed by the projector)
     double2* res;        // kResSize small results (below)
     double2* H;          // (kMaxKrylov+1) x kMaxKrylov Hessenberg, column-major (in res)
     double2* beta2;      // <phi, phi>_M of the substep's start vector (in res)
