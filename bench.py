@@ -236,7 +236,7 @@ def run_batch(torch, pkg, inputs, reps=10, count=64):
                       "1-3 nuclei Z 1..8 within 3 bohr, 2-8 orbitals (even), |E| 0.01..0.08"}
 
 
-def run_diff(torch, pkg, inputs, mesh, phi_col, steps=10, every=5, krylov_tol=1e-10):
+def run_diff(torch, pkg, inputs, mesh, phi_col, steps=6, every=3, krylov_tol=1e-10):
     """Differentiation form on the full mesh (one-electron limit: one orbital,
     no projector or mean field): the forward pass with checkpoints, the
     adjoint sweep that gives dJ/dE_k for every step, and the tangent map, each
