@@ -350,9 +350,9 @@ def run_precision_spectrum(torch, pkg, inputs, steps=300):
 # Kernel classes of the library's event timing: name, bound, unit of work.
 PROF_CLASSES = {
     0: ("Gram-Schmidt passes (krylov_update / project*_dots, FP64)", "alu", "flops"),
-    1: ("complex64 G cell pass (cell32v_kernel<p,true>)", "hbm", "bytes"),
-    2: ("float32 stiffness of the CG sweeps (cell32v_kernel<p,false>)", "hbm", "bytes"),
-    3: ("float32 CG vector kernels (dot_alpha4 / update_beta4 / p_update4)", "hbm", "bytes"),
+    1: ("complex64 G cell pass (cell32v_kernel_q4<true,L4,false>)", "hbm", "bytes"),
+    2: ("float32 stiffness of the CG sweeps with the p.Ap epilogue (cell32v_kernel_q4<false,L4,true>)", "hbm", "bytes"),
+    3: ("float32 CG vector kernels (update_beta4 / p_update4; p.Ap in the stiffness pass)", "hbm", "bytes"),
     4: ("FP64 cell passes (g_cell_kernel / cell_op_kernel)", "alu", "flops"),
 }
 # DRAM bytes per bracketed call from one ncu capture of the same kernels on
