@@ -359,7 +359,7 @@ PROF_CLASSES = {
 # the same workload (dram__bytes_read.sum + dram__bytes_write.sum, summed over
 # a class's launches of one Krylov substep / CG iteration and divided by the
 # calls); None where no capture of the current kernel exists.
-TRAFFIC_PER_CALL = {0: 353.8e6, 1: 179.0e6, 2: 114.9e6, 3: 341.8e6, 4: None}
+TRAFFIC_PER_CALL = {0: 353.8e6, 1: 182.6e6, 2: 114.9e6, 3: 341.8e6, 4: None}
 
 
 def _class_rooflines(prof, total_ms, fp64_peak, hbm, peak_src):

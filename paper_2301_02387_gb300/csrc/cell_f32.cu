@@ -190,6 +190,17 @@ __device__ __forceinline__ void scatter32v(const CellArgs32& a, int idx, float4*
     }
 }
 
+// 16-byte global -> shared copy that does not pass through registers
+// (LDGSTS): a thread issues all of its copies back to back and waits once, so
+// the gather of a cell's node rows keeps several loads in flight per thread.
+// Both addresses are 16-byte aligned (float4 rows).
+__device__ __forceinline__ void cp_async16(float4* smem_dst, const float4* gmem_src) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // Slots of the fused p.Ap sums (spread over slots to keep the FP64 atomics of
 // the cell blocks off a single address per column).
 constexpr int kPapSlots = 64;
@@ -273,10 +284,15 @@ __device__ __forceinline__ void cell32v_body(const CellArgs32& a, int64_t item, 
     if (tid < P1 * P1) s_K[tid] = a.K[tid];
     if (tid < P1) s_w[tid] = a.w[tid];
     __syncthreads();
-    // j = cell slot * NN + node
+    // j = cell slot * NN + node.  In the G pass the rows of masters are copied
+    // asynchronously, hanging points (weighted sums) and masked surface masters
+    // (zero) go through registers; the stiffness pass (fewer rows per thread,
+    // and its p.Ap epilogue at the 32-register limit) loads all in registers
     for (int it = tid; it < nc * NN * L4; it += bs) {
         const int j = it / L4, q = it - j * L4;
-        s_u[it] = gather32v(a, s_idx[j], x, L4, q);
+        const int idx = s_idx[j];
+        if (G && idx >= 0 && !(a.masked && idx >= a.n_interior)) cp_async16(s_u + it, x + int64_t(idx) * L4 + q);
+        else s_u[it] = gather32v(a, idx, x, L4, q);
     }
     if (G) {
         if (U) {
@@ -287,7 +303,9 @@ __device__ __forceinline__ void cell32v_body(const CellArgs32& a, int64_t item, 
             const float4* U4 = reinterpret_cast<const float4*>(U);
             for (int it = tid; it < nc * NN * h2; it += bs) {
                 const int j = it / h2, c = it - j * h2;
-                s_U4[j * SU + c] = gather32v(au, s_idx[j], U4, h2, c);
+                const int idx = s_idx[j];
+                if (idx >= 0) cp_async16(s_U4 + j * SU + c, U4 + int64_t(idx) * h2 + c);
+                else s_U4[j * SU + c] = gather32v(au, idx, U4, h2, c);
             }
         }
         const float* vc = a.v_cell + cell0 * NN;
@@ -301,6 +319,7 @@ __device__ __forceinline__ void cell32v_body(const CellArgs32& a, int64_t item, 
             s_pot[j] = wq * (vc[j] + a.E[0] * px + a.E[1] * py + a.E[2] * pz);
         }
     }
+    if constexpr (G) cp_async_wait_all();
     __syncthreads();
     float4 pap = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int it = tid; it < nc * NN * L4; it += bs) {
