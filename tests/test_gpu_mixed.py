@@ -92,3 +92,46 @@ def test_mixed_mctdhf_steps_within_1e6(pair):
     ng = np.real(np.sum(np.conj(pg) * ML[:, None] * pg, axis=0))
     no = np.real(np.sum(np.conj(phi_o) * ML[:, None] * phi_o, axis=0))
     np.testing.assert_allclose(ng, no, rtol=1e-6)
+
+
+CASES_N = [
+    CASE,
+    (-8.0, 8.0, 3, 4, [((0.0, 0.0, 0.7), 1.0, 2), ((0.0, 0.0, -0.7), 1.0, 2)], 2.0),
+]
+
+
+@pytest.mark.parametrize("case", CASES_N)
+@pytest.mark.parametrize("n", [1, 3, 4, 6, 8])
+def test_arnoldi_orbital_counts_with_mean_field(case, n):
+    """The G cell pass with all n^2 mean fields for odd orbital counts (the
+    scalar-lane kernel) and 2, 3 and 4 float4 quads per node (n = 4, 6, 8; 8
+    orbitals and 64 fields as in the water workload), degrees 3 and 4: one
+    Krylov step of dimension 8, FP64 within 1e-10 of the oracle, the precision
+    form within 1e-6."""
+    import torch
+    import paper_2301_02387_gb300 as pkg
+    gm = pkg.Mesh(*case)
+    om = omesh.Mesh(*case)
+    op = fem.Operators(om)
+    X, _, _ = gm.tables()
+    perm = coord_permutation(X, om.Xm)
+    interior = ~om.boundary
+    phi_o = inputs.lowdin(inputs.molecular_orbitals(om.Xm, interior, case[4], n), op.ML)
+    rng = np.random.default_rng(40 + n)
+    U_o = np.zeros((n, n, om.N), dtype=np.complex128)
+    for p in range(n):
+        for q in range(n):
+            c = rng.standard_normal(3)
+            U_o[p, q] = (0.3 + 0.2j * rng.standard_normal()) * np.exp(-0.2 * np.sum((om.Xm - c) ** 2, axis=1))
+    E = (0.01, -0.02, 0.03)
+    sim = mctdhf.MCTDHF.__new__(mctdhf.MCTDHF)
+    sim.ops, sim.mesh, sim.n = op, om, n
+    sim.interior = interior.astype(np.float64)
+    ref, *_ = krylov.arnoldi_expm(lambda v: sim.G_apply(v, phi_o, U_o, E), phi_o, sim.inner, 8, 0.01)
+    phi = torch.from_numpy(np.ascontiguousarray(phi_o[perm])).cuda()
+    U = torch.from_numpy(np.ascontiguousarray(U_o.transpose(2, 0, 1)[perm])).cuda()
+    for prec, bar in ((pkg.PREC_FP64, 1e-10), (pkg.PREC_MIXED, 1e-6)):
+        out, err, mu, brk = pkg.arnoldi_step(gm, phi, U, 8, 0.01, E=E, precision=prec)
+        torch.cuda.synchronize()
+        rel = np.linalg.norm(out.cpu().numpy() - ref[perm]) / np.linalg.norm(ref)
+        assert rel < bar, (prec, rel)
