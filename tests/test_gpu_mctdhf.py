@@ -11,10 +11,15 @@ from tests._match import coord_permutation
 
 pytestmark = pytest.mark.gpu
 
+WATER_SMALL = (-6.0, 6.0, 2, 3, [((0.0, 0.0, 0.0), 8.0, 1), ((1.4311, 1.1081, 0.0), 1.0, 1),
+                                  ((-1.4311, 1.1081, 0.0), 1.0, 1)], 2.0)
+
 CASES = [
     # (mesh, n_orb, n_alpha, n_beta)
     ((-6.0, 6.0, 3, 2, [((0.0, 0.0, 0.7), 1.0, 2), ((0.0, 0.0, -0.7), 1.0, 2)], 2.0), 2, 1, 1),
     ((-6.0, 6.0, 2, 3, [((0.0, 0.0, 0.0), 3.0, 2), ((1.2, 0.9, 0.0), 1.0, 1)], 2.0), 3, 2, 1),
+    # water-shaped: O + 2 H, 8 orbitals (64 mean fields, 64 Poisson columns), 1 alpha + 1 beta
+    (WATER_SMALL, 8, 1, 1),
 ]
 
 

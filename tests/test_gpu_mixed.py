@@ -135,3 +135,54 @@ def test_arnoldi_orbital_counts_with_mean_field(case, n):
         torch.cuda.synchronize()
         rel = np.linalg.norm(out.cpu().numpy() - ref[perm]) / np.linalg.norm(ref)
         assert rel < bar, (prec, rel)
+
+
+@pytest.mark.parametrize("n", [4, 6, 8])
+def test_mixed_poisson_column_counts(pair, n):
+    """The precision form's Poisson batch for 16 columns (fused p.Ap), 36 and 64
+    columns (9 and 16 float4 quads per node: the run-time quad count): FP64
+    backward error <= 2e-10 in the oracle's matrices."""
+    import torch
+    import paper_2301_02387_gb300 as pkg
+    gm, om, op, perm = pair
+    phi_o = inputs.lowdin(inputs.molecular_orbitals(om.Xm, ~om.boundary, CASE[4], n), op.ML)
+    ps = poisson.PoissonSolver(op)
+    rho, _ = poisson.pair_densities(op, phi_o)
+    phi = torch.from_numpy(np.ascontiguousarray(phi_o[perm])).cuda()
+    W = torch.zeros((gm.N, n * n), dtype=torch.float64, device="cuda")
+    it, rel, rc = pkg.poisson_batch(gm, phi, W, rtol=1e-10, max_it=20000, precision=pkg.PREC_MIXED)
+    assert rc == 0 and np.all(rel <= 1e-10)
+    Wg = np.empty((om.N, n * n))
+    Wg[perm] = W.cpu().numpy()
+    assert np.all(ps.residual(Wg, rho) < 2e-10)
+
+
+def test_mixed_mctdhf_water_shaped_within_1e6():
+    """Precision form of the MCTDHF step with 8 orbitals (1 alpha + 1 beta) on
+    a small O + 2 H mesh: within 1e-6 of the oracle over 2 steps."""
+    import torch
+    import paper_2301_02387_gb300 as pkg
+    case = (-6.0, 6.0, 2, 3, [((0.0, 0.0, 0.0), 8.0, 1), ((1.4311, 1.1081, 0.0), 1.0, 1),
+                              ((-1.4311, 1.1081, 0.0), 1.0, 1)], 2.0)
+    gm = pkg.Mesh(*case)
+    om = omesh.Mesh(*case)
+    op = fem.Operators(om)
+    X, _, _ = gm.tables()
+    perm = coord_permutation(X, om.Xm)
+    n, na, nb = 8, 1, 1
+    phi_o = inputs.lowdin(inputs.molecular_orbitals(om.Xm, ~om.boundary, case[4], n), op.ML)
+    C_o = inputs.initial_ci(n, na, nb, amp=0.1)
+    sim = mctdhf.MCTDHF(op, n, na, nb, poisson_method="cg", poisson_rtol=1e-13)
+    solver = pkg.MCTDHF(gm, n, na, nb, 8)
+    solver.set_precision(pkg.PREC_MIXED)
+    phi = torch.from_numpy(np.ascontiguousarray(phi_o[perm])).cuda()
+    C = torch.from_numpy(C_o.copy()).cuda()
+    W = torch.zeros((gm.N, n * n), dtype=torch.float64, device="cuda")
+    E = (0.0, 0.01, 0.03)
+    for _ in range(2):
+        phi_o, C_o, info_o = sim.step(phi_o, C_o, E, 0.02, 8)
+        info = solver.step(phi, C, W, E, 0.02, cg_rtol=1e-12)
+    torch.cuda.synchronize()
+    assert np.linalg.norm(phi.cpu().numpy() - phi_o[perm]) / np.linalg.norm(phi_o) < 1e-6
+    assert np.linalg.norm(C.cpu().numpy() - C_o) / np.linalg.norm(C_o) < 1e-6
+    assert abs(info["energy"] - info_o["energy"]) < 1e-6 * abs(info_o["energy"])

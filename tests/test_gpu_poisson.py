@@ -14,6 +14,8 @@ CASES = [
     ((-10.0, 10.0, 4, 2, [((0.0, 0.0, 0.0), 1.0, 3)], 2.0), 1),
     ((-8.0, 8.0, 3, 3, [((0.0, 0.0, 0.7), 1.0, 2), ((0.0, 0.0, -0.7), 1.0, 2)], 2.0), 3),
     ((-8.0, 8.0, 3, 4, [((0.3, -0.45, 0.7), 1.0, 2), ((-1.1, 0.2, -0.35), 2.0, 2)], 1.5), 2),
+    # 8 orbitals: 64 columns (the water workload's batch), degree 4 (shared tiles above 48 KB)
+    ((-8.0, 8.0, 3, 4, [((0.3, -0.45, 0.7), 1.0, 2), ((-1.1, 0.2, -0.35), 2.0, 2)], 1.5), 8),
 ]
 
 
