@@ -16,6 +16,8 @@ Modules and the parts of the paper they follow:
                  ("bridged" function) constraints (Sec. 3.1).
 * ``fem``      - assembled stiffness, lumped mass, pointwise potentials and the
                  one-body Hamiltonian matrix (Sec. 3.1, Eq. discretized_eom).
+* ``rows``     - selected rows of the same operators formed cell by cell, for
+                 meshes too large to assemble on the host (Sec. 3.1).
 * ``poisson``  - pair-density right-hand sides, multipole Dirichlet data and
                  the Poisson solve for the mean fields (Sec. 3.1, Eq. mean-field).
 * ``krylov``   - short-iterative Arnoldi propagator (Sec. 3.2).
