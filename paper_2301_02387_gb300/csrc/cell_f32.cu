@@ -191,9 +191,9 @@ __device__ __forceinline__ void scatter32v(const CellArgs32& a, int idx, float4*
 }
 
 // 16-byte global -> shared copy that does not pass through registers
-// (LDGSTS): a thread issues all of its copies back to back and waits once, so
-// the gather of a cell's node rows keeps several loads in flight per thread.
-// Both addresses are 16-byte aligned (float4 rows).
+// (cp.async): a thread issues all of its copies back to back and waits once,
+// so the gather of a cell's node rows keeps several loads in flight per
+// thread.  Both addresses are 16-byte aligned (float4 rows).
 __device__ __forceinline__ void cp_async16(float4* smem_dst, const float4* gmem_src) {
     const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
