@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY.  This package is a plain, slow, obviously-correct
 restatement of what the GPU library computes, built from assembled sparse
-matrices in float64 / complex128.  Only ``tests/``, ``__graft_entry__.smoke()``
+matrices in float64 / complex128 (dense PyTorch CPU maps in ``step_grad``).  Only ``tests/``, ``__graft_entry__.smoke()``
 and the CPU-baseline leg of ``bench.py`` may import it.  The CUDA library never
 imports, links or calls anything here, and nothing here imports the CUDA
 library: the two share no code, tables or constants.
@@ -25,6 +25,12 @@ Modules and the parts of the paper they follow:
                  (Sec. 2, Eqs. ci_eom and the RDM definitions).
 * ``mctdhf``   - the packed orbital operator G and one MCTDHF time step
                  (Sec. 3.2, Eq. packed_orb_eom).
+* ``adjoint``  - dense one-electron step, its tangent and adjoint (the
+                 differentiation form in the one-electron limit; Sec. 3.2).
+* ``step_grad`` - the full MCTDHF step as dense PyTorch maps on tiny meshes and
+                 the gradient of a dipole functional with respect to the field by
+                 automatic differentiation (the differentiation form beyond the
+                 one-electron limit; Sec. 2, Sec. 3.2).
 * ``pulse``    - laser pulse shapes (Sec. 4 and the sin^2 workload pulses).
 
 Every function that has no independent pin says "parity unpinned" in its
