@@ -2,8 +2,9 @@
 
 TEST INFRASTRUCTURE ONLY.  This package is a plain, slow, obviously-correct
 restatement of what the GPU library computes, built from assembled sparse
-matrices in float64 / complex128 (dense PyTorch CPU maps in ``step_grad``).  Only ``tests/``, ``__graft_entry__.smoke()``
-and the CPU-baseline leg of ``bench.py`` may import it.  The CUDA library never
+matrices in float64 / complex128 (dense PyTorch CPU maps in ``step_grad``).
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import it.  The CUDA library never
 imports, links or calls anything here, and nothing here imports the CUDA
 library: the two share no code, tables or constants.
 
