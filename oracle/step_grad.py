@@ -22,7 +22,9 @@ PyTorch (CPU, complex128), so that torch.autograd forms dJ/dE_k:
 
 with the field E e frozen over each step at its left point.  The orbital step
 is the exact exponential of G (the library's Krylov step reaches it within its
-error estimate).  J = sum_k g_k d_k over the signal at t_0 .. t_K.
+error estimate).  J = sum_k g_k d_k over the signal at t_0 .. t_K; the
+gradient dJ/dE is formed by reverse-mode differentiation, the tangent
+dd = (dd_k/dE) v along a field perturbation v by its forward counterpart.
 
 Test infrastructure only (see the package docstring).
 """
@@ -138,3 +140,11 @@ class DenseMCTDHF:
         J = torch.sum(torch.from_numpy(np.asarray(g, dtype=np.float64)) * d)
         J.backward()
         return float(J.detach()), Et.grad.numpy().copy()
+
+    def tangent(self, phi0, c0, E, dt, v):
+        """(d [K+1], dd [K+1]): the signal and its derivative along the field
+        perturbation v [K] (numpy in, numpy out)."""
+        Et = torch.tensor(np.asarray(E, dtype=np.float64))
+        vt = torch.tensor(np.asarray(v, dtype=np.float64))
+        d, dd = torch.autograd.functional.jvp(lambda x: self.signals(phi0, c0, x, dt), Et, vt)
+        return d.detach().numpy().copy(), dd.detach().numpy().copy()

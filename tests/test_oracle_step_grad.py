@@ -69,3 +69,24 @@ def test_gradient_matches_central_differences(system):
     scale = np.abs(c1).max()
     assert np.abs(grad - c1).max() <= 1e-6 * scale
     assert np.abs(grad - (4.0 * c1 - c2) / 3.0).max() <= 1e-6 * scale
+
+
+def test_tangent_dot_product_and_differences(system):
+    """The tangent map against the gradient (<g, J v> = <J^T g, v> to 1e-10)
+    and against central differences along v (1e-6)."""
+    sim, dm, phi, C = system
+    K, dt = 2, 0.01
+    rng = np.random.default_rng(9)
+    E = 0.02 * rng.standard_normal(K)
+    g = rng.standard_normal(K + 1)
+    v = rng.standard_normal(K)
+    p0, c0 = dm.restrict(phi), torch.from_numpy(C)
+    d, dd = dm.tangent(p0, c0, E, dt, v)
+    _, grad = dm.gradient(p0, c0, E, dt, g)
+    assert dd[0] == 0.0
+    assert abs(g @ dd - v @ grad) <= 1e-10 * max(abs(g @ dd), abs(v @ grad))
+    with torch.no_grad():
+        sp = dm.signals(p0, c0, torch.from_numpy(E + 1e-3 * v), dt).numpy()
+        sm = dm.signals(p0, c0, torch.from_numpy(E - 1e-3 * v), dt).numpy()
+    np.testing.assert_allclose(d, dm.signals(p0, c0, torch.from_numpy(E), dt).detach().numpy(), rtol=0, atol=1e-14)
+    assert np.abs(dd - (sp - sm) / 2e-3).max() <= 1e-6 * np.abs(dd).max()
