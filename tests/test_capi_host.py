@@ -65,6 +65,28 @@ def test_host_mesh_matches_oracle(case):
     np.testing.assert_allclose(ml, op.ML[perm], rtol=1e-12)
 
 
+def test_host_mesh_matches_oracle_benchmark_size():
+    """The host mesh builder on the H2 Q4 benchmark mesh itself (12,144 cells,
+    775,009 masters, 55,200 hanging points): the same leaves, counts, numbering
+    and lumped mass as the oracle (whose lumped mass comes from its row-wise
+    operators, without global assembly)."""
+    from paper_2301_02387_gb300 import Mesh, inputs
+    from oracle import rows
+    args = inputs.mesh_args("h2_q4")
+    lib_mesh = Mesh(*args, host_only=True)
+    om = omesh.Mesh(*args)
+    X, ml, cells = lib_mesh.tables()
+    assert (lib_mesh.N, lib_mesh.n_hanging, len(cells)) == (775009, 55200, 12144)
+    assert sorted(map(tuple, cells.tolist())) == [tuple(t) for t in om.leaf_tuples()]
+    assert lib_mesh.N == om.N and lib_mesh.n_hanging == om.n_hanging
+    assert lib_mesh.n_interior == int((~om.boundary).sum())
+    assert lib_mesh.n_constraint_entries == om.C.nnz - om.N
+    perm = coord_permutation(X, om.Xm)
+    assert not om.boundary[perm[:lib_mesh.n_interior]].any()
+    assert om.boundary[perm[lib_mesh.n_interior:]].all()
+    np.testing.assert_allclose(ml, rows.RowOperators(om).ML[perm], rtol=1e-12)
+
+
 def test_bad_descriptions_are_rejected():
     from paper_2301_02387_gb300 import Mesh, AfemError
     with pytest.raises(AfemError):
