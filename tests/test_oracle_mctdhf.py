@@ -31,6 +31,50 @@ def test_arnoldi_full_dimension_is_exact_dense_expm():
     assert np.linalg.norm(out - ref) < 1e-11 * np.linalg.norm(ref)
 
 
+def _krylov_case(seed=5, n=40):
+    rng = np.random.default_rng(seed)
+    G = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    G /= np.linalg.norm(G, 2)
+    w = rng.random(n) + 0.5
+    phi = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    return G, w, phi, (lambda u, v: np.sum(np.conj(u) * w * v))
+
+
+@pytest.mark.parametrize("m", [6, 8])
+def test_arnoldi_step_is_the_galerkin_projection_on_the_krylov_space(m):
+    """Below full dimension the step equals its definition, formed without
+    Gram-Schmidt: Q exp(-i dt Q^H W G Q) Q^H W phi with Q a W-orthonormal basis
+    of span{phi, G phi, .., G^(m-1) phi} (QR of the weighted Krylov matrix).  At
+    full dimension any coefficients satisfy the Arnoldi relation, so only this
+    pins the orthogonalisation itself."""
+    G, w, phi, inner = _krylov_case()
+    dt = 0.7
+    out, *_ = krylov.arnoldi_expm(lambda v: G @ v, phi, inner, m, dt)
+    K = np.stack([np.linalg.matrix_power(G, k) @ phi for k in range(m)], axis=1)
+    sw = np.sqrt(w)
+    Qt, _ = np.linalg.qr(sw[:, None] * K)
+    Q = Qt / sw[:, None]
+    Hq = Q.conj().T @ (w[:, None] * (G @ Q))
+    ref = Q @ (scipy.linalg.expm(-1j * dt * Hq) @ (Q.conj().T @ (w * phi)))
+    assert np.linalg.norm(out - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_arnoldi_basis_is_orthonormal_with_projected_hessenberg():
+    """The basis of the substep propagation: <v_i, v_j> = delta_ij and
+    h_ij = <v_i, G v_j> (the Galerkin projection), v_1 = phi / beta."""
+    G, w, phi, inner = _krylov_case(seed=6)
+    m = 8
+    beta, V, H, mu, brk, hlast = krylov.arnoldi_basis(lambda v: G @ v, phi, inner, m)
+    assert mu == m and not brk
+    assert abs(beta - math.sqrt(inner(phi, phi).real)) < 1e-14 * beta
+    np.testing.assert_allclose(V[0], phi / beta, rtol=0, atol=1e-15)
+    gram = np.array([[inner(V[i], V[j]) for j in range(m + 1)] for i in range(m + 1)])
+    assert np.abs(gram - np.eye(m + 1)).max() < 1e-13
+    for j in range(m):
+        for i in range(j + 2):
+            assert abs(H[i, j] - inner(V[i], G @ V[j])) < 1e-13
+
+
 def test_arnoldi_estimate_bounds_truncation_error():
     rng = np.random.default_rng(1)
     n = 60
