@@ -148,6 +148,32 @@ def test_rdm_traces_and_closed_shell_energy():
     assert abs(H[0, 0] - E) < 1e-12
 
 
+def test_integrals_symmetries_with_complex_orbitals():
+    """With orbitals of large complex phase: (pq|rs) = conj((qp|sr)) and
+    h_pq = conj(h_qp) exactly, and the Coulomb pair symmetry (pq|rs) = (rs|pq)
+    up to the truncation of the multipole surface data (the discrete solve is
+    otherwise symmetric); an (r, s) index slip breaks the latter by O(1)."""
+    case = (-6.0, 6.0, 2, 2, [((0.0, 0.0, 0.7), 1.0, 1), ((0.0, 0.0, -0.7), 1.0, 1)], 2.0)
+    m = mesh.Mesh(*case)
+    op = fem.Operators(m)
+    n = 3
+    phi = np.zeros((m.N, n), dtype=complex)
+    ks = [(0.8, 0.0, 0.3), (-0.5, 0.9, 0.0), (0.0, -0.7, 1.1)]
+    for j in range(n):
+        c = np.array([0.3 * j, -0.2, 0.1 * j])
+        phi[:, j] = np.exp(-0.8 * np.sum((m.Xm - c) ** 2, axis=1)) * np.exp(1j * m.Xm @ np.array(ks[j]))
+    phi[m.boundary] = 0
+    phi = inputs.lowdin(phi, op.ML)
+    sim = mctdhf.MCTDHF(op, n, 2, 1)
+    W, _ = sim.mean_fields(phi)
+    h, eri = sim.integrals(phi, W, (0.0, 0.01, 0.02))
+    scale = np.abs(eri).max()
+    assert np.abs(eri.imag).max() > 0.1 * scale
+    np.testing.assert_allclose(eri, eri.transpose(1, 0, 3, 2).conj(), rtol=0, atol=1e-14 * scale)
+    np.testing.assert_allclose(h, h.conj().T, rtol=0, atol=1e-13 * np.abs(h).max())
+    assert np.abs(eri - eri.transpose(2, 3, 0, 1)).max() < 1e-3 * scale
+
+
 # ------------------------------------------------------------------- MCTDHF
 def _one_electron_setup(tiny):
     m, op = tiny

@@ -159,3 +159,29 @@ def test_dense_step_with_the_two_electron_term_doubled(monkeypatch):
     C = inputs.initial_ci(2, 1, 1, amp=0.1)
     with torch.no_grad():
         _fails(T_sg.test_dense_step_equals_oracle_step, (sim, dm, phi, C))
+
+
+def test_two_electron_integrals_with_r_and_s_swapped(monkeypatch):
+    orig = mctdhf.MCTDHF.integrals
+
+    def planted(self, phi, W, E):
+        h, eri = orig(self, phi, W, E)
+        return h, eri.transpose(0, 1, 3, 2)
+
+    monkeypatch.setattr(mctdhf.MCTDHF, "integrals", planted)
+    _fails(T_mc.test_integrals_symmetries_with_complex_orbitals)
+
+
+def test_mean_field_operator_with_gamma_not_inverted(monkeypatch):
+    monkeypatch.setattr(mctdhf.MCTDHF, "mean_field_operator",
+                        lambda self, g1, g2, W: np.einsum("pqrs,rsk->pqk", np.einsum("po,oqrs->pqrs", g1, g2), W))
+    m = mesh.Mesh(*T_mc.TINY)
+    _fails(T_mc.test_two_electron_closed_shell_is_tdhf, (m, fem.Operators(m)))
+
+
+def test_orbital_operator_without_the_projector(monkeypatch):
+    orig = mctdhf.MCTDHF.G_apply
+    monkeypatch.setattr(mctdhf.MCTDHF, "G_apply",
+                        lambda self, v, phi, U, E: orig(self, v, np.zeros_like(phi), U, E))
+    m = mesh.Mesh(*T_mc.TINY)
+    _fails(T_mc.test_eigenvector_is_stationary, (m, fem.Operators(m)))
