@@ -185,3 +185,45 @@ def test_orbital_operator_without_the_projector(monkeypatch):
                         lambda self, v, phi, U, E: orig(self, v, np.zeros_like(phi), U, E))
     m = mesh.Mesh(*T_mc.TINY)
     _fails(T_mc.test_eigenvector_is_stationary, (m, fem.Operators(m)))
+
+
+def test_ci_hamiltonian_without_the_delta_term(monkeypatch):
+    orig = ci.CISpace.hamiltonian
+
+    def planted(self, h, eri):
+        H = orig(self, h, eri)
+        for p in range(self.n):
+            for q in range(self.n):
+                for s in range(self.n):
+                    H = H + 0.5 * eri[p, q, q, s] * self.E[p][s].toarray()
+        return H
+
+    monkeypatch.setattr(ci.CISpace, "hamiltonian", planted)
+    _fails(T_mc.test_ci_two_electron_first_quantised)
+
+
+def test_pair_densities_conjugating_the_wrong_factor(monkeypatch):
+    orig = poisson.pair_densities
+
+    def planted(ops, phi):
+        rho, pairs = orig(ops, phi)
+        for j, (_r, _s, part) in enumerate(pairs):
+            if part == 1:
+                rho[:, j] = -rho[:, j]
+        return rho, pairs
+
+    monkeypatch.setattr(poisson, "pair_densities", planted)
+    _fails(T_mc.test_integrals_symmetries_with_complex_orbitals)
+
+
+def test_multipole_moments_without_the_quadrature_weights(monkeypatch):
+    orig = poisson.multipole_moments
+    monkeypatch.setattr(poisson, "multipole_moments",
+                        lambda X, w, rho, c, lmax=poisson.LMAX: orig(X, np.ones_like(w), rho, c, lmax))
+    _fails(T_poi.test_multipole_matches_direct_sum_off_centre)
+
+
+def test_nuclear_force_with_the_wrong_sign(monkeypatch):
+    orig = fem.Operators.nuclear_force
+    monkeypatch.setattr(fem.Operators, "nuclear_force", lambda self, X: -orig(self, X))
+    _fails(T_adj.test_nuclear_force_is_minus_grad_potential)
