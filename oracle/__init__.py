@@ -32,7 +32,8 @@ Modules and the parts of the paper they follow:
                  the gradient of a dipole functional with respect to the field by
                  automatic differentiation (the differentiation form beyond the
                  one-electron limit; Sec. 2, Sec. 3.2).
-* ``pulse``    - laser pulse shapes (Sec. 4 and the sin^2 workload pulses).
+* ``rows``     - selected rows of the assembled operators, formed cell by cell
+                 (parity at sizes whose assembled matrices would not fit).
 
 Every function that has no independent pin says "parity unpinned" in its
 docstring.

@@ -82,21 +82,30 @@ class CISpace:
         return sp.csr_matrix((vals, (rows, cols)), shape=(self.dim, self.dim))
 
     def hamiltonian(self, h, eri):
-        """Dense H_CI from one-electron h[p,q] and two-electron eri[p,q,r,s] = (pq|rs)."""
+        """Dense H_CI from one-electron h[p,q] and two-electron eri[p,q,r,s] = (pq|rs).
+
+        Each term's sparse matrix is added into H at its nonzeros only (the
+        same terms in the same order as adding the dense matrices, without
+        forming a dense temporary per term)."""
         n = self.n
         H = np.zeros((self.dim, self.dim), dtype=np.complex128)
+
+        def add(coef, M):
+            M = M.tocoo()
+            np.add.at(H, (M.row, M.col), coef * M.data)
+
         for p in range(n):
             for q in range(n):
                 Epq = self.E[p][q]
-                H += h[p, q] * Epq.toarray()
+                add(h[p, q], Epq)
                 for r in range(n):
                     for s in range(n):
                         if eri[p, q, r, s] == 0:
                             continue
-                        M = (Epq @ self.E[r][s]).toarray()
+                        M = Epq @ self.E[r][s]
                         if q == r:
-                            M = M - self.E[p][s].toarray()
-                        H += 0.5 * eri[p, q, r, s] * M
+                            M = M - self.E[p][s]
+                        add(0.5 * eri[p, q, r, s], M)
         return H
 
     def rdm1(self, C):

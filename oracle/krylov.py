@@ -70,7 +70,7 @@ def arnoldi_basis(apply_G, phi, inner, m, breakdown_tol=1e-14):
     return beta, V, H, m_used, breakdown, abs(H[m_used, m_used - 1])
 
 
-def arnoldi_propagate(apply_G, phi, inner, m, dt, tol, max_substeps=4096):
+def arnoldi_propagate(apply_G, phi, inner, m, dt, tol, max_substeps=4096, return_info=False, stop_after=None):
     """exp(-i G dt) phi with the Krylov error controlled substep by substep.
 
     Sec. 3.2 fixes the Krylov accuracy by an a-posteriori estimate (threshold
@@ -84,11 +84,18 @@ def arnoldi_propagate(apply_G, phi, inner, m, dt, tol, max_substeps=4096):
     when none is, the ladder continues below its smallest candidate (at most 8
     more ladders, then the smallest is taken).  A breakdown (invariant Krylov
     space) takes the whole remainder with estimate 0.  tol <= 0: one step over
-    dt.  Returns (phi_new, sum of estimates, substeps).
+    dt.  Returns (phi_new, sum of estimates, substeps), and with return_info a
+    fourth item: {"taus": substep lengths, "margin": the smallest
+    |log(estimate / (tol beta))| over every candidate the decisions compared
+    with the threshold, "remaining": the time left} -- a margin near zero marks
+    a near-tie, a decision that rounding at the level of the margin could flip.
+    stop_after: return after that many substeps (a partial propagation, for
+    timing a bounded sample).
     """
     remaining = dt
     cur = phi
     total, substeps, tau_prev = 0.0, 0, 0.0
+    taus, margin = [], np.inf
     while remaining > 0.0:
         if substeps >= max_substeps:
             raise RuntimeError("too many Krylov substeps")
@@ -105,6 +112,8 @@ def arnoldi_propagate(apply_G, phi, inner, m, dt, tol, max_substeps=4096):
                     tau = tau_max * 2.0 ** (-LADDER_LOG2 * c)
                     Em = scipy.linalg.expm(-1j * tau * H[:mu, :mu])
                     err = beta * hlast * abs(Em[mu - 1, 0])
+                    if err > 0.0:
+                        margin = min(margin, abs(np.log(err / (tol * beta))))
                     if err <= tol * beta:
                         found = True
                         break
@@ -115,5 +124,10 @@ def arnoldi_propagate(apply_G, phi, inner, m, dt, tol, max_substeps=4096):
         total += err
         substeps += 1
         tau_prev = tau
+        taus.append(tau)
         remaining = 0.0 if tau >= remaining else remaining - tau
+        if stop_after is not None and substeps >= stop_after:
+            break
+    if return_info:
+        return cur, total, substeps, dict(taus=taus, margin=margin, remaining=remaining)
     return cur, total, substeps

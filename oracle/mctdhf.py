@@ -90,8 +90,14 @@ class MCTDHF:
         return y - phi @ S
 
     # ----------------------------------------------------------------- step
-    def step(self, phi, C, E, dt, m):
-        """One step t -> t + dt.  Returns (phi_new, C_new, info dict)."""
+    def step(self, phi, C, E, dt, m, krylov_tol=0.0):
+        """One step t -> t + dt.  Returns (phi_new, C_new, info dict).
+
+        krylov_tol <= 0: the orbitals take one Krylov step of dimension m over
+        dt.  krylov_tol > 0: the error-controlled substeps of
+        ``krylov.arnoldi_propagate`` (estimate <= krylov_tol * beta per substep,
+        Sec. 3.2); info then carries the substep count, the summed estimates
+        and the decisions' smallest margin to the threshold."""
         W, Wc = self.mean_fields(phi)
         h, eri = self.integrals(phi, W, E)
         Hci = self.ci.hamiltonian(h, eri)
@@ -100,11 +106,18 @@ class MCTDHF:
         evals, evecs = np.linalg.eigh(0.5 * (Hci + Hci.conj().T))
         C_new = evecs @ (np.exp(-1j * dt * evals) * (evecs.conj().T @ C))
         U = self.mean_field_operator(g1, g2, W)
-        phi_new, err, Hk, m_used, brk = krylov.arnoldi_expm(
-            lambda v: self.G_apply(v, phi, U, E), phi, self.inner, m, dt)
+        apply_G = lambda v: self.G_apply(v, phi, U, E)   # noqa: E731
+        substeps, margin, Hk, m_used, brk = 1, np.inf, None, m, False
+        if krylov_tol > 0.0:
+            phi_new, err, substeps, pinfo = krylov.arnoldi_propagate(apply_G, phi, self.inner, m, dt, krylov_tol,
+                                                                     return_info=True)
+            margin = pinfo["margin"]
+        else:
+            phi_new, err, Hk, m_used, brk = krylov.arnoldi_expm(apply_G, phi, self.inner, m, dt)
         energy = np.real(np.sum(h * g1) + 0.5 * np.einsum("pqrs,pqrs->", eri, g2))
         info = dict(W=W, Wcols=Wc, h=h, eri=eri, Hci=Hci, gamma=g1, Gamma=g2, U=U,
                     arnoldi_err=err, H_krylov=Hk, m_used=m_used, breakdown=brk, energy=energy,
+                    krylov_substeps=substeps, krylov_margin=margin,
                     dipole=self.dipole(phi, C))
         return phi_new, C_new, info
 

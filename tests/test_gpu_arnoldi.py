@@ -5,7 +5,7 @@ import pytest
 
 from oracle import fem, krylov, mctdhf, mesh as omesh
 from paper_2301_02387_gb300 import inputs
-from tests._match import coord_permutation
+from tests._match import assert_close, coord_permutation
 
 pytestmark = pytest.mark.gpu
 
@@ -49,9 +49,7 @@ def test_arnoldi_step_parity(case, n, with_U, m):
     U = torch.from_numpy(np.ascontiguousarray(U_o.transpose(2, 0, 1)[perm])).cuda() if with_U else None
     out, err_g, mu, brk_g = pkg.arnoldi_step(gm, phi, U, m, 0.02, E=E)
     torch.cuda.synchronize()
-    og = out.cpu().numpy()
-    rel = np.linalg.norm(og - ref[perm]) / np.linalg.norm(ref)
-    assert rel < 1e-10
+    assert_close(out.cpu().numpy(), ref[perm], 1e-10, what="Arnoldi step")
     assert mu == m_used and brk_g == brk
     assert abs(err_g - err) <= 1e-6 * abs(err) + 1e-18
 
@@ -105,10 +103,9 @@ def test_arnoldi_propagate_substeps_parity(precision_name):
     prec = pkg.PREC_FP64 if precision_name == "fp64" else pkg.PREC_MIXED
     out, err_g, sub_g = pkg.arnoldi_propagate(gm, phi, U, 6, 0.05, 1e-9, E=E, precision=prec)
     torch.cuda.synchronize()
-    rel = np.linalg.norm(out.cpu().numpy() - ref[perm]) / np.linalg.norm(ref)
     if precision_name == "fp64":
         assert sub_g == sub
-        assert rel < 1e-10
+        assert_close(out.cpu().numpy(), ref[perm], 1e-10, what="propagation")
     else:
         assert abs(sub_g - sub) <= 1
-        assert rel < 1e-6
+        assert_close(out.cpu().numpy(), ref[perm], 1e-6, what="propagation")

@@ -11,7 +11,7 @@ import pytest
 
 from oracle import fem, krylov, mctdhf, mesh as omesh, poisson
 from paper_2301_02387_gb300 import inputs
-from tests._match import coord_permutation
+from tests._match import assert_close, coord_permutation, rel_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -34,9 +34,9 @@ def full():
 
 
 def _relerr(a, b):
-    num = np.linalg.norm(a - b, axis=0)
-    den = np.maximum(np.linalg.norm(b, axis=0), 1e-300)
-    return (num / den).max()
+    """Worst column of: the L2 relative error and the largest entry error over
+    the column's largest reference entry (the per-entry check)."""
+    return max(rel_errors(a, b, axis=0))
 
 
 def _fields(X, n, seed):
@@ -163,27 +163,35 @@ def test_full_arnoldi_step(full, krylov_case):
         out, err, mu, brk = pkg.arnoldi_step(gm, phi, U, w["m"], dt, E=E, precision=prec)
         torch.cuda.synchronize()
         assert mu == w["m"] and not brk
-        rel = np.linalg.norm(out.cpu().numpy() - ref[perm]) / np.linalg.norm(ref)
-        assert rel < bar, (prec, rel)
+        assert_close(out.cpu().numpy(), ref[perm], bar, what=f"precision {prec}")
 
 
 def test_full_arnoldi_propagate(full, krylov_case):
     """The error-controlled propagation of the benchmark (threshold 1e-10 per
-    substep, 64-candidate ladder).  Both sides stay within their estimates of
-    the exact propagator, so they agree to about the sum of the estimates
-    whatever ladder rung a near-tie picks: FP64 within 1e-9, the precision form
-    within 1e-6; substep counts equal up to one."""
+    substep, candidates tau_max 2^(-c/8)).  Each substep takes the longest
+    candidate whose estimate meets the threshold, so both sides take the same
+    substeps unless an estimate lies within rounding of the threshold (a
+    near-tie).  The oracle reports the decisions' smallest margin
+    |log(estimate / threshold)|: above 1e-6 (FP64: the estimates agree to
+    ~1e-10 relative) the substep lengths are identical and the FP64 result is
+    held to the 1e-10 bar; the precision form (estimates within ~1e-6) needs a
+    margin above 1e-3 for equal counts and is held to 1e-6."""
     import torch
     import paper_2301_02387_gb300 as pkg
     gm, om, op, perm, w, phi_o = full
     U_o, E, apply_G, inner = krylov_case
     dt, tol = 2e-4, 1e-10
-    ref, err_o, sub_o = krylov.arnoldi_propagate(apply_G, phi_o, inner, w["m"], dt, tol)
+    ref, err_o, sub_o, pinfo = krylov.arnoldi_propagate(apply_G, phi_o, inner, w["m"], dt, tol, return_info=True)
     assert sub_o >= 2
     phi, U = _gpu_inputs(full, U_o)
-    for prec, bar in ((pkg.PREC_FP64, 1e-9), (pkg.PREC_MIXED, 1e-6)):
+    for prec, bar, tie, ebar in ((pkg.PREC_FP64, 1e-10, 1e-6, 1e-6), (pkg.PREC_MIXED, 1e-6, 1e-3, 1e-3)):
         out, err, sub = pkg.arnoldi_propagate(gm, phi, U, w["m"], dt, tol, E=E, precision=prec)
         torch.cuda.synchronize()
-        assert abs(sub - sub_o) <= 1, (prec, sub, sub_o)
-        rel = np.linalg.norm(out.cpu().numpy() - ref[perm]) / np.linalg.norm(ref)
-        assert rel < bar, (prec, rel)
+        if pinfo["margin"] > tie:
+            assert sub == sub_o, (prec, sub, sub_o)
+            assert_close(out.cpu().numpy(), ref[perm], bar, what=f"precision {prec}")
+            assert abs(err - err_o) <= ebar * err_o
+        else:   # a near-tie: both sides are within their summed estimates of the exact propagator
+            assert abs(sub - sub_o) <= 1, (prec, sub, sub_o)
+            assert_close(out.cpu().numpy(), ref[perm], max(bar, 4.0 * (err + err_o) / np.sqrt(inner(phi_o, phi_o).real)),
+                         what=f"precision {prec} near-tie")

@@ -1,13 +1,16 @@
 """GPU parity of afem_mctdhf_step against the oracle's MCTDHF step (Sec. 2,
 Sec. 3.2; Eqs. ci_eom, orb_eom, packed_orb_eom).  The GPU Poisson batch runs
 to rtol 1e-14 so that its forward error (kappa * rtol) stays far below the
-1e-10 bar on orbitals, CI vector, energy and dipole; the oracle solves directly."""
+1e-10 bar on orbitals, CI vector, energy and dipole; the oracle solves directly
+(or by CG to rtol 1e-13 where the direct factorisation of a degree-4 mesh
+would take minutes).  Vectors are held to the bar both in the L2 norm and
+entry by entry (largest entry error over the largest reference entry)."""
 import numpy as np
 import pytest
 
 from oracle import fem, mctdhf, mesh as omesh, poisson
 from paper_2301_02387_gb300 import inputs
-from tests._match import coord_permutation
+from tests._match import assert_close, coord_permutation
 
 pytestmark = pytest.mark.gpu
 
@@ -52,16 +55,19 @@ def test_mctdhf_steps_parity(case, n, na, nb):
         Wg = np.empty((om.N, n * n))
         Wg[perm] = W.cpu().numpy()
         assert np.all(sim.ps.residual(Wg, rho) < 1e-12)
-        pg = phi.cpu().numpy()
-        assert np.linalg.norm(pg - phi_o[perm]) / np.linalg.norm(phi_o) < 1e-10
-        cg = C.cpu().numpy()
-        assert np.linalg.norm(cg - C_o) / np.linalg.norm(C_o) < 1e-10
-        assert abs(info["energy"] - info_o["energy"]) < 1e-10 * abs(info_o["energy"])
-        # <sum r_i> at t (scale: the electron count times the box half-width)
-        dscale = max(np.max(np.abs(info_o["dipole"])), (na + nb) * 1.0)
-        assert np.max(np.abs(np.asarray(info["dipole"]) - info_o["dipole"])) < 1e-10 * dscale
+        _compare_step(phi, C, info, phi_o, C_o, info_o, perm, na + nb, 1e-10)
         assert info["krylov_m_used"] == info_o["m_used"]
         assert abs(info["arnoldi_err"] - info_o["arnoldi_err"]) <= 1e-6 * info_o["arnoldi_err"] + 1e-16
+
+
+def _compare_step(phi, C, info, phi_o, C_o, info_o, perm, n_el, bar):
+    """Orbitals and CI vector (L2 and per entry), energy and <sum r_i> within bar."""
+    assert_close(phi.cpu().numpy(), phi_o[perm], bar, what="orbitals")
+    assert_close(C.cpu().numpy(), C_o, bar, what="CI vector")
+    assert abs(info["energy"] - info_o["energy"]) < bar * abs(info_o["energy"])
+    # <sum r_i> at t (scale: the electron count times the box half-width)
+    dscale = max(np.max(np.abs(info_o["dipole"])), n_el * 1.0)
+    assert np.max(np.abs(np.asarray(info["dipole"]) - info_o["dipole"])) < bar * dscale
 
 
 def test_singular_density_matrix_is_reported():
@@ -84,3 +90,95 @@ def test_singular_density_matrix_is_reported():
         solver.step(phi, C, W, None, 0.02)
     assert ei.value.code == pkg._capi.AFEM_ESINGULAR
     assert torch.equal(phi, before)
+
+
+# degree 4, 3 levels toward each nucleus of H2 (h_min = 0.375): at dt = 0.04 the
+# benchmark's Krylov threshold takes about 15 substeps of dimension 10 per step
+KTOL_CASE = (-6.0, 6.0, 2, 4, [((0.0, 0.0, 0.7), 1.0, 3), ((0.0, 0.0, -0.7), 1.0, 3)], 1.0)
+
+
+@pytest.mark.parametrize("precision_name", ["fp64", "mixed"])
+def test_mctdhf_steps_krylov_tol_parity(precision_name):
+    """The step in the benchmark's mode: error-controlled Krylov substeps of
+    dimension 10 at threshold 1e-10 (Sec. 3.2).  Two steps of >= 10 substeps
+    each.  The oracle's decisions' margin to the threshold (|log(estimate /
+    threshold)|) rules out a near-tie; then the substep counts are equal and
+    the FP64 step matches the oracle to 1e-10, the precision form to 1e-6."""
+    import torch
+    import paper_2301_02387_gb300 as pkg
+    case, n, na, nb = KTOL_CASE, 2, 1, 1
+    gm = pkg.Mesh(*case)
+    om = omesh.Mesh(*case)
+    op = fem.Operators(om)
+    X, _, _ = gm.tables()
+    perm = coord_permutation(X, om.Xm)
+    phi_o = inputs.lowdin(inputs.molecular_orbitals(om.Xm, ~om.boundary, case[4], n), op.ML)
+    C_o = inputs.initial_ci(n, na, nb, amp=0.1)
+    sim = mctdhf.MCTDHF(op, n, na, nb, poisson_method="cg", poisson_rtol=1e-13)
+    solver = pkg.MCTDHF(gm, n, na, nb, 10)
+    solver.set_krylov_tol(1e-10)
+    fp64 = precision_name == "fp64"
+    if not fp64:
+        solver.set_precision(pkg.PREC_MIXED)
+    bar, tie = (1e-10, 1e-6) if fp64 else (1e-6, 1e-3)
+    phi = torch.from_numpy(np.ascontiguousarray(phi_o[perm])).cuda()
+    C = torch.from_numpy(C_o.copy()).cuda()
+    W = torch.zeros((gm.N, n * n), dtype=torch.float64, device="cuda")
+    E = (0.0, 0.01, 0.03)
+    dt = 0.04
+    for step in range(2):
+        phi_o, C_o, info_o = sim.step(phi_o, C_o, E, dt, 10, krylov_tol=1e-10)
+        info = solver.step(phi, C, W, E, dt, cg_rtol=1e-14 if fp64 else 1e-12, cg_max_it=20000,
+                           raise_on_maxit=False)
+        torch.cuda.synchronize()
+        assert info_o["krylov_substeps"] >= 10
+        assert info_o["krylov_margin"] > tie, "near-tie in the oracle's substep decisions"
+        assert info["krylov_substeps"] == info_o["krylov_substeps"]
+        _compare_step(phi, C, info, phi_o, C_o, info_o, perm, na + nb, bar)
+        assert abs(info["arnoldi_err"] - info_o["arnoldi_err"]) <= (1e-6 if fp64 else 1e-3) * info_o["arnoldi_err"]
+
+
+@pytest.fixture(scope="module")
+def water_electrons():
+    """The water workload's electron count on a small O + 2 H mesh: 8 orbitals,
+    5 alpha + 5 beta electrons (3,136 determinants), 64 mean fields; the
+    oracle's trajectory of two steps (the CI block is mesh-independent)."""
+    import paper_2301_02387_gb300 as pkg
+    case, n, na, nb = WATER_SMALL, 8, 5, 5
+    gm = pkg.Mesh(*case)
+    om = omesh.Mesh(*case)
+    op = fem.Operators(om)
+    X, _, _ = gm.tables()
+    perm = coord_permutation(X, om.Xm)
+    phi0 = inputs.lowdin(inputs.molecular_orbitals(om.Xm, ~om.boundary, case[4], n), op.ML)
+    C0 = inputs.initial_ci(n, na, nb, amp=0.1)
+    sim = mctdhf.MCTDHF(op, n, na, nb)
+    E, dt = (0.0, 0.01, 0.03), 0.02
+    traj, phi_o, C_o = [], phi0, C0
+    for step in range(2):
+        phi_o, C_o, info_o = sim.step(phi_o, C_o, E, dt, 8)
+        traj.append((phi_o, C_o, info_o))
+    return gm, perm, phi0, C0, traj, E, dt
+
+
+@pytest.mark.parametrize("precision_name", ["fp64", "mixed"])
+def test_mctdhf_water_electron_count(water_electrons, precision_name):
+    """5 alpha + 5 beta electrons in 8 orbitals (N_CI = 3,136): two steps, FP64
+    within 1e-10 of the oracle, the precision form within 1e-6."""
+    import torch
+    import paper_2301_02387_gb300 as pkg
+    gm, perm, phi0, C0, traj, E, dt = water_electrons
+    n = 8
+    solver = pkg.MCTDHF(gm, n, 5, 5, 8)
+    assert solver.ci_dim == 3136 == len(C0)
+    fp64 = precision_name == "fp64"
+    if not fp64:
+        solver.set_precision(pkg.PREC_MIXED)
+    phi = torch.from_numpy(np.ascontiguousarray(phi0[perm])).cuda()
+    C = torch.from_numpy(C0.copy()).cuda()
+    W = torch.zeros((gm.N, n * n), dtype=torch.float64, device="cuda")
+    for phi_o, C_o, info_o in traj:
+        info = solver.step(phi, C, W, E, dt, cg_rtol=1e-14 if fp64 else 1e-12, cg_max_it=20000,
+                           raise_on_maxit=False)
+        torch.cuda.synchronize()
+        _compare_step(phi, C, info, phi_o, C_o, info_o, perm, 10, 1e-10 if fp64 else 1e-6)
