@@ -136,6 +136,19 @@ int afem_convert(const void* x, void* y, int64_t n, int direction, void* stream)
 int afem_profile_enable(int on);
 int afem_profile_read(int cls, double* ms, int64_t* calls, double* work, int reset);
 
+/* Measured arithmetic peak of the current device (library instrumentation
+ * with no counterpart in the paper): fused multiply-add throughput in FP64
+ * (AFEM_PEAK_FP64) or FP32 (AFEM_PEAK_FP32), in flop/s (2 per multiply-add),
+ * from 4 blocks of 256 threads per SM, each thread running 8 independent
+ * multiply-add chains.  The loop length is calibrated so that one launch
+ * takes about target_ms (0 < target_ms <= 1e4); the best of 3 timed launches
+ * (CUDA events on `stream`) is returned in *flops_per_s.  Allocates and frees
+ * one scalar of device memory; synchronous.  Errors: AFEM_EINVAL (unknown
+ * kind, target out of range, null output), AFEM_ECUDA. */
+#define AFEM_PEAK_FP64 0
+#define AFEM_PEAK_FP32 1
+int afem_fma_peak(int kind, double target_ms, double* flops_per_s, void* stream);
+
 /* Build the mesh on the host and upload every table to the current device.
  * Sec. 3.1 (coarse cubes halved toward the nuclei; GLL tensor basis; bridged
  * functions).  *out receives a library-owned object; free it with
@@ -255,9 +268,11 @@ int afem_poisson_batch_ex(afem_mesh* mesh, const void* phi, int n_orb, void* W, 
  *
  * Limits and behaviour:
  *  - n_orb must be 1..AFEM_NOALLOC_MAX_ORB; larger values return AFEM_EINVAL.
+ *  - The current device must be the mesh's device (else AFEM_EINVAL).
  *  - The first call on a device looks up the device address of the scratch
- *    array (with that device current); make that first call before any stream
- *    capture.
+ *    array (with that device current) and uploads the solid-harmonic
+ *    constants of the expansion (two synchronous copies); make that first
+ *    call before any stream capture.
  *  - All calls share the one scratch array and each call overwrites it
  *    completely before reading it; calls that overlap on the GPU (other
  *    streams, other host threads) race and must be serialised by the caller.
@@ -269,8 +284,11 @@ int afem_poisson_boundary_noalloc(afem_mesh* mesh, const void* phi, int n_orb, v
  * operator frozen (Sec. 3.2, Eq. packed_orb_eom; Eq. orb_eom with X = 0):
  *   (G v)_p = Q [ M_L^-1 ( H1~ v_p + C^T diag(m_f) sum_q (C U_pq) o (C v_q) ) ],
  *   Q y = y - sum_j phi_j (phi_j^H M_L y),
- *   phi_out = beta V_m exp(-i dt H_m) e_1   (Arnoldi, modified Gram-Schmidt,
- *   inner product <u,v> = sum_p u_p^H M_L v_p, beta = ||phi||).
+ *   phi_out = beta V_m exp(-i dt H_m) e_1   (Arnoldi in the inner product
+ *   <u,v> = sum_p u_p^H M_L v_p, beta = ||phi||; each new vector is
+ *   orthogonalised by classical Gram-Schmidt -- all inner products in one
+ *   pass, the update in a second -- and by a second such pair of passes only
+ *   when the update left less than 1e-2 of the vector's norm).
  * phi, phi_out: complex128 [N][n_orb] device arrays (must not alias).
  * U: complex128 [N][n_orb][n_orb] device array of mean-field operator
  *   fields U_pq = sum_o (D^-1)^o_p sum_rs P^{qs}_{or} W^r_s at the masters,
@@ -278,8 +296,9 @@ int afem_poisson_boundary_noalloc(afem_mesh* mesh, const void* phi, int n_orb, v
  * krylov_m: 1..16.  err_est (host, may be NULL): beta |h_{m+1,m}|
  *   |e_m^T exp(-i dt H_m) e_1|, 0 after a happy breakdown; m_used and
  *   breakdown (host, may be NULL) report the dimension actually used.
- * Allocates (grow-only) mesh-owned workspace; synchronises `stream` once
- * per Krylov vector (breakdown test). */
+ * Allocates (grow-only) mesh-owned workspace; synchronises `stream` once,
+ * after the Krylov space is built (the breakdown test reads the Hessenberg
+ * matrix on the host). */
 int afem_arnoldi_step(afem_mesh* mesh, const double* E, const void* phi, const void* U, int n_orb,
                       int krylov_m, double dt, void* phi_out, double* err_est, int* m_used,
                       int* breakdown, void* stream);
@@ -294,15 +313,37 @@ int afem_arnoldi_step_ex(afem_mesh* mesh, const double* E, const void* phi, cons
 
 /* exp(-i G dt) phi with error control (Sec. 3.2): G frozen as in
  * afem_arnoldi_step; dt is covered by substeps tau_1, tau_2, ..., each from a
- * fresh Krylov space of dimension krylov_m built from the current vector, and
- * each chosen (halving or shrinking by (tol/err)^(1/m)) so that
- * beta |h_{m+1,m}| |e_m^T exp(-i tau H_m) e_1| <= tol * beta.  err_est (host,
- * may be NULL) receives the sum of the accepted estimates, substeps (host, may
- * be NULL) the substep count.  More than 4096 substeps returns AFEM_EINVAL.
- * Allocates (grow-only) mesh-owned workspace; synchronises `stream`. */
+ * fresh Krylov space of dimension krylov_m built from the current vector.
+ * Each substep is the longest of the candidates tau_max 2^(-c/8), c = 0..63,
+ * whose estimate beta |h_{m+1,m}| |e_m^T exp(-i tau H_m) e_1| is <= tol *
+ * beta, with tau_max the whole remainder for the first substep and
+ * min(remainder, 2 tau_previous) after it; when no candidate passes, the
+ * candidates continue below the smallest one (at most 8 more sets of 64, then
+ * the smallest is taken).  The 64 candidate exponentials are evaluated in one
+ * launch.  A breakdown takes the whole remainder exactly.  tol <= 0: one step
+ * over dt.  err_est (host, may be NULL) receives the sum of the accepted
+ * estimates, substeps (host, may be NULL) the substep count.  More than 4096
+ * substeps returns AFEM_EINVAL.  Allocates (grow-only) mesh-owned workspace;
+ * synchronises `stream` once per substep. */
 int afem_arnoldi_propagate(afem_mesh* mesh, const double* E, const void* phi, const void* U, int n_orb,
                            int krylov_m, double dt, int precision, double tol, void* phi_out,
                            double* err_est, int* substeps, void* stream);
+
+/* exp(-i G dt) phi by the rule of Sec. 3.2 (the dimension of the Krylov space
+ * is chosen by the error estimate at a fixed step): dt is split into `steps`
+ * (1..4096) equal steps tau = dt / steps; in each, the Arnoldi process of
+ * afem_arnoldi_step adds one vector at a time and, after vector j + 1,
+ * evaluates beta |h_{j+2,j+1}| |e_{j+1}^T exp(-i tau H_{j+1}) e_1|; the first
+ * dimension whose estimate is <= tol * beta is used (a breakdown uses the
+ * exact projected exponential); if none up to m_max (1..16) is, m_max is used
+ * and the step is counted in *unmet.  err_est, dim_max, dim_sum, unmet (host,
+ * each may be NULL): the summed estimates, the largest and the summed
+ * dimensions, the unmet steps.  Allocates (grow-only) mesh-owned workspace;
+ * synchronises `stream` once per added vector.  Errors: AFEM_EINVAL
+ * (arguments), AFEM_ENAN, AFEM_ENOMEM, AFEM_ECUDA. */
+int afem_arnoldi_adaptive(afem_mesh* mesh, const double* E, const void* phi, const void* U, int n_orb,
+                          int m_max, double dt, int steps, int precision, double tol, void* phi_out,
+                          double* err_est, int* dim_max, int* dim_sum, int* unmet, void* stream);
 
 /* MCTDHF time stepper (Sec. 2 and Sec. 3.2): owns the determinant-space
  * tables and its device workspace; the mesh must outlive it. */
@@ -318,6 +359,8 @@ typedef struct afem_step_info {
     int32_t krylov_substeps; /* Krylov substeps taken (1 unless a Krylov tolerance is set) */
     double dipole[3];        /* <sum_i r_i> at t: sum_pq gamma_pq phi_p^H F[x_d] phi_q, d = x, y, z
                                 (summed electron positions; the dipole moment is its negative) */
+    int32_t krylov_dim_sum;  /* Krylov dimensions summed over the substeps (G applications) */
+    int32_t krylov_unmet;    /* adaptive dimension: steps whose estimate stayed above the threshold */
 } afem_step_info;
 
 /* n_orb spatial orbitals (1..8), n_alpha / n_beta electrons per spin
@@ -340,6 +383,12 @@ int afem_mctdhf_set_precision(afem_mctdhf* solver, int precision);
  * short enough that its estimate stays below tol * ||phi|| (see
  * afem_arnoldi_propagate).  Host only. */
 int afem_mctdhf_set_krylov_tol(afem_mctdhf* solver, double tol);
+/* The Krylov rule of Sec. 3.2 for later steps: steps > 0 splits each time
+ * step into `steps` equal Krylov steps, each with the smallest dimension (up
+ * to krylov_m) whose estimate is <= tol ||phi|| (see afem_arnoldi_adaptive;
+ * tol from afem_mctdhf_set_krylov_tol, which must then be > 0); 0 (default)
+ * returns to the rule of afem_mctdhf_set_krylov_tol.  Host only. */
+int afem_mctdhf_set_krylov_adaptive(afem_mctdhf* solver, int steps);
 /* Number of determinants (host). */
 int afem_mctdhf_ci_dim(const afem_mctdhf* solver, int64_t* dim);
 
@@ -416,10 +465,13 @@ int afem_tdse_vjp(afem_mesh* mesh, const double* e_dir, const double* E, int n_s
  * The FP32 cell passes of Sec. 3.1 (Eq. discretized_eom) applied to every
  * instance of a batch of meshes (uneven sizes, degrees 1..4) by one persistent
  * kernel: for each instance i, y_i = M_L^-1 H1~(E_i) x_i with Dirichlet rows
- * zero (AFEM_OP_H1_C64: x_i, y_i complex64 [N_i][n_vec_i], n_vec_i even) or
- * y_i = A x_i (AFEM_OP_STIFF_F32: float32 [N_i][n_vec_i], n_vec_i % 4 == 0),
- * the same result as afem_op_apply on that mesh up to the order of the
- * floating-point atomic sums.  Small cells (p <= 3, few quads) are grouped
+ * zero (AFEM_OP_H1_C64: x_i, y_i complex64 [N_i][n_vec_i]) or y_i = A x_i
+ * (AFEM_OP_STIFF_F32: float32 [N_i][n_vec_i]), the same result as
+ * afem_op_apply on that mesh up to the order of the floating-point atomic
+ * sums.  The persistent kernel moves each node's values as 16-byte quads; a
+ * batch with an instance whose values are not whole quads (an odd orbital
+ * count, real columns not a multiple of 4, or a buffer not 16-byte aligned)
+ * runs the per-instance schedule below only.  Small cells (p <= 3, few quads) are grouped
  * into work items that fill a block.  The first apply of a (kind, n_vec)
  * signature times candidate schedules on the batch itself -- the persistent
  * launch with grids of 2 or all resident blocks per SM at 256 and 128
@@ -431,11 +483,11 @@ int afem_tdse_vjp(afem_mesh* mesh, const double* e_dir, const double* E, int n_s
  * table (pointers, fields) lives in device memory and is re-uploaded when
  * an argument changes, so new buffers or fields need no new capture.
  * Ownership: the batch holds the mesh handles (which must outlive it) and
- * its own device table; x_i, y_i are caller-owned device buffers, 16-byte
- * aligned, x_i != y_i.  E: host [count][3] or NULL (0 field); x, y, n_vec:
- * host arrays of count entries.  Errors: AFEM_EINVAL (count outside 1..256,
- * host-only mesh or mesh on another device, lanes not a multiple of 4,
- * misaligned or aliased buffers), AFEM_ENOMEM, AFEM_ECUDA.  Asynchronous on
+ * its own device table; x_i, y_i are caller-owned device buffers,
+ * x_i != y_i.  E: host [count][3] or NULL (0 field); x, y, n_vec: host
+ * arrays of count entries.  Errors: AFEM_EINVAL (count outside 1..256,
+ * host-only mesh or mesh on another device, n_vec_i < 1, aliased buffers),
+ * AFEM_ENOMEM, AFEM_ECUDA.  Asynchronous on
  * `stream`, except that a changed table or a new signature synchronises it. */
 #define AFEM_BATCH_MAX 256
 #define AFEM_BATCH_GRAPH 1

@@ -26,6 +26,7 @@ using namespace afem;
 
 namespace {
 constexpr int kParStreams = 16;   // streams available to the per-instance schedule
+bool aligned16(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; }
 }
 
 struct afem_batch {
@@ -121,13 +122,17 @@ int time_shape(afem_batch* b, int kind, int block, unsigned grid, size_t smem, c
 // Candidate schedules: the persistent launch with grids of 2 or all resident
 // blocks per SM at 256 and 128 threads and one block per work item, and the
 // per-instance passes on 4, 8 or 16 parallel streams (block 0, grid =
-// streams).  The fastest is kept.
-int tune(afem_batch* b, int kind, cudaStream_t s) {
+// streams).  The fastest is kept.  persistent = false (an instance whose
+// values per node are not whole 16-byte quads: an odd orbital count, real
+// columns not a multiple of 4, or unaligned buffers) leaves only the
+// per-instance schedule, whose single-instance passes take any count.
+int tune(afem_batch* b, int kind, bool persistent, cudaStream_t s) {
     b->cand_ms.clear();
     b->cand_block.clear();
     b->cand_grid.clear();
     double best = 1e30;
     for (int block : {256, 128}) {
+        if (!persistent) break;
         int per_sm = 0;
         int rc = batch32_occupancy(kind, block, b->smem, &per_sm);
         if (rc) return rc;
@@ -238,14 +243,23 @@ int afem_batch_op_apply(afem_batch* b, int kind, const double* E, void* const* x
     const int count = int(b->meshes.size());
     std::vector<int> p(count), L4(count);
     std::vector<unsigned char> staged(b->rec * count);
-    int64_t item0 = 0;   // first work item of each instance (small cells grouped per item)
+    bool quads = true;   // every instance's node values are whole 16-byte quads
     for (int i = 0; i < count; ++i) {
         if (!x[i] || !y[i] || n_vec[i] < 1) return set_error(AFEM_EINVAL, "afem_batch_op_apply: bad instance buffer");
         if (x[i] == y[i]) return set_error(AFEM_EINVAL, "afem_batch_op_apply: x and y must differ");
+        const int L = kind == AFEM_OP_H1_C64 ? 2 * n_vec[i] : n_vec[i];
+        if (L % 4 != 0 || !aligned16(x[i]) || !aligned16(y[i])) quads = false;
+    }
+    int64_t item0 = 0;   // first work item of each instance (small cells grouped per item)
+    for (int i = 0; i < count; ++i) {
+        p[i] = b->meshes[i]->dev.p;
+        if (!quads) {   // per-instance schedule only; the signature keeps the column counts
+            L4[i] = -n_vec[i];
+            continue;
+        }
         int rc = batch32_fill(b->meshes[i], kind, E ? E + 3 * i : nullptr, x[i], y[i], n_vec[i], item0,
                               staged.data() + b->rec * i);
         if (rc) return rc;
-        p[i] = b->meshes[i]->dev.p;
         L4[i] = (kind == AFEM_OP_H1_C64 ? 2 * n_vec[i] : n_vec[i]) / 4;
         item0 += batch32_items(p[i], L4[i], b->meshes[i]->dev.ncell);
     }
@@ -268,8 +282,8 @@ int afem_batch_op_apply(afem_batch* b, int kind, const double* E, void* const* x
         drop_graph(b);
         b->sig_kind = kind;
         b->sig_L4 = L4;
-        b->smem = batch32_smem(p, L4);
-        int rc = tune(b, kind, s);
+        b->smem = quads ? batch32_smem(p, L4) : 0;
+        int rc = tune(b, kind, quads, s);
         if (rc) {
             b->sig_kind = -1;
             return rc;

@@ -2,9 +2,13 @@
 degrees 1..4) in one persistent launch must give each instance what the
 single-instance afem_op_apply gives it (up to the order of the float atomic
 sums), also when replayed from the captured graph and after the fields or
-buffers change."""
+buffers change; and every instance is compared with the oracle's assembled
+operators (Sec. 3.1) directly, odd orbital counts included."""
 import numpy as np
 import pytest
+
+from oracle import fem, mesh as omesh
+from tests._match import assert_close, coord_permutation
 
 pytestmark = pytest.mark.gpu
 
@@ -87,10 +91,60 @@ def test_batch_rejects_bad_arguments():
     import paper_2301_02387_gb300 as pkg
     meshes = _meshes()[:2]
     batch = pkg.Batch(meshes)
-    xs = [torch.zeros((m.N, 3), dtype=torch.complex64, device="cuda") for m in meshes]   # odd orbital count
-    with pytest.raises(pkg.AfemError):
-        batch.apply(pkg.OP_H1_C64, xs, [torch.empty_like(x) for x in xs])
     xs = [torch.zeros((m.N, 4), dtype=torch.complex64, device="cuda") for m in meshes]
     with pytest.raises(pkg.AfemError):
         batch.apply(pkg.OP_H1_C64, xs, xs)   # aliased in/out
+    xr = [torch.zeros((m.N, 4), dtype=torch.float32, device="cuda") for m in meshes]
+    with pytest.raises(pkg.AfemError):
+        batch.apply(pkg.OP_STIFF, xr, [torch.empty_like(x) for x in xr])   # not a batched kind
+    batch.close()
+
+
+@pytest.mark.parametrize("nvec", [[1, 3, 2, 5], [2, 4, 6, 8], [7, 1, 1, 3]])
+def test_batched_instances_match_oracle(nvec):
+    """Each instance of the batch against the oracle's assembled operators:
+    y_i = M_L^-1 H1~(E_i) x_i (complex64; odd orbital counts run the
+    per-instance schedule, even ones may run the persistent launch) and the
+    stiffness on 3, 4, 5 or 12 real columns; inputs rounded to float32 on both
+    sides; 2e-5 relative per vector and per entry (float32 rounding times the
+    operator norm, the bar of the single-instance tests)."""
+    import torch
+    import paper_2301_02387_gb300 as pkg
+    meshes = _meshes()
+    rng = np.random.default_rng(sum(nvec))
+    E = [(0.01, -0.02, 0.03), (0.0, 0.0, 0.05), (0.02, 0.0, 0.0), (0.0, 0.01, 0.0)]
+    orc, perms = [], []
+    for m, c in zip(meshes, CASES):
+        om = omesh.Mesh(*c)
+        X, _, _ = m.tables()
+        perms.append(coord_permutation(X, om.Xm))
+        orc.append((om, fem.Operators(om)))
+    batch = pkg.Batch(meshes)
+    xo = []
+    for (om, op), k in zip(orc, nvec):
+        x = (rng.standard_normal((om.N, k)) + 1j * rng.standard_normal((om.N, k))).astype(np.complex64)
+        xo.append(x.astype(np.complex128))
+    xs = [torch.from_numpy(np.ascontiguousarray(x[pm]).astype(np.complex64)).cuda() for x, pm in zip(xo, perms)]
+    for graph in (False, True):
+        ys = [torch.full_like(x, float("nan")) for x in xs]
+        batch.apply(pkg.OP_H1_C64, xs, ys, E=E, graph=graph)
+        torch.cuda.synchronize()
+        for (om, op), x, y, pm, e in zip(orc, xo, ys, perms, E):
+            x = x.copy()
+            x[om.boundary] = 0.0
+            assert_close(y.to(torch.complex128).cpu().numpy(), op.h1_apply(x, E=e)[pm], 2e-5, axis=0,
+                         what=f"H1 instance N={om.N}")
+    ks = [3 + (k % 2), 4, 5, 12]
+    so = [rng.standard_normal((om.N, k)).astype(np.float32).astype(np.float64) for (om, _), k in zip(orc, ks)]
+    ss = [torch.from_numpy(np.ascontiguousarray(x[pm])).float().cuda() for x, pm in zip(so, perms)]
+    ys = [torch.empty_like(x) for x in ss]
+    batch.apply(pkg.OP_STIFF_F32, ss, ys, graph=True)
+    torch.cuda.synchronize()
+    for (om, op), x, y, pm in zip(orc, so, ys, perms):
+        assert_close(y.double().cpu().numpy(), op.stiffness_apply(x)[pm], 2e-5, axis=0,
+                     what=f"stiffness instance N={om.N}")
+    t = batch.tuning()
+    assert t["tuned"]
+    if any(2 * k % 4 for k in nvec):
+        assert t["block"] == 0   # odd orbital counts: the per-instance schedule
     batch.close()
