@@ -375,7 +375,7 @@ def _class_rooflines(prof, total_ms, fp64_peak, hbm, peak_src):
         rate = work / (ms * 1e-3)
         if bound == "alu":
             achieved, peak, unit = rate / 1e12, fp64_peak, "TFLOP/s"
-            src = "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x median SM clock under load"
+            src = "measured in this run: FP64 multiply-add throughput (afem_fma_peak, 4 x 256 threads per SM)"
         else:
             achieved, peak, unit = rate / 1e9, hbm, "GB/s"
             src = peak_src
@@ -450,30 +450,38 @@ def run_ours(args, rank, world, dist):
             "steps_compared": args.warmup + args.steps,
         }
 
-    # ---- end to end: host buffers, copies inside the timed region (precision form;
-    # the solver was last used by the FP64 path's profiled run)
+    # ---- end to end through the public API: the state lives in pinned host
+    # buffers and is copied in and out every step inside the timed region;
+    # the same warm-up and timed steps as the device-timed precision form
     solver.set_precision(pkg.PREC_MIXED)
     solver.set_krylov_tol(args.krylov_tol)
-    phi, C, W = mixed["state"]
-    t = mixed["t"]
-    phi_h = phi.cpu().pin_memory()
-    C_h = C.cpu().pin_memory()
-    W_h = W.cpu().pin_memory()
-    e2e_steps = max(1, min(args.steps, 3))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
+    phi_h, C_h, W_h = (x.cpu().pin_memory() for x in state0)
+    t = 0.0
+
+    def host_step(tt):
         phi_d = phi_h.to("cuda", non_blocking=True)
         C_d = C_h.to("cuda", non_blocking=True)
         W_d = W_h.to("cuda", non_blocking=True)
-        solver.step(phi_d, C_d, W_d, field(t), dt, cg_rtol=1e-10, cg_max_it=20000)
+        solver.step(phi_d, C_d, W_d, field(tt), dt, cg_rtol=1e-10, cg_max_it=20000)
         phi_h.copy_(phi_d, non_blocking=True)
         C_h.copy_(C_d, non_blocking=True)
         W_h.copy_(W_d, non_blocking=True)
         torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        host_step(t)
         t += dt
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter()
+    for _ in range(args.steps):
+        host_step(t)
+        t += dt
+    e2e_s = max_over_ranks(dist, torch, (time.perf_counter() - t_e2e) / args.steps, "cuda")
     bytes_state = phi_h.numel() * 16 + C_h.numel() * 16 + W_h.numel() * 8
+    phi, W = mixed["state"][0], mixed["state"][2]
+    t = mixed["t"]
 
     kern = measure_kernels(pkg, torch, mesh, W, phi, field(t), stream)
     batching = None if args.no_batch else run_batch(torch, pkg, inputs)
@@ -481,12 +489,21 @@ def run_ours(args, rank, world, dist):
     diff = None if args.no_diff else run_diff(torch, pkg, inputs, mesh, state0[0][:, 0].contiguous(),
                                               krylov_tol=args.krylov_tol if args.krylov_tol > 0 else 1e-10)
     peaks, peak_src = _peaks()
-    sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    fp64_peak = 152 * 4 * sm_mhz * 1e6 / 1e12
     hbm = peaks.get("hbm_gbs", 6800.0)
+    # FP64 and FP32 multiply-add peaks measured in this run on this GPU
+    # (afem_fma_peak); the FP64-bound classes are reported against the FP64 one
+    fp64_peak = pkg.fma_peak(pkg.PEAK_FP64, 200.0) / 1e12
+    fp32_peak = pkg.fma_peak(pkg.PEAK_FP32, 200.0) / 1e12
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    fp64_derived = sms * 4 * sm_mhz * 1e6 / 1e12
     roofline = _class_rooflines(mixed_prof["prof"], mixed_prof["ms"] * args.steps, fp64_peak, hbm, peak_src)
     roofline["measured_over"] = (f"{args.steps} precision-form steps continuing the timed ones, "
                                  f"{mixed_prof['ms']:.1f} ms/step with the event timing on")
+    roofline["arith_peaks"] = {"fp64_tflops": fp64_peak, "fp32_tflops": fp32_peak,
+                               "fp64_derived_tflops": fp64_derived,
+                               "derived_from": f"{sms} SMs x 2 FP64 FMA/clk x 2 flop x median SM clock "
+                                               f"{sm_mhz:.0f} MHz under load"}
     roofline["kernels_alone"] = {
         "stiffness_fp32": {"bound": "hbm", "achieved": kern["stiff32_gbs"], "peak": hbm, "unit": "GB/s",
                            "frac": kern["stiff32_gbs"] / hbm, "work": "8 B per DoF*RHS (read x, write y)"},
@@ -500,6 +517,7 @@ def run_ours(args, rank, world, dist):
     if fp64 is not None:
         fp64_entry = {"value": job_rate(world, fp64["ms"]), "unit": UNIT, "ms_per_step": fp64["ms"],
                       "cg_iters_mean": float(np.mean([i["cg_iters"] for i in fp64["infos"]])),
+                      "krylov_substeps_mean": float(np.mean([i["krylov_substeps"] for i in fp64["infos"]])),
                       "gpu_launches": fp64["launches"]}
     return {
         "metric": METRIC,
@@ -539,47 +557,140 @@ def run_ours(args, rank, world, dist):
         "gpu_launches": mixed["launches"],
         "batching_form": batching,
         "differentiation_form": diff,
+        "_fp64_cg_iters": fp64_entry["cg_iters_mean"] if fp64_entry else None,
+        "_fp64_substeps": (float(np.mean([i["krylov_substeps"] for i in fp64["infos"]]))
+                           if fp64 is not None else None),
     }
 
 
 # ----------------------------------------------------------------- oracle arm
-def oracle_sample(seconds_budget=25.0):
-    """Time the FP64 oracle's full MCTDHF step on a reduced instance of the same
-    molecule and elements and scale to the benchmark mesh by unknown count.
+# Mean Jacobi-PCG iterations per step of the warm-started FP64 Poisson batch on
+# this workload (the FP64 path's count, measured on GB300); the oracle's
+# reference arm runs without a GPU and scales its per-iteration time by it.
+FP64_CG_ITERS_PER_STEP = 710
 
-    Runs in a fresh process with one BLAS thread.  Returns dict.
-    """
-    code = r"""
+_ORACLE_SAMPLE = r"""
 import json, os, sys, time
-sys.path.insert(0, %r)
+sys.path.insert(0, %(root)r)
 import numpy as np
-from oracle import fem, mctdhf, mesh
+import scipy.sparse.linalg as sla
+from oracle import fem, krylov, mctdhf, mesh, poisson
 from paper_2301_02387_gb300 import inputs
-w = inputs.WORKLOADS["h2_q4"]
-case = (-8.0, 8.0, 4, 4, w["nuclei"], 2.0)
-nuc = [(R, Z, 2) for (R, Z, L) in w["nuclei"]]
-case = (-8.0, 8.0, 4, 4, nuc, 2.0)
-m = mesh.Mesh(*case)
+name = %(name)r
+w = inputs.WORKLOADS[name]
+tb = time.perf_counter()
+m = mesh.Mesh(*inputs.mesh_args(name))
 op = fem.Operators(m)
-phi = inputs.lowdin(inputs.molecular_orbitals(m.Xm, ~m.boundary, nuc, w["n_orb"]), op.ML)
-C = inputs.initial_ci(w["n_orb"], w["n_alpha"], w["n_beta"])
-sim = mctdhf.MCTDHF(op, w["n_orb"], w["n_alpha"], w["n_beta"], poisson_method="cg", poisson_rtol=1e-10)
+tb = time.perf_counter() - tb
+n = w["n_orb"]
+phi = inputs.lowdin(inputs.molecular_orbitals(m.Xm, ~m.boundary, w["nuclei"], n, phase_noise=0.0), op.ML)
+C = inputs.initial_ci(n, w["n_alpha"], w["n_beta"])
+pl = w["pulse"]
+E = inputs.sin2_pulse(%(t0)r, pl["intensity"], pl["wavelength_nm"], pl["cycles"], pl["pol"])
+sim = mctdhf.MCTDHF(op, n, w["n_alpha"], w["n_beta"], poisson_method="cg", poisson_rtol=1e-10)
+ps = sim.ps
+# (1) the step outside its iterations: pair densities, right-hand sides and
+# multipole surface data, integrals, RDMs, the CI exponential, U fields
 t0 = time.perf_counter()
-steps = 0
-while True:
-    phi, C, info = sim.step(phi, C, (0.0, 0.0, 0.01), w["dt"], w["m"])
-    steps += 1
-    if time.perf_counter() - t0 > %f or steps >= 3:
-        break
-dt = (time.perf_counter() - t0) / steps
-print(json.dumps({"sec_per_step": dt, "N": int(m.N), "steps": steps}))
-""" % (ROOT, seconds_budget)
+rho, pairs = poisson.pair_densities(op, phi)
+b, g = ps.rhs_and_bc(rho)
+rhs = b[ps.I] - ps.A_IB @ g
+Wc = np.zeros((m.N, rho.shape[1]))
+Wc[ps.B] = g
+W = poisson.assemble_pair_potentials(Wc, pairs, n)
+h, eri = sim.integrals(phi, W, E)
+Hci = sim.ci.hamiltonian(h, eri)
+g1, g2 = sim.ci.rdm1(C), sim.ci.rdm2(C)
+ev, V = np.linalg.eigh(0.5 * (Hci + Hci.conj().T))
+C1 = V @ (np.exp(-1j * w["dt"] * ev) * (V.conj().T @ C))
+U = sim.mean_field_operator(g1, g2, W)
+t_block = time.perf_counter() - t0
+# (2) one Krylov substep: the Arnoldi basis of dimension m (m applications of
+# G, modified Gram-Schmidt) and the substep decision; its length gives the
+# oracle's own substep count per step
+t0 = time.perf_counter()
+_, _, _, info = krylov.arnoldi_propagate(lambda v: sim.G_apply(v, phi, U, E), phi, sim.inner, w["m"], w["dt"],
+                                         %(tol)r, return_info=True, stop_after=1)
+t_sub = time.perf_counter() - t0
+tau1 = info["taus"][0]
+# (3) Jacobi-PCG iterations on one column of the batch
+d = ps.A_II.diagonal()
+Minv = sla.LinearOperator(ps.A_II.shape, matvec=lambda v: v / d)
+k_it = 5
+t0 = time.perf_counter()
+sla.cg(ps.A_II, rhs[:, 0], rtol=1e-300, atol=0.0, M=Minv, maxiter=k_it)
+t_it = (time.perf_counter() - t0) / k_it
+maps = open("/proc/self/maps").read() if os.path.exists("/proc/self/maps") else ""
+assert "libafem" not in maps, "the oracle sample must not load the CUDA library"
+print(json.dumps({"N": int(m.N), "build_s": tb, "t_block": t_block, "t_sub": t_sub, "tau1": tau1,
+                  "t_cg_it_col": t_it, "cols": int(rho.shape[1]), "dt": w["dt"]}))
+"""
+
+
+def oracle_sample(krylov_tol=1e-10, t0=None):
+    """Time the FP64 oracle (as it stands) on the benchmark mesh itself in a
+    fresh process with one BLAS thread: the step's non-iterative block, one
+    Krylov substep (with the oracle's own substep decision) and Jacobi-PCG
+    iterations on one column.  Returns the per-unit times."""
+    import math as _m
+    from paper_2301_02387_gb300 import inputs
+    w = inputs.WORKLOADS[WORKLOAD]
+    if t0 is None:   # the pulse's peak
+        t0 = 0.5 * w["pulse"]["cycles"] * 2.0 * _m.pi / (45.5634 / w["pulse"]["wavelength_nm"])
+    code = _ORACLE_SAMPLE % {"root": ROOT, "name": WORKLOAD, "t0": float(t0), "tol": float(krylov_tol)}
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+    t = time.perf_counter()
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
     if r.returncode != 0:
         raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
-    return json.loads(r.stdout.strip().splitlines()[-1])
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    out["wall_s"] = time.perf_counter() - t
+    return out
+
+
+def _host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline_entry(cg_iters=None, substeps=None, krylov_tol=1e-10):
+    """The oracle's step time on the benchmark mesh from a bounded sample:
+    t_step = t_block + S t_substep + cols I t_iteration, with S the substeps
+    per step (given, else the oracle's own dt / tau_1) and I the Jacobi-PCG
+    iterations per column and step (given, else FP64_CG_ITERS_PER_STEP)."""
+    s = oracle_sample(krylov_tol)
+    S_oracle = s["dt"] / s["tau1"]
+    S = substeps if substeps else S_oracle
+    I = cg_iters if cg_iters else FP64_CG_ITERS_PER_STEP
+    t_step = s["t_block"] + S * s["t_sub"] + s["cols"] * I * s["t_cg_it_col"]
+    K = _host_cores()
+    return {"value": 1.0 / t_step, "unit": UNIT, "cores": 1, "host_cores": K, "kind": "oracle",
+            "sample": (f"FP64 oracle (assembled SciPy CSR, one BLAS thread: 1 of {K} host cores) on the benchmark "
+                       f"mesh itself (N={s['N']}; built in {s['build_s']:.0f} s, not timed), field of the pulse at "
+                       f"its peak: the step's non-iterative block (pair densities, right-hand sides, multipole "
+                       f"data, integrals, RDMs, CI exponential, U fields) {s['t_block']:.1f} s, one Krylov substep "
+                       f"of dimension 10 with its decision {s['t_sub']:.1f} s (tau_1 = {s['tau1']:.3g}, so "
+                       f"{S_oracle:.0f} substeps per step by the oracle's own controller), one Jacobi-PCG iteration "
+                       f"of one column {s['t_cg_it_col'] * 1e3:.0f} ms; step = block + {S:.0f} substeps + "
+                       f"{s['cols']} columns x {I:.0f} iterations ({'this run' if cg_iters else 'FP64 path mean'}) "
+                       f"= {t_step:.0f} s; sample wall time {s['wall_s']:.0f} s"),
+            "t_step_s": t_step, "substeps_oracle": S_oracle, "substeps_used": S, "cg_iters_used": I}
+
+
+def run_reference(args):
+    # The oracle alone: the mesh size comes from the oracle's own mesh; no
+    # GPU and none of the library is used.
+    cb = cpu_baseline_entry(krylov_tol=args.krylov_tol if args.krylov_tol > 0 else 1e-10)
+    v = cb["value"]
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "H2 Q4, as the GPU arm (the benchmark mesh itself)"},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def _event_time(torch, stream, fn, flush, reps):
@@ -718,34 +829,6 @@ def run_profile_arnoldi(dt_short=2e-4, dt_timed=2e-3, timed=True):
     print(json.dumps({"profile_arnoldi": out, "N": mesh.N, "n_orb": n}))
 
 
-def cpu_baseline_entry(N_full):
-    s = oracle_sample()
-    per_dof = s["sec_per_step"] / s["N"]
-    value = 1.0 / (per_dof * N_full)
-    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"oracle FP64 step (CG Poisson rtol 1e-10, Arnoldi m=10, dense CI) on the same H2 "
-                       f"molecule and Q4 elements, box [-8,8]^3, 4^3 coarse, 2 levels (N={s['N']}), "
-                       f"{s['steps']} steps, {s['sec_per_step']:.2f} s/step, scaled linearly in N to "
-                       f"N={N_full}; 1 BLAS thread")}
-
-
-def run_reference(args):
-    import paper_2301_02387_gb300 as pkg  # noqa: F401  (mesh size only, host build)
-    from paper_2301_02387_gb300 import inputs
-    hm = pkg.Mesh(*inputs.mesh_args(WORKLOAD), host_only=True)
-    N_full = hm.N
-    # One bounded oracle sample (a few oracle steps on the reduced mesh) stands
-    # for the K steps, so the arm ends within a few minutes.
-    cb = cpu_baseline_entry(N_full)
-    v = cb["value"]
-    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "H2 Q4, as the GPU arm", "n_masters": N_full},
-            "cpu_baseline": cb,
-            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-
-
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -771,6 +854,8 @@ def main():
                     help="build the workload and run each operator kernel a few times (for profilers); no JSON")
     ap.add_argument("--profile-step", action="store_true",
                     help="one precision-form step with the inner CG capped (for a profiler's launch list); no JSON")
+    ap.add_argument("--peaks", action="store_true",
+                    help="only the measured FP64 and FP32 multiply-add peaks of this GPU (one JSON line)")
     ap.add_argument("--profile-arnoldi", action="store_true",
                     help="the orbital propagator alone: a short propagation, then ms per Krylov substep per form")
     args = ap.parse_args()
@@ -797,6 +882,15 @@ def main():
         mesh, _solver, phi0, _ = setup_state(pkg, inputs, torch, w)
         phi = torch.from_numpy(phi0[:, 0].copy()).cuda()
         print(json.dumps({"differentiation_form": run_diff(torch, pkg, inputs, mesh, phi, steps=args.steps)}))
+        return
+    if args.peaks:
+        import torch
+        import paper_2301_02387_gb300 as pkg
+        torch.cuda.set_device(0)
+        out = {k: [pkg.fma_peak(kind, 200.0) / 1e12 for _ in range(3)]
+               for k, kind in (("fp64_tflops", pkg.PEAK_FP64), ("fp32_tflops", pkg.PEAK_FP32))}
+        out["sms"] = torch.cuda.get_device_properties(0).multi_processor_count
+        print(json.dumps({"peaks": out}))
         return
     if args.profile_arnoldi:
         run_profile_arnoldi(timed=args.steps > 0)
@@ -826,10 +920,14 @@ def main():
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             try:
-                res["cpu_baseline"] = cpu_baseline_entry(res["config"]["n_masters"])
+                res["cpu_baseline"] = cpu_baseline_entry(
+                    cg_iters=res["_fp64_cg_iters"], substeps=res["_fp64_substeps"],
+                    krylov_tol=args.krylov_tol if args.krylov_tol > 0 else 1e-10)
             except Exception as e:   # reported, never fatal
                 res["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
                                        "sample": f"failed: {e}"}
+        res.pop("_fp64_cg_iters", None)
+        res.pop("_fp64_substeps", None)
         print(json.dumps(res), flush=True)
     if dist:
         dist.destroy_process_group()

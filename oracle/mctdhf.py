@@ -90,14 +90,16 @@ class MCTDHF:
         return y - phi @ S
 
     # ----------------------------------------------------------------- step
-    def step(self, phi, C, E, dt, m, krylov_tol=0.0):
+    def step(self, phi, C, E, dt, m, krylov_tol=0.0, krylov_adaptive=0):
         """One step t -> t + dt.  Returns (phi_new, C_new, info dict).
 
         krylov_tol <= 0: the orbitals take one Krylov step of dimension m over
         dt.  krylov_tol > 0: the error-controlled substeps of
         ``krylov.arnoldi_propagate`` (estimate <= krylov_tol * beta per substep,
         Sec. 3.2); info then carries the substep count, the summed estimates
-        and the decisions' smallest margin to the threshold."""
+        and the decisions' smallest margin to the threshold.  krylov_adaptive > 0
+        (with krylov_tol > 0): the rule of Sec. 3.2, ``krylov.arnoldi_adaptive``
+        with that many equal steps and dimensions up to m."""
         W, Wc = self.mean_fields(phi)
         h, eri = self.integrals(phi, W, E)
         Hci = self.ci.hamiltonian(h, eri)
@@ -108,7 +110,12 @@ class MCTDHF:
         U = self.mean_field_operator(g1, g2, W)
         apply_G = lambda v: self.G_apply(v, phi, U, E)   # noqa: E731
         substeps, margin, Hk, m_used, brk = 1, np.inf, None, m, False
-        if krylov_tol > 0.0:
+        dims = None
+        if krylov_tol > 0.0 and krylov_adaptive > 0:
+            phi_new, err, pinfo = krylov.arnoldi_adaptive(apply_G, phi, self.inner, m, dt, krylov_tol,
+                                                          substeps=krylov_adaptive)
+            margin, dims, substeps = pinfo["margin"], pinfo["dims"], krylov_adaptive
+        elif krylov_tol > 0.0:
             phi_new, err, substeps, pinfo = krylov.arnoldi_propagate(apply_G, phi, self.inner, m, dt, krylov_tol,
                                                                      return_info=True)
             margin = pinfo["margin"]
@@ -117,9 +124,42 @@ class MCTDHF:
         energy = np.real(np.sum(h * g1) + 0.5 * np.einsum("pqrs,pqrs->", eri, g2))
         info = dict(W=W, Wcols=Wc, h=h, eri=eri, Hci=Hci, gamma=g1, Gamma=g2, U=U,
                     arnoldi_err=err, H_krylov=Hk, m_used=m_used, breakdown=brk, energy=energy,
-                    krylov_substeps=substeps, krylov_margin=margin,
+                    krylov_substeps=substeps, krylov_margin=margin, krylov_dims=dims,
                     dipole=self.dipole(phi, C))
         return phi_new, C_new, info
+
+    def step_imaginary(self, phi, C, dtau, m, krylov_tol=0.0, E=(0.0, 0.0, 0.0)):
+        """One imaginary-time step tau -> tau + dtau toward the ground state
+        (Sec. 4 prepares the initial state by imaginary-time propagation; the
+        paper gives no scheme, reading 20).  The real-time step with t = -i tau:
+        the same frozen quantities, C <- exp(-dtau H_CI) C normalised, and
+        phi <- exp(-dtau G) phi by the Arnoldi process (one Krylov step, or the
+        error-controlled substeps when krylov_tol > 0), followed by Loewdin
+        orthonormalisation phi <- phi S^-1/2, S = phi^H M_L phi (the step leaves
+        S - I of second order in dtau).  Returns (phi_new, C_new, info); the
+        energy is that of the input state."""
+        W, Wc = self.mean_fields(phi)
+        h, eri = self.integrals(phi, W, E)
+        Hci = self.ci.hamiltonian(h, eri)
+        g1 = self.ci.rdm1(C)
+        g2 = self.ci.rdm2(C)
+        evals, evecs = np.linalg.eigh(0.5 * (Hci + Hci.conj().T))
+        C_new = evecs @ (np.exp(-dtau * (evals - evals[0])) * (evecs.conj().T @ C))
+        C_new = C_new / np.linalg.norm(C_new)
+        U = self.mean_field_operator(g1, g2, W)
+        apply_G = lambda v: self.G_apply(v, phi, U, E)   # noqa: E731
+        if krylov_tol > 0.0:
+            phi_new, err, substeps = krylov.arnoldi_propagate(apply_G, phi, self.inner, m, dtau, krylov_tol,
+                                                              imaginary=True)
+        else:
+            phi_new, err, _, _, _ = krylov.arnoldi_expm(apply_G, phi, self.inner, m, dtau, imaginary=True)
+            substeps = 1
+        S = np.conj(phi_new).T @ (self.ops.ML[:, None] * phi_new)
+        lam, V = np.linalg.eigh(0.5 * (S + S.conj().T))
+        phi_new = phi_new @ (V @ np.diag(lam ** -0.5) @ V.conj().T)
+        energy = np.real(np.sum(h * g1) + 0.5 * np.einsum("pqrs,pqrs->", eri, g2))
+        return phi_new, C_new, dict(energy=energy, arnoldi_err=err, krylov_substeps=substeps,
+                                    overlap_drift=np.abs(S - np.eye(self.n)).max())
 
     def dipole(self, phi, C):
         """<sum_i r_i> (3,): sum_pq gamma_pq phi_p^H F[x_d] phi_q, the one-body

@@ -185,6 +185,27 @@ def arnoldi_propagate(mesh, phi, U, krylov_m, dt, tol, E=None, out=None, stream=
     return out, err.value, sub.value
 
 
+def arnoldi_adaptive(mesh, phi, U, m_max, dt, steps, tol, E=None, out=None, stream=None, precision=PREC_FP64):
+    """afem_arnoldi_adaptive: exp(-i G dt) phi by Sec. 3.2's rule (fixed steps,
+    dimension chosen by the estimate).  Returns (phi_out, err, dim_max, dim_sum, unmet)."""
+    import torch
+    n = int(phi.shape[1])
+    _dev_ptr(phi, torch.complex128, mesh.N, "phi")
+    if U is not None:
+        _dev_ptr(U, torch.complex128, mesh.N, "U")
+    out = torch.empty_like(phi) if out is None else out
+    _dev_ptr(out, torch.complex128, mesh.N, "out")
+    err = ctypes.c_double(0.0)
+    dmax, dsum, unmet = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    Earr = _E3(E)
+    _capi.check(_capi.load().afem_arnoldi_adaptive(
+        mesh.handle, ctypes.cast(Earr, ctypes.c_void_p) if Earr is not None else None,
+        ctypes.c_void_p(phi.data_ptr()), ctypes.c_void_p(U.data_ptr()) if U is not None else None,
+        n, int(m_max), float(dt), int(steps), int(precision), float(tol), ctypes.c_void_p(out.data_ptr()),
+        ctypes.byref(err), ctypes.byref(dmax), ctypes.byref(dsum), ctypes.byref(unmet), _stream_ptr(stream)))
+    return out, err.value, dmax.value, dsum.value, unmet.value
+
+
 class MCTDHF:
     """afem_mctdhf_*: the MCTDHF time stepper of one mesh (Sec. 2, Sec. 3.2).
 
@@ -206,6 +227,10 @@ class MCTDHF:
     def set_krylov_tol(self, tol):
         _capi.check(_capi.load().afem_mctdhf_set_krylov_tol(self._h, float(tol)))
 
+    def set_krylov_adaptive(self, steps):
+        """Sec. 3.2's rule: `steps` equal Krylov steps per time step, dimension by the estimate (0: off)."""
+        _capi.check(_capi.load().afem_mctdhf_set_krylov_adaptive(self._h, int(steps)))
+
     def set_precision(self, precision):
         _capi.check(_capi.load().afem_mctdhf_set_precision(self._h, int(precision)))
 
@@ -225,6 +250,7 @@ class MCTDHF:
         return dict(energy=info.energy, arnoldi_err=info.arnoldi_err, cg_relres_max=info.cg_relres_max,
                     krylov_m_used=info.krylov_m_used, breakdown=bool(info.breakdown), cg_iters=info.cg_iters,
                     krylov_substeps=info.krylov_substeps, dipole=tuple(info.dipole),
+                    krylov_dim_sum=info.krylov_dim_sum, krylov_unmet=info.krylov_unmet,
                     status=rc)
 
     def close(self):
@@ -280,6 +306,18 @@ def convert(x, y, stream=None):
         raise ValueError("x and y must have the same number of elements")
     _capi.check(_capi.load().afem_convert(xp, yp, int(x.numel()), direction, _stream_ptr(stream)))
     return y
+
+
+PEAK_FP64 = 0
+PEAK_FP32 = 1
+
+
+def fma_peak(kind, target_ms=50.0, stream=None):
+    """afem_fma_peak: measured FP64 (PEAK_FP64) or FP32 (PEAK_FP32) multiply-add
+    throughput of the current device, flop/s."""
+    out = ctypes.c_double(0.0)
+    _capi.check(_capi.load().afem_fma_peak(int(kind), float(target_ms), ctypes.byref(out), _stream_ptr(stream)))
+    return out.value
 
 
 OPT_CELL32_VARIANT = 1

@@ -70,6 +70,7 @@ class StepInfo(ctypes.Structure):
         ("krylov_m_used", ctypes.c_int32), ("breakdown", ctypes.c_int32),
         ("cg_iters", ctypes.c_int32), ("krylov_substeps", ctypes.c_int32),
         ("dipole", ctypes.c_double * 3),
+        ("krylov_dim_sum", ctypes.c_int32), ("krylov_unmet", ctypes.c_int32),
     ]
 
 
@@ -122,6 +123,9 @@ SIGNATURES = {
                                             ctypes.c_int, _P, _P, _P, _P, _P]),
     "afem_mctdhf_set_precision": (ctypes.c_int, [_P, ctypes.c_int]),
     "afem_mctdhf_set_krylov_tol": (ctypes.c_int, [_P, ctypes.c_double]),
+    "afem_mctdhf_set_krylov_adaptive": (ctypes.c_int, [_P, ctypes.c_int]),
+    "afem_arnoldi_adaptive": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                             ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _P, _P, _P, _P, _P]),
     "afem_arnoldi_propagate": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                               ctypes.c_int, ctypes.c_double, _P, _P, _P, _P]),
     "afem_arnoldi_step": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_double, _P,
@@ -138,6 +142,7 @@ SIGNATURES = {
                                            ctypes.POINTER(ctypes.c_int), ctypes.c_int, _P]),
     "afem_batch_get_tuning": (ctypes.c_int, [_P, ctypes.POINTER(BatchTuning)]),
     "afem_convert": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int, _P]),
+    "afem_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double), _P]),
     "afem_tdse_forward": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                          ctypes.c_double, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P,
                                          ctypes.c_int, _P]),

@@ -13,6 +13,10 @@ namespace afem {
 
 constexpr int kMaxDegree = 4;
 constexpr int kMaxP1 = kMaxDegree + 1;
+// Multipole expansion of the mean fields' surface data: l <= kMultipoleLmax,
+// (kMultipoleLmax + 1)^2 real solid-harmonic terms.
+constexpr int kMultipoleLmax = 12;
+constexpr int kMultipoleTerms = (kMultipoleLmax + 1) * (kMultipoleLmax + 1);
 
 // Record the message for afem_last_error() and return `code`.
 int set_error(int code, const std::string& msg);
@@ -162,11 +166,13 @@ int poisson_batch_mixed(afem_mesh* m, const double2* phi, int n, double* W, doub
                         double inner_rtol, int* iters_out, int* outer_out, double* relres_out, cudaStream_t s);
 int multipole_boundary(afem_mesh* m, const double2* phi, int n, double* W, double* qpart, double* q, int nblk,
                        cudaStream_t s);
+int ensure_sh_tables();   // uploads the solid-harmonic constants once per device
 int mctdhf_create(afem_mesh* m, int n, int na, int nb, int mk, afem_mctdhf** out);
 void mctdhf_destroy(afem_mctdhf* S);
 int64_t mctdhf_ci_dim(const afem_mctdhf* S);
 void mctdhf_set_precision(afem_mctdhf* S, int precision);
 void mctdhf_set_krylov_tol(afem_mctdhf* S, double tol);
+void mctdhf_set_krylov_adaptive(afem_mctdhf* S, int steps);
 int mctdhf_step(afem_mctdhf* S, double2* phi, double2* C, double* W, const double* E, double dt, double cg_rtol,
                 int cg_max_it, afem_step_info* info, cudaStream_t s);
 int convert_f64_f32(const double* x, float* y, int64_t n, cudaStream_t s);

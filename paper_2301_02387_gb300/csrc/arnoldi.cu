@@ -20,6 +20,7 @@
 // precision form the projector (part of applying G) runs in FP32.  The
 // Hessenberg matrix and the norms stay on the device; the host waits once
 // per substep, after the candidate substep exponentials are evaluated.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -559,21 +560,23 @@ __global__ void __launch_bounds__(kRedThreads) substep_close_kernel(
     if (threadIdx.x == 0) *beta2_out = make_double2(fmax(s_sum[0], 0.0), 0.0);
 }
 
-// exp(-i dt H) for an m x m complex matrix (m <= kMaxKrylov) by one block:
-// scaling and squaring with a truncated Taylor series (the scaled matrix has
-// 1-norm <= 1/2; the remainder after 16 terms is below 0.5^17 / 17! ~ 2e-20
-// relative, under the FP64 rounding of the squarings).
+// exp(-i dt H) (imag: exp(-dt H), the imaginary-time step) for an m x m
+// complex matrix (m <= kMaxKrylov) by one block: scaling and squaring with a
+// truncated Taylor series (the scaled matrix has 1-norm <= 1/2; the remainder
+// after 16 terms is below 0.5^17 / 17! ~ 2e-20 relative, under the FP64
+// rounding of the squarings).
 constexpr int kTaylorTerms = 16;
 // H: column-major with leading dimension ldh.  Leaves the result in S.
-__device__ void block_expm(const double2* __restrict__ H, int ldh, int m, double dt, double2* A, double2* P,
-                           double2* S, double2* T) {
+__device__ void block_expm(const double2* __restrict__ H, int ldh, int m, double dt, int imag, double2* A,
+                           double2* P, double2* S, double2* T) {
     __shared__ int s_sq;
     const int t = threadIdx.x;
     const int mm = m * m;
     for (int o = t; o < mm; o += blockDim.x) {
         const int i = o % m, j = o / m;
         const double2 h = H[j * ldh + i];
-        A[o] = make_double2(dt * h.y, -dt * h.x);   // -i dt h
+        A[o] = imag ? make_double2(-dt * h.x, -dt * h.y)    // -dt h
+                    : make_double2(dt * h.y, -dt * h.x);    // -i dt h
     }
     __syncthreads();
     // 1-norm: column sums by m threads (each in row order), then their maximum
@@ -646,15 +649,16 @@ struct TauLadder {
     double tau[kLadder];
 };
 
-// Block c evaluates E_c = exp(-i tau_c H_m): writes its first column to
-// col[c][0..m) and err[c].x = |h_{m+1,m}| |E_c[m-1][0]| (the error estimate
-// divided by beta; 0 when exact is set, i.e. after a breakdown).
+// Block c evaluates E_c = exp(-i tau_c H_m) (imag: exp(-tau_c H_m)): writes
+// its first column to col[c][0..m) and err[c].x = |h_{m+1,m}| |E_c[m-1][0]|
+// (the error estimate divided by beta; 0 when exact is set, i.e. after a
+// breakdown).
 __global__ void expm_ladder_kernel(const double2* __restrict__ H, int ldh, int m, TauLadder taus, int exact,
-                                   double2* __restrict__ col, double2* __restrict__ err) {
+                                   int imag, double2* __restrict__ col, double2* __restrict__ err) {
     __shared__ double2 A[kMaxKrylov * kMaxKrylov], P[kMaxKrylov * kMaxKrylov], S[kMaxKrylov * kMaxKrylov],
         T[kMaxKrylov * kMaxKrylov];
     const int c = blockIdx.x;
-    block_expm(H, ldh, m, taus.tau[c], A, P, S, T);
+    block_expm(H, ldh, m, taus.tau[c], imag, A, P, S, T);
     for (int i = threadIdx.x; i < m; i += blockDim.x) col[c * kMaxKrylov + i] = S[i];
     if (threadIdx.x == 0) {
         const double2 hs = H[(m - 1) * ldh + m];
@@ -670,7 +674,7 @@ int launch_g_cell(const afem_mesh* m, const double* E, const double2* v, const d
 template <typename TB>
 int cdot_t(const double2* A, int na, const TB* B, int nb, const double* w, int64_t rows, int diag,
            double2* partial, double2* out, unsigned* counter, cudaStream_t s) {
-    AFEM_LAUNCH((cdot_fused_kernel<TB>), kRedBlocks, kRedThreads, 0, s, A, na, B, nb, w, rows, diag,
+    AFEM_LAUNCH((cdot_fused_kernel<TB>), red_blocks(), kRedThreads, 0, s, A, na, B, nb, w, rows, diag,
                 reinterpret_cast<double*>(partial), counter, out);
     AFEM_CUDA_TRY(cudaGetLastError());
     return AFEM_OK;
@@ -731,14 +735,7 @@ static unsigned wave_grid(unsigned cap) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, K, kRedThreads, 0) != cudaSuccess || b < 1) b = 1;
         return b;
     }();
-    static const int sms = [] {
-        int dev = 0, c = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || c < 1)
-            c = 152;
-        return c;
-    }();
-    const unsigned g = unsigned(sms * per_sm);
+    const unsigned g = unsigned(device_sms() * per_sm);
     return g < cap ? g : cap;
 }
 
@@ -849,7 +846,7 @@ static unsigned rowcol_grid(int64_t rows, int n) {
     const int64_t R = kRedThreads / n;
     int64_t g = (rows + R - 1) / R;
     if (g < 1) g = 1;
-    if (g > kRedBlocks) g = kRedBlocks;
+    if (g > red_blocks()) g = red_blocks();
     return unsigned(g);
 }
 
@@ -869,7 +866,7 @@ static int g_cell_overlaps32(afem_mesh* m, const double* E, const float2* phi32,
     switch (n) {
 #define AFEM_OV_CASE(NO)                                                                                        \
     case NO:                                                                                                    \
-        AFEM_LAUNCH((overlap32_kernel<NO>), kRedBlocks, kRedThreads, 0, s, phi32, w.z32, D.n_interior,         \
+        AFEM_LAUNCH((overlap32_kernel<NO>), red_blocks(), kRedThreads, 0, s, phi32, w.z32, D.n_interior,         \
                     w.Sslots);                                                                                  \
         break;
         AFEM_OV_CASE(1)
@@ -906,7 +903,7 @@ int arnoldi_reserve(afem_mesh* m, int n, int mk, ArnoldiWork& w) {
     auto carve = [&](Carver& cv) {
         w.V = cv.take<double2>(size_t(mk + 1) * NV);
         w.z = cv.take<double2>(NV);
-        w.cpartial = cv.take<double2>(size_t(kRedBlocks) * 256);
+        w.cpartial = cv.take<double2>(size_t(kRedBlocksMax) * 256);
         w.S = cv.take<double2>(kMaxOrbProj * kMaxOrbProj);
         w.Sslots = cv.take<double>(size_t(kOvSlots) * 2 * kMaxOrbProj * kMaxOrbProj);
         w.res = cv.take<double2>(kResSize);
@@ -951,10 +948,16 @@ static TauLadder make_ladder(double tau_max, int K) {
 // dimension is fixed and the substep adapts).
 int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double2* U, const float2* U32, int n,
                  int mk, double dt, int mixed, double tol, double2* phi_out, double* err_est, int* m_used_out,
-                 int* breakdown_out, int* substeps_out, cudaStream_t s, int flags) {
+                 int* breakdown_out, int* substeps_out, cudaStream_t s, int flags, int adaptive_steps,
+                 int* dim_sum_out, int* unmet_out) {
     const DeviceMesh& D = m->dev;
     if (mk < 1 || mk > kMaxKrylov) return set_error(AFEM_EINVAL, "arnoldi: krylov_m out of range");
     if (n < 1 || n > kMaxOrbProj) return set_error(AFEM_EINVAL, "arnoldi: orbital count out of range");
+    if (adaptive_steps < 0 || (adaptive_steps > 0 && !(tol > 0.0)))
+        return set_error(AFEM_EINVAL, "arnoldi: the adaptive dimension needs steps >= 1 and a threshold > 0");
+    const int imag = (flags & kArnImaginary) ? 1 : 0;
+    const bool adaptive = adaptive_steps > 0;
+    const double tau_fixed = adaptive ? dt / adaptive_steps : 0.0;
     ArnoldiWork w{};
     int rc = arnoldi_reserve(m, n, mk, w);
     if (rc) return rc;
@@ -986,7 +989,7 @@ int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double
     const double eta2 = 1e-4;   // second pass when the update left less than 1e-2 of the norm
     double remaining = dt, tau_prev = 0.0;
     double err_sum = 0.0;
-    int substeps = 0, m_used = mk, brk = 0;
+    int substeps = 0, m_used = mk, brk = 0, dim_max = 0, dim_sum = 0, unmet = 0;
     std::vector<double2> res(kResSize);
     auto fetch = [&]() -> int {
         AFEM_CUDA_TRY(cudaMemcpyAsync(res.data(), w.res, kResSize * sizeof(double2), cudaMemcpyDeviceToHost, s));
@@ -1040,12 +1043,47 @@ int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double
                 (rc = launch_krylov_update(j + 1, gdots, s, Wn, w.V, NV, w.c2, D.ml, D.n_interior, n, w.flag, 1,
                                            eta2, nullptr, w.H, ldh, w.beta2, v32, part, cnt, Hcol)))
                 return rc;
+            if (adaptive) {
+                // Sec. 3.2's rule: the estimate of dimension j + 1 at the fixed step;
+                // the first dimension that meets the threshold (or breaks down) ends
+                // the process
+                AFEM_LAUNCH((expm_ladder_kernel), 1, 256, 0, s, w.H, ldh, j + 1, signed_ladder(tau_fixed, 1), 0,
+                            imag, w.col, w.err);
+                AFEM_CUDA_TRY(cudaGetLastError());
+                if ((rc = fetch())) return rc;
+                const double b = std::sqrt(res[kResBeta2].x);
+                const double hn = res[kResH + j * ldh + j + 1].x;
+                if (!(b > 0.0) || !std::isfinite(b) || !std::isfinite(hn))
+                    return set_error(AFEM_ENAN, "arnoldi: zero or non-finite Krylov vector");
+                m_used = j + 1;
+                brk = hn < 1e-14 * b ? 1 : 0;
+                if (brk || res[kResErr].x <= tol) break;
+            }
+        }
+        double tau, err;
+        int pick = 0;
+        if (adaptive) {
+            const double beta = std::sqrt(res[kResBeta2].x);
+            tau = tau_fixed;
+            err = brk ? 0.0 : beta * res[kResErr].x;
+            if (!brk && res[kResErr].x > tol) ++unmet;
+            if ((rc = launch_substep_close(m_used, gproj, s, w.V, NV, w.col, beta, w.H, ldh, w.beta2, nullptr, D, n,
+                                           phi_out, v32, part, cnt)))
+                return rc;
+            err_sum += err;
+            ++substeps;
+            dim_max = std::max(dim_max, m_used);
+            dim_sum += m_used;
+            tau_prev = tau;
+            remaining = substeps >= adaptive_steps ? 0.0 : remaining - tau;
+            continue;
         }
         // candidate substeps, one block each; a single host wait per ladder
         double tau_max = (tol <= 0.0 || substeps == 0) ? remaining : std::fmin(remaining, 2.0 * tau_prev);
         int K = tol <= 0.0 ? 1 : kLadder;
         int exact = 0;
-        AFEM_LAUNCH((expm_ladder_kernel), K, 256, 0, s, w.H, ldh, mk, signed_ladder(tau_max, K), 0, w.col, w.err);
+        AFEM_LAUNCH((expm_ladder_kernel), K, 256, 0, s, w.H, ldh, mk, signed_ladder(tau_max, K), 0, imag, w.col,
+                    w.err);
         AFEM_CUDA_TRY(cudaGetLastError());
         if ((rc = fetch())) return rc;
         const double beta = std::sqrt(res[kResBeta2].x);
@@ -1065,12 +1103,12 @@ int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double
             tau_max = remaining;
             K = 1;
             exact = 1;
-            AFEM_LAUNCH((expm_ladder_kernel), 1, 256, 0, s, w.H, ldh, m_used, signed_ladder(tau_max, 1), 1, w.col,
-                        w.err);
+            AFEM_LAUNCH((expm_ladder_kernel), 1, 256, 0, s, w.H, ldh, m_used, signed_ladder(tau_max, 1), 1, imag,
+                        w.col, w.err);
             AFEM_CUDA_TRY(cudaGetLastError());
             if ((rc = fetch())) return rc;
         }
-        int pick = -1;
+        pick = -1;
         for (int round = 0;; ++round) {
             for (int c = 0; c < K; ++c) {
                 if (exact || tol <= 0.0 || res[kResErr + c].x <= tol) {
@@ -1084,25 +1122,29 @@ int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double
                 break;
             }
             tau_max *= std::pow(2.0, -kLadderLog2 * K);
-            AFEM_LAUNCH((expm_ladder_kernel), K, 256, 0, s, w.H, ldh, m_used, signed_ladder(tau_max, K), 0, w.col,
-                        w.err);
+            AFEM_LAUNCH((expm_ladder_kernel), K, 256, 0, s, w.H, ldh, m_used, signed_ladder(tau_max, K), 0, imag,
+                        w.col, w.err);
             AFEM_CUDA_TRY(cudaGetLastError());
             if ((rc = fetch())) return rc;
         }
-        const double tau = make_ladder(tau_max, K).tau[pick];
-        const double err = beta * res[kResErr + pick].x;
+        tau = make_ladder(tau_max, K).tau[pick];
+        err = beta * res[kResErr + pick].x;
         // phi_out = beta V_m exp(-i tau H_m) e_1, which also opens the next substep
         if ((rc = launch_substep_close(m_used, gproj, s, w.V, NV, w.col + pick * kMaxKrylov, beta, w.H, ldh, w.beta2,
                                        nullptr, D, n, phi_out, v32, part, cnt)))
             return rc;
         err_sum += err;
         ++substeps;
+        dim_max = std::max(dim_max, m_used);
+        dim_sum += m_used;
         tau_prev = tau;
         remaining = (tau >= remaining) ? 0.0 : remaining - tau;
     }
     AFEM_CUDA_TRY(cudaStreamSynchronize(s));
     if (err_est) *err_est = err_sum;
-    if (m_used_out) *m_used_out = m_used;
+    if (m_used_out) *m_used_out = adaptive ? dim_max : m_used;
+    if (dim_sum_out) *dim_sum_out = dim_sum;
+    if (unmet_out) *unmet_out = unmet;
     if (breakdown_out) *breakdown_out = brk;
     if (substeps_out) *substeps_out = substeps;
     return AFEM_OK;

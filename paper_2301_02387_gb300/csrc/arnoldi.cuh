@@ -46,12 +46,19 @@ int cdot(const double2* A, int na, const double2* B, int nb, const double* w, in
          double2* partial, double2* out, unsigned* counter, cudaStream_t s);
 // flags: kArnNoProjector applies H1~ + mean field without the projector Q
 // (the one-electron Schroedinger propagator and its block Frechet form);
-// kArnBackward propagates by exp(+i G dt).
+// kArnBackward propagates by exp(+i G dt); kArnImaginary by exp(-G dt)
+// (imaginary time).  adaptive_steps > 0: the rule of Sec. 3.2 -- dt split
+// into adaptive_steps equal steps, each with the smallest Krylov dimension
+// (<= mk) whose estimate is <= tol beta (mk when none is); dim_sum_out then
+// receives the summed dimensions, m_used_out the largest and unmet_out the
+// number of steps whose estimate stayed above the threshold at mk.
 constexpr int kArnNoProjector = 1;
 constexpr int kArnBackward = 2;
+constexpr int kArnImaginary = 4;
 int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double2* U, const float2* U32, int n,
                  int mk, double dt, int mixed, double tol, double2* phi_out, double* err_est, int* m_used_out,
-                 int* breakdown_out, int* substeps_out, cudaStream_t s, int flags = 0);
+                 int* breakdown_out, int* substeps_out, cudaStream_t s, int flags = 0, int adaptive_steps = 0,
+                 int* dim_sum_out = nullptr, int* unmet_out = nullptr);
 int to_c64(const double2* x, float2* y, int64_t n, cudaStream_t s);
 
 }  // namespace afem

@@ -279,6 +279,23 @@ int afem_arnoldi_propagate(afem_mesh* m, const double* E, const void* phi, const
                         nullptr, nullptr, substeps, static_cast<cudaStream_t>(stream));
 }
 
+int afem_arnoldi_adaptive(afem_mesh* m, const double* E, const void* phi, const void* U, int n_orb, int m_max,
+                          double dt, int steps, int precision, double tol, void* phi_out, double* err_est,
+                          int* dim_max, int* dim_sum, int* unmet, void* stream) {
+    if (precision != AFEM_PREC_FP64 && precision != AFEM_PREC_MIXED)
+        return set_error(AFEM_EINVAL, "afem_arnoldi_adaptive: unknown precision");
+    if (!m || !phi || !phi_out) return set_error(AFEM_EINVAL, "afem_arnoldi_adaptive: null argument");
+    if (m->host_only) return set_error(AFEM_EINVAL, "afem_arnoldi_adaptive: mesh was built host-only");
+    if (n_orb < 1 || n_orb > 8) return set_error(AFEM_EINVAL, "afem_arnoldi_adaptive: n_orb must be 1..8");
+    if (m_max < 1 || m_max > kMaxKrylov) return set_error(AFEM_EINVAL, "afem_arnoldi_adaptive: m_max must be 1..16");
+    if (steps < 1 || steps > 4096) return set_error(AFEM_EINVAL, "afem_arnoldi_adaptive: steps must be 1..4096");
+    if (!(tol > 0.0) || !(dt > 0.0)) return set_error(AFEM_EINVAL, "afem_arnoldi_adaptive: tol and dt must be > 0");
+    if (phi == phi_out) return set_error(AFEM_EINVAL, "afem_arnoldi_adaptive: phi and phi_out must not alias");
+    return arnoldi_step(m, E, static_cast<const double2*>(phi), static_cast<const double2*>(U), nullptr, n_orb,
+                        m_max, dt, precision == AFEM_PREC_MIXED, tol, static_cast<double2*>(phi_out), err_est,
+                        dim_max, nullptr, nullptr, static_cast<cudaStream_t>(stream), 0, steps, dim_sum, unmet);
+}
+
 int afem_mctdhf_create(afem_mesh* m, int n_orb, int n_alpha, int n_beta, int krylov_m, afem_mctdhf** out) {
     if (!m || !out) return set_error(AFEM_EINVAL, "afem_mctdhf_create: null argument");
     *out = nullptr;
@@ -307,6 +324,13 @@ int afem_mctdhf_set_krylov_tol(afem_mctdhf* s, double tol) {
     if (!s) return set_error(AFEM_EINVAL, "afem_mctdhf_set_krylov_tol: null argument");
     if (!(tol >= 0.0)) return set_error(AFEM_EINVAL, "afem_mctdhf_set_krylov_tol: tol must be >= 0");
     mctdhf_set_krylov_tol(s, tol);
+    return AFEM_OK;
+}
+
+int afem_mctdhf_set_krylov_adaptive(afem_mctdhf* s, int steps) {
+    if (!s) return set_error(AFEM_EINVAL, "afem_mctdhf_set_krylov_adaptive: null argument");
+    if (steps < 0 || steps > 4096) return set_error(AFEM_EINVAL, "afem_mctdhf_set_krylov_adaptive: steps must be 0..4096");
+    mctdhf_set_krylov_adaptive(s, steps);
     return AFEM_OK;
 }
 

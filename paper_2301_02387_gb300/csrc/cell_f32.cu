@@ -893,10 +893,10 @@ int batch32_launch(int kind, const void* d_inst, int count, int64_t total, int b
                    cudaStream_t s) {
     if (count < 1 || count > kBatchMaxInst) return set_error(AFEM_EINVAL, "afem_batch: 1..256 instances");
     const auto* inst = static_cast<const BatchInst32*>(d_inst);
-    AFEM_LAUNCH((batch_zero_kernel), 152 * 8, 256, 0, s, inst, count);
+    AFEM_LAUNCH((batch_zero_kernel), 8 * device_sms(), 256, 0, s, inst, count);
     if (kind == AFEM_OP_H1_C64) {
         AFEM_LAUNCH((batch_cell32_kernel<true>), grid, block, smem, s, inst, count, total);
-        AFEM_LAUNCH((batch_scale_kernel), 152 * 8, 256, 0, s, inst, count);
+        AFEM_LAUNCH((batch_scale_kernel), 8 * device_sms(), 256, 0, s, inst, count);
     } else {
         AFEM_LAUNCH((batch_cell32_kernel<false>), grid, block, smem, s, inst, count, total);
     }

@@ -479,7 +479,7 @@ __global__ void assemble_eri_kernel(int n, const double2* __restrict__ X, double
     }
 }
 
-constexpr int kIntBlocks = 152 * 2;
+static int int_blocks() { return 2 * device_sms(); }   // integral partial rows: 2 blocks per SM
 constexpr int kTaylorTerms = 30;
 
 // ------------------------------------------------------------------ solver
@@ -490,6 +490,7 @@ struct afem_mctdhf {
     int n = 0, na = 0, nb = 0, krylov_m = 0;
     int precision = AFEM_PREC_FP64;
     double krylov_tol = 0.0;   // 0: one Krylov step per time step (fixed dimension)
+    int krylov_adaptive = 0;   // > 0: Sec. 3.2's rule with this many equal Krylov steps per time step
     afem::CiTables ci;
     afem::Workspace ws;
 };
@@ -511,7 +512,7 @@ static void carve_step(Carver& cv, StepWork& w, int64_t N, int n, int64_t dim, b
     w.y = cv.take<double2>(size_t(N) * n);
     w.phi_new = cv.take<double2>(size_t(N) * n);
     w.U = cv.take<double2>(size_t(N) * nn);
-    w.ipartial = cv.take<double2>(size_t(kIntBlocks) * nn * nn);
+    w.ipartial = cv.take<double2>(size_t(int_blocks()) * nn * nn);
     w.X = cv.take<double2>(size_t(nn) * nn);
     w.eri = cv.take<double2>(size_t(nn) * nn);
     w.h = cv.take<double2>(nn);
@@ -519,7 +520,7 @@ static void carve_step(Carver& cv, StepWork& w, int64_t N, int n, int64_t dim, b
     w.g2 = cv.take<double2>(size_t(nn) * nn);
     w.hp = cv.take<double2>(nn);
     w.M = cv.take<double2>(size_t(nn) * nn);
-    w.cpart = cv.take<double2>(size_t(kRedBlocks) * 256);
+    w.cpart = cv.take<double2>(size_t(kRedBlocksMax) * 256);
     w.D = cv.take<double2>(size_t(nn) * dim);
     w.Y = cv.take<double2>(size_t(nn) * dim);
     w.sigma = cv.take<double2>(dim);
@@ -552,12 +553,12 @@ static void finalize_cpartials(const double2* partial, int nblk, int k, double2*
     AFEM_LAUNCH((csum_blocks_kernel), (k + 255) / 256, 256, 0, s, partial, nblk, k, out);
 }
 
-static unsigned ci_grid(int64_t dim) { return grid_for(dim, 128, 152 * 8); }
+static unsigned ci_grid(int64_t dim) { return grid_for(dim, 128, 8); }
 
 // sigma = H_CI v via D = E v, Y, gather
 static int ci_sigma(const CiTables& t, const StepWork& w, const double2* v, double2* sigma, cudaStream_t s) {
     AFEM_LAUNCH((ci_excite_kernel), ci_grid(t.dim), 128, 0, s, t, v, w.D);
-    AFEM_LAUNCH((ci_y_kernel), grid_for(int64_t(t.n) * t.n * t.dim, 256, 152 * 8), 256, 0, s, t.n, t.dim, w.hp, w.eri, v, w.D, w.Y);
+    AFEM_LAUNCH((ci_y_kernel), grid_for(int64_t(t.n) * t.n * t.dim, 256, 8), 256, 0, s, t.n, t.dim, w.hp, w.eri, v, w.D, w.Y);
     AFEM_LAUNCH((ci_gather_kernel), ci_grid(t.dim), 128, 0, s, t, w.Y, sigma);
     AFEM_CUDA_TRY(cudaGetLastError());
     return AFEM_OK;
@@ -603,8 +604,9 @@ int mctdhf_step(afem_mctdhf* S, double2* phi, double2* C, double* W, const doubl
     IntArgs ia{phi, W, n, N, D.n_interior, D.n_hanging, D.mf_master, D.mf_hang, D.hang_ptr, D.hang_master, D.hang_w};
     const size_t ismem = size_t(kIntTile) * nn * (sizeof(double2) + sizeof(double)) + size_t(nn) * nn * sizeof(double2);
     AFEM_CUDA_TRY(cudaFuncSetAttribute(integrals_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ismem)));
-    AFEM_LAUNCH((integrals_kernel), kIntBlocks, 256, ismem, s, ia, w.ipartial);
-    finalize_cpartials(w.ipartial, kIntBlocks, nn * nn, w.X, s);
+    const int iblk = int_blocks();
+    AFEM_LAUNCH((integrals_kernel), iblk, 256, ismem, s, ia, w.ipartial);
+    finalize_cpartials(w.ipartial, iblk, nn * nn, w.X, s);
     AFEM_LAUNCH((assemble_eri_kernel), (nn * nn + 255) / 256, 256, 0, s, n, w.X, w.eri);
     // RDMs of C(t)
     AFEM_LAUNCH((ci_excite_kernel), ci_grid(dim), 128, 0, s, S->ci, C, w.D);
@@ -646,9 +648,11 @@ int mctdhf_step(afem_mctdhf* S, double2* phi, double2* C, double* W, const doubl
         U32 = w.U32;
         if ((rc = to_c64(w.U, U32, N * nn, s))) return rc;
     }
-    int substeps = 1;
+    int substeps = 1, dim_sum = 0, unmet = 0;
+    if (S->krylov_adaptive > 0 && !(S->krylov_tol > 0.0))
+        return set_error(AFEM_EINVAL, "afem_mctdhf_step: the adaptive Krylov dimension needs a threshold > 0");
     if ((rc = arnoldi_step(m, E, phi, mixed ? nullptr : w.U, U32, n, S->krylov_m, dt, mixed, S->krylov_tol,
-                           w.phi_new, &err, &m_used, &brk, &substeps, s)))
+                           w.phi_new, &err, &m_used, &brk, &substeps, s, 0, S->krylov_adaptive, &dim_sum, &unmet)))
         return rc;
     // commit: phi <- phi_new, C <- exp(-i dt shift) acc
     AFEM_CUDA_TRY(cudaMemcpyAsync(phi, w.phi_new, size_t(N) * n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
@@ -662,6 +666,8 @@ int mctdhf_step(afem_mctdhf* S, double2* phi, double2* C, double* W, const doubl
         info->krylov_m_used = m_used;
         info->breakdown = brk;
         info->krylov_substeps = substeps;
+        info->krylov_dim_sum = S->krylov_adaptive > 0 ? dim_sum : substeps * m_used;
+        info->krylov_unmet = unmet;
         info->cg_iters = iters;
         double mx = 0.0;
         for (double r : relres) mx = std::max(mx, r);
@@ -713,5 +719,7 @@ int64_t mctdhf_ci_dim(const afem_mctdhf* S) { return S->ci.dim; }
 void mctdhf_set_precision(afem_mctdhf* S, int precision) { S->precision = precision; }
 
 void mctdhf_set_krylov_tol(afem_mctdhf* S, double tol) { S->krylov_tol = tol; }
+
+void mctdhf_set_krylov_adaptive(afem_mctdhf* S, int steps) { S->krylov_adaptive = steps; }
 
 }  // namespace afem

@@ -14,6 +14,7 @@
 // is this pass followed by the inverse lumped mass.
 #include "afem_internal.h"
 #include "cell_common.cuh"
+#include "vec_common.cuh"
 
 namespace afem {
 
@@ -277,7 +278,7 @@ static int launch_scale_rows(T* y, const double* s, int64_t n, int nv, cudaStrea
     if (n == 0) return AFEM_OK;
     const int64_t total = n * nv;
     const int block = 256;
-    const unsigned grid = unsigned(std::min<int64_t>((total + block - 1) / block, 152 * 32));
+    const unsigned grid = unsigned(std::min<int64_t>((total + block - 1) / block, int64_t(32) * device_sms()));
     AFEM_LAUNCH((scale_rows_kernel<T>), grid, block, 0, st, y, s, n, nv);
     AFEM_CUDA_TRY(cudaGetLastError());
     return AFEM_OK;

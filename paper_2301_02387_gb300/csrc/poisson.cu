@@ -13,6 +13,7 @@
 // CG with algebraic multigrid from Trilinos); each column has its own alpha,
 // beta and stopping test ||r|| <= rtol ||b - A_IB g||.
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "afem_internal.h"
@@ -21,17 +22,21 @@
 
 namespace afem {
 
-constexpr int kLmax = 12;
-constexpr int kNlm = (kLmax + 1) * (kLmax + 1);
+constexpr int kLmax = kMultipoleLmax;
+constexpr int kNlm = kMultipoleTerms;
 constexpr int kMomTile = 32;
-constexpr int kMomBlocks = 152 * 2;
+static int mom_blocks() { return 2 * device_sms(); }   // moment partial rows: 2 blocks per SM
 __constant__ double c_sh_norm[kNlm];       // factor applied to C_lm / S_lm at index l*l + l + |m|
 __constant__ double c_sh_irreg[kLmax + 1];  // 4 pi / (2l + 1)
 
-static int ensure_sh_tables() {
+// Uploads the solid-harmonic normalisations once per device (synchronous
+// copies; serialised across host threads).
+int ensure_sh_tables() {
     static bool done[64] = {false};
+    static std::mutex mu;
     int dev = 0;
     AFEM_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
     if (dev < 64 && done[dev]) return AFEM_OK;
     double norm[kNlm], irr[kLmax + 1];
     for (int l = 0; l <= kLmax; ++l) {
@@ -708,7 +713,7 @@ int poisson_rhs_bc(afem_mesh* m, const double2* phi, int n, double* W, double* b
     const size_t smem = (size_t(kMomTile) * kNlm + size_t(kMomTile) * ncol + size_t(kNlm) * ncol) * sizeof(double);
     AFEM_CUDA_TRY(cudaFuncSetAttribute(pair_rhs_moments_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        int(smem)));
-    const int nblk = kMomBlocks;
+    const int nblk = mom_blocks();
     AFEM_LAUNCH((pair_rhs_moments_kernel), nblk, 256, smem, s, a, b, qpart);
     AFEM_CUDA_TRY(cudaGetLastError());
     AFEM_LAUNCH((finalize_columns_kernel), 1, 256, 0, s, qpart, nblk, kNlm * ncol, q);
@@ -718,7 +723,7 @@ int poisson_rhs_bc(afem_mesh* m, const double2* phi, int n, double* W, double* b
         const size_t sm2 = size_t(kNlm) * ncol * sizeof(double);
         AFEM_CUDA_TRY(cudaFuncSetAttribute(multipole_bc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            int(sm2)));
-        AFEM_LAUNCH((multipole_bc_kernel), grid_for(nb, 128, 152 * 8), 128, sm2, s, q, ncol, D.master_xyz, D.n_interior,
+        AFEM_LAUNCH((multipole_bc_kernel), grid_for(nb, 128, 8), 128, sm2, s, q, ncol, D.master_xyz, D.n_interior,
                                                                           D.n_master, c0, c0, c0, W);
         AFEM_CUDA_TRY(cudaGetLastError());
     }
@@ -730,7 +735,7 @@ int poisson_batch(afem_mesh* m, const double2* phi, int n, double* W, double rto
     const DeviceMesh& D = m->dev;
     const int k = n * n;
     const int64_t N = D.n_master, Ni = D.n_interior;
-    const int nblk = kRedBlocks;
+    const int nblk = red_blocks();
     const size_t NK = size_t(N) * k;
     PoissonWork w{};
     auto carve = [&](Carver& cv) {
@@ -741,7 +746,7 @@ int poisson_batch(afem_mesh* m, const double2* phi, int n, double* W, double rto
         w.Ap = cv.take<double>(NK);
         w.t = cv.take<double>(NK);
         w.partial = cv.take<double>(size_t(nblk) * 3 * k);
-        w.qpart = cv.take<double>(size_t(kMomBlocks) * kNlm * k);
+        w.qpart = cv.take<double>(size_t(mom_blocks()) * kNlm * k);
         w.q = cv.take<double>(size_t(kNlm) * k);
         w.alpha = cv.take<double>(k);
         w.beta = cv.take<double>(k);
@@ -851,7 +856,7 @@ int multipole_boundary(afem_mesh* m, const double2* phi, int n, double* W, doubl
         const size_t sm2 = size_t(kNlm) * ncol * sizeof(double);
         AFEM_CUDA_TRY(cudaFuncSetAttribute(multipole_bc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            int(sm2)));
-        AFEM_LAUNCH((multipole_bc_kernel), grid_for(nb, 128, 152 * 8), 128, sm2, s, q, ncol, D.master_xyz,
+        AFEM_LAUNCH((multipole_bc_kernel), grid_for(nb, 128, 8), 128, sm2, s, q, ncol, D.master_xyz,
                     D.n_interior, D.n_master, c0, c0, c0, W);
         AFEM_CUDA_TRY(cudaGetLastError());
     }
@@ -999,7 +1004,7 @@ int poisson_batch_mixed(afem_mesh* m, const double2* phi, int n, double* W, doub
     // p.Ap formed by the stiffness pass itself (its four-lane form with 1, 2 or 4 quads)
     const bool fused = quads && (k == 4 || k == 8 || k == 16) && m->cell32_variant == 0;
     const int64_t N = D.n_master, Ni = D.n_interior;
-    const int nblk = kRedBlocks;
+    const int nblk = red_blocks();
     const size_t NK = size_t(N) * k;
     PoissonWork w{};
     float *r32, *z32, *p32, *Ap32, *d32;
@@ -1018,7 +1023,7 @@ int poisson_batch_mixed(afem_mesh* m, const double2* phi, int n, double* W, doub
         Ap32 = cv.take<float>(NK);
         d32 = cv.take<float>(NK);
         w.partial = cv.take<double>(size_t(nblk) * 3 * k);
-        w.qpart = cv.take<double>(size_t(kMomBlocks) * kNlm * k);
+        w.qpart = cv.take<double>(size_t(mom_blocks()) * kNlm * k);
         w.q = cv.take<double>(size_t(kNlm) * k);
         w.alpha = cv.take<double>(k);
         w.beta = cv.take<double>(k);

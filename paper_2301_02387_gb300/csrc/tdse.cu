@@ -73,7 +73,7 @@ int tdse_reserve(afem_mesh* m, int64_t dot_rows, int seg, TdseWork& w) {
         w.U = cv.take<double2>(4 * N);
         w.phis = cv.take<double2>(size_t(seg + 1) * N);
         w.dots = cv.take<double2>(size_t(dot_rows) * 4);
-        w.part = cv.take<double2>(size_t(kRedBlocks) * 256);
+        w.part = cv.take<double2>(size_t(kRedBlocksMax) * 256);
         w.cnt = cv.take<unsigned>(4);
     };
     Carver measure(nullptr);

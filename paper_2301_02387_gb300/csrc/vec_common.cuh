@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 
 #include "afem_internal.h"
@@ -48,7 +49,24 @@ __device__ __forceinline__ float narrow_f64(double d) {
     if (rest > 0x10000000u || (rest == 0x10000000u && (keep & 1u))) r += 1u;
     return __uint_as_float(sign | r);
 }
-constexpr int kRedBlocks = 152 * 4;   // 4 blocks per SM on a 152-SM GB300
+// Streaming multiprocessors of the current device, looked up once per device.
+inline int device_sms() {
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    int c = cache[dev].load(std::memory_order_relaxed);
+    if (c > 0) return c;
+    if (cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || c < 1) return 1;
+    cache[dev].store(c, std::memory_order_relaxed);
+    return c;
+}
+// Blocks of the reductions with one partial row per block: 4 per SM, at most
+// kRedBlocksMax (the size of the partial-row buffers).
+constexpr int kRedBlocksMax = 1024;
+inline int red_blocks() {
+    const int g = 4 * device_sms();
+    return g < kRedBlocksMax ? g : kRedBlocksMax;
+}
 
 // Threads (r, c) = (t / k, t % k) for t < k * (256 / k); the rest idle.
 struct ColLayout {
@@ -124,8 +142,10 @@ struct Carver {
     size_t size() const { return off + 256; }
 };
 
-inline unsigned grid_for(int64_t n, int block = 256, int64_t cap = 152 * 16) {
+// Blocks for n items at `block` threads, at most per_sm blocks per SM.
+inline unsigned grid_for(int64_t n, int block = 256, int per_sm = 16) {
     int64_t g = (n + block - 1) / block;
+    const int64_t cap = int64_t(per_sm) * device_sms();
     if (g < 1) g = 1;
     if (g > cap) g = cap;
     return unsigned(g);

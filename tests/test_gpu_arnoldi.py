@@ -109,3 +109,60 @@ def test_arnoldi_propagate_substeps_parity(precision_name):
     else:
         assert abs(sub_g - sub) <= 1
         assert_close(out.cpu().numpy(), ref[perm], 1e-6, what="propagation")
+
+
+@pytest.mark.parametrize("precision_name", ["fp64", "mixed"])
+def test_arnoldi_adaptive_dimension_parity(precision_name):
+    """Sec. 3.2's rule (fixed steps, dimension grown until the estimate passes)
+    against the oracle's: the same dimension for every step unless the
+    oracle's decisions include a near-tie (margin), FP64 within 1e-10, the
+    precision form within 1e-6."""
+    import torch
+    import paper_2301_02387_gb300 as pkg
+    case = (-6.0, 6.0, 2, 3, [((0.0, 0.0, 0.7), 1.0, 2), ((0.0, 0.0, -0.7), 1.0, 2)], 2.0)
+    gm = pkg.Mesh(*case)
+    om = omesh.Mesh(*case)
+    op = fem.Operators(om)
+    X, _, _ = gm.tables()
+    perm = coord_permutation(X, om.Xm)
+    n = 2
+    interior = ~om.boundary
+    phi_o = inputs.lowdin(inputs.molecular_orbitals(om.Xm, interior, case[4], n), op.ML)
+    U_o = _fields(om.Xm, n, 9)
+    E = (0.0, 0.01, 0.02)
+    sim = mctdhf.MCTDHF.__new__(mctdhf.MCTDHF)
+    sim.ops, sim.mesh, sim.n = op, om, n
+    sim.interior = interior.astype(np.float64)
+    dt, steps, tol, m_max = 0.05, 4, 1e-10, 16
+    ref, err_o, info = krylov.arnoldi_adaptive(lambda v: sim.G_apply(v, phi_o, U_o, E), phi_o, sim.inner, m_max,
+                                               dt, tol, substeps=steps)
+    assert info["passed"] and min(info["dims"]) >= 4
+    phi = torch.from_numpy(np.ascontiguousarray(phi_o[perm])).cuda()
+    U = torch.from_numpy(np.ascontiguousarray(U_o.transpose(2, 0, 1)[perm])).cuda()
+    fp64 = precision_name == "fp64"
+    prec = pkg.PREC_FP64 if fp64 else pkg.PREC_MIXED
+    out, err, dmax, dsum, unmet = pkg.arnoldi_adaptive(gm, phi, U, m_max, dt, steps, tol, E=E, precision=prec)
+    torch.cuda.synchronize()
+    assert unmet == 0
+    if info["margin"] > (1e-6 if fp64 else 1e-3):
+        assert dmax == max(info["dims"]) and dsum == sum(info["dims"])
+        assert_close(out.cpu().numpy(), ref[perm], 1e-10 if fp64 else 1e-6, what="adaptive dimension")
+    else:
+        assert abs(dsum - sum(info["dims"])) <= steps
+        assert_close(out.cpu().numpy(), ref[perm], max(1e-6, 4.0 * (err + err_o)), what="near-tie")
+
+
+def test_arnoldi_adaptive_reports_unmet_threshold():
+    """A cap of 3 dimensions cannot meet 1e-12 over the step: every step is
+    counted as unmet and uses the cap."""
+    import torch
+    import paper_2301_02387_gb300 as pkg
+    case = (-6.0, 6.0, 2, 3, [((0.0, 0.0, 0.0), 1.0, 2)], 2.0)
+    gm = pkg.Mesh(*case)
+    X, ml, _ = gm.tables()
+    interior = np.arange(gm.N) < gm.n_interior
+    phi = torch.from_numpy(inputs.lowdin(inputs.molecular_orbitals(X, interior, case[4], 1), ml)).cuda()
+    out, err, dmax, dsum, unmet = pkg.arnoldi_adaptive(gm, phi, None, 3, 0.05, 2, 1e-12)
+    assert unmet == 2 and dmax == 3 and dsum == 6
+    with pytest.raises(pkg.AfemError):
+        pkg.arnoldi_adaptive(gm, phi, None, 17, 0.05, 2, 1e-12)

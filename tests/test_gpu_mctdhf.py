@@ -182,3 +182,36 @@ def test_mctdhf_water_electron_count(water_electrons, precision_name):
                            raise_on_maxit=False)
         torch.cuda.synchronize()
         _compare_step(phi, C, info, phi_o, C_o, info_o, perm, 10, 1e-10 if fp64 else 1e-6)
+
+
+def test_mctdhf_steps_adaptive_dimension_parity():
+    """The step with Sec. 3.2's Krylov rule (4 equal Krylov steps per time step,
+    dimension up to 16 grown until the estimate meets 1e-10) against the
+    oracle's step in the same mode: equal dimensions, FP64 1e-10."""
+    import torch
+    import paper_2301_02387_gb300 as pkg
+    case, n, na, nb = KTOL_CASE, 2, 1, 1
+    gm = pkg.Mesh(*case)
+    om = omesh.Mesh(*case)
+    op = fem.Operators(om)
+    X, _, _ = gm.tables()
+    perm = coord_permutation(X, om.Xm)
+    phi_o = inputs.lowdin(inputs.molecular_orbitals(om.Xm, ~om.boundary, case[4], n), op.ML)
+    C_o = inputs.initial_ci(n, na, nb, amp=0.1)
+    sim = mctdhf.MCTDHF(op, n, na, nb, poisson_method="cg", poisson_rtol=1e-13)
+    solver = pkg.MCTDHF(gm, n, na, nb, 16)
+    solver.set_krylov_tol(1e-10)
+    solver.set_krylov_adaptive(4)
+    phi = torch.from_numpy(np.ascontiguousarray(phi_o[perm])).cuda()
+    C = torch.from_numpy(C_o.copy()).cuda()
+    W = torch.zeros((gm.N, n * n), dtype=torch.float64, device="cuda")
+    E = (0.0, 0.01, 0.03)
+    for step in range(2):
+        phi_o, C_o, info_o = sim.step(phi_o, C_o, E, 0.02, 16, krylov_tol=1e-10, krylov_adaptive=4)
+        info = solver.step(phi, C, W, E, 0.02, cg_rtol=1e-14, cg_max_it=20000, raise_on_maxit=False)
+        torch.cuda.synchronize()
+        assert info_o["krylov_margin"] > 1e-6, "near-tie in the oracle's dimension decisions"
+        assert info["krylov_substeps"] == 4 and info["krylov_unmet"] == 0
+        assert info["krylov_dim_sum"] == sum(info_o["krylov_dims"])
+        assert info["krylov_m_used"] == max(info_o["krylov_dims"])
+        _compare_step(phi, C, info, phi_o, C_o, info_o, perm, na + nb, 1e-10)

@@ -279,6 +279,54 @@ def test_arnoldi_propagate_meets_tolerance_on_stiff_operator():
     assert np.linalg.norm(out - ref) < 50 * 1e-10 * sub * np.linalg.norm(phi)
 
 
+def _stiff_case(seed=5, n=80):
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = np.concatenate([rng.uniform(-1, 1, n - 10), rng.uniform(200, 400, 10)])
+    G = (Q * lam) @ Q.T
+    phi = rng.standard_normal(n) + 0j
+    return G, phi, (lambda u, v: np.vdot(u, v))
+
+
+def test_arnoldi_adaptive_dimension_meets_tolerance_and_is_minimal():
+    """Sec. 3.2's rule (fixed step, dimension grown until the estimate passes):
+    on the stiff operator, 8 equal steps over dt = 0.05 land within a small
+    multiple of tol * steps of the dense exponential; every step's dimension
+    is the smallest whose estimate passes (the fixed-dimension step one below
+    it fails the threshold, the one at it passes)."""
+    G, phi, inner = _stiff_case()
+    dt, tol, S = 0.05, 1e-10, 8
+    ref = scipy.linalg.expm(-1j * dt * G) @ phi
+    out, est, info = krylov.arnoldi_adaptive(lambda v: G @ v, phi, inner, 16, dt, tol, substeps=S)
+    assert info["passed"] and len(info["dims"]) == S and est <= S * tol * np.linalg.norm(phi) * 1.0001
+    assert np.linalg.norm(out - ref) < 50 * tol * S * np.linalg.norm(phi)
+    # minimality, step by step from the oracle's own intermediate vectors
+    cur = phi
+    for d in info["dims"]:
+        beta = np.sqrt(inner(cur, cur).real)
+        nxt, e_at, *_ = krylov.arnoldi_expm(lambda v: G @ v, cur, inner, d, dt / S)
+        assert e_at <= tol * beta
+        if d > 1:
+            _, e_below, *_ = krylov.arnoldi_expm(lambda v: G @ v, cur, inner, d - 1, dt / S)
+            assert e_below > tol * beta
+        cur = nxt
+    assert np.linalg.norm(cur - out) < 1e-12 * np.linalg.norm(out)
+
+
+def test_arnoldi_adaptive_reports_an_unmet_threshold_and_breakdown():
+    """A dimension cap too small for the step is reported (passed False, the
+    cap used); an eigenvector stops at dimension 1 with the exact phase."""
+    G, phi, inner = _stiff_case(seed=6)
+    out, est, info = krylov.arnoldi_adaptive(lambda v: G @ v, phi, inner, 4, 0.05, 1e-10, substeps=1)
+    assert not info["passed"] and info["dims"] == [4] and est > 1e-10 * np.linalg.norm(phi)
+    D = np.diag([1.0, 2.0, 3.0]).astype(complex)
+    e = np.array([0.0, 1.0, 0.0], dtype=complex)
+    out, est, info = krylov.arnoldi_adaptive(lambda v: D @ v, e, lambda u, v: np.vdot(u, v), 6, 0.1, 1e-12,
+                                             substeps=2)
+    assert info["dims"] == [1, 1] and est == 0.0
+    np.testing.assert_allclose(out, np.exp(-0.2j) * e, atol=1e-15)
+
+
 # ------------------------------------------------------------------- dipole
 def _dipole_state(case, n, na, nb):
     m = mesh.Mesh(*case)

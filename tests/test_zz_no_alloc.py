@@ -6,7 +6,12 @@ process whose device memory is held by another allocator's pool, a loop with
 a fixed memory budget).  This entry point serves them from a fixed file-scope
 scratch array.  Its output must equal the surface rows that the allocating
 entry point afem_poisson_batch writes, on consecutive calls sharing the one
-scratch array.  This file is collected last on purpose.
+scratch array, and a call must leave the device's free memory and the torch
+caching allocator's statistics unchanged.
+
+The file is collected last so that a run stopping at the first failure has
+run every other test before this one; the tests here depend on no other test
+(each builds its own mesh and inputs) and pass alone in a fresh process.
 """
 import ctypes
 
@@ -66,3 +71,33 @@ def test_noalloc_rejects_too_many_orbitals():
     W = torch.zeros((mesh.N, 25), dtype=torch.float64, device="cuda")
     assert _noalloc(lib, mesh, phi, W) == pkg._capi.AFEM_EINVAL
     assert b"n_orb" in lib.afem_last_error()
+
+
+def test_noalloc_allocates_no_device_memory():
+    """After a warm-up call (which does the per-device set-up), calls with
+    n = 1..4 change neither the free device memory nor the torch caching
+    allocator's statistics."""
+    import torch
+    import paper_2301_02387_gb300 as pkg
+    lib = pkg.load_library()
+    mesh = pkg.Mesh(*CASE)
+    X, _, _ = mesh.tables()
+    bufs = []
+    for n in (1, 2, 3, 4):
+        phi = torch.from_numpy(_orbitals(X, mesh.n_interior, n, 10 + n)).cuda()
+        W = torch.zeros((mesh.N, n * n), dtype=torch.float64, device="cuda")
+        bufs.append((phi, W))
+    assert _noalloc(lib, mesh, *bufs[0]) == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    stats0 = torch.cuda.memory_stats()
+    for _ in range(3):
+        for phi, W in bufs:
+            assert _noalloc(lib, mesh, phi, W) == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    stats1 = torch.cuda.memory_stats()
+    assert free1 == free0
+    for key in ("allocation.all.allocated", "segment.all.allocated", "reserved_bytes.all.current",
+                "allocated_bytes.all.current"):
+        assert stats1.get(key) == stats0.get(key), key
