@@ -236,6 +236,81 @@ def run_batch(torch, pkg, inputs, reps=10, count=64):
                       "1-3 nuclei Z 1..8 within 3 bohr, 2-8 orbitals (even), |E| 0.01..0.08"}
 
 
+def run_water(torch, pkg, inputs, args):
+    """The water workload at full size (O + 2 H, [-50,50]^3, 32^3 coarse, 6 / 5
+    levels, Q4; 8 orbitals, 5 alpha + 5 beta electrons, 3,136 determinants,
+    64 Poisson columns; 800 nm 4-cycle sin^2 at 2e14 W/cm^2, dt = 0.01,
+    m = 10, Krylov threshold per substep): the plain FP64 path and the
+    precision form from the same seeded state over --warmup + --steps steps,
+    CUDA-event timed over the last --steps, and the precision form's
+    difference from the FP64 path after them."""
+    import numpy as np
+    name = "water_q4"
+    w = inputs.WORKLOADS[name]
+    t0 = time.perf_counter()
+    mesh = pkg.Mesh(*inputs.mesh_args(name))
+    build_s = time.perf_counter() - t0
+    X, ML, _ = mesh.tables()
+    interior = np.arange(mesh.N) < mesh.n_interior
+    n = w["n_orb"]
+    phi0 = inputs.lowdin(inputs.molecular_orbitals(X, interior, w["nuclei"], n, phase_noise=0.0), ML)
+    C0 = inputs.initial_ci(n, w["n_alpha"], w["n_beta"])
+    pulse, dt = w["pulse"], w["dt"]
+
+    def field(tt):
+        return inputs.sin2_pulse(tt, pulse["intensity"], pulse["wavelength_nm"], pulse["cycles"], pulse["pol"])
+
+    stream = torch.cuda.current_stream()
+    ml = torch.from_numpy(ML).cuda()
+    res = {}
+    for fname, prec in (("fp64", pkg.PREC_FP64), ("mixed", pkg.PREC_MIXED)):
+        solver = pkg.MCTDHF(mesh, n, w["n_alpha"], w["n_beta"], w["m"])
+        solver.set_precision(prec)
+        solver.set_krylov_tol(args.krylov_tol if args.krylov_tol > 0 else 1e-10)
+        phi = torch.from_numpy(phi0.copy()).cuda()
+        C = torch.from_numpy(C0.copy()).cuda()
+        W = torch.zeros((mesh.N, n * n), dtype=torch.float64, device="cuda")
+        t = 0.0
+        for _ in range(args.warmup):
+            solver.step(phi, C, W, field(t), dt, cg_rtol=1e-10, cg_max_it=20000)
+            t += dt
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        infos = []
+        a.record(stream)
+        for _ in range(args.steps):
+            infos.append(solver.step(phi, C, W, field(t), dt, cg_rtol=1e-10, cg_max_it=20000))
+            t += dt
+        b.record(stream)
+        torch.cuda.synchronize()
+        res[fname] = dict(ms=a.elapsed_time(b) / args.steps, infos=infos, phi=phi, C=C)
+        solver.close()
+    p64, p32 = res["fp64"]["phi"], res["mixed"]["phi"]
+    nrm = lambda ph: (torch.conj(ph) * ph).real.mul(ml[:, None]).sum(dim=0).cpu().numpy()   # noqa: E731
+    i64, i32 = res["fp64"]["infos"][-1], res["mixed"]["infos"][-1]
+    entry = {}
+    for fname in ("fp64", "mixed"):
+        inf = res[fname]["infos"]
+        entry[fname] = {"ms_per_step": res[fname]["ms"], "steps_per_s": 1000.0 / res[fname]["ms"],
+                        "krylov_substeps_mean": float(np.mean([i["krylov_substeps"] for i in inf])),
+                        "cg_iters_mean": float(np.mean([i["cg_iters"] for i in inf])),
+                        "energy_last": inf[-1]["energy"]}
+    return {"workload": "water-shaped O + 2 H (1.81 bohr, 104.5 deg), [-50,50]^3, 32^3 coarse, 6 levels at O and "
+                        "5 at each H, Q4; 8 orbitals, 5a+5b (3136 determinants), 64 Poisson columns; 800 nm 4-cycle "
+                        "sin^2 2e14 W/cm^2, dt=0.01, m=10, Krylov threshold 1e-10 per substep",
+            "n_masters": mesh.N, "n_cells": mesh.n_cells, "n_hanging": mesh.n_hanging, "mesh_build_s": build_s,
+            "warmup": args.warmup, "steps": args.steps, "fp64_path": entry["fp64"], "precision_form": entry["mixed"],
+            "speedup_vs_fp64_path": res["fp64"]["ms"] / res["mixed"]["ms"],
+            "accuracy_vs_fp64_path": {
+                "orbital_norms_max_rel": float(np.max(np.abs(nrm(p32) - nrm(p64)) / np.abs(nrm(p64)))),
+                "energy_rel": abs(i32["energy"] - i64["energy"]) / abs(i64["energy"]),
+                "orbitals_rel_l2": float(torch.linalg.norm(p32 - p64).item() / torch.linalg.norm(p64).item()),
+                "ci_rel_l2": float(torch.linalg.norm(res["mixed"]["C"] - res["fp64"]["C"]).item()
+                                   / torch.linalg.norm(res["fp64"]["C"]).item()),
+                "dipole_max_abs_diff": float(np.max(np.abs(np.subtract(i32["dipole"], i64["dipole"])))),
+                "steps_compared": args.warmup + args.steps}}
+
+
 def run_diff(torch, pkg, inputs, mesh, phi_col, steps=6, every=3, krylov_tol=1e-10):
     """Differentiation form on the full mesh (one-electron limit: one orbital,
     no projector or mean field): the forward pass with checkpoints, the
@@ -293,16 +368,16 @@ def run_diff(torch, pkg, inputs, mesh, phi_col, steps=6, every=3, krylov_tol=1e-
                         "field of the 800 nm sin^2 pulse from its peak, dt=0.02, e = z"}
 
 
-def run_precision_spectrum(torch, pkg, inputs, steps=300):
+def run_precision_spectrum(torch, pkg, inputs, steps=300, name=WORKLOAD, box=8.0, levels=2, nc=4):
     """The precision form against the FP64 path over a longer window on a
-    reduced mesh of the same molecule and elements (box [-8,8]^3, 4^3 coarse,
-    2 levels; the oracle's timing instance): both forms step from the same
-    state through the pulse from its peak; the <sum r_i> traces and the
-    spectra |FFT(a)|^2 of the acceleration a (second differences, Hann
-    window) are compared."""
+    reduced mesh of the same molecule and elements (box [-box,box]^3, nc^3
+    coarse, `levels` levels per nucleus): both forms step from the same state
+    through the pulse from its peak; the <sum r_i> traces and the spectra
+    |FFT(a)|^2 of the acceleration a (second differences, Hann window) are
+    compared."""
     import numpy as np
-    w = inputs.WORKLOADS[WORKLOAD]
-    args = (-8.0, 8.0, 4, w["p"], [(R, Z, 2) for (R, Z, _L) in w["nuclei"]], w["c"])
+    w = inputs.WORKLOADS[name]
+    args = (-box, box, nc, w["p"], [(R, Z, levels) for (R, Z, _L) in w["nuclei"]], w["c"])
     mesh = pkg.Mesh(*args)
     X, ml, _ = mesh.tables()
     interior = np.arange(mesh.N) < mesh.n_interior
@@ -338,13 +413,101 @@ def run_precision_spectrum(torch, pkg, inputs, steps=300):
     S64, S32 = spectrum(d64), spectrum(d32)
     freq = 2.0 * np.pi * np.arange(len(S64)) / ((len(d64) - 2) * dt) / omega
     band = freq <= 30.0
-    return {"workload": f"H2, Q4, [-8,8]^3, 4^3 coarse, 2 levels (N={mesh.N}); {steps} steps of dt={dt} from "
-                        "the 800 nm pulse's peak; FP64 path vs precision form from the same state",
+    return {"workload": f"{name} molecule, Q4, [-{box:g},{box:g}]^3, {nc}^3 coarse, {levels} levels (N={mesh.N}); "
+                        f"{n} orbitals, {w['n_alpha']}a+{w['n_beta']}b; {steps} steps of dt={dt} from the "
+                        f"{pulse['wavelength_nm']:g} nm pulse's peak; FP64 path vs precision form from the same state",
             "dipole_z_max_abs_diff": float(np.max(np.abs(d32 - d64))),
             "dipole_z_rel": float(np.max(np.abs(d32 - d64)) / np.max(np.abs(d64))),
             "spectrum_rel_l2_to_30_harmonics": float(np.linalg.norm(S32[band] - S64[band]) / np.linalg.norm(S64[band])),
             "spectrum": "|FFT(a)|^2, a = second differences of <sum z_i>, Hann window",
             "ms_per_step": ms}
+
+
+def run_krylov_rules(torch, pkg, mesh, state0, field, dt, args, ref_state, n_orb, n_alpha, n_beta):
+    """The precision form over the headline's warm-up and timed steps with
+    other Krylov rules: fixed dimension 12 and 15 with the substep ladder, and
+    Sec. 3.2's rule (fixed Krylov steps, dimension up to 16 grown until the
+    estimate meets the threshold; the step count is 1.25 x the ladder's at
+    dimension 15).  Per rule: ms per step, substeps, G applications per step
+    and the orbitals' difference from the headline run."""
+    import math as _m
+    out = {}
+    stream = torch.cuda.current_stream()
+    sub15 = None
+    for name, mk, adaptive in (("ladder_m12", 12, 0), ("ladder_m15", 15, 0), ("sec32_adaptive_m16", 16, -1)):
+        solver = pkg.MCTDHF(mesh, n_orb, n_alpha, n_beta, mk)
+        solver.set_precision(pkg.PREC_MIXED)
+        solver.set_krylov_tol(args.krylov_tol if args.krylov_tol > 0 else 1e-10)
+        steps_sec32 = 0
+        if adaptive < 0:
+            steps_sec32 = int(_m.ceil(1.25 * (sub15 or 1)))
+            solver.set_krylov_adaptive(steps_sec32)
+        phi, C, W = (x.clone() for x in state0)
+        t = 0.0
+        for _ in range(args.warmup):
+            solver.step(phi, C, W, field(t), dt, cg_rtol=1e-10, cg_max_it=20000)
+            t += dt
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        infos = []
+        a.record(stream)
+        for _ in range(args.steps):
+            infos.append(solver.step(phi, C, W, field(t), dt, cg_rtol=1e-10, cg_max_it=20000))
+            t += dt
+        b.record(stream)
+        torch.cuda.synchronize()
+        sub = sum(i["krylov_substeps"] for i in infos) / len(infos)
+        if name == "ladder_m15":
+            sub15 = sub
+        out[name] = {"krylov_m": mk, "ms_per_step": a.elapsed_time(b) / args.steps,
+                     "substeps_per_step": sub,
+                     "g_applications_per_step": sum(i["krylov_dim_sum"] for i in infos) / len(infos),
+                     "largest_dimension": max(i["krylov_m_used"] for i in infos),
+                     "unmet_steps": sum(i["krylov_unmet"] for i in infos),
+                     "orbitals_rel_diff_vs_headline": float(torch.linalg.norm(phi - ref_state[0]).item()
+                                                            / torch.linalg.norm(ref_state[0]).item())}
+        if steps_sec32:
+            out[name]["krylov_steps_per_time_step"] = steps_sec32
+        solver.close()
+    return out
+
+
+def run_poisson_solvers(torch, pkg, mesh, phi, W_warm, restore, reps=3):
+    """The Poisson batch of the live state (the workload's orbitals) alone,
+    with the Jacobi and the multigrid preconditioner, in both forms: CUDA-event
+    time per solve from the previous step's mean fields (the step's warm start)
+    and from zero, and the iterations (float32 inner ones in the precision
+    form)."""
+    import numpy as np
+    stream = torch.cuda.current_stream()
+    out = {}
+    for sname, sval in (("jacobi", pkg.POISSON_JACOBI), ("multigrid", pkg.POISSON_MULTIGRID)):
+        pkg.mesh_set_option(mesh, pkg.OPT_POISSON_SOLVER, sval)
+        for fname, prec in (("fp64", pkg.PREC_FP64), ("mixed", pkg.PREC_MIXED)):
+            ent = {}
+            for start in ("warm", "cold"):
+                W = W_warm.clone()
+                pkg.poisson_batch(mesh, phi, W, rtol=1e-10, max_it=20000, warm_start=start == "warm",
+                                  precision=prec)   # first solve builds the hierarchy
+                ts, its = [], []
+                for _ in range(reps):
+                    W.copy_(W_warm)
+                    torch.cuda.synchronize()
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    it, rel, rc = pkg.poisson_batch(mesh, phi, W, rtol=1e-10, max_it=20000,
+                                                    warm_start=start == "warm", precision=prec)
+                    b.record(stream)
+                    torch.cuda.synchronize()
+                    ts.append(a.elapsed_time(b))
+                    its.append(it)
+                ent[start] = {"ms": float(np.median(ts)), "iterations": int(np.median(its)),
+                              "max_relres": float(np.max(rel))}
+            out.setdefault(sname, {})[fname] = ent
+    pkg.mesh_set_option(mesh, pkg.OPT_POISSON_SOLVER, restore)
+    out["workload"] = ("the workload's 16 pair mean fields of its orbitals after the timed steps, rtol 1e-10; "
+                       "warm: from the previous step's fields")
+    return out
 
 
 # Kernel classes of the library's event timing: name, bound, unit of work.
@@ -403,6 +566,8 @@ def run_ours(args, rank, world, dist):
     torch.cuda.set_device(dev)
     w = inputs.WORKLOADS[WORKLOAD]
     mesh, solver, phi0, C0 = setup_state(pkg, inputs, torch, w)
+    if args.poisson == "multigrid":
+        pkg.mesh_set_option(mesh, pkg.OPT_POISSON_SOLVER, pkg.POISSON_MULTIGRID)
     n, N = w["n_orb"], mesh.N
     X, ML, _ = mesh.tables()
     state0 = (torch.from_numpy(phi0).cuda(), torch.from_numpy(C0).cuda(),
@@ -484,6 +649,17 @@ def run_ours(args, rank, world, dist):
     t = mixed["t"]
 
     kern = measure_kernels(pkg, torch, mesh, W, phi, field(t), stream)
+    psolv = None if args.no_poisson_solvers else run_poisson_solvers(
+        torch, pkg, mesh, phi, W, pkg.POISSON_MULTIGRID if args.poisson == "multigrid" else pkg.POISSON_JACOBI)
+    rules = None
+    if not args.no_rules:
+        rules = run_krylov_rules(torch, pkg, mesh, state0, field, dt, args, mixed["state"], n, w["n_alpha"],
+                                 w["n_beta"])
+        rules["headline_ladder_m10"] = {"krylov_m": w["m"], "ms_per_step": mixed["ms"],
+                                        "substeps_per_step": float(np.mean([i["krylov_substeps"]
+                                                                            for i in mixed["infos"]])),
+                                        "g_applications_per_step": float(np.mean([i["krylov_dim_sum"]
+                                                                                  for i in mixed["infos"]]))}
     batching = None if args.no_batch else run_batch(torch, pkg, inputs)
     spec = None if args.no_spectrum else run_precision_spectrum(torch, pkg, inputs)
     diff = None if args.no_diff else run_diff(torch, pkg, inputs, mesh, state0[0][:, 0].contiguous(),
@@ -534,7 +710,8 @@ def run_ours(args, rank, world, dist):
         "data": "synthetic (seeded Gaussian orbitals on the nuclei, random-phase CI vector)",
         "config": {"workload": "H2 R=1.4 bohr, [-40,40]^3, 20^3 coarse, 5 levels/nucleus, Q4, "
                                "4 orbitals (1a+1b), 800nm 3-cycle sin^2 1e14 W/cm^2, dt=0.02, m=10, rtol=1e-10, "
-                               f"Krylov error threshold {args.krylov_tol:g} per substep",
+                               f"Krylov error threshold {args.krylov_tol:g} per substep, Poisson CG with the "
+                               f"{args.poisson} preconditioner",
                    "n_masters": mesh.N, "n_cells": mesh.n_cells, "n_hanging": mesh.n_hanging,
                    "cache": "working set (Krylov basis, CG batch) larger than L2; no flush",
                    "parallelism": f"replicas x{world}"},
@@ -557,6 +734,8 @@ def run_ours(args, rank, world, dist):
         "gpu_launches": mixed["launches"],
         "batching_form": batching,
         "differentiation_form": diff,
+        "krylov_rules": rules,
+        "poisson_solvers": psolv,
         "_fp64_cg_iters": fp64_entry["cg_iters_mean"] if fp64_entry else None,
         "_fp64_substeps": (float(np.mean([i["krylov_substeps"] for i in fp64["infos"]]))
                            if fp64 is not None else None),
@@ -791,6 +970,35 @@ def run_profile_step(inner_iters=48):
     print("profile-step done", info)
 
 
+def run_profile_gs(nc=16, dt=1e-4):
+    """The precision form's Krylov propagation on a reduced coarse grid of the
+    benchmark molecule (nc^3 coarse cells, 5 levels per nucleus, Q4, 4
+    orbitals: each basis vector ~20 MB, 10 of them well above L2), a few
+    substeps: the small case on which the Gram-Schmidt kernels' DRAM traffic
+    is captured and then scaled to the benchmark mesh by N."""
+    import numpy as np
+    import torch
+    import paper_2301_02387_gb300 as pkg
+    from paper_2301_02387_gb300 import inputs
+    torch.cuda.set_device(0)
+    w = inputs.WORKLOADS[WORKLOAD]
+    mesh = pkg.Mesh(w["lo"], w["hi"], nc, w["p"], w["nuclei"], w["c"])
+    X, ml, _ = mesh.tables()
+    n = w["n_orb"]
+    interior = np.arange(mesh.N) < mesh.n_interior
+    phi = torch.from_numpy(inputs.lowdin(inputs.molecular_orbitals(X, interior, w["nuclei"], n, phase_noise=0.0),
+                                         ml)).cuda()
+    r = np.sqrt(np.sum(X ** 2, axis=1))
+    U = np.zeros((mesh.N, n, n), dtype=np.complex128)
+    for q in range(n):
+        U[:, q, q] = 1.0 / np.sqrt(r * r + 0.3 * (q + 1))
+    Ud = torch.from_numpy(U.reshape(mesh.N, n * n)).cuda()
+    _, err, sub = pkg.arnoldi_propagate(mesh, phi, Ud, w["m"], dt, 1e-10, E=(0.0, 0.0, 0.01),
+                                        precision=pkg.PREC_MIXED)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_gs": {"N": mesh.N, "n_orb": n, "substeps": sub, "err": err}}))
+
+
 def run_profile_arnoldi(dt_short=2e-4, dt_timed=2e-3, timed=True):
     """The orbital propagator alone on the workload mesh (mean fields frozen to
     a smooth synthetic field): one short error-controlled propagation (a few
@@ -840,6 +1048,15 @@ def main():
     ap.add_argument("--batch-only", action="store_true",
                     help="only the batching-form measurement (its JSON sub-entry), for profiling")
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiation-form measurement")
+    ap.add_argument("--no-poisson-solvers", action="store_true",
+                    help="skip the Poisson batch alone with the Jacobi and the multigrid preconditioner")
+    ap.add_argument("--poisson", default="jacobi", choices=["jacobi", "multigrid"],
+                    help="preconditioner of the Poisson batch in the timed steps")
+    ap.add_argument("--no-rules", action="store_true",
+                    help="skip the precision form under other Krylov rules (dimension 12, 15, Sec. 3.2's rule)")
+    ap.add_argument("--water", action="store_true",
+                    help="only the water workload (8 orbitals, 5+5 electrons): FP64 path vs precision form over "
+                         "--warmup + --steps steps (its JSON sub-entry)")
     ap.add_argument("--no-spectrum", action="store_true",
                     help="skip the precision form's dipole-trace and spectrum comparison on the reduced mesh")
     ap.add_argument("--spectrum-only", action="store_true",
@@ -854,6 +1071,9 @@ def main():
                     help="build the workload and run each operator kernel a few times (for profilers); no JSON")
     ap.add_argument("--profile-step", action="store_true",
                     help="one precision-form step with the inner CG capped (for a profiler's launch list); no JSON")
+    ap.add_argument("--profile-gs", action="store_true",
+                    help="a short precision-form propagation on a reduced coarse grid (the Gram-Schmidt kernels' "
+                         "small capture case); one JSON line")
     ap.add_argument("--peaks", action="store_true",
                     help="only the measured FP64 and FP32 multiply-add peaks of this GPU (one JSON line)")
     ap.add_argument("--profile-arnoldi", action="store_true",
@@ -883,6 +1103,17 @@ def main():
         phi = torch.from_numpy(phi0[:, 0].copy()).cuda()
         print(json.dumps({"differentiation_form": run_diff(torch, pkg, inputs, mesh, phi, steps=args.steps)}))
         return
+    if args.water:
+        import torch
+        import paper_2301_02387_gb300 as pkg
+        from paper_2301_02387_gb300 import inputs
+        torch.cuda.set_device(0)
+        out = {"water_workload": run_water(torch, pkg, inputs, args)}
+        if not args.no_spectrum:
+            out["water_precision_spectrum"] = run_precision_spectrum(torch, pkg, inputs, steps=300, name="water_q4",
+                                                                     box=8.0, levels=2, nc=4)
+        print(json.dumps(out))
+        return
     if args.peaks:
         import torch
         import paper_2301_02387_gb300 as pkg
@@ -894,6 +1125,9 @@ def main():
         return
     if args.profile_arnoldi:
         run_profile_arnoldi(timed=args.steps > 0)
+        return
+    if args.profile_gs:
+        run_profile_gs()
         return
     if args.kernels_only:
         run_kernels_only()

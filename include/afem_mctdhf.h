@@ -174,6 +174,21 @@ int afem_mesh_destroy(afem_mesh* mesh);
  * line by line with direction-wise accumulation in shared memory.  Both give
  * the same operator.  Host only. */
 #define AFEM_OPT_CELL32_VARIANT 1
+/* AFEM_OPT_POISSON_SOLVER selects the preconditioner of the batched Poisson
+ * CG (Sec. 3.1 solves the mean fields by CG with algebraic multigrid):
+ * AFEM_POISSON_JACOBI (default) or AFEM_POISSON_MULTIGRID, a geometric
+ * multigrid V-cycle over the mesh at degrees p, p/2, .., 1 and then degree 1
+ * on the octrees with the nuclear refinement levels capped at L-1, .., 0
+ * (exact interpolation between the nested spaces, restriction its transpose,
+ * Chebyshev-Jacobi smoothing of degree 3, a degree-30 Chebyshev polynomial on
+ * the uniform coarse grid).  The FP64 form runs CG with the float64 V-cycle;
+ * the precision form runs float64 defect correction whose corrections are
+ * float32 CG iterations with the float32 V-cycle.  The hierarchy (its meshes,
+ * transfer tables and eigenvalue estimates) is built on the first solve and
+ * kept by the mesh.  Same stopping test, same result to rtol. */
+#define AFEM_OPT_POISSON_SOLVER 2
+#define AFEM_POISSON_JACOBI 0
+#define AFEM_POISSON_MULTIGRID 1
 int afem_mesh_set_option(afem_mesh* mesh, int option, int value);
 
 /* Sizes of the mesh (host struct, caller-owned). */
@@ -197,6 +212,9 @@ int afem_mesh_tables(const afem_mesh* mesh, double* coords, double* lumped_mass,
 #define AFEM_OP_FORCE 5      /* y = M_L^{-1} F[e.f] x, complex128, Dirichlet, f = -grad V the nuclear
                                 force on an electron (0 at a support point on a nucleus): the
                                 potential part of the Ehrenfest acceleration along e (passed as E) */
+#define AFEM_OP_H1_VG 6      /* y = M_L^{-1} H1~(A) x, complex128, Dirichlet: the velocity-gauge one-body
+                                Hamiltonian of Sec. 2 with the vector potential A passed as E */
+#define AFEM_OP_H1_VG_C64 7  /* as AFEM_OP_H1_VG in complex64 (precision form) */
 
 /* Matrix-free operator application on n_vec vectors at once (Sec. 3.1).
  *
@@ -206,6 +224,13 @@ int afem_mesh_tables(const afem_mesh* mesh, double* coords, double* lumped_mass,
  *   arrays.  Surface entries of x are treated as zero and surface entries of
  *   y are written as zero (orbitals vanish on the box surface).  E is a host
  *   array of 3 doubles (field in a.u.); NULL means zero field.
+ * AFEM_OP_H1_VG: H1~(A) = 1/2 A + F[V] - i sum_d A_d G_d, the velocity gauge
+ *   of Sec. 2 (H1 = -1/2 Laplacian + V - i A(t) . grad; the A^2/2 term is a
+ *   global phase and is left out), with G_d = C^T (sum_K P_K^T h_K^2
+ *   (W (x) W (x) S)_d P_K) C the skew-symmetric form of int b_k d_d b_l,
+ *   S = (Dw - Dw^T) / 2, Dw[i][j] = w_i L_j'(xi_i): it equals the plain form on
+ *   conforming cells and keeps H1~(A) Hermitian across hanging faces.  A is
+ *   passed in E (NULL: A = 0).
  * AFEM_OP_STIFF: A = C^T (sum_K P_K^T A_K P_K) C with the GLL cell stiffness
  *   A_K; x and y are float64 [N][n_vec] device arrays; E is ignored.
  * n_vec: 1..64.  x and y must not overlap.  Asynchronous on `stream`. */
@@ -389,6 +414,26 @@ int afem_mctdhf_set_krylov_tol(afem_mctdhf* solver, double tol);
  * tol from afem_mctdhf_set_krylov_tol, which must then be > 0); 0 (default)
  * returns to the rule of afem_mctdhf_set_krylov_tol.  Host only. */
 int afem_mctdhf_set_krylov_adaptive(afem_mctdhf* solver, int steps);
+/* Imaginary-time steps for ground-state preparation (Sec. 4 prepares its
+ * initial state by imaginary-time propagation; the scheme is this library's
+ * reading): on = 1 makes later afem_mctdhf_step calls advance tau by dt with
+ * t = -i tau -- the same frozen quantities as the real-time step, then
+ * C <- exp(-dt H_CI) C / ||.|| (Taylor series of H_CI - <H_CI>),
+ * phi <- exp(-dt G) phi by the Arnoldi process (the Krylov rule set by the
+ * functions above, with exp(-tau H_m) in place of exp(-i tau H_m)), and
+ * phi <- phi S^-1/2 with S = phi^H M_L phi (Loewdin; the n x n root is
+ * formed on the host).  The reported energy is that of the state at the
+ * start of the step.  on = 0 (default) returns to real time.  Host only;
+ * a step in this mode returns AFEM_ESINGULAR if S is not positive definite. */
+int afem_mctdhf_set_imaginary(afem_mctdhf* solver, int on);
+/* Gauge of later steps: AFEM_GAUGE_LENGTH (default; the step's E argument is
+ * the field E(t), H1 contains E . r) or AFEM_GAUGE_VELOCITY (Sec. 2; the step's
+ * E argument is the vector potential A(t) = -int_-inf^t E, H1 contains
+ * -i A . grad as in AFEM_OP_H1_VG, in h_pq, in the G cell passes and hence in
+ * the energy).  Host only. */
+#define AFEM_GAUGE_LENGTH 0
+#define AFEM_GAUGE_VELOCITY 1
+int afem_mctdhf_set_gauge(afem_mctdhf* solver, int gauge);
 /* Number of determinants (host). */
 int afem_mctdhf_ci_dim(const afem_mctdhf* solver, int64_t* dim);
 

@@ -17,6 +17,15 @@ hanging masters it equals the consistent GLL mass exactly.
 The length-gauge one-body Hamiltonian is H1 = -1/2 Laplacian
 - sum_a Z_a / |r - R_a| + E(t) . r, so its matrix is
 H1~ = 1/2 A + F[V] + F[E . x], and orbitals vanish on the box surface.
+In the velocity gauge of Sec. 2, H1 = -1/2 Laplacian - sum_a Z_a / |r - R_a|
+- i A(t) . grad, the matrix is H1~ = 1/2 A + F[V] - i sum_d A_d G_d with G_d
+the skew-symmetric form of int b_k d_d b_l: per cell h^2 (W (x) W (x) S) for
+d = x (and its permutations), S = (Dw - Dw^T) / 2, Dw[i, j] = w_i L_j'(xi_i) =
+int L_i L_j' (GLL quadrature is exact for this degree-(2p-1) product).  For
+functions that vanish on the box surface the skew form equals the plain one
+on a conforming mesh; on the hanging-node mesh it keeps -i A . G Hermitian,
+which the plain form is not there (the lumped face quadratures of a coarse
+face and its fine subfaces differ).
 
 Test infrastructure only (see the package docstring).
 """
@@ -37,6 +46,17 @@ def cell_matrices(p):
     A_hat = np.kron(W, np.kron(W, K)) + np.kron(W, np.kron(K, W)) + np.kron(K, np.kron(W, W))
     m_hat = np.kron(w, np.kron(w, w))
     return A_hat, m_hat
+
+
+def gradient_matrices(p):
+    """G_hat[d] (d = x, y, z): reference-cube matrices of the skew-symmetric
+    form of int b_i d_d b_j (to be scaled by h^2); node index
+    i = a + (p+1) (b + (p+1) c), a along x."""
+    xi, w = gll.gll_nodes_weights(p)
+    Dw = np.diag(w) @ gll.lagrange_deriv_matrix(xi, xi)
+    S = 0.5 * (Dw - Dw.T)
+    W = np.diag(w)
+    return [np.kron(W, np.kron(W, S)), np.kron(W, np.kron(S, W)), np.kron(S, np.kron(W, W))]
 
 
 class Operators:
@@ -96,19 +116,41 @@ class Operators:
         """F[f] = C^T diag(m_f o f) C for a function f given at the support points."""
         return (self.C.T @ sp.diags(self.m_f * f) @ self.C).tocsr()
 
-    def H1_matrix(self, E=(0.0, 0.0, 0.0)):
-        """H1~ = 1/2 A + F[V + E . x] over all masters (boundary rows/cols kept)."""
+    def gradient(self, d):
+        """G_d = C^T (sum_K P_K^T h_K^2 Ghat_d P_K) C (assembled once per direction)."""
+        if not hasattr(self, "_G"):
+            self._G = [None, None, None]
+        if self._G[d] is None:
+            mesh = self.mesh
+            nn = (mesh.p + 1) ** 3
+            Gh = gradient_matrices(mesh.p)[d]
+            rows = np.repeat(mesh.cell_pts, nn, axis=1).ravel()
+            cols = np.tile(mesh.cell_pts, (1, nn)).ravel()
+            vals = (mesh.h[:, None, None] ** 2 * Gh[None, :, :]).reshape(len(mesh.lev), -1).ravel()
+            Gf = sp.csr_matrix((vals, (rows, cols)), shape=(mesh.nf, mesh.nf))
+            self._G[d] = (self.C.T @ Gf @ self.C).tocsr()
+        return self._G[d]
+
+    def H1_matrix(self, E=(0.0, 0.0, 0.0), A=None):
+        """H1~ = 1/2 A + F[V + E . x] over all masters (boundary rows/cols kept);
+        with a vector potential A (velocity gauge, Sec. 2) the term
+        -i sum_d A_d G_d is added (complex matrix)."""
         E = np.asarray(E, dtype=np.float64)
         f = self.V_f + self.mesh.X @ E
-        return (0.5 * self.A + self.pointwise(f)).tocsr()
+        H = 0.5 * self.A + self.pointwise(f)
+        if A is not None and np.any(np.asarray(A) != 0.0):
+            for d in range(3):
+                if A[d] != 0.0:
+                    H = H - 1j * A[d] * self.gradient(d)
+        return H.tocsr()
 
-    def h1_apply(self, x, E=(0.0, 0.0, 0.0)):
+    def h1_apply(self, x, E=(0.0, 0.0, 0.0), A=None):
         """y = M_L^{-1} H1~ x on interior masters; boundary entries of x are taken as 0
         and boundary entries of y are 0 (orbitals vanish on the box surface).
 
-        x: (N,) or (N, nvec), real or complex.
+        x: (N,) or (N, nvec), real or complex.  A: vector potential (velocity gauge).
         """
-        H = self.H1_matrix(E)
+        H = self.H1_matrix(E, A)
         mask = self.interior.astype(np.float64)
         xm = x * (mask if x.ndim == 1 else mask[:, None])
         y = H @ xm

@@ -35,8 +35,16 @@ class MCTDHF:
         self.poisson_method = poisson_method
         self.poisson_rtol = poisson_rtol
         self.interior = (~self.mesh.boundary).astype(np.float64)
+        self.gauge = "length"
 
     # --------------------------------------------------------------- pieces
+    def h1(self, E):
+        """H1~ at the field argument E: the field E(t) in the length gauge, the
+        vector potential A(t) in the velocity gauge (Sec. 2)."""
+        if getattr(self, "gauge", "length") == "velocity":
+            return self.ops.H1_matrix((0.0, 0.0, 0.0), A=E)
+        return self.ops.H1_matrix(E)
+
     def inner(self, u, v):
         """<u, v> = sum_p u_p^H M_L v_p for stacked orbitals (N, n)."""
         return np.sum(np.conj(u) * (self.ops.ML[:, None] * v))
@@ -49,7 +57,7 @@ class MCTDHF:
 
     def integrals(self, phi, W, E):
         """h_pq = phi_p^H H1~(E) phi_q and (pq|rs) = sum_f m_f conj(phi_p) phi_q W_rs."""
-        H1 = self.ops.H1_matrix(E)
+        H1 = self.h1(E)
         pm = phi * self.interior[:, None]
         h = np.conj(pm).T @ (H1 @ pm)
         pf = self.ops.C @ pm
@@ -75,7 +83,7 @@ class MCTDHF:
         """(G v)_p = Q [ M_L^-1 (H1~ v_p + C^T diag(m_f) sum_q (C U_pq) o (C v_q)) ] (interior)."""
         ops = self.ops
         n = self.n
-        H1 = ops.H1_matrix(E)
+        H1 = self.h1(E)
         msk = self.interior[:, None]
         vm = v * msk
         z = H1 @ vm

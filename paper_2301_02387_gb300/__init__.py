@@ -11,7 +11,8 @@ import ctypes
 import numpy as np
 
 from . import _capi
-from ._capi import AfemError, OP_H1, OP_STIFF, OP_STIFF_F32, OP_H1_C64, OP_POS, OP_FORCE  # noqa: F401
+from ._capi import (AfemError, OP_H1, OP_STIFF, OP_STIFF_F32, OP_H1_C64, OP_POS, OP_FORCE,  # noqa: F401
+                    OP_H1_VG, OP_H1_VG_C64, GAUGE_LENGTH, GAUGE_VELOCITY)
 
 __all__ = ["Mesh", "op_apply", "AfemError", "OP_H1", "OP_STIFF", "load_library"]
 
@@ -231,6 +232,14 @@ class MCTDHF:
         """Sec. 3.2's rule: `steps` equal Krylov steps per time step, dimension by the estimate (0: off)."""
         _capi.check(_capi.load().afem_mctdhf_set_krylov_adaptive(self._h, int(steps)))
 
+    def set_gauge(self, gauge):
+        """GAUGE_LENGTH (the step's E is the field) or GAUGE_VELOCITY (the step's E is A(t))."""
+        _capi.check(_capi.load().afem_mctdhf_set_gauge(self._h, int(gauge)))
+
+    def set_imaginary(self, on=True):
+        """Imaginary-time steps (ground-state preparation) when on, real time otherwise."""
+        _capi.check(_capi.load().afem_mctdhf_set_imaginary(self._h, 1 if on else 0))
+
     def set_precision(self, precision):
         _capi.check(_capi.load().afem_mctdhf_set_precision(self._h, int(precision)))
 
@@ -275,7 +284,8 @@ def op_apply(mesh, kind, x, y, E=None, stream=None):
     import torch
     dtype = {OP_H1: torch.complex128, OP_STIFF: torch.float64, OP_STIFF_F32: torch.float32,
              OP_H1_C64: torch.complex64, OP_POS: torch.complex128,
-             OP_FORCE: torch.complex128}.get(kind, x.dtype)
+             OP_FORCE: torch.complex128, OP_H1_VG: torch.complex128,
+             OP_H1_VG_C64: torch.complex64}.get(kind, x.dtype)
     xp = _dev_ptr(x, dtype, mesh.N, "x")
     yp = _dev_ptr(y, dtype, mesh.N, "y")
     if x.shape != y.shape:
@@ -321,6 +331,9 @@ def fma_peak(kind, target_ms=50.0, stream=None):
 
 
 OPT_CELL32_VARIANT = 1
+OPT_POISSON_SOLVER = 2
+POISSON_JACOBI = 0
+POISSON_MULTIGRID = 1
 
 
 def mesh_set_option(mesh, option, value):

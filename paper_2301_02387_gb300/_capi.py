@@ -29,6 +29,10 @@ OP_STIFF_F32 = 2
 OP_H1_C64 = 3
 OP_POS = 4
 OP_FORCE = 5
+OP_H1_VG = 6
+OP_H1_VG_C64 = 7
+GAUGE_LENGTH = 0
+GAUGE_VELOCITY = 1
 
 CONVERT_F64_F32 = 0
 CONVERT_F32_F64 = 1
@@ -124,6 +128,8 @@ SIGNATURES = {
     "afem_mctdhf_set_precision": (ctypes.c_int, [_P, ctypes.c_int]),
     "afem_mctdhf_set_krylov_tol": (ctypes.c_int, [_P, ctypes.c_double]),
     "afem_mctdhf_set_krylov_adaptive": (ctypes.c_int, [_P, ctypes.c_int]),
+    "afem_mctdhf_set_imaginary": (ctypes.c_int, [_P, ctypes.c_int]),
+    "afem_mctdhf_set_gauge": (ctypes.c_int, [_P, ctypes.c_int]),
     "afem_arnoldi_adaptive": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                              ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _P, _P, _P, _P, _P]),
     "afem_arnoldi_propagate": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_double,

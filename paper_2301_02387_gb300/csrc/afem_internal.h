@@ -78,6 +78,7 @@ struct Basis1D {
     double xi[kMaxP1] = {};          // nodes, ascending
     double w[kMaxP1] = {};           // quadrature weights (sum 1)
     double K[kMaxP1][kMaxP1] = {};   // 1D stiffness sum_q w_q L_i'(xi_q) L_j'(xi_q)
+    double S[kMaxP1][kMaxP1] = {};   // skew part of int L_i L_j': (w_i L_j'(xi_i) - w_j L_i'(xi_j)) / 2
 };
 Basis1D make_basis(int p);
 double lagrange_value(const Basis1D& b, int j, double t);
@@ -141,6 +142,8 @@ struct DeviceMesh {
 
 }  // namespace afem
 
+struct afem_pmg;   // multigrid hierarchy of a mesh (pmg.cu)
+
 struct afem_mesh {
     afem_mesh_desc desc;
     afem::HostMesh host;
@@ -152,6 +155,8 @@ struct afem_mesh {
     afem::Workspace ws_arnoldi;
     afem::Workspace ws_tdse;
     int cell32_variant = 0;   // FP32 four-lane cell pass: 0 node-per-thread, 1 line-ordered
+    int poisson_solver = 0;   // AFEM_POISSON_JACOBI or AFEM_POISSON_MULTIGRID
+    afem_pmg* pmg = nullptr;  // built on the first multigrid solve
 };
 
 namespace afem {
@@ -167,12 +172,15 @@ int poisson_batch_mixed(afem_mesh* m, const double2* phi, int n, double* W, doub
 int multipole_boundary(afem_mesh* m, const double2* phi, int n, double* W, double* qpart, double* q, int nblk,
                        cudaStream_t s);
 int ensure_sh_tables();   // uploads the solid-harmonic constants once per device
+void pmg_free(afem_pmg* g);
 int mctdhf_create(afem_mesh* m, int n, int na, int nb, int mk, afem_mctdhf** out);
 void mctdhf_destroy(afem_mctdhf* S);
 int64_t mctdhf_ci_dim(const afem_mctdhf* S);
 void mctdhf_set_precision(afem_mctdhf* S, int precision);
 void mctdhf_set_krylov_tol(afem_mctdhf* S, double tol);
 void mctdhf_set_krylov_adaptive(afem_mctdhf* S, int steps);
+void mctdhf_set_imaginary(afem_mctdhf* S, int on);
+void mctdhf_set_gauge(afem_mctdhf* S, int gauge);
 int mctdhf_step(afem_mctdhf* S, double2* phi, double2* C, double* W, const double* E, double dt, double cg_rtol,
                 int cg_max_it, afem_step_info* info, cudaStream_t s);
 int convert_f64_f32(const double* x, float* y, int64_t n, cudaStream_t s);

@@ -410,6 +410,9 @@ __global__ void __launch_bounds__(kRedThreads) project32_dots_kernel(
     }
     krylov_scales(H, ldh, beta2, NV, s_f);
     __syncthreads();
+    // the complex64 input of the cell pass was 2^kv V_{NV-1} (krylov_update_kernel's
+    // scaling; V_0 unscaled), so the raw vector is the result times 2^-kv
+    const int kv = (NV >= 2 && s_f[NV >= 2 ? NV - 2 : 0] > 0.0) ? ilogb(s_f[NV >= 2 ? NV - 2 : 0]) : 0;
     double acc[2 * NV + 1];
 #pragma unroll
     for (int i = 0; i < 2 * NV + 1; ++i) acc[i] = 0.0;
@@ -432,7 +435,7 @@ __global__ void __launch_bounds__(kRedThreads) project32_dots_kernel(
                     xf.x = fmaf(-f.x, c.x, fmaf(f.y, c.y, xf.x));
                     xf.y = fmaf(-f.x, c.y, fmaf(-f.y, c.x, xf.y));
                 }
-                x = make_double2(widen_f32(xf.x), widen_f32(xf.y));
+                x = make_double2(widen_f32_scaled(xf.x, -kv), widen_f32_scaled(xf.y, -kv));
                 accumulate_dots<NV>(acc, u, x, ml[k]);
             }
             w[o] = x;
@@ -465,6 +468,11 @@ __global__ void __launch_bounds__(kRedThreads) krylov_update_kernel(
     if (int(threadIdx.x) <= NV) s_c[threadIdx.x] = c[threadIdx.x];
     __syncthreads();
     const double fw = s_f[NV - 1];
+    // the complex64 copy holds 2^kw w with 2^kw ~ fw, i.e. about the true vector
+    // fw w (whose size is the Hessenberg entry): the raw vectors grow like the
+    // operator norm to the power of their index and would leave the binary32
+    // range (project32_dots_kernel undoes the factor)
+    const int kw = fw > 0.0 ? ilogb(fw) : 0;
     if (int(threadIdx.x) < NV) {
         const double f = fw > 0.0 ? s_f[threadIdx.x] / fw : 0.0;
         s_cf[threadIdx.x] = make_double2(s_c[threadIdx.x].x * f, s_c[threadIdx.x].y * f);
@@ -487,7 +495,7 @@ __global__ void __launch_bounds__(kRedThreads) krylov_update_kernel(
                 x.y = fma(-h.x, u[i].y, fma(-h.y, u[i].x, x.y));
             }
             w[o] = x;
-            if (w32) w32[o] = make_float2(narrow_f64(x.x), narrow_f64(x.y));
+            if (w32) w32[o] = make_float2(narrow_f64_scaled(x.x, kw), narrow_f64_scaled(x.y, kw));
             nrm[0] = fma(m, fma(x.x, x.x, x.y * x.y), nrm[0]);
         }
     }
@@ -669,7 +677,7 @@ __global__ void expm_ladder_kernel(const double2* __restrict__ H, int ldh, int m
 
 // ------------------------------------------------------------------- host
 int launch_g_cell(const afem_mesh* m, const double* E, const double2* v, const double2* U, double2* z, int n,
-                  cudaStream_t s);
+                  cudaStream_t s, int velocity);
 
 template <typename TB>
 int cdot_t(const double2* A, int na, const TB* B, int nb, const double* w, int64_t rows, int diag,
@@ -721,7 +729,7 @@ int to_c64(const double2* x, float2* y, int64_t n, cudaStream_t s) {
 }
 
 int launch_g_cell32(const afem_mesh* m, const double* E, const float2* v, const float2* U, float2* z, int n,
-                    cudaStream_t s);
+                    cudaStream_t s, int velocity);
 
 #define AFEM_NV_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16)
 
@@ -855,12 +863,12 @@ static unsigned rowcol_grid(int64_t rows, int n) {
 // Gram-Schmidt pass.  Precision form: the cell pass in complex64 from v32 (the
 // complex64 copy of the vector) and the overlaps from phi32.
 static int g_cell_overlaps32(afem_mesh* m, const double* E, const float2* phi32, const float2* U32, int n,
-                             const float2* v32, ArnoldiWork& w, cudaStream_t s) {
+                             const float2* v32, ArnoldiWork& w, cudaStream_t s, int velocity) {
     const DeviceMesh& D = m->dev;
     int rc;
     {   // algorithmic bytes: read v, U (n^2 fields), write z, complex64
         ProfScope ps(AFEM_PROF_GCELL32, s, double(D.n_master) * 8.0 * n * (2 + n));
-        if ((rc = launch_g_cell32(m, E, v32, U32, w.z32, n, s))) return rc;
+        if ((rc = launch_g_cell32(m, E, v32, U32, w.z32, n, s, velocity))) return rc;
     }
     auto* part = reinterpret_cast<double*>(w.cpartial);
     switch (n) {
@@ -886,13 +894,13 @@ static int g_cell_overlaps32(afem_mesh* m, const double* E, const float2* phi32,
 }
 
 static int g_cell_overlaps(afem_mesh* m, const double* E, const double2* phi, const double2* U, int n,
-                           const double2* v, ArnoldiWork& w, cudaStream_t s) {
+                           const double2* v, ArnoldiWork& w, cudaStream_t s, int velocity) {
     const DeviceMesh& D = m->dev;
     int rc;
     {
         const int p1 = D.p + 1;
         ProfScope ps(AFEM_PROF_CELL64, s, double(D.ncell) * p1 * p1 * p1 * 2.0 * n * (3.0 * p1 * 2.0 + 6.0));
-        rc = launch_g_cell(m, E, v, U, w.z, n, s);
+        rc = launch_g_cell(m, E, v, U, w.z, n, s, velocity);
     }
     if (rc) return rc;
     return cdot(phi, n, w.z, n, nullptr, D.n_interior, 0, w.cpartial, w.S, w.counters, s);
@@ -956,6 +964,7 @@ int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double
     if (adaptive_steps < 0 || (adaptive_steps > 0 && !(tol > 0.0)))
         return set_error(AFEM_EINVAL, "arnoldi: the adaptive dimension needs steps >= 1 and a threshold > 0");
     const int imag = (flags & kArnImaginary) ? 1 : 0;
+    const int velocity = (flags & kArnVelocity) ? 1 : 0;   // E holds the vector potential A
     const bool adaptive = adaptive_steps > 0;
     const double tau_fixed = adaptive ? dt / adaptive_steps : 0.0;
     ArnoldiWork w{};
@@ -1014,14 +1023,14 @@ int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double
             // update cancelled most of w
             if (!projector) {   // the cell pass alone; S stays zero
                 if (mixed) {
-                    if ((rc = launch_g_cell32(m, E, w.v32, U32, w.z32, n, s))) return rc;
+                    if ((rc = launch_g_cell32(m, E, w.v32, U32, w.z32, n, s, velocity))) return rc;
                 } else {
-                    if ((rc = launch_g_cell(m, E, w.V + j * NV, U, w.z, n, s))) return rc;
+                    if ((rc = launch_g_cell(m, E, w.V + j * NV, U, w.z, n, s, velocity))) return rc;
                 }
             } else if (mixed) {
-                if ((rc = g_cell_overlaps32(m, E, w.phi32, U32, n, w.v32, w, s))) return rc;
+                if ((rc = g_cell_overlaps32(m, E, w.phi32, U32, n, w.v32, w, s, velocity))) return rc;
             } else {
-                if ((rc = g_cell_overlaps(m, E, phi, U, n, w.V + j * NV, w, s))) return rc;
+                if ((rc = g_cell_overlaps(m, E, phi, U, n, w.V + j * NV, w, s, velocity))) return rc;
             }
             // algorithmic FP64 flops per element: 8 per basis vector in each pass
             // (one complex multiply-add), plus 4 for the new norm in the update

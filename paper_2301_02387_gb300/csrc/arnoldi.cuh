@@ -55,6 +55,7 @@ int cdot(const double2* A, int na, const double2* B, int nb, const double* w, in
 constexpr int kArnNoProjector = 1;
 constexpr int kArnBackward = 2;
 constexpr int kArnImaginary = 4;
+constexpr int kArnVelocity = 8;   // velocity gauge: the field argument is the vector potential A
 int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double2* U, const float2* U32, int n,
                  int mk, double dt, int mixed, double tol, double2* phi_out, double* err_est, int* m_used_out,
                  int* breakdown_out, int* substeps_out, cudaStream_t s, int flags = 0, int adaptive_steps = 0,

@@ -155,6 +155,8 @@ int afem_mesh_create_ex(const afem_mesh_desc* desc, int flags, afem_mesh** out) 
 int afem_mesh_destroy(afem_mesh* mesh) {
     if (!mesh) return AFEM_OK;
     if (!mesh->host_only) free_device_mesh(mesh->dev);
+    pmg_free(mesh->pmg);
+    mesh->pmg = nullptr;
     mesh->ws_poisson.release();
     mesh->ws_arnoldi.release();
     mesh->ws_tdse.release();
@@ -167,6 +169,14 @@ int afem_mesh_set_option(afem_mesh* m, int option, int value) {
     if (option == AFEM_OPT_CELL32_VARIANT) {
         if (value != 0 && value != 1) return set_error(AFEM_EINVAL, "afem_mesh_set_option: variant must be 0 or 1");
         m->cell32_variant = value;
+        return AFEM_OK;
+    }
+    if (option == AFEM_OPT_POISSON_SOLVER) {
+        if (value != AFEM_POISSON_JACOBI && value != AFEM_POISSON_MULTIGRID)
+            return set_error(AFEM_EINVAL, "afem_mesh_set_option: Poisson solver must be AFEM_POISSON_JACOBI or "
+                                          "AFEM_POISSON_MULTIGRID");
+        if (m->host_only) return set_error(AFEM_EINVAL, "afem_mesh_set_option: mesh was built host-only");
+        m->poisson_solver = value;
         return AFEM_OK;
     }
     return set_error(AFEM_EINVAL, "afem_mesh_set_option: unknown option");
@@ -331,6 +341,21 @@ int afem_mctdhf_set_krylov_adaptive(afem_mctdhf* s, int steps) {
     if (!s) return set_error(AFEM_EINVAL, "afem_mctdhf_set_krylov_adaptive: null argument");
     if (steps < 0 || steps > 4096) return set_error(AFEM_EINVAL, "afem_mctdhf_set_krylov_adaptive: steps must be 0..4096");
     mctdhf_set_krylov_adaptive(s, steps);
+    return AFEM_OK;
+}
+
+int afem_mctdhf_set_imaginary(afem_mctdhf* s, int on) {
+    if (!s) return set_error(AFEM_EINVAL, "afem_mctdhf_set_imaginary: null argument");
+    if (on != 0 && on != 1) return set_error(AFEM_EINVAL, "afem_mctdhf_set_imaginary: on must be 0 or 1");
+    mctdhf_set_imaginary(s, on);
+    return AFEM_OK;
+}
+
+int afem_mctdhf_set_gauge(afem_mctdhf* s, int gauge) {
+    if (!s) return set_error(AFEM_EINVAL, "afem_mctdhf_set_gauge: null argument");
+    if (gauge != AFEM_GAUGE_LENGTH && gauge != AFEM_GAUGE_VELOCITY)
+        return set_error(AFEM_EINVAL, "afem_mctdhf_set_gauge: gauge must be AFEM_GAUGE_LENGTH or AFEM_GAUGE_VELOCITY");
+    mctdhf_set_gauge(s, gauge);
     return AFEM_OK;
 }
 

@@ -14,6 +14,7 @@ struct BasisParams {
     double xi[kMaxP1];
     double w[kMaxP1];
     double K[kMaxP1 * kMaxP1];
+    double S[kMaxP1 * kMaxP1];   // skew part of int L_i L_j' (velocity gauge)
 };
 
 struct CellArgs {
@@ -32,6 +33,8 @@ struct CellArgs {
     double c_kin;               // factor of the stiffness term
     int with_pot;               // pointwise term: 1 F[V + E.r], 2 F[E.r], 3 F[E.force]
     int masked;                 // treat surface masters (>= n_interior) as zero, in and out
+    int vg;                     // velocity gauge: the term -i A . G with A in Avec (complex data only)
+    double Avec[3];
 };
 
 CellArgs make_cell_args(const afem_mesh* m);

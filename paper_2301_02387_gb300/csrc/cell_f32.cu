@@ -30,8 +30,11 @@ struct CellArgs32 {
     int64_t ncell;
     int64_t n_interior;
     float xi[kMaxP1], w[kMaxP1], K[kMaxP1 * kMaxP1];
+    float S[kMaxP1 * kMaxP1];   // skew part of int L_i L_j' (velocity gauge)
     float E[3];
+    float Avec[3];              // vector potential (vg != 0)
     int masked;
+    int vg;                     // velocity gauge: -i A . grad in the G pass (generic kernel only)
 };
 
 template <typename T>
@@ -69,7 +72,7 @@ __device__ __forceinline__ void scatter32(const CellArgs32& a, int idx, T* __res
 
 // y += A x for nv real columns (c_kin = 1), or the G-operator cell pass for
 // complex columns: z_p = H1~ v_p + sum_q (C U_pq) o (C v_q) weighted (U may be null).
-template <int P, typename T, bool G>
+template <int P, typename T, bool G, bool VG = false>
 __global__ void __launch_bounds__(256) cell32_kernel(CellArgs32 a, const T* __restrict__ x,
                                                      const float2* __restrict__ U, T* __restrict__ y, int nv) {
     constexpr int P1 = P + 1;
@@ -132,6 +135,24 @@ __global__ void __launch_bounds__(256) cell32_kernel(CellArgs32 a, const T* __re
         vfma(r, ck * s_w[ia] * s_w[ib], az);
         if constexpr (G) {
             vfma(r, s_pot[i], s_u[it]);
+            if constexpr (VG && sizeof(T) == sizeof(float2)) {
+                {   // -i h^2 (A_x w_b w_c (S u)_x + A_y w_a w_c (S u)_y + A_z w_a w_b (S u)_z)
+                    float2 gx = make_float2(0.f, 0.f), gy = gx, gz = gx;
+#pragma unroll
+                    for (int m = 0; m < P1; ++m) {
+                        vfma(gx, a.S[ia * P1 + m], s_u[(m + P1 * (ib + P1 * ic)) * nv + p]);
+                        vfma(gy, a.S[ib * P1 + m], s_u[(ia + P1 * (m + P1 * ic)) * nv + p]);
+                        vfma(gz, a.S[ic * P1 + m], s_u[(ia + P1 * (ib + P1 * m)) * nv + p]);
+                    }
+                    const float h2 = g.w * g.w;
+                    float2 t = make_float2(0.f, 0.f);
+                    vfma(t, h2 * a.Avec[0] * s_w[ib] * s_w[ic], gx);
+                    vfma(t, h2 * a.Avec[1] * s_w[ia] * s_w[ic], gy);
+                    vfma(t, h2 * a.Avec[2] * s_w[ia] * s_w[ib], gz);
+                    r.x += t.y;
+                    r.y -= t.x;
+                }
+            }
             if (U) {
                 float2 mf = make_float2(0.0f, 0.0f);
                 const float2* Ui = s_U + i * nn2 + p * nv;
@@ -590,7 +611,10 @@ CellArgs32 make_cell_args32(const afem_mesh* m) {
     for (int i = 0; i < p1; ++i) {
         a.xi[i] = float(b.xi[i]);
         a.w[i] = float(b.w[i]);
-        for (int j = 0; j < p1; ++j) a.K[i * p1 + j] = float(b.K[i][j]);
+        for (int j = 0; j < p1; ++j) {
+            a.K[i * p1 + j] = float(b.K[i][j]);
+            a.S[i * p1 + j] = float(b.S[i][j]);
+        }
     }
     return a;
 }
@@ -607,7 +631,9 @@ static int launch32(const afem_mesh* m, const CellArgs32& a, const T* x, const f
     switch (p) {
 #define AFEM_CASE(PP)                                                                          \
     case PP: {                                                                                 \
-        auto k = cell32_kernel<PP, T, G>;                                                      \
+        auto k = cell32_kernel<PP, T, G, false>;                                               \
+        if constexpr (G && sizeof(T) == sizeof(float2))                                        \
+            if (a.vg) k = cell32_kernel<PP, T, G, true>;                                       \
         if (smem > 48 * 1024)                                                                  \
             AFEM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                                int(smem)));                                    \
@@ -725,11 +751,18 @@ int launch_stiffness32(const afem_mesh* m, const float* x, float* y, int nv, int
 }
 
 // z = H1~ v + mean field (complex64), Dirichlet-masked.
+// velocity != 0: E holds the vector potential A (velocity gauge), applied by
+// the generic (two-lane) kernel.
 int launch_g_cell32(const afem_mesh* m, const double* E, const float2* v, const float2* U, float2* z, int n,
-                    cudaStream_t s) {
+                    cudaStream_t s, int velocity) {
     CellArgs32 a = make_cell_args32(m);
     a.masked = 1;
-    for (int i = 0; i < 3; ++i) a.E[i] = E ? float(E[i]) : 0.0f;
+    for (int i = 0; i < 3; ++i) a.E[i] = (E && !velocity) ? float(E[i]) : 0.0f;
+    if (velocity && E) {
+        a.vg = 1;
+        for (int i = 0; i < 3; ++i) a.Avec[i] = float(E[i]);
+        return launch32<float2, true>(m, a, v, U, z, n, s);
+    }
     if (n % 2 == 0 && aligned16(v) && aligned16(z))
         return launch32v<true>(m, a, reinterpret_cast<const float*>(v), U, reinterpret_cast<float*>(z), 2 * n, n, s);
     return launch32<float2, true>(m, a, v, U, z, n, s);

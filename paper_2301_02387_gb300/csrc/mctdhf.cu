@@ -188,14 +188,16 @@ __global__ void ci_rdm_kernel(int n, int64_t dim, const double2* __restrict__ C,
     }
 }
 
-// Taylor term: t_next = c_k (sigma - shift t), acc += t_next  (c_k = -i dt / k)
+// Taylor term: t_next = c_k (sigma - shift t), acc += t_next  (c_k = -i dt / k;
+// imaginary time: c_k = -dt / k)
 __global__ void ci_taylor_kernel(int64_t dim, const double2* __restrict__ sigma, const double2* __restrict__ t,
-                                 const double* __restrict__ shift, double ck, double2* __restrict__ tn,
+                                 const double* __restrict__ shift, double ck, int imag, double2* __restrict__ tn,
                                  double2* __restrict__ acc) {
     const double s = *shift;
     for (int64_t I = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; I < dim; I += int64_t(gridDim.x) * blockDim.x) {
         const double2 u = make_double2(sigma[I].x - s * t[I].x, sigma[I].y - s * t[I].y);
-        const double2 r = make_double2(ck * u.y, -ck * u.x);   // -i ck u
+        const double2 r = imag ? make_double2(-ck * u.x, -ck * u.y)    // -ck u
+                               : make_double2(ck * u.y, -ck * u.x);    // -i ck u
         tn[I] = r;
         acc[I].x += r.x;
         acc[I].y += r.y;
@@ -211,6 +213,110 @@ __global__ void ci_phase_kernel(int64_t dim, const double2* __restrict__ acc, co
         const double2 v = acc[I];
         C[I] = make_double2(cs * v.x + sn * v.y, cs * v.y - sn * v.x);
     }
+}
+
+// C = acc / ||acc|| (one block; the imaginary-time CI step)
+__global__ void ci_normalize_kernel(int64_t dim, const double2* __restrict__ acc, double2* __restrict__ C) {
+    __shared__ double sa[256];
+    __shared__ double s_scale;
+    double a = 0.0;
+    for (int64_t I = threadIdx.x; I < dim; I += blockDim.x) a += acc[I].x * acc[I].x + acc[I].y * acc[I].y;
+    sa[threadIdx.x] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double x = 0.0;
+        for (int i = 0; i < blockDim.x; ++i) x += sa[i];
+        s_scale = x > 0.0 ? 1.0 / sqrt(x) : 0.0;
+    }
+    __syncthreads();
+    const double f = s_scale;
+    for (int64_t I = threadIdx.x; I < dim; I += blockDim.x) C[I] = make_double2(f * acc[I].x, f * acc[I].y);
+}
+
+// phi[k][p] = sum_q src[k][q] T[q][p] (row-major [N][n], T [n][n]; Loewdin)
+__global__ void orbital_transform_kernel(int64_t N, int n, const double2* __restrict__ src,
+                                         const double2* __restrict__ T, double2* __restrict__ phi) {
+    __shared__ double2 sT[64];
+    for (int i = threadIdx.x; i < n * n; i += blockDim.x) sT[i] = T[i];
+    __syncthreads();
+    for (int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; o < N * n; o += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t k = o / n;
+        const int p = int(o - k * n);
+        double x = 0.0, y = 0.0;
+        for (int q = 0; q < n; ++q) {
+            const double2 a = src[k * n + q], b = sT[q * n + p];
+            x += a.x * b.x - a.y * b.y;
+            y += a.x * b.y + a.y * b.x;
+        }
+        phi[o] = make_double2(x, y);
+    }
+}
+
+// S^-1/2 of a Hermitian positive-definite n x n matrix (row-major, n <= 8) on
+// the host: cyclic Jacobi rotations on the real symmetric embedding
+// [[Re S, -Im S], [Im S, Re S]], f(R) = Q f(Lambda) Q^T, read back as
+// Re = f(R)[0:n, 0:n], Im = f(R)[n:2n, 0:n].  Returns false if S is not
+// positive definite.
+static bool inverse_sqrt_hermitian(int n, const double2* S, double2* T) {
+    const int m = 2 * n;
+    double R[16][16], Q[16][16];
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) Q[i][j] = i == j ? 1.0 : 0.0;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            const double re = 0.5 * (S[i * n + j].x + S[j * n + i].x);
+            const double im = 0.5 * (S[i * n + j].y - S[j * n + i].y);
+            R[i][j] = re;
+            R[i + n][j + n] = re;
+            R[i][j + n] = -im;
+            R[i + n][j] = im;
+        }
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < m; ++j) {
+                tot += R[i][j] * R[i][j];
+                if (i != j) off += R[i][j] * R[i][j];
+            }
+        if (off <= 1e-32 * tot) break;
+        for (int p = 0; p < m - 1; ++p)
+            for (int q = p + 1; q < m; ++q) {
+                if (R[p][q] == 0.0) continue;
+                const double theta = 0.5 * (R[q][q] - R[p][p]) / R[p][q];
+                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < m; ++k) {   // columns p, q
+                    const double rkp = R[k][p], rkq = R[k][q];
+                    R[k][p] = c * rkp - s * rkq;
+                    R[k][q] = s * rkp + c * rkq;
+                }
+                for (int k = 0; k < m; ++k) {   // rows p, q
+                    const double rpk = R[p][k], rqk = R[q][k];
+                    R[p][k] = c * rpk - s * rqk;
+                    R[q][k] = s * rpk + c * rqk;
+                }
+                for (int k = 0; k < m; ++k) {
+                    const double qkp = Q[k][p], qkq = Q[k][q];
+                    Q[k][p] = c * qkp - s * qkq;
+                    Q[k][q] = s * qkp + c * qkq;
+                }
+            }
+    }
+    double f[16];
+    for (int i = 0; i < m; ++i) {
+        if (!(R[i][i] > 0.0)) return false;
+        f[i] = 1.0 / std::sqrt(R[i][i]);
+    }
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double re = 0.0, im = 0.0;
+            for (int k = 0; k < m; ++k) {
+                re += Q[i][k] * f[k] * Q[j][k];
+                im += Q[i + n][k] * f[k] * Q[j][k];
+            }
+            T[i * n + j] = make_double2(re, im);
+        }
+    return true;
 }
 
 // shift = Re(C^H sigma) / (C^H C)   (one block)
@@ -491,6 +597,8 @@ struct afem_mctdhf {
     int precision = AFEM_PREC_FP64;
     double krylov_tol = 0.0;   // 0: one Krylov step per time step (fixed dimension)
     int krylov_adaptive = 0;   // > 0: Sec. 3.2's rule with this many equal Krylov steps per time step
+    int imaginary = 0;         // 1: imaginary-time steps (ground-state preparation)
+    int gauge = AFEM_GAUGE_LENGTH;
     afem::CiTables ci;
     afem::Workspace ws;
 };
@@ -592,7 +700,8 @@ int mctdhf_step(afem_mctdhf* S, double2* phi, double2* C, double* W, const doubl
     if (rc && rc != AFEM_ECG_MAXIT) return rc;
     const int cg_rc = rc;
     // 2. integrals: h_pq = phi_p^H M_L (M_L^-1 H1~ phi_q);  (pq|rs)
-    if ((rc = launch_op_apply(m, AFEM_OP_H1, E, phi, w.y, n, s))) return rc;
+    if ((rc = launch_op_apply(m, S->gauge == AFEM_GAUGE_VELOCITY ? AFEM_OP_H1_VG : AFEM_OP_H1, E, phi, w.y, n, s)))
+        return rc;
     AFEM_CUDA_TRY(cudaMemsetAsync(w.counters, 0, 4 * sizeof(unsigned), s));
     if ((rc = cdot(phi, n, w.y, n, D.ml, D.n_interior, 0, w.cpart, w.h, w.counters, s))) return rc;
     // position matrices Z_d[pq] = phi_p^H F[x_d] phi_q = phi_p^H M_L (M_L^-1 F[x_d] phi_q)
@@ -631,7 +740,8 @@ int mctdhf_step(afem_mctdhf* S, double2* phi, double2* C, double* W, const doubl
     double2* tn = w.t1;
     for (int k = 1; k <= kTaylorTerms; ++k) {
         if (k > 1 && (rc = ci_sigma(S->ci, w, tk, w.sigma, s))) return rc;
-        AFEM_LAUNCH((ci_taylor_kernel), ci_grid(dim), 128, 0, s, dim, w.sigma, tk, w.shift, dt / k, tn, w.acc);
+        AFEM_LAUNCH((ci_taylor_kernel), ci_grid(dim), 128, 0, s, dim, w.sigma, tk, w.shift, dt / k, S->imaginary,
+                    tn, w.acc);
         std::swap(tk, tn);
     }
     AFEM_CUDA_TRY(cudaGetLastError());
@@ -652,11 +762,29 @@ int mctdhf_step(afem_mctdhf* S, double2* phi, double2* C, double* W, const doubl
     if (S->krylov_adaptive > 0 && !(S->krylov_tol > 0.0))
         return set_error(AFEM_EINVAL, "afem_mctdhf_step: the adaptive Krylov dimension needs a threshold > 0");
     if ((rc = arnoldi_step(m, E, phi, mixed ? nullptr : w.U, U32, n, S->krylov_m, dt, mixed, S->krylov_tol,
-                           w.phi_new, &err, &m_used, &brk, &substeps, s, 0, S->krylov_adaptive, &dim_sum, &unmet)))
+                           w.phi_new, &err, &m_used, &brk, &substeps, s,
+                           (S->imaginary ? kArnImaginary : 0) | (S->gauge == AFEM_GAUGE_VELOCITY ? kArnVelocity : 0),
+                           S->krylov_adaptive, &dim_sum, &unmet)))
         return rc;
-    // commit: phi <- phi_new, C <- exp(-i dt shift) acc
-    AFEM_CUDA_TRY(cudaMemcpyAsync(phi, w.phi_new, size_t(N) * n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
-    AFEM_LAUNCH((ci_phase_kernel), ci_grid(dim), 128, 0, s, dim, w.acc, w.shift, dt, C);
+    if (S->imaginary) {
+        // commit: phi <- phi_new S^-1/2 (Loewdin, S = phi_new^H M_L phi_new), C <- acc / ||acc||
+        AFEM_CUDA_TRY(cudaMemsetAsync(w.counters, 0, 4 * sizeof(unsigned), s));
+        if ((rc = cdot(w.phi_new, n, w.phi_new, n, D.ml, D.n_interior, 0, w.cpart, w.h, w.counters, s))) return rc;
+        double2 Sh[64], Th[64];
+        AFEM_CUDA_TRY(cudaMemcpyAsync(Sh, w.h, size_t(nn) * sizeof(double2), cudaMemcpyDeviceToHost, s));
+        AFEM_CUDA_TRY(cudaStreamSynchronize(s));
+        if (!inverse_sqrt_hermitian(n, Sh, Th))
+            return set_error(AFEM_ESINGULAR, "afem_mctdhf_step: orbital overlap not positive definite (imaginary time)");
+        AFEM_CUDA_TRY(cudaMemcpyAsync(w.hp, Th, size_t(nn) * sizeof(double2), cudaMemcpyHostToDevice, s));
+        AFEM_LAUNCH((orbital_transform_kernel), grid_for(N * n), 256, 0, s, N, n, w.phi_new, w.hp, phi);
+        AFEM_LAUNCH((ci_normalize_kernel), 1, 256, 0, s, dim, w.acc, C);
+        AFEM_CUDA_TRY(cudaGetLastError());
+        AFEM_CUDA_TRY(cudaStreamSynchronize(s));   // Th is read by the copy before it leaves scope
+    } else {
+        // commit: phi <- phi_new, C <- exp(-i dt shift) acc
+        AFEM_CUDA_TRY(cudaMemcpyAsync(phi, w.phi_new, size_t(N) * n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+        AFEM_LAUNCH((ci_phase_kernel), ci_grid(dim), 128, 0, s, dim, w.acc, w.shift, dt, C);
+    }
     AFEM_CUDA_TRY(cudaGetLastError());
     AFEM_CUDA_TRY(cudaStreamSynchronize(s));
     if (info) {
@@ -721,5 +849,9 @@ void mctdhf_set_precision(afem_mctdhf* S, int precision) { S->precision = precis
 void mctdhf_set_krylov_tol(afem_mctdhf* S, double tol) { S->krylov_tol = tol; }
 
 void mctdhf_set_krylov_adaptive(afem_mctdhf* S, int steps) { S->krylov_adaptive = steps; }
+
+void mctdhf_set_imaginary(afem_mctdhf* S, int on) { S->imaginary = on ? 1 : 0; }
+
+void mctdhf_set_gauge(afem_mctdhf* S, int gauge) { S->gauge = gauge; }
 
 }  // namespace afem

@@ -99,6 +99,7 @@ Basis1D make_basis(int p) {
             double s = 0.0;
             for (int q = 0; q <= p; ++q) s += b.w[q] * D[q][i] * D[q][j];
             b.K[i][j] = s;
+            b.S[i][j] = 0.5 * (b.w[i] * D[i][j] - b.w[j] * D[j][i]);
         }
     return b;
 }

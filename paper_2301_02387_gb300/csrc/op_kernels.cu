@@ -19,7 +19,29 @@
 namespace afem {
 
 // ------------------------------------------------------------------ kernels
-template <int P, typename T>
+// Velocity-gauge term of one output node (Sec. 2: -i A(t) . grad): with the
+// skew-symmetric cell matrix h^2 (W (x) W (x) S) per direction,
+// r += -i h^2 (A_x w_b w_c (S u)_x + A_y w_a w_c (S u)_y + A_z w_a w_b (S u)_z).
+__device__ __forceinline__ void add_velocity_term(double2& r, const double* s_S, const double* s_w,
+                                                  const double2* s_u, int ia, int ib, int ic, int nv, int v,
+                                                  double h2, const double* A, int P1) {
+    double2 gx = make_double2(0.0, 0.0), gy = gx, gz = gx;
+    for (int m = 0; m < P1; ++m) {
+        vfma(gx, s_S[ia * P1 + m], s_u[(m + P1 * (ib + P1 * ic)) * nv + v]);
+        vfma(gy, s_S[ib * P1 + m], s_u[(ia + P1 * (m + P1 * ic)) * nv + v]);
+        vfma(gz, s_S[ic * P1 + m], s_u[(ia + P1 * (ib + P1 * m)) * nv + v]);
+    }
+    double2 t = make_double2(0.0, 0.0);
+    vfma(t, h2 * A[0] * s_w[ib] * s_w[ic], gx);
+    vfma(t, h2 * A[1] * s_w[ia] * s_w[ic], gy);
+    vfma(t, h2 * A[2] * s_w[ia] * s_w[ib], gz);
+    r.x += t.y;   // -i t
+    r.y -= t.x;
+}
+
+// VG: with the velocity-gauge term (complex data; a.vg set), a separate
+// instantiation so that the plain operator keeps its register budget.
+template <int P, typename T, bool VG = false>
 __global__ void __launch_bounds__(256) cell_op_kernel(CellArgs a, const T* __restrict__ x,
                                                       T* __restrict__ y, int nv) {
     constexpr int P1 = P + 1;
@@ -29,6 +51,7 @@ __global__ void __launch_bounds__(256) cell_op_kernel(CellArgs a, const T* __res
     __shared__ int s_idx[NN];
     __shared__ double s_pot[NN];
     __shared__ double s_K[P1 * P1];
+    __shared__ double s_S[P1 * P1];
     __shared__ double s_w[P1];
 
     const int64_t cell = blockIdx.x;
@@ -36,7 +59,10 @@ __global__ void __launch_bounds__(256) cell_op_kernel(CellArgs a, const T* __res
     const int bs = blockDim.x;
     const double4 g = a.geom[cell];
     for (int n = tid; n < NN; n += bs) s_idx[n] = a.cell_node[cell * NN + n];
-    if (tid < P1 * P1) s_K[tid] = a.B.K[tid];
+    if (tid < P1 * P1) {
+        s_K[tid] = a.B.K[tid];
+        s_S[tid] = a.B.S[tid];
+    }
     if (tid < P1) s_w[tid] = a.B.w[tid];
     __syncthreads();
 
@@ -86,6 +112,7 @@ __global__ void __launch_bounds__(256) cell_op_kernel(CellArgs a, const T* __res
         vfma(r, ck * s_w[ia] * s_w[ic], ay);
         vfma(r, ck * s_w[ia] * s_w[ib], az);
         if (a.with_pot) vfma(r, s_pot[n], s_u[it]);
+        if constexpr (VG) add_velocity_term(r, s_S, s_w, s_u, ia, ib, ic, nv, v, g.w * g.w, a.Avec, P1);
         scatter_value<T>(a, s_idx[n], y, nv, v, r);
     }
 }
@@ -93,7 +120,7 @@ __global__ void __launch_bounds__(256) cell_op_kernel(CellArgs a, const T* __res
 // Packed orbital operator before projection and inverse mass (Eqs. orb_eom,
 // discretized_eom):  z_p = H1~ v_p + C^T diag(m_f) sum_q (C U_pq) o (C v_q),
 // for all n orbitals of one cell at once.  U: complex [N][n][n] nodal fields.
-template <int P>
+template <int P, bool VG = false>
 __global__ void __launch_bounds__(256) g_cell_kernel(CellArgs a, const double2* __restrict__ v,
                                                      const double2* __restrict__ U, double2* __restrict__ z,
                                                      int n) {
@@ -106,6 +133,7 @@ __global__ void __launch_bounds__(256) g_cell_kernel(CellArgs a, const double2* 
     __shared__ double s_pot[NN];
     __shared__ double s_wq[NN];
     __shared__ double s_K[P1 * P1];
+    __shared__ double s_S[P1 * P1];
     __shared__ double s_w[P1];
 
     const int64_t cell = blockIdx.x;
@@ -113,7 +141,10 @@ __global__ void __launch_bounds__(256) g_cell_kernel(CellArgs a, const double2* 
     const int bs = blockDim.x;
     const double4 g = a.geom[cell];
     for (int i = tid; i < NN; i += bs) s_idx[i] = a.cell_node[cell * NN + i];
-    if (tid < P1 * P1) s_K[tid] = a.B.K[tid];
+    if (tid < P1 * P1) {
+        s_K[tid] = a.B.K[tid];
+        s_S[tid] = a.B.S[tid];
+    }
     if (tid < P1) s_w[tid] = a.B.w[tid];
     __syncthreads();
     const int nn2 = n * n;
@@ -160,6 +191,7 @@ __global__ void __launch_bounds__(256) g_cell_kernel(CellArgs a, const double2* 
         vfma(r, ck * s_w[ia] * s_w[ic], ay);
         vfma(r, ck * s_w[ia] * s_w[ib], az);
         vfma(r, s_pot[i], s_u[it]);
+        if constexpr (VG) add_velocity_term(r, s_S, s_w, s_u, ia, ib, ic, n, p, g.w * g.w, a.Avec, P1);
         if (U) {
             double2 mf = vzero<double2>();
             const double2* Ui = s_U + i * nn2 + p * n;
@@ -174,13 +206,19 @@ __global__ void __launch_bounds__(256) g_cell_kernel(CellArgs a, const double2* 
     }
 }
 
+// velocity != 0: E holds the vector potential A of the velocity gauge (the
+// field term is then -i A . grad instead of E . r).
 int launch_g_cell(const afem_mesh* m, const double* E, const double2* v, const double2* U, double2* z, int n,
-                  cudaStream_t s) {
+                  cudaStream_t s, int velocity) {
     CellArgs a = make_cell_args(m);
     a.c_kin = 0.5;
     a.with_pot = 1;
     a.masked = 1;
-    for (int i = 0; i < 3; ++i) a.E[i] = E ? E[i] : 0.0;
+    for (int i = 0; i < 3; ++i) a.E[i] = (E && !velocity) ? E[i] : 0.0;
+    if (velocity && E) {
+        a.vg = 1;
+        for (int i = 0; i < 3; ++i) a.Avec[i] = E[i];
+    }
     const int p = m->dev.p;
     const int nn = (p + 1) * (p + 1) * (p + 1);
     const size_t smem = size_t(nn) * n * sizeof(double2) + (U ? size_t(nn) * n * n * sizeof(double2) : 0);
@@ -190,7 +228,7 @@ int launch_g_cell(const afem_mesh* m, const double* E, const double2* v, const d
     switch (p) {
 #define AFEM_CASE(PP)                                                                          \
     case PP: {                                                                                 \
-        auto k = g_cell_kernel<PP>;                                                            \
+        auto k = a.vg ? g_cell_kernel<PP, true> : g_cell_kernel<PP, false>;                    \
         if (smem > 48 * 1024)                                                                  \
             AFEM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                                int(smem)));                                    \
@@ -237,7 +275,10 @@ CellArgs make_cell_args(const afem_mesh* m) {
     for (int i = 0; i < p1; ++i) {
         a.B.xi[i] = b.xi[i];
         a.B.w[i] = b.w[i];
-        for (int j = 0; j < p1; ++j) a.B.K[i * p1 + j] = b.K[i][j];
+        for (int j = 0; j < p1; ++j) {
+            a.B.K[i * p1 + j] = b.K[i][j];
+            a.B.S[i * p1 + j] = b.S[i][j];
+        }
     }
     return a;
 }
@@ -254,7 +295,9 @@ static int launch_cell_op(const afem_mesh* m, const CellArgs& a, const T* x, T* 
     switch (p) {
 #define AFEM_CASE(PP)                                                                          \
     case PP: {                                                                                 \
-        auto k = cell_op_kernel<PP, T>;                                                        \
+        auto k = cell_op_kernel<PP, T, false>;                                                 \
+        if constexpr (sizeof(T) == sizeof(double2))                                            \
+            if (a.vg) k = cell_op_kernel<PP, T, true>;                                         \
         if (smem > 48 * 1024)                                                                  \
             AFEM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                                int(smem)));                                    \
@@ -296,7 +339,7 @@ int launch_stiffness(const afem_mesh* m, const double* x, double* y, int nv, int
 int launch_stiffness32(const afem_mesh* m, const float* x, float* y, int nv, int masked, cudaStream_t s,
                        double* pap_slots = nullptr);
 int launch_g_cell32(const afem_mesh* m, const double* E, const float2* v, const float2* U, float2* z, int n,
-                    cudaStream_t s);
+                    cudaStream_t s, int velocity = 0);
 
 int launch_op_apply(afem_mesh* m, int kind, const double* E, const void* x, void* y, int nv,
                     cudaStream_t s) {
@@ -307,6 +350,18 @@ int launch_op_apply(afem_mesh* m, int kind, const double* E, const void* x, void
         a.with_pot = 1;
         a.masked = 1;
         for (int i = 0; i < 3; ++i) a.E[i] = E ? E[i] : 0.0;
+        auto* yy = static_cast<double2*>(y);
+        AFEM_CUDA_TRY(cudaMemsetAsync(yy, 0, size_t(N) * nv * sizeof(double2), s));
+        int rc = launch_cell_op<double2>(m, a, static_cast<const double2*>(x), yy, nv, s);
+        if (rc) return rc;
+        return launch_scale_rows<double2>(yy, m->dev.ml_inv, N, nv, s);
+    }
+    if (kind == AFEM_OP_H1_VG) {   // velocity gauge: E holds A
+        a.c_kin = 0.5;
+        a.with_pot = 1;
+        a.masked = 1;
+        a.vg = E ? 1 : 0;
+        for (int i = 0; i < 3; ++i) a.Avec[i] = E ? E[i] : 0.0;
         auto* yy = static_cast<double2*>(y);
         AFEM_CUDA_TRY(cudaMemsetAsync(yy, 0, size_t(N) * nv * sizeof(double2), s));
         int rc = launch_cell_op<double2>(m, a, static_cast<const double2*>(x), yy, nv, s);
@@ -334,9 +389,9 @@ int launch_op_apply(afem_mesh* m, int kind, const double* E, const void* x, void
     }
     if (kind == AFEM_OP_STIFF_F32)
         return launch_stiffness32(m, static_cast<const float*>(x), static_cast<float*>(y), nv, 0, s);
-    if (kind == AFEM_OP_H1_C64) {
+    if (kind == AFEM_OP_H1_C64 || kind == AFEM_OP_H1_VG_C64) {
         auto* yy = static_cast<float2*>(y);
-        int rc = launch_g_cell32(m, E, static_cast<const float2*>(x), nullptr, yy, nv, s);
+        int rc = launch_g_cell32(m, E, static_cast<const float2*>(x), nullptr, yy, nv, s, kind == AFEM_OP_H1_VG_C64);
         if (rc) return rc;
         return launch_scale_rows<float2>(yy, m->dev.ml_inv, N, nv, s);
     }

@@ -26,6 +26,7 @@ constexpr int kLmax = kMultipoleLmax;
 constexpr int kNlm = kMultipoleTerms;
 constexpr int kMomTile = 32;
 static int mom_blocks() { return 2 * device_sms(); }   // moment partial rows: 2 blocks per SM
+int mom_blocks_count() { return mom_blocks(); }
 __constant__ double c_sh_norm[kNlm];       // factor applied to C_lm / S_lm at index l*l + l + |m|
 __constant__ double c_sh_irreg[kLmax + 1];  // 4 pi / (2l + 1)
 
@@ -730,8 +731,13 @@ int poisson_rhs_bc(afem_mesh* m, const double2* phi, int n, double* W, double* b
     return AFEM_OK;
 }
 
+int poisson_batch_mg(afem_mesh* m, const double2* phi, int n, double* W, double rtol, int max_it, int warm, int mixed,
+                     int* iters_out, int* outer_out, double* relres_out, cudaStream_t s);
+
 int poisson_batch(afem_mesh* m, const double2* phi, int n, double* W, double rtol, int max_it, int warm,
                   int* iters_out, double* relres_out, cudaStream_t s) {
+    if (m->poisson_solver == AFEM_POISSON_MULTIGRID)
+        return poisson_batch_mg(m, phi, n, W, rtol, max_it, warm, 0, iters_out, nullptr, relres_out, s);
     const DeviceMesh& D = m->dev;
     const int k = n * n;
     const int64_t N = D.n_master, Ni = D.n_interior;
@@ -998,6 +1004,8 @@ __global__ void ru_finalize_kernel(const double* __restrict__ partial, int nblk,
 
 int poisson_batch_mixed(afem_mesh* m, const double2* phi, int n, double* W, double rtol, int max_it, int warm,
                         double delta, int* iters_out, int* outer_out, double* relres_out, cudaStream_t s) {
+    if (m->poisson_solver == AFEM_POISSON_MULTIGRID)
+        return poisson_batch_mg(m, phi, n, W, rtol, max_it, warm, 1, iters_out, outer_out, relres_out, s);
     const DeviceMesh& D = m->dev;
     const int k = n * n;
     const bool quads = (k % 4) == 0;   // four columns per thread in the float32 CG kernels

@@ -49,6 +49,39 @@ __device__ __forceinline__ float narrow_f64(double d) {
     if (rest > 0x10000000u || (rest == 0x10000000u && (keep & 1u))) r += 1u;
     return __uint_as_float(sign | r);
 }
+// narrow_f64(d * 2^k) with k added to the exponent field before rounding (no
+// floating-point multiply); zeros, infinities and NaNs as in narrow_f64.
+__device__ __forceinline__ float narrow_f64_scaled(double d, int k) {
+    const uint64_t b = static_cast<uint64_t>(__double_as_longlong(d));
+    const uint32_t sign = uint32_t(b >> 32) & 0x80000000u;
+    const int e = int((b >> 52) & 0x7FFull);
+    const uint64_t m = b & 0xFFFFFFFFFFFFFull;
+    if (e == 0x7FF) return __uint_as_float(sign | 0x7F800000u | (m ? 0x400000u : 0u));
+    if (e == 0) return __uint_as_float(sign);
+    const int ef = e - 896 + k;
+    if (ef <= 0) return __uint_as_float(sign);
+    if (ef >= 255) return __uint_as_float(sign | 0x7F800000u);
+    const uint32_t keep = uint32_t(m >> 29);
+    const uint32_t rest = uint32_t(m & 0x1FFFFFFFull);
+    uint32_t r = (uint32_t(ef) << 23) | keep;
+    if (rest > 0x10000000u || (rest == 0x10000000u && (keep & 1u))) r += 1u;
+    return __uint_as_float(sign | r);
+}
+// widen_f32(f) * 2^k through the exponent field: exact unless the result
+// leaves the binary64 normal range (zero or infinity then).
+__device__ __forceinline__ double widen_f32_scaled(float f, int k) {
+    const uint32_t u = __float_as_uint(f);
+    const int e = int((u >> 23) & 0xFFu);
+    uint64_t bits = uint64_t(u & 0x80000000u) << 32;
+    if (e == 0xFF) {
+        bits |= (0x7FFull << 52) | (uint64_t(u & 0x7FFFFFu) << 29);
+    } else if (e != 0) {
+        const int E = e + 896 + k;
+        if (E >= 0x7FF) bits |= 0x7FFull << 52;
+        else if (E > 0) bits |= (uint64_t(E) << 52) | (uint64_t(u & 0x7FFFFFu) << 29);
+    }
+    return __longlong_as_double(static_cast<long long>(bits));
+}
 // Streaming multiprocessors of the current device, looked up once per device.
 inline int device_sms() {
     static std::atomic<int> cache[64];

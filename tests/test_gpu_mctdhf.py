@@ -215,3 +215,135 @@ def test_mctdhf_steps_adaptive_dimension_parity():
         assert info["krylov_dim_sum"] == sum(info_o["krylov_dims"])
         assert info["krylov_m_used"] == max(info_o["krylov_dims"])
         _compare_step(phi, C, info, phi_o, C_o, info_o, perm, na + nb, 1e-10)
+
+
+def test_mctdhf_imaginary_time_parity():
+    """Imaginary-time steps (t = -i tau: exp(-dtau H_CI) normalised,
+    exp(-dtau G) by Arnoldi, Loewdin) against the oracle's step_imaginary:
+    two steps, FP64 within 1e-10 on orbitals, CI vector and energy."""
+    import torch
+    import paper_2301_02387_gb300 as pkg
+    case, n, na, nb = CASES[0]
+    gm = pkg.Mesh(*case)
+    om = omesh.Mesh(*case)
+    op = fem.Operators(om)
+    X, _, _ = gm.tables()
+    perm = coord_permutation(X, om.Xm)
+    phi_o = inputs.lowdin(inputs.molecular_orbitals(om.Xm, ~om.boundary, case[4], n), op.ML)
+    C_o = inputs.initial_ci(n, na, nb, amp=0.1)
+    sim = mctdhf.MCTDHF(op, n, na, nb)
+    solver = pkg.MCTDHF(gm, n, na, nb, 8)
+    solver.set_imaginary(True)
+    phi = torch.from_numpy(np.ascontiguousarray(phi_o[perm])).cuda()
+    C = torch.from_numpy(C_o.copy()).cuda()
+    W = torch.zeros((gm.N, n * n), dtype=torch.float64, device="cuda")
+    for step in range(2):
+        phi_o, C_o, info_o = sim.step_imaginary(phi_o, C_o, 0.05, 8)
+        info = solver.step(phi, C, W, None, 0.05, cg_rtol=1e-14, cg_max_it=20000, raise_on_maxit=False)
+        torch.cuda.synchronize()
+        assert_close(phi.cpu().numpy(), phi_o[perm], 1e-10, what="orbitals")
+        assert_close(C.cpu().numpy(), C_o, 1e-10, what="CI vector")
+        assert abs(info["energy"] - info_o["energy"]) < 1e-10 * abs(info_o["energy"])
+
+
+def test_mctdhf_imaginary_time_reaches_the_ground_state():
+    """One electron on a hanging-node mesh: imaginary-time steps with the
+    Krylov threshold converge to the lowest generalized eigenvalue of
+    (H1~, M_L) on the interior (scipy eigh on the oracle's matrices) within
+    1e-9; the energy decreases monotonically."""
+    import scipy.linalg
+    import torch
+    import paper_2301_02387_gb300 as pkg
+    case = (-6.0, 6.0, 2, 3, [((0.0, 0.0, 0.0), 1.0, 2)], 2.0)
+    gm = pkg.Mesh(*case)
+    om = omesh.Mesh(*case)
+    op = fem.Operators(om)
+    X, _, _ = gm.tables()
+    perm = coord_permutation(X, om.Xm)
+    I = np.nonzero(~om.boundary)[0]
+    lam = scipy.linalg.eigh(op.H1_matrix().toarray()[np.ix_(I, I)], np.diag(op.ML[I]), eigvals_only=True,
+                            subset_by_index=[0, 0])[0]
+    g = inputs.gaussian_orbital(om.Xm, ~om.boundary, alpha=0.5)[:, None]
+    phi_o = inputs.lowdin(g, op.ML)
+    solver = pkg.MCTDHF(gm, 1, 1, 0, 12)
+    solver.set_imaginary(True)
+    solver.set_krylov_tol(1e-12)
+    phi = torch.from_numpy(np.ascontiguousarray(phi_o[perm])).cuda()
+    C = torch.ones(1, dtype=torch.complex128, device="cuda")
+    W = torch.zeros((gm.N, 1), dtype=torch.float64, device="cuda")
+    energies = []
+    for _ in range(50):
+        energies.append(solver.step(phi, C, W, None, 1.0, cg_rtol=1e-12, cg_max_it=20000)["energy"])
+    energies.append(solver.step(phi, C, W, None, 1e-3, cg_rtol=1e-12, cg_max_it=20000)["energy"])
+    assert all(b <= a + 1e-9 * abs(a) for a, b in zip(energies, energies[1:]))
+    assert abs(energies[-1] - lam) < 1e-9 * abs(lam), (energies[-1], lam)
+    assert abs(-0.5 - lam) < 0.05   # the discrete hydrogen ground state (discretisation error)
+
+
+@pytest.mark.parametrize("precision_name", ["fp64", "mixed"])
+def test_mctdhf_steps_with_multigrid_poisson(precision_name):
+    """The step with the multigrid-preconditioned Poisson batch: the same
+    parity with the oracle's step (FP64 1e-10 over two steps, precision form
+    1e-6) as with the Jacobi batch."""
+    import torch
+    import paper_2301_02387_gb300 as pkg
+    case, n, na, nb = CASES[1]
+    gm = pkg.Mesh(*case)
+    pkg.mesh_set_option(gm, pkg.OPT_POISSON_SOLVER, pkg.POISSON_MULTIGRID)
+    om = omesh.Mesh(*case)
+    op = fem.Operators(om)
+    X, _, _ = gm.tables()
+    perm = coord_permutation(X, om.Xm)
+    phi_o = inputs.lowdin(inputs.molecular_orbitals(om.Xm, ~om.boundary, case[4], n), op.ML)
+    C_o = inputs.initial_ci(n, na, nb, amp=0.1)
+    sim = mctdhf.MCTDHF(op, n, na, nb)
+    solver = pkg.MCTDHF(gm, n, na, nb, 8)
+    fp64 = precision_name == "fp64"
+    if not fp64:
+        solver.set_precision(pkg.PREC_MIXED)
+    phi = torch.from_numpy(np.ascontiguousarray(phi_o[perm])).cuda()
+    C = torch.from_numpy(C_o.copy()).cuda()
+    W = torch.zeros((gm.N, n * n), dtype=torch.float64, device="cuda")
+    E = (0.0, 0.01, 0.03)
+    for step in range(2):
+        phi_o, C_o, info_o = sim.step(phi_o, C_o, E, 0.02, 8)
+        info = solver.step(phi, C, W, E, 0.02, cg_rtol=1e-14 if fp64 else 1e-12, cg_max_it=20000,
+                           raise_on_maxit=False)
+        torch.cuda.synchronize()
+        assert info["status"] == 0
+        _compare_step(phi, C, info, phi_o, C_o, info_o, perm, na + nb, 1e-10 if fp64 else 1e-6)
+
+
+@pytest.mark.parametrize("precision_name", ["fp64", "mixed"])
+def test_mctdhf_steps_velocity_gauge_parity(precision_name):
+    """The step in the velocity gauge of Sec. 2 (the step's field argument is
+    the vector potential A(t); -i A . grad in h_pq and in G) against the
+    oracle's step in the same gauge: FP64 1e-10 over two steps, precision
+    form 1e-6."""
+    import torch
+    import paper_2301_02387_gb300 as pkg
+    case, n, na, nb = CASES[1]
+    gm = pkg.Mesh(*case)
+    om = omesh.Mesh(*case)
+    op = fem.Operators(om)
+    X, _, _ = gm.tables()
+    perm = coord_permutation(X, om.Xm)
+    phi_o = inputs.lowdin(inputs.molecular_orbitals(om.Xm, ~om.boundary, case[4], n), op.ML)
+    C_o = inputs.initial_ci(n, na, nb, amp=0.1)
+    sim = mctdhf.MCTDHF(op, n, na, nb)
+    sim.gauge = "velocity"
+    solver = pkg.MCTDHF(gm, n, na, nb, 8)
+    solver.set_gauge(pkg.GAUGE_VELOCITY)
+    fp64 = precision_name == "fp64"
+    if not fp64:
+        solver.set_precision(pkg.PREC_MIXED)
+    phi = torch.from_numpy(np.ascontiguousarray(phi_o[perm])).cuda()
+    C = torch.from_numpy(C_o.copy()).cuda()
+    W = torch.zeros((gm.N, n * n), dtype=torch.float64, device="cuda")
+    A = (0.05, -0.2, 0.35)
+    for step in range(2):
+        phi_o, C_o, info_o = sim.step(phi_o, C_o, A, 0.02, 8)
+        info = solver.step(phi, C, W, A, 0.02, cg_rtol=1e-14 if fp64 else 1e-12, cg_max_it=20000,
+                           raise_on_maxit=False)
+        torch.cuda.synchronize()
+        _compare_step(phi, C, info, phi_o, C_o, info_o, perm, na + nb, 1e-10 if fp64 else 1e-6)

@@ -119,3 +119,30 @@ def test_h1_c64_within_fp32_tolerance(case, nvec, variant):
     op_apply(gm, OP_H1_C64, x, y, E=E)
     torch.cuda.synchronize()
     assert _relerr(y.to(torch.complex128).cpu().numpy(), yo[perm]) < 2e-5
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("nvec", [1, 4])
+def test_h1_velocity_gauge_parity(case, nvec):
+    """AFEM_OP_H1_VG (Sec. 2: -i A . grad, skew-symmetric form) against the
+    oracle's H1~(A): FP64 within 1e-10 per vector and per entry, complex64
+    within 2e-5 (on inputs rounded to complex64)."""
+    import torch
+    from paper_2301_02387_gb300 import op_apply, OP_H1_VG, OP_H1_VG_C64
+    gm, om, op, perm = _pair(case)
+    rng = np.random.default_rng(13)
+    xo = rng.standard_normal((om.N, nvec)) + 1j * rng.standard_normal((om.N, nvec))
+    A = (0.4, -0.25, 0.6)
+    yo = op.h1_apply(xo, A=A)
+    x = torch.from_numpy(np.ascontiguousarray(xo[perm])).cuda()
+    y = torch.empty_like(x)
+    op_apply(gm, OP_H1_VG, x, y, E=A)
+    torch.cuda.synchronize()
+    assert _relerr(y.cpu().numpy(), yo[perm]) < 1e-10
+    x32o = xo.astype(np.complex64).astype(np.complex128)
+    y32o = op.h1_apply(x32o, A=A)
+    x32 = torch.from_numpy(np.ascontiguousarray(x32o[perm])).to(torch.complex64).cuda()
+    y32 = torch.empty_like(x32)
+    op_apply(gm, OP_H1_VG_C64, x32, y32, E=A)
+    torch.cuda.synchronize()
+    assert _relerr(y32.to(torch.complex128).cpu().numpy(), y32o[perm]) < 2e-5

@@ -107,3 +107,58 @@ def test_h1_apply_masks_boundary():
     x2 = x.copy()
     x2[m.boundary] = 0
     np.testing.assert_array_equal(op.h1_apply(x2, E=(0.01, 0.0, -0.02)), y)
+
+
+# ------------------------------------------------------------- velocity gauge
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_gradient_matrices_identities(p):
+    """G_d (skew form of int b_k d_d b_l) is antisymmetric on the hanging-node
+    mesh, so -i A.G is Hermitian.  On a conforming mesh, at interior masters
+    whose support avoids the surface: G_x x = M_L and G_x y = 0, and for
+    p >= 2 G_x x^2 = 2 x M_L (GLL quadrature is exact for these degrees)."""
+    m, op = _ops(p)
+    for d in range(3):
+        G = op.gradient(d)
+        assert abs(G + G.T).max() < 1e-13 * abs(G).max()
+    mc, oc = _ops(p, dict(lo=-8.0, hi=8.0, nc=4, nuclei=[((0.3, -0.45, 0.7), 1.0, 0)], c=1.5))
+    assert mc.n_hanging == 0
+    deep = np.all(np.abs(mc.Xm) < 8.0 - 4.0 - 1e-9, axis=1)
+    for d in range(3):
+        G = oc.gradient(d)
+        xd, xo = mc.Xm[:, d], mc.Xm[:, (d + 1) % 3]
+        np.testing.assert_allclose((G @ xd)[deep], oc.ML[deep], rtol=1e-10, atol=0)
+        assert np.max(np.abs((G @ xo)[deep])) < 1e-10 * np.max(oc.ML)
+        if p >= 2:
+            np.testing.assert_allclose((G @ xd ** 2)[deep], 2.0 * xd[deep] * oc.ML[deep], rtol=1e-10,
+                                       atol=1e-10 * np.max(np.abs(xd) * oc.ML))
+
+
+def test_velocity_gauge_hamiltonian_is_hermitian_and_gauge_consistent():
+    """H1~(A) = 1/2 A + F[V] - i sum A_d G_d is Hermitian on the interior and
+    its expectation in a real orbital equals the field-free one (the
+    velocity term of a real function has zero expectation: antisymmetry)."""
+    m, op = _ops(3)
+    I = np.nonzero(~m.boundary)[0]
+    A = (0.03, -0.05, 0.08)
+    H = op.H1_matrix(A=A)[I][:, I]
+    assert abs(H - H.conj().T).max() < 1e-13 * abs(H).max()
+    rng = np.random.default_rng(2)
+    u = rng.standard_normal(len(I))
+    e0 = u @ (op.H1_matrix()[I][:, I] @ u)
+    eA = np.vdot(u, H @ u)
+    assert abs(eA.imag) < 1e-12 * abs(e0) and abs(eA.real - e0) < 1e-12 * abs(e0)
+
+
+def test_velocity_term_measures_momentum():
+    """Sign and factor of the velocity term: for u = exp(i k . x) g(x) with a
+    smooth real envelope g, <u, -i G_d u> / <u, M_L u> = k_d + O(h^p) (the
+    momentum of the plane wave; the envelope's own momentum is zero)."""
+    m, op = _ops(4, dict(lo=-8.0, hi=8.0, nc=6, nuclei=[((0.0, 0.0, 0.0), 1.0, 1)], c=1.5))
+    k = np.array([0.7, -0.4, 0.25])
+    g = np.exp(-0.15 * np.sum(m.Xm ** 2, axis=1))
+    u = g * np.exp(1j * (m.Xm @ k))
+    u[m.boundary] = 0.0
+    norm = np.vdot(u, op.ML * u).real
+    for d in range(3):
+        pd = np.vdot(u, -1j * (op.gradient(d) @ u)) / norm
+        assert abs(pd.imag) < 1e-12 and abs(pd.real - k[d]) < 2e-3, (d, pd)

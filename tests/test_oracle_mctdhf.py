@@ -327,6 +327,85 @@ def test_arnoldi_adaptive_reports_an_unmet_threshold_and_breakdown():
     np.testing.assert_allclose(out, np.exp(-0.2j) * e, atol=1e-15)
 
 
+# ------------------------------------------------------------ imaginary time
+def test_imaginary_time_one_electron_reaches_the_lowest_eigenvalue(tiny):
+    """One electron (no mean field): imaginary-time steps converge to the lowest
+    generalized eigenvalue of (H1~, M_L) on the interior (scipy eigh); the
+    energy decreases monotonically."""
+    m, op, phi0 = _one_electron_setup(tiny)
+    I = np.nonzero(~m.boundary)[0]
+    lam = scipy.linalg.eigh(op.H1_matrix().toarray()[np.ix_(I, I)], np.diag(op.ML[I]), eigvals_only=True)[0]
+    sim = mctdhf.MCTDHF(op, 1, 1, 0)
+    phi, C = phi0.copy(), np.array([1.0 + 0j])
+    energies = []
+    for _ in range(40):
+        phi, C, info = sim.step_imaginary(phi, C, 1.0, 12, krylov_tol=1e-12)
+        energies.append(info["energy"])
+    assert all(b <= a + 1e-13 for a, b in zip(energies, energies[1:]))
+    assert abs(sim.energy(phi, C) - lam) < 1e-9 * abs(lam)
+    assert abs(np.sum(op.ML * np.abs(phi[:, 0]) ** 2) - 1.0) < 1e-13
+
+
+def _scf_closed_shell(sim, op, phi, iters=200):
+    """Closed-shell Hartree-Fock of two electrons in one orbital by the
+    Roothaan fixed point, an independent route to the stationary state:
+    phi <- lowest generalized eigenvector of H1~ + F[V] on the interior, with
+    the Hartree potential V damped (V <- (V + W(|phi|^2)) / 2, which removes
+    the fixed point's two-cycle); energy 2 h + (00|00)."""
+    m = op.mesh
+    I = np.nonzero(~m.boundary)[0]
+    H1 = op.H1_matrix()
+    V = sim.mean_fields(phi)[0][0, 0].real
+    for _ in range(iters):
+        F = (H1 + op.pointwise(op.C @ V)).toarray()[np.ix_(I, I)]
+        ev, X = scipy.linalg.eigh(F, np.diag(op.ML[I]))
+        phi = np.zeros((m.N, 1), dtype=np.complex128)
+        phi[I, 0] = X[:, 0]
+        Wn = sim.mean_fields(phi)[0][0, 0].real
+        if np.abs(Wn - V).max() < 1e-13:
+            break
+        V = 0.5 * (V + Wn)
+    h, eri = sim.integrals(phi, sim.mean_fields(phi)[0], (0.0, 0.0, 0.0))
+    return phi, (2.0 * h[0, 0] + eri[0, 0, 0, 0]).real
+
+
+def test_imaginary_time_closed_shell_reaches_hartree_fock(tiny):
+    """Two electrons in one orbital: imaginary time converges to the
+    closed-shell Hartree-Fock state that the Roothaan fixed point gives."""
+    m, op, phi0 = _one_electron_setup(tiny)
+    sim = mctdhf.MCTDHF(op, 1, 1, 1)
+    _, e_hf = _scf_closed_shell(sim, op, phi0)
+    phi, C = phi0.copy(), np.array([1.0 + 0j])
+    energies = []
+    for _ in range(80):
+        phi, C, info = sim.step_imaginary(phi, C, 0.5, 12, krylov_tol=1e-12)
+        energies.append(info["energy"])
+    # monotone up to the second-order terms of the frozen-operator step near convergence
+    assert all(b <= a + 1e-9 * abs(a) for a, b in zip(energies, energies[1:]))
+    assert abs(sim.energy(phi, C) - e_hf) < 1e-8 * abs(e_hf)
+
+
+def test_imaginary_time_two_orbitals_lower_than_hartree_fock(tiny):
+    """Two orbitals, one alpha + one beta electron: the energy decreases
+    monotonically, ends below the closed-shell Hartree-Fock energy (the
+    variational space contains it) and the orbitals stay orthonormal."""
+    m, op = tiny
+    interior = ~m.boundary
+    phi = inputs.lowdin(inputs.molecular_orbitals(m.Xm, interior, TINY[4], 2, phase_noise=0.0), op.ML)
+    C = inputs.initial_ci(2, 1, 1, amp=0.1)
+    sim = mctdhf.MCTDHF(op, 2, 1, 1)
+    m1, op1, phi1 = _one_electron_setup(tiny)
+    _, e_hf = _scf_closed_shell(mctdhf.MCTDHF(op, 1, 1, 1), op, phi1)
+    energies = []
+    for _ in range(30):
+        phi, C, info = sim.step_imaginary(phi, C, 0.5, 12, krylov_tol=1e-12)
+        energies.append(info["energy"])
+    assert all(b <= a + 1e-9 * abs(a) for a, b in zip(energies, energies[1:]))
+    assert sim.energy(phi, C) < e_hf
+    S = np.conj(phi).T @ (op.ML[:, None] * phi)
+    assert np.abs(S - np.eye(2)).max() < 1e-13
+
+
 # ------------------------------------------------------------------- dipole
 def _dipole_state(case, n, na, nb):
     m = mesh.Mesh(*case)
