@@ -78,7 +78,25 @@ typedef struct afem_mesh_desc {
     double nuc_charge[AFEM_MAX_NUCLEI];     /* nuclear charges Z_a */
     int32_t nuc_levels[AFEM_MAX_NUCLEI];    /* refinement levels L_a toward each nucleus */
     double refine_c;                        /* refinement radius in units of the cell side */
+    int32_t refine_mode;                    /* AFEM_REFINE_GEOMETRIC (0) or AFEM_REFINE_KELLY (1) */
+    int32_t kelly_max_level;                /* Kelly: finest level (smallest cell h0 / 2^level), 0..12 */
+    double kelly_threshold;                 /* Kelly: split a leaf while eta_K > threshold (> 0) */
 } afem_mesh_desc;
+/* Refinement rules.  AFEM_REFINE_GEOMETRIC: a leaf of level l is split while
+ * some nucleus a with l < nuc_levels[a] lies within refine_c * h_l of the
+ * closed cell.  AFEM_REFINE_KELLY (Sec. 3.1): every round splits each leaf
+ * below kelly_max_level whose Kelly indicator on the nuclear Coulomb potential
+ * exceeds kelly_threshold, eta_K^2 = (h_K / 24) sum over its faces of
+ * int_F [d_n V_h]^2 (V_h the cellwise interpolant of V = -sum Z_a / |r - R_a|
+ * at the cell's GLL nodes, at a node on a nucleus with 1/|r| replaced by its
+ * mean over a cube of the node's GLL volume; a coarser or equal neighbour leaf covers the whole
+ * face, four finer ones a quarter each; (p+1)^2-point Gauss-Legendre rule per
+ * (sub)face; no term on the box surface; a leaf whose closed box contains a
+ * nucleus counts as above any threshold), until no leaf splits.  Both rules
+ * end with 2:1 balance across faces, edges and vertices (Kelly: after every
+ * round). */
+#define AFEM_REFINE_GEOMETRIC 0
+#define AFEM_REFINE_KELLY 1
 
 typedef struct afem_mesh_info {
     int64_t n_cells;        /* leaf cells */

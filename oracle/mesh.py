@@ -2,10 +2,11 @@
 
 Sec. 3.1: the box is first covered by coarse uniform cubes; cells near the
 nuclei are repeatedly halved.  The paper drives the refinement by Kelly's
-indicator on the nuclear Coulomb potential; this oracle uses the geometric
-rule of the workloads instead: a leaf of level l is split while some nucleus a
-with l < L_a lies within distance c * h_l of the closed cell, and afterwards
-the leaves are 2:1 balanced across faces, edges and vertices.
+indicator on the nuclear Coulomb potential (`refine_leaves_kelly`, with a
+threshold and a smallest cell size); the workloads use a geometric rule:
+a leaf of level l is split while some nucleus a with l < L_a lies within
+distance c * h_l of the closed cell.  Either way the leaves are 2:1 balanced
+across faces, edges and vertices.
 
 The finite-element space is the conforming Q_p space on the leaves: the cell
 basis functions are tensor products of 1D Lagrange polynomials through the
@@ -112,6 +113,144 @@ def balance_leaves(leaves, nc):
                 leafset.add((l + 1, 2 * i + a, 2 * j + b, 2 * k + d))
 
 
+# ------------------------------------------------------- Kelly refinement
+# mean of 1/|r| over the unit cube centred at the origin: 3 ln(2 + sqrt 3) - pi/2
+_CUBE_MEAN_INV_R = 3.0 * np.log(2.0 + np.sqrt(3.0)) - np.pi / 2.0
+
+
+def _coulomb(X, nuclei, s):
+    """V = -sum Z / |x - R| at the points X; at a point on a nucleus the mean of
+    1/|r| over a cube of side s (the point's GLL volume) replaces 1/|r|."""
+    V = np.zeros(len(X))
+    for (R, Z, _L) in nuclei:
+        d = np.linalg.norm(X - R[None, :], axis=1)
+        on = d <= 1e-10
+        V[~on] -= Z / d[~on]
+        V[on] -= Z * _CUBE_MEAN_INV_R / s[on]
+    return V
+
+
+def _contains_nucleus(corner, h, nuclei):
+    return any(_box_dist2(corner, h, R) == 0.0 for (R, _Z, _L) in nuclei)
+
+
+def kelly_indicators(leafset, nc, lo, h0, p, nuclei):
+    """eta_K^2 of every leaf: (h_K / 24) sum over its faces F of int_F [d_n V_h]^2.
+
+    Sec. 3.1: Kelly's indicator on the Coulomb potential of the nuclei.  V_h is
+    the cellwise interpolant of V = -sum Z_a / |r - R_a| at the cell's GLL
+    nodes; [d_n V_h] the jump of its normal derivative between the cell and
+    the leaf across each (sub)face (a coarser leaf covers the whole face, four
+    finer leaves a quarter each; at a node on a nucleus 1/|r| is replaced by
+    its mean over a cube of the node's GLL volume, as for the potential), integrated by the (p+1) x (p+1)
+    Gauss-Legendre rule of the (sub)face; faces on the box surface carry no
+    jump.  A leaf whose closed box contains a nucleus gets +inf (V is
+    unbounded there).  Returns {leaf: eta^2}.
+    """
+    xi, w = gll.gll_nodes_weights(p)
+    wcube = np.array([np.cbrt(w[a] * w[b] * w[cc])
+                      for cc in range(p + 1) for b in range(p + 1) for a in range(p + 1)])
+    gx, gw = np.polynomial.legendre.leggauss(p + 1)
+    gx = 0.5 * (gx + 1.0)
+    gw = 0.5 * gw
+    cache = {}
+
+    def cell_geom(leaf):
+        l, i, j, k = leaf
+        h = h0 / 2 ** l
+        return h, np.array([lo + i * h, lo + j * h, lo + k * h])
+
+    def coeffs(leaf):
+        if leaf not in cache:
+            h, c0 = cell_geom(leaf)
+            pts = np.array([[c0[0] + h * xi[a], c0[1] + h * xi[b], c0[2] + h * xi[cc]]
+                             for cc in range(p + 1) for b in range(p + 1) for a in range(p + 1)])
+            cache[leaf] = _coulomb(pts, nuclei, h * wcube).reshape(p + 1, p + 1, p + 1)   # [c][b][a]
+        return cache[leaf]
+
+    def dn(leaf, X, d):
+        """d/dx_d of the leaf's interpolant at the points X (m, 3)."""
+        h, c0 = cell_geom(leaf)
+        T = (X - c0[None, :]) / h
+        Lx = gll.lagrange_matrix(xi, T[:, 0])
+        Ly = gll.lagrange_matrix(xi, T[:, 1])
+        Lz = gll.lagrange_matrix(xi, T[:, 2])
+        D = gll.lagrange_deriv_matrix(xi, T[:, d]) / h
+        M = [Lx, Ly, Lz]
+        M[d] = D
+        return np.einsum("cba,ma,mb,mc->m", coeffs(leaf), M[0], M[1], M[2])
+
+    def face_points(c0, h, d, side):
+        """Gauss points (m, 3) and weights (m,) of the face x_d = c0_d + side h."""
+        o = [a for a in range(3) if a != d]
+        U, W = np.meshgrid(gx, gx, indexing="ij")
+        X = np.zeros((U.size, 3))
+        X[:, d] = c0[d] + side * h
+        X[:, o[0]] = c0[o[0]] + h * U.ravel()
+        X[:, o[1]] = c0[o[1]] + h * W.ravel()
+        wts = (gw[:, None] * gw[None, :]).ravel() * h * h
+        return X, wts
+
+    eta2 = {}
+    for leaf in leafset:
+        l, i, j, k = leaf
+        h, c0 = cell_geom(leaf)
+        if _contains_nucleus(c0, h, nuclei):
+            eta2[leaf] = np.inf
+            continue
+        n = nc << l
+        tot = 0.0
+        for d in range(3):
+            for side in (0, 1):
+                nb = [i, j, k]
+                nb[d] += 1 if side else -1
+                if not (0 <= nb[d] < n):
+                    continue
+                f = _find_leaf(leafset, l, *nb)
+                if f is not None:   # a leaf of the same or a coarser level covers the face
+                    X, wts = face_points(c0, h, d, side)
+                    J = dn(leaf, X, d) - dn(f, X, d)
+                    tot += np.sum(wts * J * J)
+                else:               # four finer leaves (2:1 balance), one quarter face each
+                    hs = 0.5 * h
+                    o = [a for a in range(3) if a != d]
+                    for u in (0, 1):
+                        for v in (0, 1):
+                            ch = [2 * nb[0], 2 * nb[1], 2 * nb[2]]
+                            ch[d] += 0 if side else 1
+                            ch[o[0]] += u
+                            ch[o[1]] += v
+                            fine = (l + 1, ch[0], ch[1], ch[2])
+                            cs = c0.copy()
+                            cs[o[0]] += u * hs
+                            cs[o[1]] += v * hs
+                            X, wts = face_points(cs, hs, d, 0)
+                            X[:, d] = c0[d] + side * h
+                            J = dn(leaf, X, d) - dn(fine, X, d)
+                            tot += np.sum(wts * J * J)
+        eta2[leaf] = h / 24.0 * tot
+    return eta2
+
+
+def refine_leaves_kelly(nc, lo, h0, p, nuclei, theta, max_level):
+    """Leaves after Kelly refinement (Sec. 3.1): starting from the uniform
+    coarse cubes, every round splits each leaf with eta_K > theta (eta_K^2
+    from `kelly_indicators`) whose level is below max_level (the smallest
+    cell size; the largest is the coarse cube), then restores the 2:1 balance;
+    rounds repeat until no leaf is split."""
+    leaves = set(itertools.product([0], range(nc), range(nc), range(nc)))
+    while True:
+        eta2 = kelly_indicators(leaves, nc, lo, h0, p, nuclei)
+        marked = [lf for lf in leaves if lf[0] < max_level and eta2[lf] > theta * theta]
+        if not marked:
+            return leaves
+        for (l, i, j, k) in marked:
+            leaves.remove((l, i, j, k))
+            for a, b, d in itertools.product((0, 1), repeat=3):
+                leaves.add((l + 1, 2 * i + a, 2 * j + b, 2 * k + d))
+        leaves = balance_leaves(leaves, nc)
+
+
 class Mesh:
     """Leaves, support points, masters, hanging constraints and the boundary.
 
@@ -128,14 +267,20 @@ class Mesh:
       Xm (N, 3)                        master coordinates
     """
 
-    def __init__(self, lo, hi, nc, p, nuclei, c=2.0):
+    def __init__(self, lo, hi, nc, p, nuclei, c=2.0, kelly=None):
+        """kelly: None (the geometric rule) or (theta, max_level) for Kelly
+        refinement on the Coulomb potential (`refine_leaves_kelly`)."""
         self.lo, self.hi, self.nc, self.p = float(lo), float(hi), int(nc), int(p)
         self.h0 = (self.hi - self.lo) / self.nc
         self.nuclei = [(np.asarray(R, dtype=np.float64), float(Z), int(L)) for (R, Z, L) in nuclei]
         self.c = float(c)
         self.xi, self.w = gll.gll_nodes_weights(self.p)
-        leaves = refine_leaves(self.nc, self.lo, self.h0, self.nuclei, self.c)
-        leaves = balance_leaves(leaves, self.nc)
+        if kelly is None:
+            leaves = refine_leaves(self.nc, self.lo, self.h0, self.nuclei, self.c)
+            leaves = balance_leaves(leaves, self.nc)
+        else:
+            leaves = refine_leaves_kelly(self.nc, self.lo, self.h0, self.p, self.nuclei, float(kelly[0]),
+                                         int(kelly[1]))
         leaves = sorted(leaves)
         self.lev = np.array([t[0] for t in leaves], dtype=np.int64)
         self.ijk = np.array([t[1:] for t in leaves], dtype=np.int64)

@@ -44,9 +44,11 @@ class Mesh:
     """Adaptive octree mesh (Sec. 3.1) built on the host and resident on the current GPU.
 
     nuclei: sequence of (position (3,), charge Z, refinement levels L).
+    kelly: None (the geometric rule toward the nuclei) or (threshold,
+    max_level) for Kelly refinement on the nuclear Coulomb potential.
     """
 
-    def __init__(self, lo, hi, n_coarse, degree, nuclei, refine_c=2.0, host_only=False):
+    def __init__(self, lo, hi, n_coarse, degree, nuclei, refine_c=2.0, host_only=False, kelly=None):
         lib = _capi.load()
         d = _capi.MeshDesc()
         d.lo, d.hi = float(lo), float(hi)
@@ -61,6 +63,10 @@ class Mesh:
             d.nuc_charge[a] = float(Z)
             d.nuc_levels[a] = int(L)
         d.refine_c = float(refine_c)
+        if kelly is not None:
+            d.refine_mode = 1
+            d.kelly_threshold = float(kelly[0])
+            d.kelly_max_level = int(kelly[1])
         self.desc = d
         self.nuclei = [(np.asarray(R, dtype=np.float64), float(Z), int(L)) for (R, Z, L) in nuclei]
         h = ctypes.c_void_p()

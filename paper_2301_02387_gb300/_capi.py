@@ -54,6 +54,8 @@ class MeshDesc(ctypes.Structure):
         ("nuc_charge", ctypes.c_double * MAX_NUCLEI),
         ("nuc_levels", ctypes.c_int32 * MAX_NUCLEI),
         ("refine_c", ctypes.c_double),
+        ("refine_mode", ctypes.c_int32), ("kelly_max_level", ctypes.c_int32),
+        ("kelly_threshold", ctypes.c_double),
     ]
 
 

@@ -109,6 +109,13 @@ struct HostMesh {
 };
 
 int build_host_mesh(const afem_mesh_desc& d, HostMesh& out);
+// The same from explicit leaves (level, i, j, k), 2:1-balanced here; the
+// description supplies the box, degree and nuclei (its refinement is unused).
+int build_host_mesh_cells(const afem_mesh_desc& d, const std::vector<int32_t>& lev, const std::vector<int32_t>& ci,
+                          const std::vector<int32_t>& cj, const std::vector<int32_t>& ck, HostMesh& out);
+// A device mesh from explicit leaves (see build_host_mesh_cells).
+int create_mesh_from_cells(const afem_mesh_desc& d, const std::vector<int32_t>& lev, const std::vector<int32_t>& ci,
+                           const std::vector<int32_t>& cj, const std::vector<int32_t>& ck, afem_mesh** out);
 
 // Device-resident mesh.
 struct DeviceMesh {

@@ -79,6 +79,29 @@ ProfScope::~ProfScope() {
 
 using namespace afem;
 
+namespace afem {
+int create_mesh_from_cells(const afem_mesh_desc& d, const std::vector<int32_t>& lev, const std::vector<int32_t>& ci,
+                           const std::vector<int32_t>& cj, const std::vector<int32_t>& ck, afem_mesh** out) {
+    *out = nullptr;
+    afem_mesh* m = new (std::nothrow) afem_mesh();
+    if (!m) return set_error(AFEM_ENOMEM, "mesh: host allocation failed");
+    m->desc = d;
+    int rc = build_host_mesh_cells(d, lev, ci, cj, ck, m->host);
+    if (rc == AFEM_OK) {
+        m->basis = make_basis(d.degree);
+        cudaError_t e = cudaGetDevice(&m->device);
+        rc = e == cudaSuccess ? upload_mesh(m) : cuda_error(e, "cudaGetDevice");
+    }
+    if (rc != AFEM_OK) {
+        free_device_mesh(m->dev);
+        delete m;
+        return rc;
+    }
+    *out = m;
+    return AFEM_OK;
+}
+}  // namespace afem
+
 extern "C" {
 
 const char* afem_last_error(void) { return last_error_cstr(); }
@@ -131,6 +154,12 @@ int afem_mesh_create_ex(const afem_mesh_desc* desc, int flags, afem_mesh** out) 
     for (int n = 0; n < d.n_nuclei; ++n)
         if (d.nuc_levels[n] < 0 || d.nuc_levels[n] > 12)
             return set_error(AFEM_EINVAL, "afem_mesh_create: nuc_levels must be 0..12");
+    if (d.refine_mode != AFEM_REFINE_GEOMETRIC && d.refine_mode != AFEM_REFINE_KELLY)
+        return set_error(AFEM_EINVAL, "afem_mesh_create: unknown refine_mode");
+    if (d.refine_mode == AFEM_REFINE_KELLY &&
+        (d.kelly_max_level < 0 || d.kelly_max_level > 12 || !(d.kelly_threshold > 0.0)))
+        return set_error(AFEM_EINVAL, "afem_mesh_create: Kelly refinement needs kelly_max_level 0..12 and a "
+                                      "threshold > 0");
     afem_mesh* m = new (std::nothrow) afem_mesh();
     if (!m) return set_error(AFEM_ENOMEM, "afem_mesh_create: host allocation failed");
     m->desc = d;
@@ -151,6 +180,7 @@ int afem_mesh_create_ex(const afem_mesh_desc* desc, int flags, afem_mesh** out) 
     *out = m;
     return AFEM_OK;
 }
+
 
 int afem_mesh_destroy(afem_mesh* mesh) {
     if (!mesh) return AFEM_OK;

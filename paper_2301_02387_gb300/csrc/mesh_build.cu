@@ -111,6 +111,36 @@ double lagrange_value(const Basis1D& b, int j, double t) {
     return v;
 }
 
+// L_j'(t) by the product rule on the Lagrange product form.
+static double lagrange_deriv(const Basis1D& b, int j, double t) {
+    double d = 0.0;
+    for (int k = 0; k <= b.p; ++k) {
+        if (k == j) continue;
+        double term = 1.0 / (b.xi[j] - b.xi[k]);
+        for (int m = 0; m <= b.p; ++m)
+            if (m != j && m != k) term *= (t - b.xi[m]) / (b.xi[j] - b.xi[m]);
+        d += term;
+    }
+    return d;
+}
+
+// n-point Gauss-Legendre rule on [0, 1] (roots of P_n by Newton's method).
+static void gauss_legendre01(int n, double* x, double* w) {
+    for (int i = 0; i < n; ++i) {
+        double t = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+        double P = 0.0, dP = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            legendre_and_deriv(n, t, P, dP);
+            const double step = P / dP;
+            t -= step;
+            if (std::fabs(step) < 1e-16) break;
+        }
+        legendre_and_deriv(n, t, P, dP);
+        x[n - 1 - i] = 0.5 * (t + 1.0);
+        w[n - 1 - i] = 1.0 / ((1.0 - t * t) * dP * dP);   // 2 / ((1 - t^2) P'^2), halved for [0, 1]
+    }
+}
+
 // ------------------------------------------------------------ octree
 namespace {
 
@@ -147,7 +177,132 @@ uint64_t spread3(uint64_t v) {  // 21 bits -> every third bit
 
 }  // namespace
 
-int build_host_mesh(const afem_mesh_desc& d, HostMesh& M) {
+// eta_K^2 of Kelly's indicator on the Coulomb potential of the nuclei (Sec. 3.1):
+// (h_K / 24) sum over the faces F of int_F [d_n V_h]^2, V_h the cellwise GLL
+// interpolant of V = -sum Z_a / |r - R_a|, [d_n V_h] the jump of its normal
+// derivative to the leaf across each (sub)face (a coarser or equal leaf covers
+// the whole face, four finer leaves a quarter each), integrated by the
+// (p+1) x (p+1) Gauss-Legendre rule of the (sub)face; no term on the box
+// surface; +inf for a leaf whose closed box contains a nucleus.
+static const double kelly_c3 = 3.0 * std::log(2.0 + std::sqrt(3.0)) - M_PI / 2.0;
+
+template <typename FindLeaf>
+static double kelly_eta2(const afem_mesh_desc& d, const Basis1D& B, const Leaf& c, FindLeaf& find_leaf) {
+    const int p = B.p, p1 = p + 1;
+    const double h0 = (d.hi - d.lo) / d.n_coarse;
+    auto geom = [&](const Leaf& f, double& h, double* c0) {
+        h = h0 / double(int64_t(1) << f.l);
+        c0[0] = d.lo + double(f.i) * h;
+        c0[1] = d.lo + double(f.j) * h;
+        c0[2] = d.lo + double(f.k) * h;
+    };
+    double h, c0[3];
+    geom(c, h, c0);
+    for (int n = 0; n < d.n_nuclei; ++n) {
+        bool in = true;
+        for (int ax = 0; ax < 3; ++ax)
+            if (d.nuc_pos[n][ax] < c0[ax] || d.nuc_pos[n][ax] > c0[ax] + h) in = false;
+        if (in) return HUGE_VAL;
+    }
+    // nodal values V[c][b][a] of a leaf
+    auto values = [&](const Leaf& f, double* V) {
+        double hf, cf[3];
+        geom(f, hf, cf);
+        for (int cz = 0; cz < p1; ++cz)
+            for (int cy = 0; cy < p1; ++cy)
+                for (int cx = 0; cx < p1; ++cx) {
+                    const double x = cf[0] + hf * B.xi[cx], y = cf[1] + hf * B.xi[cy], z = cf[2] + hf * B.xi[cz];
+                    double v = 0.0;
+                    for (int n = 0; n < d.n_nuclei; ++n) {
+                        const double dx = x - d.nuc_pos[n][0], dy = y - d.nuc_pos[n][1], dz = z - d.nuc_pos[n][2];
+                        const double r = std::sqrt(dx * dx + dy * dy + dz * dz);
+                        // a node on a nucleus: the mean of 1/|r| over a cube of the node's GLL volume
+                        v -= r > 1e-10 ? d.nuc_charge[n] / r
+                                       : d.nuc_charge[n] * kelly_c3 / (hf * std::cbrt(B.w[cx] * B.w[cy] * B.w[cz]));
+                    }
+                    V[(cz * p1 + cy) * p1 + cx] = v;
+                }
+    };
+    // d/dx_ax of a leaf's interpolant at point X
+    auto dn = [&](const Leaf& f, const double* V, const double* X, int ax) {
+        double hf, cf[3];
+        geom(f, hf, cf);
+        double L[3][kMaxP1];
+        for (int q = 0; q < 3; ++q) {
+            const double t = (X[q] - cf[q]) / hf;
+            for (int a = 0; a < p1; ++a) L[q][a] = q == ax ? lagrange_deriv(B, a, t) / hf : lagrange_value(B, a, t);
+        }
+        double r = 0.0;
+        for (int cz = 0; cz < p1; ++cz)
+            for (int cy = 0; cy < p1; ++cy)
+                for (int cx = 0; cx < p1; ++cx) r += V[(cz * p1 + cy) * p1 + cx] * L[0][cx] * L[1][cy] * L[2][cz];
+        return r;
+    };
+    double gx[kMaxP1], gw[kMaxP1];
+    gauss_legendre01(p1, gx, gw);
+    double Vc[kMaxP1 * kMaxP1 * kMaxP1], Vn[kMaxP1 * kMaxP1 * kMaxP1];
+    values(c, Vc);
+    const int64_t nmax = int64_t(d.n_coarse) << c.l;
+    double tot = 0.0;
+    // int over the square face (corner fc, side hs, normal ax at x_ax = xf) of the jump to leaf f
+    auto face = [&](const Leaf& f, const double* Vf, const double* fc, double hs, int ax, double xf) {
+        const int o0 = ax == 0 ? 1 : 0, o1 = ax == 2 ? 1 : 2;
+        double acc = 0.0;
+        for (int a = 0; a < p1; ++a)
+            for (int b = 0; b < p1; ++b) {
+                double X[3];
+                X[ax] = xf;
+                X[o0] = fc[o0] + hs * gx[a];
+                X[o1] = fc[o1] + hs * gx[b];
+                const double J = dn(c, Vc, X, ax) - dn(f, Vf, X, ax);
+                acc += gw[a] * gw[b] * hs * hs * J * J;
+            }
+        return acc;
+    };
+    for (int ax = 0; ax < 3; ++ax)
+        for (int side = 0; side < 2; ++side) {
+            int64_t nb[3] = {c.i, c.j, c.k};
+            nb[ax] += side ? 1 : -1;
+            if (nb[ax] < 0 || nb[ax] >= nmax) continue;
+            Leaf f;
+            const double xf = c0[ax] + side * h;
+            if (find_leaf(c.l, nb[0], nb[1], nb[2], f)) {
+                values(f, Vn);
+                tot += face(f, Vn, c0, h, ax, xf);
+            } else {
+                const int o0 = ax == 0 ? 1 : 0, o1 = ax == 2 ? 1 : 2;
+                for (int u = 0; u < 2; ++u)
+                    for (int v = 0; v < 2; ++v) {
+                        int64_t ch[3] = {2 * nb[0], 2 * nb[1], 2 * nb[2]};
+                        ch[ax] += side ? 0 : 1;
+                        ch[o0] += u;
+                        ch[o1] += v;
+                        const Leaf fine{c.l + 1, ch[0], ch[1], ch[2]};
+                        double cs[3] = {c0[0], c0[1], c0[2]};
+                        cs[o0] += u * 0.5 * h;
+                        cs[o1] += v * 0.5 * h;
+                        values(fine, Vn);
+                        tot += face(fine, Vn, cs, 0.5 * h, ax, xf);
+                    }
+            }
+        }
+    return h / 24.0 * tot;
+}
+
+static int build_host_mesh_leaves(const afem_mesh_desc& d, const std::vector<Leaf>* given, HostMesh& M);
+
+int build_host_mesh(const afem_mesh_desc& d, HostMesh& M) { return build_host_mesh_leaves(d, nullptr, M); }
+
+int build_host_mesh_cells(const afem_mesh_desc& d, const std::vector<int32_t>& lev, const std::vector<int32_t>& ci,
+                          const std::vector<int32_t>& cj, const std::vector<int32_t>& ck, HostMesh& M) {
+    std::vector<Leaf> given(lev.size());
+    for (size_t q = 0; q < lev.size(); ++q) given[q] = {lev[q], ci[q], cj[q], ck[q]};
+    return build_host_mesh_leaves(d, &given, M);
+}
+
+// Builds the mesh from `given` leaves (balanced here) when non-null, else
+// from the refinement rule of the description.
+static int build_host_mesh_leaves(const afem_mesh_desc& d, const std::vector<Leaf>* given, HostMesh& M) {
     const int p = d.degree;
     const int p1 = p + 1;
     const int nn = p1 * p1 * p1;
@@ -160,53 +315,7 @@ int build_host_mesh(const afem_mesh_desc& d, HostMesh& M) {
     const double h0 = M.h0;
     const Basis1D B = make_basis(p);
 
-    // ---- refinement toward the nuclei (geometric stand-in for Kelly's indicator)
     std::vector<Leaf> leaves;
-    leaves.reserve(size_t(nc) * nc * nc);
-    for (int i = 0; i < nc; ++i)
-        for (int j = 0; j < nc; ++j)
-            for (int k = 0; k < nc; ++k) leaves.push_back({0, i, j, k});
-    for (;;) {
-        bool any = false;
-        std::vector<Leaf> next;
-        next.reserve(leaves.size() * 2);
-        for (const Leaf& c : leaves) {
-            const double h = h0 / double(int64_t(1) << c.l);
-            const double a[3] = {d.lo + double(c.i) * h, d.lo + double(c.j) * h, d.lo + double(c.k) * h};
-            bool split = false;
-            for (int n = 0; n < d.n_nuclei && !split; ++n) {
-                if (c.l >= d.nuc_levels[n]) continue;
-                double d2 = 0.0;
-                for (int ax = 0; ax < 3; ++ax) {
-                    const double R = d.nuc_pos[n][ax];
-                    const double b = a[ax] + h;
-                    if (R < a[ax]) {
-                        const double t = a[ax] - R;
-                        d2 += t * t;
-                    } else if (R > b) {
-                        const double t = R - b;
-                        d2 += t * t;
-                    }
-                }
-                const double ch = d.refine_c * h;
-                split = d2 <= ch * ch;
-            }
-            if (split) {
-                any = true;
-                for (int s = 0; s < 8; ++s)
-                    next.push_back({c.l + 1, 2 * c.i + (s & 1), 2 * c.j + ((s >> 1) & 1),
-                                    2 * c.k + ((s >> 2) & 1)});
-            } else {
-                next.push_back(c);
-            }
-        }
-        leaves.swap(next);
-        if (!any) break;
-        if (leaves.size() > (size_t(1) << 26))
-            return set_error(AFEM_EMESH, "mesh: more than 2^26 leaves");
-    }
-
-    // ---- 2:1 balance across faces, edges and vertices
     std::unordered_set<uint64_t> leafset;
     auto rebuild_set = [&]() {
         leafset.clear();
@@ -224,37 +333,113 @@ int build_host_mesh(const afem_mesh_desc& d, HostMesh& M) {
         }
         return false;
     };
-    rebuild_set();
-    for (;;) {
-        std::unordered_set<uint64_t> split;
-        for (const Leaf& c : leaves) {
-            if (c.l < 2) continue;
-            const int64_t n = int64_t(nc) << c.l;
-            for (int dz = -1; dz <= 1; ++dz)
-                for (int dy = -1; dy <= 1; ++dy)
-                    for (int dx = -1; dx <= 1; ++dx) {
-                        if (!dx && !dy && !dz) continue;
-                        const int64_t a = c.i + dx, b = c.j + dy, e = c.k + dz;
-                        if (a < 0 || b < 0 || e < 0 || a >= n || b >= n || e >= n) continue;
-                        Leaf f;
-                        if (find_leaf(c.l, a, b, e, f) && f.l < c.l - 1)
-                            split.insert(leaf_key(f.l, f.i, f.j, f.k));
-                    }
-        }
-        if (split.empty()) break;
-        std::vector<Leaf> next;
-        next.reserve(leaves.size() + 8 * split.size());
-        for (const Leaf& c : leaves) {
-            if (split.count(leaf_key(c.l, c.i, c.j, c.k))) {
-                for (int s = 0; s < 8; ++s)
-                    next.push_back({c.l + 1, 2 * c.i + (s & 1), 2 * c.j + ((s >> 1) & 1),
-                                    2 * c.k + ((s >> 2) & 1)});
-            } else {
-                next.push_back(c);
-            }
-        }
-        leaves.swap(next);
+    auto split_into = [](const Leaf& c, std::vector<Leaf>& next) {
+        for (int s = 0; s < 8; ++s)
+            next.push_back({c.l + 1, 2 * c.i + (s & 1), 2 * c.j + ((s >> 1) & 1), 2 * c.k + ((s >> 2) & 1)});
+    };
+    // 2:1 balance across faces, edges and vertices
+    auto balance = [&]() -> int {
         rebuild_set();
+        for (;;) {
+            std::unordered_set<uint64_t> split;
+            for (const Leaf& c : leaves) {
+                if (c.l < 2) continue;
+                const int64_t n = int64_t(nc) << c.l;
+                for (int dz = -1; dz <= 1; ++dz)
+                    for (int dy = -1; dy <= 1; ++dy)
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            if (!dx && !dy && !dz) continue;
+                            const int64_t a = c.i + dx, b = c.j + dy, e = c.k + dz;
+                            if (a < 0 || b < 0 || e < 0 || a >= n || b >= n || e >= n) continue;
+                            Leaf f;
+                            if (find_leaf(c.l, a, b, e, f) && f.l < c.l - 1)
+                                split.insert(leaf_key(f.l, f.i, f.j, f.k));
+                        }
+            }
+            if (split.empty()) return AFEM_OK;
+            std::vector<Leaf> next;
+            next.reserve(leaves.size() + 8 * split.size());
+            for (const Leaf& c : leaves) {
+                if (split.count(leaf_key(c.l, c.i, c.j, c.k))) split_into(c, next);
+                else next.push_back(c);
+            }
+            leaves.swap(next);
+            if (leaves.size() > (size_t(1) << 26)) return set_error(AFEM_EMESH, "mesh: more than 2^26 leaves");
+            rebuild_set();
+        }
+    };
+    int brc;
+    if (given) {
+        // ---- explicit leaves (a coarsened copy of another mesh's octree)
+        leaves = *given;
+        if ((brc = balance())) return brc;
+    } else if (d.refine_mode == AFEM_REFINE_KELLY) {
+        // ---- Kelly's indicator on the Coulomb potential of the nuclei (Sec. 3.1)
+        for (int i = 0; i < nc; ++i)
+            for (int j = 0; j < nc; ++j)
+                for (int k = 0; k < nc; ++k) leaves.push_back({0, i, j, k});
+        rebuild_set();
+        for (;;) {
+            std::vector<Leaf> next;
+            next.reserve(leaves.size() * 2);
+            bool any = false;
+            for (const Leaf& c : leaves) {
+                if (c.l < d.kelly_max_level && kelly_eta2(d, B, c, find_leaf) > d.kelly_threshold * d.kelly_threshold) {
+                    split_into(c, next);
+                    any = true;
+                } else {
+                    next.push_back(c);
+                }
+            }
+            if (!any) break;
+            leaves.swap(next);
+            if (leaves.size() > (size_t(1) << 26)) return set_error(AFEM_EMESH, "mesh: more than 2^26 leaves");
+            if ((brc = balance())) return brc;
+        }
+    } else {
+        // ---- the geometric rule toward the nuclei
+        leaves.reserve(size_t(nc) * nc * nc);
+        for (int i = 0; i < nc; ++i)
+            for (int j = 0; j < nc; ++j)
+                for (int k = 0; k < nc; ++k) leaves.push_back({0, i, j, k});
+        for (;;) {
+            bool any = false;
+            std::vector<Leaf> next;
+            next.reserve(leaves.size() * 2);
+            for (const Leaf& c : leaves) {
+                const double h = h0 / double(int64_t(1) << c.l);
+                const double a[3] = {d.lo + double(c.i) * h, d.lo + double(c.j) * h, d.lo + double(c.k) * h};
+                bool split = false;
+                for (int n = 0; n < d.n_nuclei && !split; ++n) {
+                    if (c.l >= d.nuc_levels[n]) continue;
+                    double d2 = 0.0;
+                    for (int ax = 0; ax < 3; ++ax) {
+                        const double R = d.nuc_pos[n][ax];
+                        const double b = a[ax] + h;
+                        if (R < a[ax]) {
+                            const double t = a[ax] - R;
+                            d2 += t * t;
+                        } else if (R > b) {
+                            const double t = R - b;
+                            d2 += t * t;
+                        }
+                    }
+                    const double ch = d.refine_c * h;
+                    split = d2 <= ch * ch;
+                }
+                if (split) {
+                    any = true;
+                    split_into(c, next);
+                } else {
+                    next.push_back(c);
+                }
+            }
+            leaves.swap(next);
+            if (!any) break;
+            if (leaves.size() > (size_t(1) << 26))
+                return set_error(AFEM_EMESH, "mesh: more than 2^26 leaves");
+        }
+        if ((brc = balance())) return brc;
     }
     int Lf = 0;
     for (const Leaf& c : leaves) Lf = std::max(Lf, int(c.l));

@@ -4,10 +4,11 @@
 // octree the library already holds).
 //
 // Levels, fine to coarse: the mesh itself (degree p); the same leaves at
-// degree p/2, ..., 1 (p-coarsening); then degree 1 on the octrees built with
-// the nuclear refinement levels capped at L-1, ..., 0 (h-coarsening; the last
-// is the uniform coarse grid).  Every leaf of a level has an ancestor-or-self
-// leaf on the next coarser octree, and the coarse finite-element space is a
+// degree p/2, ..., 1 (p-coarsening); then degree 1 on the octree truncated at
+// levels L-1, ..., 0 (h-coarsening: every leaf finer than the cap replaced by
+// its ancestor there; the last is the uniform coarse grid).  Every leaf of a
+// level has an ancestor-or-self leaf on the next coarser octree, whatever rule
+// refined the mesh, and the coarse finite-element space is a
 // subspace of the fine one, so the prolongation P is exact interpolation: the
 // value of the coarse function at each interior fine master, evaluated in one
 // "owner" cell that holds the master as a node (the lowest-index such cell).
@@ -28,6 +29,7 @@
 #include <map>
 #include <new>
 #include <tuple>
+#include <unordered_set>
 #include <vector>
 
 #include "afem_internal.h"
@@ -534,31 +536,43 @@ static int pmg_setup(afem_mesh* m, cudaStream_t s) {
     top.mesh = m;
     g->lv.push_back(top);
     int rc = AFEM_OK;
-    afem_mesh_desc d = m->desc;
-    int maxL = 0;
-    for (int a = 0; a < d.n_nuclei; ++a) maxL = std::max(maxL, int(d.nuc_levels[a]));
-    // p-coarsening, then h-coarsening of degree 1
-    std::vector<afem_mesh_desc> descs;
-    for (int p = d.degree; p > 1;) {
+    // p-coarsening on the same leaves, then degree 1 on the leaves truncated at
+    // levels Lf-1, ..., 0 (every leaf finer than the cap replaced by its
+    // ancestor at the cap): each level's octree coarsens the previous one
+    const HostMesh& F = m->host;
+    const int Lf = F.max_level;
+    std::vector<int> degrees;
+    for (int p = m->desc.degree; p > 1;) {
         p = p >= 4 ? p / 2 : 1;
-        afem_mesh_desc e = d;
-        e.degree = p;
-        descs.push_back(e);
+        degrees.push_back(p);
     }
-    for (int cap = maxL - 1; cap >= 0; --cap) {
-        afem_mesh_desc e = d;
-        e.degree = 1;
-        for (int a = 0; a < e.n_nuclei; ++a) e.nuc_levels[a] = std::min(int(e.nuc_levels[a]), cap);
-        descs.push_back(e);
-    }
-    for (const auto& e : descs) {
+    auto add_level = [&](int degree, int cap) -> int {
+        afem_mesh_desc e = m->desc;
+        e.degree = degree;
+        std::vector<int32_t> lev, ci, cj, ck;
+        std::unordered_set<uint64_t> seen;
+        for (size_t q = 0; q < F.lev.size(); ++q) {
+            const int sh = F.lev[q] > cap ? F.lev[q] - cap : 0;
+            const int32_t l = F.lev[q] - sh, i = F.ci[q] >> sh, j = F.cj[q] >> sh, k = F.ck[q] >> sh;
+            const uint64_t key = (uint64_t(l) << 60) | (uint64_t(i) << 40) | (uint64_t(j) << 20) | uint64_t(k);
+            if (!seen.insert(key).second) continue;
+            lev.push_back(l);
+            ci.push_back(i);
+            cj.push_back(j);
+            ck.push_back(k);
+        }
         afem_mesh* lm = nullptr;
-        if ((rc = afem_mesh_create_ex(&e, 0, &lm))) break;
+        int r = create_mesh_from_cells(e, lev, ci, cj, ck, &lm);
+        if (r) return r;
         PmgLevel L;
         L.mesh = lm;
         L.owned = true;
         g->lv.push_back(L);
-    }
+        return AFEM_OK;
+    };
+    for (int p : degrees)
+        if (rc == AFEM_OK) rc = add_level(p, Lf);
+    for (int cap = Lf - 1; rc == AFEM_OK && cap >= 0; --cap) rc = add_level(1, cap);
     for (size_t l = 0; rc == AFEM_OK && l + 1 < g->lv.size(); ++l)
         rc = build_transfer(g->lv[l].mesh->host, g->lv[l + 1].mesh->host, g->lv[l]);
     for (size_t l = 0; rc == AFEM_OK && l < g->lv.size(); ++l) rc = estimate_lambda(g->lv[l].mesh, &g->lv[l].lam_max, s);

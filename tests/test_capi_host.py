@@ -181,3 +181,21 @@ def test_spline_and_harmonic_yield_helpers():
     ref = np.sum(np.abs(A[band]) ** 2)
     got = adj.harmonic_yield(torch.from_numpy(d), dt, w0, 3, 9).item()
     assert abs(got - ref) <= 1e-12 * ref
+
+
+@pytest.mark.parametrize("case,kelly", [
+    ((-8.0, 8.0, 4, 2, [((0.0, 0.0, 0.7), 1.0, 5), ((0.0, 0.0, -0.7), 1.0, 5)], 2.0), (0.3, 4)),
+    ((-6.0, 6.0, 3, 3, [((0.3, -0.2, 0.1), 3.0, 5)], 2.0), (0.5, 3)),
+    ((-8.0, 8.0, 2, 4, [((0.0, 0.0, 0.0), 8.0, 5), ((1.43, 1.1, 0.0), 1.0, 5), ((-1.43, 1.1, 0.0), 1.0, 5)], 2.0),
+     (1.0, 4)),
+])
+def test_host_kelly_mesh_matches_oracle(case, kelly):
+    """Kelly refinement (Sec. 3.1) on the host builder and in the oracle: the
+    same leaves, masters and hanging points (threshold decisions in FP64 on
+    both sides; a tie at the threshold would show here)."""
+    from paper_2301_02387_gb300 import Mesh
+    lib_mesh = Mesh(*case, host_only=True, kelly=kelly)
+    om = omesh.Mesh(*case, kelly=kelly)
+    X, ml, cells = lib_mesh.tables()
+    assert sorted(map(tuple, cells.tolist())) == [tuple(t) for t in om.leaf_tuples()]
+    assert lib_mesh.N == om.N and lib_mesh.n_hanging == om.n_hanging

@@ -183,7 +183,7 @@ def test_full_arnoldi_propagate(full, krylov_case, krylov_m):
     import paper_2301_02387_gb300 as pkg
     gm, om, op, perm, w, phi_o = full
     U_o, E, apply_G, inner = krylov_case
-    dt, tol = 2e-4, 1e-10
+    dt, tol = (2e-4 if krylov_m == 10 else 1e-3), 1e-10   # at least two substeps either way
     ref, err_o, sub_o, pinfo = krylov.arnoldi_propagate(apply_G, phi_o, inner, krylov_m, dt, tol, return_info=True)
     assert sub_o >= 2
     phi, U = _gpu_inputs(full, U_o)

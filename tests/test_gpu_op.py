@@ -74,7 +74,7 @@ def test_op_apply_rejects_bad_arguments():
     gm = Mesh(-3.0, 3.0, 2, 2, [], 2.0)
     x = torch.zeros((gm.N, 2), dtype=torch.complex128, device="cuda")
     with pytest.raises(AfemError):
-        op_apply(gm, 7, x, torch.empty_like(x))
+        op_apply(gm, 99, x, torch.empty_like(x))   # not an operator kind
     with pytest.raises(AfemError):
         op_apply(gm, OP_H1, x, x)
 
@@ -146,3 +146,30 @@ def test_h1_velocity_gauge_parity(case, nvec):
     op_apply(gm, OP_H1_VG_C64, x32, y32, E=A)
     torch.cuda.synchronize()
     assert _relerr(y32.to(torch.complex128).cpu().numpy(), y32o[perm]) < 2e-5
+
+
+def test_h1_and_stiffness_on_a_kelly_mesh():
+    """The operators on a mesh refined by Kelly's indicator (Sec. 3.1) against
+    the oracle's assembled ones on its own Kelly mesh (the same leaves)."""
+    import torch
+    from paper_2301_02387_gb300 import Mesh, op_apply, OP_H1, OP_STIFF
+    case = (-8.0, 8.0, 4, 3, [((0.0, 0.0, 0.7), 1.0, 5), ((0.0, 0.0, -0.7), 1.0, 5)], 2.0)
+    gm = Mesh(*case, kelly=(0.3, 4))
+    om = omesh.Mesh(*case, kelly=(0.3, 4))
+    op = fem.Operators(om)
+    X, _, _ = gm.tables()
+    perm = coord_permutation(X, om.Xm)
+    rng = np.random.default_rng(17)
+    xo = rng.standard_normal((om.N, 2)) + 1j * rng.standard_normal((om.N, 2))
+    E = (0.01, 0.02, -0.03)
+    x = torch.from_numpy(np.ascontiguousarray(xo[perm])).cuda()
+    y = torch.empty_like(x)
+    op_apply(gm, OP_H1, x, y, E=E)
+    torch.cuda.synchronize()
+    assert _relerr(y.cpu().numpy(), op.h1_apply(xo, E=E)[perm]) < 1e-10
+    so = rng.standard_normal((om.N, 4))
+    s = torch.from_numpy(np.ascontiguousarray(so[perm])).cuda()
+    ys = torch.empty_like(s)
+    op_apply(gm, OP_STIFF, s, ys)
+    torch.cuda.synchronize()
+    assert _relerr(ys.cpu().numpy(), op.stiffness_apply(so)[perm]) < 1e-10

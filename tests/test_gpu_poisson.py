@@ -141,3 +141,28 @@ def test_poisson_multigrid_zero_density_and_maxit():
     assert rc == pkg._capi.AFEM_ECG_MAXIT and it == 1
     with pytest.raises(pkg.AfemError):
         pkg.mesh_set_option(gm, pkg.OPT_POISSON_SOLVER, 7)
+
+
+def test_poisson_multigrid_on_a_kelly_mesh():
+    """The multigrid hierarchy of a Kelly-refined mesh (coarse levels by
+    truncating its octree) solves to the oracle's backward-error bar."""
+    import torch
+    import paper_2301_02387_gb300 as pkg
+    case = (-8.0, 8.0, 4, 3, [((0.0, 0.0, 0.7), 1.0, 5), ((0.0, 0.0, -0.7), 1.0, 5)], 2.0)
+    gm = pkg.Mesh(*case, kelly=(0.3, 4))
+    om = omesh.Mesh(*case, kelly=(0.3, 4))
+    op = fem.Operators(om)
+    ps = poisson.PoissonSolver(op)
+    X, _, _ = gm.tables()
+    perm = coord_permutation(X, om.Xm)
+    phi_o = _orbitals(om.Xm, om.boundary, case[4], 2, 5)
+    rho, _ = poisson.pair_densities(op, phi_o)
+    pkg.mesh_set_option(gm, pkg.OPT_POISSON_SOLVER, pkg.POISSON_MULTIGRID)
+    for prec in (pkg.PREC_FP64, pkg.PREC_MIXED):
+        phi = torch.from_numpy(np.ascontiguousarray(phi_o[perm])).cuda()
+        W = torch.zeros((gm.N, 4), dtype=torch.float64, device="cuda")
+        it, rel, rc = pkg.poisson_batch(gm, phi, W, rtol=1e-10, max_it=5000, precision=prec)
+        assert rc == 0 and np.all(rel <= 1e-10)
+        Wg = np.empty((om.N, 4))
+        Wg[perm] = W.cpu().numpy()
+        assert np.all(ps.residual(Wg, rho) < 2e-10)

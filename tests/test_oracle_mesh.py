@@ -103,3 +103,88 @@ def test_boundary_flags():
     m = _mk(H_CASE, 2)
     on = np.any(np.isclose(np.abs(m.Xm), 10.0, atol=1e-12), axis=1)
     assert np.array_equal(on, m.boundary)
+
+
+# ------------------------------------------------------- Kelly refinement
+KELLY_CASE = dict(lo=-8.0, hi=8.0, nc=4, nuclei=[((0.0, 0.0, 0.7), 1.0, 5), ((0.0, 0.0, -0.7), 1.0, 5)])
+
+
+def test_kelly_face_quadrature_is_exact_for_the_jump():
+    """The (p+1)^2-point Gauss rule integrates the squared jump of the normal
+    derivative exactly (a polynomial of degree 2p per face direction): the
+    indicator of a leaf equals the same sum by a fine midpoint rule."""
+    p = 2
+    nuc = [(np.array(R), Z, L) for (R, Z, L) in KELLY_CASE["nuclei"]]
+    leaves = mesh.balance_leaves({(0, i, j, k) for i in range(4) for j in range(4) for k in range(4)} -
+                                 {(0, 1, 1, 1)} | {(1, 2 + a, 2 + b, 2 + c) for a in (0, 1) for b in (0, 1)
+                                                    for c in (0, 1)}, 4)
+    eta2 = mesh.kelly_indicators(leaves, 4, -8.0, 4.0, p, nuc)
+    leaf = (0, 0, 1, 1)   # a coarse leaf beside the refined one (a face with four finer neighbours)
+    xi, _ = gll.gll_nodes_weights(p)
+    h, c0 = 4.0, np.array([-8.0, -4.0, -4.0])
+
+    def interp_grad(lf, X, d):
+        hh = 4.0 / 2 ** lf[0]
+        cc = np.array([-8.0 + lf[1] * hh, -8.0 + lf[2] * hh, -8.0 + lf[3] * hh])
+        pts = np.array([[cc[0] + hh * xi[a], cc[1] + hh * xi[b], cc[2] + hh * xi[e]]
+                        for e in range(p + 1) for b in range(p + 1) for a in range(p + 1)])
+        V = -sum(Z / np.linalg.norm(pts - R, axis=1) for (R, Z, _L) in nuc).reshape(p + 1, p + 1, p + 1)
+        T = (X - cc) / hh
+        M = [gll.lagrange_matrix(xi, T[:, q]) for q in range(3)]
+        M[d] = gll.lagrange_deriv_matrix(xi, T[:, d]) / hh
+        return np.einsum("cba,ma,mb,mc->m", V, M[0], M[1], M[2])
+
+    tot = 0.0
+    n = 80
+    g = (np.arange(n) + 0.5) / n
+    U, W = np.meshgrid(g, g, indexing="ij")
+    for d in range(3):
+        for side in (0, 1):
+            nb = [leaf[1], leaf[2], leaf[3]]
+            nb[d] += 1 if side else -1
+            if not 0 <= nb[d] < 4:
+                continue
+            o = [a for a in range(3) if a != d]
+            X = np.zeros((n * n, 3))
+            X[:, d] = c0[d] + side * h
+            X[:, o[0]] = c0[o[0]] + h * U.ravel()
+            X[:, o[1]] = c0[o[1]] + h * W.ravel()
+            # the neighbour leaf of each sample point
+            J = np.zeros(n * n)
+            for m_ in range(n * n):
+                pt = X[m_].copy()
+                pt[d] += (1e-9 if side else -1e-9)
+                nbl = next(lf for lf in leaves
+                           if all(-8.0 + lf[q + 1] * 4.0 / 2 ** lf[0] <= pt[q] <= -8.0 + (lf[q + 1] + 1) * 4.0 / 2 ** lf[0]
+                                  for q in range(3)))
+                J[m_] = interp_grad(leaf, X[m_:m_ + 1], d)[0] - interp_grad(nbl, X[m_:m_ + 1], d)[0]
+            tot += np.sum(J * J) * (h / n) ** 2
+    assert abs(h / 24.0 * tot - eta2[leaf]) < 2e-3 * eta2[leaf]   # midpoint rule error ~ (1/n)^2
+
+
+def test_kelly_refinement_properties():
+    """No nuclei: nothing refines.  With nuclei: the leaves tile the box, are
+    2:1 balanced, reach the level cap exactly at the nuclei, and no leaf below
+    the cap keeps an indicator above the threshold; a smaller threshold never
+    gives fewer leaves."""
+    assert len(mesh.refine_leaves_kelly(3, -6.0, 4.0, 2, [], 0.1, 4)) == 27
+    nuc = [(np.array(R), Z, L) for (R, Z, L) in KELLY_CASE["nuclei"]]
+    counts = []
+    for theta in (1.0, 0.3):
+        m = mesh.Mesh(KELLY_CASE["lo"], KELLY_CASE["hi"], KELLY_CASE["nc"], 2, KELLY_CASE["nuclei"], kelly=(theta, 4))
+        assert abs(np.sum(m.h ** 3) - 16.0 ** 3) < 1e-9
+        lo, hi = m.corner, m.corner + m.h[:, None]
+        for a in range(len(m.lev)):
+            touch = np.all((lo <= hi[a] + 1e-12) & (hi >= lo[a] - 1e-12), axis=1)
+            assert np.all(np.abs(m.lev[touch] - m.lev[a]) <= 1)
+        eta2 = mesh.kelly_indicators(set(m.leaf_tuples()), 4, -8.0, 4.0, 2, nuc)
+        for lf, e in eta2.items():
+            if lf[0] < 4:
+                assert e <= theta * theta
+            l, i, j, k = lf
+            hh = 4.0 / 2 ** l
+            cc = np.array([-8.0 + i * hh, -8.0 + j * hh, -8.0 + k * hh])
+            if any(np.all((R >= cc) & (R <= cc + hh)) for (R, _Z, _L) in nuc):
+                assert l == 4
+        counts.append(len(m.lev))
+    assert counts[1] >= counts[0]
