@@ -166,7 +166,7 @@ def _timed_form(pkg, torch, solver, state0, precision, args, field, dt, dist, st
 
 def run_batch(torch, pkg, inputs, reps=10, count=64):
     """Batching form: the complex64 orbital operator of `count` seeded uneven
-    instances (DoFs log-uniform 5e4..2e6, p 2..4, 2-8 orbitals) in one
+    instances (DoFs log-uniform 5e4..2e6, p 2..4, 1-8 orbitals) in one
     persistent launch replayed from a CUDA graph, against the same instances
     applied one by one (FP32, then the plain FP64 form).  Inputs (~GB) are far
     larger than L2.  Returns the JSON sub-entry."""
@@ -233,7 +233,7 @@ def run_batch(torch, pkg, inputs, reps=10, count=64):
             "graph": "the chosen schedule (zero, cell pass, M_L^-1 of every instance) captured once, replayed per apply",
             "mesh_build_s": build_s,
             "recipe": "inputs.batch_instances(64): seeded, DoFs log-uniform 5e4..2e6, p in {2,3,4}, "
-                      "1-3 nuclei Z 1..8 within 3 bohr, 2-8 orbitals (even), |E| 0.01..0.08"}
+                      "1-3 nuclei Z 1..8 within 3 bohr, 1-8 orbitals, |E| 0.01..0.08"}
 
 
 def run_water(torch, pkg, inputs, args):

@@ -67,6 +67,24 @@ def triangular_pulse(t, intensity, wavelength_nm, pol=(1.0, 0.0, 0.0)):
     return tuple(e * float(c) for c in pol)
 
 
+def triangular_vector_potential(t, intensity, wavelength_nm, pol=(1.0, 0.0, 0.0)):
+    """A(t) = -int_-inf^t E of the triangular pulse (the velocity gauge's field
+    input): with ph = omega t and int u sin u = sin u - u cos u,
+    -A / (E0 / omega) = (sin ph - ph cos ph) / (2 pi) up to ph = 2 pi and
+    (ph cos ph - 4 pi cos ph - sin ph) / (2 pi) up to 4 pi; 0 outside."""
+    E0 = math.sqrt(intensity / _AU_INTENSITY_W_CM2)
+    omega = _AU_ENERGY_NM / wavelength_nm
+    ph = omega * t
+    if ph <= 0.0 or ph >= 4.0 * math.pi:
+        return (0.0, 0.0, 0.0)
+    if ph <= 2 * math.pi:
+        f = (math.sin(ph) - ph * math.cos(ph)) / (2 * math.pi)
+    else:
+        f = (ph * math.cos(ph) - 4 * math.pi * math.cos(ph) - math.sin(ph)) / (2 * math.pi)
+    a = -E0 / omega * f
+    return tuple(a * float(c) for c in pol)
+
+
 def _splitmix64(x):
     x = (x + np.uint64(0x9E3779B97F4A7C15)) & np.uint64(0xFFFFFFFFFFFFFFFF)
     z = x
@@ -141,8 +159,8 @@ def initial_ci(n_orb, n_alpha, n_beta, seed=BASE_SEED, amp=1e-2):
 def batch_instances(count=64, seed=BASE_SEED, dof_range=(5e4, 2e6), box=30.0):
     """Seeded instances of the batching form: target DoF counts log-uniform in
     dof_range, degree p in {2, 3, 4}, 1-3 nuclei with Z in 1..8 uniformly within
-    3 bohr of the origin (2 refinement levels each), an even orbital count in
-    {2, 4, 6, 8} (the batched FP32 pass takes orbitals in pairs), and a field of
+    3 bohr of the origin (2 refinement levels each), an orbital count in 1..8,
+    and a field of
     amplitude uniform in [0.01, 0.08] along a random direction.  The coarse
     count n_c = round(N_target^(1/3) / p) (at least 2) sets the size; the
     refinement adds a few percent.  Returns a list of dicts with mesh_args,
@@ -159,7 +177,7 @@ def batch_instances(count=64, seed=BASE_SEED, dof_range=(5e4, 2e6), box=30.0):
             d = rng.standard_normal(3)
             d *= rng.uniform(0.0, 3.0) / max(np.linalg.norm(d), 1e-12)
             nuclei.append(((float(d[0]), float(d[1]), float(d[2])), float(rng.integers(1, 9)), 2))
-        n_orb = int(2 * rng.integers(1, 5))
+        n_orb = int(rng.integers(1, 9))
         e = rng.standard_normal(3)
         e *= rng.uniform(0.01, 0.08) / np.linalg.norm(e)
         out.append(dict(mesh_args=(-box, box, nc, p, nuclei, 2.0), n_orb=n_orb, E=tuple(float(v) for v in e),

@@ -347,3 +347,36 @@ def test_mctdhf_steps_velocity_gauge_parity(precision_name):
                            raise_on_maxit=False)
         torch.cuda.synchronize()
         _compare_step(phi, C, info, phi_o, C_o, info_o, perm, na + nb, 1e-10 if fp64 else 1e-6)
+
+
+def test_mctdhf_velocity_gauge_with_the_papers_pulse():
+    """Sec. 4's pulse (400 nm, 8e14 W/cm^2, 2-cycle triangular envelope) in the
+    velocity gauge of Sec. 2 (the step's field argument is A(t)) over four
+    steps of dt = 0.01 from the pulse's first quarter: FP64 within 1e-10 of
+    the oracle's step in the same gauge."""
+    import math
+    import torch
+    import paper_2301_02387_gb300 as pkg
+    case, n, na, nb = CASES[0]
+    gm = pkg.Mesh(*case)
+    om = omesh.Mesh(*case)
+    op = fem.Operators(om)
+    X, _, _ = gm.tables()
+    perm = coord_permutation(X, om.Xm)
+    phi_o = inputs.lowdin(inputs.molecular_orbitals(om.Xm, ~om.boundary, case[4], n), op.ML)
+    C_o = inputs.initial_ci(n, na, nb, amp=0.1)
+    sim = mctdhf.MCTDHF(op, n, na, nb)
+    sim.gauge = "velocity"
+    solver = pkg.MCTDHF(gm, n, na, nb, 8)
+    solver.set_gauge(pkg.GAUGE_VELOCITY)
+    phi = torch.from_numpy(np.ascontiguousarray(phi_o[perm])).cuda()
+    C = torch.from_numpy(C_o.copy()).cuda()
+    W = torch.zeros((gm.N, n * n), dtype=torch.float64, device="cuda")
+    t0 = 0.25 * 4 * math.pi / (45.5634 / 400.0)
+    for k in range(4):
+        A = inputs.triangular_vector_potential(t0 + 0.01 * k, 8e14, 400.0, (0.0, 0.0, 1.0))
+        assert abs(A[2]) > 0.1
+        phi_o, C_o, info_o = sim.step(phi_o, C_o, A, 0.01, 8)
+        info = solver.step(phi, C, W, A, 0.01, cg_rtol=1e-14, cg_max_it=20000, raise_on_maxit=False)
+        torch.cuda.synchronize()
+        _compare_step(phi, C, info, phi_o, C_o, info_o, perm, na + nb, 1e-10)

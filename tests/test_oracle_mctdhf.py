@@ -448,3 +448,17 @@ def test_dipole_is_the_field_derivative_of_the_energy(tiny):
         Ep[k] = eps
         fd = (sim.energy(phi, C, Ep) - sim.energy(phi, C, -Ep)) / (2 * eps)
         assert abs(fd - d[k]) <= 1e-9 * max(1.0, abs(d[k]))
+
+
+def test_triangular_pulse_vector_potential_is_minus_the_field_integral():
+    """A(t) of the paper's 400 nm 2-cycle triangular pulse: dA/dt = -E by
+    central differences, A = 0 before and after the pulse (no DC term)."""
+    I, lam = 8e14, 400.0
+    T = 4 * math.pi / (45.5634 / lam)
+    for t in np.linspace(0.01 * T, 0.99 * T, 37):
+        h = 1e-5
+        dA = (inputs.triangular_vector_potential(t + h, I, lam)[0]
+              - inputs.triangular_vector_potential(t - h, I, lam)[0]) / (2 * h)
+        assert abs(dA + inputs.triangular_pulse(t, I, lam)[0]) < 1e-7
+    assert inputs.triangular_vector_potential(-1.0, I, lam) == (0.0, 0.0, 0.0)
+    assert abs(inputs.triangular_vector_potential(T * (1 - 1e-12), I, lam)[0]) < 1e-9
