@@ -267,14 +267,16 @@ __global__ void pmg_restrict_kernel(XferArgs a, const T* __restrict__ rf, T* __r
 }
 
 // One Chebyshev step on the interior rows: res = b - A x (ax = A x, or x = 0
-// when ax is null), d = c1 d + c2 D^-1 res, x += d.
+// when ax is null), d = c1 d + c2 D^-1 res, x += d.  first: d = c2 D^-1 res
+// (d is not read: on the first step it holds whatever the workspace held).
 template <typename T>
 __global__ void pmg_cheb_kernel(T* __restrict__ x, T* __restrict__ d, const T* __restrict__ b,
-                                const T* __restrict__ ax, const T* __restrict__ dinv, int64_t ni, int k, T c1, T c2) {
+                                const T* __restrict__ ax, const T* __restrict__ dinv, int64_t ni, int k, T c1, T c2,
+                                int first) {
     const int64_t n = ni * k;
     for (int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; o < n; o += int64_t(gridDim.x) * blockDim.x) {
         const T res = ax ? b[o] - ax[o] : b[o];
-        const T dn = c1 * d[o] + c2 * dinv[o / k] * res;
+        const T dn = (first ? T(0) : c1 * d[o]) + c2 * dinv[o / k] * res;
         d[o] = dn;
         x[o] = ax ? x[o] + dn : dn;
     }
@@ -311,7 +313,8 @@ __global__ void pmg_coldot_kernel(const T* __restrict__ x, const T* __restrict__
     }
 }
 
-// p = z + beta p with beta = rz / rz_old per column (0 when rz_old = 0).
+// p = z + beta p with beta = rz / rz_old per column (0 when rz_old = 0);
+// first: p = z (p is not read).
 template <typename T>
 __global__ void pmg_pupdate_kernel(T* __restrict__ p, const T* __restrict__ z, const double* __restrict__ rz,
                                    const double* __restrict__ rz_old, int64_t ni, int k, int first) {
@@ -319,8 +322,11 @@ __global__ void pmg_pupdate_kernel(T* __restrict__ p, const T* __restrict__ z, c
     for (int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; o < n; o += int64_t(gridDim.x) * blockDim.x) {
         const int c = int(o % k);
         const double ro = rz_old[c];
-        const T beta = (first || !(ro > 0.0)) ? T(0) : T(rz[c] / ro);
-        p[o] = z[o] + beta * p[o];
+        if (first || !(ro > 0.0)) {
+            p[o] = z[o];
+            continue;
+        }
+        p[o] = z[o] + T(rz[c] / ro) * p[o];
     }
 }
 
@@ -452,7 +458,7 @@ static int chebyshev(const afem_mesh* m, LevelVec<T>& v, int k, double lo, doubl
             rho = rho_new;
         }
         AFEM_LAUNCH((pmg_cheb_kernel<T>), grid, 256, 0, s, v.x, v.d, v.b, x_zero ? nullptr : v.t, dinv, ni, k, T(c1),
-                    T(c2));
+                    T(c2), it == 0 ? 1 : 0);
     }
     AFEM_CUDA_TRY(cudaGetLastError());
     return AFEM_OK;
