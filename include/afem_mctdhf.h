@@ -189,14 +189,17 @@ int afem_mesh_destroy(afem_mesh* mesh);
 /* Kernel-shape options of a mesh (library tuning; no counterpart in the paper).
  * AFEM_OPT_CELL32_VARIANT selects the float32 four-lane cell pass: 0 (default)
  * computes each output node in one thread, 1 computes the 1D contractions
- * line by line with direction-wise accumulation in shared memory.  Both give
- * the same operator.  Host only. */
+ * line by line with direction-wise accumulation in shared memory, 2 does the
+ * same for the stiffness with one thread per (line, column pair) and the 1D
+ * matrix in registers (1, 2 or 4 column quads; other passes as for 0).  All
+ * give the same operator up to float rounding order.  Host only. */
 #define AFEM_OPT_CELL32_VARIANT 1
 /* AFEM_OPT_POISSON_SOLVER selects the preconditioner of the batched Poisson
  * CG (Sec. 3.1 solves the mean fields by CG with algebraic multigrid):
  * AFEM_POISSON_JACOBI (default) or AFEM_POISSON_MULTIGRID, a geometric
  * multigrid V-cycle over the mesh at degrees p, p/2, .., 1 and then degree 1
- * on the octrees with the nuclear refinement levels capped at L-1, .., 0
+ * on the octree truncated at levels L-1, .., 0 (every leaf finer than the cap
+ * replaced by its ancestor there; so for meshes of either refinement rule)
  * (exact interpolation between the nested spaces, restriction its transpose,
  * Chebyshev-Jacobi smoothing of degree 3, a degree-30 Chebyshev polynomial on
  * the uniform coarse grid).  The FP64 form runs CG with the float64 V-cycle;
@@ -208,6 +211,26 @@ int afem_mesh_destroy(afem_mesh* mesh);
 #define AFEM_POISSON_JACOBI 0
 #define AFEM_POISSON_MULTIGRID 1
 int afem_mesh_set_option(afem_mesh* mesh, int option, int value);
+
+/* Exterior complex scaling of the kinetic energy (Sec. 4: an absorbing
+ * boundary by ECS outside an inner box; the paper leaves the construction to
+ * its references).  Built: Cartesian scaling with a sharp onset at the faces of
+ * the inner box |x_d| <= half_width[d], x_d -> +-R_d + e^{i theta} (x_d -+ R_d)
+ * outside.  A cell outside the box along the axes with flag f_d has
+ * eta_d = e^{i theta f_d}, J = prod_d eta_d, the weak-form stiffness
+ * h sum_d (J / eta_d^2) (d-th Kronecker term) and the mass J h^3 W (x) W (x) W;
+ * with M_theta = C^T (J m_f) the kinetic operator becomes
+ * 1/2 M_theta^-1 A_theta.  The nuclear potential, E . r and the mean fields
+ * keep their real weights; the orbital inner product stays u^H M_L v.  Every
+ * one-body operator of the orbital path then uses it: AFEM_OP_H1 and
+ * AFEM_OP_H1_C64, afem_arnoldi_step / _propagate and afem_mctdhf_step (whose
+ * h_pq and CI Hamiltonian become non-Hermitian).  Not built with it (AFEM_EINVAL):
+ * the velocity gauge, imaginary-time steps, the afem_tdse_* adjoint, the batch.
+ * theta in [0, pi/2); theta = 0 removes the scaling.  Every cell must lie wholly
+ * inside or outside the box along each axis (else AFEM_EMESH).  The current
+ * device must be the mesh's.  Host set-up plus a synchronous upload of per-cell
+ * flags and per-master factors M_L / M_theta (library-owned). */
+int afem_mesh_set_ecs(afem_mesh* mesh, double theta, const double half_width[3]);
 
 /* Sizes of the mesh (host struct, caller-owned). */
 int afem_mesh_get_info(const afem_mesh* mesh, afem_mesh_info* info);

@@ -27,6 +27,21 @@ on a conforming mesh; on the hanging-node mesh it keeps -i A . G Hermitian,
 which the plain form is not there (the lumped face quadratures of a coarse
 face and its fine subfaces differ).
 
+Exterior complex scaling (Sec. 4 absorbs the outgoing flux by ECS outside an
+inner box, with the details left to the cited literature).  Reading taken
+here: Cartesian scaling with a sharp onset at the faces of an inner box
+|x_d| <= R_d, x_d -> +-R_d + e^{i theta} (x_d -+ R_d) outside, applied to the
+kinetic energy; cells lie wholly inside or outside the box along each axis.
+In the weak form a cell scaled along the axes f_d (eta_d = e^{i theta f_d},
+J = prod_d eta_d) has the stiffness h sum_d (J / eta_d^2) (the d-th Kronecker
+term) and the mass J h^3 W (x) W (x) W; with M_theta = C^T (J m_f) the
+kinetic operator on nodal vectors is -1/2 Laplacian -> 1/2 M_theta^-1 A_theta.
+The pointwise terms (nuclear potential, E . r, mean fields) keep their real
+weights, and the orbital inner product stays <u, v> = u^H M_L v, so the
+one-body matrix in that inner product is
+H1~ = 1/2 diag(M_L / M_theta) A_theta + F[V + E . x]
+(H1~ of the unscaled case when theta = 0).
+
 Test infrastructure only (see the package docstring).
 """
 import numpy as np
@@ -57,6 +72,19 @@ def gradient_matrices(p):
     S = 0.5 * (Dw - Dw.T)
     W = np.diag(w)
     return [np.kron(W, np.kron(W, S)), np.kron(W, np.kron(S, W)), np.kron(S, np.kron(W, W))]
+
+
+def ecs_cell_flags(mesh, R, tol=1e-9):
+    """(ncell, 3) 0/1: cell lies outside the inner box |x_d| <= R_d along axis d.
+    ValueError when a face of the inner box cuts a cell."""
+    R = np.asarray(R, dtype=np.float64)
+    lo = mesh.corner
+    hi = lo + mesh.h[:, None]
+    inside = (lo >= -R - tol) & (hi <= R + tol)
+    outside = (lo >= R - tol) | (hi <= -R + tol)
+    if np.any(~(inside | outside)):
+        raise ValueError("a face of the complex-scaling box cuts a cell")
+    return outside.astype(np.int64)
 
 
 class Operators:
@@ -131,12 +159,48 @@ class Operators:
             self._G[d] = (self.C.T @ Gf @ self.C).tocsr()
         return self._G[d]
 
+    def set_ecs(self, theta, R):
+        """Exterior complex scaling of the kinetic energy outside |x_d| <= R_d
+        by the angle theta (module docstring); theta = 0 removes it."""
+        self.ecs = None
+        if theta == 0.0:
+            return
+        mesh = self.mesh
+        f = ecs_cell_flags(mesh, R)
+        eta = np.exp(1j * theta)
+        J = eta ** f.sum(axis=1)
+        s = J[:, None] / eta ** (2 * f)            # (ncell, 3): J / eta_d^2
+        K = gll.stiffness_1d(mesh.p)
+        W = np.diag(mesh.w)
+        Ad = [np.kron(W, np.kron(W, K)), np.kron(W, np.kron(K, W)), np.kron(K, np.kron(W, W))]
+        nn = (mesh.p + 1) ** 3
+        ncell = len(mesh.lev)
+        vals = mesh.h[:, None, None] * (s[:, 0, None, None] * Ad[0][None] + s[:, 1, None, None] * Ad[1][None]
+                                        + s[:, 2, None, None] * Ad[2][None])
+        rows = np.repeat(mesh.cell_pts, nn, axis=1).ravel()
+        cols = np.tile(mesh.cell_pts, (1, nn)).ravel()
+        Af = sp.csr_matrix((vals.reshape(ncell, -1).ravel(), (rows, cols)), shape=(mesh.nf, mesh.nf))
+        self.A_theta = (self.C.T @ Af @ self.C).tocsr()
+        _, m_hat = cell_matrices(mesh.p)
+        wts = (J[:, None] * mesh.h[:, None] ** 3 * m_hat[None, :]).ravel()
+        pts = mesh.cell_pts.ravel()
+        m_theta_f = (np.bincount(pts, weights=wts.real, minlength=mesh.nf)
+                     + 1j * np.bincount(pts, weights=wts.imag, minlength=mesh.nf))
+        self.M_theta = self.C.T @ m_theta_f
+        self.rho = self.ML / self.M_theta
+        self.ecs = (float(theta), tuple(float(r) for r in R), f)
+
     def H1_matrix(self, E=(0.0, 0.0, 0.0), A=None):
         """H1~ = 1/2 A + F[V + E . x] over all masters (boundary rows/cols kept);
         with a vector potential A (velocity gauge, Sec. 2) the term
-        -i sum_d A_d G_d is added (complex matrix)."""
+        -i sum_d A_d G_d is added (complex matrix); with complex scaling
+        (set_ecs) the kinetic part is 1/2 diag(M_L / M_theta) A_theta."""
         E = np.asarray(E, dtype=np.float64)
         f = self.V_f + self.mesh.X @ E
+        if getattr(self, "ecs", None) is not None:
+            if A is not None and np.any(np.asarray(A) != 0.0):
+                raise ValueError("complex scaling is built for the length gauge")
+            return (0.5 * sp.diags(self.rho) @ self.A_theta + self.pointwise(f)).tocsr()
         H = 0.5 * self.A + self.pointwise(f)
         if A is not None and np.any(np.asarray(A) != 0.0):
             for d in range(3):

@@ -20,6 +20,7 @@ same time-t quantities.
 Test infrastructure only (see the package docstring).
 """
 import numpy as np
+import scipy.linalg
 
 from . import ci as ci_mod
 from . import krylov, poisson
@@ -113,8 +114,12 @@ class MCTDHF:
         Hci = self.ci.hamiltonian(h, eri)
         g1 = self.ci.rdm1(C)
         g2 = self.ci.rdm2(C)
-        evals, evecs = np.linalg.eigh(0.5 * (Hci + Hci.conj().T))
-        C_new = evecs @ (np.exp(-1j * dt * evals) * (evecs.conj().T @ C))
+        if getattr(self.ops, "ecs", None) is not None:
+            # complex scaling: h_pq, and so H_CI, is not Hermitian
+            C_new = scipy.linalg.expm(-1j * dt * Hci) @ C
+        else:
+            evals, evecs = np.linalg.eigh(0.5 * (Hci + Hci.conj().T))
+            C_new = evecs @ (np.exp(-1j * dt * evals) * (evecs.conj().T @ C))
         U = self.mean_field_operator(g1, g2, W)
         apply_G = lambda v: self.G_apply(v, phi, U, E)   # noqa: E731
         substeps, margin, Hk, m_used, brk = 1, np.inf, None, m, False

@@ -347,6 +347,13 @@ def mesh_set_option(mesh, option, value):
     _capi.check(_capi.load().afem_mesh_set_option(mesh.handle, int(option), int(value)))
 
 
+def mesh_set_ecs(mesh, theta, half_width):
+    """afem_mesh_set_ecs: exterior complex scaling of the kinetic energy by the
+    angle theta outside the box |x_d| <= half_width[d]; theta = 0 removes it."""
+    hw = (ctypes.c_double * 3)(*[float(v) for v in half_width])
+    _capi.check(_capi.load().afem_mesh_set_ecs(mesh.handle, float(theta), hw))
+
+
 from ._capi import (PROF_GS, PROF_GCELL32, PROF_STIFF32, PROF_CGVEC32, PROF_CELL64,  # noqa: E402,F401
                     PROF_COUNT)
 

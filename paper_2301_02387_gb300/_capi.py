@@ -118,6 +118,7 @@ SIGNATURES = {
     "afem_mesh_destroy": (ctypes.c_int, [_P]),
     "afem_mesh_get_info": (ctypes.c_int, [_P, ctypes.POINTER(MeshInfo)]),
     "afem_mesh_set_option": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
+    "afem_mesh_set_ecs": (ctypes.c_int, [_P, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
     "afem_mesh_tables": (ctypes.c_int, [_P, _P, _P, _P]),
     "afem_op_apply": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, ctypes.c_int, _P]),
     "afem_poisson_batch": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_double, ctypes.c_int,

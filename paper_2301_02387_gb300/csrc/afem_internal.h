@@ -164,6 +164,13 @@ struct afem_mesh {
     int cell32_variant = 0;   // FP32 four-lane cell pass: 0 node-per-thread, 1 line-ordered
     int poisson_solver = 0;   // AFEM_POISSON_JACOBI or AFEM_POISSON_MULTIGRID
     afem_pmg* pmg = nullptr;  // built on the first multigrid solve
+    // exterior complex scaling of the kinetic energy (afem_mesh_set_ecs)
+    int ecs_on = 0;
+    double ecs_theta = 0.0;
+    double ecs_half_width[3] = {0.0, 0.0, 0.0};
+    uint8_t* ecs_flags = nullptr;   // [ncell] bit d: the cell lies outside the inner box along axis d
+    double2* ecs_rho = nullptr;     // [N] M_L / M_theta
+    float2* ecs_rho32 = nullptr;    // [N] the same in complex64
 };
 
 namespace afem {
@@ -180,6 +187,8 @@ int multipole_boundary(afem_mesh* m, const double2* phi, int n, double* W, doubl
                        cudaStream_t s);
 int ensure_sh_tables();   // uploads the solid-harmonic constants once per device
 void pmg_free(afem_pmg* g);
+int mesh_set_ecs(afem_mesh* m, double theta, const double half_width[3]);
+void mesh_free_ecs(afem_mesh* m);
 int mctdhf_create(afem_mesh* m, int n, int na, int nb, int mk, afem_mctdhf** out);
 void mctdhf_destroy(afem_mctdhf* S);
 int64_t mctdhf_ci_dim(const afem_mctdhf* S);

@@ -677,7 +677,45 @@ __global__ void expm_ladder_kernel(const double2* __restrict__ H, int ldh, int m
 
 // ------------------------------------------------------------------- host
 int launch_g_cell(const afem_mesh* m, const double* E, const double2* v, const double2* U, double2* z, int n,
-                  cudaStream_t s, int velocity);
+                  cudaStream_t s, int velocity, const double2* U_hang = nullptr);
+
+// The frozen mean fields at the hanging points, Uh[h] = sum_e w_e U[master_e]
+// (the constraint rows C; the same products in the same order as the cell
+// passes' own gather, so the cell pass gives the same bits either way), formed
+// once per propagation instead of in every cell pass of every Krylov vector.
+__global__ void hang_rows64_kernel(const double2* __restrict__ U, const int32_t* __restrict__ hp,
+                                   const int32_t* __restrict__ hm, const double* __restrict__ hw, int64_t nh, int k,
+                                   double2* __restrict__ Uh) {
+    const int64_t n = nh * k;
+    for (int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; o < n; o += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t h = o / k;
+        const int c = int(o - h * k);
+        double2 v = make_double2(0.0, 0.0);
+        for (int e = hp[h]; e < hp[h + 1]; ++e) {
+            const double2 u = U[int64_t(hm[e]) * k + c];
+            v.x = fma(hw[e], u.x, v.x);
+            v.y = fma(hw[e], u.y, v.y);
+        }
+        Uh[o] = v;
+    }
+}
+
+__global__ void hang_rows32_kernel(const float2* __restrict__ U, const int32_t* __restrict__ hp,
+                                   const int32_t* __restrict__ hm, const float* __restrict__ hw, int64_t nh, int k,
+                                   float2* __restrict__ Uh) {
+    const int64_t n = nh * k;
+    for (int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; o < n; o += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t h = o / k;
+        const int c = int(o - h * k);
+        float2 v = make_float2(0.0f, 0.0f);
+        for (int e = hp[h]; e < hp[h + 1]; ++e) {
+            const float2 u = U[int64_t(hm[e]) * k + c];
+            v.x = fmaf(hw[e], u.x, v.x);
+            v.y = fmaf(hw[e], u.y, v.y);
+        }
+        Uh[o] = v;
+    }
+}
 
 template <typename TB>
 int cdot_t(const double2* A, int na, const TB* B, int nb, const double* w, int64_t rows, int diag,
@@ -729,7 +767,7 @@ int to_c64(const double2* x, float2* y, int64_t n, cudaStream_t s) {
 }
 
 int launch_g_cell32(const afem_mesh* m, const double* E, const float2* v, const float2* U, float2* z, int n,
-                    cudaStream_t s, int velocity);
+                    cudaStream_t s, int velocity, const float2* U_hang = nullptr);
 
 #define AFEM_NV_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16)
 
@@ -868,7 +906,7 @@ static int g_cell_overlaps32(afem_mesh* m, const double* E, const float2* phi32,
     int rc;
     {   // algorithmic bytes: read v, U (n^2 fields), write z, complex64
         ProfScope ps(AFEM_PROF_GCELL32, s, double(D.n_master) * 8.0 * n * (2 + n));
-        if ((rc = launch_g_cell32(m, E, v32, U32, w.z32, n, s, velocity))) return rc;
+        if ((rc = launch_g_cell32(m, E, v32, U32, w.z32, n, s, velocity, w.uh32))) return rc;
     }
     auto* part = reinterpret_cast<double*>(w.cpartial);
     switch (n) {
@@ -900,7 +938,7 @@ static int g_cell_overlaps(afem_mesh* m, const double* E, const double2* phi, co
     {
         const int p1 = D.p + 1;
         ProfScope ps(AFEM_PROF_CELL64, s, double(D.ncell) * p1 * p1 * p1 * 2.0 * n * (3.0 * p1 * 2.0 + 6.0));
-        rc = launch_g_cell(m, E, v, U, w.z, n, s, velocity);
+        rc = launch_g_cell(m, E, v, U, w.z, n, s, velocity, w.uh);
     }
     if (rc) return rc;
     return cdot(phi, n, w.z, n, nullptr, D.n_interior, 0, w.cpartial, w.S, w.counters, s);
@@ -921,6 +959,8 @@ int arnoldi_reserve(afem_mesh* m, int n, int mk, ArnoldiWork& w) {
         w.z32 = cv.take<float2>(NV);
         w.phi32 = cv.take<float2>(NV);
         w.U32 = cv.take<float2>(NV * n);
+        w.Uh = cv.take<double2>(size_t(m->dev.n_hanging) * n * n);
+        w.Uh32 = cv.take<float2>(size_t(m->dev.n_hanging) * n * n);
         w.counters = cv.take<unsigned>(4);
         w.flag = cv.take<int>(4);
     };
@@ -987,6 +1027,22 @@ int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double
         }
         if ((rc = to_c64(phi, w.phi32, NV, s))) return rc;
     }
+    w.uh = nullptr;
+    w.uh32 = nullptr;
+    if (D.n_hanging > 0 && (mixed ? U32 != nullptr : U != nullptr)) {
+        const int64_t nh = D.n_hanging;
+        const int k = n * n;
+        if (mixed) {
+            AFEM_LAUNCH((hang_rows32_kernel), grid_for(nh * k), 256, 0, s, U32, D.hang_ptr, D.hang_master,
+                        D.hang_w32, nh, k, w.Uh32);
+            w.uh32 = w.Uh32;
+        } else {
+            AFEM_LAUNCH((hang_rows64_kernel), grid_for(nh * k), 256, 0, s, U, D.hang_ptr, D.hang_master, D.hang_w,
+                        nh, k, w.Uh);
+            w.uh = w.Uh;
+        }
+        AFEM_CUDA_TRY(cudaGetLastError());
+    }
     AFEM_CUDA_TRY(cudaMemsetAsync(w.counters, 0, 4 * sizeof(unsigned), s));
     AFEM_CUDA_TRY(cudaMemsetAsync(w.flag, 0, 4 * sizeof(int), s));
     AFEM_CUDA_TRY(cudaMemsetAsync(w.Sslots, 0, sizeof(double) * kOvSlots * 2 * kMaxOrbProj * kMaxOrbProj, s));
@@ -1023,9 +1079,9 @@ int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double
             // update cancelled most of w
             if (!projector) {   // the cell pass alone; S stays zero
                 if (mixed) {
-                    if ((rc = launch_g_cell32(m, E, w.v32, U32, w.z32, n, s, velocity))) return rc;
+                    if ((rc = launch_g_cell32(m, E, w.v32, U32, w.z32, n, s, velocity, w.uh32))) return rc;
                 } else {
-                    if ((rc = launch_g_cell(m, E, w.V + j * NV, U, w.z, n, s, velocity))) return rc;
+                    if ((rc = launch_g_cell(m, E, w.V + j * NV, U, w.z, n, s, velocity, w.uh))) return rc;
                 }
             } else if (mixed) {
                 if ((rc = g_cell_overlaps32(m, E, w.phi32, U32, n, w.v32, w, s, velocity))) return rc;

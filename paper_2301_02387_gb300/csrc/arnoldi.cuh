@@ -37,6 +37,10 @@ struct ArnoldiWork {
     float2* z32;         // [N][n] complex64 cell-pass output (mixed form)
     float2* phi32;       // [N][n] complex64 copy of the frozen orbitals (mixed-form projector)
     float2* U32;         // [N][n][n] complex64 mean-field fields (mixed form)
+    double2* Uh;         // [nh][n][n] the mean fields at the hanging points (C U), FP64 cell pass
+    float2* Uh32;        // [nh][n][n] the same in complex64
+    const double2* uh;   // Uh once formed for this call, else null (interpolated in every cell pass)
+    const float2* uh32;
     unsigned* counters;  // last-block reduction counters (zeroed per call)
     int* flag;           // second-pass flag
     int64_t stride;      // N * n

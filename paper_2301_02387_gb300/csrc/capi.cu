@@ -187,6 +187,7 @@ int afem_mesh_destroy(afem_mesh* mesh) {
     if (!mesh->host_only) free_device_mesh(mesh->dev);
     pmg_free(mesh->pmg);
     mesh->pmg = nullptr;
+    if (!mesh->host_only) mesh_free_ecs(mesh);
     mesh->ws_poisson.release();
     mesh->ws_arnoldi.release();
     mesh->ws_tdse.release();
@@ -197,7 +198,8 @@ int afem_mesh_destroy(afem_mesh* mesh) {
 int afem_mesh_set_option(afem_mesh* m, int option, int value) {
     if (!m) return set_error(AFEM_EINVAL, "afem_mesh_set_option: null mesh");
     if (option == AFEM_OPT_CELL32_VARIANT) {
-        if (value != 0 && value != 1) return set_error(AFEM_EINVAL, "afem_mesh_set_option: variant must be 0 or 1");
+        if (value < 0 || value > 2)
+            return set_error(AFEM_EINVAL, "afem_mesh_set_option: variant must be 0, 1 or 2");
         m->cell32_variant = value;
         return AFEM_OK;
     }
@@ -210,6 +212,15 @@ int afem_mesh_set_option(afem_mesh* m, int option, int value) {
         return AFEM_OK;
     }
     return set_error(AFEM_EINVAL, "afem_mesh_set_option: unknown option");
+}
+
+int afem_mesh_set_ecs(afem_mesh* m, double theta, const double half_width[3]) {
+    if (!m) return set_error(AFEM_EINVAL, "afem_mesh_set_ecs: null mesh");
+    if (m->host_only) return set_error(AFEM_EINVAL, "afem_mesh_set_ecs: mesh was built host-only");
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != m->device)
+        return set_error(AFEM_EINVAL, "afem_mesh_set_ecs: the current device is not the mesh's");
+    return mesh_set_ecs(m, theta, half_width);
 }
 
 int afem_mesh_get_info(const afem_mesh* m, afem_mesh_info* info) {

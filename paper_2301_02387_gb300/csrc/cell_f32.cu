@@ -7,6 +7,7 @@
 // runs inside the cell loop.  Callers keep the accuracy-critical parts in FP64
 // (Krylov Gram-Schmidt, residuals of the Poisson refinement).
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 
 #include "afem_internal.h"
@@ -14,6 +15,12 @@
 #include "vec_common.cuh"
 
 namespace afem {
+
+// Entries of a hanging point's constraint row loaded together by the
+// four-lane gather (1: one at a time).
+#ifndef AFEM_HANG_UNROLL
+#define AFEM_HANG_UNROLL 4
+#endif
 
 struct CellArgs32 {
     const int32_t* cell_node;
@@ -35,7 +42,18 @@ struct CellArgs32 {
     float Avec[3];              // vector potential (vg != 0)
     int masked;
     int vg;                     // velocity gauge: -i A . grad in the G pass (generic kernel only)
+    // G pass: the mean fields at the hanging points, [nh][n^2] complex64 rows
+    // (C U, formed once per propagation); null: interpolated from the masters
+    const float2* u_hang;
+    // complex scaling of the kinetic term (the ECS variant of the generic kernel)
+    const uint8_t* ecs_flags;   // [ncell] bit d: scaled along axis d
+    const float2* ecs_rho;      // [N] M_L / M_theta
+    float2 ecs_e[6];            // e^{i m theta}, m = -2..3
 };
+
+__device__ __forceinline__ float2 cmul32(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
 
 template <typename T>
 __device__ __forceinline__ T gather32(const CellArgs32& a, int idx, const T* __restrict__ x, int nv, int v) {
@@ -70,9 +88,30 @@ __device__ __forceinline__ void scatter32(const CellArgs32& a, int idx, T* __res
     }
 }
 
+// Scatter of a complex-scaled cell's output: the kinetic part rk enters master
+// m as rho_m rk, the pointwise part rp unchanged (both through C^T).
+__device__ __forceinline__ void scatter32_ecs(const CellArgs32& a, int idx, float2* __restrict__ y, int nv, int v,
+                                              float2 rk, float2 rp) {
+    if (idx >= 0) {
+        if (!(a.masked && idx >= a.n_interior)) {
+            const float2 t = cmul32(a.ecs_rho[idx], rk);
+            vatomic_add(&y[int64_t(idx) * nv + v], make_float2(t.x + rp.x, t.y + rp.y));
+        }
+    } else {
+        const int hh = -idx - 1;
+        for (int e = a.hp[hh]; e < a.hp[hh + 1]; ++e) {
+            const int m = a.hm[e];
+            if (a.masked && m >= a.n_interior) continue;
+            const float2 t = cmul32(a.ecs_rho[m], rk);
+            vatomic_add(&y[int64_t(m) * nv + v], fscale(make_float2(t.x + rp.x, t.y + rp.y), a.hw[e]));
+        }
+    }
+}
+
 // y += A x for nv real columns (c_kin = 1), or the G-operator cell pass for
 // complex columns: z_p = H1~ v_p + sum_q (C U_pq) o (C v_q) weighted (U may be null).
-template <int P, typename T, bool G, bool VG = false>
+// ECS (complex columns, G): the kinetic term complex-scaled (afem_mesh_set_ecs).
+template <int P, typename T, bool G, bool VG = false, bool ECS = false>
 __global__ void __launch_bounds__(256) cell32_kernel(CellArgs32 a, const T* __restrict__ x,
                                                      const float2* __restrict__ U, T* __restrict__ y, int nv) {
     constexpr int P1 = P + 1;
@@ -103,7 +142,9 @@ __global__ void __launch_bounds__(256) cell32_kernel(CellArgs32 a, const T* __re
             au.masked = 0;
             for (int it = tid; it < NN * nn2; it += bs) {
                 const int i = it / nn2, pq = it - i * nn2;
-                s_U[it] = gather32<float2>(au, s_idx[i], U, nn2, pq);
+                const int idx = s_idx[i];
+                s_U[it] = (idx < 0 && a.u_hang) ? a.u_hang[int64_t(-idx - 1) * nn2 + pq]
+                                                : gather32<float2>(au, idx, U, nn2, pq);
             }
         }
         const float h3 = g.w * g.w * g.w;
@@ -130,9 +171,21 @@ __global__ void __launch_bounds__(256) cell32_kernel(CellArgs32 a, const T* __re
             vfma(az, s_K[ic * P1 + m], s_u[(ia + P1 * (ib + P1 * m)) * nv + p]);
         }
         T r = vzero<T>();
-        vfma(r, ck * s_w[ib] * s_w[ic], ax);
-        vfma(r, ck * s_w[ia] * s_w[ic], ay);
-        vfma(r, ck * s_w[ia] * s_w[ib], az);
+        float2 rk = make_float2(0.f, 0.f);
+        if constexpr (ECS && G && sizeof(T) == sizeof(float2)) {
+            // the cell's stiffness factors J / eta_d^2 (k scaled axes: J = e^{i k theta})
+            const int f = a.ecs_flags[cell];
+            const int k = (f & 1) + ((f >> 1) & 1) + ((f >> 2) & 1);
+            const float cx = ck * s_w[ib] * s_w[ic], cy = ck * s_w[ia] * s_w[ic], cz = ck * s_w[ia] * s_w[ib];
+            const float2 tx = cmul32(a.ecs_e[k - 2 * (f & 1) + 2], make_float2(cx * ax.x, cx * ax.y));
+            const float2 ty = cmul32(a.ecs_e[k - 2 * ((f >> 1) & 1) + 2], make_float2(cy * ay.x, cy * ay.y));
+            const float2 tz = cmul32(a.ecs_e[k - 2 * ((f >> 2) & 1) + 2], make_float2(cz * az.x, cz * az.y));
+            rk = make_float2(tx.x + ty.x + tz.x, tx.y + ty.y + tz.y);
+        } else {
+            vfma(r, ck * s_w[ib] * s_w[ic], ax);
+            vfma(r, ck * s_w[ia] * s_w[ic], ay);
+            vfma(r, ck * s_w[ia] * s_w[ib], az);
+        }
         if constexpr (G) {
             vfma(r, s_pot[i], s_u[it]);
             if constexpr (VG && sizeof(T) == sizeof(float2)) {
@@ -164,7 +217,8 @@ __global__ void __launch_bounds__(256) cell32_kernel(CellArgs32 a, const T* __re
                 vfma(r, s_wq[i], mf);
             }
         }
-        scatter32<T>(a, s_idx[i], y, nv, p, r);
+        if constexpr (ECS && G && sizeof(T) == sizeof(float2)) scatter32_ecs(a, s_idx[i], y, nv, p, rk, r);
+        else scatter32<T>(a, s_idx[i], y, nv, p, r);
     }
 }
 
@@ -186,8 +240,38 @@ __device__ __forceinline__ float4 gather32v(const CellArgs32& a, int idx, const 
     if (idx >= 0) {
         if (!(a.masked && idx >= a.n_interior)) val = x[int64_t(idx) * L4 + q];
     } else {
+        // a hanging point: its constraint row (17 masters on average at degree 4)
+        // walked AFEM_HANG_UNROLL entries at a time, the index loads and then the
+        // row loads issued together, so the walk waits on a fraction of the
+        // dependent index -> value latencies; masked masters add zero
         const int hh = -idx - 1;
-        for (int e = a.hp[hh]; e < a.hp[hh + 1]; ++e) {
+        const int e1 = a.hp[hh + 1];
+        int e = a.hp[hh];
+#if AFEM_HANG_UNROLL >= 4
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (; e + 4 <= e1; e += 4) {
+            const int m0 = a.hm[e], m1 = a.hm[e + 1], m2 = a.hm[e + 2], m3 = a.hm[e + 3];
+            // masked (surface) masters are not read: their rows may hold anything
+            const float4 x0 = (a.masked && m0 >= a.n_interior) ? z4 : x[int64_t(m0) * L4 + q];
+            const float4 x1 = (a.masked && m1 >= a.n_interior) ? z4 : x[int64_t(m1) * L4 + q];
+            const float4 x2 = (a.masked && m2 >= a.n_interior) ? z4 : x[int64_t(m2) * L4 + q];
+            const float4 x3 = (a.masked && m3 >= a.n_interior) ? z4 : x[int64_t(m3) * L4 + q];
+            f4fma(val, a.hw[e], x0);
+            f4fma(val, a.hw[e + 1], x1);
+            f4fma(val, a.hw[e + 2], x2);
+            f4fma(val, a.hw[e + 3], x3);
+        }
+#elif AFEM_HANG_UNROLL >= 2
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (; e + 2 <= e1; e += 2) {
+            const int m0 = a.hm[e], m1 = a.hm[e + 1];
+            const float4 x0 = (a.masked && m0 >= a.n_interior) ? z4 : x[int64_t(m0) * L4 + q];
+            const float4 x1 = (a.masked && m1 >= a.n_interior) ? z4 : x[int64_t(m1) * L4 + q];
+            f4fma(val, a.hw[e], x0);
+            f4fma(val, a.hw[e + 1], x1);
+        }
+#endif
+        for (; e < e1; ++e) {
             const int m = a.hm[e];
             if (a.masked && m >= a.n_interior) continue;
             f4fma(val, a.hw[e], x[int64_t(m) * L4 + q]);
@@ -201,8 +285,26 @@ __device__ __forceinline__ void scatter32v(const CellArgs32& a, int idx, float4*
     if (idx >= 0) {
         if (!(a.masked && idx >= a.n_interior)) atomicAdd(&y[int64_t(idx) * L4 + q], r);
     } else {
+        // the constraint row four entries per round: its index and weight loads
+        // issued before the round's atomics (which the loads may not pass)
         const int hh = -idx - 1;
-        for (int e = a.hp[hh]; e < a.hp[hh + 1]; ++e) {
+        const int e1 = a.hp[hh + 1];
+        int e = a.hp[hh];
+        for (; e + 4 <= e1; e += 4) {
+            int mm[4];
+            float ww[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                mm[u] = a.hm[e + u];
+                ww[u] = a.hw[e + u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (!(a.masked && mm[u] >= a.n_interior))
+                    atomicAdd(&y[int64_t(mm[u]) * L4 + q],
+                              make_float4(ww[u] * r.x, ww[u] * r.y, ww[u] * r.z, ww[u] * r.w));
+        }
+        for (; e < e1; ++e) {
             const int m = a.hm[e];
             if (a.masked && m >= a.n_interior) continue;
             const float w = a.hw[e];
@@ -326,6 +428,8 @@ __device__ __forceinline__ void cell32v_body(const CellArgs32& a, int64_t item, 
                 const int j = it / h2, c = it - j * h2;
                 const int idx = s_idx[j];
                 if (idx >= 0) cp_async16(s_U4 + j * SU + c, U4 + int64_t(idx) * h2 + c);
+                else if (a.u_hang)
+                    cp_async16(s_U4 + j * SU + c, reinterpret_cast<const float4*>(a.u_hang) + int64_t(-idx - 1) * h2 + c);
                 else s_U4[j * SU + c] = gather32v(au, idx, U4, h2, c);
             }
         }
@@ -494,7 +598,9 @@ __global__ void __launch_bounds__(128) cell32L_kernel(CellArgs32 a, const float4
             au.masked = 0;
             for (int it = tid; it < NN * nn2; it += bs) {
                 const int i = it / nn2, pq = it - i * nn2;
-                s_U[it] = gather32<float2>(au, s_idx[i], U, nn2, pq);
+                const int idx = s_idx[i];
+                s_U[it] = (idx < 0 && a.u_hang) ? a.u_hang[int64_t(-idx - 1) * nn2 + pq]
+                                                : gather32<float2>(au, idx, U, nn2, pq);
             }
         }
         const float h3 = g.w * g.w * g.w;
@@ -632,8 +738,10 @@ static int launch32(const afem_mesh* m, const CellArgs32& a, const T* x, const f
 #define AFEM_CASE(PP)                                                                          \
     case PP: {                                                                                 \
         auto k = cell32_kernel<PP, T, G, false>;                                               \
-        if constexpr (G && sizeof(T) == sizeof(float2))                                        \
+        if constexpr (G && sizeof(T) == sizeof(float2)) {                                      \
             if (a.vg) k = cell32_kernel<PP, T, G, true>;                                       \
+            if (a.ecs_flags) k = cell32_kernel<PP, T, G, false, true>;                         \
+        }                                                                                      \
         if (smem > 48 * 1024)                                                                  \
             AFEM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                                int(smem)));                                    \
@@ -654,6 +762,164 @@ static int launch32(const afem_mesh* m, const CellArgs32& a, const T* x, const f
 
 // The four-lane kernel for a quad count (compile-time for 1..4), with the p.Ap
 // epilogue when asked (stiffness, 1, 2 or 4 quads).
+// Column-pair line pass of the stiffness (AFEM_OPT_CELL32_VARIANT = 2): the
+// three 1D contractions of the sum factorisation each run over whole lines of
+// a cell, one thread per (line, column pair): it reads the p+1 values of its
+// line once, forms the p+1 outputs in registers (the 1D matrix is read from the
+// kernel's parameters), and accumulates them in shared memory, which the next
+// direction re-reads along its own lines.  Shared-memory traffic per output is
+// one load and one store per direction instead of 3 (p+1) loads, and the
+// float2 granularity keeps the line in p+1 register pairs.  Small cells are
+// grouped so that a direction's items fill the block.
+__host__ __device__ constexpr int cells_per_itemT(int P, int L2) {
+    return (P + 1) * (P + 1) * L2 >= 256 ? 1 : 256 / ((P + 1) * (P + 1) * L2);
+}
+
+__host__ __device__ constexpr size_t cell32T_smem(int P, int L2) {
+    return size_t(cells_per_itemT(P, L2)) *
+           (16 + size_t((P + 1) * (P + 1) * (P + 1)) * (size_t(L2) * 16 + sizeof(int)));
+}
+
+template <int P, int L2, bool PAP>
+__global__ void __launch_bounds__(256, 8) cell32T_kernel(const __grid_constant__ CellArgs32 a,
+                                                         const float4* __restrict__ x, float4* __restrict__ y) {
+    constexpr int P1 = P + 1;
+    constexpr int NN = P1 * P1 * P1;
+    constexpr int NL = P1 * P1;
+    constexpr int L4 = L2 / 2;
+    constexpr int CB = cells_per_itemT(P, L2);
+    static_assert(L2 % 2 == 0 && CB * NL * L2 <= 256, "one direction's items must fit the block");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float4* s_g = reinterpret_cast<float4*>(smem_raw);        // [CB] corner, side
+    float2* s_u = reinterpret_cast<float2*>(s_g + CB);        // [CB][NN][L2] the gathered input
+    float2* s_acc = s_u + CB * NN * L2;                       // [CB][NN][L2] the cell outputs
+    int* s_idx = reinterpret_cast<int*>(s_acc + CB * NN * L2);   // [CB][NN]
+    const int64_t cell0 = int64_t(blockIdx.x) * CB;
+    const int nc = int(a.ncell - cell0 < CB ? a.ncell - cell0 : CB);
+    const int tid = threadIdx.x;
+    for (int j = tid; j < nc * NN; j += blockDim.x) s_idx[j] = a.cell_node[cell0 * NN + j];
+    if (tid < nc) s_g[tid] = a.geom[cell0 + tid];
+    __syncthreads();
+    float4* s_u4 = reinterpret_cast<float4*>(s_u);
+    for (int it = tid; it < nc * NN * L4; it += blockDim.x) {
+        const int j = it / L4, q = it - j * L4;
+        s_u4[it] = gather32v(a, s_idx[j], x, L4, q);
+    }
+    __syncthreads();
+    // this thread's item in every direction: (cell slot, line, column pair)
+    const int c2 = tid % L2;
+    const int line = (tid / L2) % NL;
+    const int cb = tid / (L2 * NL);
+    const bool act = cb < nc;
+    const int l0 = line % P1, l1 = line / P1;
+    const float2* ub = s_u + (cb * NN) * L2 + c2;
+    float2* ab = s_acc + (cb * NN) * L2 + c2;
+    const float sc = act ? s_g[cb].w * a.w[l0] * a.w[l1] : 0.0f;
+    float2 u[P1];
+    // direction x: line (b, c) = (l0, l1), nodes m + P1 line
+    if (act) {
+#pragma unroll
+        for (int m = 0; m < P1; ++m) u[m] = ub[(m + P1 * line) * L2];
+#pragma unroll
+        for (int o = 0; o < P1; ++o) {
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int m = 0; m < P1; ++m) vfma(acc, a.K[o * P1 + m], u[m]);
+            ab[(o + P1 * line) * L2] = make_float2(sc * acc.x, sc * acc.y);
+        }
+    }
+    __syncthreads();
+    // direction y: line (a, c) = (l0, l1), nodes l0 + P1 (m + P1 l1)
+    if (act) {
+#pragma unroll
+        for (int m = 0; m < P1; ++m) u[m] = ub[(l0 + P1 * (m + P1 * l1)) * L2];
+#pragma unroll
+        for (int o = 0; o < P1; ++o) {
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int m = 0; m < P1; ++m) vfma(acc, a.K[o * P1 + m], u[m]);
+            float2& r = ab[(l0 + P1 * (o + P1 * l1)) * L2];
+            r.x = fmaf(sc, acc.x, r.x);
+            r.y = fmaf(sc, acc.y, r.y);
+        }
+    }
+    __syncthreads();
+    // direction z: line (a, b) = (l0, l1), nodes line + NL m
+    if (act) {
+#pragma unroll
+        for (int m = 0; m < P1; ++m) u[m] = ub[(line + NL * m) * L2];
+#pragma unroll
+        for (int o = 0; o < P1; ++o) {
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int m = 0; m < P1; ++m) vfma(acc, a.K[o * P1 + m], u[m]);
+            float2& r = ab[(line + NL * o) * L2];
+            r.x = fmaf(sc, acc.x, r.x);
+            r.y = fmaf(sc, acc.y, r.y);
+        }
+    }
+    __syncthreads();
+    const float4* s_acc4 = reinterpret_cast<const float4*>(s_acc);
+    float4 pap = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int it = tid; it < nc * NN * L4; it += blockDim.x) {
+        const int j = it / L4, q = it - j * L4;
+        const float4 r = s_acc4[it];
+        scatter32v(a, s_idx[j], y, L4, q, r);
+        if constexpr (PAP) {   // the cell's part of p.Ap (p is zero on the surface)
+            const float4 v = s_u4[it];
+            pap.x = fmaf(v.x, r.x, pap.x);
+            pap.y = fmaf(v.y, r.y, pap.y);
+            pap.z = fmaf(v.z, r.z, pap.z);
+            pap.w = fmaf(v.w, r.w, pap.w);
+        }
+    }
+    if constexpr (PAP) {
+        static_assert(32 % L4 == 0, "the p.Ap lanes of one column quad are L4 apart");
+        // blockDim is a multiple of 32 and of L4, so a lane's quad is tid % L4 in every iteration
+#pragma unroll
+        for (int off = L4; off < 32; off <<= 1) {
+            pap.x += __shfl_xor_sync(0xffffffffu, pap.x, off);
+            pap.y += __shfl_xor_sync(0xffffffffu, pap.y, off);
+            pap.z += __shfl_xor_sync(0xffffffffu, pap.z, off);
+            pap.w += __shfl_xor_sync(0xffffffffu, pap.w, off);
+        }
+        __shared__ float4 s_pap[8][L4];
+        const int lane = tid & 31, warp = tid >> 5;
+        if (lane < L4 && warp < 8) s_pap[warp][lane] = pap;
+        __syncthreads();
+        if (tid < 4 * L4) {
+            const int q = tid >> 2, comp = tid & 3;
+            double xs = 0.0;
+            for (int w8 = 0; w8 < 8 && w8 * 32 < int(blockDim.x); ++w8) {
+                const float4 v = s_pap[w8][q];
+                xs += widen_f32(comp == 0 ? v.x : comp == 1 ? v.y : comp == 2 ? v.z : v.w);
+            }
+            atomicAdd(&a.pap_slots[int64_t(blockIdx.x % kPapSlots) * (4 * L4) + tid], xs);
+        }
+    }
+}
+
+template <int PP, int L2>
+static int launch32T_l(const afem_mesh* m, const CellArgs32& a, const float4* x, float4* y, cudaStream_t s) {
+    constexpr int CB = cells_per_itemT(PP, L2);
+    const size_t smem = cell32T_smem(PP, L2);
+    auto k = a.pap_slots ? cell32T_kernel<PP, L2, true> : cell32T_kernel<PP, L2, false>;
+    if (smem > 48 * 1024)
+        AFEM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    const unsigned items = unsigned((m->dev.ncell + CB - 1) / CB);
+    AFEM_LAUNCH((k), items, 256, smem, s, a, x, y);
+    AFEM_CUDA_TRY(cudaGetLastError());
+    return AFEM_OK;
+}
+
+// The column-pair line pass of the stiffness for 1, 2 or 4 column quads.
+template <int PP>
+static int launch32T(const afem_mesh* m, const CellArgs32& a, const float4* x, float4* y, int L4, cudaStream_t s) {
+    if (L4 == 1) return launch32T_l<PP, 2>(m, a, x, y, s);
+    if (L4 == 2) return launch32T_l<PP, 4>(m, a, x, y, s);
+    return launch32T_l<PP, 8>(m, a, x, y, s);
+}
+
 template <int PP, bool G>
 static auto pick32v(int L4, bool pap) {
     if constexpr (!G) {
@@ -680,6 +946,15 @@ static int launch32v(const afem_mesh* m, const CellArgs32& a, const float* x, co
     if (grid == 0) return AFEM_OK;
     const float4* x4 = reinterpret_cast<const float4*>(x);
     float4* y4 = reinterpret_cast<float4*>(y);
+    if (!G && m->cell32_variant == 2 && (L4 == 1 || L4 == 2 || L4 == 4)) {
+        switch (p) {
+            case 1: return launch32T<1>(m, a, x4, y4, L4, s);
+            case 2: return launch32T<2>(m, a, x4, y4, L4, s);
+            case 3: return launch32T<3>(m, a, x4, y4, L4, s);
+            case 4: return launch32T<4>(m, a, x4, y4, L4, s);
+            default: return set_error(AFEM_EINVAL, "degree out of range");
+        }
+    }
     if (m->cell32_variant == 1) {
         const size_t smemL =
             2 * size_t(nn) * L4 * sizeof(float4) + ((G && U) ? size_t(nn) * n * n * sizeof(float2) : 0);
@@ -742,7 +1017,7 @@ int launch_stiffness32(const afem_mesh* m, const float* x, float* y, int nv, int
     a.masked = masked;
     const bool quads = nv % 4 == 0 && aligned16(x) && aligned16(y);
     if (pap_slots) {
-        if (!quads || !(nv == 4 || nv == 8 || nv == 16) || m->cell32_variant != 0)
+        if (!quads || !(nv == 4 || nv == 8 || nv == 16) || m->cell32_variant == 1)
             return set_error(AFEM_EINVAL, "stiffness: fused p.Ap needs 4, 8 or 16 aligned columns");
         a.pap_slots = pap_slots;
     }
@@ -754,10 +1029,19 @@ int launch_stiffness32(const afem_mesh* m, const float* x, float* y, int nv, int
 // velocity != 0: E holds the vector potential A (velocity gauge), applied by
 // the generic (two-lane) kernel.
 int launch_g_cell32(const afem_mesh* m, const double* E, const float2* v, const float2* U, float2* z, int n,
-                    cudaStream_t s, int velocity) {
+                    cudaStream_t s, int velocity, const float2* U_hang) {
     CellArgs32 a = make_cell_args32(m);
     a.masked = 1;
+    a.u_hang = U ? U_hang : nullptr;
     for (int i = 0; i < 3; ++i) a.E[i] = (E && !velocity) ? float(E[i]) : 0.0f;
+    if (m->ecs_on) {   // complex-scaled kinetic term: the generic (two-lane) kernel
+        if (velocity) return set_error(AFEM_EINVAL, "complex scaling is built for the length gauge");
+        a.ecs_flags = m->ecs_flags;
+        a.ecs_rho = m->ecs_rho32;
+        for (int k = -2; k <= 3; ++k)
+            a.ecs_e[k + 2] = make_float2(float(std::cos(k * m->ecs_theta)), float(std::sin(k * m->ecs_theta)));
+        return launch32<float2, true>(m, a, v, U, z, n, s);
+    }
     if (velocity && E) {
         a.vg = 1;
         for (int i = 0; i < 3; ++i) a.Avec[i] = float(E[i]);
@@ -788,6 +1072,7 @@ size_t batch32_inst_bytes() { return sizeof(BatchInst32); }
 // orbitals, nvec even) or AFEM_OP_STIFF_F32 (nvec real columns, nvec % 4 == 0).
 int batch32_fill(const afem_mesh* m, int kind, const double* E, const void* x, void* y, int nvec, int64_t cell0,
                  void* out) {
+    if (m->ecs_on) return set_error(AFEM_EINVAL, "afem_batch: not built for a complex-scaled mesh");
     BatchInst32 b{};
     b.a = make_cell_args32(m);
     const int L = kind == AFEM_OP_H1_C64 ? 2 * nvec : nvec;

@@ -680,6 +680,8 @@ int mctdhf_step(afem_mctdhf* S, double2* phi, double2* C, double* W, const doubl
     const DeviceMesh& D = m->dev;
     const int n = S->n, nn = n * n;
     const int64_t N = D.n_master, dim = S->ci.dim;
+    if (m->ecs_on && (S->imaginary || S->gauge == AFEM_GAUGE_VELOCITY))
+        return set_error(AFEM_EINVAL, "afem_mctdhf_step: complex scaling is built for real-time, length-gauge steps");
     StepWork w{};
     Carver measure(nullptr);
     const bool mixed_form = S->precision == AFEM_PREC_MIXED;

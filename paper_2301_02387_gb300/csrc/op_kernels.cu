@@ -12,6 +12,8 @@
 //   -> scatter-add through C^T (atomics) ,
 // and the one-body operator of Eq. discretized_eom, H1~ = 1/2 A + F[V + E.r],
 // is this pass followed by the inverse lumped mass.
+#include <cmath>
+
 #include "afem_internal.h"
 #include "cell_common.cuh"
 #include "vec_common.cuh"
@@ -39,9 +41,20 @@ __device__ __forceinline__ void add_velocity_term(double2& r, const double* s_S,
     r.y -= t.x;
 }
 
+// The kinetic part of a complex-scaled cell: ck (sx w_b w_c ax + sy w_a w_c ay
+// + sz w_a w_b az) with the cell's complex factors (afem_mesh_set_ecs).
+__device__ __forceinline__ double2 ecs_kinetic(double2 sx, double2 sy, double2 sz, double cx, double cy,
+                                               double cz, double2 ax, double2 ay, double2 az) {
+    const double2 tx = cmul(sx, make_double2(cx * ax.x, cx * ax.y));
+    const double2 ty = cmul(sy, make_double2(cy * ay.x, cy * ay.y));
+    const double2 tz = cmul(sz, make_double2(cz * az.x, cz * az.y));
+    return make_double2(tx.x + ty.x + tz.x, tx.y + ty.y + tz.y);
+}
+
 // VG: with the velocity-gauge term (complex data; a.vg set), a separate
 // instantiation so that the plain operator keeps its register budget.
-template <int P, typename T, bool VG = false>
+// ECS: complex-scaled kinetic term (complex data; the mesh's scaling set).
+template <int P, typename T, bool VG = false, bool ECS = false>
 __global__ void __launch_bounds__(256) cell_op_kernel(CellArgs a, const T* __restrict__ x,
                                                       T* __restrict__ y, int nv) {
     constexpr int P1 = P + 1;
@@ -107,20 +120,30 @@ __global__ void __launch_bounds__(256) cell_op_kernel(CellArgs a, const T* __res
             vfma(ay, s_K[ib * P1 + m], s_u[(ia + P1 * (m + P1 * ic)) * nv + v]);
             vfma(az, s_K[ic * P1 + m], s_u[(ia + P1 * (ib + P1 * m)) * nv + v]);
         }
-        T r = vzero<T>();
-        vfma(r, ck * s_w[ib] * s_w[ic], ax);
-        vfma(r, ck * s_w[ia] * s_w[ic], ay);
-        vfma(r, ck * s_w[ia] * s_w[ib], az);
-        if (a.with_pot) vfma(r, s_pot[n], s_u[it]);
-        if constexpr (VG) add_velocity_term(r, s_S, s_w, s_u, ia, ib, ic, nv, v, g.w * g.w, a.Avec, P1);
-        scatter_value<T>(a, s_idx[n], y, nv, v, r);
+        if constexpr (ECS) {
+            double2 sx, sy, sz;
+            ecs_factors(a.ecs, cell, sx, sy, sz);
+            const double2 rk = ecs_kinetic(sx, sy, sz, ck * s_w[ib] * s_w[ic], ck * s_w[ia] * s_w[ic],
+                                           ck * s_w[ia] * s_w[ib], ax, ay, az);
+            double2 rp = make_double2(0.0, 0.0);
+            if (a.with_pot) vfma(rp, s_pot[n], s_u[it]);
+            scatter_ecs(a, s_idx[n], y, nv, v, rk, rp);
+        } else {
+            T r = vzero<T>();
+            vfma(r, ck * s_w[ib] * s_w[ic], ax);
+            vfma(r, ck * s_w[ia] * s_w[ic], ay);
+            vfma(r, ck * s_w[ia] * s_w[ib], az);
+            if (a.with_pot) vfma(r, s_pot[n], s_u[it]);
+            if constexpr (VG) add_velocity_term(r, s_S, s_w, s_u, ia, ib, ic, nv, v, g.w * g.w, a.Avec, P1);
+            scatter_value<T>(a, s_idx[n], y, nv, v, r);
+        }
     }
 }
 
 // Packed orbital operator before projection and inverse mass (Eqs. orb_eom,
 // discretized_eom):  z_p = H1~ v_p + C^T diag(m_f) sum_q (C U_pq) o (C v_q),
 // for all n orbitals of one cell at once.  U: complex [N][n][n] nodal fields.
-template <int P, bool VG = false>
+template <int P, bool VG = false, bool ECS = false>
 __global__ void __launch_bounds__(256) g_cell_kernel(CellArgs a, const double2* __restrict__ v,
                                                      const double2* __restrict__ U, double2* __restrict__ z,
                                                      int n) {
@@ -157,7 +180,9 @@ __global__ void __launch_bounds__(256) g_cell_kernel(CellArgs a, const double2* 
         au.masked = 0;   // the mean fields are defined on all masters
         for (int it = tid; it < NN * nn2; it += bs) {
             const int i = it / nn2, pq = it - i * nn2;
-            s_U[it] = gather_value<double2>(au, s_idx[i], U, nn2, pq);
+            const int idx = s_idx[i];
+            s_U[it] = (idx < 0 && a.u_hang) ? a.u_hang[int64_t(-idx - 1) * nn2 + pq]
+                                            : gather_value<double2>(au, idx, U, nn2, pq);
         }
     }
     {
@@ -187,9 +212,17 @@ __global__ void __launch_bounds__(256) g_cell_kernel(CellArgs a, const double2* 
             vfma(az, s_K[ic * P1 + m], s_u[(ia + P1 * (ib + P1 * m)) * n + p]);
         }
         double2 r = vzero<double2>();
-        vfma(r, ck * s_w[ib] * s_w[ic], ax);
-        vfma(r, ck * s_w[ia] * s_w[ic], ay);
-        vfma(r, ck * s_w[ia] * s_w[ib], az);
+        double2 rk = vzero<double2>();
+        if constexpr (ECS) {   // kinetic part apart (scaled at the scatter); r keeps the pointwise terms
+            double2 sx, sy, sz;
+            ecs_factors(a.ecs, cell, sx, sy, sz);
+            rk = ecs_kinetic(sx, sy, sz, ck * s_w[ib] * s_w[ic], ck * s_w[ia] * s_w[ic], ck * s_w[ia] * s_w[ib], ax,
+                             ay, az);
+        } else {
+            vfma(r, ck * s_w[ib] * s_w[ic], ax);
+            vfma(r, ck * s_w[ia] * s_w[ic], ay);
+            vfma(r, ck * s_w[ia] * s_w[ib], az);
+        }
         vfma(r, s_pot[i], s_u[it]);
         if constexpr (VG) add_velocity_term(r, s_S, s_w, s_u, ia, ib, ic, n, p, g.w * g.w, a.Avec, P1);
         if (U) {
@@ -202,19 +235,23 @@ __global__ void __launch_bounds__(256) g_cell_kernel(CellArgs a, const double2* 
             }
             vfma(r, s_wq[i], mf);
         }
-        scatter_value<double2>(a, s_idx[i], z, n, p, r);
+        if constexpr (ECS) scatter_ecs(a, s_idx[i], z, n, p, rk, r);
+        else scatter_value<double2>(a, s_idx[i], z, n, p, r);
     }
 }
 
 // velocity != 0: E holds the vector potential A of the velocity gauge (the
 // field term is then -i A . grad instead of E . r).
 int launch_g_cell(const afem_mesh* m, const double* E, const double2* v, const double2* U, double2* z, int n,
-                  cudaStream_t s, int velocity) {
+                  cudaStream_t s, int velocity, const double2* U_hang) {
     CellArgs a = make_cell_args(m);
+    a.u_hang = U ? U_hang : nullptr;
     a.c_kin = 0.5;
     a.with_pot = 1;
     a.masked = 1;
     for (int i = 0; i < 3; ++i) a.E[i] = (E && !velocity) ? E[i] : 0.0;
+    if (velocity && m->ecs_on)
+        return set_error(AFEM_EINVAL, "complex scaling is built for the length gauge");
     if (velocity && E) {
         a.vg = 1;
         for (int i = 0; i < 3; ++i) a.Avec[i] = E[i];
@@ -229,6 +266,7 @@ int launch_g_cell(const afem_mesh* m, const double* E, const double2* v, const d
 #define AFEM_CASE(PP)                                                                          \
     case PP: {                                                                                 \
         auto k = a.vg ? g_cell_kernel<PP, true> : g_cell_kernel<PP, false>;                    \
+        if (m->ecs_on) k = g_cell_kernel<PP, false, true>;                                     \
         if (smem > 48 * 1024)                                                                  \
             AFEM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                                int(smem)));                                    \
@@ -270,6 +308,12 @@ CellArgs make_cell_args(const afem_mesh* m) {
     a.f_master = D.f_master;
     a.f_hang = D.f_hang;
     a.n_interior = D.n_interior;
+    if (m->ecs_on) {
+        a.ecs.flags = m->ecs_flags;
+        a.ecs.rho = m->ecs_rho;
+        for (int k = -2; k <= 3; ++k)
+            a.ecs.e[k + 2] = make_double2(std::cos(k * m->ecs_theta), std::sin(k * m->ecs_theta));
+    }
     const Basis1D& b = m->basis;
     const int p1 = b.p + 1;
     for (int i = 0; i < p1; ++i) {
@@ -296,8 +340,10 @@ static int launch_cell_op(const afem_mesh* m, const CellArgs& a, const T* x, T* 
 #define AFEM_CASE(PP)                                                                          \
     case PP: {                                                                                 \
         auto k = cell_op_kernel<PP, T, false>;                                                 \
-        if constexpr (sizeof(T) == sizeof(double2))                                            \
+        if constexpr (sizeof(T) == sizeof(double2)) {                                          \
             if (a.vg) k = cell_op_kernel<PP, T, true>;                                         \
+            if (a.ecs.flags) k = cell_op_kernel<PP, T, false, true>;                           \
+        }                                                                                      \
         if (smem > 48 * 1024)                                                                  \
             AFEM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                                int(smem)));                                    \
@@ -339,7 +385,7 @@ int launch_stiffness(const afem_mesh* m, const double* x, double* y, int nv, int
 int launch_stiffness32(const afem_mesh* m, const float* x, float* y, int nv, int masked, cudaStream_t s,
                        double* pap_slots = nullptr);
 int launch_g_cell32(const afem_mesh* m, const double* E, const float2* v, const float2* U, float2* z, int n,
-                    cudaStream_t s, int velocity = 0);
+                    cudaStream_t s, int velocity = 0, const float2* U_hang = nullptr);
 
 int launch_op_apply(afem_mesh* m, int kind, const double* E, const void* x, void* y, int nv,
                     cudaStream_t s) {
@@ -356,6 +402,8 @@ int launch_op_apply(afem_mesh* m, int kind, const double* E, const void* x, void
         if (rc) return rc;
         return launch_scale_rows<double2>(yy, m->dev.ml_inv, N, nv, s);
     }
+    if ((kind == AFEM_OP_H1_VG || kind == AFEM_OP_H1_VG_C64) && m->ecs_on)
+        return set_error(AFEM_EINVAL, "afem_op_apply: complex scaling is built for the length gauge");
     if (kind == AFEM_OP_H1_VG) {   // velocity gauge: E holds A
         a.c_kin = 0.5;
         a.with_pot = 1;

@@ -1010,7 +1010,7 @@ int poisson_batch_mixed(afem_mesh* m, const double2* phi, int n, double* W, doub
     const int k = n * n;
     const bool quads = (k % 4) == 0;   // four columns per thread in the float32 CG kernels
     // p.Ap formed by the stiffness pass itself (its four-lane form with 1, 2 or 4 quads)
-    const bool fused = quads && (k == 4 || k == 8 || k == 16) && m->cell32_variant == 0;
+    const bool fused = quads && (k == 4 || k == 8 || k == 16) && m->cell32_variant != 1;
     const int64_t N = D.n_master, Ni = D.n_interior;
     const int nblk = red_blocks();
     const size_t NK = size_t(N) * k;

@@ -107,6 +107,8 @@ int check_common(afem_mesh* m, const double* e_dir, const double* E, int K, doub
     if (observable != AFEM_OP_POS && observable != AFEM_OP_FORCE)
         return set_error(AFEM_EINVAL, w + ": observable must be AFEM_OP_POS or AFEM_OP_FORCE");
     if (!m || !e_dir || (K > 0 && !E)) return set_error(AFEM_EINVAL, w + ": null argument");
+    if (m->ecs_on)   // the adjoint sweep takes the operator as self-adjoint, which complex scaling breaks
+        return set_error(AFEM_EINVAL, w + ": not built for a complex-scaled mesh");
     if (K < 0) return set_error(AFEM_EINVAL, w + ": n_steps must be >= 0");
     if (!(dt > 0.0)) return set_error(AFEM_EINVAL, w + ": dt must be > 0");
     if (mk < 1 || mk > kMaxKrylov) return set_error(AFEM_EINVAL, w + ": krylov_m must be 1..16");

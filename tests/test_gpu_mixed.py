@@ -135,20 +135,26 @@ def test_arnoldi_orbital_counts_with_mean_field(case, n):
         assert_close(out.cpu().numpy(), ref[perm], bar, what=f"precision {prec}")
 
 
-@pytest.mark.parametrize("n", [4, 6, 8])
-def test_mixed_poisson_column_counts(pair, n):
-    """The precision form's Poisson batch for 16 columns (fused p.Ap), 36 and 64
-    columns (9 and 16 float4 quads per node: the run-time quad count): FP64
+@pytest.mark.parametrize("n", [2, 4, 6, 8])
+@pytest.mark.parametrize("variant", [0, 2])
+def test_mixed_poisson_column_counts(pair, n, variant):
+    """The precision form's Poisson batch for 4 and 16 columns (fused p.Ap), 36
+    and 64 columns (9 and 16 float4 quads per node: the run-time quad count),
+    with the node-per-thread and the column-pair line stiffness pass: FP64
     backward error <= 2e-10 in the oracle's matrices."""
     import torch
     import paper_2301_02387_gb300 as pkg
     gm, om, op, perm = pair
+    pkg.mesh_set_option(gm, pkg.OPT_CELL32_VARIANT, variant)
     phi_o = inputs.lowdin(inputs.molecular_orbitals(om.Xm, ~om.boundary, CASE[4], n), op.ML)
     ps = poisson.PoissonSolver(op)
     rho, _ = poisson.pair_densities(op, phi_o)
     phi = torch.from_numpy(np.ascontiguousarray(phi_o[perm])).cuda()
     W = torch.zeros((gm.N, n * n), dtype=torch.float64, device="cuda")
-    it, rel, rc = pkg.poisson_batch(gm, phi, W, rtol=1e-10, max_it=20000, precision=pkg.PREC_MIXED)
+    try:
+        it, rel, rc = pkg.poisson_batch(gm, phi, W, rtol=1e-10, max_it=20000, precision=pkg.PREC_MIXED)
+    finally:
+        pkg.mesh_set_option(gm, pkg.OPT_CELL32_VARIANT, 0)
     assert rc == 0 and np.all(rel <= 1e-10)
     Wg = np.empty((om.N, n * n))
     Wg[perm] = W.cpu().numpy()

@@ -84,7 +84,8 @@ def test_op_apply_rejects_bad_arguments():
 # group on these meshes)
 @pytest.mark.parametrize("case", CASES)
 @pytest.mark.parametrize("nvec", [3, 4, 8, 12, 16])
-@pytest.mark.parametrize("variant", [0, 1])   # four-lane: node-per-thread / line-ordered
+# four-lane: node-per-thread / line-ordered / column-pair lines (1, 2, 4 quads)
+@pytest.mark.parametrize("variant", [0, 1, 2])
 def test_stiffness_f32_within_fp32_tolerance(case, nvec, variant):
     """Precision form of the stiffness: relative error a few float32 ulps x operator norm."""
     import torch
