@@ -70,8 +70,9 @@ def test_ecs_removed_restores_the_operator():
     pkg.mesh_set_ecs(gm, 0.0, R)
     pkg.op_apply(gm, pkg.OP_H1, x, y2)
     torch.cuda.synchronize()
-    assert torch.equal(y0, y2)
-    assert not torch.equal(y0, y1)
+    # the scatter adds by atomics, so repeated applies agree to rounding order only
+    assert_close(y2.cpu().numpy(), y0.cpu().numpy(), 1e-14, what="unscaled again")
+    assert (y1 - y0).abs().max().item() > 1e-3 * y0.abs().max().item()
 
 
 def test_ecs_argument_checks():
