@@ -50,7 +50,9 @@ extern "C" {
 /* Arithmetic forms.  AFEM_PREC_FP64: everything in float64 / complex128.
  * AFEM_PREC_MIXED: the cell operators (stiffness in the Poisson CG sweeps,
  * the packed orbital operator G) run in float32 / complex64; the Poisson
- * solution is refined with float64 residuals to the requested rtol, and the
+ * solution is refined with float64 residuals to the requested rtol; the
+ * two-electron integrals run on the tensor cores (TF32 operands split hi/lo
+ * for float32 accuracy, float64 sums of 32-point tiles); and the
  * Arnoldi Gram-Schmidt, the small Krylov exponential, the density-matrix
  * inverse and the CI propagation stay float64. */
 #define AFEM_PREC_FP64 0
@@ -345,6 +347,24 @@ int afem_poisson_batch_ex(afem_mesh* mesh, const void* phi, int n_orb, void* W, 
  * Asynchronous on `stream`. */
 #define AFEM_NOALLOC_MAX_ORB 4
 int afem_poisson_boundary_noalloc(afem_mesh* mesh, const void* phi, int n_orb, void* W, void* stream);
+
+/* Two-electron integrals of orbitals phi with their pair mean fields W (Sec. 2,
+ * the integrals of Eq. ci_eom with the potentials of Eq. mean-field):
+ *   (pq|rs) = sum_f m_f conj(phi_p(f)) phi_q(f) W^r_s(f)
+ * over every support point f (hanging points through the constraints C), m_f
+ * the assembled GLL weight.  The same quantity the MCTDHF step forms.
+ * phi: complex128 [N][n_orb] device (surface entries treated as zero);
+ * W: float64 [N][n_orb^2] device in the column layout of afem_poisson_batch;
+ * eri: complex128 [n_orb^2][n_orb^2] device, caller-owned, written
+ *   eri[(p n + q) n^2 + (r n + s)] = (pq|rs).  n_orb: 1..8.
+ * precision: AFEM_PREC_FP64 (float64 sums) or AFEM_PREC_MIXED (the contraction
+ *   as tcgen05 tensor-core MMAs: TF32 operands split hi/lo, three products per
+ *   tile, float32 sums of 32 support points added in float64).
+ * Allocates (grow-only) device workspace owned by the mesh on first use.
+ * Synchronises `stream` (reads a status word); AFEM_ECUDA if a tensor-core
+ * block gave up waiting for its MMAs (bounded waits; no hang). */
+int afem_two_electron_integrals(afem_mesh* mesh, const void* phi, int n_orb, const void* W, void* eri,
+                                int precision, void* stream);
 
 /* One short-iterative Arnoldi step of the packed orbital equation with the
  * operator frozen (Sec. 3.2, Eq. packed_orb_eom; Eq. orb_eom with X = 0):

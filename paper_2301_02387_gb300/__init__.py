@@ -139,6 +139,25 @@ def poisson_batch(mesh, phi, W, rtol=1e-10, max_it=20000, warm_start=False, stre
     return it.value, rel, rc
 
 
+def two_electron_integrals(mesh, phi, W, eri=None, precision=PREC_FP64, stream=None):
+    """afem_two_electron_integrals: (pq|rs) as a [n^2, n^2] complex128 tensor,
+    eri[p n + q, r n + s], from orbitals phi ([N, n] complex128) and their pair
+    mean fields W ([N, n^2] float64, the column layout of poisson_batch)."""
+    import torch
+    n = int(phi.shape[1])
+    _dev_ptr(phi, torch.complex128, mesh.N, "phi")
+    _dev_ptr(W, torch.float64, mesh.N, "W")
+    if W.shape[1] != n * n:
+        raise ValueError("W must have n_orb^2 columns")
+    if eri is None:
+        eri = torch.empty((n * n, n * n), dtype=torch.complex128, device=phi.device)
+    _dev_ptr(eri, torch.complex128, n * n, "eri")
+    _capi.check(_capi.load().afem_two_electron_integrals(
+        mesh.handle, ctypes.c_void_p(phi.data_ptr()), n, ctypes.c_void_p(W.data_ptr()),
+        ctypes.c_void_p(eri.data_ptr()), int(precision), _stream_ptr(stream)))
+    return eri
+
+
 def _E3(E):
     if E is None:
         return None

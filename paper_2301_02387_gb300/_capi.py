@@ -126,6 +126,7 @@ SIGNATURES = {
     "afem_poisson_batch_ex": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_double, ctypes.c_int,
                                              ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]),
     "afem_poisson_boundary_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P]),
+    "afem_two_electron_integrals": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P, ctypes.c_int, _P]),
     "afem_arnoldi_step_ex": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                             ctypes.c_int, _P, _P, _P, _P, _P]),
     "afem_mctdhf_set_precision": (ctypes.c_int, [_P, ctypes.c_int]),

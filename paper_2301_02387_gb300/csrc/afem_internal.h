@@ -161,6 +161,7 @@ struct afem_mesh {
     afem::Workspace ws_poisson;
     afem::Workspace ws_arnoldi;
     afem::Workspace ws_tdse;
+    afem::Workspace ws_int;   // afem_two_electron_integrals
     int cell32_variant = 0;   // FP32 four-lane cell pass: 0 node-per-thread, 1 line-ordered
     int poisson_solver = 0;   // AFEM_POISSON_JACOBI or AFEM_POISSON_MULTIGRID
     afem_pmg* pmg = nullptr;  // built on the first multigrid solve
@@ -199,6 +200,15 @@ void mctdhf_set_imaginary(afem_mctdhf* S, int on);
 void mctdhf_set_gauge(afem_mctdhf* S, int gauge);
 int mctdhf_step(afem_mctdhf* S, double2* phi, double2* C, double* W, const double* E, double dt, double cg_rtol,
                 int cg_max_it, afem_step_info* info, cudaStream_t s);
+// Two-electron integral columns X[pq][c] = sum_f m_f conj(phi_p) phi_q Wcol_c over
+// all support points on the tensor cores (TF32 hi/lo split, FP64 sums of
+// 32-point tiles), n = 1..8: partial [grid][n^2][n^2] complex sums per block
+// (integrals_tc.cu); *status (device, zeroed by the caller) becomes nonzero if
+// a block gave up waiting for its MMAs.
+int integrals_tc(const afem_mesh* m, const double2* phi, const double* W, int n, double2* partial, int grid,
+                 int* status, cudaStream_t s);
+int two_electron_integrals(afem_mesh* m, const double2* phi, int n, const double* W, double2* eri, int precision,
+                           cudaStream_t s);
 int convert_f64_f32(const double* x, float* y, int64_t n, cudaStream_t s);
 int convert_f32_f64(const float* x, double* y, int64_t n, cudaStream_t s);
 int tdse_forward(afem_mesh* m, const double* e_dir, const double* E, int K, double dt, int mk, double tol,

@@ -191,6 +191,7 @@ int afem_mesh_destroy(afem_mesh* mesh) {
     mesh->ws_poisson.release();
     mesh->ws_arnoldi.release();
     mesh->ws_tdse.release();
+    mesh->ws_int.release();
     delete mesh;
     return AFEM_OK;
 }
@@ -290,6 +291,17 @@ int afem_poisson_batch_ex(afem_mesh* m, const void* phi, int n_orb, void* W, dou
     if (outer_out) *outer_out = 0;
     return poisson_batch(m, static_cast<const double2*>(phi), n_orb, static_cast<double*>(W), rtol, max_it,
                          warm_start, iters_out, relres_out, static_cast<cudaStream_t>(stream));
+}
+
+int afem_two_electron_integrals(afem_mesh* m, const void* phi, int n_orb, const void* W, void* eri, int precision,
+                                void* stream) {
+    if (precision != AFEM_PREC_FP64 && precision != AFEM_PREC_MIXED)
+        return set_error(AFEM_EINVAL, "afem_two_electron_integrals: unknown precision");
+    if (!m || !phi || !W || !eri) return set_error(AFEM_EINVAL, "afem_two_electron_integrals: null argument");
+    if (m->host_only) return set_error(AFEM_EINVAL, "afem_two_electron_integrals: mesh was built host-only");
+    if (n_orb < 1 || n_orb > 8) return set_error(AFEM_EINVAL, "afem_two_electron_integrals: n_orb must be 1..8");
+    return two_electron_integrals(m, static_cast<const double2*>(phi), n_orb, static_cast<const double*>(W),
+                                  static_cast<double2*>(eri), precision, static_cast<cudaStream_t>(stream));
 }
 
 int afem_arnoldi_step(afem_mesh* m, const double* E, const void* phi, const void* U, int n_orb, int krylov_m,

@@ -611,6 +611,7 @@ struct StepWork {
     double2* Z;   // [3][n][n] phi_p^H F[x_d] phi_q
     double *energy, *shift, *dip;
     int* status;
+    int* tc_status;   // tensor-core integrals: nonzero if a block gave up waiting
     float2* U32;
     unsigned* counters;
 };
@@ -640,6 +641,7 @@ static void carve_step(Carver& cv, StepWork& w, int64_t N, int n, int64_t dim, b
     w.Z = cv.take<double2>(size_t(3) * nn);
     w.dip = cv.take<double>(3);
     w.status = cv.take<int>(1);
+    w.tc_status = cv.take<int>(1);
     w.U32 = mixed ? cv.take<float2>(size_t(N) * nn) : nullptr;
     w.counters = cv.take<unsigned>(4);
 }
@@ -659,6 +661,54 @@ __global__ void csum_blocks_kernel(const double2* __restrict__ partial, int nblk
 
 static void finalize_cpartials(const double2* partial, int nblk, int k, double2* out, cudaStream_t s) {
     AFEM_LAUNCH((csum_blocks_kernel), (k + 255) / 256, 256, 0, s, partial, nblk, k, out);
+}
+
+// eri[pq][rs] = (pq|rs) of orbitals phi with the pair mean fields W: the
+// contraction X[pq][c] over all support points (FP64 kernel, or the tensor
+// cores in the precision form), the fixed-order sum of the block partials and
+// the assembly of the complex W^r_s columns.  partial: [int_blocks()][n^4]
+// complex; tc_status: device int, zeroed by the caller.
+static int pair_integrals(const afem_mesh* m, const double2* phi, const double* W, int n, bool tensor_cores,
+                          double2* partial, double2* X, double2* eri, int* tc_status, cudaStream_t s) {
+    const DeviceMesh& D = m->dev;
+    const int nn = n * n;
+    const int iblk = int_blocks();
+    if (tensor_cores) {
+        const int rc = integrals_tc(m, phi, W, n, partial, iblk, tc_status, s);
+        if (rc) return rc;
+    } else {
+        IntArgs ia{phi, W, n, D.n_master, D.n_interior, D.n_hanging, D.mf_master, D.mf_hang, D.hang_ptr,
+                   D.hang_master, D.hang_w};
+        const size_t ismem =
+            size_t(kIntTile) * nn * (sizeof(double2) + sizeof(double)) + size_t(nn) * nn * sizeof(double2);
+        AFEM_CUDA_TRY(
+            cudaFuncSetAttribute(integrals_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ismem)));
+        AFEM_LAUNCH((integrals_kernel), iblk, 256, ismem, s, ia, partial);
+    }
+    finalize_cpartials(partial, iblk, nn * nn, X, s);
+    AFEM_LAUNCH((assemble_eri_kernel), (nn * nn + 255) / 256, 256, 0, s, n, X, eri);
+    AFEM_CUDA_TRY(cudaGetLastError());
+    return AFEM_OK;
+}
+
+int two_electron_integrals(afem_mesh* m, const double2* phi, int n, const double* W, double2* eri, int precision,
+                           cudaStream_t s) {
+    const int nn = n * n;
+    const size_t part_bytes = size_t(int_blocks()) * nn * nn * sizeof(double2);
+    const size_t x_bytes = size_t(nn) * nn * sizeof(double2);
+    int rc = m->ws_int.reserve(part_bytes + x_bytes + 256);
+    if (rc) return rc;
+    char* base = static_cast<char*>(m->ws_int.ptr);
+    double2* partial = reinterpret_cast<double2*>(base);
+    double2* X = reinterpret_cast<double2*>(base + part_bytes);
+    int* status = reinterpret_cast<int*>(base + part_bytes + x_bytes);
+    AFEM_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
+    if ((rc = pair_integrals(m, phi, W, n, precision == AFEM_PREC_MIXED, partial, X, eri, status, s))) return rc;
+    int st = 0;
+    AFEM_CUDA_TRY(cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AFEM_CUDA_TRY(cudaStreamSynchronize(s));
+    if (st) return set_error(AFEM_ECUDA, "afem_two_electron_integrals: tensor-core blocks gave up waiting for their MMAs");
+    return AFEM_OK;
 }
 
 static unsigned ci_grid(int64_t dim) { return grid_for(dim, 128, 8); }
@@ -712,13 +762,8 @@ int mctdhf_step(afem_mctdhf* S, double2* phi, double2* C, double* W, const doubl
         if ((rc = launch_op_apply(m, AFEM_OP_POS, e, phi, w.y, n, s))) return rc;
         if ((rc = cdot(phi, n, w.y, n, D.ml, D.n_interior, 0, w.cpart, w.Z + d * nn, w.counters, s))) return rc;
     }
-    IntArgs ia{phi, W, n, N, D.n_interior, D.n_hanging, D.mf_master, D.mf_hang, D.hang_ptr, D.hang_master, D.hang_w};
-    const size_t ismem = size_t(kIntTile) * nn * (sizeof(double2) + sizeof(double)) + size_t(nn) * nn * sizeof(double2);
-    AFEM_CUDA_TRY(cudaFuncSetAttribute(integrals_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ismem)));
-    const int iblk = int_blocks();
-    AFEM_LAUNCH((integrals_kernel), iblk, 256, ismem, s, ia, w.ipartial);
-    finalize_cpartials(w.ipartial, iblk, nn * nn, w.X, s);
-    AFEM_LAUNCH((assemble_eri_kernel), (nn * nn + 255) / 256, 256, 0, s, n, w.X, w.eri);
+    AFEM_CUDA_TRY(cudaMemsetAsync(w.tc_status, 0, sizeof(int), s));
+    if ((rc = pair_integrals(m, phi, W, n, mixed_form, w.ipartial, w.X, w.eri, w.tc_status, s))) return rc;
     // RDMs of C(t)
     AFEM_LAUNCH((ci_excite_kernel), ci_grid(dim), 128, 0, s, S->ci, C, w.D);
     AFEM_LAUNCH((ci_rdm_kernel), (nn + nn * nn + 127) / 128, 128, 0, s, n, dim, C, w.D, w.g1, w.g2);
@@ -729,9 +774,13 @@ int mctdhf_step(afem_mctdhf* S, double2* phi, double2* C, double* W, const doubl
     int status = 0;
     double energy = 0.0, dipole[3] = {0.0, 0.0, 0.0};
     AFEM_CUDA_TRY(cudaMemcpyAsync(&status, w.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    int tc_status = 0;
+    AFEM_CUDA_TRY(cudaMemcpyAsync(&tc_status, w.tc_status, sizeof(int), cudaMemcpyDeviceToHost, s));
     AFEM_CUDA_TRY(cudaMemcpyAsync(&energy, w.energy, sizeof(double), cudaMemcpyDeviceToHost, s));
     AFEM_CUDA_TRY(cudaMemcpyAsync(dipole, w.dip, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
     AFEM_CUDA_TRY(cudaStreamSynchronize(s));
+    if (tc_status)
+        return set_error(AFEM_ECUDA, "afem_mctdhf_step: tensor-core integrals gave up waiting for their MMAs");
     if (status) return set_error(AFEM_ESINGULAR, "afem_mctdhf_step: one-body density matrix is singular");
     // 3. C(t+dt) = exp(-i dt H_CI) C(t): Taylor series of (H - shift), times exp(-i dt shift)
     if ((rc = ci_sigma(S->ci, w, C, w.sigma, s))) return rc;
