@@ -597,6 +597,23 @@ def run_ours(args, rank, world, dist):
     if fp64 is not None:
         fp64_prof = _timed_form(pkg, torch, solver, fp64["state"], pkg.PREC_FP64, args, field, dt, dist, stream,
                                 profile=True, t0=fp64["t"], warmup=0)
+    # the same K steps with the G cell pass gathering its mean-field rows in the
+    # pass instead of staging frozen per-cell blocks by bulk copies
+    gcell_staging = None
+    if not args.no_rules:
+        pkg.mesh_set_option(mesh, pkg.OPT_GCELL_BLOCKS, 0)
+        try:
+            gathered = _timed_form(pkg, torch, solver, mixed["state"], pkg.PREC_MIXED, args, field, dt, dist,
+                                   stream, profile=True, t0=mixed["t"], warmup=0)
+        finally:
+            pkg.mesh_set_option(mesh, pkg.OPT_GCELL_BLOCKS, 1)
+
+        def _gcell(run):
+            ms_c, calls_c, _w = run["prof"][pkg.PROF_GCELL32]
+            return {"ms_per_step": run["ms"], "gcell_us_per_call": 1e3 * ms_c / max(calls_c, 1),
+                    "gcell_calls": calls_c}
+        gcell_staging = {"blocks_bulk_copy": _gcell(mixed_prof), "rows_gathered": _gcell(gathered),
+                         "note": "precision form, the K steps after the timed ones, kernel-class event timing on"}
 
     # accuracy of the precision form against the FP64 path after warmup + K steps
     ml = torch.from_numpy(ML).cuda()
@@ -737,6 +754,7 @@ def run_ours(args, rank, world, dist):
         "batching_form": batching,
         "differentiation_form": diff,
         "krylov_rules": rules,
+        "gcell_staging": gcell_staging,
         "poisson_solvers": psolv,
         # the oracle solves by Jacobi-PCG: its iteration count is the FP64
         # Jacobi count (the timed steps', or the Jacobi solve of poisson_solvers)

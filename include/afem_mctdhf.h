@@ -212,6 +212,15 @@ int afem_mesh_destroy(afem_mesh* mesh);
 #define AFEM_OPT_POISSON_SOLVER 2
 #define AFEM_POISSON_JACOBI 0
 #define AFEM_POISSON_MULTIGRID 1
+/* AFEM_OPT_GCELL_BLOCKS (degree-4 meshes, even orbital counts, precision
+ * form, length gauge, no complex scaling): 1 (default) forms, once per
+ * orbital propagation, the frozen pointwise part of G at every cell node,
+ * m_node (U_pq + delta_pq (V + E.x)), as one contiguous block per cell, which
+ * the float32 G cell pass stages into shared memory with one bulk copy
+ * (cp.async.bulk, the tensor memory accelerator) instead of gathering the
+ * mean-field rows node by node; 0 gathers them (and forms the potential term)
+ * inside the pass.  Same operator either way (float32 rounding aside). */
+#define AFEM_OPT_GCELL_BLOCKS 3
 int afem_mesh_set_option(afem_mesh* mesh, int option, int value);
 
 /* Exterior complex scaling of the kinetic energy (Sec. 4: an absorbing

@@ -357,6 +357,7 @@ def fma_peak(kind, target_ms=50.0, stream=None):
 
 OPT_CELL32_VARIANT = 1
 OPT_POISSON_SOLVER = 2
+OPT_GCELL_BLOCKS = 3
 POISSON_JACOBI = 0
 POISSON_MULTIGRID = 1
 

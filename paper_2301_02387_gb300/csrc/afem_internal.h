@@ -162,7 +162,9 @@ struct afem_mesh {
     afem::Workspace ws_arnoldi;
     afem::Workspace ws_tdse;
     afem::Workspace ws_int;   // afem_two_electron_integrals
+    afem::Workspace ws_gblocks;   // frozen per-cell blocks of the G cell pass
     int cell32_variant = 0;   // FP32 four-lane cell pass: 0 node-per-thread, 1 line-ordered
+    int gcell_blocks = 1;     // G cell pass on frozen per-cell blocks (AFEM_OPT_GCELL_BLOCKS)
     int poisson_solver = 0;   // AFEM_POISSON_JACOBI or AFEM_POISSON_MULTIGRID
     afem_pmg* pmg = nullptr;  // built on the first multigrid solve
     // exterior complex scaling of the kinetic energy (afem_mesh_set_ecs)
@@ -208,6 +210,14 @@ int mctdhf_step(afem_mctdhf* S, double2* phi, double2* C, double* W, const doubl
 int integrals_tc(const afem_mesh* m, const double2* phi, const double* W, int n, double2* partial, int grid,
                  int* status, cudaStream_t s);
 int two_electron_integrals(afem_mesh* m, const double2* phi, int n, const double* W, double2* eri, int precision,
+                           cudaStream_t s);
+// The G cell pass on frozen per-cell blocks (cell_f32.cu): applicability,
+// block storage, formation once per propagation, and the pass itself.
+bool gcell_blocks_apply(const afem_mesh* m, int n, int velocity);
+size_t gcell_blocks_bytes(const afem_mesh* m, int n);
+int build_gcell_blocks32(const afem_mesh* m, const double* E, const float2* U, const float2* U_hang, int n,
+                         float4* B, cudaStream_t s);
+int launch_g_cell32_blocks(const afem_mesh* m, const float2* v, const float4* B, float2* z, int n, double* err,
                            cudaStream_t s);
 int convert_f64_f32(const double* x, float* y, int64_t n, cudaStream_t s);
 int convert_f32_f64(const float* x, double* y, int64_t n, cudaStream_t s);

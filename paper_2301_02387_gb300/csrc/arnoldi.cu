@@ -906,7 +906,9 @@ static int g_cell_overlaps32(afem_mesh* m, const double* E, const float2* phi32,
     int rc;
     {   // algorithmic bytes: read v, U (n^2 fields), write z, complex64
         ProfScope ps(AFEM_PROF_GCELL32, s, double(D.n_master) * 8.0 * n * (2 + n));
-        if ((rc = launch_g_cell32(m, E, v32, U32, w.z32, n, s, velocity, w.uh32))) return rc;
+        rc = w.gb ? launch_g_cell32_blocks(m, v32, w.gb, w.z32, n, w.bulk_err, s)
+                  : launch_g_cell32(m, E, v32, U32, w.z32, n, s, velocity, w.uh32);
+        if (rc) return rc;
     }
     auto* part = reinterpret_cast<double*>(w.cpartial);
     switch (n) {
@@ -975,6 +977,8 @@ int arnoldi_reserve(afem_mesh* m, int n, int mk, ArnoldiWork& w) {
     w.beta2 = w.res + kResBeta2;
     w.col = w.res + kResCol;
     w.err = w.res + kResErr;
+    w.bulk_err = reinterpret_cast<double*>(w.res + kResFlag);
+    w.gb = nullptr;
     return AFEM_OK;
 }
 
@@ -1043,6 +1047,16 @@ int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double
         }
         AFEM_CUDA_TRY(cudaGetLastError());
     }
+    w.gb = nullptr;
+    if (mixed && U32 && gcell_blocks_apply(m, n, velocity)) {
+        // the frozen pointwise part of G, one contiguous block per cell, staged by
+        // the cell pass with one bulk copy (formed once for all substeps)
+        if ((rc = m->ws_gblocks.reserve(gcell_blocks_bytes(m, n)))) return rc;
+        auto* B = static_cast<float4*>(m->ws_gblocks.ptr);
+        if ((rc = build_gcell_blocks32(m, E, U32, w.uh32, n, B, s))) return rc;
+        w.gb = B;
+        AFEM_CUDA_TRY(cudaMemsetAsync(w.bulk_err, 0, sizeof(double), s));
+    }
     AFEM_CUDA_TRY(cudaMemsetAsync(w.counters, 0, 4 * sizeof(unsigned), s));
     AFEM_CUDA_TRY(cudaMemsetAsync(w.flag, 0, 4 * sizeof(int), s));
     AFEM_CUDA_TRY(cudaMemsetAsync(w.Sslots, 0, sizeof(double) * kOvSlots * 2 * kMaxOrbProj * kMaxOrbProj, s));
@@ -1059,6 +1073,8 @@ int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double
     auto fetch = [&]() -> int {
         AFEM_CUDA_TRY(cudaMemcpyAsync(res.data(), w.res, kResSize * sizeof(double2), cudaMemcpyDeviceToHost, s));
         AFEM_CUDA_TRY(cudaStreamSynchronize(s));
+        if (w.gb && res[kResFlag].x != 0.0)
+            return set_error(AFEM_ECUDA, "arnoldi: a G cell pass gave up waiting for a per-cell block copy");
         return AFEM_OK;
     };
     float2* v32 = mixed ? w.v32 : nullptr;
@@ -1079,7 +1095,9 @@ int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double
             // update cancelled most of w
             if (!projector) {   // the cell pass alone; S stays zero
                 if (mixed) {
-                    if ((rc = launch_g_cell32(m, E, w.v32, U32, w.z32, n, s, velocity, w.uh32))) return rc;
+                    rc = w.gb ? launch_g_cell32_blocks(m, w.v32, w.gb, w.z32, n, w.bulk_err, s)
+                              : launch_g_cell32(m, E, w.v32, U32, w.z32, n, s, velocity, w.uh32);
+                    if (rc) return rc;
                 } else {
                     if ((rc = launch_g_cell(m, E, w.V + j * NV, U, w.z, n, s, velocity, w.uh))) return rc;
                 }

@@ -18,7 +18,8 @@ constexpr int kResH = 0;
 constexpr int kResBeta2 = (kMaxKrylov + 1) * kMaxKrylov;
 constexpr int kResCol = kResBeta2 + 1;
 constexpr int kResErr = kResCol + kLadder * kMaxKrylov;
-constexpr int kResSize = kResErr + kLadder;
+constexpr int kResFlag = kResErr + kLadder;   // .x != 0: a G cell pass gave up waiting for a block copy
+constexpr int kResSize = kResFlag + 1;
 
 struct ArnoldiWork {
     double2* V;          // [m+1][N][n] Krylov basis
@@ -43,6 +44,8 @@ struct ArnoldiWork {
     const float2* uh32;
     unsigned* counters;  // last-block reduction counters (zeroed per call)
     int* flag;           // second-pass flag
+    const float4* gb;    // frozen per-cell blocks of the G cell pass for this call, else null
+    double* bulk_err;    // res[kResFlag].x
     int64_t stride;      // N * n
 };
 

@@ -192,6 +192,7 @@ int afem_mesh_destroy(afem_mesh* mesh) {
     mesh->ws_arnoldi.release();
     mesh->ws_tdse.release();
     mesh->ws_int.release();
+    mesh->ws_gblocks.release();
     delete mesh;
     return AFEM_OK;
 }
@@ -202,6 +203,11 @@ int afem_mesh_set_option(afem_mesh* m, int option, int value) {
         if (value < 0 || value > 2)
             return set_error(AFEM_EINVAL, "afem_mesh_set_option: variant must be 0, 1 or 2");
         m->cell32_variant = value;
+        return AFEM_OK;
+    }
+    if (option == AFEM_OPT_GCELL_BLOCKS) {
+        if (value != 0 && value != 1) return set_error(AFEM_EINVAL, "afem_mesh_set_option: G cell blocks must be 0 or 1");
+        m->gcell_blocks = value;
         return AFEM_OK;
     }
     if (option == AFEM_OPT_POISSON_SOLVER) {

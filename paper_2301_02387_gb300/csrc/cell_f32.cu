@@ -12,6 +12,7 @@
 
 #include "afem_internal.h"
 #include "cell_common.cuh"
+#include "mbarrier.cuh"
 #include "vec_common.cuh"
 
 namespace afem {
@@ -559,6 +560,152 @@ constexpr auto cell32v_pick() {
     else return cell32v_kernel<P, G, L4C, PAP>;
 }
 
+// ------------------------------------------------ frozen per-cell blocks
+// Within one orbital propagation (Sec. 3.2: phi, U and E frozen over the
+// step) the pointwise part of the G cell pass does not change between its
+// Krylov applications: at every cell node it is the n x n complex matrix
+//   B_pq = m_node (U_pq(node) + delta_pq (V(node) + E . x_node)),
+// m_node the node's quadrature weight h^3 w_a w_b w_c.  It is formed once per
+// propagation, cell by cell in node order ([ncell][(p+1)^3][SU] float4, each
+// node's n^2 complex entries row by row as float4 pairs, SU = (n^2/2) | 1
+// quads per node: the odd stride keeps the rows that a quarter warp reads on
+// distinct banks), so each cell's block is one contiguous, 16-byte aligned
+// run that the cell pass stages into shared memory with a single bulk copy of
+// the tensor memory accelerator (cp.async.bulk) instead of one gather per
+// node row; hanging nodes take the mean fields interpolated through C.
+__host__ __device__ constexpr int gblock_quads(int n) { return ((n * n) / 2) | 1; }
+
+// One float4 of B per thread: (cell, node, quad k); row p = k / (n/2), columns
+// 2 (k % (n/2)) and + 1; the padding quad is zero.
+__global__ void gcell_blocks32_kernel(const CellArgs32 a, const float2* __restrict__ U,
+                                      const float2* __restrict__ U_hang, int n, int P1, float4* __restrict__ B) {
+    const int NN = P1 * P1 * P1;
+    const int SU = gblock_quads(n), half = n / 2, nn = n * n;
+    const int64_t total = a.ncell * NN * SU;
+    for (int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; o < total;
+         o += int64_t(gridDim.x) * blockDim.x) {
+        const int k = int(o % SU);
+        const int64_t cj = o / SU;                 // cell * NN + node
+        const int64_t cell = cj / NN;
+        const int j = int(cj - cell * NN);
+        float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (k < nn / 2) {
+            const int p = k / half, q0 = 2 * (k - p * half);
+            const int ia = j % P1, ib = (j / P1) % P1, ic = j / (P1 * P1);
+            const float4 g = a.geom[cell];
+            const float px = g.x + g.w * a.xi[ia], py = g.y + g.w * a.xi[ib], pz = g.z + g.w * a.xi[ic];
+            const float wq = g.w * g.w * g.w * a.w[ia] * a.w[ib] * a.w[ic];
+            const float pot = a.v_cell[cj] + a.E[0] * px + a.E[1] * py + a.E[2] * pz;
+            const int idx = a.cell_node[cj];
+            const float2* row = idx >= 0 ? U + int64_t(idx) * nn : U_hang + int64_t(-idx - 1) * nn;
+            float2 u0 = row[p * n + q0], u1 = row[p * n + q0 + 1];
+            if (q0 == p) u0.x += pot;
+            if (q0 + 1 == p) u1.x += pot;
+            out = make_float4(wq * u0.x, wq * u0.y, wq * u1.x, wq * u1.y);
+        }
+        B[o] = out;
+    }
+}
+
+constexpr int kBulkMaxPolls = 1 << 20;   // polls of a cell's block copy before the pass gives up
+
+// The degree-4 G cell pass on staged per-cell blocks: one cell per block of
+// 256 threads, L4C = n/2 complex orbital pairs per node (n = 2, 4, 6, 8).
+// Thread 0 starts the bulk copy of the cell's block first; the gathers of the
+// Krylov vector (asynchronous 16-byte copies for masters, the constraint walk
+// for hanging points) overlap it.  The kinetic term is the node-per-thread
+// sum factorisation of cell32v_body; the pointwise part is sum_q B_pq v_q.
+// A copy that does not complete within the poll limit sets *err (a value the
+// host reads with every substep's results) and the cell is skipped.
+template <int L4C>
+__global__ void __launch_bounds__(256, 8) gcell32b_kernel(const __grid_constant__ CellArgs32 a,
+                                                          const float4* __restrict__ x,
+                                                          const float4* __restrict__ B, float4* __restrict__ y,
+                                                          double* __restrict__ err) {
+    constexpr int P1 = 5, NN = 125, L4 = L4C, n = 2 * L4C;
+    constexpr int SU = gblock_quads(n);
+    constexpr uint32_t kBytes = uint32_t(NN * SU * 16);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float4* s_B = reinterpret_cast<float4*>(smem_raw);   // [NN][SU]
+    float4* s_u = s_B + NN * SU;                         // [NN][L4]
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_idx[NN];
+    __shared__ float4 s_g;
+    __shared__ float s_K[P1 * P1];
+    __shared__ float s_w[P1];
+    const int64_t cell = blockIdx.x;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        tc::mbar_init(&bar, 1);
+        tc::mbar_fence_init();
+        tc::mbar_arrive_expect_tx(&bar, kBytes);
+        tc::bulk_copy_g2s(s_B, B + cell * (NN * SU), kBytes, &bar);
+        s_g = a.geom[cell];
+    }
+    for (int i = tid; i < NN; i += 256) s_idx[i] = a.cell_node[cell * NN + i];
+    if (tid < P1 * P1) s_K[tid] = a.K[tid];
+    if (tid < P1) s_w[tid] = a.w[tid];
+    __syncthreads();
+    for (int it = tid; it < NN * L4; it += 256) {
+        const int j = it / L4, q = it - j * L4;
+        const int idx = s_idx[j];
+        if (idx >= 0 && !(a.masked && idx >= a.n_interior)) cp_async16(s_u + it, x + int64_t(idx) * L4 + q);
+        else s_u[it] = gather32v(a, idx, x, L4, q);
+    }
+    cp_async_wait_all();
+    const bool got = tc::mbar_wait(&bar, 0u, kBulkMaxPolls);
+    if (__syncthreads_or(!got)) {
+        // the copy may still be in flight: wait once more (bounded) before the
+        // block's shared memory is released
+        if (tid == 0) {
+            *err = 1.0;
+            tc::mbar_wait(&bar, 0u, kBulkMaxPolls);
+        }
+        __syncthreads();
+        return;
+    }
+    const float ck = 0.5f * s_g.w;
+    for (int it = tid; it < NN * L4; it += 256) {
+        const int j = it / L4, q = it - j * L4;
+        const int ia = j % P1, ib = (j / P1) % P1, ic = j / (P1 * P1);
+        const float4* u0 = s_u + q;
+        float4 ax = make_float4(0.f, 0.f, 0.f, 0.f), ay = ax, az = ax;
+#pragma unroll
+        for (int m = 0; m < P1; ++m) {
+            f4fma(ax, s_K[ia * P1 + m], u0[(m + P1 * (ib + P1 * ic)) * L4]);
+            f4fma(ay, s_K[ib * P1 + m], u0[(ia + P1 * (m + P1 * ic)) * L4]);
+            f4fma(az, s_K[ic * P1 + m], u0[(ia + P1 * (ib + P1 * m)) * L4]);
+        }
+        float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+        f4fma(r, ck * s_w[ib] * s_w[ic], ax);
+        f4fma(r, ck * s_w[ia] * s_w[ic], ay);
+        f4fma(r, ck * s_w[ia] * s_w[ib], az);
+        // rows p0 = 2q (lanes x, y) and p1 = 2q + 1 (lanes z, w) of the node's
+        // block against its orbitals, read as 16-byte quads
+        const float4* Br = s_B + j * SU + q * n;
+        float2 m0 = make_float2(0.f, 0.f), m1 = m0;
+#pragma unroll
+        for (int c = 0; c < L4C; ++c) {
+            const float4 u = s_u[j * L4 + c];
+            const float4 a0 = Br[c];
+            const float4 a1 = Br[L4C + c];
+            m0.x = fmaf(a0.x, u.x, fmaf(-a0.y, u.y, m0.x));
+            m0.y = fmaf(a0.x, u.y, fmaf(a0.y, u.x, m0.y));
+            m0.x = fmaf(a0.z, u.z, fmaf(-a0.w, u.w, m0.x));
+            m0.y = fmaf(a0.z, u.w, fmaf(a0.w, u.z, m0.y));
+            m1.x = fmaf(a1.x, u.x, fmaf(-a1.y, u.y, m1.x));
+            m1.y = fmaf(a1.x, u.y, fmaf(a1.y, u.x, m1.y));
+            m1.x = fmaf(a1.z, u.z, fmaf(-a1.w, u.w, m1.x));
+            m1.y = fmaf(a1.z, u.w, fmaf(a1.w, u.z, m1.y));
+        }
+        r.x += m0.x;
+        r.y += m0.y;
+        r.z += m1.x;
+        r.w += m1.y;
+        scatter32v(a, s_idx[j], y, L4, q, r);
+    }
+}
+
 // Line-ordered form of the four-lane pass: the three 1D contractions run as
 // whole lines (each thread loads the P1 values of one line once and writes P1
 // outputs), accumulated direction by direction in shared memory, which cuts
@@ -1050,6 +1197,66 @@ int launch_g_cell32(const afem_mesh* m, const double* E, const float2* v, const 
     if (n % 2 == 0 && aligned16(v) && aligned16(z))
         return launch32v<true>(m, a, reinterpret_cast<const float*>(v), U, reinterpret_cast<float*>(z), 2 * n, n, s);
     return launch32<float2, true>(m, a, v, U, z, n, s);
+}
+
+// Whether the G cell pass of this mesh and orbital count runs on frozen
+// per-cell blocks (degree 4, n even, length gauge, no complex scaling, the
+// option on).
+bool gcell_blocks_apply(const afem_mesh* m, int n, int velocity) {
+    return m->gcell_blocks && m->dev.p == 4 && n % 2 == 0 && n <= 8 && !velocity && !m->ecs_on;
+}
+
+size_t gcell_blocks_bytes(const afem_mesh* m, int n) {
+    return size_t(m->dev.ncell) * 125 * gblock_quads(n) * sizeof(float4);
+}
+
+// B of every cell (see gcell_blocks32_kernel) from the complex64 mean fields at
+// the masters (U) and at the hanging points (U_hang), field E.
+int build_gcell_blocks32(const afem_mesh* m, const double* E, const float2* U, const float2* U_hang, int n,
+                         float4* B, cudaStream_t s) {
+    if (m->dev.n_hanging > 0 && !U_hang) return set_error(AFEM_EINVAL, "G cell blocks: hanging mean fields missing");
+    CellArgs32 a = make_cell_args32(m);
+    for (int i = 0; i < 3; ++i) a.E[i] = E ? float(E[i]) : 0.0f;
+    const int64_t total = m->dev.ncell * 125 * gblock_quads(n);
+    AFEM_LAUNCH((gcell_blocks32_kernel), grid_for(total), 256, 0, s, a, U, U_hang, n, m->dev.p + 1, B);
+    AFEM_CUDA_TRY(cudaGetLastError());
+    return AFEM_OK;
+}
+
+// z = H1~ v + mean field (complex64, Dirichlet-masked) on the frozen blocks B;
+// err: a double that becomes 1 if a block copy did not complete.
+int launch_g_cell32_blocks(const afem_mesh* m, const float2* v, const float4* B, float2* z, int n, double* err,
+                           cudaStream_t s) {
+    if (!aligned16(v) || !aligned16(z) || !aligned16(B))
+        return set_error(AFEM_EINVAL, "G cell blocks: vectors must be 16-byte aligned");
+    CellArgs32 a = make_cell_args32(m);
+    a.masked = 1;
+    const int64_t N = m->dev.n_master;
+    AFEM_CUDA_TRY(cudaMemsetAsync(z, 0, size_t(N) * n * sizeof(float2), s));
+    if (m->dev.ncell == 0) return AFEM_OK;
+    const unsigned grid = unsigned(m->dev.ncell);
+    const float4* x4 = reinterpret_cast<const float4*>(v);
+    float4* y4 = reinterpret_cast<float4*>(z);
+    switch (n) {
+#define AFEM_GB_CASE(NO)                                                                                      \
+    case NO: {                                                                                                \
+        const size_t smem = size_t(125) * (gblock_quads(NO) + NO / 2) * sizeof(float4);                       \
+        if (smem > 48 * 1024)                                                                                 \
+            AFEM_CUDA_TRY(cudaFuncSetAttribute(gcell32b_kernel<NO / 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                               int(smem)));                                                   \
+        AFEM_LAUNCH((gcell32b_kernel<NO / 2>), grid, 256, smem, s, a, x4, B, y4, err);                        \
+        break;                                                                                                \
+    }
+        AFEM_GB_CASE(2)
+        AFEM_GB_CASE(4)
+        AFEM_GB_CASE(6)
+        AFEM_GB_CASE(8)
+#undef AFEM_GB_CASE
+        default:
+            return set_error(AFEM_EINVAL, "G cell blocks: n must be 2, 4, 6 or 8");
+    }
+    AFEM_CUDA_TRY(cudaGetLastError());
+    return AFEM_OK;
 }
 
 // ---------------------------------------------------------------- batching

@@ -19,12 +19,10 @@
 #pragma once
 #include <cstdint>
 
+#include "mbarrier.cuh"
+
 namespace afem {
 namespace tc {
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
 
 // Shared-memory matrix descriptor: start address, leading-dimension byte
 // offset, stride byte offset (each in 16-byte units), the fixed field value 1
@@ -73,25 +71,6 @@ __device__ __forceinline__ void commit(uint64_t* bar) {
                  : "memory");
 }
 
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-// Bounded wait for the completion of the mbarrier phase with the given
-// parity; false when max_polls polls did not see it.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int max_polls) {
-    uint32_t done = 0;
-    for (int i = 0; i < max_polls && !done; ++i) {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(smem_u32(bar)), "r"(parity)
-            : "memory");
-    }
-    return done != 0;
-}
-
 __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 // Generic-proxy writes to shared memory made visible to the tensor cores.
@@ -116,14 +95,6 @@ __device__ __forceinline__ void ld_x16(uint32_t taddr, float (&v)[16]) {
 // part is exact there.  Finite inputs below 2^127 in magnitude.
 __device__ __forceinline__ float tf32_round(float x) {
     return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
-}
-
-// x = hi + lo + O(2^-22 |x|) with hi and lo both exact in TF32: the operand
-// split of the three-product FP32-accurate tensor-core contraction
-// (A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi).
-__device__ __forceinline__ void tf32_split(double x, float& hi, float& lo) {
-    hi = tf32_round(__double2float_rn(x));
-    lo = tf32_round(__double2float_rn(x - static_cast<double>(hi)));
 }
 
 // Byte offset of element (row, k) in an operand tile with KT columns laid out

@@ -100,16 +100,20 @@ CASES_N = [
 
 
 @pytest.mark.parametrize("case", CASES_N)
-@pytest.mark.parametrize("n", [1, 3, 4, 6, 8])
-def test_arnoldi_orbital_counts_with_mean_field(case, n):
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 6, 8])
+@pytest.mark.parametrize("blocks", [1, 0])
+def test_arnoldi_orbital_counts_with_mean_field(case, n, blocks):
     """The G cell pass with all n^2 mean fields for odd orbital counts (the
-    scalar-lane kernel) and 2, 3 and 4 float4 quads per node (n = 4, 6, 8; 8
-    orbitals and 64 fields as in the water workload), degrees 3 and 4: one
+    scalar-lane kernel) and 1 to 4 float4 quads per node (n = 2, 4, 6, 8; 8
+    orbitals and 64 fields as in the water workload), degrees 3 and 4, with
+    the degree-4 precision form on frozen per-cell blocks staged by bulk copies
+    (blocks = 1) and with the mean-field rows gathered in the pass (0): one
     Krylov step of dimension 8, FP64 within 1e-10 of the oracle, the precision
     form within 1e-6."""
     import torch
     import paper_2301_02387_gb300 as pkg
     gm = pkg.Mesh(*case)
+    pkg.mesh_set_option(gm, pkg.OPT_GCELL_BLOCKS, blocks)
     om = omesh.Mesh(*case)
     op = fem.Operators(om)
     X, _, _ = gm.tables()
