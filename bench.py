@@ -250,6 +250,8 @@ def run_water(torch, pkg, inputs, args):
     t0 = time.perf_counter()
     mesh = pkg.Mesh(*inputs.mesh_args(name))
     build_s = time.perf_counter() - t0
+    if args.poisson == "multigrid":
+        pkg.mesh_set_option(mesh, pkg.OPT_POISSON_SOLVER, pkg.POISSON_MULTIGRID)
     X, ML, _ = mesh.tables()
     interior = np.arange(mesh.N) < mesh.n_interior
     n = w["n_orb"]
@@ -297,7 +299,8 @@ def run_water(torch, pkg, inputs, args):
                         "energy_last": inf[-1]["energy"]}
     return {"workload": "water-shaped O + 2 H (1.81 bohr, 104.5 deg), [-50,50]^3, 32^3 coarse, 6 levels at O and "
                         "5 at each H, Q4; 8 orbitals, 5a+5b (3136 determinants), 64 Poisson columns; 800 nm 4-cycle "
-                        "sin^2 2e14 W/cm^2, dt=0.01, m=10, Krylov threshold 1e-10 per substep",
+                        "sin^2 2e14 W/cm^2, dt=0.01, m=10, Krylov threshold 1e-10 per substep, Poisson CG with the "
+                        + ("multigrid" if args.poisson == "multigrid" else "Jacobi") + " preconditioner",
             "n_masters": mesh.N, "n_cells": mesh.n_cells, "n_hanging": mesh.n_hanging, "mesh_build_s": build_s,
             "warmup": args.warmup, "steps": args.steps, "fp64_path": entry["fp64"], "precision_form": entry["mixed"],
             "speedup_vs_fp64_path": res["fp64"]["ms"] / res["mixed"]["ms"],
@@ -601,19 +604,21 @@ def run_ours(args, rank, world, dist):
     # pass instead of staging frozen per-cell blocks by bulk copies
     gcell_staging = None
     if not args.no_rules:
-        pkg.mesh_set_option(mesh, pkg.OPT_GCELL_BLOCKS, 0)
-        try:
-            gathered = _timed_form(pkg, torch, solver, mixed["state"], pkg.PREC_MIXED, args, field, dt, dist,
-                                   stream, profile=True, t0=mixed["t"], warmup=0)
-        finally:
-            pkg.mesh_set_option(mesh, pkg.OPT_GCELL_BLOCKS, 1)
-
         def _gcell(run):
             ms_c, calls_c, _w = run["prof"][pkg.PROF_GCELL32]
             return {"ms_per_step": run["ms"], "gcell_us_per_call": 1e3 * ms_c / max(calls_c, 1),
                     "gcell_calls": calls_c}
-        gcell_staging = {"blocks_bulk_copy": _gcell(mixed_prof), "rows_gathered": _gcell(gathered),
-                         "note": "precision form, the K steps after the timed ones, kernel-class event timing on"}
+        gcell_staging = {"blocks_bulk_copy": _gcell(mixed_prof),
+                         "note": "precision form, the K steps after the timed ones, kernel-class event timing on; "
+                                 "pipelined includes forming v at the hanging points"}
+        for label, mode in (("rows_gathered", 0), ("blocks_pipelined", 2)):
+            pkg.mesh_set_option(mesh, pkg.OPT_GCELL_BLOCKS, mode)
+            try:
+                run = _timed_form(pkg, torch, solver, mixed["state"], pkg.PREC_MIXED, args, field, dt, dist,
+                                  stream, profile=True, t0=mixed["t"], warmup=0)
+            finally:
+                pkg.mesh_set_option(mesh, pkg.OPT_GCELL_BLOCKS, 1)
+            gcell_staging[label] = _gcell(run)
 
     # accuracy of the precision form against the FP64 path after warmup + K steps
     ml = torch.from_numpy(ML).cuda()
@@ -668,6 +673,7 @@ def run_ours(args, rank, world, dist):
     t = mixed["t"]
 
     kern = measure_kernels(pkg, torch, mesh, W, phi, field(t), stream)
+    integrals = measure_integrals(pkg, torch, mesh, phi, W, stream)
     psolv = None if args.no_poisson_solvers else run_poisson_solvers(
         torch, pkg, mesh, phi, W, pkg.POISSON_MULTIGRID if args.poisson == "multigrid" else pkg.POISSON_JACOBI)
     rules = None
@@ -755,6 +761,7 @@ def run_ours(args, rank, world, dist):
         "differentiation_form": diff,
         "krylov_rules": rules,
         "gcell_staging": gcell_staging,
+        "tensor_core_integrals": integrals,
         "poisson_solvers": psolv,
         # the oracle solves by Jacobi-PCG: its iteration count is the FP64
         # Jacobi count (the timed steps', or the Jacobi solve of poisson_solvers)
@@ -1022,6 +1029,60 @@ def run_profile_gs(nc=16, dt=1e-4):
     print(json.dumps({"profile_gs": {"N": mesh.N, "n_orb": n, "substeps": sub, "err": err}}))
 
 
+def measure_integrals(pkg, torch, mesh, phi, W, stream, reps=5):
+    """The two-electron integrals (pq|rs) of the live orbitals and mean fields:
+    the FP64 contraction against the tensor-core one (tcgen05 MMAs, TF32 hi/lo
+    operands, FP64 sums of 32-point tiles), CUDA events on the launching stream
+    around `reps` calls each (after one untimed call), and the largest entry
+    difference relative to the largest FP64 entry."""
+    n = int(phi.shape[1])
+    nn = n * n
+    out = {}
+    res = {}
+    for name, prec in (("fp64", pkg.PREC_FP64), ("tensor_cores", pkg.PREC_MIXED)):
+        eri = torch.empty((nn, nn), dtype=torch.complex128, device="cuda")
+        pkg.two_electron_integrals(mesh, phi, W, eri, precision=prec)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            pkg.two_electron_integrals(mesh, phi, W, eri, precision=prec)
+        b.record(stream)
+        torch.cuda.synchronize()
+        out[name] = {"ms_per_call": a.elapsed_time(b) / reps}
+        res[name] = eri
+    npts = mesh.n_hanging + mesh.N
+    # algorithmic work: 2 (n^2 complex = 2 n^2 real rows) x n^2 columns x support points
+    flops = 2.0 * (2 * nn) * nn * npts
+    for name in out:
+        out[name]["tflops"] = flops / (out[name]["ms_per_call"] * 1e-3) / 1e12
+    ref = res["fp64"]
+    out["max_rel_diff"] = float((res["tensor_cores"] - ref).abs().max().item() / ref.abs().max().item())
+    out["support_points"] = int(npts)
+    out["n_orb"] = n
+    return out
+
+
+def run_profile_integrals(reps=5):
+    """The workload's integrals alone (seeded orbitals, their Poisson mean
+    fields): one untimed and `reps` timed calls of each form; small enough for a
+    profiler capture of the tensor-core kernel."""
+    import torch
+    import paper_2301_02387_gb300 as pkg
+    from paper_2301_02387_gb300 import inputs
+    torch.cuda.set_device(0)
+    w = inputs.WORKLOADS[WORKLOAD]
+    mesh, solver, phi0, C0 = setup_state(pkg, inputs, torch, w)
+    n = w["n_orb"]
+    phi = torch.from_numpy(phi0).cuda()
+    W = torch.zeros((mesh.N, n * n), dtype=torch.float64, device="cuda")
+    pkg.mesh_set_option(mesh, pkg.OPT_POISSON_SOLVER, pkg.POISSON_MULTIGRID)
+    pkg.poisson_batch(mesh, phi, W, rtol=1e-10, max_it=20000)
+    torch.cuda.synchronize()
+    out = measure_integrals(pkg, torch, mesh, phi, W, torch.cuda.current_stream(), reps=reps)
+    print(json.dumps({"profile_integrals": out, "N": mesh.N}))
+
+
 def run_profile_arnoldi(dt_short=2e-4, dt_timed=2e-3, timed=True):
     """The orbital propagator alone on the workload mesh (mean fields frozen to
     a smooth synthetic field): one short error-controlled propagation (a few
@@ -1094,6 +1155,8 @@ def main():
                     help="build the workload and run each operator kernel a few times (for profilers); no JSON")
     ap.add_argument("--profile-step", action="store_true",
                     help="one precision-form step with the inner CG capped (for a profiler's launch list); no JSON")
+    ap.add_argument("--profile-integrals", action="store_true",
+                    help="time the two-electron integrals (FP64 and tensor cores) on the workload mesh")
     ap.add_argument("--profile-gs", action="store_true",
                     help="a short precision-form propagation on a reduced coarse grid (the Gram-Schmidt kernels' "
                          "small capture case); one JSON line")
@@ -1148,6 +1211,9 @@ def main():
         return
     if args.profile_arnoldi:
         run_profile_arnoldi(timed=args.steps > 0)
+        return
+    if args.profile_integrals:
+        run_profile_integrals()
         return
     if args.profile_gs:
         run_profile_gs()

@@ -219,7 +219,10 @@ int afem_mesh_destroy(afem_mesh* mesh);
  * the float32 G cell pass stages into shared memory with one bulk copy
  * (cp.async.bulk, the tensor memory accelerator) instead of gathering the
  * mean-field rows node by node; 0 gathers them (and forms the potential term)
- * inside the pass.  Same operator either way (float32 rounding aside). */
+ * inside the pass; 2 (n <= 4) runs the blocks in a persistent, double-buffered
+ * loop over cells (the next cell's copies in flight while a cell is computed,
+ * v at the hanging points formed first), measured slower than 1 on GB300.
+ * Same operator in every form (float32 rounding aside). */
 #define AFEM_OPT_GCELL_BLOCKS 3
 int afem_mesh_set_option(afem_mesh* mesh, int option, int value);
 

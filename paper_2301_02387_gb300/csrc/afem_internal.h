@@ -164,7 +164,7 @@ struct afem_mesh {
     afem::Workspace ws_int;   // afem_two_electron_integrals
     afem::Workspace ws_gblocks;   // frozen per-cell blocks of the G cell pass
     int cell32_variant = 0;   // FP32 four-lane cell pass: 0 node-per-thread, 1 line-ordered
-    int gcell_blocks = 1;     // G cell pass on frozen per-cell blocks (AFEM_OPT_GCELL_BLOCKS)
+    int gcell_blocks = 1;     // G cell pass on frozen per-cell blocks: 0 off, 1 one cell per block, 2 pipelined (n <= 4)
     int poisson_solver = 0;   // AFEM_POISSON_JACOBI or AFEM_POISSON_MULTIGRID
     afem_pmg* pmg = nullptr;  // built on the first multigrid solve
     // exterior complex scaling of the kinetic energy (afem_mesh_set_ecs)
@@ -218,7 +218,7 @@ size_t gcell_blocks_bytes(const afem_mesh* m, int n);
 int build_gcell_blocks32(const afem_mesh* m, const double* E, const float2* U, const float2* U_hang, int n,
                          float4* B, cudaStream_t s);
 int launch_g_cell32_blocks(const afem_mesh* m, const float2* v, const float4* B, float2* z, int n, double* err,
-                           cudaStream_t s);
+                           float4* vh, cudaStream_t s);
 int convert_f64_f32(const double* x, float* y, int64_t n, cudaStream_t s);
 int convert_f32_f64(const float* x, double* y, int64_t n, cudaStream_t s);
 int tdse_forward(afem_mesh* m, const double* e_dir, const double* E, int K, double dt, int mk, double tol,

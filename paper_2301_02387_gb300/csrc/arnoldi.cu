@@ -906,7 +906,7 @@ static int g_cell_overlaps32(afem_mesh* m, const double* E, const float2* phi32,
     int rc;
     {   // algorithmic bytes: read v, U (n^2 fields), write z, complex64
         ProfScope ps(AFEM_PROF_GCELL32, s, double(D.n_master) * 8.0 * n * (2 + n));
-        rc = w.gb ? launch_g_cell32_blocks(m, v32, w.gb, w.z32, n, w.bulk_err, s)
+        rc = w.gb ? launch_g_cell32_blocks(m, v32, w.gb, w.z32, n, w.bulk_err, w.vh32, s)
                   : launch_g_cell32(m, E, v32, U32, w.z32, n, s, velocity, w.uh32);
         if (rc) return rc;
     }
@@ -963,6 +963,7 @@ int arnoldi_reserve(afem_mesh* m, int n, int mk, ArnoldiWork& w) {
         w.U32 = cv.take<float2>(NV * n);
         w.Uh = cv.take<double2>(size_t(m->dev.n_hanging) * n * n);
         w.Uh32 = cv.take<float2>(size_t(m->dev.n_hanging) * n * n);
+        w.vh32 = reinterpret_cast<float4*>(cv.take<float2>(size_t(m->dev.n_hanging) * n + 2));
         w.counters = cv.take<unsigned>(4);
         w.flag = cv.take<int>(4);
     };
@@ -1095,7 +1096,7 @@ int arnoldi_step(afem_mesh* m, const double* E, const double2* phi, const double
             // update cancelled most of w
             if (!projector) {   // the cell pass alone; S stays zero
                 if (mixed) {
-                    rc = w.gb ? launch_g_cell32_blocks(m, w.v32, w.gb, w.z32, n, w.bulk_err, s)
+                    rc = w.gb ? launch_g_cell32_blocks(m, w.v32, w.gb, w.z32, n, w.bulk_err, w.vh32, s)
                               : launch_g_cell32(m, E, w.v32, U32, w.z32, n, s, velocity, w.uh32);
                     if (rc) return rc;
                 } else {

@@ -45,6 +45,7 @@ struct ArnoldiWork {
     unsigned* counters;  // last-block reduction counters (zeroed per call)
     int* flag;           // second-pass flag
     const float4* gb;    // frozen per-cell blocks of the G cell pass for this call, else null
+    float4* vh32;        // [nh][n/2] C v at the hanging points (pipelined G cell pass)
     double* bulk_err;    // res[kResFlag].x
     int64_t stride;      // N * n
 };

@@ -206,7 +206,8 @@ int afem_mesh_set_option(afem_mesh* m, int option, int value) {
         return AFEM_OK;
     }
     if (option == AFEM_OPT_GCELL_BLOCKS) {
-        if (value != 0 && value != 1) return set_error(AFEM_EINVAL, "afem_mesh_set_option: G cell blocks must be 0 or 1");
+        if (value < 0 || value > 2)
+            return set_error(AFEM_EINVAL, "afem_mesh_set_option: G cell blocks must be 0, 1 or 2");
         m->gcell_blocks = value;
         return AFEM_OK;
     }

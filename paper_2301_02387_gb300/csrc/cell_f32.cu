@@ -706,6 +706,138 @@ __global__ void __launch_bounds__(256, 8) gcell32b_kernel(const __grid_constant_
     }
 }
 
+// Complex64 quads of v at the hanging points, C v (interior masters only: the
+// G pass is Dirichlet-masked), [nh][L4]; formed once per application so that
+// the pipelined pass below gathers every node row by an asynchronous copy.
+__global__ void hang_expand32v_kernel(const int32_t* __restrict__ hp, const int32_t* __restrict__ hm,
+                                      const float* __restrict__ hw, int64_t nh, int64_t n_interior,
+                                      const float4* __restrict__ x, int L4, float4* __restrict__ xh) {
+    for (int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; o < nh * L4;
+         o += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t h = o / L4;
+        const int q = int(o - h * L4);
+        float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int e = hp[h]; e < hp[h + 1]; ++e) {
+            const int m = hm[e];
+            if (m < n_interior) f4fma(val, hw[e], x[int64_t(m) * L4 + q]);
+        }
+        xh[o] = val;
+    }
+}
+
+// Pipelined form of gcell32b_kernel (n = 2 or 4): a block walks the cells
+// blockIdx.x, + gridDim.x, ... with two shared-memory buffers; while it
+// computes one cell, the next cell's block (one bulk copy) and node rows
+// (16-byte asynchronous copies of v, or of C v at hanging nodes; zeros at
+// surface masters) are already in flight into the other buffer.  One block
+// barrier per cell.
+template <int L4C>
+__global__ void __launch_bounds__(256, 4) gcell32p_kernel(const __grid_constant__ CellArgs32 a,
+                                                          const float4* __restrict__ x,
+                                                          const float4* __restrict__ xh,
+                                                          const float4* __restrict__ B, float4* __restrict__ y,
+                                                          double* __restrict__ err) {
+    constexpr int P1 = 5, NN = 125, L4 = L4C, n = 2 * L4C;
+    constexpr int SU = gblock_quads(n);
+    constexpr uint32_t kBytes = uint32_t(NN * SU * 16);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float4* s_B = reinterpret_cast<float4*>(smem_raw);   // [2][NN][SU]
+    float4* s_u = s_B + 2 * NN * SU;                     // [2][NN][L4]
+    int* s_idx = reinterpret_cast<int*>(s_u + 2 * NN * L4);   // [2][NN]
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ float4 s_g[2];
+    __shared__ float s_K[P1 * P1];
+    __shared__ float s_w[P1];
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        tc::mbar_init(&bar[0], 1);
+        tc::mbar_init(&bar[1], 1);
+        tc::mbar_fence_init();
+    }
+    if (tid < P1 * P1) s_K[tid] = a.K[tid];
+    if (tid < P1) s_w[tid] = a.w[tid];
+    __syncthreads();
+    auto stage = [&](int64_t c, int b) {
+        if (tid == 0) {
+            tc::mbar_arrive_expect_tx(&bar[b], kBytes);
+            tc::bulk_copy_g2s(s_B + b * NN * SU, B + c * (NN * SU), kBytes, &bar[b]);
+            s_g[b] = a.geom[c];
+        }
+        for (int it = tid; it < NN * L4; it += 256) {
+            const int j = it / L4, q = it - j * L4;
+            const int idx = a.cell_node[c * NN + j];
+            if (q == 0) s_idx[b * NN + j] = idx;
+            float4* dst = s_u + b * NN * L4 + it;
+            if (idx < 0) cp_async16(dst, xh + int64_t(-idx - 1) * L4 + q);
+            else if (idx < a.n_interior) cp_async16(dst, x + int64_t(idx) * L4 + q);
+            else *dst = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    int64_t cell = blockIdx.x;
+    if (cell < a.ncell) stage(cell, 0);
+    uint32_t parity = 0u;   // bit b: phase parity of buffer b's barrier
+    int b = 0;
+    for (; cell < a.ncell; cell += gridDim.x, b ^= 1) {
+        cp_async_wait_all();
+        const uint32_t ph = (parity >> b) & 1u;
+        const bool got = tc::mbar_wait(&bar[b], ph, kBulkMaxPolls);
+        parity ^= 1u << b;
+        if (__syncthreads_or(!got)) {
+            // the block copy may still be in flight: wait once more (bounded)
+            // before the block's shared memory is released
+            if (tid == 0) {
+                *err = 1.0;
+                tc::mbar_wait(&bar[b], ph, kBulkMaxPolls);
+            }
+            __syncthreads();
+            return;
+        }
+        const int64_t next = cell + gridDim.x;
+        if (next < a.ncell) stage(next, b ^ 1);
+        const float4* ub = s_u + b * NN * L4;
+        const float4* Bb = s_B + b * NN * SU;
+        const int* ib_ = s_idx + b * NN;
+        const float ck = 0.5f * s_g[b].w;
+        for (int it = tid; it < NN * L4; it += 256) {
+            const int j = it / L4, q = it - j * L4;
+            const int ia = j % P1, ib = (j / P1) % P1, ic = j / (P1 * P1);
+            const float4* u0 = ub + q;
+            float4 ax = make_float4(0.f, 0.f, 0.f, 0.f), ay = ax, az = ax;
+#pragma unroll
+            for (int m = 0; m < P1; ++m) {
+                f4fma(ax, s_K[ia * P1 + m], u0[(m + P1 * (ib + P1 * ic)) * L4]);
+                f4fma(ay, s_K[ib * P1 + m], u0[(ia + P1 * (m + P1 * ic)) * L4]);
+                f4fma(az, s_K[ic * P1 + m], u0[(ia + P1 * (ib + P1 * m)) * L4]);
+            }
+            float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+            f4fma(r, ck * s_w[ib] * s_w[ic], ax);
+            f4fma(r, ck * s_w[ia] * s_w[ic], ay);
+            f4fma(r, ck * s_w[ia] * s_w[ib], az);
+            const float4* Br = Bb + j * SU + q * n;
+            float2 m0 = make_float2(0.f, 0.f), m1 = m0;
+#pragma unroll
+            for (int c = 0; c < L4C; ++c) {
+                const float4 u = ub[j * L4 + c];
+                const float4 a0 = Br[c];
+                const float4 a1 = Br[L4C + c];
+                m0.x = fmaf(a0.x, u.x, fmaf(-a0.y, u.y, m0.x));
+                m0.y = fmaf(a0.x, u.y, fmaf(a0.y, u.x, m0.y));
+                m0.x = fmaf(a0.z, u.z, fmaf(-a0.w, u.w, m0.x));
+                m0.y = fmaf(a0.z, u.w, fmaf(a0.w, u.z, m0.y));
+                m1.x = fmaf(a1.x, u.x, fmaf(-a1.y, u.y, m1.x));
+                m1.y = fmaf(a1.x, u.y, fmaf(a1.y, u.x, m1.y));
+                m1.x = fmaf(a1.z, u.z, fmaf(-a1.w, u.w, m1.x));
+                m1.y = fmaf(a1.z, u.w, fmaf(a1.w, u.z, m1.y));
+            }
+            r.x += m0.x;
+            r.y += m0.y;
+            r.z += m1.x;
+            r.w += m1.y;
+            scatter32v(a, ib_[j], y, L4, q, r);
+        }
+    }
+}
+
 // Line-ordered form of the four-lane pass: the three 1D contractions run as
 // whole lines (each thread loads the P1 values of one line once and writes P1
 // outputs), accumulated direction by direction in shared memory, which cuts
@@ -1226,7 +1358,7 @@ int build_gcell_blocks32(const afem_mesh* m, const double* E, const float2* U, c
 // z = H1~ v + mean field (complex64, Dirichlet-masked) on the frozen blocks B;
 // err: a double that becomes 1 if a block copy did not complete.
 int launch_g_cell32_blocks(const afem_mesh* m, const float2* v, const float4* B, float2* z, int n, double* err,
-                           cudaStream_t s) {
+                           float4* vh, cudaStream_t s) {
     if (!aligned16(v) || !aligned16(z) || !aligned16(B))
         return set_error(AFEM_EINVAL, "G cell blocks: vectors must be 16-byte aligned");
     CellArgs32 a = make_cell_args32(m);
@@ -1237,6 +1369,27 @@ int launch_g_cell32_blocks(const afem_mesh* m, const float2* v, const float4* B,
     const unsigned grid = unsigned(m->dev.ncell);
     const float4* x4 = reinterpret_cast<const float4*>(v);
     float4* y4 = reinterpret_cast<float4*>(z);
+    if (vh && n <= 4 && m->gcell_blocks == 2) {
+        // pipelined persistent form: C v at the hanging points first
+        const int L4 = n / 2;
+        const int64_t nh = m->dev.n_hanging;
+        if (nh > 0) {
+            AFEM_LAUNCH((hang_expand32v_kernel), grid_for(nh * L4), 256, 0, s, m->dev.hang_ptr, m->dev.hang_master,
+                        m->dev.hang_w32, nh, m->dev.n_interior, x4, L4, vh);
+        }
+        const size_t smem = size_t(2) * 125 * (gblock_quads(n) + L4) * sizeof(float4) + size_t(2) * 125 * sizeof(int);
+        auto k = n == 2 ? gcell32p_kernel<1> : gcell32p_kernel<2>;
+        if (smem > 48 * 1024)
+            AFEM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        int per_sm = 0;
+        AFEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem));
+        if (per_sm < 1) per_sm = 1;
+        int64_t g = int64_t(per_sm) * device_sms();
+        if (g > m->dev.ncell) g = m->dev.ncell;
+        AFEM_LAUNCH((k), unsigned(g), 256, smem, s, a, x4, vh, B, y4, err);
+        AFEM_CUDA_TRY(cudaGetLastError());
+        return AFEM_OK;
+    }
     switch (n) {
 #define AFEM_GB_CASE(NO)                                                                                      \
     case NO: {                                                                                                \

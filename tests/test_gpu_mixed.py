@@ -101,13 +101,14 @@ CASES_N = [
 
 @pytest.mark.parametrize("case", CASES_N)
 @pytest.mark.parametrize("n", [1, 2, 3, 4, 6, 8])
-@pytest.mark.parametrize("blocks", [1, 0])
+@pytest.mark.parametrize("blocks", [1, 2, 0])
 def test_arnoldi_orbital_counts_with_mean_field(case, n, blocks):
     """The G cell pass with all n^2 mean fields for odd orbital counts (the
     scalar-lane kernel) and 1 to 4 float4 quads per node (n = 2, 4, 6, 8; 8
     orbitals and 64 fields as in the water workload), degrees 3 and 4, with
     the degree-4 precision form on frozen per-cell blocks staged by bulk copies
-    (blocks = 1) and with the mean-field rows gathered in the pass (0): one
+    (blocks = 1: one cell per thread block; 2: the pipelined persistent pass
+    for n <= 4) and with the mean-field rows gathered in the pass (0): one
     Krylov step of dimension 8, FP64 within 1e-10 of the oracle, the precision
     form within 1e-6."""
     import torch
