@@ -124,24 +124,33 @@ __global__ void __launch_bounds__(128, 1) integrals_tc_kernel(TcIntArgs a, doubl
         }
         __syncthreads();
         // 2. operand tiles: A rows 2 pq / 2 pq + 1 = Re / Im of m_f conj(phi_p) phi_q,
-        //    B row c = W column c; each value split into TF32 hi and lo
-        for (int it = tid; it < KT * nn; it += 128) {
-            const int t = it / nn, pq = it - t * nn;
-            const int p = pq / n, q = pq - p * n;
-            const float2 x = s_phi[t * 8 + p], y = s_phi[t * 8 + q];
-            const float mf = s_mf[t];
-            const float re = mf * fmaf(x.x, y.x, x.y * y.y);
-            const float im = mf * fmaf(x.x, y.y, -x.y * y.x);
-            const float wv = s_w[t * 64 + pq];
-            const float re_h = tc::tf32_round(re), im_h = tc::tf32_round(im), w_h = tc::tf32_round(wv);
-            const uint32_t oa0 = tc::tile_offset(2 * pq, t, KT), oa1 = tc::tile_offset(2 * pq + 1, t, KT);
-            const uint32_t ob = tc::tile_offset(pq, t, KT);
-            *reinterpret_cast<float*>(sAh + oa0) = re_h;
-            *reinterpret_cast<float*>(sAl + oa0) = tc::tf32_round(re - re_h);
-            *reinterpret_cast<float*>(sAh + oa1) = im_h;
-            *reinterpret_cast<float*>(sAl + oa1) = tc::tf32_round(im - im_h);
-            *reinterpret_cast<float*>(sBh + ob) = w_h;
-            *reinterpret_cast<float*>(sBl + ob) = tc::tf32_round(wv - w_h);
+        //    B row c = W column c; each value split into TF32 hi and lo.  A warp
+        //    writes one 8-row x 4-column core matrix per store (lane = 4 r + k,
+        //    128 contiguous bytes: no bank conflicts).
+        {
+            constexpr int KG = KT / 4;
+            const int a_cms = (2 * nn + 7) / 8 * KG;   // core matrices of A holding rows < 2 nn
+            const int b_cms = (nn + 7) / 8 * KG;
+            for (int cm = warp; cm < a_cms + b_cms; cm += 4) {
+                const bool isA = cm < a_cms;
+                const int c2 = isA ? cm : cm - a_cms;
+                const int row = (c2 / KG) * 8 + (lane >> 2), t = (c2 % KG) * 4 + (lane & 3);
+                float v = 0.f;
+                if (isA) {
+                    if (row < 2 * nn) {
+                        const int pq = row >> 1, p = pq / n, q = pq - p * n;
+                        const float2 x = s_phi[t * 8 + p], y = s_phi[t * 8 + q];
+                        v = s_mf[t] * ((row & 1) ? fmaf(x.x, y.y, -x.y * y.x) : fmaf(x.x, y.x, x.y * y.y));
+                    }
+                } else if (row < nn) {
+                    v = s_w[t * 64 + row];
+                }
+                const float h = tc::tf32_round(v);
+                float* hi = reinterpret_cast<float*>(isA ? sAh : sBh);
+                float* lo = reinterpret_cast<float*>(isA ? sAl : sBl);
+                hi[c2 * 32 + lane] = h;
+                lo[c2 * 32 + lane] = tc::tf32_round(v - h);
+            }
         }
         tc::fence_proxy_async();
         tc::fence_before_sync();

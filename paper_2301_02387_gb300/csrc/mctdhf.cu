@@ -585,7 +585,7 @@ __global__ void assemble_eri_kernel(int n, const double2* __restrict__ X, double
     }
 }
 
-static int int_blocks() { return 2 * device_sms(); }   // integral partial rows: 2 blocks per SM
+static int int_blocks() { return 4 * device_sms(); }   // integral partial rows: 4 blocks per SM
 constexpr int kTaylorTerms = 30;
 
 // ------------------------------------------------------------------ solver
