@@ -527,6 +527,38 @@ int afem_mctdhf_ci_dim(const afem_mctdhf* solver, int64_t* dim);
 int afem_mctdhf_step(afem_mctdhf* solver, void* phi, void* C, void* W, const double* E, double dt,
                      double cg_rtol, int cg_max_it, afem_step_info* info, void* stream);
 
+/* Batching form of the time step: one afem_mctdhf_step of each of `count`
+ * independent instances (solvers with their own meshes, sizes, degrees,
+ * orbital counts and arithmetic forms) per call.  Each instance computes
+ * exactly what afem_mctdhf_step computes for it; the batch shares the
+ * schedule: instances are spread over W worker streams (longest estimated
+ * cost first, instances that share a mesh on one worker), one host thread per
+ * stream issues its instances' steps, and the GPU overlaps them.  W is tuned
+ * on the batch's own steps: the first call (which allocates workspaces) runs
+ * on 4 streams, the next calls each try one of 1, 2, 4, 8, 16 (up to count),
+ * and later calls use the fastest (afem_batch_stepper_tuning).
+ * solvers: host array of `count` solver handles (caller-owned, kept alive
+ *   while the batch exists), all on the current device.
+ * phi, C, W: host arrays of `count` device pointers, each as afem_mctdhf_step
+ *   takes them; E: host [count][3] fields at t (NULL: field-free).
+ * infos: host [count] (may be NULL).  The caller's `stream` is ordered before
+ *   and after the batch by events; the call returns when every instance's
+ *   step has completed on the GPU.
+ * Returns the first hard error (with the instance number in the message),
+ * else AFEM_ECG_MAXIT if some instance's Poisson batch hit its limit.
+ * Kernel-class timing (afem_profile_enable) must be off during the call. */
+typedef struct afem_batch_stepper afem_batch_stepper;
+int afem_batch_stepper_create(afem_mctdhf* const* solvers, int count, afem_batch_stepper** out);
+int afem_batch_stepper_destroy(afem_batch_stepper* batch);
+int afem_batch_stepper_step(afem_batch_stepper* batch, void* const* phi, void* const* C, void* const* W,
+                            const double* E, double dt, double cg_rtol, int cg_max_it, afem_step_info* infos,
+                            void* stream);
+/* streams: the tuned worker count (0 while still tuning); cand_streams /
+ * cand_ms (host, n_candidates entries, each may be NULL): the candidates and
+ * their measured wall time per batched step. */
+int afem_batch_stepper_tuning(const afem_batch_stepper* batch, int* streams, int* n_candidates,
+                              int* cand_streams, double* cand_ms);
+
 /* ---- Differentiation form: the one-electron limit of the orbital step.
  * With one orbital and one configuration the mean fields and the projector
  * of Eq. orb_eom vanish and the step is the Schroedinger propagator of the

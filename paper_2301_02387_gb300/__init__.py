@@ -299,6 +299,70 @@ class MCTDHF:
             pass
 
 
+class BatchStepper:
+    """afem_batch_stepper_*: one MCTDHF step of every instance per call (the
+    batching form at the level of the time step).  solvers: MCTDHF objects
+    (kept alive by this object); each instance computes what its own
+    MCTDHF.step computes."""
+
+    def __init__(self, solvers):
+        self.solvers = list(solvers)
+        n = len(self.solvers)
+        arr = (ctypes.c_void_p * n)(*[s._h.value for s in self.solvers])
+        h = ctypes.c_void_p()
+        _capi.check(_capi.load().afem_batch_stepper_create(ctypes.cast(arr, ctypes.c_void_p), n, ctypes.byref(h)))
+        self._h = h
+
+    def step(self, phis, Cs, Ws, Es, dt, cg_rtol=1e-10, cg_max_it=20000, stream=None, raise_on_maxit=True):
+        import torch
+        n = len(self.solvers)
+        if not (len(phis) == len(Cs) == len(Ws) == n):
+            raise ValueError("one phi, C and W per instance")
+        for s, phi, C, W in zip(self.solvers, phis, Cs, Ws):
+            _dev_ptr(phi, torch.complex128, s.mesh.N, "phi")
+            _dev_ptr(C, torch.complex128, s.ci_dim, "C")
+            _dev_ptr(W, torch.float64, s.mesh.N, "W")
+        P = ctypes.c_void_p * n
+        pa = P(*[t.data_ptr() for t in phis])
+        ca = P(*[t.data_ptr() for t in Cs])
+        wa = P(*[t.data_ptr() for t in Ws])
+        Earr = None
+        if Es is not None:
+            flat = []
+            for e in Es:
+                flat.extend(float(v) for v in (e if e is not None else (0.0, 0.0, 0.0)))
+            Earr = (ctypes.c_double * (3 * n))(*flat)
+        infos = (_capi.StepInfo * n)()
+        rc = _capi.load().afem_batch_stepper_step(
+            self._h, ctypes.cast(pa, ctypes.c_void_p), ctypes.cast(ca, ctypes.c_void_p),
+            ctypes.cast(wa, ctypes.c_void_p), ctypes.cast(Earr, ctypes.c_void_p) if Earr is not None else None,
+            float(dt), float(cg_rtol), int(cg_max_it), ctypes.cast(infos, ctypes.c_void_p), _stream_ptr(stream))
+        if rc != _capi.AFEM_OK and (raise_on_maxit or rc != _capi.AFEM_ECG_MAXIT):
+            _capi.check(rc)
+        return [dict(energy=i.energy, arnoldi_err=i.arnoldi_err, cg_iters=i.cg_iters,
+                     krylov_substeps=i.krylov_substeps, dipole=tuple(i.dipole)) for i in infos]
+
+    def tuning(self):
+        streams, nc = ctypes.c_int(0), ctypes.c_int(0)
+        cs = (ctypes.c_int * 8)()
+        cm = (ctypes.c_double * 8)()
+        _capi.check(_capi.load().afem_batch_stepper_tuning(self._h, ctypes.byref(streams), ctypes.byref(nc),
+                                                           ctypes.cast(cs, ctypes.c_void_p),
+                                                           ctypes.cast(cm, ctypes.c_void_p)))
+        return {"streams": streams.value, "candidates": [(cs[i], cm[i]) for i in range(nc.value)]}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _capi.load().afem_batch_stepper_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def op_apply(mesh, kind, x, y, E=None, stream=None):
     """afem_op_apply: y = op(x) for all columns of x ([N, n_vec], DoF-major).
 

@@ -127,6 +127,12 @@ SIGNATURES = {
                                              ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]),
     "afem_poisson_boundary_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P]),
     "afem_two_electron_integrals": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P, ctypes.c_int, _P]),
+    "afem_batch_stepper_create": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P)]),
+    "afem_batch_stepper_destroy": (ctypes.c_int, [_P]),
+    "afem_batch_stepper_step": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                               _P, _P]),
+    "afem_batch_stepper_tuning": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                                 _P, _P]),
     "afem_arnoldi_step_ex": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                             ctypes.c_int, _P, _P, _P, _P, _P]),
     "afem_mctdhf_set_precision": (ctypes.c_int, [_P, ctypes.c_int]),

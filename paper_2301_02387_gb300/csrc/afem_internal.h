@@ -32,6 +32,16 @@ int64_t launch_count();
         kern<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);    \
     } while (0)
 
+// Lets kernel `func` use the device's opt-in maximum of dynamic shared memory
+// (less its static shared memory), once per device and kernel.  The limit is
+// only ever raised, to the same value, so launches from several host threads
+// cannot lower it below another launch's need.
+cudaError_t allow_dyn_smem_fn(const void* func);
+template <typename K>
+inline cudaError_t allow_dyn_smem(K func) {
+    return allow_dyn_smem_fn(reinterpret_cast<const void*>(func));
+}
+
 // Kernel-class timing (afem_profile_*): while enabled, a ProfScope brackets
 // the launches made in its lifetime with CUDA events on stream s and adds
 // `work` (the class's algorithmic flops or bytes) to the class.
@@ -195,6 +205,8 @@ void mesh_free_ecs(afem_mesh* m);
 int mctdhf_create(afem_mesh* m, int n, int na, int nb, int mk, afem_mctdhf** out);
 void mctdhf_destroy(afem_mctdhf* S);
 int64_t mctdhf_ci_dim(const afem_mctdhf* S);
+afem_mesh* mctdhf_mesh_of(const afem_mctdhf* S);
+int mctdhf_orbitals_of(const afem_mctdhf* S);
 void mctdhf_set_precision(afem_mctdhf* S, int precision);
 void mctdhf_set_krylov_tol(afem_mctdhf* S, double tol);
 void mctdhf_set_krylov_adaptive(afem_mctdhf* S, int steps);

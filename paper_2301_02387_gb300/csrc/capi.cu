@@ -1,18 +1,37 @@
 // C ABI entry points (declared in include/afem_mctdhf.h).
+#include <atomic>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <set>
+#include <utility>
 
 #include "afem_internal.h"
 #include "arnoldi.cuh"
-
-#include <atomic>
-
-#include <mutex>
 
 namespace afem {
 const char* last_error_cstr();
 static std::atomic<int64_t> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+cudaError_t allow_dyn_smem_fn(const void* func) {
+    static std::mutex mu;
+    static std::set<std::pair<int, const void*>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count({dev, func})) return cudaSuccess;
+    int optin = 0;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa{};
+    e = cudaFuncGetAttributes(&fa, func);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - int(fa.sharedSizeBytes));
+    if (e == cudaSuccess) done.insert({dev, func});
+    return e;
+}
 int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 // Kernel-class timing: event pairs are kept per class until read, events are

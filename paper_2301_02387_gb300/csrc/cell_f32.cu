@@ -1022,8 +1022,7 @@ static int launch32(const afem_mesh* m, const CellArgs32& a, const T* x, const f
             if (a.ecs_flags) k = cell32_kernel<PP, T, G, false, true>;                         \
         }                                                                                      \
         if (smem > 48 * 1024)                                                                  \
-            AFEM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                               int(smem)));                                    \
+            AFEM_CUDA_TRY(allow_dyn_smem(k));                                    \
         AFEM_LAUNCH((k), grid, 256, smem, s, a, x, U, y, nv);                                  \
         break;                                                                                 \
     }
@@ -1184,7 +1183,7 @@ static int launch32T_l(const afem_mesh* m, const CellArgs32& a, const float4* x,
     const size_t smem = cell32T_smem(PP, L2);
     auto k = a.pap_slots ? cell32T_kernel<PP, L2, true> : cell32T_kernel<PP, L2, false>;
     if (smem > 48 * 1024)
-        AFEM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        AFEM_CUDA_TRY(allow_dyn_smem(k));
     const unsigned items = unsigned((m->dev.ncell + CB - 1) / CB);
     AFEM_LAUNCH((k), items, 256, smem, s, a, x, y);
     AFEM_CUDA_TRY(cudaGetLastError());
@@ -1242,8 +1241,7 @@ static int launch32v(const afem_mesh* m, const CellArgs32& a, const float* x, co
     case PP: {                                                                                 \
         auto k = cell32L_kernel<PP, G>;                                                        \
         if (smemL > 48 * 1024)                                                                 \
-            AFEM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                               int(smemL)));                                   \
+            AFEM_CUDA_TRY(allow_dyn_smem(k));                                   \
         AFEM_LAUNCH((k), grid, 128, smemL, s, a, x4, U, y4, L4, n);                            \
         break;                                                                                 \
     }
@@ -1268,8 +1266,7 @@ static int launch32v(const afem_mesh* m, const CellArgs32& a, const float* x, co
     case PP: {                                                                                 \
         auto k = pick32v<PP, G>(L4, a.pap_slots != nullptr);                                   \
         if (smem > 48 * 1024)                                                                  \
-            AFEM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                               int(smem)));                                    \
+            AFEM_CUDA_TRY(allow_dyn_smem(k));                                    \
         AFEM_LAUNCH((k), items, 256, smem, s, a, x4, U, y4, L4, n);                            \
         break;                                                                                 \
     }
@@ -1380,7 +1377,7 @@ int launch_g_cell32_blocks(const afem_mesh* m, const float2* v, const float4* B,
         const size_t smem = size_t(2) * 125 * (gblock_quads(n) + L4) * sizeof(float4) + size_t(2) * 125 * sizeof(int);
         auto k = n == 2 ? gcell32p_kernel<1> : gcell32p_kernel<2>;
         if (smem > 48 * 1024)
-            AFEM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+            AFEM_CUDA_TRY(allow_dyn_smem(k));
         int per_sm = 0;
         AFEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem));
         if (per_sm < 1) per_sm = 1;
@@ -1395,8 +1392,7 @@ int launch_g_cell32_blocks(const afem_mesh* m, const float2* v, const float4* B,
     case NO: {                                                                                                \
         const size_t smem = size_t(125) * (gblock_quads(NO) + NO / 2) * sizeof(float4);                       \
         if (smem > 48 * 1024)                                                                                 \
-            AFEM_CUDA_TRY(cudaFuncSetAttribute(gcell32b_kernel<NO / 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                               int(smem)));                                                   \
+            AFEM_CUDA_TRY(allow_dyn_smem(gcell32b_kernel<NO / 2>));                                                   \
         AFEM_LAUNCH((gcell32b_kernel<NO / 2>), grid, 256, smem, s, a, x4, B, y4, err);                        \
         break;                                                                                                \
     }
@@ -1560,7 +1556,7 @@ int64_t batch32_items(int p, int L4, int64_t ncell) {
 int batch32_occupancy(int kind, int block, size_t smem, int* per_sm) {
     const void* k = kind == AFEM_OP_H1_C64 ? reinterpret_cast<const void*>(batch_cell32_kernel<true>)
                                            : reinterpret_cast<const void*>(batch_cell32_kernel<false>);
-    if (smem > 48 * 1024) AFEM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    if (smem > 48 * 1024) AFEM_CUDA_TRY(allow_dyn_smem(k));
     AFEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k, block, smem));
     if (*per_sm < 1) return set_error(AFEM_EINVAL, "afem_batch: the batched cell pass does not fit on an SM");
     return AFEM_OK;

@@ -216,8 +216,7 @@ __global__ void __launch_bounds__(128, 1) integrals_tc_kernel(TcIntArgs a, doubl
 template <int NC>
 int launch_tc(const TcIntArgs& a, double2* partial, int grid, int* status, cudaStream_t s) {
     const size_t smem = tc_int_smem(NC);
-    AFEM_CUDA_TRY(cudaFuncSetAttribute(integrals_tc_kernel<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       int(smem)));
+    AFEM_CUDA_TRY(allow_dyn_smem(integrals_tc_kernel<NC>));
     AFEM_LAUNCH((integrals_tc_kernel<NC>), grid, 128, smem, s, a, reinterpret_cast<double*>(partial), status);
     AFEM_CUDA_TRY(cudaGetLastError());
     return AFEM_OK;

@@ -682,7 +682,7 @@ static int pair_integrals(const afem_mesh* m, const double2* phi, const double* 
         const size_t ismem =
             size_t(kIntTile) * nn * (sizeof(double2) + sizeof(double)) + size_t(nn) * nn * sizeof(double2);
         AFEM_CUDA_TRY(
-            cudaFuncSetAttribute(integrals_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ismem)));
+            allow_dyn_smem(integrals_kernel));
         AFEM_LAUNCH((integrals_kernel), iblk, 256, ismem, s, ia, partial);
     }
     finalize_cpartials(partial, iblk, nn * nn, X, s);
@@ -798,7 +798,7 @@ int mctdhf_step(afem_mctdhf* S, double2* phi, double2* C, double* W, const doubl
     AFEM_CUDA_TRY(cudaGetLastError());
     // 4. mean-field operator fields and the orbital step
     const size_t usmem = size_t(nn) * nn * sizeof(double2);
-    AFEM_CUDA_TRY(cudaFuncSetAttribute(ufield_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(usmem)));
+    AFEM_CUDA_TRY(allow_dyn_smem(ufield_kernel));
     AFEM_LAUNCH((ufield_kernel), grid_for(N * nn), 256, usmem, s, n, N, w.M, W, w.U);
     AFEM_CUDA_TRY(cudaGetLastError());
     double err = 0.0;
@@ -894,6 +894,10 @@ void mctdhf_destroy(afem_mctdhf* S) {
 }
 
 int64_t mctdhf_ci_dim(const afem_mctdhf* S) { return S->ci.dim; }
+
+afem_mesh* mctdhf_mesh_of(const afem_mctdhf* S) { return S->mesh; }
+
+int mctdhf_orbitals_of(const afem_mctdhf* S) { return S->n; }
 
 void mctdhf_set_precision(afem_mctdhf* S, int precision) { S->precision = precision; }
 

@@ -268,8 +268,7 @@ int launch_g_cell(const afem_mesh* m, const double* E, const double2* v, const d
         auto k = a.vg ? g_cell_kernel<PP, true> : g_cell_kernel<PP, false>;                    \
         if (m->ecs_on) k = g_cell_kernel<PP, false, true>;                                     \
         if (smem > 48 * 1024)                                                                  \
-            AFEM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                               int(smem)));                                    \
+            AFEM_CUDA_TRY(allow_dyn_smem(k));                                    \
         AFEM_LAUNCH((k), grid, 256, smem, s, a, v, U, z, n);                                              \
         break;                                                                                 \
     }
@@ -345,8 +344,7 @@ static int launch_cell_op(const afem_mesh* m, const CellArgs& a, const T* x, T* 
             if (a.ecs.flags) k = cell_op_kernel<PP, T, false, true>;                           \
         }                                                                                      \
         if (smem > 48 * 1024)                                                                  \
-            AFEM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                               int(smem)));                                    \
+            AFEM_CUDA_TRY(allow_dyn_smem(k));                                    \
         AFEM_LAUNCH((k), grid, block, smem, s, a, x, y, nv);                                              \
         break;                                                                                 \
     }

@@ -712,8 +712,7 @@ int poisson_rhs_bc(afem_mesh* m, const double2* phi, int n, double* W, double* b
     a.cx = a.cy = a.cz = c0;
     AFEM_CUDA_TRY(cudaMemsetAsync(b, 0, size_t(D.n_master) * ncol * sizeof(double), s));
     const size_t smem = (size_t(kMomTile) * kNlm + size_t(kMomTile) * ncol + size_t(kNlm) * ncol) * sizeof(double);
-    AFEM_CUDA_TRY(cudaFuncSetAttribute(pair_rhs_moments_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       int(smem)));
+    AFEM_CUDA_TRY(allow_dyn_smem(pair_rhs_moments_kernel));
     const int nblk = mom_blocks();
     AFEM_LAUNCH((pair_rhs_moments_kernel), nblk, 256, smem, s, a, b, qpart);
     AFEM_CUDA_TRY(cudaGetLastError());
@@ -722,8 +721,7 @@ int poisson_rhs_bc(afem_mesh* m, const double2* phi, int n, double* W, double* b
     const int64_t nb = D.n_master - D.n_interior;
     if (nb > 0) {
         const size_t sm2 = size_t(kNlm) * ncol * sizeof(double);
-        AFEM_CUDA_TRY(cudaFuncSetAttribute(multipole_bc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           int(sm2)));
+        AFEM_CUDA_TRY(allow_dyn_smem(multipole_bc_kernel));
         AFEM_LAUNCH((multipole_bc_kernel), grid_for(nb, 128, 8), 128, sm2, s, q, ncol, D.master_xyz, D.n_interior,
                                                                           D.n_master, c0, c0, c0, W);
         AFEM_CUDA_TRY(cudaGetLastError());
@@ -852,16 +850,14 @@ int multipole_boundary(afem_mesh* m, const double2* phi, int n, double* W, doubl
     const double c0 = 0.5 * (m->desc.lo + m->desc.hi);
     a.cx = a.cy = a.cz = c0;
     const size_t smem = (size_t(kMomTile) * kNlm + size_t(kMomTile) * ncol + size_t(kNlm) * ncol) * sizeof(double);
-    AFEM_CUDA_TRY(cudaFuncSetAttribute(pair_rhs_moments_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       int(smem)));
+    AFEM_CUDA_TRY(allow_dyn_smem(pair_rhs_moments_kernel));
     AFEM_LAUNCH((pair_rhs_moments_kernel), nblk, 256, smem, s, a, static_cast<double*>(nullptr), qpart);
     AFEM_LAUNCH((finalize_columns_kernel), 1, 256, 0, s, qpart, nblk, kNlm * ncol, q);
     AFEM_CUDA_TRY(cudaGetLastError());
     const int64_t nb = D.n_master - D.n_interior;
     if (nb > 0) {
         const size_t sm2 = size_t(kNlm) * ncol * sizeof(double);
-        AFEM_CUDA_TRY(cudaFuncSetAttribute(multipole_bc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           int(sm2)));
+        AFEM_CUDA_TRY(allow_dyn_smem(multipole_bc_kernel));
         AFEM_LAUNCH((multipole_bc_kernel), grid_for(nb, 128, 8), 128, sm2, s, q, ncol, D.master_xyz,
                     D.n_interior, D.n_master, c0, c0, c0, W);
         AFEM_CUDA_TRY(cudaGetLastError());
