@@ -236,7 +236,7 @@ def run_batch(torch, pkg, inputs, reps=10, count=64):
                       "1-3 nuclei Z 1..8 within 3 bohr, 1-8 orbitals, |E| 0.01..0.08"}
 
 
-def run_batch_steps(torch, pkg, inputs, count=64, steps=2, dt=0.01, krylov_m=10):
+def run_batch_steps(torch, pkg, inputs, count=64, steps=1, dt=0.01, krylov_m=10):
     """Batching form at the level of the time step: one MCTDHF step of each of
     `count` seeded uneven instances (inputs.batch_instances: DoFs log-uniform
     5e4..2e6, p 2..4, 1-3 nuclei Z 1..8, 1-8 orbitals, N_e = min(sum Z, n)
