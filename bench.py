@@ -585,7 +585,7 @@ def run_poisson_solvers(torch, pkg, mesh, phi, W_warm, restore, reps=3):
 # Kernel classes of the library's event timing: name, bound, unit of work.
 PROF_CLASSES = {
     0: ("Gram-Schmidt passes (krylov_update / project*_dots, FP64)", "alu", "flops"),
-    1: ("complex64 G cell pass (cell32v_kernel_q4<true,L4,false>)", "hbm", "bytes"),
+    1: ("complex64 G cell pass (gcell32b_kernel on frozen per-cell blocks; cell32v_kernel_q4<true,L4,false> when gathered)", "hbm", "bytes"),
     2: ("float32 stiffness of the CG sweeps with the p.Ap epilogue (cell32v_kernel_q4<false,L4,true>)", "hbm", "bytes"),
     3: ("float32 CG vector kernels (update_beta4 / p_update4; p.Ap in the stiffness pass)", "hbm", "bytes"),
     4: ("FP64 cell passes (g_cell_kernel / cell_op_kernel)", "alu", "flops"),
@@ -594,10 +594,10 @@ PROF_CLASSES = {
 # (dram__bytes_read.sum + dram__bytes_write.sum, summed over a class's launches
 # of one Krylov substep / CG iteration and divided by the calls); class 0 is
 # captured on the reduced 16^3-coarse mesh of the molecule (N = 508,385) and
-# scaled by N to the benchmark mesh (every term is a whole-vector pass); None
-# where no capture of the current kernel exists (class 1: the G cell pass reads
-# the hanging points' mean fields from their own rows since its capture).
-TRAFFIC_PER_CALL = {0: 343.9e6, 1: None, 2: 114.9e6, 3: 341.8e6, 4: None}
+# scaled by N to the benchmark mesh (every term is a whole-vector pass); class 1
+# is the G cell pass on frozen per-cell blocks (gcell32b_kernel, one launch on
+# the benchmark mesh itself); None where no capture of the current kernel exists.
+TRAFFIC_PER_CALL = {0: 343.9e6, 1: 300.0e6, 2: 114.9e6, 3: 341.8e6, 4: None}
 
 
 def _class_rooflines(prof, total_ms, fp64_peak, hbm, peak_src):
@@ -1049,8 +1049,8 @@ def run_kernels_only(reps=3):
 
 
 def run_profile_step(inner_iters=48):
-    """One precision-form MCTDHF step of the workload with the Poisson inner CG
-    capped at `inner_iters` iterations and one Krylov step: every kernel of a
+    """One precision-form MCTDHF step of the workload (multigrid Poisson, inner
+    CG capped at `inner_iters` iterations) with one Krylov step: every kernel of a
     step appears, in a launch count small enough for a profiler's launch list."""
     import torch
     import paper_2301_02387_gb300 as pkg
@@ -1058,6 +1058,7 @@ def run_profile_step(inner_iters=48):
     torch.cuda.set_device(0)
     w = inputs.WORKLOADS[WORKLOAD]
     mesh, solver, phi0, C0 = setup_state(pkg, inputs, torch, w)
+    pkg.mesh_set_option(mesh, pkg.OPT_POISSON_SOLVER, pkg.POISSON_MULTIGRID)
     n = w["n_orb"]
     phi = torch.from_numpy(phi0).cuda()
     C = torch.from_numpy(C0).cuda()
