@@ -123,6 +123,29 @@ def test_batch_create_rejects_bad_inputs_host_side():
     assert lib.afem_batch_create(arr, 1, ctypes.byref(h)) == _capi.AFEM_EINVAL and not h.value
 
 
+def test_new_entry_points_reject_bad_inputs_host_side():
+    """The integrals entry, the batch stepper and the G-pass staging option
+    check their arguments before touching a device (host-only mesh, null
+    pointers, out-of-range values)."""
+    import ctypes
+    from paper_2301_02387_gb300 import _capi, Mesh, OPT_GCELL_BLOCKS
+    lib = _capi.load()
+    m = Mesh(-2.0, 2.0, 1, 2, [], 2.0, host_only=True)
+    dummy = ctypes.c_void_p(16)
+    assert lib.afem_two_electron_integrals(None, dummy, 2, dummy, dummy, 0, None) == _capi.AFEM_EINVAL
+    assert lib.afem_two_electron_integrals(m.handle, dummy, 2, dummy, dummy, 0, None) == _capi.AFEM_EINVAL
+    assert lib.afem_two_electron_integrals(m.handle, dummy, 2, dummy, dummy, 5, None) == _capi.AFEM_EINVAL
+    assert b"precision" in lib.afem_last_error()
+    h = ctypes.c_void_p()
+    assert lib.afem_batch_stepper_create(None, 0, ctypes.byref(h)) == _capi.AFEM_EINVAL and not h.value
+    arr = (ctypes.c_void_p * 1)(None)
+    assert lib.afem_batch_stepper_create(arr, 1, None) == _capi.AFEM_EINVAL
+    assert lib.afem_batch_stepper_step(None, None, None, None, None, 0.01, 1e-10, 10, None, None) == _capi.AFEM_EINVAL
+    assert lib.afem_batch_stepper_tuning(None, None, None, None, None) == _capi.AFEM_EINVAL
+    assert lib.afem_mesh_set_option(m.handle, OPT_GCELL_BLOCKS, 3) == _capi.AFEM_EINVAL
+    assert lib.afem_mesh_set_option(m.handle, OPT_GCELL_BLOCKS, 0) == _capi.AFEM_OK
+
+
 def test_tdse_entry_points_reject_bad_inputs_host_side():
     """afem_tdse_* refuse host-only meshes, negative step counts, non-positive
     dt, bad Krylov dimensions and missing checkpoints before any device work."""
