@@ -132,18 +132,6 @@ __device__ void solid_harmonics_order(double x, double y, double z, int m, doubl
     }
 }
 
-// Column c of the pair-density right-hand sides from orbital values at one point.
-// Order: c < n: |phi_c|^2; then for r < s: Re(conj(phi_r) phi_s), Im(...).
-__device__ __forceinline__ void pair_columns(const double2* ph, int n, double* rho) {
-    for (int r = 0; r < n; ++r) rho[r] = ph[r].x * ph[r].x + ph[r].y * ph[r].y;
-    int c = n;
-    for (int r = 0; r < n; ++r)
-        for (int s = r + 1; s < n; ++s) {
-            rho[c++] = ph[r].x * ph[s].x + ph[r].y * ph[s].y;
-            rho[c++] = ph[r].x * ph[s].y - ph[r].y * ph[s].x;
-        }
-}
-
 struct PointArgs {
     const double2* phi;     // [N][n]
     int n;
@@ -160,6 +148,10 @@ struct PointArgs {
 };
 
 // RHS b = 4 pi C^T (m_f o rho) (atomics into zeroed b) and per-block moment partials.
+// Per tile of kMomTile support points, every phase is spread over the block:
+// (point, orbital) items stage the orbital values (hanging points through C),
+// (point, column) items form m_f rho_c and the right-hand side, then the
+// harmonics and the moment contraction.
 __global__ void __launch_bounds__(256) pair_rhs_moments_kernel(PointArgs a, double* __restrict__ b,
                                                                double* __restrict__ qpart) {
     extern __shared__ __align__(16) double smem_d[];
@@ -167,63 +159,81 @@ __global__ void __launch_bounds__(256) pair_rhs_moments_kernel(PointArgs a, doub
     double* s_w = s_R + kMomTile * kNlm;           // [kMomTile][ncol]
     double* s_Q = s_w + kMomTile * a.ncol;         // [kNlm][ncol]
     __shared__ double4 s_pt[kMomTile];             // point relative to the centre, valid flag
-    const int ncol = a.ncol;
+    __shared__ double2 s_ph[kMomTile][8];          // orbital values at the tile's points
+    __shared__ double s_mf[kMomTile];
+    __shared__ int s_col[64];                      // column c -> r | s << 8 | part << 16
+    const int ncol = a.ncol, n = a.n;
     const int tid = threadIdx.x;
     for (int o = tid; o < kNlm * ncol; o += blockDim.x) s_Q[o] = 0.0;
+    if (tid == 0) {
+        int c = 0;
+        for (int r = 0; r < n; ++r) s_col[c++] = r | (r << 8);
+        for (int r = 0; r < n; ++r)
+            for (int t = r + 1; t < n; ++t) {
+                s_col[c++] = r | (t << 8);
+                s_col[c++] = r | (t << 8) | (1 << 16);
+            }
+    }
     const int64_t npts = a.N + a.nh;
     const int64_t ntiles = (npts + kMomTile - 1) / kMomTile;
-    double2 ph[8];
-    double rho[64];
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         __syncthreads();
-        if (tid < kMomTile) {
-            const int64_t f = tile * kMomTile + tid;
-            double* Rrow = s_R + tid * kNlm;
-            double* wrow = s_w + tid * ncol;
-            if (f < npts) {
-                double mf, x, y, z;
-                if (f < a.N) {
-                    const bool inner = f < a.n_int;
-                    for (int r = 0; r < a.n; ++r)
-                        ph[r] = inner ? a.phi[f * a.n + r] : make_double2(0.0, 0.0);
-                    mf = a.mf_m[f];
-                    x = a.xyz_m[3 * f];
-                    y = a.xyz_m[3 * f + 1];
-                    z = a.xyz_m[3 * f + 2];
-                } else {
-                    const int64_t h = f - a.N;
-                    for (int r = 0; r < a.n; ++r) ph[r] = make_double2(0.0, 0.0);
-                    for (int e = a.hp[h]; e < a.hp[h + 1]; ++e) {
-                        const int m = a.hm[e];
-                        if (m >= a.n_int) continue;
-                        for (int r = 0; r < a.n; ++r) vfma(ph[r], a.hw[e], a.phi[int64_t(m) * a.n + r]);
-                    }
-                    mf = a.mf_h[h];
-                    x = a.xyz_h[3 * h];
-                    y = a.xyz_h[3 * h + 1];
-                    z = a.xyz_h[3 * h + 2];
+        // orbital values (zero at surface masters; hanging points from interior masters)
+        for (int it = tid; it < kMomTile * n; it += blockDim.x) {
+            const int tp = it / n, r = it - tp * n;
+            const int64_t f = tile * kMomTile + tp;
+            double2 v = make_double2(0.0, 0.0);
+            if (f < a.N) {
+                if (f < a.n_int) v = a.phi[f * n + r];
+            } else if (f < npts) {
+                const int64_t h = f - a.N;
+                for (int e = a.hp[h]; e < a.hp[h + 1]; ++e) {
+                    const int m = a.hm[e];
+                    if (m >= a.n_int) continue;
+                    vfma(v, a.hw[e], a.phi[int64_t(m) * n + r]);
                 }
-                pair_columns(ph, a.n, rho);
-                for (int c = 0; c < ncol; ++c) wrow[c] = mf * rho[c];
-                // right-hand side through C^T
+            }
+            s_ph[tp][r] = v;
+        }
+        for (int tp = tid; tp < kMomTile; tp += blockDim.x) {
+            const int64_t f = tile * kMomTile + tp;
+            if (f < a.N) {
+                s_mf[tp] = a.mf_m[f];
+                s_pt[tp] = make_double4(a.xyz_m[3 * f] - a.cx, a.xyz_m[3 * f + 1] - a.cy, a.xyz_m[3 * f + 2] - a.cz,
+                                        1.0);
+            } else if (f < npts) {
+                const int64_t h = f - a.N;
+                s_mf[tp] = a.mf_h[h];
+                s_pt[tp] = make_double4(a.xyz_h[3 * h] - a.cx, a.xyz_h[3 * h + 1] - a.cy, a.xyz_h[3 * h + 2] - a.cz,
+                                        1.0);
+            } else {
+                s_mf[tp] = 0.0;
+                s_pt[tp] = make_double4(0.0, 0.0, 0.0, 0.0);
+            }
+        }
+        __syncthreads();
+        // m_f rho_c and the right-hand side through C^T
+        for (int it = tid; it < kMomTile * ncol; it += blockDim.x) {
+            const int tp = it / ncol, c = it - tp * ncol;
+            const int64_t f = tile * kMomTile + tp;
+            double wv = 0.0;
+            if (f < npts) {
+                const int code = s_col[c];
+                const double2 x = s_ph[tp][code & 0xFF], y = s_ph[tp][(code >> 8) & 0xFF];
+                const double rho = (code >> 16) ? x.x * y.y - x.y * y.x : x.x * y.x + x.y * y.y;
+                wv = s_mf[tp] * rho;
                 const double fpi = 4.0 * M_PI;
                 if (!b) {
                     // moments only
                 } else if (f < a.N) {
-                    for (int c = 0; c < ncol; ++c) atomicAdd(&b[f * ncol + c], fpi * wrow[c]);
+                    atomicAdd(&b[f * ncol + c], fpi * wv);
                 } else {
                     const int64_t h = f - a.N;
-                    for (int e = a.hp[h]; e < a.hp[h + 1]; ++e) {
-                        const int64_t m = a.hm[e];
-                        for (int c = 0; c < ncol; ++c) atomicAdd(&b[m * ncol + c], fpi * a.hw[e] * wrow[c]);
-                    }
+                    for (int e = a.hp[h]; e < a.hp[h + 1]; ++e)
+                        atomicAdd(&b[int64_t(a.hm[e]) * ncol + c], fpi * a.hw[e] * wv);
                 }
-                s_pt[tid] = make_double4(x - a.cx, y - a.cy, z - a.cz, 1.0);
-            } else {
-                for (int c = 0; c < ncol; ++c) wrow[c] = 0.0;
-                s_pt[tid] = make_double4(0.0, 0.0, 0.0, 0.0);
             }
-            (void)Rrow;
+            s_w[tp * ncol + c] = wv;
         }
         __syncthreads();
         // harmonics of the tile: 8 threads per point, orders m and m + 8
