@@ -268,6 +268,7 @@ def run_batch_steps(torch, pkg, inputs, count=64, steps=1, dt=0.01, krylov_m=10)
         states.append((torch.from_numpy(phi).cuda(), torch.from_numpy(inputs.initial_ci(n, na, nb)).cuda(),
                        torch.zeros((m.N, n * n), dtype=torch.float64, device="cuda")))
         Es.append(d["E"])
+    init = [tuple(x.clone() for x in st) for st in states]
     seq_states = [tuple(x.clone() for x in st) for st in states]
     batch = pkg.BatchStepper(solvers)
     args_ = ([st[0] for st in states], [st[1] for st in states], [st[2] for st in states], Es, dt)
@@ -284,12 +285,32 @@ def run_batch_steps(torch, pkg, inputs, count=64, steps=1, dt=0.01, krylov_m=10)
     for sv, st, e in zip(solvers, seq_states, Es):   # warm the one-by-one path's first step
         sv.step(st[0], st[1], st[2], e, dt, cg_rtol=1e-10, cg_max_it=20000, raise_on_maxit=False)
     torch.cuda.synchronize()
+    first_mixed = [(st[0].clone(), st[1].clone()) for st in seq_states]   # one precision-form step from init
     t2 = time.perf_counter()
     for _ in range(steps):
         for sv, st, e in zip(solvers, seq_states, Es):
             sv.step(st[0], st[1], st[2], e, dt, cg_rtol=1e-10, cg_max_it=20000, raise_on_maxit=False)
     torch.cuda.synchronize()
     t_seq = (time.perf_counter() - t2) / steps
+    # the plain FP64 path of the same instances, one by one from the initial
+    # state: a first step (compared with the precision form's first step) and
+    # `steps` timed ones
+    del seq_states
+    for sv in solvers:
+        sv.set_precision(pkg.PREC_FP64)
+    worst_phi = worst_ci = 0.0
+    for k, (sv, st, e) in enumerate(zip(solvers, init, Es)):
+        sv.step(st[0], st[1], st[2], e, dt, cg_rtol=1e-10, cg_max_it=20000, raise_on_maxit=False)
+        p32, c32 = first_mixed[k]
+        worst_phi = max(worst_phi, float(torch.linalg.norm(p32 - st[0]).item() / torch.linalg.norm(st[0]).item()))
+        worst_ci = max(worst_ci, float(torch.linalg.norm(c32 - st[1]).item() / torch.linalg.norm(st[1]).item()))
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    for _ in range(steps):
+        for sv, st, e in zip(solvers, init, Es):
+            sv.step(st[0], st[1], st[2], e, dt, cg_rtol=1e-10, cg_max_it=20000, raise_on_maxit=False)
+    torch.cuda.synchronize()
+    t_fp64 = (time.perf_counter() - t3) / steps
     tun = batch.tuning()
     batch.close()
     for sv in solvers:
@@ -298,6 +319,11 @@ def run_batch_steps(torch, pkg, inputs, count=64, steps=1, dt=0.01, krylov_m=10)
             "value": count / t_batch, "instances": count, "dofs": int(sum(m.N for m in meshes)),
             "ms_per_batched_step": t_batch * 1e3, "one_by_one": {"value": count / t_seq, "ms": t_seq * 1e3},
             "speedup_vs_one_by_one": t_seq / t_batch,
+            "one_by_one_fp64_path": {"value": count / t_fp64, "ms": t_fp64 * 1e3},
+            "speedup_vs_fp64_path": t_fp64 / t_batch,
+            "accuracy_vs_fp64_path": {"orbitals_rel_l2_max": worst_phi, "ci_rel_l2_max": worst_ci,
+                                      "note": "one step of every instance from the same initial state, precision "
+                                              "form against the FP64 path; worst instance"},
             "tuning": {"streams": tun["streams"],
                        "candidates_ms": [[c, round(ms, 2)] for c, ms in tun["candidates"]], "tuning_s": tune_s},
             "mode": f"precision form, one Krylov step of dimension {krylov_m} per time step, dt = {dt}, "
